@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the fast-hybrid 2D scattering path on GB300.
+
+One step = the whole path over one synthetic problem (kite obstacle, 40-pulse
+incident train over [0, 400], 256 frequencies on [0, 40], N_j by 8 points per
+wavelength (64..480), 1024 targets on r = 3, 4096 times up to T = 1e4):
+  a1 nodes/tables -> a2 CFIE assembly -> a3 LU + solve (255 frequency solves)
+  -> a4 window spectra (29 windows) -> a5 target fields -> a6 synthesis
+  weights -> a7 synthesis contraction.
+
+Headline `value`: frequency solves/s of whole steps with inputs resident in
+HBM (device-pointer entry points).  `e2e`: the same through the host-pointer
+C-ABI calls, host<->device copies included.  Also reported: time samples/s,
+per-step p50/p99 latency, the dominant kernel against its roofline, the
+oracle timed on the host cores, and SM clocks sampled during the timed
+region.  L2 is flushed (256 MiB write) between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--precision fp64|mixed]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fh_inputs as fi  # noqa: E402
+
+METRIC = "frequency solves/s & time samples/s at 1e-10 rel err (mixed vs FP64); p50/p99"
+WORKLOAD = "kite_pulses: kite, 40 pulses over [0,400], J=256 on [0,40], N=64..480 (8 ppw), 1024 targets, 4096 times to T=1e4"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------- algorithmic work
+
+def lu_flops(N):
+    """Complex LU with partial pivoting + one solve: (8/3) N^3 + 8 N^2 real flops."""
+    N = np.asarray(N, dtype=np.float64)
+    return float(np.sum(8.0 / 3.0 * N ** 3 + 8.0 * N ** 2))
+
+
+def contract_flops(n_x, n_T, J):
+    """u = [Vr|Vi][Gr;Gm]: 2 flops per multiply-add over inner dimension 2J."""
+    return 2.0 * n_x * n_T * 2 * J
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample_step(wl, n_solve=24, n_tgt=24):
+    """The oracle as it stands on a bounded sample of one step, extrapolated to
+    the whole step by unit counts.  Returns (est_step_seconds, description)."""
+    import oracle as O
+    S = wl.J - 1
+    js = np.unique(np.linspace(1, wl.J - 1, n_solve).round().astype(int))
+    t0 = time.perf_counter()
+    psi = {}
+    for j in js:
+        psi[j] = O.solve_density(wl.curve, int(wl.N[j]) // 2, float(wl.omega[j]), wl.c, wl.p)
+    t_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s, B = O.window_spectra(wl.a, wl.t0, wl.dt, wl.H, wl.omega)
+    t_spec = time.perf_counter() - t0
+    xs = wl.x[: 2 * n_tgt]
+    t0 = time.perf_counter()
+    for j in js:
+        O.target_field(wl.curve, int(wl.N[j]) // 2, float(wl.omega[j]), psi[j], xs, wl.c)
+    t_field = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((n_tgt, wl.J)) + 1j * rng.standard_normal((n_tgt, wl.J))
+    t0 = time.perf_counter()
+    O.synthesize(B, s, wl.omega, V, wl.T)
+    t_syn = time.perf_counter() - t0
+    # solves scale with the mix of N^3 actually sampled
+    n3 = np.asarray(wl.N[1:], dtype=float) ** 3
+    frac = float(np.sum(np.asarray(wl.N[js], dtype=float) ** 3) / np.sum(n3))
+    est = (t_solve / frac + t_spec + t_field * (S / len(js)) * (wl.n_x / n_tgt)
+           + t_syn * (wl.n_x / n_tgt))
+    desc = (f"oracle on {len(js)} of {S} solves (N^3-weighted), window spectra in full, "
+            f"target fields for {n_tgt} of {wl.n_x} targets at the sampled frequencies, "
+            f"synthesis for {n_tgt} targets x {wl.T.size} times; extrapolated to one step "
+            f"(measured {t_solve + t_spec + t_field + t_syn:.1f} s)")
+    return est, desc
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------- arms
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    wl = fi.kite_pulses()
+    S = wl.J - 1
+    for _ in range(args.warmup):
+        oracle_sample_step(wl, 2, 2)
+    ests = []
+    desc = ""
+    for _ in range(args.steps):
+        est, desc = oracle_sample_step(wl)
+        ests.append(est)
+    total = sum(ests)
+    value = S * args.steps / total
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(),
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_1807_02718_gb300 import build
+    from paper_1807_02718_gb300 import fh as F
+
+    build.build()
+    torch.cuda.set_device(local)
+    prec = F.FH_FP64 if args.precision == "fp64" else F.FH_MIXED_FP32
+    wl = fi.kite_pulses()
+    S = wl.J - 1
+    n_x, n_T = wl.n_x, wl.T.size
+    pr = F.Problem(local, prec)
+    stream = torch.cuda.current_stream()
+    F.fh_set_stream(pr.ctx, stream.cuda_stream)
+    dev = torch.device("cuda", local)
+    d_a = torch.tensor(wl.a, device=dev, dtype=torch.float64)
+    d_x = torch.tensor(wl.x, device=dev, dtype=torch.float64)
+    d_T = torch.tensor(wl.T, device=dev, dtype=torch.float64)
+    d_u = torch.empty(n_x * n_T, device=dev, dtype=torch.float64)
+    flush = torch.empty(256 * 1024 * 1024 // 8, device=dev, dtype=torch.float64)
+
+    def step():
+        F.fh_discretize(pr.ctx, wl.curve, wl.omega, wl.N, wl.c, wl.p)
+        F.fh_solve_frequencies(pr.ctx)
+        F.fh_window_spectra_dev(pr.ctx, d_a, wl.t0, wl.dt, wl.H)
+        F.fh_sample_dev(pr.ctx, d_x, d_T, d_u)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    F.fh_get_timings(pr.ctx, reset=True)
+
+    # ---- device-resident timed region ----
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = []
+    for k in range(args.steps):
+        flush.fill_(float(k))                      # L2 flush between steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(per_step)
+    tim = F.fh_get_timings(pr.ctx, reset=True)
+    launches = sum(v["launches"] for v in tim.values())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * S * args.steps / (total_ms / 1e3)
+    samples_per_s = world * n_x * n_T * args.steps / (total_ms / 1e3)
+
+    # ---- per-kernel timing pass (events around each kernel group) ----
+    F.fh_set_timing(pr.ctx, True)
+    reps = max(2, min(args.steps, 3))
+    for k in range(reps):
+        flush.fill_(float(k))
+        step()
+    phases = F.fh_get_timings(pr.ctx, reset=True)
+    F.fh_set_timing(pr.ctx, False)
+    per_launch = {n: (v["ms"] / v["events"] if v["events"] else 0.0) for n, v in phases.items()}
+    step_ms_phases = {n: v["ms"] / reps for n, v in phases.items()}
+    dominant = max(step_ms_phases, key=step_ms_phases.get)
+
+    # ---- end to end through the host-pointer API ----
+    u_host = np.empty((n_x, n_T))
+    e2e_times = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F.fh_discretize(pr.ctx, wl.curve, wl.omega, wl.N, wl.c, wl.p)
+        F.fh_solve_frequencies(pr.ctx)
+        F.fh_window_spectra(pr.ctx, wl.a, wl.t0, wl.dt, wl.H)
+        u_host = F.fh_sample(pr.ctx, wl.x, wl.T)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    assert np.all(np.isfinite(u_host))
+    h2d = wl.a.nbytes + wl.x.nbytes + wl.T.nbytes + wl.omega.nbytes + wl.N.nbytes
+    d2h = u_host.nbytes
+
+    # ---- roofline of the dominant kernel ----
+    fp64_peak = F.fh_probe_fma_peak(local, True, 4096)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if dominant == "factor":
+        work = lu_flops(wl.N[1:])
+        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "lu_solve_fp64_kernel",
+                "work_per_launch": work}
+        achieved = work / (per_launch["factor"] * 1e-3) / 1e12
+        roof.update({"achieved": achieved, "peak": fp64_peak,
+                     "peak_source": "measured FP64 FMA-chain probe on this GPU (fh_probe_fma_peak)"})
+    elif dominant == "contract":
+        work = contract_flops(n_x, n_T, wl.J)
+        achieved = work / (per_launch["contract"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "contract_kernel", "achieved": achieved,
+                "peak": fp64_peak, "peak_source": "measured FP64 FMA-chain probe on this GPU",
+                "work_per_launch": work}
+    else:
+        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": dominant, "achieved": None,
+                "peak": fp64_peak, "peak_source": "measured FP64 FMA-chain probe on this GPU"}
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["phase_ms_per_step"] = step_ms_phases
+    roof["hbm_peak_gbs"] = peaks.get("hbm_gbs")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, desc = oracle_sample_step(wl)
+        cpu = {"value": S / est, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "solves_per_step": S, "time_samples_per_step": n_x * n_T,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "time_samples_per_s": samples_per_s,
+            "p50_ms": float(np.percentile(per_step, 50)),
+            "p99_ms": float(np.percentile(per_step, 99)),
+            "e2e": {"value": world * S * args.steps / e2e_total, "unit": "solves/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": 1e3 * e2e_total / args.steps},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    pr.close()
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "gb300" and torch.cuda.is_available()) else "gloo"
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * fh.h -- C ABI of the GB300 fast-hybrid 2D scattering library (libfh).
+ *
+ * The library computes the time-domain field scattered by a 2D sound-soft
+ * obstacle under single-direction incidence by the frequency/time hybrid
+ * method of Anderson, Bruno & Lyon ("fast-hybrid" wave solver, Part I):
+ *
+ *   F3  J frequency-domain CFIE solves (Sec. 2.3, eq. CFIE_direct), one per
+ *       non-zero frequency of a fixed mesh, for plane-wave data e^{i kappa p.r};
+ *   F1-F2  recentred window spectra B_k^slow(omega_j) of the incident signal
+ *       (Sec. 3.1 eq. window_func; Sec. 3.2 eq. Bkslow_eqn);
+ *   F4-F5, T0-T6  target fields V(x, omega_j) = int psi G dsigma and the
+ *       band-limited, recentred Fourier synthesis (Sec. 3.2 eqs. Ukslow_repr,
+ *       ukW; Sec. 4.1 eqs. fourier_approx, approx) giving u(x, T) at any T at
+ *       a cost independent of T.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an fh_status.  On failure the outputs are untouched,
+ *    the context keeps its previous state, and fh_last_error() holds a message.
+ *  - Host pointers are owned by the caller and only read/written during the
+ *    call.  "_dev" variants take device pointers on the context's device; they
+ *    are stream-ordered on the context stream (fh_set_stream) and the caller
+ *    keeps them alive until that stream has passed the call.
+ *  - Device memory for densities, spectra and work space is owned by the
+ *    context and released by fh_destroy().
+ *  - Calls out of order (fh_sample before fh_solve_frequencies and
+ *    fh_window_spectra) return FH_ESTATE.
+ *  - A context is not thread-safe; use one context per thread / serving slot.
+ *  - Complex arrays are interleaved (re, im) doubles.
+ *  - The library never falls back to the CPU: without a usable CUDA device,
+ *    fh_create fails with FH_ECUDA.
+ */
+#ifndef FH_H
+#define FH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fh_ctx fh_ctx;
+
+typedef enum {
+    FH_OK = 0,
+    FH_EINVAL = 1,     /* invalid argument (message says which)            */
+    FH_ENOMEM = 2,     /* device allocation failed                         */
+    FH_ECUDA = 3,      /* CUDA runtime error (message has the CUDA string)  */
+    FH_ESTATE = 4,     /* call order: required earlier step missing        */
+    FH_ESINGULAR = 5,  /* zero or non-finite pivot in a frequency solve    */
+    FH_ENOCONV = 6,    /* iterative refinement did not reach its tolerance */
+    FH_ETIMEOUT = 7    /* a bounded device wait gave up                    */
+} fh_status;
+
+/* Precision of the frequency solves (fh_create). */
+enum {
+    FH_FP64 = 0,        /* assembly, LU and solve in IEEE binary64          */
+    FH_MIXED_FP32 = 1   /* FP64 assembly; FP32 LU; FP64 iterative refinement */
+};
+
+/* Obstacle descriptions: smooth closed curves, counter-clockwise in t. */
+enum {
+    FH_CURVE_CIRCLE = 0,  /* z = center + r0 (cos t, sin t)                          */
+    FH_CURVE_KITE = 1,    /* z = center + (cos t + 0.65 cos 2t - 0.65, 1.5 sin t)   */
+    FH_CURVE_STAR = 2     /* z = center + r(t)(cos t, sin t),
+                             r = r0 + sum_{k=1}^{n_harm} amp[k-1] cos(k t + phase[k-1]) */
+};
+#define FH_MAX_HARMONICS 16
+
+typedef struct {
+    int kind;
+    double r0;
+    int n_harm;
+    double amp[FH_MAX_HARMONICS];
+    double phase[FH_MAX_HARMONICS];
+    double center[2];
+} fh_curve;
+
+typedef struct {
+    int n_solves;            /* frequency solves performed (omega_j > 0)          */
+    int max_N;               /* largest boundary size                             */
+    long long matrix_entries;/* sum of N_j^2                                      */
+    int refine_iters_max;    /* FH_MIXED_FP32: most refinement sweeps of any solve */
+    double residual_max;     /* FH_MIXED_FP32: largest final relative residual     */
+} fh_solve_stats;
+
+/* Create a context on CUDA device `device` with solve precision `precision`
+ * (FH_FP64 or FH_MIXED_FP32).  *out receives the context.  The context owns a
+ * non-blocking CUDA stream until fh_set_stream selects another one.
+ * Errors: FH_EINVAL (bad precision / NULL out), FH_ECUDA (no such device). */
+fh_status fh_create(fh_ctx **out, int device, int precision);
+
+/* Release all device memory and the owned stream.  NULL is accepted. */
+void fh_destroy(fh_ctx *ctx);
+
+/* Message of the last failing call on this context ("" if none). */
+const char *fh_last_error(const fh_ctx *ctx);
+
+/* Use `cuda_stream` (a cudaStream_t on the context's device; NULL restores
+ * the context's own stream) for all later work of this context. */
+fh_status fh_set_stream(fh_ctx *ctx, void *cuda_stream);
+
+/* Steps F3 set-up (Sec. 5 "Overall algorithm", Sec. 2.3): fix the obstacle,
+ * the frequency mesh and the incidence direction.
+ *   curve   obstacle (host struct, copied)
+ *   J       number of frequencies, 2 <= J <= 4097
+ *   omega   J frequencies, ascending, uniform, omega[0] == 0 (host).  omega[J-1]
+ *           is the band limit W; the synthesis uses M = 2(J-1) full-band nodes.
+ *   N       J boundary sizes (host; N[j] even, 8 <= N[j] <= 8192); N[0] is
+ *           ignored (no solve at omega = 0).  NULL: N[j] = 64 for all j.
+ *   c       wave speed (> 0); kappa_j = omega_j / c
+ *   p       unit incidence direction (host, 2 doubles)
+ * The Nystrom nodes t_i = pi i / n (i < N = 2n) and z, z', z'' are computed on
+ * the device.  Invalidates earlier densities, spectra and target fields. */
+fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double *omega,
+                        const int *N, double c, const double p[2]);
+
+/* Step F3 (Sec. 5; eq. CFIE_direct): assemble and solve the J-1 CFIE systems
+ * A_j psi_j = g_j, g = dB/dn - i eta B for B = e^{i kappa p.r}.  Densities stay
+ * resident on the device.
+ *   eta    coupling per frequency (host, J doubles; eta[0] ignored) or NULL
+ *          for eta_j = omega_j.
+ *   stats  may be NULL.
+ * Errors: FH_ESTATE (no fh_discretize), FH_ESINGULAR (zero/non-finite pivot;
+ * the message names the frequency), FH_ENOCONV (mixed precision only). */
+fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *stats);
+
+/* Steps F1-F2 (Sec. 3.1 eq. window_func; Sec. 3.2 eqs. ak_signal_def,
+ * Bkslow_eqn): window spectra B_k^slow(omega_j) = int_{-H}^{H} w(tau)
+ * a(s_k + tau) e^{i omega_j tau} dtau by the trapezoidal rule on the sample
+ * grid, for s_k = 1.5 H (k-1), k = 1..K, K = #{k >= 1 : s_k - H < t_last}.
+ *   a          n_samples real samples a(t0 + q dt) (host); a = 0 outside them
+ *   t0, dt     sample grid; H/dt and (H + t0)/dt must be integers (1e-9)
+ *   H          window half-width (the paper uses H = 10)
+ * Requires fh_discretize.  Spectra stay resident on the device. */
+fh_status fh_window_spectra(fh_ctx *ctx, const double *a, int n_samples, double t0,
+                            double dt, double H);
+
+/* As fh_window_spectra with `d_a` in device memory. */
+fh_status fh_window_spectra_dev(fh_ctx *ctx, const double *d_a, int n_samples, double t0,
+                                double dt, double H);
+
+/* Steps F4-F5 and T0-T6 (Sec. 5): scattered field u(x_i, T_l).
+ *   x      2*n_x doubles, interleaved (x0, y0, x1, y1, ...) (host)
+ *   T      n_T sample times (host), any real values
+ *   u_out  n_x*n_T doubles, row-major by target (u_out[i*n_T + l]) (host)
+ * Target fields V(x, omega_j) are recomputed for every call (V(x, 0) := 1, the
+ * 2D low-frequency limit); the densities and spectra are reused, never
+ * re-solved.  n_x == 0 or n_T == 0 is a no-op.  Requires
+ * fh_solve_frequencies and fh_window_spectra. */
+fh_status fh_sample(fh_ctx *ctx, const double *x, int n_x, const double *T, int n_T,
+                    double *u_out);
+
+/* As fh_sample with device pointers d_x, d_T and d_u (same layouts). */
+fh_status fh_sample_dev(fh_ctx *ctx, const double *d_x, int n_x, const double *d_T, int n_T,
+                        double *d_u);
+
+/* ---- inspection of resident state (host buffers; used by parity tests) ---- */
+
+/* Number of windows K of the last fh_window_spectra. */
+fh_status fh_get_num_windows(fh_ctx *ctx, int *K);
+
+/* Window centres s (K doubles) and spectra B (K*J complex, B[k*J + j]). */
+fh_status fh_get_window_spectra(fh_ctx *ctx, double *s, double *B);
+
+/* Nodes of frequency j: z, dz, ddz as 2*N_j doubles each, interleaved. */
+fh_status fh_get_geometry(fh_ctx *ctx, int j, double *z, double *dz, double *ddz);
+
+/* Assemble the CFIE matrix of frequency j (coupling eta_j) into a scratch
+ * buffer and copy it out: A (N_j*N_j complex, row-major A[i*N_j + l]) and the
+ * right side g (N_j complex).  Does not change the context's state. */
+fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double *g);
+
+/* Density psi_j of frequency j (N_j complex) after fh_solve_frequencies. */
+fh_status fh_get_density(fh_ctx *ctx, int j, double *psi);
+
+/* Replace the resident densities by caller data (all j > 0 concatenated,
+ * sum_j N_j complex values) and mark them solved.  Lets the synthesis be
+ * checked independently of the solver. */
+fh_status fh_set_densities(fh_ctx *ctx, const double *psi_all);
+
+/* Target fields V(x_i, omega_j) of the last fh_sample (n_x*J complex,
+ * V[i*J + j]). */
+fh_status fh_get_target_field(fh_ctx *ctx, double *V);
+
+/* Synthesis only (steps T0-T6) from caller-given target fields V (n_x*J
+ * complex, V[i*J + j], host) and the resident spectra; u_out as fh_sample. */
+fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, int n_T,
+                        double *u_out);
+
+/* ---- kernel timing and launch accounting ---- */
+
+/* Phases of the path, in order: nodes and tables (a1), CFIE assembly with
+ * right sides (a2), LU + solve / refinement (a3), window spectra (a4),
+ * target fields (a5), synthesis weights (a6), synthesis contraction (a7). */
+enum { FH_PH_GEOMETRY = 0, FH_PH_ASSEMBLE, FH_PH_FACTOR, FH_PH_SPECTRA, FH_PH_FIELD,
+       FH_PH_WEIGHTS, FH_PH_CONTRACT, FH_NUM_PHASES };
+
+typedef struct {
+    double ms[FH_NUM_PHASES];           /* device time per phase (CUDA events) */
+    long long launches[FH_NUM_PHASES];  /* kernels launched per phase            */
+    long long events[FH_NUM_PHASES];    /* timed launch groups per phase         */
+} fh_timings;
+
+/* enable != 0: bracket every kernel group with CUDA events on the context
+ * stream (adds two event records per group).  Launch counts are always kept. */
+fh_status fh_set_timing(fh_ctx *ctx, int enable);
+
+/* Synchronise the context stream, fold pending event pairs into the totals,
+ * copy them to *out, and zero them if reset != 0. */
+fh_status fh_get_timings(fh_ctx *ctx, fh_timings *out, int reset);
+
+/* Measured FMA throughput of device `device` in TFLOP/s (2 flops per FMA):
+ * fp64 != 0 for binary64, else binary32; `iters` FMAs per chain (e.g. 4096).
+ * Not part of the scattering path: it gives the arithmetic roofline against
+ * which the ALU-bound kernels are reported. */
+fh_status fh_probe_fma_peak(int device, int fp64, int iters, double *tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FH_H */

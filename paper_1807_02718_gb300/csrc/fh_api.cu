@@ -1,0 +1,747 @@
+// libfh host library: the C ABI of include/fh.h.
+//
+// The context owns the device state of one scattering problem: nodes and
+// quadrature tables per frequency, the resident densities Psi (Sec. 3.2 eq.
+// psikslow_repr: one fixed set, reused for every window), the window spectra
+// B_k^slow, and work space for the target fields and synthesis weights.  All
+// work is stream-ordered on the context stream; host-pointer calls copy in,
+// launch, and copy out on that stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fh_internal.h"
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+}  // namespace
+
+struct fh_ctx {
+    int device = 0;
+    int precision = FH_FP64;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    bool geom = false, solved = false, spectra = false, have_V = false;
+    fh_curve curve{};
+    int J = 0, M = 0;
+    double W = 0.0, c = 1.0, p[2] = {1.0, 0.0};
+    std::vector<double> omega;
+    std::vector<int> Nj;
+
+    // frequency solves: s = 0..S-1 <-> j = s + 1
+    int S = 0, maxN = 0, n_tab = 0;
+    long long mat_total = 0, n_tiles = 0;
+    int vec_total = 0, tab_total = 0;
+    std::vector<int> solve_j, solve_N, vec_off, tab_of, tab_N, tab_off, order;
+    std::vector<long long> mat_off, tile_off;
+    std::vector<double> kappa_s, eta_s;
+
+    DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
+        d_order, d_tile_off;
+    DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_ph;
+    DevBuf d_A32, d_piv, d_g, d_iters, d_resid;
+
+    int K = 0;
+    double H = 10.0;
+    std::vector<double> s;
+    DevBuf d_s, d_B, d_wa, d_a, d_omega;
+
+    int n_x_last = 0;
+    DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm;
+
+    // single-matrix scratch for fh_assemble_matrix
+    DevBuf d_tmpA, d_tmpg, d_tmp_i, d_tmp_ll, d_tmp_d;
+
+    // timing: pending (phase, start, stop) event triples and totals
+    bool timing = false;
+    struct Pending { int phase; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    double ms[FH_NUM_PHASES] = {};
+    long long launches[FH_NUM_PHASES] = {};
+    long long groups[FH_NUM_PHASES] = {};
+
+    ~fh_ctx() {
+        DevBuf *all[] = {&d_N, &d_mat_off, &d_vec_off, &d_tab, &d_tab_off, &d_tab_N, &d_kappa,
+                         &d_eta, &d_solve_j, &d_order, &d_tile_off, &d_z, &d_dz, &d_ddz,
+                         &d_kress, &d_logsin, &d_A, &d_psi, &d_info, &d_nu, &d_ph, &d_A32,
+                         &d_piv, &d_g, &d_iters, &d_resid, &d_s, &d_B, &d_wa, &d_a, &d_omega,
+                         &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_tmpA, &d_tmpg, &d_tmp_i,
+                         &d_tmp_ll, &d_tmp_d};
+        for (DevBuf *b : all)
+            if (b->p) cudaFree(b->p);
+        for (auto &pe : pending) {
+            cudaEventDestroy(pe.a);
+            cudaEventDestroy(pe.b);
+        }
+        if (own) cudaStreamDestroy(own);
+    }
+};
+
+namespace {
+
+fh_status fail(fh_ctx *ctx, fh_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return st;
+}
+
+#define FH_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FH_ENOMEM : FH_ECUDA,         \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define FH_TRY(expr)                    \
+    do {                                \
+        fh_status s_ = (expr);          \
+        if (s_ != FH_OK) return s_;     \
+    } while (0)
+
+fh_status ensure(fh_ctx *ctx, DevBuf &b, size_t bytes) {
+    if (b.cap >= bytes && b.p) return FH_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(ctx, e == cudaErrorMemoryAllocation ? FH_ENOMEM : FH_ECUDA,
+                    "device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    }
+    b.cap = want;
+    return FH_OK;
+}
+
+template <class T>
+fh_status upload(fh_ctx *ctx, DevBuf &b, const std::vector<T> &v) {
+    FH_TRY(ensure(ctx, b, v.size() * sizeof(T)));
+    if (!v.empty())
+        FH_CUDA(ctx, cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    return FH_OK;
+}
+
+fh_status enter(fh_ctx *ctx) {
+    if (!ctx) return FH_EINVAL;
+    ctx->err.clear();
+    FH_CUDA(ctx, cudaSetDevice(ctx->device));
+    return FH_OK;
+}
+
+fh_status check_launch(fh_ctx *ctx, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    return FH_OK;
+}
+
+// Brackets one kernel group of a phase: counts its launches and, with
+// timing enabled, records CUDA events around it on the context stream.
+struct PhaseScope {
+    fh_ctx *ctx;
+    int phase;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PhaseScope(fh_ctx *c, int ph, int n_launch) : ctx(c), phase(ph) {
+        ctx->launches[ph] += n_launch;
+        if (ctx->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, ctx->stream);
+    }
+    ~PhaseScope() {
+        if (a && b) {
+            cudaEventRecord(b, ctx->stream);
+            ctx->pending.push_back({phase, a, b});
+        } else {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    }
+};
+
+fh::SolveTables tables(fh_ctx *ctx) {
+    fh::SolveTables t;
+    t.N = ctx->d_N.as<int>();
+    t.mat_off = ctx->d_mat_off.as<long long>();
+    t.vec_off = ctx->d_vec_off.as<int>();
+    t.tab = ctx->d_tab.as<int>();
+    t.tab_off = ctx->d_tab_off.as<int>();
+    t.kappa = ctx->d_kappa.as<double>();
+    t.eta = ctx->d_eta.as<double>();
+    return t;
+}
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+fh_status spectra_common(fh_ctx *ctx, const double *d_a, int n_samples, double t0, double dt,
+                         double H) {
+    if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_window_spectra: call fh_discretize first");
+    if (n_samples < 1) return fail(ctx, FH_EINVAL, "n_samples must be >= 1 (got %d)", n_samples);
+    if (!(dt > 0.0) || !is_fin(dt)) return fail(ctx, FH_EINVAL, "dt must be positive and finite");
+    if (!(H > 0.0) || !is_fin(H)) return fail(ctx, FH_EINVAL, "H must be positive and finite");
+    if (!is_fin(t0)) return fail(ctx, FH_EINVAL, "t0 must be finite");
+    const double qd = 2.0 * H / dt;
+    const long long Q = llround(qd);
+    if (Q < 2 || std::fabs(qd - (double)Q) > 1e-9 * std::max(1.0, qd) || Q > 50000000)
+        return fail(ctx, FH_EINVAL, "2H/dt = %.17g must be an integer in [2, 5e7]", qd);
+    const double stepd = 1.5 * H / dt;
+    const long long step = llround(stepd);
+    if (std::fabs(stepd - (double)step) > 1e-9 * std::max(1.0, stepd))
+        return fail(ctx, FH_EINVAL, "1.5H/dt = %.17g must be an integer", stepd);
+    const double t_last = t0 + (n_samples - 1) * dt;
+    int K = 0;
+    while (1.5 * H * K - H < t_last) {
+        ++K;
+        if (K > 1000000) return fail(ctx, FH_EINVAL, "too many windows");
+    }
+    K = std::max(K, 1);
+    std::vector<double> s(K);
+    long long start0 = 0;
+    for (int k = 0; k < K; ++k) {
+        s[k] = 1.5 * H * k;
+        const double sd = (s[k] - H - t0) / dt;
+        const long long st = llround(sd);
+        if (std::fabs(sd - (double)st) > 1e-6)
+            return fail(ctx, FH_EINVAL, "window start (s_k - H - t0)/dt = %.17g is not on the sample grid", sd);
+        if (k == 0) start0 = st;
+        else if (st != start0 + (long long)k * step)
+            return fail(ctx, FH_EINVAL, "window starts are not equispaced on the sample grid");
+    }
+    const size_t wa_bytes = (size_t)K * (size_t)(Q + 1) * sizeof(double);
+    FH_TRY(ensure(ctx, ctx->d_wa, wa_bytes));
+    FH_TRY(ensure(ctx, ctx->d_B, (size_t)K * ctx->J * sizeof(double2)));
+    FH_TRY(upload(ctx, ctx->d_s, s));
+    PhaseScope ps(ctx, FH_PH_SPECTRA, 2);
+    fh::launch_window_spectra(d_a, n_samples, start0, step, (int)Q, dt, H, K, ctx->J,
+                              ctx->d_omega.as<double>(), ctx->d_wa.as<double>(),
+                              ctx->d_B.as<double2>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "window spectra"));
+    ctx->K = K;
+    ctx->H = H;
+    ctx->s = s;
+    ctx->spectra = true;
+    return FH_OK;
+}
+
+fh_status synth_common(fh_ctx *ctx, int n_x, const double *d_T, int n_T, double *d_u) {
+    FH_TRY(ensure(ctx, ctx->d_Gr, (size_t)ctx->J * n_T * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_Gm, (size_t)ctx->J * n_T * sizeof(double)));
+    {
+    PhaseScope ps(ctx, FH_PH_WEIGHTS, 1);
+    fh::launch_synth_weights(ctx->J, ctx->M, ctx->W, ctx->K, ctx->d_s.as<double>(),
+                             ctx->d_B.as<double2>(), ctx->d_nu.as<double2>(),
+                             ctx->d_ph.as<double2>(), d_T, n_T, ctx->d_Gr.as<double>(),
+                             ctx->d_Gm.as<double>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "synthesis weights"));
+    }
+    PhaseScope ps(ctx, FH_PH_CONTRACT, 1);
+    fh::launch_synth_contract(ctx->J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Gr.as<double>(),
+                              ctx->d_Gm.as<double>(), d_u, ctx->stream);
+    return check_launch(ctx, "synthesis contraction");
+}
+
+fh_status sample_common(fh_ctx *ctx, const double *d_x, int n_x, const double *d_T, int n_T,
+                        double *d_u) {
+    FH_TRY(ensure(ctx, ctx->d_V, (size_t)ctx->J * n_x * sizeof(double2)));
+    {
+    PhaseScope ps(ctx, FH_PH_FIELD, ctx->S > 0 ? 2 : 1);
+    fh::launch_target_field(tables(ctx), ctx->S, ctx->d_solve_j.as<int>(), ctx->maxN,
+                            ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                            ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_V.as<double2>(),
+                            ctx->stream);
+    FH_TRY(check_launch(ctx, "target field"));
+    }
+    ctx->n_x_last = n_x;
+    ctx->have_V = true;
+    return synth_common(ctx, n_x, d_T, n_T, d_u);
+}
+
+fh_status check_sample_args(fh_ctx *ctx, int n_x, int n_T) {
+    if (!ctx->solved) return fail(ctx, FH_ESTATE, "fh_sample: call fh_solve_frequencies first");
+    if (!ctx->spectra) return fail(ctx, FH_ESTATE, "fh_sample: call fh_window_spectra first");
+    if (n_x < 0 || n_T < 0) return fail(ctx, FH_EINVAL, "n_x and n_T must be >= 0");
+    return FH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fh_status fh_create(fh_ctx **out, int device, int precision) {
+    if (!out) return FH_EINVAL;
+    *out = nullptr;
+    if (precision != FH_FP64 && precision != FH_MIXED_FP32) return FH_EINVAL;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return FH_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return FH_ECUDA;
+    fh_ctx *ctx = new fh_ctx();
+    ctx->device = device;
+    ctx->precision = precision;
+    if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return FH_ECUDA;
+    }
+    ctx->stream = ctx->own;
+    *out = ctx;
+    return FH_OK;
+}
+
+void fh_destroy(fh_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+}
+
+const char *fh_last_error(const fh_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+fh_status fh_set_stream(fh_ctx *ctx, void *cuda_stream) {
+    FH_TRY(enter(ctx));
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own;
+    return FH_OK;
+}
+
+fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double *omega,
+                        const int *N, double c, const double p[2]) {
+    FH_TRY(enter(ctx));
+    if (!curve || !omega || !p) return fail(ctx, FH_EINVAL, "curve, omega and p must be non-NULL");
+    if (curve->kind < FH_CURVE_CIRCLE || curve->kind > FH_CURVE_STAR)
+        return fail(ctx, FH_EINVAL, "unknown curve kind %d", curve->kind);
+    if (curve->kind == FH_CURVE_STAR && (curve->n_harm < 0 || curve->n_harm > FH_MAX_HARMONICS))
+        return fail(ctx, FH_EINVAL, "n_harm must be in [0, %d]", FH_MAX_HARMONICS);
+    if (curve->kind != FH_CURVE_KITE && !(curve->r0 > 0.0))
+        return fail(ctx, FH_EINVAL, "r0 must be positive");
+    if (J < 2 || J > 4097) return fail(ctx, FH_EINVAL, "J must be in [2, 4097] (got %d)", J);
+    if (!(c > 0.0) || !is_fin(c)) return fail(ctx, FH_EINVAL, "c must be positive");
+    const double pn = std::hypot(p[0], p[1]);
+    if (!(std::fabs(pn - 1.0) < 1e-12)) return fail(ctx, FH_EINVAL, "p must be a unit vector");
+    if (omega[0] != 0.0) return fail(ctx, FH_EINVAL, "omega[0] must be 0");
+    const double W = omega[J - 1];
+    if (!(W > 0.0) || !is_fin(W)) return fail(ctx, FH_EINVAL, "omega[J-1] must be positive");
+    const double dw = W / (J - 1);
+    for (int j = 0; j < J; ++j) {
+        if (!is_fin(omega[j]) || std::fabs(omega[j] - j * dw) > 1e-9 * W)
+            return fail(ctx, FH_EINVAL, "omega must be uniform on [0, W] (omega[%d] = %.17g)", j, omega[j]);
+    }
+    std::vector<int> Nv(J, 64);
+    if (N) for (int j = 0; j < J; ++j) Nv[j] = N[j];
+    for (int j = 1; j < J; ++j)
+        if (Nv[j] < 8 || Nv[j] > 8192 || (Nv[j] & 1))
+            return fail(ctx, FH_EINVAL, "N[%d] = %d must be even and in [8, 8192]", j, Nv[j]);
+
+    ctx->geom = ctx->solved = ctx->spectra = ctx->have_V = false;
+    ctx->curve = *curve;
+    ctx->J = J;
+    ctx->M = 2 * (J - 1);
+    ctx->W = W;
+    ctx->c = c;
+    ctx->p[0] = p[0] / pn;
+    ctx->p[1] = p[1] / pn;
+    ctx->omega.assign(omega, omega + J);
+    ctx->Nj = Nv;
+
+    const int S = J - 1;
+    ctx->S = S;
+    ctx->solve_j.resize(S);
+    ctx->solve_N.resize(S);
+    ctx->vec_off.resize(S);
+    ctx->mat_off.resize(S);
+    ctx->tab_of.resize(S);
+    ctx->tile_off.resize(S + 1);
+    ctx->kappa_s.resize(S);
+    ctx->eta_s.resize(S);
+    ctx->tab_N.clear();
+    ctx->tab_off.clear();
+    std::map<int, int> tab_index;
+    long long mo = 0, to = 0;
+    int vo = 0, tb = 0, maxN = 0;
+    for (int s = 0; s < S; ++s) {
+        const int j = s + 1, n = Nv[j];
+        ctx->solve_j[s] = j;
+        ctx->solve_N[s] = n;
+        ctx->vec_off[s] = vo;
+        ctx->mat_off[s] = mo;
+        ctx->tile_off[s] = to;
+        ctx->kappa_s[s] = omega[j] / c;
+        ctx->eta_s[s] = omega[j];
+        auto it = tab_index.find(n);
+        if (it == tab_index.end()) {
+            it = tab_index.emplace(n, (int)ctx->tab_N.size()).first;
+            ctx->tab_N.push_back(n);
+            ctx->tab_off.push_back(tb);
+            tb += n;
+        }
+        ctx->tab_of[s] = it->second;
+        vo += n;
+        mo += (long long)n * n;
+        const long long nt = (n + 31) / 32;
+        to += nt * nt;
+        maxN = std::max(maxN, n);
+    }
+    ctx->tile_off[S] = to;
+    ctx->vec_total = vo;
+    ctx->mat_total = mo;
+    ctx->n_tiles = to;
+    ctx->tab_total = tb;
+    ctx->n_tab = (int)ctx->tab_N.size();
+    ctx->maxN = maxN;
+    ctx->order.resize(S);
+    for (int s = 0; s < S; ++s) ctx->order[s] = s;
+    std::stable_sort(ctx->order.begin(), ctx->order.end(),
+                     [&](int a, int b) { return ctx->solve_N[a] > ctx->solve_N[b]; });
+
+    FH_TRY(upload(ctx, ctx->d_N, ctx->solve_N));
+    FH_TRY(upload(ctx, ctx->d_mat_off, ctx->mat_off));
+    FH_TRY(upload(ctx, ctx->d_vec_off, ctx->vec_off));
+    FH_TRY(upload(ctx, ctx->d_tab, ctx->tab_of));
+    FH_TRY(upload(ctx, ctx->d_tab_off, ctx->tab_off));
+    FH_TRY(upload(ctx, ctx->d_tab_N, ctx->tab_N));
+    FH_TRY(upload(ctx, ctx->d_kappa, ctx->kappa_s));
+    FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
+    FH_TRY(upload(ctx, ctx->d_solve_j, ctx->solve_j));
+    FH_TRY(upload(ctx, ctx->d_order, ctx->order));
+    FH_TRY(upload(ctx, ctx->d_tile_off, ctx->tile_off));
+    FH_TRY(upload(ctx, ctx->d_omega, ctx->omega));
+    FH_TRY(ensure(ctx, ctx->d_z, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_dz, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_ddz, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_psi, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_kress, (size_t)tb * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_logsin, (size_t)tb * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_A, (size_t)mo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_info, (size_t)S * sizeof(int)));
+    FH_TRY(ensure(ctx, ctx->d_nu, (size_t)fh::kFarTerms * J * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_ph, (size_t)ctx->M * sizeof(double2)));
+
+    fh::CurveParams cp{};
+    cp.kind = curve->kind;
+    cp.n_harm = curve->kind == FH_CURVE_STAR ? curve->n_harm : 0;
+    cp.r0 = curve->r0;
+    cp.cx = curve->center[0];
+    cp.cy = curve->center[1];
+    for (int k = 0; k < FH_MAX_HARMONICS; ++k) {
+        cp.amp[k] = curve->amp[k];
+        cp.phase[k] = curve->phase[k];
+    }
+    PhaseScope ps(ctx, FH_PH_GEOMETRY, 3);
+    fh::launch_geometry(cp, S, maxN, ctx->d_N.as<int>(), ctx->d_vec_off.as<int>(),
+                        ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(),
+                        ctx->stream);
+    FH_TRY(check_launch(ctx, "geometry"));
+    fh::launch_kress_tables(ctx->n_tab, maxN, ctx->d_tab_N.as<int>(), ctx->d_tab_off.as<int>(),
+                            ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "kress tables"));
+    fh::launch_far_table(J, ctx->M, ctx->d_nu.as<double2>(), ctx->d_ph.as<double2>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "far table"));
+    ctx->geom = true;
+    return FH_OK;
+}
+
+fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *stats) {
+    FH_TRY(enter(ctx));
+    if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_solve_frequencies: call fh_discretize first");
+    for (int s = 0; s < ctx->S; ++s) {
+        const double e = eta ? eta[ctx->solve_j[s]] : ctx->omega[ctx->solve_j[s]];
+        if (!is_fin(e)) return fail(ctx, FH_EINVAL, "eta[%d] is not finite", ctx->solve_j[s]);
+        ctx->eta_s[s] = e;
+    }
+    ctx->solved = false;
+    FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
+    const fh::SolveTables t = tables(ctx);
+    {
+    PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
+    fh::launch_assemble(t, ctx->S, ctx->d_tile_off.as<long long>(), ctx->n_tiles,
+                        ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(),
+                        ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(),
+                        ctx->d_A.as<double2>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "assemble"));
+    fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                   ctx->p[0], ctx->p[1], ctx->d_psi.as<double2>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "rhs"));
+    }
+    FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
+    int iters_max = 0;
+    double resid_max = 0.0;
+    if (ctx->precision == FH_FP64) {
+        PhaseScope ps(ctx, FH_PH_FACTOR, 1);
+        fh::launch_lu_solve_fp64(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
+                                 ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
+                                 ctx->d_A.as<double2>(), ctx->d_psi.as<double2>(),
+                                 ctx->d_info.as<int>(), ctx->stream);
+        FH_TRY(check_launch(ctx, "lu fp64"));
+    } else {
+        return fail(ctx, FH_EINVAL, "precision %d is not available in this build", ctx->precision);
+    }
+    std::vector<int> info(ctx->S);
+    FH_CUDA(ctx, cudaMemcpyAsync(info.data(), ctx->d_info.p, (size_t)ctx->S * sizeof(int),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int s = 0; s < ctx->S; ++s)
+        if (info[s] != 0)
+            return fail(ctx, FH_ESINGULAR, "frequency j=%d (omega=%.17g): zero or non-finite pivot in column %d",
+                        ctx->solve_j[s], ctx->omega[ctx->solve_j[s]], info[s] - 1);
+    ctx->solved = true;
+    if (stats) {
+        stats->n_solves = ctx->S;
+        stats->max_N = ctx->maxN;
+        stats->matrix_entries = ctx->mat_total;
+        stats->refine_iters_max = iters_max;
+        stats->residual_max = resid_max;
+    }
+    return FH_OK;
+}
+
+fh_status fh_window_spectra(fh_ctx *ctx, const double *a, int n_samples, double t0, double dt,
+                            double H) {
+    FH_TRY(enter(ctx));
+    if (!a) return fail(ctx, FH_EINVAL, "a must be non-NULL");
+    if (n_samples < 1) return fail(ctx, FH_EINVAL, "n_samples must be >= 1");
+    FH_TRY(ensure(ctx, ctx->d_a, (size_t)n_samples * sizeof(double)));
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_a.p, a, (size_t)n_samples * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    FH_TRY(spectra_common(ctx, ctx->d_a.as<double>(), n_samples, t0, dt, H));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FH_OK;
+}
+
+fh_status fh_window_spectra_dev(fh_ctx *ctx, const double *d_a, int n_samples, double t0,
+                                double dt, double H) {
+    FH_TRY(enter(ctx));
+    if (!d_a) return fail(ctx, FH_EINVAL, "d_a must be non-NULL");
+    return spectra_common(ctx, d_a, n_samples, t0, dt, H);
+}
+
+fh_status fh_sample(fh_ctx *ctx, const double *x, int n_x, const double *T, int n_T,
+                    double *u_out) {
+    FH_TRY(enter(ctx));
+    FH_TRY(check_sample_args(ctx, n_x, n_T));
+    if (n_x == 0 || n_T == 0) return FH_OK;
+    if (!x || !T || !u_out) return fail(ctx, FH_EINVAL, "x, T and u_out must be non-NULL");
+    FH_TRY(ensure(ctx, ctx->d_x, (size_t)2 * n_x * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_T, (size_t)n_T * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_u, (size_t)n_x * n_T * sizeof(double)));
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_x.p, x, (size_t)2 * n_x * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_T.p, T, (size_t)n_T * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    FH_TRY(sample_common(ctx, ctx->d_x.as<double>(), n_x, ctx->d_T.as<double>(), n_T,
+                         ctx->d_u.as<double>()));
+    FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FH_OK;
+}
+
+fh_status fh_sample_dev(fh_ctx *ctx, const double *d_x, int n_x, const double *d_T, int n_T,
+                        double *d_u) {
+    FH_TRY(enter(ctx));
+    FH_TRY(check_sample_args(ctx, n_x, n_T));
+    if (n_x == 0 || n_T == 0) return FH_OK;
+    if (!d_x || !d_T || !d_u) return fail(ctx, FH_EINVAL, "d_x, d_T and d_u must be non-NULL");
+    return sample_common(ctx, d_x, n_x, d_T, n_T, d_u);
+}
+
+fh_status fh_get_num_windows(fh_ctx *ctx, int *K) {
+    FH_TRY(enter(ctx));
+    if (!K) return fail(ctx, FH_EINVAL, "K must be non-NULL");
+    if (!ctx->spectra) return fail(ctx, FH_ESTATE, "no window spectra yet");
+    *K = ctx->K;
+    return FH_OK;
+}
+
+fh_status fh_get_window_spectra(fh_ctx *ctx, double *s, double *B) {
+    FH_TRY(enter(ctx));
+    if (!ctx->spectra) return fail(ctx, FH_ESTATE, "no window spectra yet");
+    if (s) std::memcpy(s, ctx->s.data(), ctx->s.size() * sizeof(double));
+    if (B) {
+        FH_CUDA(ctx, cudaMemcpyAsync(B, ctx->d_B.p, (size_t)ctx->K * ctx->J * sizeof(double2),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+        FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return FH_OK;
+}
+
+fh_status fh_get_geometry(fh_ctx *ctx, int j, double *z, double *dz, double *ddz) {
+    FH_TRY(enter(ctx));
+    if (!ctx->geom) return fail(ctx, FH_ESTATE, "call fh_discretize first");
+    if (j < 1 || j >= ctx->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
+    const int s = j - 1, n = ctx->solve_N[s];
+    const size_t off = (size_t)ctx->vec_off[s] * sizeof(double2), by = (size_t)n * sizeof(double2);
+    if (z) FH_CUDA(ctx, cudaMemcpyAsync(z, (char *)ctx->d_z.p + off, by, cudaMemcpyDeviceToHost, ctx->stream));
+    if (dz) FH_CUDA(ctx, cudaMemcpyAsync(dz, (char *)ctx->d_dz.p + off, by, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ddz) FH_CUDA(ctx, cudaMemcpyAsync(ddz, (char *)ctx->d_ddz.p + off, by, cudaMemcpyDeviceToHost, ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FH_OK;
+}
+
+fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double *g) {
+    FH_TRY(enter(ctx));
+    if (!ctx->geom) return fail(ctx, FH_ESTATE, "call fh_discretize first");
+    if (j < 1 || j >= ctx->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
+    if (!is_fin(eta_j)) return fail(ctx, FH_EINVAL, "eta_j must be finite");
+    const int s = j - 1, n = ctx->solve_N[s];
+    const long long nt = (n + 31) / 32;
+    // one-solve tables pointing at the context's node data and Kress tables
+    std::vector<int> iv = {n, ctx->vec_off[s], ctx->tab_of[s]};
+    std::vector<long long> lv = {0, 0, nt * nt};   // mat_off, tile_off[0], tile_off[1]
+    std::vector<double> dv = {ctx->kappa_s[s], eta_j};
+    FH_TRY(upload(ctx, ctx->d_tmp_i, iv));
+    FH_TRY(upload(ctx, ctx->d_tmp_ll, lv));
+    FH_TRY(upload(ctx, ctx->d_tmp_d, dv));
+    FH_TRY(ensure(ctx, ctx->d_tmpA, (size_t)n * n * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_tmpg, (size_t)ctx->vec_total * sizeof(double2)));
+    fh::SolveTables t;
+    t.N = ctx->d_tmp_i.as<int>();
+    t.vec_off = ctx->d_tmp_i.as<int>() + 1;
+    t.tab = ctx->d_tmp_i.as<int>() + 2;
+    t.tab_off = ctx->d_tab_off.as<int>();
+    t.mat_off = ctx->d_tmp_ll.as<long long>();
+    t.kappa = ctx->d_tmp_d.as<double>();
+    t.eta = ctx->d_tmp_d.as<double>() + 1;
+    fh::launch_assemble(t, 1, ctx->d_tmp_ll.as<long long>() + 1, nt * nt, ctx->d_z.as<double2>(),
+                        ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(),
+                        ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(),
+                        ctx->d_tmpA.as<double2>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "assemble (single)"));
+    // rhs for this one solve is written at the context's vector offset of s
+    fh::launch_rhs(t, 1, n, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(), ctx->p[0],
+                   ctx->p[1], ctx->d_tmpg.as<double2>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "rhs (single)"));
+    std::vector<double2> colmajor((size_t)n * n);
+    FH_CUDA(ctx, cudaMemcpyAsync(colmajor.data(), ctx->d_tmpA.p, colmajor.size() * sizeof(double2),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double2> gv(n);
+    FH_CUDA(ctx, cudaMemcpyAsync(gv.data(), (char *)ctx->d_tmpg.p + (size_t)ctx->vec_off[s] * sizeof(double2),
+                                 (size_t)n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (A)
+        for (int i = 0; i < n; ++i)
+            for (int l = 0; l < n; ++l) {
+                const double2 v = colmajor[(size_t)l * n + i];
+                A[2 * ((size_t)i * n + l)] = v.x;
+                A[2 * ((size_t)i * n + l) + 1] = v.y;
+            }
+    if (g) std::memcpy(g, gv.data(), (size_t)n * sizeof(double2));
+    return FH_OK;
+}
+
+fh_status fh_get_density(fh_ctx *ctx, int j, double *psi) {
+    FH_TRY(enter(ctx));
+    if (!ctx->solved) return fail(ctx, FH_ESTATE, "no densities yet");
+    if (j < 1 || j >= ctx->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
+    if (!psi) return fail(ctx, FH_EINVAL, "psi must be non-NULL");
+    const int s = j - 1;
+    FH_CUDA(ctx, cudaMemcpyAsync(psi, (char *)ctx->d_psi.p + (size_t)ctx->vec_off[s] * sizeof(double2),
+                                 (size_t)ctx->solve_N[s] * sizeof(double2), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FH_OK;
+}
+
+fh_status fh_set_densities(fh_ctx *ctx, const double *psi_all) {
+    FH_TRY(enter(ctx));
+    if (!ctx->geom) return fail(ctx, FH_ESTATE, "call fh_discretize first");
+    if (!psi_all) return fail(ctx, FH_EINVAL, "psi_all must be non-NULL");
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_psi.p, psi_all, (size_t)ctx->vec_total * sizeof(double2),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->solved = true;
+    return FH_OK;
+}
+
+fh_status fh_get_target_field(fh_ctx *ctx, double *V) {
+    FH_TRY(enter(ctx));
+    if (!ctx->have_V) return fail(ctx, FH_ESTATE, "no target field yet");
+    if (!V) return fail(ctx, FH_EINVAL, "V must be non-NULL");
+    const int n_x = ctx->n_x_last, J = ctx->J;
+    std::vector<double2> h((size_t)J * n_x);
+    FH_CUDA(ctx, cudaMemcpyAsync(h.data(), ctx->d_V.p, h.size() * sizeof(double2),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n_x; ++i)
+        for (int j = 0; j < J; ++j) {
+            V[2 * ((size_t)i * J + j)] = h[(size_t)j * n_x + i].x;
+            V[2 * ((size_t)i * J + j) + 1] = h[(size_t)j * n_x + i].y;
+        }
+    return FH_OK;
+}
+
+fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, int n_T,
+                        double *u_out) {
+    FH_TRY(enter(ctx));
+    if (!ctx->spectra) return fail(ctx, FH_ESTATE, "fh_synthesize: call fh_window_spectra first");
+    if (n_x < 0 || n_T < 0) return fail(ctx, FH_EINVAL, "n_x and n_T must be >= 0");
+    if (n_x == 0 || n_T == 0) return FH_OK;
+    if (!V || !T || !u_out) return fail(ctx, FH_EINVAL, "V, T and u_out must be non-NULL");
+    const int J = ctx->J;
+    std::vector<double2> h((size_t)J * n_x);
+    for (int i = 0; i < n_x; ++i)
+        for (int j = 0; j < J; ++j)
+            h[(size_t)j * n_x + i] = make_double2(V[2 * ((size_t)i * J + j)], V[2 * ((size_t)i * J + j) + 1]);
+    FH_TRY(upload(ctx, ctx->d_V, h));
+    ctx->n_x_last = n_x;
+    ctx->have_V = true;
+    FH_TRY(ensure(ctx, ctx->d_T, (size_t)n_T * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_u, (size_t)n_x * n_T * sizeof(double)));
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_T.p, T, (size_t)n_T * sizeof(double), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    FH_TRY(synth_common(ctx, n_x, ctx->d_T.as<double>(), n_T, ctx->d_u.as<double>()));
+    FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FH_OK;
+}
+
+fh_status fh_set_timing(fh_ctx *ctx, int enable) {
+    FH_TRY(enter(ctx));
+    ctx->timing = enable != 0;
+    return FH_OK;
+}
+
+fh_status fh_get_timings(fh_ctx *ctx, fh_timings *out, int reset) {
+    FH_TRY(enter(ctx));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto &pe : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+            ctx->ms[pe.phase] += ms;
+            ctx->groups[pe.phase] += 1;
+        }
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    ctx->pending.clear();
+    cudaGetLastError();
+    if (out)
+        for (int i = 0; i < FH_NUM_PHASES; ++i) {
+            out->ms[i] = ctx->ms[i];
+            out->launches[i] = ctx->launches[i];
+            out->events[i] = ctx->groups[i];
+        }
+    if (reset)
+        for (int i = 0; i < FH_NUM_PHASES; ++i) ctx->ms[i] = 0.0, ctx->launches[i] = 0, ctx->groups[i] = 0;
+    return FH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations of libfh: device-side parameter blocks and kernel
+// launchers.  Host library code (fh_api.cu) owns all state; the kernels only
+// see plain pointers and sizes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fh.h"
+
+namespace fh {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kEulerGamma = 0.57721566490153286061;
+
+// Obstacle parameters passed by value to the geometry kernel.
+struct CurveParams {
+    int kind;
+    int n_harm;
+    double r0;
+    double cx, cy;
+    double amp[FH_MAX_HARMONICS];
+    double phase[FH_MAX_HARMONICS];
+};
+
+// Per-solve tables (one entry per frequency with omega > 0).
+struct SolveTables {
+    const int *N;            // boundary size N_s (= 2 n_s)
+    const long long *mat_off;// element offset of matrix s (N_s^2 complex)
+    const int *vec_off;      // element offset of node data / density of s
+    const int *tab;          // index of the Kress / log-sin table for N_s
+    const int *tab_off;      // element offset of table t
+    const double *kappa;     // kappa_s = omega_s / c
+    const double *eta;       // CFIE coupling eta_s
+};
+
+// ---- geometry and quadrature tables (k_geometry.cu) ----
+void launch_geometry(const CurveParams &cp, int S, int maxN, const int *N, const int *vec_off,
+                     double2 *z, double2 *dz, double2 *ddz, cudaStream_t st);
+void launch_kress_tables(int n_tab, int maxN, const int *tab_N, const int *tab_off,
+                         double *kress, double *logsin, cudaStream_t st);
+
+// ---- CFIE assembly (k_assemble.cu) ----
+// Matrices are column-major: A_s(i, l) = A[mat_off[s] + l * N_s + i].
+void launch_assemble(const SolveTables &t, int S, const long long *tile_off, long long n_tiles,
+                     const double2 *z, const double2 *dz, const double2 *ddz,
+                     const double *kress, const double *logsin, double2 *A, cudaStream_t st);
+void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
+                double p0, double p1, double2 *g, cudaStream_t st);
+
+// ---- batched dense LU with partial pivoting and solve (k_lu.cu) ----
+// Solves A_s x = b_s in place (b_s overwritten by x_s); A_s overwritten by
+// its LU factors.  order[] lists solves largest first.  info[s] = 0 on
+// success, else 1 + column of the first zero / non-finite pivot.
+void launch_lu_solve_fp64(const int *order, int S, const int *N, const long long *mat_off,
+                          const int *vec_off, double2 *A, double2 *b, int *info, cudaStream_t st);
+
+// Mixed precision: FP32 copy of A, FP32 LU, FP64 residual refinement.
+void launch_convert_fp32(const double2 *A, float2 *A32, long long n, cudaStream_t st);
+void launch_lu_factor_fp32(const int *order, int S, const int *N, const long long *mat_off,
+                           float2 *A32, int *piv, const int *vec_off, int *info, cudaStream_t st);
+void launch_lu_refine(const int *order, int S, const int *N, const long long *mat_off,
+                      const int *vec_off, const double2 *A, const float2 *LU32, const int *piv,
+                      const double2 *g, double2 *x, int max_iters, double tol, int *iters,
+                      double *resid, int *info, cudaStream_t st);
+
+// ---- window spectra (k_window.cu) ----
+void launch_window_spectra(const double *a, int n_samples, long long start0, long long step,
+                           int Q, double dt, double H, int K, int J, const double *omega,
+                           double *wa_scratch, double2 *B, cudaStream_t st);
+
+// ---- target fields (k_field.cu) ----
+// V[j * n_x + i] = V(x_i, omega_j); V[0 * n_x + i] = 1 (omega_0 = 0).
+void launch_target_field(const SolveTables &t, int S, const int *solve_j, int maxN,
+                         const double2 *z, const double2 *dz, const double2 *psi,
+                         const double *x, int n_x, double2 *V, cudaStream_t st);
+
+// ---- synthesis (k_synth.cu) ----
+// nu[p * R + r] = sum_{m=-h}^{h-1} (-1)^m (m/h)^r e^{-2 pi i m p / M}.
+constexpr int kFarTerms = 60;
+void launch_far_table(int J, int M, double2 *nu, double2 *phase_tab, cudaStream_t st);
+// Gr/Gm: planes [p][t] with u(x,t) = sum_p Vr[p][x] Gr[p][t] + Vi[p][x] Gm[p][t].
+void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
+                          const double2 *nu, const double2 *phase_tab, const double *T,
+                          int n_T, double *Gr, double *Gm, cudaStream_t st);
+void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,
+                           const double *Gm, double *u, cudaStream_t st);
+
+}  // namespace fh

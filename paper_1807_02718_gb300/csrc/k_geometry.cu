@@ -1,0 +1,96 @@
+// Step a1: Nystrom nodes and curve derivatives; Kress log-kernel weights.
+//
+// Nodes t_i = pi i / n, i < N = 2n (Sec. 2.3, Nystrom method of Colton &
+// Kress Sec. 3.5 cited there).  Curves are the circle, the kite of Sec. 6.2
+// and star shapes r(t)(cos t, sin t).
+#include "fh_internal.h"
+
+namespace fh {
+namespace {
+
+__device__ void curve_eval(const CurveParams &cp, double t, double2 &z, double2 &dz,
+                           double2 &ddz) {
+    double s1, c1;
+    sincos(t, &s1, &c1);
+    if (cp.kind == FH_CURVE_KITE) {
+        double s2, c2;
+        sincos(2.0 * t, &s2, &c2);
+        z = make_double2(cp.cx + c1 + 0.65 * c2 - 0.65, cp.cy + 1.5 * s1);
+        dz = make_double2(-s1 - 1.3 * s2, 1.5 * c1);
+        ddz = make_double2(-c1 - 2.6 * c2, -1.5 * s1);
+        return;
+    }
+    double r = cp.r0, dr = 0.0, ddr = 0.0;
+    if (cp.kind == FH_CURVE_STAR) {
+        for (int k = 1; k <= cp.n_harm; ++k) {
+            double sk, ck;
+            sincos(k * t + cp.phase[k - 1], &sk, &ck);
+            const double a = cp.amp[k - 1];
+            r += a * ck;
+            dr += -k * a * sk;
+            ddr += -(double)(k * k) * a * ck;
+        }
+    }
+    z = make_double2(cp.cx + r * c1, cp.cy + r * s1);
+    dz = make_double2(dr * c1 - r * s1, dr * s1 + r * c1);
+    ddz = make_double2(ddr * c1 - 2.0 * dr * s1 - r * c1, ddr * s1 + 2.0 * dr * c1 - r * s1);
+}
+
+__global__ void geometry_kernel(CurveParams cp, const int *__restrict__ Ns,
+                                const int *__restrict__ vec_off, double2 *__restrict__ z,
+                                double2 *__restrict__ dz, double2 *__restrict__ ddz) {
+    const int s = blockIdx.y;
+    const int N = Ns[s];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n = N / 2;
+    const double t = kPi * (double)i / (double)n;
+    double2 a, b, c;
+    curve_eval(cp, t, a, b, c);
+    const int o = vec_off[s] + i;
+    z[o] = a;
+    dz[o] = b;
+    ddz[o] = c;
+}
+
+// R_d = -(2 pi / n) sum_{m=1}^{n-1} cos(m pi d / n) / m - (pi / n^2) cos(pi d)
+// and the log kernel ln(4 sin^2(pi d / N)) (d != 0), for d = 0..N-1.
+__global__ void kress_kernel(const int *__restrict__ tab_N, const int *__restrict__ tab_off,
+                             double *__restrict__ kress, double *__restrict__ logsin) {
+    const int tb = blockIdx.y;
+    const int N = tab_N[tb];
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= N) return;
+    const int n = N / 2;
+    double acc = 0.0;
+    for (int m = 1; m < n; ++m) {
+        const int q = (int)(((long long)m * d) % N);   // cos(pi m d / n) = cospi(q / n)
+        acc += cospi((double)q / (double)n) / (double)m;
+    }
+    const double sgn = (d & 1) ? -1.0 : 1.0;
+    kress[tab_off[tb] + d] = -(2.0 * kPi / n) * acc - (kPi / ((double)n * n)) * sgn;
+    double ls = 0.0;
+    if (d != 0) {
+        const double sv = sinpi((double)d / (double)N);
+        ls = log(4.0 * sv * sv);
+    }
+    logsin[tab_off[tb] + d] = ls;
+}
+
+}  // namespace
+
+void launch_geometry(const CurveParams &cp, int S, int maxN, const int *N, const int *vec_off,
+                     double2 *z, double2 *dz, double2 *ddz, cudaStream_t st) {
+    if (S <= 0) return;
+    dim3 grid((maxN + 127) / 128, S);
+    geometry_kernel<<<grid, 128, 0, st>>>(cp, N, vec_off, z, dz, ddz);
+}
+
+void launch_kress_tables(int n_tab, int maxN, const int *tab_N, const int *tab_off,
+                         double *kress, double *logsin, cudaStream_t st) {
+    if (n_tab <= 0) return;
+    dim3 grid((maxN + 127) / 128, n_tab);
+    kress_kernel<<<grid, 128, 0, st>>>(tab_N, tab_off, kress, logsin);
+}
+
+}  // namespace fh

@@ -1,0 +1,315 @@
+"""Thin Python binding of libfh (include/fh.h): argument marshalling only.
+
+Every function has the name of the C entry point it wraps and raises FHError
+on a non-zero status.  Every step of the scattering path runs in libfh's CUDA
+kernels; nothing here computes.  If libfh.so has not been built (see
+paper_1807_02718_gb300.build) the first call raises: there is no CPU fallback.
+
+Device-pointer variants accept torch CUDA tensors (float64, contiguous).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfh.so")
+
+FH_OK, FH_EINVAL, FH_ENOMEM, FH_ECUDA, FH_ESTATE, FH_ESINGULAR, FH_ENOCONV, FH_ETIMEOUT = range(8)
+FH_FP64, FH_MIXED_FP32 = 0, 1
+FH_CURVE_CIRCLE, FH_CURVE_KITE, FH_CURVE_STAR = 0, 1, 2
+FH_MAX_HARMONICS = 16
+
+STATUS_NAMES = {0: "FH_OK", 1: "FH_EINVAL", 2: "FH_ENOMEM", 3: "FH_ECUDA", 4: "FH_ESTATE",
+                5: "FH_ESINGULAR", 6: "FH_ENOCONV", 7: "FH_ETIMEOUT"}
+
+EXPORTED = [
+    "fh_create", "fh_destroy", "fh_last_error", "fh_set_stream", "fh_discretize",
+    "fh_solve_frequencies", "fh_window_spectra", "fh_window_spectra_dev", "fh_sample",
+    "fh_sample_dev", "fh_get_num_windows", "fh_get_window_spectra", "fh_get_geometry",
+    "fh_assemble_matrix", "fh_get_density", "fh_set_densities", "fh_get_target_field",
+    "fh_synthesize", "fh_set_timing", "fh_get_timings", "fh_probe_fma_peak",
+]
+
+PHASES = ["geometry", "assemble", "factor", "spectra", "field", "weights", "contract"]
+
+
+class fh_curve(C.Structure):
+    _fields_ = [("kind", C.c_int), ("r0", C.c_double), ("n_harm", C.c_int),
+                ("amp", C.c_double * FH_MAX_HARMONICS), ("phase", C.c_double * FH_MAX_HARMONICS),
+                ("center", C.c_double * 2)]
+
+
+class fh_solve_stats(C.Structure):
+    _fields_ = [("n_solves", C.c_int), ("max_N", C.c_int), ("matrix_entries", C.c_longlong),
+                ("refine_iters_max", C.c_int), ("residual_max", C.c_double)]
+
+
+class fh_timings(C.Structure):
+    _fields_ = [("ms", C.c_double * 7), ("launches", C.c_longlong * 7), ("events", C.c_longlong * 7)]
+
+
+class FHError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+
+
+def load_library(path: str | None = None):
+    """Load libfh.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfh.so not found at {path}; build it first "
+                           "(python -m paper_1807_02718_gb300.build)")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    sig = {
+        "fh_create": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int]),
+        "fh_destroy": (None, [vp]),
+        "fh_last_error": (C.c_char_p, [vp]),
+        "fh_set_stream": (C.c_int, [vp, vp]),
+        "fh_discretize": (C.c_int, [vp, C.POINTER(fh_curve), C.c_int, _DP, _IP, C.c_double, _DP]),
+        "fh_solve_frequencies": (C.c_int, [vp, _DP, C.POINTER(fh_solve_stats)]),
+        "fh_window_spectra": (C.c_int, [vp, _DP, C.c_int, C.c_double, C.c_double, C.c_double]),
+        "fh_window_spectra_dev": (C.c_int, [vp, vp, C.c_int, C.c_double, C.c_double, C.c_double]),
+        "fh_sample": (C.c_int, [vp, _DP, C.c_int, _DP, C.c_int, _DP]),
+        "fh_sample_dev": (C.c_int, [vp, vp, C.c_int, vp, C.c_int, vp]),
+        "fh_get_num_windows": (C.c_int, [vp, _IP]),
+        "fh_get_window_spectra": (C.c_int, [vp, _DP, _DP]),
+        "fh_get_geometry": (C.c_int, [vp, C.c_int, _DP, _DP, _DP]),
+        "fh_assemble_matrix": (C.c_int, [vp, C.c_int, C.c_double, _DP, _DP]),
+        "fh_get_density": (C.c_int, [vp, C.c_int, _DP]),
+        "fh_set_densities": (C.c_int, [vp, _DP]),
+        "fh_get_target_field": (C.c_int, [vp, _DP]),
+        "fh_synthesize": (C.c_int, [vp, _DP, C.c_int, _DP, C.c_int, _DP]),
+        "fh_set_timing": (C.c_int, [vp, C.c_int]),
+        "fh_get_timings": (C.c_int, [vp, C.POINTER(fh_timings), C.c_int]),
+        "fh_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(ctx, st):
+    if st != FH_OK:
+        msg = load_library().fh_last_error(ctx).decode() if ctx else ""
+        raise FHError(st, msg)
+
+
+def _dev_ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def make_curve(curve) -> fh_curve:
+    """fh_curve from an object with kind, r0, amp, phase, center (e.g. fh_inputs.Curve)."""
+    c = fh_curve()
+    c.kind = int(curve.kind)
+    c.r0 = float(curve.r0)
+    amp = list(getattr(curve, "amp", []) or [])
+    ph = list(getattr(curve, "phase", []) or [])
+    c.n_harm = len(amp)
+    for k, (a, p) in enumerate(zip(amp, ph)):
+        c.amp[k] = a
+        c.phase[k] = p
+    c.center[0], c.center[1] = curve.center
+    return c
+
+
+# ---------------------------------------------------------------- entry points
+
+def fh_create(device: int = 0, precision: int = FH_FP64):
+    lib = load_library()
+    h = C.c_void_p()
+    st = lib.fh_create(C.byref(h), device, precision)
+    if st != FH_OK:
+        raise FHError(st, f"fh_create(device={device}, precision={precision}) failed")
+    return h
+
+
+def fh_destroy(ctx):
+    load_library().fh_destroy(ctx)
+
+
+def fh_last_error(ctx) -> str:
+    return load_library().fh_last_error(ctx).decode()
+
+
+def fh_set_stream(ctx, stream_handle: int | None):
+    _check(ctx, load_library().fh_set_stream(ctx, C.c_void_p(stream_handle or 0)))
+
+
+def fh_discretize(ctx, curve, omega, N=None, c: float = 1.0, p=(1.0, 0.0)):
+    om = _f64(omega)
+    Nv = None if N is None else np.ascontiguousarray(N, dtype=np.int32)
+    cv = curve if isinstance(curve, fh_curve) else make_curve(curve)
+    pv = _f64(p)
+    _check(ctx, load_library().fh_discretize(ctx, C.byref(cv), om.size, _dp(om),
+                                             None if Nv is None else Nv.ctypes.data_as(_IP),
+                                             float(c), _dp(pv)))
+
+
+def fh_solve_frequencies(ctx, eta=None) -> fh_solve_stats:
+    st = fh_solve_stats()
+    e = None if eta is None else _f64(eta)
+    _check(ctx, load_library().fh_solve_frequencies(ctx, _dp(e), C.byref(st)))
+    return st
+
+
+def fh_window_spectra(ctx, a, t0: float, dt: float, H: float = 10.0):
+    av = _f64(a)
+    _check(ctx, load_library().fh_window_spectra(ctx, _dp(av), av.size, float(t0), float(dt), float(H)))
+
+
+def fh_window_spectra_dev(ctx, d_a, t0: float, dt: float, H: float = 10.0):
+    _check(ctx, load_library().fh_window_spectra_dev(ctx, _dev_ptr(d_a), d_a.numel(), float(t0),
+                                                     float(dt), float(H)))
+
+
+def fh_sample(ctx, x, T):
+    xv, Tv = _f64(x), _f64(T)
+    n_x, n_T = xv.size // 2, Tv.size
+    u = np.empty((n_x, n_T), dtype=np.float64)
+    _check(ctx, load_library().fh_sample(ctx, _dp(xv), n_x, _dp(Tv), n_T, _dp(u)))
+    return u
+
+
+def fh_sample_dev(ctx, d_x, d_T, d_u):
+    n_x, n_T = d_x.numel() // 2, d_T.numel()
+    if d_u.numel() != n_x * n_T:
+        raise ValueError("d_u must hold n_x * n_T doubles")
+    _check(ctx, load_library().fh_sample_dev(ctx, _dev_ptr(d_x), n_x, _dev_ptr(d_T), n_T,
+                                             _dev_ptr(d_u)))
+
+
+def fh_get_num_windows(ctx) -> int:
+    K = C.c_int()
+    _check(ctx, load_library().fh_get_num_windows(ctx, C.byref(K)))
+    return K.value
+
+
+def fh_get_window_spectra(ctx, J: int):
+    K = fh_get_num_windows(ctx)
+    s = np.empty(K)
+    B = np.empty((K, J), dtype=np.complex128)
+    _check(ctx, load_library().fh_get_window_spectra(ctx, _dp(s), B.ctypes.data_as(_DP)))
+    return s, B
+
+
+def fh_get_geometry(ctx, j: int, N: int):
+    z = np.empty(N, dtype=np.complex128)
+    dz = np.empty(N, dtype=np.complex128)
+    ddz = np.empty(N, dtype=np.complex128)
+    _check(ctx, load_library().fh_get_geometry(ctx, j, z.ctypes.data_as(_DP), dz.ctypes.data_as(_DP),
+                                               ddz.ctypes.data_as(_DP)))
+    return z, dz, ddz
+
+
+def fh_assemble_matrix(ctx, j: int, eta_j: float, N: int):
+    A = np.empty((N, N), dtype=np.complex128)
+    g = np.empty(N, dtype=np.complex128)
+    _check(ctx, load_library().fh_assemble_matrix(ctx, j, float(eta_j), A.ctypes.data_as(_DP),
+                                                  g.ctypes.data_as(_DP)))
+    return A, g
+
+
+def fh_get_density(ctx, j: int, N: int):
+    psi = np.empty(N, dtype=np.complex128)
+    _check(ctx, load_library().fh_get_density(ctx, j, psi.ctypes.data_as(_DP)))
+    return psi
+
+
+def fh_set_densities(ctx, psi_all):
+    v = np.ascontiguousarray(psi_all, dtype=np.complex128)
+    _check(ctx, load_library().fh_set_densities(ctx, v.ctypes.data_as(_DP)))
+
+
+def fh_get_target_field(ctx, n_x: int, J: int):
+    V = np.empty((n_x, J), dtype=np.complex128)
+    _check(ctx, load_library().fh_get_target_field(ctx, V.ctypes.data_as(_DP)))
+    return V
+
+
+def fh_synthesize(ctx, V, T):
+    Vv = np.ascontiguousarray(V, dtype=np.complex128)
+    Tv = _f64(T)
+    n_x = Vv.shape[0]
+    u = np.empty((n_x, Tv.size), dtype=np.float64)
+    _check(ctx, load_library().fh_synthesize(ctx, Vv.ctypes.data_as(_DP), n_x, _dp(Tv), Tv.size,
+                                             _dp(u)))
+    return u
+
+
+def fh_set_timing(ctx, enable: bool):
+    _check(ctx, load_library().fh_set_timing(ctx, 1 if enable else 0))
+
+
+def fh_get_timings(ctx, reset: bool = False) -> dict:
+    t = fh_timings()
+    _check(ctx, load_library().fh_get_timings(ctx, C.byref(t), 1 if reset else 0))
+    return {name: {"ms": t.ms[i], "launches": t.launches[i], "events": t.events[i]}
+            for i, name in enumerate(PHASES)}
+
+
+def fh_probe_fma_peak(device: int = 0, fp64: bool = True, iters: int = 4096) -> float:
+    v = C.c_double()
+    st = load_library().fh_probe_fma_peak(device, 1 if fp64 else 0, iters, C.byref(v))
+    if st != FH_OK:
+        raise FHError(st, "fh_probe_fma_peak failed")
+    return v.value
+
+
+class Problem:
+    """Owns one context: discretise, solve, window, sample (numpy in/out)."""
+
+    def __init__(self, device: int = 0, precision: int = FH_FP64):
+        self.ctx = fh_create(device, precision)
+        self.J = 0
+
+    def close(self):
+        if self.ctx:
+            fh_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def discretize(self, curve, omega, N=None, c=1.0, p=(1.0, 0.0)):
+        fh_discretize(self.ctx, curve, omega, N, c, p)
+        self.J = len(omega)
+
+    def solve(self, eta=None):
+        return fh_solve_frequencies(self.ctx, eta)
+
+    def window_spectra(self, a, t0, dt, H=10.0):
+        fh_window_spectra(self.ctx, a, t0, dt, H)
+
+    def sample(self, x, T):
+        return fh_sample(self.ctx, x, T)
