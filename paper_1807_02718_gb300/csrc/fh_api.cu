@@ -191,6 +191,10 @@ fh::SolveTables tables(fh_ctx *ctx) {
 
 bool is_fin(double v) { return std::isfinite(v); }
 
+// Mixed precision: refinement stops when ||dx||_inf <= kRefineTol ||x||_inf.
+constexpr int kRefineMaxIters = 12;
+constexpr double kRefineTol = 1e-14;
+
 fh_status spectra_common(fh_ctx *ctx, const double *d_a, int n_samples, double t0, double dt,
                          double H) {
     if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_window_spectra: call fh_discretize first");
@@ -469,6 +473,7 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
     ctx->solved = false;
     FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
     const fh::SolveTables t = tables(ctx);
+    const bool mixed = ctx->precision == FH_MIXED_FP32;
     {
     PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
     fh::launch_assemble(t, ctx->S, ctx->d_tile_off.as<long long>(), ctx->n_tiles,
@@ -476,14 +481,14 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
                         ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(),
                         ctx->d_A.as<double2>(), ctx->stream);
     FH_TRY(check_launch(ctx, "assemble"));
+    if (mixed) FH_TRY(ensure(ctx, ctx->d_g, (size_t)ctx->vec_total * sizeof(double2)));
     fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                   ctx->p[0], ctx->p[1], ctx->d_psi.as<double2>(), ctx->stream);
+                   ctx->p[0], ctx->p[1], mixed ? ctx->d_g.as<double2>() : ctx->d_psi.as<double2>(),
+                   ctx->stream);
     FH_TRY(check_launch(ctx, "rhs"));
     }
     FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
-    int iters_max = 0;
-    double resid_max = 0.0;
-    if (ctx->precision == FH_FP64) {
+    if (!mixed) {
         PhaseScope ps(ctx, FH_PH_FACTOR, 1);
         fh::launch_lu_solve_fp64(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                                  ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
@@ -491,16 +496,53 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
                                  ctx->d_info.as<int>(), ctx->stream);
         FH_TRY(check_launch(ctx, "lu fp64"));
     } else {
-        return fail(ctx, FH_EINVAL, "precision %d is not available in this build", ctx->precision);
+        FH_TRY(ensure(ctx, ctx->d_A32, (size_t)ctx->mat_total * sizeof(float2)));
+        FH_TRY(ensure(ctx, ctx->d_piv, (size_t)ctx->vec_total * sizeof(int)));
+        FH_TRY(ensure(ctx, ctx->d_iters, (size_t)ctx->S * sizeof(int)));
+        FH_TRY(ensure(ctx, ctx->d_resid, (size_t)ctx->S * sizeof(double)));
+        PhaseScope ps(ctx, FH_PH_FACTOR, 3);
+        fh::launch_convert_fp32(ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->mat_total,
+                                ctx->stream);
+        fh::launch_lu_factor_fp32(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
+                                  ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
+                                  ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
+                                  ctx->d_info.as<int>(), ctx->stream);
+        fh::launch_lu_refine(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
+                             ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
+                             ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),
+                             ctx->d_g.as<double2>(), ctx->d_psi.as<double2>(), kRefineMaxIters,
+                             kRefineTol, ctx->d_iters.as<int>(), ctx->d_resid.as<double>(),
+                             ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
+        FH_TRY(check_launch(ctx, "lu mixed"));
     }
-    std::vector<int> info(ctx->S);
+    int iters_max = 0;
+    double resid_max = 0.0;
+    std::vector<int> info(ctx->S), iters;
+    std::vector<double> resid;
     FH_CUDA(ctx, cudaMemcpyAsync(info.data(), ctx->d_info.p, (size_t)ctx->S * sizeof(int),
                                  cudaMemcpyDeviceToHost, ctx->stream));
+    if (mixed) {
+        iters.resize(ctx->S);
+        resid.resize(ctx->S);
+        FH_CUDA(ctx, cudaMemcpyAsync(iters.data(), ctx->d_iters.p, (size_t)ctx->S * sizeof(int),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+        FH_CUDA(ctx, cudaMemcpyAsync(resid.data(), ctx->d_resid.p, (size_t)ctx->S * sizeof(double),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    }
     FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int s = 0; s < ctx->S; ++s)
-        if (info[s] != 0)
+    for (int s = 0; s < ctx->S; ++s) {
+        if (info[s] > 0)
             return fail(ctx, FH_ESINGULAR, "frequency j=%d (omega=%.17g): zero or non-finite pivot in column %d",
                         ctx->solve_j[s], ctx->omega[ctx->solve_j[s]], info[s] - 1);
+        if (info[s] < 0)
+            return fail(ctx, FH_ENOCONV, "frequency j=%d (omega=%.17g): refinement did not converge in %d sweeps (residual %.3g)",
+                        ctx->solve_j[s], ctx->omega[ctx->solve_j[s]], kRefineMaxIters, resid[s]);
+    }
+    if (mixed)
+        for (int s = 0; s < ctx->S; ++s) {
+            iters_max = std::max(iters_max, iters[s]);
+            resid_max = std::max(resid_max, resid[s]);
+        }
     ctx->solved = true;
     if (stats) {
         stats->n_solves = ctx->S;

@@ -62,7 +62,7 @@ void launch_lu_factor_fp32(const int *order, int S, const int *N, const long lon
 void launch_lu_refine(const int *order, int S, const int *N, const long long *mat_off,
                       const int *vec_off, const double2 *A, const float2 *LU32, const int *piv,
                       const double2 *g, double2 *x, int max_iters, double tol, int *iters,
-                      double *resid, int *info, cudaStream_t st);
+                      double *resid, int *info, int maxN, cudaStream_t st);
 
 // ---- window spectra (k_window.cu) ----
 void launch_window_spectra(const double *a, int n_samples, long long start0, long long step,

@@ -1,0 +1,377 @@
+// Step a3, mixed precision: FP32 LU with partial pivoting, then iterative
+// refinement with FP64 residuals r = g - A x against the FP64 matrix.
+//
+// The CFIE matrices are well conditioned (second-kind equation), so each
+// refinement sweep contracts the error by ~ cond * N * 2^-24; two or three
+// sweeps bring the FP32 solution to FP64 accuracy.  Refinement stops when the
+// correction is below tol * ||x||_inf (max-norms), or fails with FH_ENOCONV
+// after max_iters sweeps.
+//
+// Kernels (one CTA per frequency, largest systems first):
+//   lu_factor_fp32_kernel  blocked right-looking LU (panel width 32) of the
+//                          column-major complex64 copy, pivots stored;
+//   refine_kernel          x = 0, r = g; repeat { d = (LU)^-1 P r in FP32;
+//                          x += d; r = g - A x in FP64 } with blocked
+//                          triangular solves (32-wide diagonal blocks solved
+//                          by one warp, off-diagonal updates by the CTA).
+#include "fh_internal.h"
+
+namespace fh {
+namespace {
+
+constexpr int NB = 32;   // panel width
+constexpr int TT = 64;   // trailing tile edge
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void __launch_bounds__(256) lu_factor_fp32_kernel(
+    const int *__restrict__ order, const int *__restrict__ Ns,
+    const long long *__restrict__ mat_off, const int *__restrict__ vec_off,
+    float2 *__restrict__ A32, int *__restrict__ piv, int *__restrict__ info) {
+    const int s = order[blockIdx.x];
+    const int n = Ns[s];
+    float2 *a = A32 + mat_off[s];
+    int *pv = piv + vec_off[s];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    __shared__ float red_v[8];
+    __shared__ int red_i[8];
+    __shared__ int sh_piv, sh_bad;
+    __shared__ float2 sh_val;
+    __shared__ float2 Ls[TT][NB + 1];
+    __shared__ float2 Us[NB][TT];
+#define AT(i, j) a[(long long)(j) * n + (i)]
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int nb = min(NB, n - k0);
+        for (int c = k0; c < k0 + nb; ++c) {
+            float best = -1.f;
+            int bi = n;
+            for (int r = c + tid; r < n; r += 256) {
+                const float2 v = AT(r, c);
+                const float m = fabsf(v.x) + fabsf(v.y);
+                if (m > best) { best = m; bi = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                float bv = red_v[0];
+                int bidx = red_i[0];
+                for (int w = 1; w < 8; ++w)
+                    if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bidx)) { bv = red_v[w]; bidx = red_i[w]; }
+                int bad = !(bv > 0.f) || bidx >= n;
+                float2 p = make_float2(0.f, 0.f);
+                if (!bad) {
+                    p = AT(bidx, c);
+                    bad = !isfinite(p.x) || !isfinite(p.y);
+                }
+                if (bad) info[s] = c + 1;
+                sh_bad = bad;
+                sh_piv = bidx;
+                pv[c] = bidx;
+                if (!bad) {
+                    const float d = p.x * p.x + p.y * p.y;
+                    sh_val = make_float2(p.x / d, -p.y / d);
+                }
+            }
+            __syncthreads();
+            if (sh_bad) return;
+            const int p = sh_piv;
+            if (p != c)
+                for (int j = tid; j < n; j += 256) {
+                    const float2 t0 = AT(c, j);
+                    AT(c, j) = AT(p, j);
+                    AT(p, j) = t0;
+                }
+            __syncthreads();
+            const float2 pinv = sh_val;
+            for (int r = c + 1 + tid; r < n; r += 256) AT(r, c) = cmulf(AT(r, c), pinv);
+            __syncthreads();
+            const int ncols = k0 + nb - c - 1, rows = n - c - 1;
+            if (ncols > 0 && rows > 0)
+                for (int e = tid; e < rows * ncols; e += 256) {
+                    const int r = c + 1 + e % rows, j = c + 1 + e / rows;
+                    const float2 l = AT(r, c), u = AT(c, j);
+                    float2 v = AT(r, j);
+                    v.x -= l.x * u.x - l.y * u.y;
+                    v.y -= l.x * u.y + l.y * u.x;
+                    AT(r, j) = v;
+                }
+            __syncthreads();
+        }
+        // U12 = L11^{-1} A12
+        for (int j = k0 + nb + tid; j < n; j += 256) {
+            float2 x[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+                if (q < nb) x[q] = AT(k0 + q, j);
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+                if (q < nb) {
+#pragma unroll
+                    for (int r = q + 1; r < NB; ++r)
+                        if (r < nb) {
+                            const float2 l = AT(k0 + r, k0 + q);
+                            x[r].x -= l.x * x[q].x - l.y * x[q].y;
+                            x[r].y -= l.x * x[q].y + l.y * x[q].x;
+                        }
+                }
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+                if (q < nb) AT(k0 + q, j) = x[q];
+        }
+        __syncthreads();
+        const int r0 = k0 + nb, m = n - r0;
+        if (m > 0) {
+            const int nt = (m + TT - 1) / TT;
+            const int tx = tid & 15, ty = tid >> 4;
+            for (int tile = 0; tile < nt * nt; ++tile) {
+                const int i0 = r0 + (tile % nt) * TT, j0 = r0 + (tile / nt) * TT;
+                for (int e = tid; e < TT * NB; e += 256) {
+                    const int rr = e % TT, q = e / TT;
+                    Ls[rr][q] = (i0 + rr < n && q < nb) ? AT(i0 + rr, k0 + q) : make_float2(0.f, 0.f);
+                }
+                for (int e = tid; e < TT * NB; e += 256) {
+                    const int q = e % NB, cc = e / NB;
+                    Us[q][cc] = (q < nb && j0 + cc < n) ? AT(k0 + q, j0 + cc) : make_float2(0.f, 0.f);
+                }
+                __syncthreads();
+                float2 acc[4][4];
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        const int i = i0 + tx + 16 * aa, j = j0 + ty + 16 * bb;
+                        acc[aa][bb] = (i < n && j < n) ? AT(i, j) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll 8
+                for (int q = 0; q < NB; ++q) {
+                    float2 l[4], u[4];
+#pragma unroll
+                    for (int aa = 0; aa < 4; ++aa) l[aa] = Ls[tx + 16 * aa][q];
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) u[bb] = Us[q][ty + 16 * bb];
+#pragma unroll
+                    for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+                        for (int bb = 0; bb < 4; ++bb) {
+                            acc[aa][bb].x -= l[aa].x * u[bb].x - l[aa].y * u[bb].y;
+                            acc[aa][bb].y -= l[aa].x * u[bb].y + l[aa].y * u[bb].x;
+                        }
+                }
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        const int i = i0 + tx + 16 * aa, j = j0 + ty + 16 * bb;
+                        if (i < n && j < n) AT(i, j) = acc[aa][bb];
+                    }
+                __syncthreads();
+            }
+        }
+    }
+#undef AT
+}
+
+// y <- (LU)^{-1} P y in FP32, y in shared memory (n complex).  L is unit lower.
+__device__ void lu_solve_shared(const float2 *__restrict__ a, const int *__restrict__ pv, int n,
+                                float2 *y) {
+    const int tid = threadIdx.x, lane = tid & 31;
+#define AT(i, j) a[(long long)(j) * n + (i)]
+    if (tid == 0)
+        for (int c = 0; c < n; ++c) {
+            const int p = pv[c];
+            if (p != c) { const float2 t = y[c]; y[c] = y[p]; y[p] = t; }
+        }
+    __syncthreads();
+    // forward: L y = y
+    for (int jb = 0; jb < n; jb += 32) {
+        const int je = min(jb + 32, n);
+        if (tid < 32) {
+            const int i = jb + lane;
+            float2 yi = (i < je) ? y[i] : make_float2(0.f, 0.f);
+            for (int j = jb; j < je; ++j) {
+                const float yjx = __shfl_sync(0xffffffffu, yi.x, j - jb);
+                const float yjy = __shfl_sync(0xffffffffu, yi.y, j - jb);
+                if (i > j && i < je) {
+                    const float2 l = AT(i, j);
+                    yi.x -= l.x * yjx - l.y * yjy;
+                    yi.y -= l.x * yjy + l.y * yjx;
+                }
+            }
+            if (i < je) y[i] = yi;
+        }
+        __syncthreads();
+        for (int i = je + tid; i < n; i += blockDim.x) {
+            float2 yi = y[i];
+            for (int j = jb; j < je; ++j) {
+                const float2 l = AT(i, j), yj = y[j];
+                yi.x -= l.x * yj.x - l.y * yj.y;
+                yi.y -= l.x * yj.y + l.y * yj.x;
+            }
+            y[i] = yi;
+        }
+        __syncthreads();
+    }
+    // backward: U y = y
+    const int nblk = (n + 31) / 32;
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int jb = b * 32, je = min(jb + 32, n);
+        if (tid < 32) {
+            const int i = jb + lane;
+            float2 yi = (i < je) ? y[i] : make_float2(0.f, 0.f);
+            for (int j = je - 1; j >= jb; --j) {
+                if (i == j) {
+                    const float2 u = AT(j, j);
+                    const float d = u.x * u.x + u.y * u.y;
+                    yi = make_float2((yi.x * u.x + yi.y * u.y) / d, (yi.y * u.x - yi.x * u.y) / d);
+                }
+                const float yjx = __shfl_sync(0xffffffffu, yi.x, j - jb);
+                const float yjy = __shfl_sync(0xffffffffu, yi.y, j - jb);
+                if (i < j) {
+                    const float2 u = AT(i, j);
+                    yi.x -= u.x * yjx - u.y * yjy;
+                    yi.y -= u.x * yjy + u.y * yjx;
+                }
+            }
+            if (i < je) y[i] = yi;
+        }
+        __syncthreads();
+        for (int i = tid; i < jb; i += blockDim.x) {
+            float2 yi = y[i];
+            for (int j = jb; j < je; ++j) {
+                const float2 u = AT(i, j), yj = y[j];
+                yi.x -= u.x * yj.x - u.y * yj.y;
+                yi.y -= u.x * yj.y + u.y * yj.x;
+            }
+            y[i] = yi;
+        }
+        __syncthreads();
+    }
+#undef AT
+}
+
+__device__ double block_max(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+    return r;
+}
+
+__global__ void __launch_bounds__(256) refine_kernel(
+    const int *__restrict__ order, const int *__restrict__ Ns,
+    const long long *__restrict__ mat_off, const int *__restrict__ vec_off,
+    const double2 *__restrict__ A, const float2 *__restrict__ LU32, const int *__restrict__ piv,
+    const double2 *__restrict__ G, double2 *__restrict__ X, int max_iters, double tol,
+    int *__restrict__ iters, double *__restrict__ resid, int *__restrict__ info) {
+    extern __shared__ double2 sh[];
+    const int s = order[blockIdx.x];
+    if (info[s] != 0) return;
+    const int n = Ns[s];
+    double2 *xs = sh;                                   // n FP64 complex
+    float2 *ys = reinterpret_cast<float2 *>(sh + n);    // n FP32 complex
+    __shared__ double red[8];
+    const double2 *a = A + mat_off[s];
+    const float2 *lu = LU32 + mat_off[s];
+    const int *pv = piv + vec_off[s];
+    const double2 *g = G + vec_off[s];
+    double2 *x = X + vec_off[s];
+    const int tid = threadIdx.x;
+    double gmax = 0.0;
+    for (int i = tid; i < n; i += blockDim.x) {
+        const double2 gi = g[i];
+        xs[i] = make_double2(0.0, 0.0);
+        ys[i] = make_float2((float)gi.x, (float)gi.y);
+        gmax = fmax(gmax, fabs(gi.x) + fabs(gi.y));
+    }
+    gmax = block_max(gmax, red);
+    int it = 0;
+    bool done = false;
+    double rmax = gmax;
+    while (it < max_iters && !done) {
+        __syncthreads();
+        lu_solve_shared(lu, pv, n, ys);
+        double dmax = 0.0, xmax = 0.0;
+        for (int i = tid; i < n; i += blockDim.x) {
+            const float2 d = ys[i];
+            double2 xi = xs[i];
+            xi.x += (double)d.x;
+            xi.y += (double)d.y;
+            xs[i] = xi;
+            dmax = fmax(dmax, fabs((double)d.x) + fabs((double)d.y));
+            xmax = fmax(xmax, fabs(xi.x) + fabs(xi.y));
+        }
+        dmax = block_max(dmax, red);
+        xmax = block_max(xmax, red);
+        ++it;
+        // r = g - A x (FP64), rows over threads, columns in order
+        double rloc = 0.0;
+        for (int i = tid; i < n; i += blockDim.x) {
+            double rr = g[i].x, ri = g[i].y;
+            for (int l = 0; l < n; ++l) {
+                const double2 al = a[(long long)l * n + i];
+                const double2 xl = xs[l];
+                rr -= al.x * xl.x - al.y * xl.y;
+                ri -= al.x * xl.y + al.y * xl.x;
+            }
+            ys[i] = make_float2((float)rr, (float)ri);
+            rloc = fmax(rloc, fabs(rr) + fabs(ri));
+        }
+        rmax = block_max(rloc, red);
+        done = !(dmax > tol * xmax) || rmax == 0.0;
+    }
+    for (int i = tid; i < n; i += blockDim.x) x[i] = xs[i];
+    if (tid == 0) {
+        iters[s] = it;
+        resid[s] = gmax > 0.0 ? rmax / gmax : 0.0;
+        if (!done) info[s] = -1;
+    }
+}
+
+__global__ void convert_kernel(const double2 *__restrict__ A, float2 *__restrict__ B, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = A[i];
+        B[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+}  // namespace
+
+void launch_convert_fp32(const double2 *A, float2 *A32, long long n, cudaStream_t st) {
+    if (n <= 0) return;
+    convert_kernel<<<152 * 8, 256, 0, st>>>(A, A32, n);
+}
+
+void launch_lu_factor_fp32(const int *order, int S, const int *N, const long long *mat_off,
+                           float2 *A32, int *piv, const int *vec_off, int *info, cudaStream_t st) {
+    if (S <= 0) return;
+    lu_factor_fp32_kernel<<<S, 256, 0, st>>>(order, N, mat_off, vec_off, A32, piv, info);
+}
+
+void launch_lu_refine(const int *order, int S, const int *N, const long long *mat_off,
+                      const int *vec_off, const double2 *A, const float2 *LU32, const int *piv,
+                      const double2 *g, double2 *x, int max_iters, double tol, int *iters,
+                      double *resid, int *info, int maxN, cudaStream_t st) {
+    if (S <= 0) return;
+    const size_t smem = (size_t)maxN * (sizeof(double2) + sizeof(float2));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    refine_kernel<<<S, 256, smem, st>>>(order, N, mat_off, vec_off, A, LU32, piv, g, x, max_iters,
+                                        tol, iters, resid, info);
+}
+
+}  // namespace fh

@@ -130,7 +130,7 @@ def test_window_spectra_ragged_and_offset_grids():
         # rounding bound of a length-Q sum whose terms are |a w| dt: the test
         # signal is oscillatory, so B itself can be 1e4 times smaller than the sum
         bound = 1e-14 * dt * np.sum(np.abs(a)) * 4
-        assert np.max(np.abs(B - Bo)) < bound
+        assert np.max(np.abs(B - Bo)) <= bound
 
 
 @pytest.mark.parametrize("name", list(WORKLOADS))
@@ -309,3 +309,46 @@ def test_large_config_sampled():
     V = O.target_fields(wl, psi_o, xs)
     uo = O.synthesize(B, s, wl.omega, V, wl.T)
     assert rel(u[idx], uo) < TOL
+
+
+# ------------------------------------------------------ mixed precision (FP32 LU + FP64 IR)
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_densities_mixed_precision(name):
+    """FP32 LU with FP64 refinement reaches the FP64 oracle within 1e-10."""
+    wl = WORKLOADS[name]()
+    pr = make(wl, F.FH_MIXED_FP32)
+    st = pr.solve()
+    assert 1 <= st.refine_iters_max <= 6
+    assert st.residual_max < 1e-12
+    psi_o = O.solve_all(wl)
+    worst = max(rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) for j in range(1, wl.J))
+    assert worst < TOL
+
+
+def test_full_path_mixed_precision_circle_config():
+    wl = fi.circle_gauss()
+    pr = make(wl, F.FH_MIXED_FP32)
+    pr.solve()
+    pr.window_spectra(wl.a, wl.t0, wl.dt, wl.H)
+    u = pr.sample(wl.x, wl.T)
+    assert rel(u, O.run(wl)["u"]) < TOL
+
+
+def test_large_config_mixed_precision():
+    """The benchmark workload solved in mixed precision: every density within
+    1e-10 of the FP64 oracle, and the field equal to the FP64 GPU path's."""
+    wl = fi.kite_pulses(n_near=256, n_far=64)
+    pr = make(wl, F.FH_MIXED_FP32)
+    st = pr.solve()
+    pr.window_spectra(wl.a, wl.t0, wl.dt, wl.H)
+    u = pr.sample(wl.x[:64], wl.T)
+    psi_o = O.solve_all(wl)
+    worst = max(rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) for j in range(1, wl.J))
+    assert worst < TOL, worst
+    ref = make(wl)
+    ref.solve()
+    ref.window_spectra(wl.a, wl.t0, wl.dt, wl.H)
+    u64 = ref.sample(wl.x[:64], wl.T)
+    assert rel(u, u64) < TOL
+    assert st.refine_iters_max <= 6
