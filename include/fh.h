@@ -208,6 +208,13 @@ fh_status fh_set_timing(fh_ctx *ctx, int enable);
  * copy them to *out, and zero them if reset != 0. */
 fh_status fh_get_timings(fh_ctx *ctx, fh_timings *out, int reset);
 
+/* The kernels' Bessel routine on n host arguments x > 0 (current device):
+ * out[6i .. 6i+5] = J0, Y0, J1, Y1 from the joint routine used in assembly,
+ * then J0, Y0 from the H0 routine used for target fields.  Diagnostic entry
+ * point for checking the Hankel kernels of Sec. 2.3 against reference values;
+ * allocates its own device scratch. */
+fh_status fh_eval_bessel(const double *x, int n, double *out);
+
 /* Measured FMA throughput of device `device` in TFLOP/s (2 flops per FMA):
  * fp64 != 0 for binary64, else binary32; `iters` FMAs per chain (e.g. 4096).
  * Not part of the scattering path: it gives the arithmetic roofline against

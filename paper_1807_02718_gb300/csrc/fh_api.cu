@@ -755,6 +755,26 @@ fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, 
     return FH_OK;
 }
 
+fh_status fh_eval_bessel(const double *x, int n, double *out) {
+    if (!x || !out || n < 0) return FH_EINVAL;
+    if (n == 0) return FH_OK;
+    double *d = nullptr;
+    if (cudaMalloc(&d, (size_t)n * 7 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return FH_ENOMEM;
+    }
+    fh_status st = FH_OK;
+    if (cudaMemcpy(d, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) st = FH_ECUDA;
+    if (st == FH_OK) {
+        fh::launch_bessel_eval(d, n, d + n, 0);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(out, d + n, (size_t)n * 6 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = FH_ECUDA;
+    }
+    cudaFree(d);
+    return st;
+}
+
 fh_status fh_set_timing(fh_ctx *ctx, int enable) {
     FH_TRY(enter(ctx));
     ctx->timing = enable != 0;

@@ -75,6 +75,10 @@ void launch_target_field(const SolveTables &t, int S, const int *solve_j, int ma
                          const double2 *z, const double2 *dz, const double2 *psi,
                          const double *x, int n_x, double2 *V, cudaStream_t st);
 
+// Kernel Bessel routine on n arguments: out[6i..6i+5] = J0, Y0, J1, Y1 (joint
+// routine) and J0, Y0 (H0-only routine).
+void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st);
+
 // ---- synthesis (k_synth.cu) ----
 // nu[p * R + r] = sum_{m=-h}^{h-1} (-1)^m (m/h)^r e^{-2 pi i m p / M}.
 constexpr int kFarTerms = 60;

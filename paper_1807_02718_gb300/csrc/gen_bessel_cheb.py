@@ -1,0 +1,109 @@
+"""Generate bessel_cheb.h: Chebyshev coefficients for J0, Y0, J1, Y1 in FP64.
+
+The device routine (bessel.cuh) evaluates the four functions together:
+
+  x < 8 (variable t = x^2/32 - 1 in [-1, 1]; all four series are entire in x^2):
+      J0(x)            = A0(t)
+      Y0(x)            = (2/pi) J0(x) ln(x/2) + A1(t)
+      J1(x)            = x A2(t)
+      Y1(x)            = (2/pi) J1(x) ln(x/2) - 2/(pi x) + x A3(t)
+  x >= 8 (Hankel's asymptotic form, H_nu = sqrt(2/(pi x)) (P_nu + i Q_nu) e^{i chi_nu},
+          chi_nu = x - (2 nu + 1) pi/4; variable u = (x0/x)^2 on each piece):
+      P0 = B0(t), Q0 = (8/x) B1(t), P1 = B2(t), Q1 = (8/x) B3(t)
+  on the pieces x in [8, 20] and [20, inf).
+
+Each function is interpolated at Chebyshev points of the first kind with
+mpmath at 40 digits and its Chebyshev series truncated once the remaining
+coefficients fall below 1e-17 of the function scale.  This is Chebyshev
+interpolation of the functions defined by their series and by the Hankel
+asymptotic form (Abramowitz & Stegun 9.1.10-9.1.11 and 9.2.5-9.2.6); the
+coefficients are this script's output, not taken from any library.
+
+    python gen_bessel_cheb.py > bessel_cheb.h      (needs mpmath)
+"""
+import mpmath as mp
+
+mp.mp.dps = 40
+TWO_PI_INV = 2 / mp.pi
+TOL = mp.mpf("1e-17")
+NPTS = 48
+
+
+def cheb(f, n=NPTS):
+    xs = [mp.cos(mp.pi * (k + mp.mpf(1) / 2) / n) for k in range(n)]
+    fs = [f(x) for x in xs]
+    c = []
+    for j in range(n):
+        s = mp.fsum(fs[k] * mp.cos(mp.pi * j * (k + mp.mpf(1) / 2) / n) for k in range(n))
+        c.append(2 * s / n if j else s / n)
+    scale = max(abs(v) for v in c)
+    last = max(j for j, v in enumerate(c) if abs(v) > TOL * max(scale, 1))
+    return c[: last + 1]
+
+
+def x_small(t):
+    return mp.sqrt(32 * (t + 1))
+
+
+def a0(t):
+    return mp.besselj(0, x_small(t))
+
+
+def a1(t):
+    x = x_small(t)
+    return mp.bessely(0, x) - TWO_PI_INV * mp.besselj(0, x) * mp.log(x / 2)
+
+
+def a2(t):
+    x = x_small(t)
+    return mp.besselj(1, x) / x
+
+
+def a3(t):
+    x = x_small(t)
+    return (mp.bessely(1, x) - TWO_PI_INV * mp.besselj(1, x) * mp.log(x / 2) + 2 / (mp.pi * x)) / x
+
+
+def pq(nu, x):
+    chi = x - (2 * nu + 1) * mp.pi / 4
+    h = mp.hankel1(nu, x) * mp.exp(-1j * chi) * mp.sqrt(mp.pi * x / 2)
+    return h.real, h.imag
+
+
+def large(x0, x1):
+    """Pieces on x in [x0, x1] (x1 = inf allowed) in u = (x0/x)^2, t = affine map of u."""
+    u1 = mp.mpf(1)
+    u0 = mp.mpf(0) if x1 == mp.inf else (x0 / x1) ** 2
+
+    def x_of(t):
+        u = u0 + (u1 - u0) * (t + 1) / 2
+        return x0 / mp.sqrt(u)
+
+    fs = [lambda t: pq(0, x_of(t))[0], lambda t: pq(0, x_of(t))[1] * x_of(t) / 8,
+          lambda t: pq(1, x_of(t))[0], lambda t: pq(1, x_of(t))[1] * x_of(t) / 8]
+    return [cheb(f) for f in fs], u0
+
+
+def emit(name, c):
+    body = ",\n    ".join(mp.nstr(v, 20, min_fixed=-1, max_fixed=-1) for v in c)
+    return f"constexpr int {name}_N = {len(c)};\nstatic __device__ __constant__ double {name}[{len(c)}] = {{\n    {body}}};\n"
+
+
+def main():
+    out = ["// Generated by gen_bessel_cheb.py (Chebyshev interpolation with mpmath);",
+           "// do not edit.  See that script and bessel.cuh for the definitions.",
+           "#pragma once", ""]
+    for name, f in (("kA0", a0), ("kA1", a1), ("kA2", a2), ("kA3", a3)):
+        out.append(emit(name, cheb(f)))
+    (b_lo, u0_lo) = large(mp.mpf(8), mp.mpf(20))
+    (b_hi, u0_hi) = large(mp.mpf(20), mp.inf)
+    out.append(f"constexpr double kBLoU0 = {mp.nstr(u0_lo, 20)};   // (8/20)^2")
+    for k, c in enumerate(b_lo):
+        out.append(emit(f"kBLo{k}", c))
+    for k, c in enumerate(b_hi):
+        out.append(emit(f"kBHi{k}", c))
+    print("\n".join(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -17,6 +17,7 @@
 // One CTA assembles one 32 x 32 tile of one frequency's matrix; tiles of all
 // frequencies form one flat launch (prefix offsets tile_off).  Each warp
 // writes 32 consecutive rows of a column: column-major stores of 512 B.
+#include "bessel.cuh"
 #include "fh_internal.h"
 
 namespace fh {
@@ -77,7 +78,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(
             const double d1 = zl.x - zi.x, d2 = zl.y - zi.y;
             const double r = sqrt(d1 * d1 + d2 * d2);
             const double x = kappa * r;
-            const double J0 = j0(x), Y0 = y0(x), J1 = j1(x), Y1 = y1(x);
+            double J0, Y0, J1, Y1;
+            bessel_j0y0j1y1(x, J0, Y0, J1, Y1);
             const double Nil = dzi.y * d1 - dzi.x * d2;
             const double ls = logsin[to + d];
             const double g = Nil * sl / (si * r);

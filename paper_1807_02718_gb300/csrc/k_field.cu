@@ -8,6 +8,7 @@
 //
 // One CTA per (frequency, 128 targets); source nodes are staged through
 // shared memory with the weights c_i = (pi/n) |z'_i| psi_i / 4 premultiplied.
+#include "bessel.cuh"
 #include "fh_internal.h"
 
 namespace fh {
@@ -52,7 +53,8 @@ __global__ void __launch_bounds__(kTgt) field_kernel(
             for (int e = 0; e < ne; ++e) {
                 const double d1 = px - zs[e].x, d2 = py - zs[e].y;
                 const double arg = kappa * sqrt(d1 * d1 + d2 * d2);
-                const double J0 = j0(arg), Y0 = y0(arg);
+                double J0, Y0;
+                bessel_j0y0(arg, J0, Y0);
                 // (i)(J0 + i Y0) c = (-Y0 + i J0) c
                 const double2 c = cs[e];
                 vr += -Y0 * c.x - J0 * c.y;
@@ -68,7 +70,26 @@ __global__ void field_zero_freq_kernel(int n_x, double2 *__restrict__ V) {
     if (i < n_x) V[i] = make_double2(1.0, 0.0);
 }
 
+__global__ void bessel_eval_kernel(const double *__restrict__ x, int n, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double J0, Y0, J1, Y1;
+    bessel_j0y0j1y1(x[i], J0, Y0, J1, Y1);
+    double a, b;
+    bessel_j0y0(x[i], a, b);
+    out[6 * i + 0] = J0;
+    out[6 * i + 1] = Y0;
+    out[6 * i + 2] = J1;
+    out[6 * i + 3] = Y1;
+    out[6 * i + 4] = a;
+    out[6 * i + 5] = b;
+}
+
 }  // namespace
+
+void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st) {
+    if (n > 0) bessel_eval_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, n, out);
+}
 
 void launch_target_field(const SolveTables &t, int S, const int *solve_j, int maxN,
                          const double2 *z, const double2 *dz, const double2 *psi,

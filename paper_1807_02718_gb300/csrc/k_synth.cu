@@ -25,31 +25,60 @@
 namespace fh {
 namespace {
 
-__global__ void far_table_kernel(int J, int M, double2 *__restrict__ nu,
-                                 double2 *__restrict__ ph) {
+// One CTA per p: phases e^{-2 pi i m p / M} (-1)^m for a chunk of m are staged
+// in shared memory; thread r accumulates sum_m phase_m (m/h)^r, the power by
+// binary exponentiation.
+__device__ __forceinline__ double ipow(double x, int r) {
+    double y = 1.0;
+    while (r) {
+        if (r & 1) y *= x;
+        x *= x;
+        r >>= 1;
+    }
+    return y;
+}
+
+constexpr int kFarChunk = 256;
+
+__global__ void __launch_bounds__(64) far_table_kernel(int J, int M, double2 *__restrict__ nu,
+                                                       double2 *__restrict__ ph) {
     const int p = blockIdx.x;
     const int r = threadIdx.x;
     const int h = M / 2;
-    if (p == 0) {
+    __shared__ double2 phs[kFarChunk];
+    if (p == 0)
         for (int q = r; q < M; q += blockDim.x) {
             double sn, cs;
             sincospi(-2.0 * (double)q / (double)M, &sn, &cs);
             ph[q] = make_double2(cs, sn);
         }
-    }
-    if (r >= kFarTerms) return;
     double sr = 0.0, si = 0.0;
-    for (int m = -h; m < h; ++m) {
-        const long long mm = ((long long)(m % M) + M) % M;
-        const int q = (int)((mm * p) % M);
-        double sn, cs;
-        sincospi(-2.0 * (double)q / (double)M, &sn, &cs);
-        const double sg = (m & 1) ? -1.0 : 1.0;
-        const double pw = (r == 0) ? 1.0 : pow((double)m / (double)h, (double)r);
-        sr += sg * pw * cs;
-        si += sg * pw * sn;
+    for (int m0 = -h; m0 < h; m0 += kFarChunk) {
+        __syncthreads();
+        for (int e = r; e < kFarChunk; e += blockDim.x) {
+            const int m = m0 + e;
+            double2 v = make_double2(0.0, 0.0);
+            if (m < h) {
+                const long long mm = ((long long)(m % M) + M) % M;
+                const int q = (int)((mm * p) % M);
+                double sn, cs;
+                sincospi(-2.0 * (double)q / (double)M, &sn, &cs);
+                const double sg = (m & 1) ? -1.0 : 1.0;
+                v = make_double2(sg * cs, sg * sn);
+            }
+            phs[e] = v;
+        }
+        __syncthreads();
+        if (r < kFarTerms) {
+            const int me = min(kFarChunk, h - m0);
+            for (int e = 0; e < me; ++e) {
+                const double pw = ipow((double)(m0 + e) / (double)h, r);
+                sr = fma(pw, phs[e].x, sr);
+                si = fma(pw, phs[e].y, si);
+            }
+        }
     }
-    nu[(long long)r * J + p] = make_double2(sr, si);
+    if (r < kFarTerms) nu[(long long)r * J + p] = make_double2(sr, si);
 }
 
 __global__ void __launch_bounds__(256) weights_kernel(

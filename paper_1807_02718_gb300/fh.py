@@ -30,6 +30,7 @@ EXPORTED = [
     "fh_sample_dev", "fh_get_num_windows", "fh_get_window_spectra", "fh_get_geometry",
     "fh_assemble_matrix", "fh_get_density", "fh_set_densities", "fh_get_target_field",
     "fh_synthesize", "fh_set_timing", "fh_get_timings", "fh_probe_fma_peak",
+    "fh_eval_bessel",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "spectra", "field", "weights", "contract"]
@@ -94,6 +95,7 @@ def load_library(path: str | None = None):
         "fh_set_timing": (C.c_int, [vp, C.c_int]),
         "fh_get_timings": (C.c_int, [vp, C.POINTER(fh_timings), C.c_int]),
         "fh_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
+        "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -281,6 +283,16 @@ def fh_probe_fma_peak(device: int = 0, fp64: bool = True, iters: int = 4096) -> 
     if st != FH_OK:
         raise FHError(st, "fh_probe_fma_peak failed")
     return v.value
+
+
+def fh_eval_bessel(x):
+    """(n, 6) array: J0, Y0, J1, Y1 (joint routine), J0, Y0 (H0 routine)."""
+    xv = _f64(x)
+    out = np.empty((xv.size, 6))
+    st = load_library().fh_eval_bessel(_dp(xv), xv.size, _dp(out))
+    if st != FH_OK:
+        raise FHError(st, "fh_eval_bessel failed")
+    return out
 
 
 class Problem:
