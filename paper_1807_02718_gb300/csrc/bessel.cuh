@@ -58,6 +58,51 @@ __device__ __forceinline__ void hankel_pq(double x, double &P0, double &Q0, doub
     }
 }
 
+// P0, Q0, P1, Q1 at x >= 8 given r8 = 8/x (shared by the grouped kernels).
+template <bool want1>
+__device__ __forceinline__ void hankel_pq_r8(double x, double r8, double &P0, double &Q0,
+                                             double &P1, double &Q1) {
+    if (x < 20.0) {
+        const double t = (r8 * r8 - kBLoU0) * (2.0 / (1.0 - kBLoU0)) - 1.0;
+        P0 = clenshaw<kBLo0_N>(kBLo0, t);
+        Q0 = r8 * clenshaw<kBLo1_N>(kBLo1, t);
+        if (want1) {
+            P1 = clenshaw<kBLo2_N>(kBLo2, t);
+            Q1 = r8 * clenshaw<kBLo3_N>(kBLo3, t);
+        }
+    } else {
+        const double r20 = 2.5 * r8;
+        const double t = 2.0 * r20 * r20 - 1.0;
+        P0 = clenshaw<kBHi0_N>(kBHi0, t);
+        Q0 = r8 * clenshaw<kBHi1_N>(kBHi1, t);
+        if (want1) {
+            P1 = clenshaw<kBHi2_N>(kBHi2, t);
+            Q1 = r8 * clenshaw<kBHi3_N>(kBHi3, t);
+        }
+    }
+}
+
+// Small-argument branch (x < 8) of the joint routine.
+__device__ __forceinline__ void bessel_small(double x, double &J0, double &Y0, double &J1,
+                                             double &Y1) {
+    const double t = x * x * (1.0 / 32.0) - 1.0;
+    J0 = clenshaw<kA0_N>(kA0, t);
+    const double a1 = clenshaw<kA1_N>(kA1, t);
+    const double a2 = clenshaw<kA2_N>(kA2, t);
+    const double a3 = clenshaw<kA3_N>(kA3, t);
+    const double L = kTwoOverPi * log(0.5 * x);
+    Y0 = fma(L, J0, a1);
+    J1 = x * a2;
+    Y1 = fma(L, J1, fma(x, a3, -kTwoOverPi / x));
+}
+
+__device__ __forceinline__ void bessel_small0(double x, double &J0, double &Y0) {
+    const double t = x * x * (1.0 / 32.0) - 1.0;
+    J0 = clenshaw<kA0_N>(kA0, t);
+    const double a1 = clenshaw<kA1_N>(kA1, t);
+    Y0 = fma(kTwoOverPi * log(0.5 * x), J0, a1);
+}
+
 __device__ __forceinline__ void bessel_j0y0j1y1(double x, double &J0, double &Y0, double &J1,
                                                 double &Y1) {
     if (x < 8.0) {

@@ -48,6 +48,13 @@ struct fh_ctx {
     std::vector<int> solve_j, solve_N, vec_off, tab_of, tab_N, tab_off, order;
     std::vector<long long> mat_off, tile_off;
     std::vector<double> kappa_s, eta_s;
+    // frequency subgroups (equal N, at most fh::kGroup consecutive solves)
+    int n_groups = 0;
+    long long group_tiles = 0;
+    std::vector<int2> sg;
+    std::vector<long long> sg_tile_off;
+    std::vector<double> sg_dk;
+    DevBuf d_sg, d_sg_tile_off, d_sg_dk, d_tmp_sg;
 
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_order, d_tile_off;
@@ -79,7 +86,7 @@ struct fh_ctx {
                          &d_kress, &d_logsin, &d_A, &d_psi, &d_info, &d_nu, &d_ph, &d_A32,
                          &d_piv, &d_g, &d_iters, &d_resid, &d_s, &d_B, &d_wa, &d_a, &d_omega,
                          &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_tmpA, &d_tmpg, &d_tmp_i,
-                         &d_tmp_ll, &d_tmp_d};
+                         &d_tmp_ll, &d_tmp_d, &d_sg, &d_sg_tile_off, &d_sg_dk, &d_tmp_sg};
         for (DevBuf *b : all)
             if (b->p) cudaFree(b->p);
         for (auto &pe : pending) {
@@ -195,6 +202,14 @@ bool is_fin(double v) { return std::isfinite(v); }
 constexpr int kRefineMaxIters = 12;
 constexpr double kRefineTol = 1e-14;
 
+fh::Subgroups groups(fh_ctx *ctx) {
+    fh::Subgroups g;
+    g.sg = ctx->d_sg.as<int2>();
+    g.tile_off = ctx->d_sg_tile_off.as<long long>();
+    g.dkappa = ctx->d_sg_dk.as<double>();
+    return g;
+}
+
 fh_status spectra_common(fh_ctx *ctx, const double *d_a, int n_samples, double t0, double dt,
                          double H) {
     if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_window_spectra: call fh_discretize first");
@@ -267,7 +282,7 @@ fh_status sample_common(fh_ctx *ctx, const double *d_x, int n_x, const double *d
     FH_TRY(ensure(ctx, ctx->d_V, (size_t)ctx->J * n_x * sizeof(double2)));
     {
     PhaseScope ps(ctx, FH_PH_FIELD, ctx->S > 0 ? 2 : 1);
-    fh::launch_target_field(tables(ctx), ctx->S, ctx->d_solve_j.as<int>(), ctx->maxN,
+    fh::launch_target_field(tables(ctx), groups(ctx), ctx->n_groups, ctx->d_solve_j.as<int>(),
                             ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                             ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_V.as<double2>(),
                             ctx->stream);
@@ -345,7 +360,7 @@ fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double 
     if (!(W > 0.0) || !is_fin(W)) return fail(ctx, FH_EINVAL, "omega[J-1] must be positive");
     const double dw = W / (J - 1);
     for (int j = 0; j < J; ++j) {
-        if (!is_fin(omega[j]) || std::fabs(omega[j] - j * dw) > 1e-9 * W)
+        if (!is_fin(omega[j]) || std::fabs(omega[j] - j * dw) > 1e-10 * W)
             return fail(ctx, FH_EINVAL, "omega must be uniform on [0, W] (omega[%d] = %.17g)", j, omega[j]);
     }
     std::vector<int> Nv(J, 64);
@@ -404,6 +419,23 @@ fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double 
         maxN = std::max(maxN, n);
     }
     ctx->tile_off[S] = to;
+    ctx->sg.clear();
+    ctx->sg_tile_off.clear();
+    ctx->sg_dk.clear();
+    long long gt = 0;
+    for (int s = 0; s < S;) {
+        int cnt = 1;
+        while (s + cnt < S && cnt < fh::kGroup && ctx->solve_N[s + cnt] == ctx->solve_N[s]) ++cnt;
+        ctx->sg.push_back(make_int2(s, cnt));
+        ctx->sg_tile_off.push_back(gt);
+        ctx->sg_dk.push_back(cnt > 1 ? (ctx->kappa_s[s + cnt - 1] - ctx->kappa_s[s]) / (cnt - 1) : 0.0);
+        const long long nt = (ctx->solve_N[s] + 31) / 32;
+        gt += nt * nt;
+        s += cnt;
+    }
+    ctx->sg_tile_off.push_back(gt);
+    ctx->n_groups = (int)ctx->sg.size();
+    ctx->group_tiles = gt;
     ctx->vec_total = vo;
     ctx->mat_total = mo;
     ctx->n_tiles = to;
@@ -427,6 +459,9 @@ fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double 
     FH_TRY(upload(ctx, ctx->d_order, ctx->order));
     FH_TRY(upload(ctx, ctx->d_tile_off, ctx->tile_off));
     FH_TRY(upload(ctx, ctx->d_omega, ctx->omega));
+    FH_TRY(upload(ctx, ctx->d_sg, ctx->sg));
+    FH_TRY(upload(ctx, ctx->d_sg_tile_off, ctx->sg_tile_off));
+    FH_TRY(upload(ctx, ctx->d_sg_dk, ctx->sg_dk));
     FH_TRY(ensure(ctx, ctx->d_z, (size_t)vo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_dz, (size_t)vo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_ddz, (size_t)vo * sizeof(double2)));
@@ -476,10 +511,10 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
     const bool mixed = ctx->precision == FH_MIXED_FP32;
     {
     PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
-    fh::launch_assemble(t, ctx->S, ctx->d_tile_off.as<long long>(), ctx->n_tiles,
-                        ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(),
-                        ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(),
-                        ctx->d_A.as<double2>(), ctx->stream);
+    fh::launch_assemble_groups(t, groups(ctx), ctx->n_groups, ctx->group_tiles,
+                               ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                               ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
+                               ctx->d_logsin.as<double>(), ctx->d_A.as<double2>(), 0, ctx->stream);
     FH_TRY(check_launch(ctx, "assemble"));
     if (mixed) FH_TRY(ensure(ctx, ctx->d_g, (size_t)ctx->vec_total * sizeof(double2)));
     fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
@@ -643,39 +678,44 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     if (j < 1 || j >= ctx->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
     if (!is_fin(eta_j)) return fail(ctx, FH_EINVAL, "eta_j must be finite");
     const int s = j - 1, n = ctx->solve_N[s];
+    // the subgroup containing s is assembled exactly as in fh_solve_frequencies
+    int gi = 0;
+    while (!(ctx->sg[gi].x <= s && s < ctx->sg[gi].x + ctx->sg[gi].y)) ++gi;
+    const int2 sgv = ctx->sg[gi];
     const long long nt = (n + 31) / 32;
-    // one-solve tables pointing at the context's node data and Kress tables
-    std::vector<int> iv = {n, ctx->vec_off[s], ctx->tab_of[s]};
-    std::vector<long long> lv = {0, 0, nt * nt};   // mat_off, tile_off[0], tile_off[1]
-    std::vector<double> dv = {ctx->kappa_s[s], eta_j};
-    FH_TRY(upload(ctx, ctx->d_tmp_i, iv));
-    FH_TRY(upload(ctx, ctx->d_tmp_ll, lv));
-    FH_TRY(upload(ctx, ctx->d_tmp_d, dv));
-    FH_TRY(ensure(ctx, ctx->d_tmpA, (size_t)n * n * sizeof(double2)));
+    std::vector<double> eta = ctx->eta_s;
+    eta[s] = eta_j;
+    FH_TRY(upload(ctx, ctx->d_eta, eta));
+    std::vector<int2> sg1 = {sgv};
+    std::vector<long long> to1 = {0, nt * nt};
+    std::vector<double> dk1 = {ctx->sg_dk[gi]};
+    FH_TRY(upload(ctx, ctx->d_tmp_sg, sg1));
+    FH_TRY(upload(ctx, ctx->d_tmp_ll, to1));
+    FH_TRY(upload(ctx, ctx->d_tmp_d, dk1));
+    const long long base = ctx->mat_off[sgv.x];
+    FH_TRY(ensure(ctx, ctx->d_tmpA, (size_t)sgv.y * n * n * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_tmpg, (size_t)ctx->vec_total * sizeof(double2)));
-    fh::SolveTables t;
-    t.N = ctx->d_tmp_i.as<int>();
-    t.vec_off = ctx->d_tmp_i.as<int>() + 1;
-    t.tab = ctx->d_tmp_i.as<int>() + 2;
-    t.tab_off = ctx->d_tab_off.as<int>();
-    t.mat_off = ctx->d_tmp_ll.as<long long>();
-    t.kappa = ctx->d_tmp_d.as<double>();
-    t.eta = ctx->d_tmp_d.as<double>() + 1;
-    fh::launch_assemble(t, 1, ctx->d_tmp_ll.as<long long>() + 1, nt * nt, ctx->d_z.as<double2>(),
-                        ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(),
-                        ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(),
-                        ctx->d_tmpA.as<double2>(), ctx->stream);
+    fh::Subgroups g1;
+    g1.sg = ctx->d_tmp_sg.as<int2>();
+    g1.tile_off = ctx->d_tmp_ll.as<long long>();
+    g1.dkappa = ctx->d_tmp_d.as<double>();
+    const fh::SolveTables t = tables(ctx);
+    fh::launch_assemble_groups(t, g1, 1, nt * nt, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                               ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
+                               ctx->d_logsin.as<double>(), ctx->d_tmpA.as<double2>(), -base,
+                               ctx->stream);
     FH_TRY(check_launch(ctx, "assemble (single)"));
-    // rhs for this one solve is written at the context's vector offset of s
-    fh::launch_rhs(t, 1, n, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(), ctx->p[0],
-                   ctx->p[1], ctx->d_tmpg.as<double2>(), ctx->stream);
+    fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                   ctx->p[0], ctx->p[1], ctx->d_tmpg.as<double2>(), ctx->stream);
     FH_TRY(check_launch(ctx, "rhs (single)"));
     std::vector<double2> colmajor((size_t)n * n);
-    FH_CUDA(ctx, cudaMemcpyAsync(colmajor.data(), ctx->d_tmpA.p, colmajor.size() * sizeof(double2),
-                                 cudaMemcpyDeviceToHost, ctx->stream));
+    FH_CUDA(ctx, cudaMemcpyAsync(colmajor.data(),
+                                 (char *)ctx->d_tmpA.p + (size_t)(ctx->mat_off[s] - base) * sizeof(double2),
+                                 colmajor.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<double2> gv(n);
     FH_CUDA(ctx, cudaMemcpyAsync(gv.data(), (char *)ctx->d_tmpg.p + (size_t)ctx->vec_off[s] * sizeof(double2),
                                  (size_t)n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
     FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (A)
         for (int i = 0; i < n; ++i)

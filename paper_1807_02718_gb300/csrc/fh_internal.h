@@ -40,11 +40,27 @@ void launch_geometry(const CurveParams &cp, int S, int maxN, const int *N, const
 void launch_kress_tables(int n_tab, int maxN, const int *tab_N, const int *tab_off,
                          double *kress, double *logsin, cudaStream_t st);
 
+// Frequency subgroups: up to kGroup consecutive solves with equal N (hence
+// identical nodes).  Their kernels share the geometry of each node pair and
+// advance e^{i kappa_j r} from one frequency to the next by a complex product
+// instead of a sincos per frequency.
+constexpr int kGroup = 8;
+struct Subgroups {
+    const int2 *sg;            // (first solve s0, count) per subgroup
+    const long long *tile_off; // assembly tiles, prefix over subgroups
+    const double *dkappa;      // mean kappa step inside each subgroup
+};
+
 // ---- CFIE assembly (k_assemble.cu) ----
 // Matrices are column-major: A_s(i, l) = A[mat_off[s] + l * N_s + i].
 void launch_assemble(const SolveTables &t, int S, const long long *tile_off, long long n_tiles,
                      const double2 *z, const double2 *dz, const double2 *ddz,
                      const double *kress, const double *logsin, double2 *A, cudaStream_t st);
+// Grouped assembly: every matrix of subgroup g at A + mat_off[s] + out_shift.
+void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
+                            long long n_tiles, const double2 *z, const double2 *dz,
+                            const double2 *ddz, const double *kress, const double *logsin,
+                            double2 *A, long long out_shift, cudaStream_t st);
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
                 double p0, double p1, double2 *g, cudaStream_t st);
 
@@ -71,9 +87,10 @@ void launch_window_spectra(const double *a, int n_samples, long long start0, lon
 
 // ---- target fields (k_field.cu) ----
 // V[j * n_x + i] = V(x_i, omega_j); V[0 * n_x + i] = 1 (omega_0 = 0).
-void launch_target_field(const SolveTables &t, int S, const int *solve_j, int maxN,
-                         const double2 *z, const double2 *dz, const double2 *psi,
-                         const double *x, int n_x, double2 *V, cudaStream_t st);
+void launch_target_field(const SolveTables &t, const Subgroups &g, int n_groups,
+                         const int *solve_j, const double2 *z, const double2 *dz,
+                         const double2 *psi, const double *x, int n_x, double2 *V,
+                         cudaStream_t st);
 
 // Kernel Bessel routine on n arguments: out[6i..6i+5] = J0, Y0, J1, Y1 (joint
 // routine) and J0, Y0 (H0-only routine).

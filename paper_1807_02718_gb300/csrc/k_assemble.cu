@@ -102,6 +102,119 @@ __global__ void __launch_bounds__(256) assemble_kernel(
     }
 }
 
+// Grouped assembly: one CTA per 32 x 32 tile of a frequency subgroup (up to
+// kGroup consecutive frequencies with the same N, hence the same nodes).  The
+// geometry of each entry (r, N_il, Kress weight, log kernel, speeds) and the
+// phase e^{i(kappa_0 r - pi/4)} with its step e^{i dkappa r} are computed once;
+// each frequency then evaluates the P/Q series and writes its own matrix.
+__global__ void __launch_bounds__(256) assemble_group_kernel(
+    SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ z,
+    const double2 *__restrict__ dz, const double2 *__restrict__ ddz,
+    const double *__restrict__ kress, const double *__restrict__ logsin,
+    double2 *__restrict__ A, long long out_shift) {
+    const long long b = blockIdx.x;
+    const int g = find_solve(grp.tile_off, n_groups, b);
+    const int2 sgv = grp.sg[g];
+    const int s0 = sgv.x, cnt = sgv.y;
+    const int N = t.N[s0];
+    const int nt = (N + kTile - 1) / kTile;
+    const long long lt = b - grp.tile_off[g];
+    const int tr = (int)(lt % nt), tc = (int)(lt / nt);
+    __shared__ double kap[kGroup], eta[kGroup], ikap[kGroup], isqk[kGroup], corr[kGroup];
+    __shared__ long long moff[kGroup];
+    const double dk = grp.dkappa[g];
+    if (threadIdx.x < kGroup) {
+        const int j = threadIdx.x;
+        const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
+        kap[j] = k;
+        eta[j] = (j < cnt) ? t.eta[s0 + j] : 0.0;
+        ikap[j] = 1.0 / k;
+        isqk[j] = 1.0 / sqrt(k);
+        moff[j] = ((j < cnt) ? t.mat_off[s0 + j] : 0) + out_shift;
+    }
+    __syncthreads();
+    if (threadIdx.x < kGroup) corr[threadIdx.x] = kap[threadIdx.x] - (kap[0] + threadIdx.x * dk);
+    __syncthreads();
+    const int i = tr * kTile + (threadIdx.x & 31);
+    if (i >= N) return;
+    const int vo = t.vec_off[s0];
+    const int to = t.tab_off[t.tab[s0]];
+    const double pin = 2.0 * kPi / (double)N;   // pi / n
+    const double2 zi = z[vo + i], dzi = dz[vo + i];
+    const double si = sqrt(dzi.x * dzi.x + dzi.y * dzi.y);
+    const double inv4pi = 1.0 / (4.0 * kPi);
+
+    for (int q = threadIdx.x >> 5; q < kTile; q += 8) {
+        const int l = tc * kTile + q;
+        if (l >= N) break;
+        int d = i - l;
+        if (d < 0) d += N;
+        const double Rw = kress[to + d];
+        const double2 dzl = dz[vo + l];
+        const double sl = sqrt(dzl.x * dzl.x + dzl.y * dzl.y);
+        const long long e_off = (long long)l * N + i;
+        if (l == i) {
+            const double2 dd = ddz[vo + i];
+            const double M1 = -si * inv4pi;
+            const double L2r = (dd.x * dzi.y - dd.y * dzi.x) * inv4pi / (si * si);
+            for (int j = 0; j < cnt; ++j) {
+                const double M2r = (-kEulerGamma / (2.0 * kPi) - log(kap[j] * si * 0.5) / (2.0 * kPi)) * si;
+                const double M2i = 0.25 * si;
+                const double ar = 0.5 + pin * (L2r + eta[j] * M2i);
+                const double ai = Rw * (-eta[j] * M1) + pin * (0.0 - eta[j] * M2r);
+                A[moff[j] + e_off] = make_double2(ar, ai);
+            }
+            continue;
+        }
+        const double2 zl = z[vo + l];
+        const double d1 = zl.x - zi.x, d2 = zl.y - zi.y;
+        const double r = sqrt(d1 * d1 + d2 * d2);
+        const double ir = 1.0 / r;
+        const double Nil = dzi.y * d1 - dzi.x * d2;
+        const double ls = logsin[to + d];
+        const double gg = Nil * sl / (si * r);
+        const double amp = sqrt(kTwoOverPi * ir);
+        double sn, cs, ss, sc;
+        sincos(kap[0] * r, &sn, &cs);
+        sincos(dk * r, &ss, &sc);
+        double c0 = (cs + sn) * kSqrtHalf, s0v = (sn - cs) * kSqrtHalf;   // e^{i(x0 - pi/4)}
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+            if (j < cnt) {
+                const double kappa = kap[j];
+                const double x = kappa * r;
+                double J0, Y0, J1, Y1;
+                if (x >= 8.0) {
+                    const double dl = corr[j] * r;
+                    const double c = c0 - dl * s0v, sv = s0v + dl * c0;
+                    double P0, Q0, P1, Q1;
+                    hankel_pq_r8<true>(x, 8.0 * ir * ikap[j], P0, Q0, P1, Q1);
+                    const double Am = amp * isqk[j];
+                    J0 = Am * (P0 * c - Q0 * sv);
+                    Y0 = Am * (P0 * sv + Q0 * c);
+                    J1 = Am * (P1 * sv + Q1 * c);
+                    Y1 = Am * (Q1 * sv - P1 * c);
+                } else {
+                    bessel_small(x, J0, Y0, J1, Y1);
+                }
+                const double Mr = -0.25 * Y0 * sl, Mi = 0.25 * J0 * sl;
+                const double M1 = -J0 * sl * inv4pi;
+                const double M2r = Mr - M1 * ls;
+                const double Lr = -0.25 * kappa * Y1 * gg, Li = 0.25 * kappa * J1 * gg;
+                const double L1 = -kappa * inv4pi * J1 * gg;
+                const double L2r = Lr - L1 * ls;
+                const double et = eta[j];
+                const double ar = Rw * L1 + pin * (L2r + et * Mi);
+                const double ai = Rw * (-et * M1) + pin * (Li - et * M2r);
+                A[moff[j] + e_off] = make_double2(ar, ai);
+                const double cn = c0 * sc - s0v * ss;
+                s0v = s0v * sc + c0 * ss;
+                c0 = cn;
+            }
+        }
+    }
+}
+
 // g_i = dB/dn - i eta B = i (kappa p.nu_i - eta) e^{i kappa p.z_i}
 __global__ void rhs_kernel(SolveTables t, const double2 *__restrict__ z,
                            const double2 *__restrict__ dz, double p0, double p1,
@@ -129,6 +242,15 @@ void launch_assemble(const SolveTables &t, int S, const long long *tile_off, lon
     if (n_tiles <= 0) return;
     assemble_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, S, tile_off, z, dz, ddz, kress,
                                                        logsin, A);
+}
+
+void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
+                            long long n_tiles, const double2 *z, const double2 *dz,
+                            const double2 *ddz, const double *kress, const double *logsin,
+                            double2 *A, long long out_shift, cudaStream_t st) {
+    if (n_tiles <= 0 || n_groups <= 0) return;
+    assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
+                                                             logsin, A, out_shift);
 }
 
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,

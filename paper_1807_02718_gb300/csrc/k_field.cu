@@ -15,36 +15,67 @@ namespace fh {
 namespace {
 
 constexpr int kTgt = 128;
-constexpr int kSrc = 256;
+constexpr int kSrc = 128;
 
-__global__ void __launch_bounds__(kTgt) field_kernel(
-    SolveTables t, const int *__restrict__ solve_j, const double2 *__restrict__ z,
-    const double2 *__restrict__ dz, const double2 *__restrict__ psi,
-    const double *__restrict__ x, int n_x, double2 *__restrict__ V) {
-    const int s = blockIdx.y;
-    const int N = t.N[s];
-    const int vo = t.vec_off[s];
-    const double kappa = t.kappa[s];
+// One CTA per (128 targets, frequency subgroup).  For each target-node pair
+// the distance r, 1/r, sqrt(2/(pi r)), e^{i(kappa_0 r - pi/4)} and the step
+// e^{i dkappa r} are formed once; frequency j of the subgroup then needs only
+// the short P0/Q0 Chebyshev series (x = kappa_j r >= 8) or the small-argument
+// series (x < 8).  The phase carries the exact kappa_j through a first-order
+// correction e^{i (kappa_j - kappa_0 - j dkappa) r} (the difference is at
+// rounding level for a uniform mesh).
+__global__ void __launch_bounds__(kTgt) field_group_kernel(
+    SolveTables t, Subgroups grp, const int *__restrict__ solve_j,
+    const double2 *__restrict__ z, const double2 *__restrict__ dz,
+    const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
+    double2 *__restrict__ V) {
+    const int g = blockIdx.y;
+    const int2 sgv = grp.sg[g];
+    const int s0 = sgv.x, cnt = sgv.y;
+    const int N = t.N[s0];
+    const int vo0 = t.vec_off[s0];
     const double w = 2.0 * kPi / (double)N * 0.25;   // (pi/n) / 4
+    const double dk = grp.dkappa[g];
+    __shared__ double kap[kGroup], ikap[kGroup], isqk[kGroup], corr[kGroup];
+    __shared__ int voff[kGroup];
+    __shared__ double2 zs[kSrc];
+    __shared__ double2 ps[kGroup][kSrc];   // (pi/n)|z'|/4 * psi_j at each node
+    if (threadIdx.x < kGroup) {
+        const int j = threadIdx.x;
+        const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
+        kap[j] = k;
+        ikap[j] = 1.0 / k;
+        isqk[j] = 1.0 / sqrt(k);
+        voff[j] = (j < cnt) ? t.vec_off[s0 + j] : vo0;
+    }
+    __syncthreads();
+    if (threadIdx.x < kGroup) corr[threadIdx.x] = kap[threadIdx.x] - (kap[0] + threadIdx.x * dk);
     const int it = blockIdx.x * kTgt + threadIdx.x;
     double px = 0.0, py = 0.0;
     if (it < n_x) { px = x[2 * it]; py = x[2 * it + 1]; }
-    __shared__ double2 zs[kSrc];
-    __shared__ double2 cs[kSrc];
-    double vr = 0.0, vi = 0.0;
+    double2 acc[kGroup];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j) acc[j] = make_double2(0.0, 0.0);
     for (int i0 = 0; i0 < N; i0 += kSrc) {
         __syncthreads();
         for (int e = threadIdx.x; e < kSrc; e += kTgt) {
             const int i = i0 + e;
+            double2 zz = make_double2(0.0, 0.0);
+            double sp = 0.0;
             if (i < N) {
-                const double2 d = dz[vo + i];
-                const double sp = sqrt(d.x * d.x + d.y * d.y) * w;
-                const double2 p = psi[vo + i];
-                zs[e] = z[vo + i];
-                cs[e] = make_double2(p.x * sp, p.y * sp);
-            } else {
-                zs[e] = make_double2(0.0, 0.0);
-                cs[e] = make_double2(0.0, 0.0);
+                const double2 d = dz[vo0 + i];
+                sp = sqrt(d.x * d.x + d.y * d.y) * w;
+                zz = z[vo0 + i];
+            }
+            zs[e] = zz;
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                double2 v = make_double2(0.0, 0.0);
+                if (i < N && j < cnt) {
+                    const double2 q = psi[voff[j] + i];
+                    v = make_double2(q.x * sp, q.y * sp);
+                }
+                ps[j][e] = v;
             }
         }
         __syncthreads();
@@ -52,17 +83,44 @@ __global__ void __launch_bounds__(kTgt) field_kernel(
             const int ne = min(kSrc, N - i0);
             for (int e = 0; e < ne; ++e) {
                 const double d1 = px - zs[e].x, d2 = py - zs[e].y;
-                const double arg = kappa * sqrt(d1 * d1 + d2 * d2);
-                double J0, Y0;
-                bessel_j0y0(arg, J0, Y0);
-                // (i)(J0 + i Y0) c = (-Y0 + i J0) c
-                const double2 c = cs[e];
-                vr += -Y0 * c.x - J0 * c.y;
-                vi += -Y0 * c.y + J0 * c.x;
+                const double r = sqrt(d1 * d1 + d2 * d2);
+                const double ir = 1.0 / r;
+                const double ar = sqrt(kTwoOverPi * ir);
+                double sn, cs, ss, sc;
+                sincos(kap[0] * r, &sn, &cs);
+                sincos(dk * r, &ss, &sc);
+                double c0 = (cs + sn) * kSqrtHalf, s0v = (sn - cs) * kSqrtHalf;   // e^{i(x0 - pi/4)}
+#pragma unroll
+                for (int j = 0; j < kGroup; ++j) {
+                    if (j < cnt) {
+                        const double xj = kap[j] * r;
+                        double J0, Y0;
+                        if (xj >= 8.0) {
+                            const double dl = corr[j] * r;
+                            const double c = c0 - dl * s0v, sv = s0v + dl * c0;
+                            double P0, Q0, P1, Q1;
+                            hankel_pq_r8<false>(xj, 8.0 * ir * ikap[j], P0, Q0, P1, Q1);
+                            const double A = ar * isqk[j];
+                            J0 = A * (P0 * c - Q0 * sv);
+                            Y0 = A * (P0 * sv + Q0 * c);
+                        } else {
+                            bessel_small0(xj, J0, Y0);
+                        }
+                        const double2 q = ps[j][e];
+                        acc[j].x += -Y0 * q.x - J0 * q.y;
+                        acc[j].y += -Y0 * q.y + J0 * q.x;
+                        const double cn = c0 * sc - s0v * ss;
+                        s0v = s0v * sc + c0 * ss;
+                        c0 = cn;
+                    }
+                }
             }
         }
     }
-    if (it < n_x) V[(long long)solve_j[s] * n_x + it] = make_double2(vr, vi);
+    if (it < n_x)
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j)
+            if (j < cnt) V[(long long)solve_j[s0 + j] * n_x + it] = acc[j];
 }
 
 __global__ void field_zero_freq_kernel(int n_x, double2 *__restrict__ V) {
@@ -91,15 +149,15 @@ void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st) {
     if (n > 0) bessel_eval_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, n, out);
 }
 
-void launch_target_field(const SolveTables &t, int S, const int *solve_j, int maxN,
-                         const double2 *z, const double2 *dz, const double2 *psi,
-                         const double *x, int n_x, double2 *V, cudaStream_t st) {
-    (void)maxN;
+void launch_target_field(const SolveTables &t, const Subgroups &g, int n_groups,
+                         const int *solve_j, const double2 *z, const double2 *dz,
+                         const double2 *psi, const double *x, int n_x, double2 *V,
+                         cudaStream_t st) {
     if (n_x <= 0) return;
     field_zero_freq_kernel<<<(n_x + 255) / 256, 256, 0, st>>>(n_x, V);
-    if (S <= 0) return;
-    dim3 grid((n_x + kTgt - 1) / kTgt, S);
-    field_kernel<<<grid, kTgt, 0, st>>>(t, solve_j, z, dz, psi, x, n_x, V);
+    if (n_groups <= 0) return;
+    dim3 grid((n_x + kTgt - 1) / kTgt, n_groups);
+    field_group_kernel<<<grid, kTgt, 0, st>>>(t, g, solve_j, z, dz, psi, x, n_x, V);
 }
 
 }  // namespace fh
