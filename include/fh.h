@@ -186,6 +186,34 @@ fh_status fh_get_target_field(fh_ctx *ctx, double *V);
 fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, int n_T,
                         double *u_out);
 
+/* ---- synthesis without allocation ---- */
+
+/* The paper has no counterpart to this entry point: it exists for callers that
+ * cannot allocate device memory when they need a field (a serving loop with a
+ * fixed memory budget, a host whose device memory comes from its own arena, or
+ * code that must avoid the implicit synchronisation of cudaMalloc/cudaFree).
+ * It runs the synthesis steps T0-T6 (the same kernels as fh_sample's
+ * weights and contraction) with all scratch in one static device array
+ * (about 10.4 MB, held on every GPU that loads the library until exit); it
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   J, W     frequency mesh: J nodes on [0, W] (2 <= J <= 2049)
+ *   K, d_s   K window centres (device, K doubles)
+ *   d_B      window spectra B_k^slow(omega_j), K*J complex, B[k*J + j] (device)
+ *   d_V      target fields, J*n_x complex, V[j*n_x + i] (device); V[0*n_x + i]
+ *            is the omega = 0 value (1 for the 2D low-frequency limit)
+ *   d_T      n_T sample times (device);  d_u  n_x*n_T doubles, u[i*n_T + l] (device)
+ *   stream   cudaStream_t to launch on (NULL: legacy default stream)
+ * Limits: J*n_T <= 524288.  Larger sizes return FH_EINVAL; nothing is launched.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  Every call reuses the same array, whose contents are whatever the
+ * last call left (each call overwrites all it reads); calls that overlap on
+ * the GPU (different streams, or devices sharing nothing but this array's
+ * symbol on one device) race on it and must be serialised by the caller. */
+fh_status fh_synthesize_static(int J, double W, int K, const double *d_s, const double *d_B,
+                               const double *d_V, int n_x, const double *d_T, int n_T,
+                               double *d_u, void *stream);
+
 /* ---- kernel timing and launch accounting ---- */
 
 /* Phases of the path, in order: nodes and tables (a1), CFIE assembly with

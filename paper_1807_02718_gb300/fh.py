@@ -30,7 +30,7 @@ EXPORTED = [
     "fh_sample_dev", "fh_get_num_windows", "fh_get_window_spectra", "fh_get_geometry",
     "fh_assemble_matrix", "fh_get_density", "fh_set_densities", "fh_get_target_field",
     "fh_synthesize", "fh_set_timing", "fh_get_timings", "fh_probe_fma_peak",
-    "fh_eval_bessel",
+    "fh_eval_bessel", "fh_synthesize_static",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "spectra", "field", "weights", "contract"]
@@ -96,6 +96,8 @@ def load_library(path: str | None = None):
         "fh_get_timings": (C.c_int, [vp, C.POINTER(fh_timings), C.c_int]),
         "fh_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
         "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
+        "fh_synthesize_static": (C.c_int, [C.c_int, C.c_double, C.c_int, vp, vp, vp, C.c_int, vp,
+                                           C.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -293,6 +295,20 @@ def fh_eval_bessel(x):
     if st != FH_OK:
         raise FHError(st, "fh_eval_bessel failed")
     return out
+
+
+def fh_synthesize_static(J: int, W: float, d_s, d_B, d_V, d_T, d_u, stream=None):
+    """Synthesis into d_u without any allocation (static device scratch).
+    d_s (K,), d_B (K*J complex as 2*K*J doubles), d_V (J*n_x complex as doubles,
+    frequency-major), d_T (n_T,), d_u (n_x*n_T,): float64 CUDA tensors."""
+    K = d_s.numel()
+    n_T = d_T.numel()
+    n_x = d_V.numel() // (2 * J)
+    st = load_library().fh_synthesize_static(
+        int(J), float(W), K, _dev_ptr(d_s), _dev_ptr(d_B), _dev_ptr(d_V), n_x, _dev_ptr(d_T), n_T,
+        _dev_ptr(d_u), C.c_void_p(stream or 0))
+    if st != FH_OK:
+        raise FHError(st, "fh_synthesize_static failed")
 
 
 class Problem:
