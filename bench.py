@@ -161,6 +161,17 @@ def oracle_sample_step(wl, n_solve=24, n_tgt=24):
     return est, desc
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """Max of a per-rank scalar over all ranks (identity at world size 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -256,10 +267,7 @@ def run_gpu(args, world, rank, local):
     total_ms = sum(per_step)
     tim = F.fh_get_timings(pr.ctx, reset=True)
     launches = sum(v["launches"] for v in tim.values())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     value = world * S * args.steps / (total_ms / 1e3)
     samples_per_s = world * n_x * n_T * args.steps / (total_ms / 1e3)
 
@@ -288,10 +296,7 @@ def run_gpu(args, world, rank, local):
         u_host = F.fh_sample(pr.ctx, wl.x, wl.T)
         e2e_times.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, world, dev)
     assert np.all(np.isfinite(u_host))
     h2d = wl.a.nbytes + wl.x.nbytes + wl.T.nbytes + wl.omega.nbytes + wl.N.nbytes
     d2h = u_host.nbytes
