@@ -82,6 +82,43 @@ __device__ __forceinline__ void hankel_pq_r8(double x, double r8, double &P0, do
     }
 }
 
+// Horner form of P0, Q0 (and P1, Q1) for x >= 8 on the intervals of kPQ:
+// the table is staged in shared memory by pq_stage() (threads of a warp may
+// fall into different intervals).
+struct PQShared {
+    double c[kPQ_NI * 4 * kPQ_TERMS];
+    double uc[kPQ_NI], iuh[kPQ_NI];
+};
+
+__device__ __forceinline__ void pq_stage(PQShared &tb) {
+    for (int i = threadIdx.x; i < kPQ_NI * 4 * kPQ_TERMS; i += blockDim.x) tb.c[i] = kPQ[i];
+    for (int i = threadIdx.x; i < kPQ_NI; i += blockDim.x) {
+        tb.uc[i] = kPQ_UC[i];
+        tb.iuh[i] = 1.0 / kPQ_UH[i];
+    }
+}
+
+__device__ __forceinline__ double horner8(const double *c, double t) {
+    double a = c[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) a = fma(a, t, c[k]);
+    return a;
+}
+
+template <bool want1>
+__device__ __forceinline__ void pq_horner(const PQShared &tb, double x, double r8, double &P0,
+                                          double &Q0, double &P1, double &Q1) {
+    const int k = (x >= 10.0) + (x >= 13.0) + (x >= 18.0) + (x >= 28.0) + (x >= 60.0);
+    const double t = (r8 * r8 - tb.uc[k]) * tb.iuh[k];
+    const double *c = tb.c + k * 4 * kPQ_TERMS;
+    P0 = horner8(c, t);
+    Q0 = r8 * horner8(c + kPQ_TERMS, t);
+    if (want1) {
+        P1 = horner8(c + 2 * kPQ_TERMS, t);
+        Q1 = r8 * horner8(c + 3 * kPQ_TERMS, t);
+    }
+}
+
 // Small-argument branch (x < 8) of the joint routine.
 __device__ __forceinline__ void bessel_small(double x, double &J0, double &Y0, double &J1,
                                              double &Y1) {

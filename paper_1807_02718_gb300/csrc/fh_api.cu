@@ -541,7 +541,7 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         fh::launch_lu_factor_fp32(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                                   ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
                                   ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
-                                  ctx->d_info.as<int>(), ctx->stream);
+                                  ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
         fh::launch_lu_refine(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                              ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
                              ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),

@@ -73,8 +73,10 @@ void launch_lu_solve_fp64(const int *order, int S, const int *N, const long long
 
 // Mixed precision: FP32 copy of A, FP32 LU, FP64 residual refinement.
 void launch_convert_fp32(const double2 *A, float2 *A32, long long n, cudaStream_t st);
+// piv (per system, length N) holds the inverse row permutation on return.
 void launch_lu_factor_fp32(const int *order, int S, const int *N, const long long *mat_off,
-                           float2 *A32, int *piv, const int *vec_off, int *info, cudaStream_t st);
+                           float2 *A32, int *piv, const int *vec_off, int *info, int maxN,
+                           cudaStream_t st);
 void launch_lu_refine(const int *order, int S, const int *N, const long long *mat_off,
                       const int *vec_off, const double2 *A, const float2 *LU32, const int *piv,
                       const double2 *g, double2 *x, int max_iters, double tol, int *iters,

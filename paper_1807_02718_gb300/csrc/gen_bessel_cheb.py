@@ -84,6 +84,54 @@ def large(x0, x1):
     return [cheb(f) for f in fs], u0
 
 
+PQ_BREAKS = [8, 10, 13, 18, 28, 60]   # x intervals [8,10), ..., [60, inf)
+PQ_TERMS = 8
+
+
+def cheb_to_monomial(c):
+    """Monomial coefficients a_k of sum_j c_j T_j(t) (exact in mpmath)."""
+    n = len(c)
+    T = [[mp.mpf(1)] + [mp.mpf(0)] * (n - 1), [mp.mpf(0), mp.mpf(1)] + [mp.mpf(0)] * (n - 2)]
+    for j in range(2, n):
+        nxt = [mp.mpf(0)] * n
+        for k in range(n):
+            if k + 1 < n:
+                nxt[k + 1] += 2 * T[j - 1][k]
+            nxt[k] -= T[j - 2][k]
+        T.append(nxt)
+    a = [mp.mpf(0)] * n
+    for j in range(n):
+        for k in range(n):
+            a[k] += c[j] * T[j][k]
+    return a
+
+
+def pq_table():
+    """Horner tables for P0, q0, P1, q1 (Q = (8/x) q) on each x interval, in the
+    variable t = (u - uc)/uh of u = (8/x)^2 mapped to [-1, 1]."""
+    rows, ucs, uhs = [], [], []
+    bounds = PQ_BREAKS + [mp.inf]
+    for x0, x1 in zip(bounds[:-1], bounds[1:]):
+        u_hi = (mp.mpf(8) / x0) ** 2
+        u_lo = mp.mpf(0) if x1 == mp.inf else (mp.mpf(8) / x1) ** 2
+        uc, uh = (u_hi + u_lo) / 2, (u_hi - u_lo) / 2
+
+        def x_of(t, uc=uc, uh=uh):
+            return 8 / mp.sqrt(uc + uh * t)
+
+        fs = [lambda t: pq(0, x_of(t))[0], lambda t: pq(0, x_of(t))[1] * x_of(t) / 8,
+              lambda t: pq(1, x_of(t))[0], lambda t: pq(1, x_of(t))[1] * x_of(t) / 8]
+        for f in fs:
+            c = cheb(f)
+            if len(c) > PQ_TERMS:
+                raise SystemExit(f"interval [{x0},{x1}) needs {len(c)} terms")
+            c = c + [mp.mpf(0)] * (PQ_TERMS - len(c))
+            rows.append(cheb_to_monomial(c))
+        ucs.append(uc)
+        uhs.append(uh)
+    return rows, ucs, uhs
+
+
 def emit(name, c):
     body = ",\n    ".join(mp.nstr(v, 20, min_fixed=-1, max_fixed=-1) for v in c)
     return f"constexpr int {name}_N = {len(c)};\nstatic __device__ __constant__ double {name}[{len(c)}] = {{\n    {body}}};\n"
@@ -102,6 +150,15 @@ def main():
         out.append(emit(f"kBLo{k}", c))
     for k, c in enumerate(b_hi):
         out.append(emit(f"kBHi{k}", c))
+    rows, ucs, uhs = pq_table()
+    ni = len(ucs)
+    out.append(f"constexpr int kPQ_NI = {ni};          // x intervals {PQ_BREAKS} .. inf")
+    out.append(f"constexpr int kPQ_TERMS = {PQ_TERMS};")
+    out.append("// Horner coefficients [interval][P0, q0, P1, q1][power of t], t = (u - uc)/uh, u = (8/x)^2")
+    flat = [v for r in rows for v in r]
+    out.append(emit("kPQ", flat))
+    out.append(emit("kPQ_UC", ucs))
+    out.append(emit("kPQ_UH", uhs))
     print("\n".join(out))
 
 

@@ -122,6 +122,8 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
     const int tr = (int)(lt % nt), tc = (int)(lt / nt);
     __shared__ double kap[kGroup], eta[kGroup], ikap[kGroup], isqk[kGroup], corr[kGroup];
     __shared__ long long moff[kGroup];
+    __shared__ PQShared pqt;
+    pq_stage(pqt);
     const double dk = grp.dkappa[g];
     if (threadIdx.x < kGroup) {
         const int j = threadIdx.x;
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
                     const double dl = corr[j] * r;
                     const double c = c0 - dl * s0v, sv = s0v + dl * c0;
                     double P0, Q0, P1, Q1;
-                    hankel_pq_r8<true>(x, 8.0 * ir * ikap[j], P0, Q0, P1, Q1);
+                    pq_horner<true>(pqt, x, 8.0 * ir * ikap[j], P0, Q0, P1, Q1);
                     const double Am = amp * isqk[j];
                     J0 = Am * (P0 * c - Q0 * sv);
                     Y0 = Am * (P0 * sv + Q0 * c);

@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(kTgt) field_group_kernel(
     __shared__ int voff[kGroup];
     __shared__ double2 zs[kSrc];
     __shared__ double2 ps[kGroup][kSrc];   // (pi/n)|z'|/4 * psi_j at each node
+    __shared__ PQShared pqt;
+    pq_stage(pqt);
     if (threadIdx.x < kGroup) {
         const int j = threadIdx.x;
         const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(kTgt) field_group_kernel(
                             const double dl = corr[j] * r;
                             const double c = c0 - dl * s0v, sv = s0v + dl * c0;
                             double P0, Q0, P1, Q1;
-                            hankel_pq_r8<false>(xj, 8.0 * ir * ikap[j], P0, Q0, P1, Q1);
+                            pq_horner<false>(pqt, xj, 8.0 * ir * ikap[j], P0, Q0, P1, Q1);
                             const double A = ar * isqk[j];
                             J0 = A * (P0 * c - Q0 * sv);
                             Y0 = A * (P0 * sv + Q0 * c);

@@ -177,33 +177,43 @@ __global__ void __launch_bounds__(256) lu_factor_fp32_kernel(
         }
     }
 #undef AT
-}
-
-// y <- (LU)^{-1} P y in FP32, y in shared memory (n complex).  L is unit lower.
-__device__ void lu_solve_shared(const float2 *__restrict__ a, const int *__restrict__ pv, int n,
-                                float2 *y) {
-    const int tid = threadIdx.x, lane = tid & 31;
-#define AT(i, j) a[(long long)(j) * n + (i)]
+    // Replace the swap sequence by the inverse row permutation: row i of the
+    // original system becomes row iperm[i] of the factored one.
+    extern __shared__ int perm[];
+    for (int i = tid; i < n; i += 256) perm[i] = i;
+    __syncthreads();
     if (tid == 0)
         for (int c = 0; c < n; ++c) {
             const int p = pv[c];
-            if (p != c) { const float2 t = y[c]; y[c] = y[p]; y[p] = t; }
+            if (p != c) { const int t0 = perm[c]; perm[c] = perm[p]; perm[p] = t0; }
         }
     __syncthreads();
-    // forward: L y = y
+    for (int k = tid; k < n; k += 256) pv[perm[k]] = k;
+}
+
+// y <- U^{-1} L^{-1} y in FP32 (y already in factored row order), y in shared
+// memory.  L is unit lower.  Each 32-wide diagonal block is first loaded into
+// registers (lane i holds row i of the block), so the warp's dependent chain
+// runs on shuffles only; the rest of the CTA then applies the block to the
+// remaining rows.
+__device__ void lu_solve_shared(const float2 *__restrict__ a, int n, float2 *y) {
+    const int tid = threadIdx.x, lane = tid & 31;
+#define AT(i, j) a[(long long)(j) * n + (i)]
     for (int jb = 0; jb < n; jb += 32) {
         const int je = min(jb + 32, n);
         if (tid < 32) {
             const int i = jb + lane;
+            float2 row[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                row[q] = (i < je && jb + q < i) ? AT(i, jb + q) : make_float2(0.f, 0.f);
             float2 yi = (i < je) ? y[i] : make_float2(0.f, 0.f);
-            for (int j = jb; j < je; ++j) {
-                const float yjx = __shfl_sync(0xffffffffu, yi.x, j - jb);
-                const float yjy = __shfl_sync(0xffffffffu, yi.y, j - jb);
-                if (i > j && i < je) {
-                    const float2 l = AT(i, j);
-                    yi.x -= l.x * yjx - l.y * yjy;
-                    yi.y -= l.x * yjy + l.y * yjx;
-                }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const float yjx = __shfl_sync(0xffffffffu, yi.x, q);
+                const float yjy = __shfl_sync(0xffffffffu, yi.y, q);
+                yi.x -= row[q].x * yjx - row[q].y * yjy;
+                yi.y -= row[q].x * yjy + row[q].y * yjx;
             }
             if (i < je) y[i] = yi;
         }
@@ -219,25 +229,28 @@ __device__ void lu_solve_shared(const float2 *__restrict__ a, const int *__restr
         }
         __syncthreads();
     }
-    // backward: U y = y
     const int nblk = (n + 31) / 32;
     for (int b = nblk - 1; b >= 0; --b) {
         const int jb = b * 32, je = min(jb + 32, n);
         if (tid < 32) {
             const int i = jb + lane;
+            float2 row[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                row[q] = (i < je && jb + q >= i && jb + q < je) ? AT(i, jb + q) : make_float2(0.f, 0.f);
             float2 yi = (i < je) ? y[i] : make_float2(0.f, 0.f);
-            for (int j = je - 1; j >= jb; --j) {
-                if (i == j) {
-                    const float2 u = AT(j, j);
+#pragma unroll
+            for (int q = 31; q >= 0; --q) {
+                if (jb + q == i && i < je) {
+                    const float2 u = row[q];
                     const float d = u.x * u.x + u.y * u.y;
                     yi = make_float2((yi.x * u.x + yi.y * u.y) / d, (yi.y * u.x - yi.x * u.y) / d);
                 }
-                const float yjx = __shfl_sync(0xffffffffu, yi.x, j - jb);
-                const float yjy = __shfl_sync(0xffffffffu, yi.y, j - jb);
-                if (i < j) {
-                    const float2 u = AT(i, j);
-                    yi.x -= u.x * yjx - u.y * yjy;
-                    yi.y -= u.x * yjy + u.y * yjx;
+                const float yjx = __shfl_sync(0xffffffffu, yi.x, q);
+                const float yjy = __shfl_sync(0xffffffffu, yi.y, q);
+                if (jb + q > i && jb + q < je) {
+                    yi.x -= row[q].x * yjx - row[q].y * yjy;
+                    yi.y -= row[q].x * yjy + row[q].y * yjx;
                 }
             }
             if (i < je) y[i] = yi;
@@ -291,7 +304,7 @@ __global__ void __launch_bounds__(256) refine_kernel(
     for (int i = tid; i < n; i += blockDim.x) {
         const double2 gi = g[i];
         xs[i] = make_double2(0.0, 0.0);
-        ys[i] = make_float2((float)gi.x, (float)gi.y);
+        ys[pv[i]] = make_float2((float)gi.x, (float)gi.y);
         gmax = fmax(gmax, fabs(gi.x) + fabs(gi.y));
     }
     gmax = block_max(gmax, red);
@@ -300,7 +313,7 @@ __global__ void __launch_bounds__(256) refine_kernel(
     double rmax = gmax;
     while (it < max_iters && !done) {
         __syncthreads();
-        lu_solve_shared(lu, pv, n, ys);
+        lu_solve_shared(lu, n, ys);
         double dmax = 0.0, xmax = 0.0;
         for (int i = tid; i < n; i += blockDim.x) {
             const float2 d = ys[i];
@@ -324,7 +337,7 @@ __global__ void __launch_bounds__(256) refine_kernel(
                 rr -= al.x * xl.x - al.y * xl.y;
                 ri -= al.x * xl.y + al.y * xl.x;
             }
-            ys[i] = make_float2((float)rr, (float)ri);
+            ys[pv[i]] = make_float2((float)rr, (float)ri);
             rloc = fmax(rloc, fabs(rr) + fabs(ri));
         }
         rmax = block_max(rloc, red);
@@ -354,9 +367,16 @@ void launch_convert_fp32(const double2 *A, float2 *A32, long long n, cudaStream_
 }
 
 void launch_lu_factor_fp32(const int *order, int S, const int *N, const long long *mat_off,
-                           float2 *A32, int *piv, const int *vec_off, int *info, cudaStream_t st) {
+                           float2 *A32, int *piv, const int *vec_off, int *info, int maxN,
+                           cudaStream_t st) {
     if (S <= 0) return;
-    lu_factor_fp32_kernel<<<S, 256, 0, st>>>(order, N, mat_off, vec_off, A32, piv, info);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(lu_factor_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        attr = true;
+    }
+    lu_factor_fp32_kernel<<<S, 256, maxN * sizeof(int), st>>>(order, N, mat_off, vec_off, A32, piv,
+                                                              info);
 }
 
 void launch_lu_refine(const int *order, int S, const int *N, const long long *mat_off,
