@@ -194,7 +194,7 @@ fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, 
  * code that must avoid the implicit synchronisation of cudaMalloc/cudaFree).
  * It runs the synthesis steps T0-T6 (the same kernels as fh_sample's
  * weights and contraction) with all scratch in one static device array
- * (about 10.4 MB, held on every GPU that loads the library until exit); it
+ * (about 14.0 MB, held on every GPU that loads the library until exit); it
  * calls no cudaMalloc, cudaFree or other allocating routine.
  *   J, W     frequency mesh: J nodes on [0, W] (2 <= J <= 2049)
  *   K, d_s   K window centres (device, K doubles)

@@ -54,7 +54,9 @@ struct fh_ctx {
     std::vector<int2> sg;
     std::vector<long long> sg_tile_off;
     std::vector<double> sg_dk;
-    DevBuf d_sg, d_sg_tile_off, d_sg_dk, d_tmp_sg;
+    std::vector<int2> field_items;      // (subgroup, first node)
+    std::vector<int> item_first;        // per subgroup, + end
+    DevBuf d_sg, d_sg_tile_off, d_sg_dk, d_tmp_sg, d_items, d_item_first, d_part;
 
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_order, d_tile_off;
@@ -86,7 +88,8 @@ struct fh_ctx {
                          &d_kress, &d_logsin, &d_A, &d_psi, &d_info, &d_nu, &d_ph, &d_A32,
                          &d_piv, &d_g, &d_iters, &d_resid, &d_s, &d_B, &d_wa, &d_a, &d_omega,
                          &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_tmpA, &d_tmpg, &d_tmp_i,
-                         &d_tmp_ll, &d_tmp_d, &d_sg, &d_sg_tile_off, &d_sg_dk, &d_tmp_sg};
+                         &d_tmp_ll, &d_tmp_d, &d_sg, &d_sg_tile_off, &d_sg_dk, &d_tmp_sg,
+                         &d_items, &d_item_first, &d_part};
         for (DevBuf *b : all)
             if (b->p) cudaFree(b->p);
         for (auto &pe : pending) {
@@ -280,12 +283,15 @@ fh_status synth_common(fh_ctx *ctx, int n_x, const double *d_T, int n_T, double 
 fh_status sample_common(fh_ctx *ctx, const double *d_x, int n_x, const double *d_T, int n_T,
                         double *d_u) {
     FH_TRY(ensure(ctx, ctx->d_V, (size_t)ctx->J * n_x * sizeof(double2)));
+    const size_t n_items = ctx->field_items.size();
+    FH_TRY(ensure(ctx, ctx->d_part, n_items * fh::kGroup * (size_t)n_x * sizeof(double2)));
     {
-    PhaseScope ps(ctx, FH_PH_FIELD, ctx->S > 0 ? 2 : 1);
-    fh::launch_target_field(tables(ctx), groups(ctx), ctx->n_groups, ctx->d_solve_j.as<int>(),
+    PhaseScope ps(ctx, FH_PH_FIELD, ctx->S > 0 ? 3 : 1);
+    fh::launch_target_field(tables(ctx), groups(ctx), ctx->n_groups, ctx->d_items.as<int2>(),
+                            (int)n_items, ctx->d_item_first.as<int>(), ctx->d_solve_j.as<int>(),
                             ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                            ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_V.as<double2>(),
-                            ctx->stream);
+                            ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_part.as<double2>(),
+                            ctx->d_V.as<double2>(), ctx->stream);
     FH_TRY(check_launch(ctx, "target field"));
     }
     ctx->n_x_last = n_x;
@@ -435,6 +441,15 @@ fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double 
     }
     ctx->sg_tile_off.push_back(gt);
     ctx->n_groups = (int)ctx->sg.size();
+    // field work items: each subgroup's nodes in chunks of kFieldChunk
+    ctx->field_items.clear();
+    ctx->item_first.assign(ctx->n_groups + 1, 0);
+    for (int g = 0; g < ctx->n_groups; ++g) {
+        ctx->item_first[g] = (int)ctx->field_items.size();
+        const int n = ctx->solve_N[ctx->sg[g].x];
+        for (int i0 = 0; i0 < n; i0 += fh::kFieldChunk) ctx->field_items.push_back(make_int2(g, i0));
+    }
+    ctx->item_first[ctx->n_groups] = (int)ctx->field_items.size();
     ctx->group_tiles = gt;
     ctx->vec_total = vo;
     ctx->mat_total = mo;
@@ -462,6 +477,8 @@ fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double 
     FH_TRY(upload(ctx, ctx->d_sg, ctx->sg));
     FH_TRY(upload(ctx, ctx->d_sg_tile_off, ctx->sg_tile_off));
     FH_TRY(upload(ctx, ctx->d_sg_dk, ctx->sg_dk));
+    FH_TRY(upload(ctx, ctx->d_items, ctx->field_items));
+    FH_TRY(upload(ctx, ctx->d_item_first, ctx->item_first));
     FH_TRY(ensure(ctx, ctx->d_z, (size_t)vo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_dz, (size_t)vo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_ddz, (size_t)vo * sizeof(double2)));

@@ -89,10 +89,15 @@ void launch_window_spectra(const double *a, int n_samples, long long start0, lon
 
 // ---- target fields (k_field.cu) ----
 // V[j * n_x + i] = V(x_i, omega_j); V[0 * n_x + i] = 1 (omega_0 = 0).
+// Work items (subgroup, first node) of kFieldChunk nodes; item_first[g] is
+// the first item of subgroup g (n_groups + 1 entries).  part: scratch of
+// n_items * kGroup * n_x complex values.
+constexpr int kFieldChunk = 64;
 void launch_target_field(const SolveTables &t, const Subgroups &g, int n_groups,
+                         const int2 *items, int n_items, const int *item_first,
                          const int *solve_j, const double2 *z, const double2 *dz,
-                         const double2 *psi, const double *x, int n_x, double2 *V,
-                         cudaStream_t st);
+                         const double2 *psi, const double *x, int n_x, double2 *part,
+                         double2 *V, cudaStream_t st);
 
 // Kernel Bessel routine on n arguments: out[6i..6i+5] = J0, Y0, J1, Y1 (joint
 // routine) and J0, Y0 (H0-only routine).
@@ -100,7 +105,7 @@ void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st);
 
 // ---- synthesis (k_synth.cu) ----
 // nu[p * R + r] = sum_{m=-h}^{h-1} (-1)^m (m/h)^r e^{-2 pi i m p / M}.
-constexpr int kFarTerms = 60;
+constexpr int kFarTerms = 170;
 void launch_far_table(int J, int M, double2 *nu, double2 *phase_tab, cudaStream_t st);
 // Gr/Gm: planes [p][t] with u(x,t) = sum_p Vr[p][x] Gr[p][t] + Vi[p][x] Gm[p][t].
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,

@@ -15,31 +15,34 @@ namespace fh {
 namespace {
 
 constexpr int kTgt = 128;
-constexpr int kSrc = 128;
+constexpr int kChunk = 64;   // source nodes per work item
 
-// One CTA per (128 targets, frequency subgroup).  For each target-node pair
-// the distance r, 1/r, sqrt(2/(pi r)), e^{i(kappa_0 r - pi/4)} and the step
-// e^{i dkappa r} are formed once; frequency j of the subgroup then needs only
-// the short P0/Q0 Chebyshev series (x = kappa_j r >= 8) or the small-argument
-// series (x < 8).  The phase carries the exact kappa_j through a first-order
-// correction e^{i (kappa_j - kappa_0 - j dkappa) r} (the difference is at
-// rounding level for a uniform mesh).
-__global__ void __launch_bounds__(kTgt) field_group_kernel(
-    SolveTables t, Subgroups grp, const int *__restrict__ solve_j,
+// Work item w = (subgroup g, node chunk c).  One CTA per (128 targets, item):
+// for each target-node pair the distance r, 1/r, sqrt(2/(pi r)),
+// e^{i(kappa_0 r - pi/4)} and the step e^{i dkappa r} are formed once; each
+// frequency j of the subgroup then needs only the Horner P0/Q0 series
+// (x = kappa_j r >= 8) or the small-argument series (x < 8).  The phase
+// carries the exact kappa_j through a first-order correction
+// e^{i (kappa_j - kappa_0 - j dkappa) r}.  Partial sums per item go to
+// scratch; field_reduce_kernel adds them in a fixed order (the result does
+// not depend on scheduling).
+__global__ void __launch_bounds__(kTgt) field_partial_kernel(
+    SolveTables t, Subgroups grp, const int2 *__restrict__ items,
     const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
-    double2 *__restrict__ V) {
-    const int g = blockIdx.y;
+    double2 *__restrict__ part) {
+    const int w = blockIdx.y;
+    const int2 item = items[w];                 // (subgroup, first node)
+    const int g = item.x, i0 = item.y;
     const int2 sgv = grp.sg[g];
     const int s0 = sgv.x, cnt = sgv.y;
     const int N = t.N[s0];
     const int vo0 = t.vec_off[s0];
-    const double w = 2.0 * kPi / (double)N * 0.25;   // (pi/n) / 4
+    const double wq = 2.0 * kPi / (double)N * 0.25;   // (pi/n) / 4
     const double dk = grp.dkappa[g];
     __shared__ double kap[kGroup], ikap[kGroup], isqk[kGroup], corr[kGroup];
-    __shared__ int voff[kGroup];
-    __shared__ double2 zs[kSrc];
-    __shared__ double2 ps[kGroup][kSrc];   // (pi/n)|z'|/4 * psi_j at each node
+    __shared__ double2 zs[kChunk];
+    __shared__ double2 ps[kGroup][kChunk];   // (pi/n)|z'|/4 * psi_j at each node
     __shared__ PQShared pqt;
     pq_stage(pqt);
     if (threadIdx.x < kGroup) {
@@ -48,81 +51,93 @@ __global__ void __launch_bounds__(kTgt) field_group_kernel(
         kap[j] = k;
         ikap[j] = 1.0 / k;
         isqk[j] = 1.0 / sqrt(k);
-        voff[j] = (j < cnt) ? t.vec_off[s0 + j] : vo0;
+    }
+    const int ne = min(kChunk, N - i0);
+    for (int e = threadIdx.x; e < kChunk; e += kTgt) {
+        const int i = i0 + e;
+        double2 zz = make_double2(0.0, 0.0);
+        double sp = 0.0;
+        if (e < ne) {
+            const double2 d = dz[vo0 + i];
+            sp = sqrt(d.x * d.x + d.y * d.y) * wq;
+            zz = z[vo0 + i];
+        }
+        zs[e] = zz;
+        for (int j = 0; j < kGroup; ++j) {
+            double2 v = make_double2(0.0, 0.0);
+            if (e < ne && j < cnt) {
+                const double2 q = psi[t.vec_off[s0 + j] + i];
+                v = make_double2(q.x * sp, q.y * sp);
+            }
+            ps[j][e] = v;
+        }
     }
     __syncthreads();
     if (threadIdx.x < kGroup) corr[threadIdx.x] = kap[threadIdx.x] - (kap[0] + threadIdx.x * dk);
+    __syncthreads();
     const int it = blockIdx.x * kTgt + threadIdx.x;
-    double px = 0.0, py = 0.0;
-    if (it < n_x) { px = x[2 * it]; py = x[2 * it + 1]; }
+    if (it >= n_x) return;
+    const double px = x[2 * it], py = x[2 * it + 1];
     double2 acc[kGroup];
 #pragma unroll
     for (int j = 0; j < kGroup; ++j) acc[j] = make_double2(0.0, 0.0);
-    for (int i0 = 0; i0 < N; i0 += kSrc) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < kSrc; e += kTgt) {
-            const int i = i0 + e;
-            double2 zz = make_double2(0.0, 0.0);
-            double sp = 0.0;
-            if (i < N) {
-                const double2 d = dz[vo0 + i];
-                sp = sqrt(d.x * d.x + d.y * d.y) * w;
-                zz = z[vo0 + i];
-            }
-            zs[e] = zz;
+    for (int e = 0; e < ne; ++e) {
+        const double d1 = px - zs[e].x, d2 = py - zs[e].y;
+        const double r = sqrt(d1 * d1 + d2 * d2);
+        const double ir = 1.0 / r;
+        const double ar = sqrt(kTwoOverPi * ir);
+        double sn, cs, ss, sc;
+        sincos(kap[0] * r, &sn, &cs);
+        sincos(dk * r, &ss, &sc);
+        double c0 = (cs + sn) * kSqrtHalf, s0v = (sn - cs) * kSqrtHalf;   // e^{i(x0 - pi/4)}
 #pragma unroll
-            for (int j = 0; j < kGroup; ++j) {
-                double2 v = make_double2(0.0, 0.0);
-                if (i < N && j < cnt) {
-                    const double2 q = psi[voff[j] + i];
-                    v = make_double2(q.x * sp, q.y * sp);
+        for (int j = 0; j < kGroup; ++j) {
+            if (j < cnt) {
+                const double xj = kap[j] * r;
+                double J0, Y0;
+                if (xj >= 8.0) {
+                    const double dl = corr[j] * r;
+                    const double c = c0 - dl * s0v, sv = s0v + dl * c0;
+                    double P0, Q0, P1, Q1;
+                    pq_horner<false>(pqt, xj, 8.0 * ir * ikap[j], P0, Q0, P1, Q1);
+                    const double A = ar * isqk[j];
+                    J0 = A * (P0 * c - Q0 * sv);
+                    Y0 = A * (P0 * sv + Q0 * c);
+                } else {
+                    bessel_small0(xj, J0, Y0);
                 }
-                ps[j][e] = v;
-            }
-        }
-        __syncthreads();
-        if (it < n_x) {
-            const int ne = min(kSrc, N - i0);
-            for (int e = 0; e < ne; ++e) {
-                const double d1 = px - zs[e].x, d2 = py - zs[e].y;
-                const double r = sqrt(d1 * d1 + d2 * d2);
-                const double ir = 1.0 / r;
-                const double ar = sqrt(kTwoOverPi * ir);
-                double sn, cs, ss, sc;
-                sincos(kap[0] * r, &sn, &cs);
-                sincos(dk * r, &ss, &sc);
-                double c0 = (cs + sn) * kSqrtHalf, s0v = (sn - cs) * kSqrtHalf;   // e^{i(x0 - pi/4)}
-#pragma unroll
-                for (int j = 0; j < kGroup; ++j) {
-                    if (j < cnt) {
-                        const double xj = kap[j] * r;
-                        double J0, Y0;
-                        if (xj >= 8.0) {
-                            const double dl = corr[j] * r;
-                            const double c = c0 - dl * s0v, sv = s0v + dl * c0;
-                            double P0, Q0, P1, Q1;
-                            pq_horner<false>(pqt, xj, 8.0 * ir * ikap[j], P0, Q0, P1, Q1);
-                            const double A = ar * isqk[j];
-                            J0 = A * (P0 * c - Q0 * sv);
-                            Y0 = A * (P0 * sv + Q0 * c);
-                        } else {
-                            bessel_small0(xj, J0, Y0);
-                        }
-                        const double2 q = ps[j][e];
-                        acc[j].x += -Y0 * q.x - J0 * q.y;
-                        acc[j].y += -Y0 * q.y + J0 * q.x;
-                        const double cn = c0 * sc - s0v * ss;
-                        s0v = s0v * sc + c0 * ss;
-                        c0 = cn;
-                    }
-                }
+                const double2 q = ps[j][e];
+                acc[j].x += -Y0 * q.x - J0 * q.y;
+                acc[j].y += -Y0 * q.y + J0 * q.x;
+                const double cn = c0 * sc - s0v * ss;
+                s0v = s0v * sc + c0 * ss;
+                c0 = cn;
             }
         }
     }
-    if (it < n_x)
 #pragma unroll
-        for (int j = 0; j < kGroup; ++j)
-            if (j < cnt) V[(long long)solve_j[s0 + j] * n_x + it] = acc[j];
+    for (int j = 0; j < kGroup; ++j)
+        if (j < cnt) part[((long long)w * kGroup + j) * n_x + it] = acc[j];
+}
+
+// V[solve_j[s0 + j]][x] = sum over the subgroup's items, in item order.
+__global__ void field_reduce_kernel(Subgroups grp, const int *__restrict__ item_first,
+                                    const int *__restrict__ solve_j, const double2 *__restrict__ part,
+                                    int n_x, double2 *__restrict__ V) {
+    const int g = blockIdx.y;
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= n_x) return;
+    const int2 sgv = grp.sg[g];
+    const int w0 = item_first[g], w1 = item_first[g + 1];
+    for (int j = 0; j < sgv.y; ++j) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int w = w0; w < w1; ++w) {
+            const double2 v = part[((long long)w * kGroup + j) * n_x + it];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        V[(long long)solve_j[sgv.x + j] * n_x + it] = acc;
+    }
 }
 
 __global__ void field_zero_freq_kernel(int n_x, double2 *__restrict__ V) {
@@ -152,14 +167,17 @@ void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st) {
 }
 
 void launch_target_field(const SolveTables &t, const Subgroups &g, int n_groups,
+                         const int2 *items, int n_items, const int *item_first,
                          const int *solve_j, const double2 *z, const double2 *dz,
-                         const double2 *psi, const double *x, int n_x, double2 *V,
-                         cudaStream_t st) {
+                         const double2 *psi, const double *x, int n_x, double2 *part,
+                         double2 *V, cudaStream_t st) {
     if (n_x <= 0) return;
     field_zero_freq_kernel<<<(n_x + 255) / 256, 256, 0, st>>>(n_x, V);
     if (n_groups <= 0) return;
-    dim3 grid((n_x + kTgt - 1) / kTgt, n_groups);
-    field_group_kernel<<<grid, kTgt, 0, st>>>(t, g, solve_j, z, dz, psi, x, n_x, V);
+    dim3 grid((n_x + kTgt - 1) / kTgt, n_items);
+    field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, z, dz, psi, x, n_x, part);
+    dim3 g2((n_x + 127) / 128, n_groups);
+    field_reduce_kernel<<<g2, 128, 0, st>>>(g, item_first, solve_j, part, n_x, V);
 }
 
 }  // namespace fh

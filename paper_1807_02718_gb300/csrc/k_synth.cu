@@ -15,7 +15,7 @@
 // the targets (the O(1)-in-T part); the contraction over p is a real GEMM
 // u = [Vr | Vi] [Gr ; -Gi] with inner dimension 2J.
 //
-// D_p for windows far from t (|y| >= M, y = W tau/pi) uses the convergent
+// D_p for windows far from t (|y| >= 1.25 h, y = W tau/pi) uses the convergent
 // expansion 1/(y - m) = (1/y) sum_r (m/y)^r:
 //   D_p = (2W/M) sin(pi y)/(pi y) sum_r (h/y)^r nu_{p,r},
 //   nu_{p,r} = sum_m (-1)^m (m/h)^r e^{-2 pi i m p / M},
@@ -40,7 +40,7 @@ __device__ __forceinline__ double ipow(double x, int r) {
 
 constexpr int kFarChunk = 256;
 
-__global__ void __launch_bounds__(64) far_table_kernel(int J, int M, double2 *__restrict__ nu,
+__global__ void __launch_bounds__(256) far_table_kernel(int J, int M, double2 *__restrict__ nu,
                                                        double2 *__restrict__ ph) {
     const int p = blockIdx.x;
     const int r = threadIdx.x;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) weights_kernel(
     for (int k = 0; k < K; ++k) {
         const double y = W * (tt - s[k]) / kPi;
         double dr = 0.0, di = 0.0;
-        if (fabs(y) < (double)M) {
+        if (fabs(y) < 1.25 * (double)h) {
             __syncthreads();
             for (int m = threadIdx.x; m < M; m += blockDim.x) {
                 const double d = y - (double)(m - h);
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) contract_kernel(int J, int n_x, int n_T,
 }  // namespace
 
 void launch_far_table(int J, int M, double2 *nu, double2 *phase_tab, cudaStream_t st) {
-    far_table_kernel<<<J, 64, 0, st>>>(J, M, nu, phase_tab);
+    far_table_kernel<<<J, 192, 0, st>>>(J, M, nu, phase_tab);
 }
 
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
