@@ -81,17 +81,47 @@ __global__ void __launch_bounds__(256) far_table_kernel(int J, int M, double2 *_
     if (r < kFarTerms) nu[(long long)r * J + p] = make_double2(sr, si);
 }
 
+// Double-float (FP32 pair) arithmetic for the near-window sums: FP32 runs at
+// 64x the FP64 rate on this GPU.  A value is hi + lo with |lo| <= ulp(hi)/2;
+// products use the exact FMA residual (Dekker / Ogita-Rump-Oishi two-product),
+// sums the two-sum of Knuth, giving ~2^-44 relative accuracy per operation.
+struct dfl { float hi, lo; };
+
+__device__ __forceinline__ dfl df_split(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+// acc += a * b (a, b double-float; acc double-float)
+__device__ __forceinline__ void df_mac(float &sh, float &sl, dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    const float t = sh + p;
+    const float z = t - sh;
+    const float err = (sh - (t - z)) + (p - z);
+    sl += err + pe;
+    sh = t;
+}
+
 __global__ void __launch_bounds__(256) weights_kernel(
     int J, int M, double W, int K, const double *__restrict__ s, const double2 *__restrict__ B,
     const double2 *__restrict__ nu, const double2 *__restrict__ ph_g,
     const double *__restrict__ T, int n_T, double *__restrict__ Gr, double *__restrict__ Gm) {
-    extern __shared__ double smem[];
-    double2 *ph = reinterpret_cast<double2 *>(smem);       // M phases
-    double *sc = smem + 2 * M;                              // M sinc values
+    extern __shared__ float smf[];
+    float2 *phc = reinterpret_cast<float2 *>(smf);          // M: cos (hi, lo)
+    float2 *phs = phc + M;                                   // M: sin (hi, lo)
+    float2 *sc = phs + M;                                    // M: sinc (hi, lo)
     const int t = blockIdx.x;
     const int p = blockIdx.y * blockDim.x + threadIdx.x;
     const int h = M / 2;
-    for (int q = threadIdx.x; q < M; q += blockDim.x) ph[q] = ph_g[q];
+    for (int q = threadIdx.x; q < M; q += blockDim.x) {
+        const double2 e = ph_g[q];
+        const dfl c = df_split(e.x), sn = df_split(e.y);
+        phc[q] = make_float2(c.hi, c.lo);
+        phs[q] = make_float2(sn.hi, sn.lo);
+    }
     const double tt = T[t];
     const double scale = 2.0 * W / (double)M;
     double qr = 0.0, qi = 0.0;
@@ -102,22 +132,28 @@ __global__ void __launch_bounds__(256) weights_kernel(
             __syncthreads();
             for (int m = threadIdx.x; m < M; m += blockDim.x) {
                 const double d = y - (double)(m - h);
-                sc[m] = (d == 0.0) ? 1.0 : sinpi(d) / (kPi * d);
+                const dfl v = df_split((d == 0.0) ? 1.0 : sinpi(d) / (kPi * d));
+                sc[m] = make_float2(v.hi, v.lo);
             }
             __syncthreads();
             if (p < J) {
+                float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
                 int q = (int)((((long long)(-h) % M + M) % M) * p % M);
                 for (int m = 0; m < M; ++m) {
-                    const double2 e = ph[q];
-                    const double v = sc[m];
-                    dr += e.x * v;
-                    di += e.y * v;
+                    const float2 v2 = sc[m];
+                    const float2 c2 = phc[q], s2 = phs[q];
+                    const dfl v = {v2.x, v2.y};
+                    df_mac(rh, rl, {c2.x, c2.y}, v);
+                    df_mac(ih, il, {s2.x, s2.y}, v);
                     q += p;
                     if (q >= M) q -= M;
-                    if (q >= M) q %= M;
+                    if ((m & 31) == 31) {   // renormalise the accumulators
+                        float tr = rh + rl; rl = rl - (tr - rh); rh = tr;
+                        float ti = ih + il; il = il - (ti - ih); ih = ti;
+                    }
                 }
-                dr *= scale;
-                di *= scale;
+                dr = scale * ((double)rh + (double)rl);
+                di = scale * ((double)ih + (double)il);
             }
         } else if (p < J) {
             const double rho = (double)h / y;
@@ -218,7 +254,7 @@ void launch_synth_weights(int J, int M, double W, int K, const double *s, const 
                           const double2 *nu, const double2 *phase_tab, const double *T,
                           int n_T, double *Gr, double *Gm, cudaStream_t st) {
     if (n_T <= 0) return;
-    const size_t smem = (size_t)M * 3 * sizeof(double);
+    const size_t smem = (size_t)M * 3 * sizeof(float2);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
