@@ -153,6 +153,43 @@ fh_status fh_sample(fh_ctx *ctx, const double *x, int n_x, const double *T, int 
 fh_status fh_sample_dev(fh_ctx *ctx, const double *d_x, int n_x, const double *d_T, int n_T,
                         double *d_u);
 
+/* ---- batches: several problems solved in the same launches ---- */
+
+/* Like fh_discretize for P problems at once (frequency parallelism across
+ * problems, Sec. 1 and Sec. 5 step F3): problem q has curve curves[q], J[q]
+ * frequencies omega[o_q .. o_q + J[q] - 1] and sizes N[o_q ..] (o_q = sum of
+ * J[0..q-1]; N may be NULL), wave speed c[q] and direction p[2q], p[2q+1].
+ * fh_solve_frequencies then assembles and factorises the systems of all
+ * problems in shared launches (largest first); spectra and sampling are per
+ * problem (the _p calls).  The single-problem calls act on problem 0; eta for
+ * fh_solve_frequencies is indexed like omega.  Each problem's results equal
+ * those of solving it alone. */
+fh_status fh_discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int *J,
+                              const double *omega, const int *N, const double *c,
+                              const double *p);
+
+/* Number of problems of the context (1 after fh_discretize). */
+fh_status fh_num_problems(fh_ctx *ctx, int *P);
+
+/* fh_window_spectra / fh_sample (and device variants) for problem `problem`. */
+fh_status fh_window_spectra_p(fh_ctx *ctx, int problem, const double *a, int n_samples,
+                              double t0, double dt, double H);
+fh_status fh_window_spectra_p_dev(fh_ctx *ctx, int problem, const double *d_a, int n_samples,
+                                  double t0, double dt, double H);
+fh_status fh_sample_p(fh_ctx *ctx, int problem, const double *x, int n_x, const double *T,
+                      int n_T, double *u_out);
+fh_status fh_sample_p_dev(fh_ctx *ctx, int problem, const double *d_x, int n_x,
+                          const double *d_T, int n_T, double *d_u);
+
+/* Density psi_j (N_j complex) of frequency j of problem `problem`. */
+fh_status fh_get_density_p(fh_ctx *ctx, int problem, int j, double *psi);
+
+/* Device bytes a context needs for P problems with J[q] frequencies and sizes
+ * N (laid out as in fh_discretize_batch) at `precision`, excluding the
+ * per-call sampling work space (about 16 (J + n_items) n_x + 16 J n_T bytes).
+ * Used for admission by memory footprint.  No device is touched. */
+fh_status fh_footprint(const int *J, const int *N, int P, int precision, long long *bytes);
+
 /* ---- inspection of resident state (host buffers; used by parity tests) ---- */
 
 /* Number of windows K of the last fh_window_spectra. */

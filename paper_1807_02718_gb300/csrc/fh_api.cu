@@ -1,11 +1,14 @@
 // libfh host library: the C ABI of include/fh.h.
 //
-// The context owns the device state of one scattering problem: nodes and
-// quadrature tables per frequency, the resident densities Psi (Sec. 3.2 eq.
-// psikslow_repr: one fixed set, reused for every window), the window spectra
-// B_k^slow, and work space for the target fields and synthesis weights.  All
-// work is stream-ordered on the context stream; host-pointer calls copy in,
-// launch, and copy out on that stream.
+// A context owns the device state of a batch of P scattering problems (P = 1
+// for fh_discretize): nodes and quadrature tables per frequency, the resident
+// densities Psi (Sec. 3.2 eq. psikslow_repr: one fixed set per problem, reused
+// for every window), each problem's window spectra B_k^slow and synthesis
+// tables, and work space for target fields and synthesis weights.  The
+// frequency solves of all problems share one set of launches (assembly,
+// factorisation, refinement); sampling runs per problem.  All work is
+// stream-ordered on the context stream; host-pointer calls copy in, launch and
+// copy out on that stream.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -25,6 +28,33 @@ struct DevBuf {
     template <class T> T *as() const { return reinterpret_cast<T *>(p); }
 };
 
+void free_buf(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+// One problem of the batch.  Its solves are s_begin .. s_begin + J - 2
+// (frequency j = s - s_begin + 1), its frequency subgroups g_begin .. g_end-1
+// and its field work items item_begin .. item_end-1 (global indices).
+struct Problem {
+    fh_curve curve{};
+    int J = 0, M = 0;
+    double W = 0.0, c = 1.0, p[2] = {1.0, 0.0};
+    std::vector<double> omega;
+    std::vector<int> Nj;
+    int s_begin = 0;
+    int g_begin = 0, g_end = 0;
+    int item_begin = 0, item_end = 0;
+    long long nu_off = 0, ph_off = 0, omega_off = 0;   // into the pooled tables
+    bool spectra = false;
+    int K = 0;
+    double H = 10.0;
+    std::vector<double> s;
+    DevBuf d_s, d_B;
+    int S() const { return J - 1; }
+};
+
 }  // namespace
 
 struct fh_ctx {
@@ -34,45 +64,35 @@ struct fh_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
 
-    bool geom = false, solved = false, spectra = false, have_V = false;
-    fh_curve curve{};
-    int J = 0, M = 0;
-    double W = 0.0, c = 1.0, p[2] = {1.0, 0.0};
-    std::vector<double> omega;
-    std::vector<int> Nj;
+    bool geom = false, solved = false, have_V = false;
+    int v_problem = 0;           // problem of the last target fields
+    std::vector<Problem> probs;
 
-    // frequency solves: s = 0..S-1 <-> j = s + 1
+    // frequency solves of all problems, problem-major
     int S = 0, maxN = 0, n_tab = 0;
-    long long mat_total = 0, n_tiles = 0;
+    long long mat_total = 0;
     int vec_total = 0, tab_total = 0;
-    std::vector<int> solve_j, solve_N, vec_off, tab_of, tab_N, tab_off, order;
-    std::vector<long long> mat_off, tile_off;
+    std::vector<int> solve_prob, solve_j, solve_N, vec_off, tab_of, tab_N, tab_off, order;
+    std::vector<long long> mat_off;
     std::vector<double> kappa_s, eta_s;
-    // frequency subgroups (equal N, at most fh::kGroup consecutive solves)
+    // frequency subgroups (one problem, equal N, at most fh::kGroup solves)
     int n_groups = 0;
     long long group_tiles = 0;
     std::vector<int2> sg;
     std::vector<long long> sg_tile_off;
     std::vector<double> sg_dk;
     std::vector<int2> field_items;      // (subgroup, first node)
-    std::vector<int> item_first;        // per subgroup, + end
+    std::vector<int> item_first;        // first item per subgroup, + end
+
     DevBuf d_sg, d_sg_tile_off, d_sg_dk, d_tmp_sg, d_items, d_item_first, d_part;
-
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
-        d_order, d_tile_off;
-    DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_ph;
+        d_solve_prob, d_order, d_curves, d_pdir;
+    DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_ph, d_omega;
     DevBuf d_A32, d_piv, d_g, d_iters, d_resid;
-
-    int K = 0;
-    double H = 10.0;
-    std::vector<double> s;
-    DevBuf d_s, d_B, d_wa, d_a, d_omega;
-
+    DevBuf d_wa, d_a;
     int n_x_last = 0;
     DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm;
-
-    // single-matrix scratch for fh_assemble_matrix
-    DevBuf d_tmpA, d_tmpg, d_tmp_i, d_tmp_ll, d_tmp_d;
+    DevBuf d_tmpA, d_tmpg, d_tmp_ll, d_tmp_d;
 
     // timing: pending (phase, start, stop) event triples and totals
     bool timing = false;
@@ -82,16 +102,24 @@ struct fh_ctx {
     long long launches[FH_NUM_PHASES] = {};
     long long groups[FH_NUM_PHASES] = {};
 
+    void free_problems() {
+        for (Problem &pb : probs) {
+            free_buf(pb.d_s);
+            free_buf(pb.d_B);
+        }
+        probs.clear();
+    }
+
     ~fh_ctx() {
-        DevBuf *all[] = {&d_N, &d_mat_off, &d_vec_off, &d_tab, &d_tab_off, &d_tab_N, &d_kappa,
-                         &d_eta, &d_solve_j, &d_order, &d_tile_off, &d_z, &d_dz, &d_ddz,
-                         &d_kress, &d_logsin, &d_A, &d_psi, &d_info, &d_nu, &d_ph, &d_A32,
-                         &d_piv, &d_g, &d_iters, &d_resid, &d_s, &d_B, &d_wa, &d_a, &d_omega,
-                         &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_tmpA, &d_tmpg, &d_tmp_i,
-                         &d_tmp_ll, &d_tmp_d, &d_sg, &d_sg_tile_off, &d_sg_dk, &d_tmp_sg,
-                         &d_items, &d_item_first, &d_part};
-        for (DevBuf *b : all)
-            if (b->p) cudaFree(b->p);
+        DevBuf *all[] = {&d_sg, &d_sg_tile_off, &d_sg_dk, &d_tmp_sg, &d_items, &d_item_first,
+                         &d_part, &d_N, &d_mat_off, &d_vec_off, &d_tab, &d_tab_off, &d_tab_N,
+                         &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
+                         &d_pdir, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
+                         &d_info, &d_nu, &d_ph, &d_omega, &d_A32, &d_piv, &d_g, &d_iters,
+                         &d_resid, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
+                         &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
+        for (DevBuf *b : all) free_buf(*b);
+        free_problems();
         for (auto &pe : pending) {
             cudaEventDestroy(pe.a);
             cudaEventDestroy(pe.b);
@@ -128,9 +156,7 @@ fh_status fail(fh_ctx *ctx, fh_status st, const char *fmt, ...) {
 
 fh_status ensure(fh_ctx *ctx, DevBuf &b, size_t bytes) {
     if (b.cap >= bytes && b.p) return FH_OK;
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.cap = 0;
+    free_buf(b);
     size_t want = std::max<size_t>(bytes, 256);
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
@@ -199,12 +225,6 @@ fh::SolveTables tables(fh_ctx *ctx) {
     return t;
 }
 
-bool is_fin(double v) { return std::isfinite(v); }
-
-// Mixed precision: refinement stops when ||dx||_inf <= kRefineTol ||x||_inf.
-constexpr int kRefineMaxIters = 12;
-constexpr double kRefineTol = 1e-14;
-
 fh::Subgroups groups(fh_ctx *ctx) {
     fh::Subgroups g;
     g.sg = ctx->d_sg.as<int2>();
@@ -213,9 +233,233 @@ fh::Subgroups groups(fh_ctx *ctx) {
     return g;
 }
 
-fh_status spectra_common(fh_ctx *ctx, const double *d_a, int n_samples, double t0, double dt,
-                         double H) {
-    if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_window_spectra: call fh_discretize first");
+bool is_fin(double v) { return std::isfinite(v); }
+
+// Mixed precision: refinement stops when ||dx||_inf <= kRefineTol ||x||_inf.
+constexpr int kRefineMaxIters = 12;
+constexpr double kRefineTol = 1e-14;
+
+fh_status get_problem(fh_ctx *ctx, int problem, Problem **out) {
+    if (!ctx->geom) return fail(ctx, FH_ESTATE, "call fh_discretize first");
+    if (problem < 0 || problem >= (int)ctx->probs.size())
+        return fail(ctx, FH_EINVAL, "problem %d out of range [0, %d)", problem, (int)ctx->probs.size());
+    *out = &ctx->probs[problem];
+    return FH_OK;
+}
+
+fh_status check_problem_args(fh_ctx *ctx, const fh_curve *curve, int J, const double *omega,
+                             const int *N, double c, const double *p, int q) {
+    if (!curve || !omega || !p) return fail(ctx, FH_EINVAL, "curve, omega and p must be non-NULL");
+    if (curve->kind < FH_CURVE_CIRCLE || curve->kind > FH_CURVE_STAR)
+        return fail(ctx, FH_EINVAL, "problem %d: unknown curve kind %d", q, curve->kind);
+    if (curve->kind == FH_CURVE_STAR && (curve->n_harm < 0 || curve->n_harm > FH_MAX_HARMONICS))
+        return fail(ctx, FH_EINVAL, "problem %d: n_harm must be in [0, %d]", q, FH_MAX_HARMONICS);
+    if (curve->kind != FH_CURVE_KITE && !(curve->r0 > 0.0))
+        return fail(ctx, FH_EINVAL, "problem %d: r0 must be positive", q);
+    if (J < 2 || J > 4097) return fail(ctx, FH_EINVAL, "problem %d: J must be in [2, 4097] (got %d)", q, J);
+    if (!(c > 0.0) || !is_fin(c)) return fail(ctx, FH_EINVAL, "problem %d: c must be positive", q);
+    const double pn = std::hypot(p[0], p[1]);
+    if (!(std::fabs(pn - 1.0) < 1e-12)) return fail(ctx, FH_EINVAL, "problem %d: p must be a unit vector", q);
+    if (omega[0] != 0.0) return fail(ctx, FH_EINVAL, "problem %d: omega[0] must be 0", q);
+    const double W = omega[J - 1];
+    if (!(W > 0.0) || !is_fin(W)) return fail(ctx, FH_EINVAL, "problem %d: omega[J-1] must be positive", q);
+    const double dw = W / (J - 1);
+    for (int j = 0; j < J; ++j)
+        if (!is_fin(omega[j]) || std::fabs(omega[j] - j * dw) > 1e-10 * W)
+            return fail(ctx, FH_EINVAL, "problem %d: omega must be uniform on [0, W] (omega[%d] = %.17g)",
+                        q, j, omega[j]);
+    if (N)
+        for (int j = 1; j < J; ++j)
+            if (N[j] < 8 || N[j] > 8192 || (N[j] & 1))
+                return fail(ctx, FH_EINVAL, "problem %d: N[%d] = %d must be even and in [8, 8192]", q, j, N[j]);
+    return FH_OK;
+}
+
+// Builds every per-solve / per-subgroup table of a batch and launches the
+// node, Kress and synthesis-table kernels.
+fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int *Js,
+                           const double *omega_all, const int *N_all, const double *cs,
+                           const double *ps) {
+    if (P < 1) return fail(ctx, FH_EINVAL, "P must be >= 1");
+    if (!curves || !Js || !omega_all || !cs || !ps)
+        return fail(ctx, FH_EINVAL, "curves, J, omega, c and p must be non-NULL");
+    long long jo = 0;
+    for (int q = 0; q < P; ++q) {
+        FH_TRY(check_problem_args(ctx, &curves[q], Js[q], omega_all + jo, N_all ? N_all + jo : nullptr,
+                                  cs[q], ps + 2 * q, q));
+        jo += Js[q];
+    }
+    ctx->geom = ctx->solved = ctx->have_V = false;
+    ctx->free_problems();
+    ctx->probs.resize(P);
+    ctx->solve_prob.clear();
+    ctx->solve_j.clear();
+    ctx->solve_N.clear();
+    ctx->vec_off.clear();
+    ctx->mat_off.clear();
+    ctx->tab_of.clear();
+    ctx->kappa_s.clear();
+    ctx->eta_s.clear();
+    ctx->tab_N.clear();
+    ctx->tab_off.clear();
+    std::map<int, int> tab_index;
+    long long mo = 0, nu_off = 0, ph_off = 0;
+    int vo = 0, tb = 0, maxN = 0;
+    std::vector<fh::CurveParams> cps(P);
+    std::vector<double2> pdir(P);
+    jo = 0;
+    for (int q = 0; q < P; ++q) {
+        Problem &pb = ctx->probs[q];
+        const int J = Js[q];
+        const double *omega = omega_all + jo;
+        const double pn = std::hypot(ps[2 * q], ps[2 * q + 1]);
+        pb.curve = curves[q];
+        pb.J = J;
+        pb.M = 2 * (J - 1);
+        pb.W = omega[J - 1];
+        pb.c = cs[q];
+        pb.p[0] = ps[2 * q] / pn;
+        pb.p[1] = ps[2 * q + 1] / pn;
+        pb.omega.assign(omega, omega + J);
+        pb.Nj.assign(J, 64);
+        if (N_all) for (int j = 0; j < J; ++j) pb.Nj[j] = N_all[jo + j];
+        pb.s_begin = (int)ctx->solve_N.size();
+        pb.omega_off = jo;
+        pb.nu_off = nu_off;
+        pb.ph_off = ph_off;
+        nu_off += (long long)fh::kFarTerms * J;
+        ph_off += pb.M;
+        for (int j = 1; j < J; ++j) {
+            const int n = pb.Nj[j];
+            ctx->solve_prob.push_back(q);
+            ctx->solve_j.push_back(j);
+            ctx->solve_N.push_back(n);
+            ctx->vec_off.push_back(vo);
+            ctx->mat_off.push_back(mo);
+            ctx->kappa_s.push_back(omega[j] / pb.c);
+            ctx->eta_s.push_back(omega[j]);
+            auto it = tab_index.find(n);
+            if (it == tab_index.end()) {
+                it = tab_index.emplace(n, (int)ctx->tab_N.size()).first;
+                ctx->tab_N.push_back(n);
+                ctx->tab_off.push_back(tb);
+                tb += n;
+            }
+            ctx->tab_of.push_back(it->second);
+            vo += n;
+            mo += (long long)n * n;
+            maxN = std::max(maxN, n);
+        }
+        fh::CurveParams &cp = cps[q];
+        cp = fh::CurveParams{};
+        cp.kind = pb.curve.kind;
+        cp.n_harm = pb.curve.kind == FH_CURVE_STAR ? pb.curve.n_harm : 0;
+        cp.r0 = pb.curve.r0;
+        cp.cx = pb.curve.center[0];
+        cp.cy = pb.curve.center[1];
+        for (int k = 0; k < FH_MAX_HARMONICS; ++k) {
+            cp.amp[k] = pb.curve.amp[k];
+            cp.phase[k] = pb.curve.phase[k];
+        }
+        pdir[q] = make_double2(pb.p[0], pb.p[1]);
+        jo += J;
+    }
+    const int S = (int)ctx->solve_N.size();
+    ctx->S = S;
+    ctx->vec_total = vo;
+    ctx->mat_total = mo;
+    ctx->tab_total = tb;
+    ctx->n_tab = (int)ctx->tab_N.size();
+    ctx->maxN = maxN;
+
+    // subgroups never cross problems; field items are 64-node chunks of them
+    ctx->sg.clear();
+    ctx->sg_tile_off.clear();
+    ctx->sg_dk.clear();
+    ctx->field_items.clear();
+    ctx->item_first.clear();
+    long long gt = 0;
+    for (int q = 0; q < P; ++q) {
+        Problem &pb = ctx->probs[q];
+        pb.g_begin = (int)ctx->sg.size();
+        pb.item_begin = (int)ctx->field_items.size();
+        const int s_end = pb.s_begin + pb.S();
+        for (int s = pb.s_begin; s < s_end;) {
+            int cnt = 1;
+            while (s + cnt < s_end && cnt < fh::kGroup && ctx->solve_N[s + cnt] == ctx->solve_N[s]) ++cnt;
+            const int g = (int)ctx->sg.size();
+            ctx->sg.push_back(make_int2(s, cnt));
+            ctx->sg_tile_off.push_back(gt);
+            ctx->sg_dk.push_back(cnt > 1 ? (ctx->kappa_s[s + cnt - 1] - ctx->kappa_s[s]) / (cnt - 1) : 0.0);
+            const long long nt = (ctx->solve_N[s] + 31) / 32;
+            gt += nt * nt;
+            ctx->item_first.push_back((int)ctx->field_items.size());
+            for (int i0 = 0; i0 < ctx->solve_N[s]; i0 += fh::kFieldChunk)
+                ctx->field_items.push_back(make_int2(g, i0));
+            s += cnt;
+        }
+        pb.g_end = (int)ctx->sg.size();
+        pb.item_end = (int)ctx->field_items.size();
+    }
+    ctx->sg_tile_off.push_back(gt);
+    ctx->item_first.push_back((int)ctx->field_items.size());
+    ctx->n_groups = (int)ctx->sg.size();
+    ctx->group_tiles = gt;
+    ctx->order.resize(S);
+    for (int s = 0; s < S; ++s) ctx->order[s] = s;
+    std::stable_sort(ctx->order.begin(), ctx->order.end(),
+                     [&](int a, int b) { return ctx->solve_N[a] > ctx->solve_N[b]; });
+
+    std::vector<double> omega_v(omega_all, omega_all + jo);
+    FH_TRY(upload(ctx, ctx->d_N, ctx->solve_N));
+    FH_TRY(upload(ctx, ctx->d_mat_off, ctx->mat_off));
+    FH_TRY(upload(ctx, ctx->d_vec_off, ctx->vec_off));
+    FH_TRY(upload(ctx, ctx->d_tab, ctx->tab_of));
+    FH_TRY(upload(ctx, ctx->d_tab_off, ctx->tab_off));
+    FH_TRY(upload(ctx, ctx->d_tab_N, ctx->tab_N));
+    FH_TRY(upload(ctx, ctx->d_kappa, ctx->kappa_s));
+    FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
+    FH_TRY(upload(ctx, ctx->d_solve_j, ctx->solve_j));
+    FH_TRY(upload(ctx, ctx->d_solve_prob, ctx->solve_prob));
+    FH_TRY(upload(ctx, ctx->d_order, ctx->order));
+    FH_TRY(upload(ctx, ctx->d_omega, omega_v));
+    FH_TRY(upload(ctx, ctx->d_sg, ctx->sg));
+    FH_TRY(upload(ctx, ctx->d_sg_tile_off, ctx->sg_tile_off));
+    FH_TRY(upload(ctx, ctx->d_sg_dk, ctx->sg_dk));
+    FH_TRY(upload(ctx, ctx->d_items, ctx->field_items));
+    FH_TRY(upload(ctx, ctx->d_item_first, ctx->item_first));
+    FH_TRY(upload(ctx, ctx->d_curves, cps));
+    FH_TRY(upload(ctx, ctx->d_pdir, pdir));
+    FH_TRY(ensure(ctx, ctx->d_z, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_dz, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_ddz, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_psi, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_kress, (size_t)tb * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_logsin, (size_t)tb * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_A, (size_t)mo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_info, (size_t)S * sizeof(int)));
+    FH_TRY(ensure(ctx, ctx->d_nu, (size_t)nu_off * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_ph, (size_t)ph_off * sizeof(double2)));
+
+    PhaseScope ps_(ctx, FH_PH_GEOMETRY, 2 + P);
+    fh::launch_geometry(ctx->d_curves.as<fh::CurveParams>(), ctx->d_solve_prob.as<int>(), S, maxN,
+                        ctx->d_N.as<int>(), ctx->d_vec_off.as<int>(), ctx->d_z.as<double2>(),
+                        ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "geometry"));
+    fh::launch_kress_tables(ctx->n_tab, maxN, ctx->d_tab_N.as<int>(), ctx->d_tab_off.as<int>(),
+                            ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(), ctx->stream);
+    FH_TRY(check_launch(ctx, "kress tables"));
+    for (Problem &pb : ctx->probs) {
+        fh::launch_far_table(pb.J, pb.M, ctx->d_nu.as<double2>() + pb.nu_off,
+                             ctx->d_ph.as<double2>() + pb.ph_off, ctx->stream);
+        FH_TRY(check_launch(ctx, "far table"));
+    }
+    ctx->geom = true;
+    return FH_OK;
+}
+
+fh_status spectra_common(fh_ctx *ctx, Problem &pb, const double *d_a, int n_samples, double t0,
+                         double dt, double H) {
     if (n_samples < 1) return fail(ctx, FH_EINVAL, "n_samples must be >= 1 (got %d)", n_samples);
     if (!(dt > 0.0) || !is_fin(dt)) return fail(ctx, FH_EINVAL, "dt must be positive and finite");
     if (!(H > 0.0) || !is_fin(H)) return fail(ctx, FH_EINVAL, "H must be positive and finite");
@@ -249,60 +493,99 @@ fh_status spectra_common(fh_ctx *ctx, const double *d_a, int n_samples, double t
     }
     const size_t wa_bytes = (size_t)K * (size_t)(Q + 1) * sizeof(double);
     FH_TRY(ensure(ctx, ctx->d_wa, wa_bytes));
-    FH_TRY(ensure(ctx, ctx->d_B, (size_t)K * ctx->J * sizeof(double2)));
-    FH_TRY(upload(ctx, ctx->d_s, s));
+    FH_TRY(ensure(ctx, pb.d_B, (size_t)K * pb.J * sizeof(double2)));
+    FH_TRY(upload(ctx, pb.d_s, s));
     PhaseScope ps(ctx, FH_PH_SPECTRA, 2);
-    fh::launch_window_spectra(d_a, n_samples, start0, step, (int)Q, dt, H, K, ctx->J,
-                              ctx->d_omega.as<double>(), ctx->d_wa.as<double>(),
-                              ctx->d_B.as<double2>(), ctx->stream);
+    fh::launch_window_spectra(d_a, n_samples, start0, step, (int)Q, dt, H, K, pb.J,
+                              ctx->d_omega.as<double>() + pb.omega_off, ctx->d_wa.as<double>(),
+                              pb.d_B.as<double2>(), ctx->stream);
     FH_TRY(check_launch(ctx, "window spectra"));
-    ctx->K = K;
-    ctx->H = H;
-    ctx->s = s;
-    ctx->spectra = true;
+    pb.K = K;
+    pb.H = H;
+    pb.s = s;
+    pb.spectra = true;
     return FH_OK;
 }
 
-fh_status synth_common(fh_ctx *ctx, int n_x, const double *d_T, int n_T, double *d_u) {
-    FH_TRY(ensure(ctx, ctx->d_Gr, (size_t)ctx->J * n_T * sizeof(double)));
-    FH_TRY(ensure(ctx, ctx->d_Gm, (size_t)ctx->J * n_T * sizeof(double)));
+fh_status synth_common(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
+    FH_TRY(ensure(ctx, ctx->d_Gr, (size_t)pb.J * n_T * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_Gm, (size_t)pb.J * n_T * sizeof(double)));
     {
-    PhaseScope ps(ctx, FH_PH_WEIGHTS, 1);
-    fh::launch_synth_weights(ctx->J, ctx->M, ctx->W, ctx->K, ctx->d_s.as<double>(),
-                             ctx->d_B.as<double2>(), ctx->d_nu.as<double2>(),
-                             ctx->d_ph.as<double2>(), d_T, n_T, ctx->d_Gr.as<double>(),
-                             ctx->d_Gm.as<double>(), ctx->stream);
-    FH_TRY(check_launch(ctx, "synthesis weights"));
+        PhaseScope ps(ctx, FH_PH_WEIGHTS, 1);
+        fh::launch_synth_weights(pb.J, pb.M, pb.W, pb.K, pb.d_s.as<double>(), pb.d_B.as<double2>(),
+                                 ctx->d_nu.as<double2>() + pb.nu_off,
+                                 ctx->d_ph.as<double2>() + pb.ph_off, d_T, n_T,
+                                 ctx->d_Gr.as<double>(), ctx->d_Gm.as<double>(), ctx->stream);
+        FH_TRY(check_launch(ctx, "synthesis weights"));
     }
     PhaseScope ps(ctx, FH_PH_CONTRACT, 1);
-    fh::launch_synth_contract(ctx->J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Gr.as<double>(),
+    fh::launch_synth_contract(pb.J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Gr.as<double>(),
                               ctx->d_Gm.as<double>(), d_u, ctx->stream);
     return check_launch(ctx, "synthesis contraction");
 }
 
-fh_status sample_common(fh_ctx *ctx, const double *d_x, int n_x, const double *d_T, int n_T,
-                        double *d_u) {
-    FH_TRY(ensure(ctx, ctx->d_V, (size_t)ctx->J * n_x * sizeof(double2)));
-    const size_t n_items = ctx->field_items.size();
-    FH_TRY(ensure(ctx, ctx->d_part, n_items * fh::kGroup * (size_t)n_x * sizeof(double2)));
+fh_status sample_common(fh_ctx *ctx, int q, const double *d_x, int n_x, const double *d_T,
+                        int n_T, double *d_u) {
+    Problem &pb = ctx->probs[q];
+    FH_TRY(ensure(ctx, ctx->d_V, (size_t)pb.J * n_x * sizeof(double2)));
+    const int n_items = pb.item_end - pb.item_begin;
+    FH_TRY(ensure(ctx, ctx->d_part, (size_t)n_items * fh::kGroup * (size_t)n_x * sizeof(double2)));
     {
-    PhaseScope ps(ctx, FH_PH_FIELD, ctx->S > 0 ? 3 : 1);
-    fh::launch_target_field(tables(ctx), groups(ctx), ctx->n_groups, ctx->d_items.as<int2>(),
-                            (int)n_items, ctx->d_item_first.as<int>(), ctx->d_solve_j.as<int>(),
-                            ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                            ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_part.as<double2>(),
-                            ctx->d_V.as<double2>(), ctx->stream);
-    FH_TRY(check_launch(ctx, "target field"));
+        PhaseScope ps(ctx, FH_PH_FIELD, pb.S() > 0 ? 3 : 1);
+        fh::launch_target_field(tables(ctx), groups(ctx), pb.g_begin, pb.g_end - pb.g_begin,
+                                ctx->d_items.as<int2>(), pb.item_begin, n_items,
+                                ctx->d_item_first.as<int>(), ctx->d_solve_j.as<int>(),
+                                ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                                ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_part.as<double2>(),
+                                ctx->d_V.as<double2>(), ctx->stream);
+        FH_TRY(check_launch(ctx, "target field"));
     }
     ctx->n_x_last = n_x;
+    ctx->v_problem = q;
     ctx->have_V = true;
-    return synth_common(ctx, n_x, d_T, n_T, d_u);
+    return synth_common(ctx, pb, n_x, d_T, n_T, d_u);
 }
 
-fh_status check_sample_args(fh_ctx *ctx, int n_x, int n_T) {
+fh_status check_sample_args(fh_ctx *ctx, int q, int n_x, int n_T) {
+    Problem *pb;
+    FH_TRY(get_problem(ctx, q, &pb));
     if (!ctx->solved) return fail(ctx, FH_ESTATE, "fh_sample: call fh_solve_frequencies first");
-    if (!ctx->spectra) return fail(ctx, FH_ESTATE, "fh_sample: call fh_window_spectra first");
+    if (!pb->spectra) return fail(ctx, FH_ESTATE, "fh_sample: call fh_window_spectra first");
     if (n_x < 0 || n_T < 0) return fail(ctx, FH_EINVAL, "n_x and n_T must be >= 0");
+    return FH_OK;
+}
+
+fh_status sample_host(fh_ctx *ctx, int q, const double *x, int n_x, const double *T, int n_T,
+                      double *u_out) {
+    FH_TRY(check_sample_args(ctx, q, n_x, n_T));
+    if (n_x == 0 || n_T == 0) return FH_OK;
+    if (!x || !T || !u_out) return fail(ctx, FH_EINVAL, "x, T and u_out must be non-NULL");
+    FH_TRY(ensure(ctx, ctx->d_x, (size_t)2 * n_x * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_T, (size_t)n_T * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_u, (size_t)n_x * n_T * sizeof(double)));
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_x.p, x, (size_t)2 * n_x * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_T.p, T, (size_t)n_T * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    FH_TRY(sample_common(ctx, q, ctx->d_x.as<double>(), n_x, ctx->d_T.as<double>(), n_T,
+                         ctx->d_u.as<double>()));
+    FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FH_OK;
+}
+
+fh_status spectra_host(fh_ctx *ctx, int q, const double *a, int n_samples, double t0, double dt,
+                       double H) {
+    Problem *pb;
+    FH_TRY(get_problem(ctx, q, &pb));
+    if (!a) return fail(ctx, FH_EINVAL, "a must be non-NULL");
+    if (n_samples < 1) return fail(ctx, FH_EINVAL, "n_samples must be >= 1");
+    FH_TRY(ensure(ctx, ctx->d_a, (size_t)n_samples * sizeof(double)));
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_a.p, a, (size_t)n_samples * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    FH_TRY(spectra_common(ctx, *pb, ctx->d_a.as<double>(), n_samples, t0, dt, H));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return FH_OK;
 }
 
@@ -350,167 +633,20 @@ fh_status fh_set_stream(fh_ctx *ctx, void *cuda_stream) {
 fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double *omega,
                         const int *N, double c, const double p[2]) {
     FH_TRY(enter(ctx));
-    if (!curve || !omega || !p) return fail(ctx, FH_EINVAL, "curve, omega and p must be non-NULL");
-    if (curve->kind < FH_CURVE_CIRCLE || curve->kind > FH_CURVE_STAR)
-        return fail(ctx, FH_EINVAL, "unknown curve kind %d", curve->kind);
-    if (curve->kind == FH_CURVE_STAR && (curve->n_harm < 0 || curve->n_harm > FH_MAX_HARMONICS))
-        return fail(ctx, FH_EINVAL, "n_harm must be in [0, %d]", FH_MAX_HARMONICS);
-    if (curve->kind != FH_CURVE_KITE && !(curve->r0 > 0.0))
-        return fail(ctx, FH_EINVAL, "r0 must be positive");
-    if (J < 2 || J > 4097) return fail(ctx, FH_EINVAL, "J must be in [2, 4097] (got %d)", J);
-    if (!(c > 0.0) || !is_fin(c)) return fail(ctx, FH_EINVAL, "c must be positive");
-    const double pn = std::hypot(p[0], p[1]);
-    if (!(std::fabs(pn - 1.0) < 1e-12)) return fail(ctx, FH_EINVAL, "p must be a unit vector");
-    if (omega[0] != 0.0) return fail(ctx, FH_EINVAL, "omega[0] must be 0");
-    const double W = omega[J - 1];
-    if (!(W > 0.0) || !is_fin(W)) return fail(ctx, FH_EINVAL, "omega[J-1] must be positive");
-    const double dw = W / (J - 1);
-    for (int j = 0; j < J; ++j) {
-        if (!is_fin(omega[j]) || std::fabs(omega[j] - j * dw) > 1e-10 * W)
-            return fail(ctx, FH_EINVAL, "omega must be uniform on [0, W] (omega[%d] = %.17g)", j, omega[j]);
-    }
-    std::vector<int> Nv(J, 64);
-    if (N) for (int j = 0; j < J; ++j) Nv[j] = N[j];
-    for (int j = 1; j < J; ++j)
-        if (Nv[j] < 8 || Nv[j] > 8192 || (Nv[j] & 1))
-            return fail(ctx, FH_EINVAL, "N[%d] = %d must be even and in [8, 8192]", j, Nv[j]);
+    return discretize_batch(ctx, 1, curve, &J, omega, N, &c, p);
+}
 
-    ctx->geom = ctx->solved = ctx->spectra = ctx->have_V = false;
-    ctx->curve = *curve;
-    ctx->J = J;
-    ctx->M = 2 * (J - 1);
-    ctx->W = W;
-    ctx->c = c;
-    ctx->p[0] = p[0] / pn;
-    ctx->p[1] = p[1] / pn;
-    ctx->omega.assign(omega, omega + J);
-    ctx->Nj = Nv;
+fh_status fh_discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int *J,
+                              const double *omega, const int *N, const double *c,
+                              const double *p) {
+    FH_TRY(enter(ctx));
+    return discretize_batch(ctx, P, curves, J, omega, N, c, p);
+}
 
-    const int S = J - 1;
-    ctx->S = S;
-    ctx->solve_j.resize(S);
-    ctx->solve_N.resize(S);
-    ctx->vec_off.resize(S);
-    ctx->mat_off.resize(S);
-    ctx->tab_of.resize(S);
-    ctx->tile_off.resize(S + 1);
-    ctx->kappa_s.resize(S);
-    ctx->eta_s.resize(S);
-    ctx->tab_N.clear();
-    ctx->tab_off.clear();
-    std::map<int, int> tab_index;
-    long long mo = 0, to = 0;
-    int vo = 0, tb = 0, maxN = 0;
-    for (int s = 0; s < S; ++s) {
-        const int j = s + 1, n = Nv[j];
-        ctx->solve_j[s] = j;
-        ctx->solve_N[s] = n;
-        ctx->vec_off[s] = vo;
-        ctx->mat_off[s] = mo;
-        ctx->tile_off[s] = to;
-        ctx->kappa_s[s] = omega[j] / c;
-        ctx->eta_s[s] = omega[j];
-        auto it = tab_index.find(n);
-        if (it == tab_index.end()) {
-            it = tab_index.emplace(n, (int)ctx->tab_N.size()).first;
-            ctx->tab_N.push_back(n);
-            ctx->tab_off.push_back(tb);
-            tb += n;
-        }
-        ctx->tab_of[s] = it->second;
-        vo += n;
-        mo += (long long)n * n;
-        const long long nt = (n + 31) / 32;
-        to += nt * nt;
-        maxN = std::max(maxN, n);
-    }
-    ctx->tile_off[S] = to;
-    ctx->sg.clear();
-    ctx->sg_tile_off.clear();
-    ctx->sg_dk.clear();
-    long long gt = 0;
-    for (int s = 0; s < S;) {
-        int cnt = 1;
-        while (s + cnt < S && cnt < fh::kGroup && ctx->solve_N[s + cnt] == ctx->solve_N[s]) ++cnt;
-        ctx->sg.push_back(make_int2(s, cnt));
-        ctx->sg_tile_off.push_back(gt);
-        ctx->sg_dk.push_back(cnt > 1 ? (ctx->kappa_s[s + cnt - 1] - ctx->kappa_s[s]) / (cnt - 1) : 0.0);
-        const long long nt = (ctx->solve_N[s] + 31) / 32;
-        gt += nt * nt;
-        s += cnt;
-    }
-    ctx->sg_tile_off.push_back(gt);
-    ctx->n_groups = (int)ctx->sg.size();
-    // field work items: each subgroup's nodes in chunks of kFieldChunk
-    ctx->field_items.clear();
-    ctx->item_first.assign(ctx->n_groups + 1, 0);
-    for (int g = 0; g < ctx->n_groups; ++g) {
-        ctx->item_first[g] = (int)ctx->field_items.size();
-        const int n = ctx->solve_N[ctx->sg[g].x];
-        for (int i0 = 0; i0 < n; i0 += fh::kFieldChunk) ctx->field_items.push_back(make_int2(g, i0));
-    }
-    ctx->item_first[ctx->n_groups] = (int)ctx->field_items.size();
-    ctx->group_tiles = gt;
-    ctx->vec_total = vo;
-    ctx->mat_total = mo;
-    ctx->n_tiles = to;
-    ctx->tab_total = tb;
-    ctx->n_tab = (int)ctx->tab_N.size();
-    ctx->maxN = maxN;
-    ctx->order.resize(S);
-    for (int s = 0; s < S; ++s) ctx->order[s] = s;
-    std::stable_sort(ctx->order.begin(), ctx->order.end(),
-                     [&](int a, int b) { return ctx->solve_N[a] > ctx->solve_N[b]; });
-
-    FH_TRY(upload(ctx, ctx->d_N, ctx->solve_N));
-    FH_TRY(upload(ctx, ctx->d_mat_off, ctx->mat_off));
-    FH_TRY(upload(ctx, ctx->d_vec_off, ctx->vec_off));
-    FH_TRY(upload(ctx, ctx->d_tab, ctx->tab_of));
-    FH_TRY(upload(ctx, ctx->d_tab_off, ctx->tab_off));
-    FH_TRY(upload(ctx, ctx->d_tab_N, ctx->tab_N));
-    FH_TRY(upload(ctx, ctx->d_kappa, ctx->kappa_s));
-    FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
-    FH_TRY(upload(ctx, ctx->d_solve_j, ctx->solve_j));
-    FH_TRY(upload(ctx, ctx->d_order, ctx->order));
-    FH_TRY(upload(ctx, ctx->d_tile_off, ctx->tile_off));
-    FH_TRY(upload(ctx, ctx->d_omega, ctx->omega));
-    FH_TRY(upload(ctx, ctx->d_sg, ctx->sg));
-    FH_TRY(upload(ctx, ctx->d_sg_tile_off, ctx->sg_tile_off));
-    FH_TRY(upload(ctx, ctx->d_sg_dk, ctx->sg_dk));
-    FH_TRY(upload(ctx, ctx->d_items, ctx->field_items));
-    FH_TRY(upload(ctx, ctx->d_item_first, ctx->item_first));
-    FH_TRY(ensure(ctx, ctx->d_z, (size_t)vo * sizeof(double2)));
-    FH_TRY(ensure(ctx, ctx->d_dz, (size_t)vo * sizeof(double2)));
-    FH_TRY(ensure(ctx, ctx->d_ddz, (size_t)vo * sizeof(double2)));
-    FH_TRY(ensure(ctx, ctx->d_psi, (size_t)vo * sizeof(double2)));
-    FH_TRY(ensure(ctx, ctx->d_kress, (size_t)tb * sizeof(double)));
-    FH_TRY(ensure(ctx, ctx->d_logsin, (size_t)tb * sizeof(double)));
-    FH_TRY(ensure(ctx, ctx->d_A, (size_t)mo * sizeof(double2)));
-    FH_TRY(ensure(ctx, ctx->d_info, (size_t)S * sizeof(int)));
-    FH_TRY(ensure(ctx, ctx->d_nu, (size_t)fh::kFarTerms * J * sizeof(double2)));
-    FH_TRY(ensure(ctx, ctx->d_ph, (size_t)ctx->M * sizeof(double2)));
-
-    fh::CurveParams cp{};
-    cp.kind = curve->kind;
-    cp.n_harm = curve->kind == FH_CURVE_STAR ? curve->n_harm : 0;
-    cp.r0 = curve->r0;
-    cp.cx = curve->center[0];
-    cp.cy = curve->center[1];
-    for (int k = 0; k < FH_MAX_HARMONICS; ++k) {
-        cp.amp[k] = curve->amp[k];
-        cp.phase[k] = curve->phase[k];
-    }
-    PhaseScope ps(ctx, FH_PH_GEOMETRY, 3);
-    fh::launch_geometry(cp, S, maxN, ctx->d_N.as<int>(), ctx->d_vec_off.as<int>(),
-                        ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(),
-                        ctx->stream);
-    FH_TRY(check_launch(ctx, "geometry"));
-    fh::launch_kress_tables(ctx->n_tab, maxN, ctx->d_tab_N.as<int>(), ctx->d_tab_off.as<int>(),
-                            ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(), ctx->stream);
-    FH_TRY(check_launch(ctx, "kress tables"));
-    fh::launch_far_table(J, ctx->M, ctx->d_nu.as<double2>(), ctx->d_ph.as<double2>(), ctx->stream);
-    FH_TRY(check_launch(ctx, "far table"));
-    ctx->geom = true;
+fh_status fh_num_problems(fh_ctx *ctx, int *P) {
+    FH_TRY(enter(ctx));
+    if (!P) return fail(ctx, FH_EINVAL, "P must be non-NULL");
+    *P = (int)ctx->probs.size();
     return FH_OK;
 }
 
@@ -518,8 +654,10 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
     FH_TRY(enter(ctx));
     if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_solve_frequencies: call fh_discretize first");
     for (int s = 0; s < ctx->S; ++s) {
-        const double e = eta ? eta[ctx->solve_j[s]] : ctx->omega[ctx->solve_j[s]];
-        if (!is_fin(e)) return fail(ctx, FH_EINVAL, "eta[%d] is not finite", ctx->solve_j[s]);
+        const Problem &pb = ctx->probs[ctx->solve_prob[s]];
+        const int j = ctx->solve_j[s];
+        const double e = eta ? eta[pb.omega_off + j] : pb.omega[j];
+        if (!is_fin(e)) return fail(ctx, FH_EINVAL, "eta[%lld] is not finite", pb.omega_off + j);
         ctx->eta_s[s] = e;
     }
     ctx->solved = false;
@@ -527,17 +665,17 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
     const fh::SolveTables t = tables(ctx);
     const bool mixed = ctx->precision == FH_MIXED_FP32;
     {
-    PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
-    fh::launch_assemble_groups(t, groups(ctx), ctx->n_groups, ctx->group_tiles,
-                               ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                               ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
-                               ctx->d_logsin.as<double>(), ctx->d_A.as<double2>(), 0, ctx->stream);
-    FH_TRY(check_launch(ctx, "assemble"));
-    if (mixed) FH_TRY(ensure(ctx, ctx->d_g, (size_t)ctx->vec_total * sizeof(double2)));
-    fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                   ctx->p[0], ctx->p[1], mixed ? ctx->d_g.as<double2>() : ctx->d_psi.as<double2>(),
-                   ctx->stream);
-    FH_TRY(check_launch(ctx, "rhs"));
+        PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
+        fh::launch_assemble_groups(t, groups(ctx), ctx->n_groups, ctx->group_tiles,
+                                   ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                                   ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
+                                   ctx->d_logsin.as<double>(), ctx->d_A.as<double2>(), 0, ctx->stream);
+        FH_TRY(check_launch(ctx, "assemble"));
+        if (mixed) FH_TRY(ensure(ctx, ctx->d_g, (size_t)ctx->vec_total * sizeof(double2)));
+        fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                       ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
+                       mixed ? ctx->d_g.as<double2>() : ctx->d_psi.as<double2>(), ctx->stream);
+        FH_TRY(check_launch(ctx, "rhs"));
     }
     FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
     if (!mixed) {
@@ -583,12 +721,13 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
     }
     FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     for (int s = 0; s < ctx->S; ++s) {
+        const int q = ctx->solve_prob[s], j = ctx->solve_j[s];
         if (info[s] > 0)
-            return fail(ctx, FH_ESINGULAR, "frequency j=%d (omega=%.17g): zero or non-finite pivot in column %d",
-                        ctx->solve_j[s], ctx->omega[ctx->solve_j[s]], info[s] - 1);
+            return fail(ctx, FH_ESINGULAR, "problem %d, frequency j=%d (omega=%.17g): zero or non-finite pivot in column %d",
+                        q, j, ctx->probs[q].omega[j], info[s] - 1);
         if (info[s] < 0)
-            return fail(ctx, FH_ENOCONV, "frequency j=%d (omega=%.17g): refinement did not converge in %d sweeps (residual %.3g)",
-                        ctx->solve_j[s], ctx->omega[ctx->solve_j[s]], kRefineMaxIters, resid[s]);
+            return fail(ctx, FH_ENOCONV, "problem %d, frequency j=%d (omega=%.17g): refinement did not converge in %d sweeps (residual %.3g)",
+                        q, j, ctx->probs[q].omega[j], kRefineMaxIters, resid[s]);
     }
     if (mixed)
         for (int s = 0; s < ctx->S; ++s) {
@@ -609,67 +748,81 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
 fh_status fh_window_spectra(fh_ctx *ctx, const double *a, int n_samples, double t0, double dt,
                             double H) {
     FH_TRY(enter(ctx));
-    if (!a) return fail(ctx, FH_EINVAL, "a must be non-NULL");
-    if (n_samples < 1) return fail(ctx, FH_EINVAL, "n_samples must be >= 1");
-    FH_TRY(ensure(ctx, ctx->d_a, (size_t)n_samples * sizeof(double)));
-    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_a.p, a, (size_t)n_samples * sizeof(double),
-                                 cudaMemcpyHostToDevice, ctx->stream));
-    FH_TRY(spectra_common(ctx, ctx->d_a.as<double>(), n_samples, t0, dt, H));
-    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return FH_OK;
+    return spectra_host(ctx, 0, a, n_samples, t0, dt, H);
+}
+
+fh_status fh_window_spectra_p(fh_ctx *ctx, int problem, const double *a, int n_samples,
+                              double t0, double dt, double H) {
+    FH_TRY(enter(ctx));
+    return spectra_host(ctx, problem, a, n_samples, t0, dt, H);
 }
 
 fh_status fh_window_spectra_dev(fh_ctx *ctx, const double *d_a, int n_samples, double t0,
                                 double dt, double H) {
     FH_TRY(enter(ctx));
+    Problem *pb;
+    FH_TRY(get_problem(ctx, 0, &pb));
     if (!d_a) return fail(ctx, FH_EINVAL, "d_a must be non-NULL");
-    return spectra_common(ctx, d_a, n_samples, t0, dt, H);
+    return spectra_common(ctx, *pb, d_a, n_samples, t0, dt, H);
+}
+
+fh_status fh_window_spectra_p_dev(fh_ctx *ctx, int problem, const double *d_a, int n_samples,
+                                  double t0, double dt, double H) {
+    FH_TRY(enter(ctx));
+    Problem *pb;
+    FH_TRY(get_problem(ctx, problem, &pb));
+    if (!d_a) return fail(ctx, FH_EINVAL, "d_a must be non-NULL");
+    return spectra_common(ctx, *pb, d_a, n_samples, t0, dt, H);
 }
 
 fh_status fh_sample(fh_ctx *ctx, const double *x, int n_x, const double *T, int n_T,
                     double *u_out) {
     FH_TRY(enter(ctx));
-    FH_TRY(check_sample_args(ctx, n_x, n_T));
-    if (n_x == 0 || n_T == 0) return FH_OK;
-    if (!x || !T || !u_out) return fail(ctx, FH_EINVAL, "x, T and u_out must be non-NULL");
-    FH_TRY(ensure(ctx, ctx->d_x, (size_t)2 * n_x * sizeof(double)));
-    FH_TRY(ensure(ctx, ctx->d_T, (size_t)n_T * sizeof(double)));
-    FH_TRY(ensure(ctx, ctx->d_u, (size_t)n_x * n_T * sizeof(double)));
-    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_x.p, x, (size_t)2 * n_x * sizeof(double),
-                                 cudaMemcpyHostToDevice, ctx->stream));
-    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_T.p, T, (size_t)n_T * sizeof(double),
-                                 cudaMemcpyHostToDevice, ctx->stream));
-    FH_TRY(sample_common(ctx, ctx->d_x.as<double>(), n_x, ctx->d_T.as<double>(), n_T,
-                         ctx->d_u.as<double>()));
-    FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
-                                 cudaMemcpyDeviceToHost, ctx->stream));
-    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return FH_OK;
+    return sample_host(ctx, 0, x, n_x, T, n_T, u_out);
+}
+
+fh_status fh_sample_p(fh_ctx *ctx, int problem, const double *x, int n_x, const double *T,
+                      int n_T, double *u_out) {
+    FH_TRY(enter(ctx));
+    return sample_host(ctx, problem, x, n_x, T, n_T, u_out);
 }
 
 fh_status fh_sample_dev(fh_ctx *ctx, const double *d_x, int n_x, const double *d_T, int n_T,
                         double *d_u) {
     FH_TRY(enter(ctx));
-    FH_TRY(check_sample_args(ctx, n_x, n_T));
+    FH_TRY(check_sample_args(ctx, 0, n_x, n_T));
     if (n_x == 0 || n_T == 0) return FH_OK;
     if (!d_x || !d_T || !d_u) return fail(ctx, FH_EINVAL, "d_x, d_T and d_u must be non-NULL");
-    return sample_common(ctx, d_x, n_x, d_T, n_T, d_u);
+    return sample_common(ctx, 0, d_x, n_x, d_T, n_T, d_u);
+}
+
+fh_status fh_sample_p_dev(fh_ctx *ctx, int problem, const double *d_x, int n_x,
+                          const double *d_T, int n_T, double *d_u) {
+    FH_TRY(enter(ctx));
+    FH_TRY(check_sample_args(ctx, problem, n_x, n_T));
+    if (n_x == 0 || n_T == 0) return FH_OK;
+    if (!d_x || !d_T || !d_u) return fail(ctx, FH_EINVAL, "d_x, d_T and d_u must be non-NULL");
+    return sample_common(ctx, problem, d_x, n_x, d_T, n_T, d_u);
 }
 
 fh_status fh_get_num_windows(fh_ctx *ctx, int *K) {
     FH_TRY(enter(ctx));
     if (!K) return fail(ctx, FH_EINVAL, "K must be non-NULL");
-    if (!ctx->spectra) return fail(ctx, FH_ESTATE, "no window spectra yet");
-    *K = ctx->K;
+    Problem *pb;
+    FH_TRY(get_problem(ctx, 0, &pb));
+    if (!pb->spectra) return fail(ctx, FH_ESTATE, "no window spectra yet");
+    *K = pb->K;
     return FH_OK;
 }
 
 fh_status fh_get_window_spectra(fh_ctx *ctx, double *s, double *B) {
     FH_TRY(enter(ctx));
-    if (!ctx->spectra) return fail(ctx, FH_ESTATE, "no window spectra yet");
-    if (s) std::memcpy(s, ctx->s.data(), ctx->s.size() * sizeof(double));
+    Problem *pb;
+    FH_TRY(get_problem(ctx, 0, &pb));
+    if (!pb->spectra) return fail(ctx, FH_ESTATE, "no window spectra yet");
+    if (s) std::memcpy(s, pb->s.data(), pb->s.size() * sizeof(double));
     if (B) {
-        FH_CUDA(ctx, cudaMemcpyAsync(B, ctx->d_B.p, (size_t)ctx->K * ctx->J * sizeof(double2),
+        FH_CUDA(ctx, cudaMemcpyAsync(B, pb->d_B.p, (size_t)pb->K * pb->J * sizeof(double2),
                                      cudaMemcpyDeviceToHost, ctx->stream));
         FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
@@ -678,9 +831,10 @@ fh_status fh_get_window_spectra(fh_ctx *ctx, double *s, double *B) {
 
 fh_status fh_get_geometry(fh_ctx *ctx, int j, double *z, double *dz, double *ddz) {
     FH_TRY(enter(ctx));
-    if (!ctx->geom) return fail(ctx, FH_ESTATE, "call fh_discretize first");
-    if (j < 1 || j >= ctx->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
-    const int s = j - 1, n = ctx->solve_N[s];
+    Problem *pb;
+    FH_TRY(get_problem(ctx, 0, &pb));
+    if (j < 1 || j >= pb->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
+    const int s = pb->s_begin + j - 1, n = ctx->solve_N[s];
     const size_t off = (size_t)ctx->vec_off[s] * sizeof(double2), by = (size_t)n * sizeof(double2);
     if (z) FH_CUDA(ctx, cudaMemcpyAsync(z, (char *)ctx->d_z.p + off, by, cudaMemcpyDeviceToHost, ctx->stream));
     if (dz) FH_CUDA(ctx, cudaMemcpyAsync(dz, (char *)ctx->d_dz.p + off, by, cudaMemcpyDeviceToHost, ctx->stream));
@@ -691,12 +845,13 @@ fh_status fh_get_geometry(fh_ctx *ctx, int j, double *z, double *dz, double *ddz
 
 fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double *g) {
     FH_TRY(enter(ctx));
-    if (!ctx->geom) return fail(ctx, FH_ESTATE, "call fh_discretize first");
-    if (j < 1 || j >= ctx->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
+    Problem *pb;
+    FH_TRY(get_problem(ctx, 0, &pb));
+    if (j < 1 || j >= pb->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
     if (!is_fin(eta_j)) return fail(ctx, FH_EINVAL, "eta_j must be finite");
-    const int s = j - 1, n = ctx->solve_N[s];
+    const int s = pb->s_begin + j - 1, n = ctx->solve_N[s];
     // the subgroup containing s is assembled exactly as in fh_solve_frequencies
-    int gi = 0;
+    int gi = pb->g_begin;
     while (!(ctx->sg[gi].x <= s && s < ctx->sg[gi].x + ctx->sg[gi].y)) ++gi;
     const int2 sgv = ctx->sg[gi];
     const long long nt = (n + 31) / 32;
@@ -723,7 +878,8 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
                                ctx->stream);
     FH_TRY(check_launch(ctx, "assemble (single)"));
     fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                   ctx->p[0], ctx->p[1], ctx->d_tmpg.as<double2>(), ctx->stream);
+                   ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
+                   ctx->d_tmpg.as<double2>(), ctx->stream);
     FH_TRY(check_launch(ctx, "rhs (single)"));
     std::vector<double2> colmajor((size_t)n * n);
     FH_CUDA(ctx, cudaMemcpyAsync(colmajor.data(),
@@ -745,18 +901,22 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     return FH_OK;
 }
 
-fh_status fh_get_density(fh_ctx *ctx, int j, double *psi) {
+fh_status fh_get_density_p(fh_ctx *ctx, int problem, int j, double *psi) {
     FH_TRY(enter(ctx));
+    Problem *pb;
+    FH_TRY(get_problem(ctx, problem, &pb));
     if (!ctx->solved) return fail(ctx, FH_ESTATE, "no densities yet");
-    if (j < 1 || j >= ctx->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
+    if (j < 1 || j >= pb->J) return fail(ctx, FH_EINVAL, "j must be in [1, J-1]");
     if (!psi) return fail(ctx, FH_EINVAL, "psi must be non-NULL");
-    const int s = j - 1;
+    const int s = pb->s_begin + j - 1;
     FH_CUDA(ctx, cudaMemcpyAsync(psi, (char *)ctx->d_psi.p + (size_t)ctx->vec_off[s] * sizeof(double2),
                                  (size_t)ctx->solve_N[s] * sizeof(double2), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return FH_OK;
 }
+
+fh_status fh_get_density(fh_ctx *ctx, int j, double *psi) { return fh_get_density_p(ctx, 0, j, psi); }
 
 fh_status fh_set_densities(fh_ctx *ctx, const double *psi_all) {
     FH_TRY(enter(ctx));
@@ -773,7 +933,7 @@ fh_status fh_get_target_field(fh_ctx *ctx, double *V) {
     FH_TRY(enter(ctx));
     if (!ctx->have_V) return fail(ctx, FH_ESTATE, "no target field yet");
     if (!V) return fail(ctx, FH_EINVAL, "V must be non-NULL");
-    const int n_x = ctx->n_x_last, J = ctx->J;
+    const int n_x = ctx->n_x_last, J = ctx->probs[ctx->v_problem].J;
     std::vector<double2> h((size_t)J * n_x);
     FH_CUDA(ctx, cudaMemcpyAsync(h.data(), ctx->d_V.p, h.size() * sizeof(double2),
                                  cudaMemcpyDeviceToHost, ctx->stream));
@@ -789,26 +949,46 @@ fh_status fh_get_target_field(fh_ctx *ctx, double *V) {
 fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, int n_T,
                         double *u_out) {
     FH_TRY(enter(ctx));
-    if (!ctx->spectra) return fail(ctx, FH_ESTATE, "fh_synthesize: call fh_window_spectra first");
+    Problem *pb;
+    FH_TRY(get_problem(ctx, 0, &pb));
+    if (!pb->spectra) return fail(ctx, FH_ESTATE, "fh_synthesize: call fh_window_spectra first");
     if (n_x < 0 || n_T < 0) return fail(ctx, FH_EINVAL, "n_x and n_T must be >= 0");
     if (n_x == 0 || n_T == 0) return FH_OK;
     if (!V || !T || !u_out) return fail(ctx, FH_EINVAL, "V, T and u_out must be non-NULL");
-    const int J = ctx->J;
+    const int J = pb->J;
     std::vector<double2> h((size_t)J * n_x);
     for (int i = 0; i < n_x; ++i)
         for (int j = 0; j < J; ++j)
             h[(size_t)j * n_x + i] = make_double2(V[2 * ((size_t)i * J + j)], V[2 * ((size_t)i * J + j) + 1]);
     FH_TRY(upload(ctx, ctx->d_V, h));
     ctx->n_x_last = n_x;
+    ctx->v_problem = 0;
     ctx->have_V = true;
     FH_TRY(ensure(ctx, ctx->d_T, (size_t)n_T * sizeof(double)));
     FH_TRY(ensure(ctx, ctx->d_u, (size_t)n_x * n_T * sizeof(double)));
     FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_T.p, T, (size_t)n_T * sizeof(double), cudaMemcpyHostToDevice,
                                  ctx->stream));
-    FH_TRY(synth_common(ctx, n_x, ctx->d_T.as<double>(), n_T, ctx->d_u.as<double>()));
+    FH_TRY(synth_common(ctx, *pb, n_x, ctx->d_T.as<double>(), n_T, ctx->d_u.as<double>()));
     FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
                                  cudaMemcpyDeviceToHost, ctx->stream));
     FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FH_OK;
+}
+
+fh_status fh_footprint(const int *J, const int *N, int P, int precision, long long *bytes) {
+    if (!J || !N || !bytes || P < 1) return FH_EINVAL;
+    long long b = 0, jo = 0;
+    for (int q = 0; q < P; ++q) {
+        if (J[q] < 2) return FH_EINVAL;
+        for (int j = 1; j < J[q]; ++j) {
+            const long long n = N[jo + j];
+            b += n * n * 16 + n * (16 * 4 + 16 + 8);          // matrix, nodes, density, tables
+            if (precision == FH_MIXED_FP32) b += n * n * 8 + n * (16 + 4);   // FP32 copy, rhs, perm
+        }
+        b += (long long)fh::kFarTerms * J[q] * 16 + 2LL * (J[q] - 1) * 16;
+        jo += J[q];
+    }
+    *bytes = b;
     return FH_OK;
 }
 

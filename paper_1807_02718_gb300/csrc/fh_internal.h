@@ -35,8 +35,9 @@ struct SolveTables {
 };
 
 // ---- geometry and quadrature tables (k_geometry.cu) ----
-void launch_geometry(const CurveParams &cp, int S, int maxN, const int *N, const int *vec_off,
-                     double2 *z, double2 *dz, double2 *ddz, cudaStream_t st);
+// Solve s uses curve curves[prob[s]] (device arrays).
+void launch_geometry(const CurveParams *curves, const int *prob, int S, int maxN, const int *N,
+                     const int *vec_off, double2 *z, double2 *dz, double2 *ddz, cudaStream_t st);
 void launch_kress_tables(int n_tab, int maxN, const int *tab_N, const int *tab_off,
                          double *kress, double *logsin, cudaStream_t st);
 
@@ -53,16 +54,14 @@ struct Subgroups {
 
 // ---- CFIE assembly (k_assemble.cu) ----
 // Matrices are column-major: A_s(i, l) = A[mat_off[s] + l * N_s + i].
-void launch_assemble(const SolveTables &t, int S, const long long *tile_off, long long n_tiles,
-                     const double2 *z, const double2 *dz, const double2 *ddz,
-                     const double *kress, const double *logsin, double2 *A, cudaStream_t st);
 // Grouped assembly: every matrix of subgroup g at A + mat_off[s] + out_shift.
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long n_tiles, const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             double2 *A, long long out_shift, cudaStream_t st);
+// Solve s uses the incidence direction pdir[prob[s]].
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
-                double p0, double p1, double2 *g, cudaStream_t st);
+                const int *prob, const double2 *pdir, double2 *g, cudaStream_t st);
 
 // ---- batched dense LU with partial pivoting and solve (k_lu.cu) ----
 // Solves A_s x = b_s in place (b_s overwritten by x_s); A_s overwritten by
@@ -90,11 +89,13 @@ void launch_window_spectra(const double *a, int n_samples, long long start0, lon
 // ---- target fields (k_field.cu) ----
 // V[j * n_x + i] = V(x_i, omega_j); V[0 * n_x + i] = 1 (omega_0 = 0).
 // Work items (subgroup, first node) of kFieldChunk nodes; item_first[g] is
-// the first item of subgroup g (n_groups + 1 entries).  part: scratch of
+// the first item of subgroup g (global, one entry past the last subgroup).
+// One problem's subgroups g_begin .. g_begin + n_groups - 1 own the items
+// item_begin .. item_begin + n_items - 1.  part: scratch of
 // n_items * kGroup * n_x complex values.
 constexpr int kFieldChunk = 64;
-void launch_target_field(const SolveTables &t, const Subgroups &g, int n_groups,
-                         const int2 *items, int n_items, const int *item_first,
+void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
+                         const int2 *items, int item_begin, int n_items, const int *item_first,
                          const int *solve_j, const double2 *z, const double2 *dz,
                          const double2 *psi, const double *x, int n_x, double2 *part,
                          double2 *V, cudaStream_t st);

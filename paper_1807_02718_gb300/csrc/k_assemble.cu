@@ -14,9 +14,10 @@
 // Diagonal limits: M1 = -s/4pi, M2 = [i/4 - C/2pi - ln(kappa s/2)/2pi] s,
 // L1 = 0, L2 = (z1'' z2' - z2'' z1') / (4 pi s^2).
 //
-// One CTA assembles one 32 x 32 tile of one frequency's matrix; tiles of all
-// frequencies form one flat launch (prefix offsets tile_off).  Each warp
-// writes 32 consecutive rows of a column: column-major stores of 512 B.
+// One CTA assembles one 32 x 32 tile for up to kGroup frequencies; tiles of
+// all frequencies (of all problems of a batch) form one flat launch (prefix
+// offsets tile_off).  Each warp writes 32 consecutive rows of a column:
+// column-major stores of 512 B.
 #include "bessel.cuh"
 #include "fh_internal.h"
 
@@ -32,74 +33,6 @@ __device__ __forceinline__ int find_solve(const long long *__restrict__ off, int
         if (off[mid] <= b) lo = mid; else hi = mid;
     }
     return lo;
-}
-
-__global__ void __launch_bounds__(256) assemble_kernel(
-    SolveTables t, int S, const long long *__restrict__ tile_off,
-    const double2 *__restrict__ z, const double2 *__restrict__ dz,
-    const double2 *__restrict__ ddz, const double *__restrict__ kress,
-    const double *__restrict__ logsin, double2 *__restrict__ A) {
-    const long long b = blockIdx.x;
-    const int s = find_solve(tile_off, S, b);
-    const int N = t.N[s];
-    const int nt = (N + kTile - 1) / kTile;
-    const long long lt = b - tile_off[s];
-    const int tr = (int)(lt % nt), tc = (int)(lt / nt);
-    const int i = tr * kTile + (threadIdx.x & 31);
-    if (i >= N) return;
-    const int vo = t.vec_off[s];
-    const int to = t.tab_off[t.tab[s]];
-    const double kappa = t.kappa[s], eta = t.eta[s];
-    const double pin = 2.0 * kPi / (double)N;   // pi / n
-    const double2 zi = z[vo + i], dzi = dz[vo + i];
-    const double si = sqrt(dzi.x * dzi.x + dzi.y * dzi.y);
-    double2 *Acol = A + t.mat_off[s];
-    const double inv4pi = 1.0 / (4.0 * kPi);
-
-    for (int q = threadIdx.x >> 5; q < kTile; q += 8) {
-        const int l = tc * kTile + q;
-        if (l >= N) break;
-        int d = i - l;
-        if (d < 0) d += N;
-        const double Rw = kress[to + d];
-        const double2 dzl = dz[vo + l];
-        const double sl = sqrt(dzl.x * dzl.x + dzl.y * dzl.y);
-        double L1, L2r, L2i, M1, M2r, M2i;
-        if (l == i) {
-            const double2 dd = ddz[vo + i];
-            M1 = -si * inv4pi;
-            M2r = (-kEulerGamma / (2.0 * kPi) - log(kappa * si * 0.5) / (2.0 * kPi)) * si;
-            M2i = 0.25 * si;
-            L1 = 0.0;
-            L2r = (dd.x * dzi.y - dd.y * dzi.x) * inv4pi / (si * si);
-            L2i = 0.0;
-        } else {
-            const double2 zl = z[vo + l];
-            const double d1 = zl.x - zi.x, d2 = zl.y - zi.y;
-            const double r = sqrt(d1 * d1 + d2 * d2);
-            const double x = kappa * r;
-            double J0, Y0, J1, Y1;
-            bessel_j0y0j1y1(x, J0, Y0, J1, Y1);
-            const double Nil = dzi.y * d1 - dzi.x * d2;
-            const double ls = logsin[to + d];
-            const double g = Nil * sl / (si * r);
-            // M = (i/4)(J0 + i Y0) s_l
-            const double Mr = -0.25 * Y0 * sl, Mi = 0.25 * J0 * sl;
-            M1 = -J0 * sl * inv4pi;
-            M2r = Mr - M1 * ls;
-            M2i = Mi;
-            // L = (i kappa/4)(J1 + i Y1) g
-            const double Lr = -0.25 * kappa * Y1 * g, Li = 0.25 * kappa * J1 * g;
-            L1 = -kappa * inv4pi * J1 * g;
-            L2r = Lr - L1 * ls;
-            L2i = Li;
-        }
-        // R (L1 - i eta M1) + (pi/n)(L2 - i eta M2)
-        double ar = Rw * L1 + pin * (L2r + eta * M2i);
-        double ai = Rw * (-eta * M1) + pin * (L2i - eta * M2r);
-        if (l == i) ar += 0.5;
-        Acol[(long long)l * N + i] = make_double2(ar, ai);
-    }
 }
 
 // Grouped assembly: one CTA per 32 x 32 tile of a frequency subgroup (up to
@@ -219,12 +152,14 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
 
 // g_i = dB/dn - i eta B = i (kappa p.nu_i - eta) e^{i kappa p.z_i}
 __global__ void rhs_kernel(SolveTables t, const double2 *__restrict__ z,
-                           const double2 *__restrict__ dz, double p0, double p1,
-                           double2 *__restrict__ g) {
+                           const double2 *__restrict__ dz, const int *__restrict__ prob,
+                           const double2 *__restrict__ pdir, double2 *__restrict__ g) {
     const int s = blockIdx.y;
     const int N = t.N[s];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const double2 pd = pdir[prob[s]];
+    const double p0 = pd.x, p1 = pd.y;
     const int o = t.vec_off[s] + i;
     const double kappa = t.kappa[s], eta = t.eta[s];
     const double2 zi = z[o], d = dz[o];
@@ -238,14 +173,6 @@ __global__ void rhs_kernel(SolveTables t, const double2 *__restrict__ z,
 
 }  // namespace
 
-void launch_assemble(const SolveTables &t, int S, const long long *tile_off, long long n_tiles,
-                     const double2 *z, const double2 *dz, const double2 *ddz,
-                     const double *kress, const double *logsin, double2 *A, cudaStream_t st) {
-    if (n_tiles <= 0) return;
-    assemble_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, S, tile_off, z, dz, ddz, kress,
-                                                       logsin, A);
-}
-
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long n_tiles, const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
@@ -256,10 +183,10 @@ void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_grou
 }
 
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
-                double p0, double p1, double2 *g, cudaStream_t st) {
+                const int *prob, const double2 *pdir, double2 *g, cudaStream_t st) {
     if (S <= 0) return;
     dim3 grid((maxN + 127) / 128, S);
-    rhs_kernel<<<grid, 128, 0, st>>>(t, z, dz, p0, p1, g);
+    rhs_kernel<<<grid, 128, 0, st>>>(t, z, dz, prob, pdir, g);
 }
 
 }  // namespace fh

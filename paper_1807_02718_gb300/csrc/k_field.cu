@@ -27,12 +27,12 @@ constexpr int kChunk = 64;   // source nodes per work item
 // scratch; field_reduce_kernel adds them in a fixed order (the result does
 // not depend on scheduling).
 __global__ void __launch_bounds__(kTgt) field_partial_kernel(
-    SolveTables t, Subgroups grp, const int2 *__restrict__ items,
+    SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin,
     const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
     double2 *__restrict__ part) {
     const int w = blockIdx.y;
-    const int2 item = items[w];                 // (subgroup, first node)
+    const int2 item = items[item_begin + w];    // (subgroup, first node)
     const int g = item.x, i0 = item.y;
     const int2 sgv = grp.sg[g];
     const int s0 = sgv.x, cnt = sgv.y;
@@ -121,14 +121,15 @@ __global__ void __launch_bounds__(kTgt) field_partial_kernel(
 }
 
 // V[solve_j[s0 + j]][x] = sum over the subgroup's items, in item order.
-__global__ void field_reduce_kernel(Subgroups grp, const int *__restrict__ item_first,
-                                    const int *__restrict__ solve_j, const double2 *__restrict__ part,
-                                    int n_x, double2 *__restrict__ V) {
-    const int g = blockIdx.y;
+__global__ void field_reduce_kernel(Subgroups grp, int g_begin, const int *__restrict__ item_first,
+                                    int item_begin, const int *__restrict__ solve_j,
+                                    const double2 *__restrict__ part, int n_x,
+                                    double2 *__restrict__ V) {
+    const int g = g_begin + blockIdx.y;
     const int it = blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= n_x) return;
     const int2 sgv = grp.sg[g];
-    const int w0 = item_first[g], w1 = item_first[g + 1];
+    const int w0 = item_first[g] - item_begin, w1 = item_first[g + 1] - item_begin;
     for (int j = 0; j < sgv.y; ++j) {
         double2 acc = make_double2(0.0, 0.0);
         for (int w = w0; w < w1; ++w) {
@@ -166,18 +167,18 @@ void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st) {
     if (n > 0) bessel_eval_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, n, out);
 }
 
-void launch_target_field(const SolveTables &t, const Subgroups &g, int n_groups,
-                         const int2 *items, int n_items, const int *item_first,
+void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
+                         const int2 *items, int item_begin, int n_items, const int *item_first,
                          const int *solve_j, const double2 *z, const double2 *dz,
                          const double2 *psi, const double *x, int n_x, double2 *part,
                          double2 *V, cudaStream_t st) {
     if (n_x <= 0) return;
     field_zero_freq_kernel<<<(n_x + 255) / 256, 256, 0, st>>>(n_x, V);
-    if (n_groups <= 0) return;
+    if (n_groups <= 0 || n_items <= 0) return;
     dim3 grid((n_x + kTgt - 1) / kTgt, n_items);
-    field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, z, dz, psi, x, n_x, part);
+    field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, part);
     dim3 g2((n_x + 127) / 128, n_groups);
-    field_reduce_kernel<<<g2, 128, 0, st>>>(g, item_first, solve_j, part, n_x, V);
+    field_reduce_kernel<<<g2, 128, 0, st>>>(g, g_begin, item_first, item_begin, solve_j, part, n_x, V);
 }
 
 }  // namespace fh

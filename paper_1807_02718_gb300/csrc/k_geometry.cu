@@ -36,13 +36,15 @@ __device__ void curve_eval(const CurveParams &cp, double t, double2 &z, double2 
     ddz = make_double2(ddr * c1 - 2.0 * dr * s1 - r * c1, ddr * s1 + 2.0 * dr * c1 - r * s1);
 }
 
-__global__ void geometry_kernel(CurveParams cp, const int *__restrict__ Ns,
+__global__ void geometry_kernel(const CurveParams *__restrict__ curves,
+                                const int *__restrict__ prob, const int *__restrict__ Ns,
                                 const int *__restrict__ vec_off, double2 *__restrict__ z,
                                 double2 *__restrict__ dz, double2 *__restrict__ ddz) {
     const int s = blockIdx.y;
     const int N = Ns[s];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const CurveParams &cp = curves[prob[s]];
     const int n = N / 2;
     const double t = kPi * (double)i / (double)n;
     double2 a, b, c;
@@ -79,11 +81,11 @@ __global__ void kress_kernel(const int *__restrict__ tab_N, const int *__restric
 
 }  // namespace
 
-void launch_geometry(const CurveParams &cp, int S, int maxN, const int *N, const int *vec_off,
-                     double2 *z, double2 *dz, double2 *ddz, cudaStream_t st) {
+void launch_geometry(const CurveParams *curves, const int *prob, int S, int maxN, const int *N,
+                     const int *vec_off, double2 *z, double2 *dz, double2 *ddz, cudaStream_t st) {
     if (S <= 0) return;
     dim3 grid((maxN + 127) / 128, S);
-    geometry_kernel<<<grid, 128, 0, st>>>(cp, N, vec_off, z, dz, ddz);
+    geometry_kernel<<<grid, 128, 0, st>>>(curves, prob, N, vec_off, z, dz, ddz);
 }
 
 void launch_kress_tables(int n_tab, int maxN, const int *tab_N, const int *tab_off,

@@ -30,7 +30,9 @@ EXPORTED = [
     "fh_sample_dev", "fh_get_num_windows", "fh_get_window_spectra", "fh_get_geometry",
     "fh_assemble_matrix", "fh_get_density", "fh_set_densities", "fh_get_target_field",
     "fh_synthesize", "fh_set_timing", "fh_get_timings", "fh_probe_fma_peak",
-    "fh_eval_bessel", "fh_synthesize_static",
+    "fh_eval_bessel", "fh_synthesize_static", "fh_discretize_batch", "fh_num_problems",
+    "fh_window_spectra_p", "fh_window_spectra_p_dev", "fh_sample_p", "fh_sample_p_dev",
+    "fh_get_density_p", "fh_footprint",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "spectra", "field", "weights", "contract"]
@@ -96,6 +98,14 @@ def load_library(path: str | None = None):
         "fh_get_timings": (C.c_int, [vp, C.POINTER(fh_timings), C.c_int]),
         "fh_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
         "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
+        "fh_discretize_batch": (C.c_int, [vp, C.c_int, C.POINTER(fh_curve), _IP, _DP, _IP, _DP, _DP]),
+        "fh_num_problems": (C.c_int, [vp, _IP]),
+        "fh_window_spectra_p": (C.c_int, [vp, C.c_int, _DP, C.c_int, C.c_double, C.c_double, C.c_double]),
+        "fh_window_spectra_p_dev": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_double, C.c_double, C.c_double]),
+        "fh_sample_p": (C.c_int, [vp, C.c_int, _DP, C.c_int, _DP, C.c_int, _DP]),
+        "fh_sample_p_dev": (C.c_int, [vp, C.c_int, vp, C.c_int, vp, C.c_int, vp]),
+        "fh_get_density_p": (C.c_int, [vp, C.c_int, C.c_int, _DP]),
+        "fh_footprint": (C.c_int, [_IP, _IP, C.c_int, C.c_int, C.POINTER(C.c_longlong)]),
         "fh_synthesize_static": (C.c_int, [C.c_int, C.c_double, C.c_int, vp, vp, vp, C.c_int, vp,
                                            C.c_int, vp, vp]),
     }
@@ -309,6 +319,70 @@ def fh_synthesize_static(J: int, W: float, d_s, d_B, d_V, d_T, d_u, stream=None)
         _dev_ptr(d_u), C.c_void_p(stream or 0))
     if st != FH_OK:
         raise FHError(st, "fh_synthesize_static failed")
+
+
+def fh_discretize_batch(ctx, curves, omegas, Ns=None, cs=None, ps=None):
+    """Discretise P problems in one context (lists of curves, omega arrays, N arrays)."""
+    P = len(curves)
+    arr = (fh_curve * P)(*[c if isinstance(c, fh_curve) else make_curve(c) for c in curves])
+    J = np.asarray([len(o) for o in omegas], dtype=np.int32)
+    om = _f64(np.concatenate([np.asarray(o, dtype=np.float64) for o in omegas]))
+    Nv = None if Ns is None else np.ascontiguousarray(np.concatenate(Ns), dtype=np.int32)
+    cv = _f64(np.ones(P) if cs is None else cs)
+    pv = _f64(np.tile([1.0, 0.0], P) if ps is None else np.asarray(ps, dtype=np.float64).reshape(-1))
+    _check(ctx, load_library().fh_discretize_batch(ctx, P, arr, J.ctypes.data_as(_IP), _dp(om),
+                                                   None if Nv is None else Nv.ctypes.data_as(_IP),
+                                                   _dp(cv), _dp(pv)))
+
+
+def fh_num_problems(ctx) -> int:
+    P = C.c_int()
+    _check(ctx, load_library().fh_num_problems(ctx, C.byref(P)))
+    return P.value
+
+
+def fh_window_spectra_p(ctx, problem: int, a, t0: float, dt: float, H: float = 10.0):
+    av = _f64(a)
+    _check(ctx, load_library().fh_window_spectra_p(ctx, problem, _dp(av), av.size, float(t0),
+                                                   float(dt), float(H)))
+
+
+def fh_window_spectra_p_dev(ctx, problem: int, d_a, t0: float, dt: float, H: float = 10.0):
+    _check(ctx, load_library().fh_window_spectra_p_dev(ctx, problem, _dev_ptr(d_a), d_a.numel(),
+                                                       float(t0), float(dt), float(H)))
+
+
+def fh_sample_p(ctx, problem: int, x, T):
+    xv, Tv = _f64(x), _f64(T)
+    n_x, n_T = xv.size // 2, Tv.size
+    u = np.empty((n_x, n_T), dtype=np.float64)
+    _check(ctx, load_library().fh_sample_p(ctx, problem, _dp(xv), n_x, _dp(Tv), n_T, _dp(u)))
+    return u
+
+
+def fh_sample_p_dev(ctx, problem: int, d_x, d_T, d_u):
+    n_x, n_T = d_x.numel() // 2, d_T.numel()
+    if d_u.numel() != n_x * n_T:
+        raise ValueError("d_u must hold n_x * n_T doubles")
+    _check(ctx, load_library().fh_sample_p_dev(ctx, problem, _dev_ptr(d_x), n_x, _dev_ptr(d_T), n_T,
+                                               _dev_ptr(d_u)))
+
+
+def fh_get_density_p(ctx, problem: int, j: int, N: int):
+    psi = np.empty(N, dtype=np.complex128)
+    _check(ctx, load_library().fh_get_density_p(ctx, problem, j, psi.ctypes.data_as(_DP)))
+    return psi
+
+
+def fh_footprint(Js, Ns, precision: int = FH_FP64) -> int:
+    J = np.ascontiguousarray(Js, dtype=np.int32)
+    N = np.ascontiguousarray(np.concatenate(Ns), dtype=np.int32)
+    out = C.c_longlong()
+    st = load_library().fh_footprint(J.ctypes.data_as(_IP), N.ctypes.data_as(_IP), J.size,
+                                     precision, C.byref(out))
+    if st != FH_OK:
+        raise FHError(st, "fh_footprint failed")
+    return out.value
 
 
 class Problem:
