@@ -280,6 +280,15 @@ fh_status fh_get_timings(fh_ctx *ctx, fh_timings *out, int reset);
  * allocates its own device scratch. */
 fh_status fh_eval_bessel(const double *x, int n, double *out);
 
+/* Tensor-core (tcgen05) check: C = A B^T for host FP32 arrays A (M x K) and
+ * B (N x K), row-major, with the operands taken as BF16 (kind = 1, rounded to
+ * nearest) or TF32 (kind = 2) and FP32 accumulation in tensor memory; C is
+ * M x N row-major.  M % 128 == 0, N % 256 == 0, K % 64 == 0.  Diagnostic for
+ * the tensor-core building blocks used by the solver; allocates its own
+ * device buffers.  FH_ETIMEOUT if an MMA completion wait gave up. */
+fh_status fh_tc_gemm_test(int kind, int M, int N, int K, const float *A, const float *B,
+                          float *C);
+
 /* Measured FMA throughput of device `device` in TFLOP/s (2 flops per FMA):
  * fp64 != 0 for binary64, else binary32; `iters` FMAs per chain (e.g. 4096).
  * Not part of the scattering path: it gives the arithmetic roofline against

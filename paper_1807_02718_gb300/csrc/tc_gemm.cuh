@@ -1,0 +1,135 @@
+// Fifth-generation tensor-core (tcgen05) building blocks for sm_103a.
+//
+// A CTA of 128 threads owns one 128 x BN FP32 accumulator tile in tensor
+// memory (TMEM: lane = row, column = output column).  Operands are staged in
+// shared memory by the threads in the canonical K-major layout without
+// swizzle: "core matrices" of 8 rows x 16 bytes stored as 128 contiguous
+// bytes; core matrices adjacent in K are LBO = 128 bytes apart, adjacent
+// 8-row groups SBO = (K_chunk bytes / 16) * 128 bytes apart.  One elected
+// thread issues tcgen05.mma for each K step (16 elements for BF16, 8 for
+// TF32), commits to an mbarrier, and every thread waits on it with a bounded
+// spin (on time-out the CTA records an error flag and skips the tile's
+// epilogue instead of hanging).  The epilogue reads the accumulator with
+// tcgen05.ld (each warp its 32 TMEM lanes).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fh {
+namespace tc {
+
+constexpr int kM = 128;                  // rows per tile (TMEM lanes)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;              // descriptor version for tcgen05
+    return d;                            // base offset 0, relative LBO, no swizzle
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, M x N.
+// ab_format: 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32).
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int M, int N) {
+    return (1u << 4)                      // D format F32
+           | (ab_format << 7)             // A format
+           | (ab_format << 10)            // B format
+           | ((uint32_t)(N >> 3) << 17)
+           | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the phase of the given parity; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long max_iters) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < max_iters; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Warp-collective TMEM allocation of ncols (power of two >= 32) columns; the
+// TMEM address is written to *slot (shared memory).
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(slot)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+template <int kKind>   // 1: kind::f16 (BF16 operands), 2: kind::tf32
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                    uint32_t accumulate) {
+    if (kKind == 1)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate) : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) of a K-major no-swizzle tile whose rows hold
+// kbytes bytes (k-chunk): core matrix (row/8, k-byte/16) at (row/8)*SBO +
+// (kbyte/16)*128, row%8 at 16-byte rows inside it.
+__device__ __forceinline__ uint32_t kmajor_offset(int row, int kbyte, int kbytes) {
+    return (uint32_t)((row >> 3) * (kbytes / 16) * 128 + (kbyte >> 4) * 128 + (row & 7) * 16 +
+                      (kbyte & 15));
+}
+
+}  // namespace tc
+}  // namespace fh

@@ -32,7 +32,7 @@ EXPORTED = [
     "fh_synthesize", "fh_set_timing", "fh_get_timings", "fh_probe_fma_peak",
     "fh_eval_bessel", "fh_synthesize_static", "fh_discretize_batch", "fh_num_problems",
     "fh_window_spectra_p", "fh_window_spectra_p_dev", "fh_sample_p", "fh_sample_p_dev",
-    "fh_get_density_p", "fh_footprint",
+    "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "spectra", "field", "weights", "contract"]
@@ -106,6 +106,8 @@ def load_library(path: str | None = None):
         "fh_sample_p_dev": (C.c_int, [vp, C.c_int, vp, C.c_int, vp, C.c_int, vp]),
         "fh_get_density_p": (C.c_int, [vp, C.c_int, C.c_int, _DP]),
         "fh_footprint": (C.c_int, [_IP, _IP, C.c_int, C.c_int, C.POINTER(C.c_longlong)]),
+        "fh_tc_gemm_test": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float),
+                                      C.POINTER(C.c_float), C.POINTER(C.c_float)]),
         "fh_synthesize_static": (C.c_int, [C.c_int, C.c_double, C.c_int, vp, vp, vp, C.c_int, vp,
                                            C.c_int, vp, vp]),
     }
@@ -383,6 +385,21 @@ def fh_footprint(Js, Ns, precision: int = FH_FP64) -> int:
     if st != FH_OK:
         raise FHError(st, "fh_footprint failed")
     return out.value
+
+
+def fh_tc_gemm_test(kind: int, A, B):
+    """C = A B^T on the tensor cores (kind 1: BF16 operands, 2: TF32)."""
+    Af = np.ascontiguousarray(A, dtype=np.float32)
+    Bf = np.ascontiguousarray(B, dtype=np.float32)
+    M, K = Af.shape
+    N = Bf.shape[0]
+    Cf = np.empty((M, N), dtype=np.float32)
+    fp = C.POINTER(C.c_float)
+    st = load_library().fh_tc_gemm_test(kind, M, N, K, Af.ctypes.data_as(fp), Bf.ctypes.data_as(fp),
+                                        Cf.ctypes.data_as(fp))
+    if st != FH_OK:
+        raise FHError(st, "fh_tc_gemm_test failed")
+    return Cf
 
 
 class Problem:

@@ -47,3 +47,35 @@ def test_bessel_routine_dense_grid():
 def test_fp64_peak_probe_runs():
     v = F.fh_probe_fma_peak(0, True, 256)
     assert v > 0.1
+
+
+def _bf16(a):
+    """Round float32 to bfloat16 (nearest even), returned as float64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 512, 192)])
+def test_tcgen05_gemm_bf16(M, N, K):
+    """BF16 products are exact and accumulate in FP32: C = A B^T to FP32 rounding."""
+    rng = np.random.default_rng(M + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    C = F.fh_tc_gemm_test(1, A, B)
+    ref = _bf16(A) @ _bf16(B).T
+    assert np.max(np.abs(C - ref)) < 1e-5 * np.sqrt(K) * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 256, 128)])
+def test_tcgen05_gemm_tf32(M, N, K):
+    """TF32 operands (10-bit mantissa): C = A B^T to ~2^-11 relative per product."""
+    rng = np.random.default_rng(7 * M + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    C = F.fh_tc_gemm_test(2, A, B)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    err = np.max(np.abs(C - ref)) / (np.sqrt(K) * np.max(np.abs(A)) * np.max(np.abs(B)))
+    assert err < 2e-3
+    # the result is not a plain FP32 GEMM in disguise of zeros or garbage
+    assert np.corrcoef(C.ravel(), ref.ravel())[0, 1] > 0.999
