@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -217,7 +217,7 @@ def run_gpu(args, world, rank, local):
 
     build.build()
     torch.cuda.set_device(local)
-    prec = F.FH_FP64 if args.precision == "fp64" else F.FH_MIXED_FP32
+    prec = {"fp64": F.FH_FP64, "mixed": F.FH_MIXED_FP32, "tf32": F.FH_MIXED_TF32}[args.precision]
     wl = fi.kite_pulses()
     S = wl.J - 1
     n_x, n_T = wl.n_x, wl.T.size

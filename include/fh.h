@@ -53,7 +53,10 @@ typedef enum {
 /* Precision of the frequency solves (fh_create). */
 enum {
     FH_FP64 = 0,        /* assembly, LU and solve in IEEE binary64          */
-    FH_MIXED_FP32 = 1   /* FP64 assembly; FP32 LU; FP64 iterative refinement */
+    FH_MIXED_FP32 = 1,  /* FP64 assembly; FP32 LU; FP64 iterative refinement */
+    FH_MIXED_TF32 = 2   /* FP64 assembly; LU with trailing updates on the tensor
+                           cores (tcgen05, 3xTF32 split, FP32 accumulation);
+                           FP64 iterative refinement                         */
 };
 
 /* Obstacle descriptions: smooth closed curves, counter-clockwise in t. */
@@ -78,12 +81,12 @@ typedef struct {
     int n_solves;            /* frequency solves performed (omega_j > 0)          */
     int max_N;               /* largest boundary size                             */
     long long matrix_entries;/* sum of N_j^2                                      */
-    int refine_iters_max;    /* FH_MIXED_FP32: most refinement sweeps of any solve */
-    double residual_max;     /* FH_MIXED_FP32: largest final relative residual     */
+    int refine_iters_max;    /* mixed modes: most refinement sweeps of any solve  */
+    double residual_max;     /* mixed modes: largest final relative residual      */
 } fh_solve_stats;
 
 /* Create a context on CUDA device `device` with solve precision `precision`
- * (FH_FP64 or FH_MIXED_FP32).  *out receives the context.  The context owns a
+ * (FH_FP64, FH_MIXED_FP32 or FH_MIXED_TF32).  *out receives the context.  The context owns a
  * non-blocking CUDA stream until fh_set_stream selects another one.
  * Errors: FH_EINVAL (bad precision / NULL out), FH_ECUDA (no such device). */
 fh_status fh_create(fh_ctx **out, int device, int precision);
@@ -120,7 +123,8 @@ fh_status fh_discretize(fh_ctx *ctx, const fh_curve *curve, int J, const double 
  *          for eta_j = omega_j.
  *   stats  may be NULL.
  * Errors: FH_ESTATE (no fh_discretize), FH_ESINGULAR (zero/non-finite pivot;
- * the message names the frequency), FH_ENOCONV (mixed precision only). */
+ * the message names the frequency), FH_ENOCONV (mixed precision only),
+ * FH_ETIMEOUT (a bounded tensor-core completion wait gave up). */
 fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *stats);
 
 /* Steps F1-F2 (Sec. 3.1 eq. window_func; Sec. 3.2 eqs. ak_signal_def,

@@ -88,7 +88,7 @@ struct fh_ctx {
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_solve_prob, d_order, d_curves, d_pdir;
     DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_ph, d_omega;
-    DevBuf d_A32, d_piv, d_g, d_iters, d_resid;
+    DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr;
     DevBuf d_wa, d_a;
     int n_x_last = 0;
     DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm;
@@ -116,7 +116,7 @@ struct fh_ctx {
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_ph, &d_omega, &d_A32, &d_piv, &d_g, &d_iters,
-                         &d_resid, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
+                         &d_resid, &d_tcerr, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
         for (DevBuf *b : all) free_buf(*b);
         free_problems();
@@ -596,7 +596,8 @@ extern "C" {
 fh_status fh_create(fh_ctx **out, int device, int precision) {
     if (!out) return FH_EINVAL;
     *out = nullptr;
-    if (precision != FH_FP64 && precision != FH_MIXED_FP32) return FH_EINVAL;
+    if (precision != FH_FP64 && precision != FH_MIXED_FP32 && precision != FH_MIXED_TF32)
+        return FH_EINVAL;
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
         cudaGetLastError();
@@ -663,7 +664,7 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
     ctx->solved = false;
     FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
     const fh::SolveTables t = tables(ctx);
-    const bool mixed = ctx->precision == FH_MIXED_FP32;
+    const bool mixed = ctx->precision != FH_FP64;
     {
         PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
         fh::launch_assemble_groups(t, groups(ctx), ctx->n_groups, ctx->group_tiles,
@@ -693,10 +694,20 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         PhaseScope ps(ctx, FH_PH_FACTOR, 3);
         fh::launch_convert_fp32(ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->mat_total,
                                 ctx->stream);
-        fh::launch_lu_factor_fp32(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
-                                  ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
-                                  ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
-                                  ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
+        if (ctx->precision == FH_MIXED_TF32) {
+            FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
+            FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
+            fh::launch_lu_factor_tc(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
+                                    ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
+                                    ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
+                                    ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->maxN,
+                                    ctx->stream);
+        } else {
+            fh::launch_lu_factor_fp32(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
+                                      ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
+                                      ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
+                                      ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
+        }
         fh::launch_lu_refine(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                              ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
                              ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),
@@ -725,6 +736,9 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         if (info[s] > 0)
             return fail(ctx, FH_ESINGULAR, "problem %d, frequency j=%d (omega=%.17g): zero or non-finite pivot in column %d",
                         q, j, ctx->probs[q].omega[j], info[s] - 1);
+        if (info[s] == -2)
+            return fail(ctx, FH_ETIMEOUT, "problem %d, frequency j=%d: a tensor-core completion wait gave up",
+                        q, j);
         if (info[s] < 0)
             return fail(ctx, FH_ENOCONV, "problem %d, frequency j=%d (omega=%.17g): refinement did not converge in %d sweeps (residual %.3g)",
                         q, j, ctx->probs[q].omega[j], kRefineMaxIters, resid[s]);
@@ -983,7 +997,7 @@ fh_status fh_footprint(const int *J, const int *N, int P, int precision, long lo
         for (int j = 1; j < J[q]; ++j) {
             const long long n = N[jo + j];
             b += n * n * 16 + n * (16 * 4 + 16 + 8);          // matrix, nodes, density, tables
-            if (precision == FH_MIXED_FP32) b += n * n * 8 + n * (16 + 4);   // FP32 copy, rhs, perm
+            if (precision != FH_FP64) b += n * n * 8 + n * (16 + 4);   // FP32 copy, rhs, perm
         }
         b += (long long)fh::kFarTerms * J[q] * 16 + 2LL * (J[q] - 1) * 16;
         jo += J[q];

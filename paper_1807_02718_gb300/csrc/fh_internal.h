@@ -76,6 +76,11 @@ void launch_convert_fp32(const double2 *A, float2 *A32, long long n, cudaStream_
 void launch_lu_factor_fp32(const int *order, int S, const int *N, const long long *mat_off,
                            float2 *A32, int *piv, const int *vec_off, int *info, int maxN,
                            cudaStream_t st);
+// Tensor-core variant of launch_lu_factor_fp32 (3xTF32 trailing updates on
+// tcgen05); err is set if a tensor-core completion wait gave up.
+void launch_lu_factor_tc(const int *order, int S, const int *N, const long long *mat_off,
+                         float2 *A32, int *piv, const int *vec_off, int *info, int *err, int maxN,
+                         cudaStream_t st);
 void launch_lu_refine(const int *order, int S, const int *N, const long long *mat_off,
                       const int *vec_off, const double2 *A, const float2 *LU32, const int *piv,
                       const double2 *g, double2 *x, int max_iters, double tol, int *iters,

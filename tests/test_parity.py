@@ -352,3 +352,41 @@ def test_large_config_mixed_precision():
     u64 = ref.sample(wl.x[:64], wl.T)
     assert rel(u, u64) < TOL
     assert st.refine_iters_max <= 6
+
+
+# ------------------------------------- tensor-core LU (tcgen05, 3xTF32) + FP64 IR
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_densities_tensor_core_lu(name):
+    """Trailing updates on tcgen05 with TF32 operands: after FP64 refinement
+    every density is within 1e-10 of the FP64 oracle."""
+    wl = WORKLOADS[name]()
+    pr = make(wl, F.FH_MIXED_TF32)
+    st = pr.solve()
+    assert 1 <= st.refine_iters_max <= 8
+    assert st.residual_max < 1e-12
+    psi_o = O.solve_all(wl)
+    worst = max(rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) for j in range(1, wl.J))
+    assert worst < TOL
+
+
+def test_large_config_tensor_core_lu():
+    """The benchmark workload (N = 64..480) with the tensor-core LU."""
+    wl = fi.kite_pulses(n_near=256, n_far=64)
+    pr = make(wl, F.FH_MIXED_TF32)
+    st = pr.solve()
+    psi_o = O.solve_all(wl)
+    worst = max(rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) for j in range(1, wl.J))
+    assert worst < TOL, worst
+    assert st.refine_iters_max <= 8
+
+
+def test_tensor_core_lu_large_system():
+    """One system of N = 1536 (many 128-row tiles and column-tile pairs)."""
+    wl = fi.small_kite(J=3, W=60.0)
+    wl.N = np.asarray([0, 1536, 1024], dtype=np.int32)
+    pr = make(wl, F.FH_MIXED_TF32)
+    pr.solve()
+    psi_o = O.solve_all(wl)
+    for j in (1, 2):
+        assert rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) < TOL
