@@ -265,6 +265,20 @@ def kite_pulses(J: int = 256, W: float = 40.0, n_x: int = 1024, n_near: int = 30
         x=targets_on_circle(n_x, 3.0), T=T)
 
 
+def kite_wide(J: int = 512, W: float = 160.0, n_x: int = 1024, n_near: int = 3072,
+              n_far: int = 1024, seed: int = 1, dt: float = 0.005, n_cap: int | None = None,
+              n_force: int | None = None) -> Workload:
+    """Wide-band kite problem: J frequencies on [0, W] (8 points per wavelength,
+    N up to ~1920 at W = 160; n_force scales N linearly with frequency up to
+    n_force instead), the 40-pulse train with centre frequencies U[5, 30]."""
+    wl = kite_pulses(J=J, W=W, n_x=n_x, n_near=n_near, n_far=n_far, seed=seed, dt=dt, n_cap=n_cap)
+    if n_force is not None:
+        N = np.ceil(n_force * wl.omega / W / 32.0).astype(np.int64) * 32
+        wl.N = np.maximum(N, 64).astype(np.int32)
+    wl.name = f"kite_wide_J{J}_W{int(W)}"
+    return wl
+
+
 def small_kite(J: int = 12, W: float = 6.0, n_x: int = 5, n_T: int = 37, seed: int = 3) -> Workload:
     """A tiny kite problem with ragged sizes for fast element-wise parity."""
     rng = np.random.default_rng(seed)
