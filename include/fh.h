@@ -54,9 +54,10 @@ typedef enum {
 enum {
     FH_FP64 = 0,        /* assembly, LU and solve in IEEE binary64          */
     FH_MIXED_FP32 = 1,  /* FP64 assembly; FP32 LU; FP64 iterative refinement */
-    FH_MIXED_TF32 = 2   /* FP64 assembly; LU with trailing updates on the tensor
+    FH_MIXED_TF32 = 2,  /* FP64 assembly; LU with trailing updates on the tensor
                            cores (tcgen05, 3xTF32 split, FP32 accumulation);
-                           FP64 iterative refinement                         */
+                           FP64 iterative refinement; N <= 4096              */
+    FH_MIXED_BF16 = 3   /* as FH_MIXED_TF32 with BF16 operands (3xBF16 split) */
 };
 
 /* Obstacle descriptions: smooth closed curves, counter-clockwise in t. */
@@ -86,7 +87,7 @@ typedef struct {
 } fh_solve_stats;
 
 /* Create a context on CUDA device `device` with solve precision `precision`
- * (FH_FP64, FH_MIXED_FP32 or FH_MIXED_TF32).  *out receives the context.  The context owns a
+ * (FH_FP64, FH_MIXED_FP32, FH_MIXED_TF32 or FH_MIXED_BF16).  *out receives the context.  The context owns a
  * non-blocking CUDA stream until fh_set_stream selects another one.
  * Errors: FH_EINVAL (bad precision / NULL out), FH_ECUDA (no such device). */
 fh_status fh_create(fh_ctx **out, int device, int precision);

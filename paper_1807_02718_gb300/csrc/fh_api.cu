@@ -88,7 +88,8 @@ struct fh_ctx {
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_solve_prob, d_order, d_curves, d_pdir;
     DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_ph, d_omega;
-    DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr;
+    DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk;
+    int n_rchunk = 0;
     DevBuf d_wa, d_a;
     int n_x_last = 0;
     DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm;
@@ -116,7 +117,7 @@ struct fh_ctx {
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_ph, &d_omega, &d_A32, &d_piv, &d_g, &d_iters,
-                         &d_resid, &d_tcerr, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
+                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
         for (DevBuf *b : all) free_buf(*b);
         free_problems();
@@ -410,6 +411,12 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     std::stable_sort(ctx->order.begin(), ctx->order.end(),
                      [&](int a, int b) { return ctx->solve_N[a] > ctx->solve_N[b]; });
 
+    std::vector<int2> rchunk;   // (solve, first row) of each refinement residual chunk
+    for (int s = 0; s < S; ++s)
+        for (int r0 = 0; r0 < ctx->solve_N[s]; r0 += fh::kResidRows) rchunk.push_back(make_int2(s, r0));
+    ctx->n_rchunk = (int)rchunk.size();
+    FH_TRY(upload(ctx, ctx->d_rchunk, rchunk));
+
     std::vector<double> omega_v(omega_all, omega_all + jo);
     FH_TRY(upload(ctx, ctx->d_N, ctx->solve_N));
     FH_TRY(upload(ctx, ctx->d_mat_off, ctx->mat_off));
@@ -596,7 +603,8 @@ extern "C" {
 fh_status fh_create(fh_ctx **out, int device, int precision) {
     if (!out) return FH_EINVAL;
     *out = nullptr;
-    if (precision != FH_FP64 && precision != FH_MIXED_FP32 && precision != FH_MIXED_TF32)
+    if (precision != FH_FP64 && precision != FH_MIXED_FP32 && precision != FH_MIXED_TF32 &&
+        precision != FH_MIXED_BF16)
         return FH_EINVAL;
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
@@ -687,33 +695,45 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
                                  ctx->d_info.as<int>(), ctx->stream);
         FH_TRY(check_launch(ctx, "lu fp64"));
     } else {
+        const bool tc = ctx->precision == FH_MIXED_TF32 || ctx->precision == FH_MIXED_BF16;
+        if (tc && ctx->maxN > fh::kTcMaxN)
+            return fail(ctx, FH_EINVAL, "tensor-core LU supports N <= %d (largest N is %d)",
+                        fh::kTcMaxN, ctx->maxN);
         FH_TRY(ensure(ctx, ctx->d_A32, (size_t)ctx->mat_total * sizeof(float2)));
         FH_TRY(ensure(ctx, ctx->d_piv, (size_t)ctx->vec_total * sizeof(int)));
         FH_TRY(ensure(ctx, ctx->d_iters, (size_t)ctx->S * sizeof(int)));
         FH_TRY(ensure(ctx, ctx->d_resid, (size_t)ctx->S * sizeof(double)));
+        FH_TRY(ensure(ctx, ctx->d_y32, (size_t)ctx->vec_total * sizeof(float2)));
+        FH_TRY(ensure(ctx, ctx->d_rstate, fh::refine_state_bytes(ctx->S)));
         PhaseScope ps(ctx, FH_PH_FACTOR, 3);
-        fh::launch_convert_fp32(ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->mat_total,
-                                ctx->stream);
-        if (ctx->precision == FH_MIXED_TF32) {
+        if (tc) {
             FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
             FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
-            fh::launch_lu_factor_tc(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
-                                    ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
-                                    ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
-                                    ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->maxN,
-                                    ctx->stream);
+            fh::launch_convert_rowmajor(ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
+                                        ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->stream);
+            const cudaError_t e = fh::launch_lu_factor_tc(
+                ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->d_order.as<int>(), ctx->order.data(),
+                ctx->solve_N.data(), ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
+                ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
+                ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->stream);
+            if (e != cudaSuccess)
+                return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
         } else {
+            fh::launch_convert_fp32(ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->mat_total,
+                                    ctx->stream);
             fh::launch_lu_factor_fp32(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                                       ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
                                       ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
                                       ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
         }
-        fh::launch_lu_refine(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
+        fh::launch_lu_refine(tc, ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                              ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
-                             ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),
-                             ctx->d_g.as<double2>(), ctx->d_psi.as<double2>(), kRefineMaxIters,
-                             kRefineTol, ctx->d_iters.as<int>(), ctx->d_resid.as<double>(),
-                             ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
+                             ctx->d_rchunk.as<int2>(), ctx->n_rchunk, ctx->d_A.as<double2>(),
+                             ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_g.as<double2>(),
+                             ctx->d_psi.as<double2>(), ctx->d_y32.as<float2>(), ctx->d_rstate.p,
+                             kRefineMaxIters, kRefineTol, ctx->d_iters.as<int>(),
+                             ctx->d_resid.as<double>(), ctx->d_info.as<int>(), ctx->maxN,
+                             ctx->stream);
         FH_TRY(check_launch(ctx, "lu mixed"));
     }
     int iters_max = 0;
@@ -997,7 +1017,7 @@ fh_status fh_footprint(const int *J, const int *N, int P, int precision, long lo
         for (int j = 1; j < J[q]; ++j) {
             const long long n = N[jo + j];
             b += n * n * 16 + n * (16 * 4 + 16 + 8);          // matrix, nodes, density, tables
-            if (precision != FH_FP64) b += n * n * 8 + n * (16 + 4);   // FP32 copy, rhs, perm
+            if (precision != FH_FP64) b += n * n * 8 + n * (16 + 4 + 8);   // FP32 copy, rhs, perm, FP32 rhs
         }
         b += (long long)fh::kFarTerms * J[q] * 16 + 2LL * (J[q] - 1) * 16;
         jo += J[q];

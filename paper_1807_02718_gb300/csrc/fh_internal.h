@@ -76,15 +76,27 @@ void launch_convert_fp32(const double2 *A, float2 *A32, long long n, cudaStream_
 void launch_lu_factor_fp32(const int *order, int S, const int *N, const long long *mat_off,
                            float2 *A32, int *piv, const int *vec_off, int *info, int maxN,
                            cudaStream_t st);
-// Tensor-core variant of launch_lu_factor_fp32 (3xTF32 trailing updates on
-// tcgen05); err is set if a tensor-core completion wait gave up.
-void launch_lu_factor_tc(const int *order, int S, const int *N, const long long *mat_off,
-                         float2 *A32, int *piv, const int *vec_off, int *info, int *err, int maxN,
-                         cudaStream_t st);
-void launch_lu_refine(const int *order, int S, const int *N, const long long *mat_off,
-                      const int *vec_off, const double2 *A, const float2 *LU32, const int *piv,
-                      const double2 *g, double2 *x, int max_iters, double tol, int *iters,
-                      double *resid, int *info, int maxN, cudaStream_t st);
+// Tensor-core LU of the row-major FP32 copy (launch_convert_rowmajor); kind 2:
+// 3xTF32 operands, kind 1: 3xBF16.  order_h / N_h: host copies of order (by
+// decreasing N) and N, used to launch each cluster size (1, 2, 4, 8 CTAs for
+// N <= 512, 1024, 2048, 4096) separately.  err is set and info[s] = -2 if a
+// tensor-core completion wait gave up.
+constexpr int kTcMaxN = 4096;
+void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const double2 *A,
+                             float2 *A32, cudaStream_t st);
+cudaError_t launch_lu_factor_tc(int kind, const int *order, const int *order_h, const int *N_h, int S,
+                                const int *N, const long long *mat_off, float2 *A32, int *piv,
+                                const int *vec_off, int *info, int *err, cudaStream_t st);
+// FP64 iterative refinement against the column-major FP64 matrices; chunks
+// lists (solve, first row) per kResidRows rows; state holds
+// refine_state_bytes(S) bytes; y32 one FP32 complex per unknown.
+constexpr int kResidRows = 64;
+size_t refine_state_bytes(int S);
+void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
+                      const long long *mat_off, const int *vec_off, const int2 *chunks,
+                      int n_chunks, const double2 *A, const float2 *LU32, const int *piv,
+                      const double2 *g, double2 *x, float2 *y32, void *state, int max_iters,
+                      double tol, int *iters, double *resid, int *info, int maxN, cudaStream_t st);
 
 // ---- window spectra (k_window.cu) ----
 void launch_window_spectra(const double *a, int n_samples, long long start0, long long step,

@@ -7,13 +7,18 @@
 // correction is below tol * ||x||_inf (max-norms), or fails with FH_ENOCONV
 // after max_iters sweeps.
 //
-// Kernels (one CTA per frequency, largest systems first):
+// Kernels (largest systems first):
 //   lu_factor_fp32_kernel  blocked right-looking LU (panel width 32) of the
-//                          column-major complex64 copy, pivots stored;
-//   refine_kernel          x = 0, r = g; repeat { d = (LU)^-1 P r in FP32;
-//                          x += d; r = g - A x in FP64 } with blocked
-//                          triangular solves (32-wide diagonal blocks solved
-//                          by one warp, off-diagonal updates by the CTA).
+//                          column-major complex64 copy, one CTA per system;
+//   refine_*               x = 0, y = P g; per sweep: refine_solve_kernel
+//                          (d = (LU)^-1 y in FP32, x += d; one CTA per
+//                          system; 32-wide diagonal blocks solved by one warp,
+//                          off-diagonal updates by the CTA), then
+//                          refine_resid_kernel (y = P (g - A x) in FP64, 64
+//                          rows per CTA so the FP64 work of a sweep spreads
+//                          over all SMs).  A system that has converged skips
+//                          the remaining sweeps.  The factors may be
+//                          column-major (SIMT LU) or row-major (tensor-core LU).
 #include "fh_internal.h"
 
 namespace fh {
@@ -196,9 +201,10 @@ __global__ void __launch_bounds__(256) lu_factor_fp32_kernel(
 // registers (lane i holds row i of the block), so the warp's dependent chain
 // runs on shuffles only; the rest of the CTA then applies the block to the
 // remaining rows.
+template <bool kRowMajor>
 __device__ void lu_solve_shared(const float2 *__restrict__ a, int n, float2 *y) {
     const int tid = threadIdx.x, lane = tid & 31;
-#define AT(i, j) a[(long long)(j) * n + (i)]
+#define AT(i, j) (kRowMajor ? a[(long long)(i) * n + (j)] : a[(long long)(j) * n + (i)])
     for (int jb = 0; jb < n; jb += 32) {
         const int je = min(jb + 32, n);
         if (tid < 32) {
@@ -281,74 +287,135 @@ __device__ double block_max(double v, double *red) {
     return r;
 }
 
-__global__ void __launch_bounds__(256) refine_kernel(
-    const int *__restrict__ order, const int *__restrict__ Ns,
-    const long long *__restrict__ mat_off, const int *__restrict__ vec_off,
-    const double2 *__restrict__ A, const float2 *__restrict__ LU32, const int *__restrict__ piv,
-    const double2 *__restrict__ G, double2 *__restrict__ X, int max_iters, double tol,
-    int *__restrict__ iters, double *__restrict__ resid, int *__restrict__ info) {
-    extern __shared__ double2 sh[];
-    const int s = order[blockIdx.x];
-    if (info[s] != 0) return;
-    const int n = Ns[s];
-    double2 *xs = sh;                                   // n FP64 complex
-    float2 *ys = reinterpret_cast<float2 *>(sh + n);    // n FP32 complex
+// Refinement state of one system.
+struct RefineState {
+    double gmax, dmax, xmax;
+    unsigned long long rbits;     // max_i |r_i|_1 as the bits of a non-negative double
+    int conv, pad;
+};
+
+// x = 0, y = P g (FP32), ||g||.
+__global__ void __launch_bounds__(256) refine_setup_kernel(
+    const int *__restrict__ Ns, const int *__restrict__ vec_off, const int *__restrict__ piv,
+    const double2 *__restrict__ G, double2 *__restrict__ X, float2 *__restrict__ Y32,
+    RefineState *__restrict__ st, int *__restrict__ iters, const int *__restrict__ info) {
     __shared__ double red[8];
-    const double2 *a = A + mat_off[s];
-    const float2 *lu = LU32 + mat_off[s];
-    const int *pv = piv + vec_off[s];
-    const double2 *g = G + vec_off[s];
-    double2 *x = X + vec_off[s];
-    const int tid = threadIdx.x;
+    const int s = blockIdx.x, n = Ns[s], vo = vec_off[s];
     double gmax = 0.0;
-    for (int i = tid; i < n; i += blockDim.x) {
-        const double2 gi = g[i];
-        xs[i] = make_double2(0.0, 0.0);
-        ys[pv[i]] = make_float2((float)gi.x, (float)gi.y);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double2 gi = G[vo + i];
+        X[vo + i] = make_double2(0.0, 0.0);
+        Y32[vo + piv[vo + i]] = make_float2((float)gi.x, (float)gi.y);
         gmax = fmax(gmax, fabs(gi.x) + fabs(gi.y));
     }
     gmax = block_max(gmax, red);
-    int it = 0;
-    bool done = false;
-    double rmax = gmax;
-    while (it < max_iters && !done) {
-        __syncthreads();
-        lu_solve_shared(lu, n, ys);
-        double dmax = 0.0, xmax = 0.0;
-        for (int i = tid; i < n; i += blockDim.x) {
-            const float2 d = ys[i];
-            double2 xi = xs[i];
-            xi.x += (double)d.x;
-            xi.y += (double)d.y;
-            xs[i] = xi;
-            dmax = fmax(dmax, fabs((double)d.x) + fabs((double)d.y));
-            xmax = fmax(xmax, fabs(xi.x) + fabs(xi.y));
-        }
-        dmax = block_max(dmax, red);
-        xmax = block_max(xmax, red);
-        ++it;
-        // r = g - A x (FP64), rows over threads, columns in order
-        double rloc = 0.0;
-        for (int i = tid; i < n; i += blockDim.x) {
-            double rr = g[i].x, ri = g[i].y;
-            for (int l = 0; l < n; ++l) {
-                const double2 al = a[(long long)l * n + i];
-                const double2 xl = xs[l];
-                rr -= al.x * xl.x - al.y * xl.y;
-                ri -= al.x * xl.y + al.y * xl.x;
-            }
-            ys[pv[i]] = make_float2((float)rr, (float)ri);
-            rloc = fmax(rloc, fabs(rr) + fabs(ri));
-        }
-        rmax = block_max(rloc, red);
-        done = !(dmax > tol * xmax) || rmax == 0.0;
+    if (threadIdx.x == 0) {
+        RefineState r;
+        r.gmax = gmax;
+        r.dmax = r.xmax = 0.0;
+        r.rbits = 0ull;
+        r.conv = info[s] != 0;
+        r.pad = 0;
+        st[s] = r;
+        iters[s] = 0;
     }
-    for (int i = tid; i < n; i += blockDim.x) x[i] = xs[i];
-    if (tid == 0) {
+}
+
+// Sweep `it`: stop if sweep it-1 converged; else d = (LU)^{-1} y, x += d.
+template <bool kRowMajor>
+__global__ void __launch_bounds__(256) refine_solve_kernel(
+    const int *__restrict__ order, const int *__restrict__ Ns, const long long *__restrict__ mat_off,
+    const int *__restrict__ vec_off, const float2 *__restrict__ LU32, double2 *__restrict__ X,
+    const float2 *__restrict__ Y32, RefineState *__restrict__ st, int it, double tol,
+    int *__restrict__ iters) {
+    extern __shared__ float2 ys[];
+    __shared__ double red[8];
+    const int s = order[blockIdx.x];
+    RefineState *rs = st + s;
+    if (rs->conv) return;
+    if (it > 1 && (!(rs->dmax > tol * rs->xmax) || rs->rbits == 0ull)) {
+        if (threadIdx.x == 0) rs->conv = 1;
+        return;
+    }
+    const int n = Ns[s], vo = vec_off[s];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = Y32[vo + i];
+    __syncthreads();
+    lu_solve_shared<kRowMajor>(LU32 + mat_off[s], n, ys);
+    double dmax = 0.0, xmax = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 d = ys[i];
+        double2 xi = X[vo + i];
+        xi.x += (double)d.x;
+        xi.y += (double)d.y;
+        X[vo + i] = xi;
+        dmax = fmax(dmax, fabs((double)d.x) + fabs((double)d.y));
+        xmax = fmax(xmax, fabs(xi.x) + fabs(xi.y));
+    }
+    dmax = block_max(dmax, red);
+    xmax = block_max(xmax, red);
+    if (threadIdx.x == 0) {
+        rs->dmax = dmax;
+        rs->xmax = xmax;
+        rs->rbits = 0ull;
         iters[s] = it;
-        resid[s] = gmax > 0.0 ? rmax / gmax : 0.0;
-        if (!done) info[s] = -1;
     }
+}
+
+
+
+// r = g - A x in FP64 for 64 rows of one system (A column-major); y = P r.
+// Four column phases per row, summed in a fixed order.
+__global__ void __launch_bounds__(256) refine_resid_kernel(
+    const int2 *__restrict__ chunks, const int *__restrict__ Ns, const long long *__restrict__ mat_off,
+    const int *__restrict__ vec_off, const double2 *__restrict__ A, const int *__restrict__ piv,
+    const double2 *__restrict__ G, const double2 *__restrict__ X, float2 *__restrict__ Y32,
+    RefineState *__restrict__ st) {
+    extern __shared__ double2 xs[];
+    __shared__ double2 part[4][kResidRows];
+    __shared__ double red[8];
+    const int2 ch = chunks[blockIdx.x];
+    const int s = ch.x, r0 = ch.y;
+    if (st[s].conv) return;
+    const int n = Ns[s], vo = vec_off[s];
+    const double2 *a = A + mat_off[s];
+    for (int l = threadIdx.x; l < n; l += blockDim.x) xs[l] = X[vo + l];
+    __syncthreads();
+    const int ri = threadIdx.x & (kResidRows - 1), ph = threadIdx.x / kResidRows, i = r0 + ri;
+    double rr = 0.0, rim = 0.0;
+    if (i < n)
+        for (int l = ph; l < n; l += 4) {
+            const double2 al = a[(long long)l * n + i];
+            const double2 xl = xs[l];
+            rr = fma(al.x, xl.x, rr);
+            rr = fma(-al.y, xl.y, rr);
+            rim = fma(al.x, xl.y, rim);
+            rim = fma(al.y, xl.x, rim);
+        }
+    part[ph][ri] = make_double2(rr, rim);
+    __syncthreads();
+    double m = 0.0;
+    if (ph == 0 && i < n) {
+        const double2 gi = G[vo + i];
+        const double sr = ((part[0][ri].x + part[1][ri].x) + part[2][ri].x) + part[3][ri].x;
+        const double si = ((part[0][ri].y + part[1][ri].y) + part[2][ri].y) + part[3][ri].y;
+        const double r_re = gi.x - sr, r_im = gi.y - si;
+        Y32[vo + piv[vo + i]] = make_float2((float)r_re, (float)r_im);
+        m = fabs(r_re) + fabs(r_im);
+    }
+    m = block_max(m, red);
+    if (threadIdx.x == 0 && m > 0.0)
+        atomicMax(&st[s].rbits, (unsigned long long)__double_as_longlong(m));
+}
+
+// After the last sweep: convergence verdict and relative residual.
+__global__ void refine_final_kernel(int S, const RefineState *__restrict__ st, double tol,
+                                    double *__restrict__ resid, int *__restrict__ info) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || info[s] != 0) return;
+    const RefineState r = st[s];
+    const double rmax = __longlong_as_double((long long)r.rbits);
+    if (!r.conv && r.dmax > tol * r.xmax && r.rbits != 0ull) info[s] = -1;
+    resid[s] = r.gmax > 0.0 ? rmax / r.gmax : 0.0;
 }
 
 __global__ void convert_kernel(const double2 *__restrict__ A, float2 *__restrict__ B, long long n) {
@@ -379,19 +446,34 @@ void launch_lu_factor_fp32(const int *order, int S, const int *N, const long lon
                                                               info);
 }
 
-void launch_lu_refine(const int *order, int S, const int *N, const long long *mat_off,
-                      const int *vec_off, const double2 *A, const float2 *LU32, const int *piv,
-                      const double2 *g, double2 *x, int max_iters, double tol, int *iters,
-                      double *resid, int *info, int maxN, cudaStream_t st) {
+size_t refine_state_bytes(int S) { return (size_t)S * sizeof(RefineState); }
+
+void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
+                      const long long *mat_off, const int *vec_off, const int2 *chunks,
+                      int n_chunks, const double2 *A, const float2 *LU32, const int *piv,
+                      const double2 *g, double2 *x, float2 *y32, void *state, int max_iters,
+                      double tol, int *iters, double *resid, int *info, int maxN, cudaStream_t st) {
     if (S <= 0) return;
-    const size_t smem = (size_t)maxN * (sizeof(double2) + sizeof(float2));
+    RefineState *rs = static_cast<RefineState *>(state);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(refine_resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(refine_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(refine_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    refine_kernel<<<S, 256, smem, st>>>(order, N, mat_off, vec_off, A, LU32, piv, g, x, max_iters,
-                                        tol, iters, resid, info);
+    refine_setup_kernel<<<S, 256, 0, st>>>(N, vec_off, piv, g, x, y32, rs, iters, info);
+    for (int it = 1; it <= max_iters; ++it) {
+        if (row_major)
+            refine_solve_kernel<true><<<S, 256, (size_t)maxN * sizeof(float2), st>>>(
+                order, N, mat_off, vec_off, LU32, x, y32, rs, it, tol, iters);
+        else
+            refine_solve_kernel<false><<<S, 256, (size_t)maxN * sizeof(float2), st>>>(
+                order, N, mat_off, vec_off, LU32, x, y32, rs, it, tol, iters);
+        refine_resid_kernel<<<n_chunks, 256, (size_t)maxN * sizeof(double2), st>>>(
+            chunks, N, mat_off, vec_off, A, piv, g, x, y32, rs);
+    }
+    refine_final_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, rs, tol, resid, info);
 }
 
 }  // namespace fh

@@ -17,7 +17,7 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfh.so")
 
 FH_OK, FH_EINVAL, FH_ENOMEM, FH_ECUDA, FH_ESTATE, FH_ESINGULAR, FH_ENOCONV, FH_ETIMEOUT = range(8)
-FH_FP64, FH_MIXED_FP32, FH_MIXED_TF32 = 0, 1, 2
+FH_FP64, FH_MIXED_FP32, FH_MIXED_TF32, FH_MIXED_BF16 = 0, 1, 2, 3
 FH_CURVE_CIRCLE, FH_CURVE_KITE, FH_CURVE_STAR = 0, 1, 2
 FH_MAX_HARMONICS = 16
 
