@@ -16,7 +16,7 @@ oracle timed on the host cores, and SM clocks sampled during the timed
 region.  L2 is flushed (256 MiB write) between timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--precision fp64|mixed]
+                    [--precision fp64|mixed|tf32|bf16]
 """
 from __future__ import annotations
 
@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tf32"])
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "mixed", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -217,7 +217,8 @@ def run_gpu(args, world, rank, local):
 
     build.build()
     torch.cuda.set_device(local)
-    prec = {"fp64": F.FH_FP64, "mixed": F.FH_MIXED_FP32, "tf32": F.FH_MIXED_TF32}[args.precision]
+    prec = {"fp64": F.FH_FP64, "mixed": F.FH_MIXED_FP32, "tf32": F.FH_MIXED_TF32,
+            "bf16": F.FH_MIXED_BF16}[args.precision]
     wl = fi.kite_pulses()
     S = wl.J - 1
     n_x, n_T = wl.n_x, wl.T.size

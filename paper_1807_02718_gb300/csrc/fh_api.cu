@@ -87,7 +87,7 @@ struct fh_ctx {
     DevBuf d_sg, d_sg_tile_off, d_sg_dk, d_tmp_sg, d_items, d_item_first, d_part;
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_solve_prob, d_order, d_curves, d_pdir;
-    DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_ph, d_omega;
+    DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_nu_f, d_ph, d_omega, d_pw;
     DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk;
     int n_rchunk = 0;
     DevBuf d_wa, d_a;
@@ -116,7 +116,7 @@ struct fh_ctx {
                          &d_part, &d_N, &d_mat_off, &d_vec_off, &d_tab, &d_tab_off, &d_tab_N,
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
-                         &d_info, &d_nu, &d_ph, &d_omega, &d_A32, &d_piv, &d_g, &d_iters,
+                         &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_A32, &d_piv, &d_g, &d_iters,
                          &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
         for (DevBuf *b : all) free_buf(*b);
@@ -445,10 +445,13 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     FH_TRY(ensure(ctx, ctx->d_logsin, (size_t)tb * sizeof(double)));
     FH_TRY(ensure(ctx, ctx->d_A, (size_t)mo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_info, (size_t)S * sizeof(int)));
-    FH_TRY(ensure(ctx, ctx->d_nu, (size_t)nu_off * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_nu_f, (size_t)nu_off * sizeof(float4)));
     FH_TRY(ensure(ctx, ctx->d_ph, (size_t)ph_off * sizeof(double2)));
 
-    PhaseScope ps_(ctx, FH_PH_GEOMETRY, 2 + P);
+    int maxM = 0;
+    for (const Problem &pb : ctx->probs) maxM = std::max(maxM, pb.M);
+    FH_TRY(ensure(ctx, ctx->d_pw, (size_t)maxM * fh::kFarTerms * sizeof(double)));
+    PhaseScope ps_(ctx, FH_PH_GEOMETRY, 2 + 2 * P);
     fh::launch_geometry(ctx->d_curves.as<fh::CurveParams>(), ctx->d_solve_prob.as<int>(), S, maxN,
                         ctx->d_N.as<int>(), ctx->d_vec_off.as<int>(), ctx->d_z.as<double2>(),
                         ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(), ctx->stream);
@@ -457,7 +460,8 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
                             ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(), ctx->stream);
     FH_TRY(check_launch(ctx, "kress tables"));
     for (Problem &pb : ctx->probs) {
-        fh::launch_far_table(pb.J, pb.M, ctx->d_nu.as<double2>() + pb.nu_off,
+        fh::launch_far_table(pb.J, pb.M, ctx->d_pw.as<double>(), nullptr,
+                             ctx->d_nu_f.as<float4>() + pb.nu_off,
                              ctx->d_ph.as<double2>() + pb.ph_off, ctx->stream);
         FH_TRY(check_launch(ctx, "far table"));
     }
@@ -520,14 +524,14 @@ fh_status synth_common(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int
     {
         PhaseScope ps(ctx, FH_PH_WEIGHTS, 1);
         fh::launch_synth_weights(pb.J, pb.M, pb.W, pb.K, pb.d_s.as<double>(), pb.d_B.as<double2>(),
-                                 ctx->d_nu.as<double2>() + pb.nu_off,
+                                 ctx->d_nu_f.as<float4>() + pb.nu_off,
                                  ctx->d_ph.as<double2>() + pb.ph_off, d_T, n_T,
                                  ctx->d_Gr.as<double>(), ctx->d_Gm.as<double>(), ctx->stream);
         FH_TRY(check_launch(ctx, "synthesis weights"));
     }
     PhaseScope ps(ctx, FH_PH_CONTRACT, 1);
     fh::launch_synth_contract(pb.J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Gr.as<double>(),
-                              ctx->d_Gm.as<double>(), d_u, ctx->stream);
+                              ctx->d_Gm.as<double>(), d_u, ctx->precision != FH_FP64, ctx->stream);
     return check_launch(ctx, "synthesis contraction");
 }
 
@@ -705,7 +709,10 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         FH_TRY(ensure(ctx, ctx->d_resid, (size_t)ctx->S * sizeof(double)));
         FH_TRY(ensure(ctx, ctx->d_y32, (size_t)ctx->vec_total * sizeof(float2)));
         FH_TRY(ensure(ctx, ctx->d_rstate, fh::refine_state_bytes(ctx->S)));
-        PhaseScope ps(ctx, FH_PH_FACTOR, 3);
+        // launches: conversion, one LU launch per cluster size (SIMT: one), and
+        // the refinement's set-up, two kernels per sweep and the verdict
+        PhaseScope ps(ctx, FH_PH_FACTOR, 1 + (tc ? fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S) : 1) +
+                                             2 + 2 * kRefineMaxIters);
         if (tc) {
             FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
             FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));

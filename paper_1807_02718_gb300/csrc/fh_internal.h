@@ -82,6 +82,7 @@ void launch_lu_factor_fp32(const int *order, int S, const int *N, const long lon
 // N <= 512, 1024, 2048, 4096) separately.  err is set and info[s] = -2 if a
 // tensor-core completion wait gave up.
 constexpr int kTcMaxN = 4096;
+int lu_tc_launches(const int *order_h, const int *N_h, int S);
 void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const double2 *A,
                              float2 *A32, cudaStream_t st);
 cudaError_t launch_lu_factor_tc(int kind, const int *order, const int *order_h, const int *N_h, int S,
@@ -122,14 +123,19 @@ void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, 
 void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st);
 
 // ---- synthesis (k_synth.cu) ----
-// nu[p * R + r] = sum_{m=-h}^{h-1} (-1)^m (m/h)^r e^{-2 pi i m p / M}.
+// nu[r * J + p] = sum_{m=-h}^{h-1} (-1)^m (m/h)^r e^{-2 pi i m p / M} (nu may
+// be null), and nu_f the same as double-float pairs (re hi, re lo, im hi,
+// im lo); pw is scratch of M * kFarTerms doubles.
 constexpr int kFarTerms = 170;
-void launch_far_table(int J, int M, double2 *nu, double2 *phase_tab, cudaStream_t st);
+void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, double2 *phase_tab,
+                      cudaStream_t st);
 // Gr/Gm: planes [p][t] with u(x,t) = sum_p Vr[p][x] Gr[p][t] + Vi[p][x] Gm[p][t].
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
-                          const double2 *nu, const double2 *phase_tab, const double *T,
+                          const float4 *nu_f, const double2 *phase_tab, const double *T,
                           int n_T, double *Gr, double *Gm, cudaStream_t st);
+// double_float: operands split into FP32 pairs, products exact, double-float
+// accumulation (mixed-precision paths); else FP64 FMAs.
 void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,
-                           const double *Gm, double *u, cudaStream_t st);
+                           const double *Gm, double *u, bool double_float, cudaStream_t st);
 
 }  // namespace fh

@@ -16,9 +16,10 @@ namespace {
 
 // Scratch capacity: J * n_T <= kMaxGridPoints, J <= kMaxJ.
 constexpr long long kMaxGridPoints = 1LL << 19;     // G planes: 2 x 8 B x 2^19 = 8 MiB
+static_assert(2 * kMaxGridPoints >= 2LL * 2048 * fh::kFarTerms, "power table fits in the G planes");
 constexpr int kMaxJ = 2049;                         // M = 2(J-1) <= 4096
 constexpr size_t kScratchDoubles = 2 * (size_t)kMaxGridPoints   // Gr, Gm
-                                   + 2 * (size_t)fh::kFarTerms * kMaxJ   // far-field table
+                                   + 2 * (size_t)fh::kFarTerms * kMaxJ   // far-field table (double-float)
                                    + 2 * (size_t)(2 * (kMaxJ - 1));      // phase table
 
 // Every GPU that loads the library holds this array until the process exits.
@@ -66,12 +67,13 @@ extern "C" fh_status fh_synthesize_static(int J, double W, int K, const double *
     const int M = 2 * (J - 1);
     double *Gr = scratch;
     double *Gm = Gr + (size_t)J * n_T;
-    double2 *nu = reinterpret_cast<double2 *>(scratch + 2 * (size_t)kMaxGridPoints);
-    double2 *ph = nu + (size_t)fh::kFarTerms * kMaxJ;
-    fh::launch_far_table(J, M, nu, ph, stream);
-    fh::launch_synth_weights(J, M, W, K, d_s, reinterpret_cast<const double2 *>(d_B), nu, ph, d_T,
+    double *pw = scratch;   // power table of the far-field table; G is written after it is used
+    float4 *nu_f = reinterpret_cast<float4 *>(scratch + 2 * (size_t)kMaxGridPoints);
+    double2 *ph = reinterpret_cast<double2 *>(nu_f + (size_t)fh::kFarTerms * kMaxJ);
+    fh::launch_far_table(J, M, pw, nullptr, nu_f, ph, stream);
+    fh::launch_synth_weights(J, M, W, K, d_s, reinterpret_cast<const double2 *>(d_B), nu_f, ph, d_T,
                              n_T, Gr, Gm, stream);
     fh::launch_synth_contract(J, n_x, n_T, reinterpret_cast<const double2 *>(d_V), Gr, Gm, d_u,
-                              stream);
+                              false, stream);
     return cudaGetLastError() == cudaSuccess ? FH_OK : FH_ECUDA;
 }

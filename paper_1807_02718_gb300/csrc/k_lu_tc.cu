@@ -615,6 +615,13 @@ int cluster_for(int n) { return n <= 512 ? 1 : n <= 1024 ? 2 : n <= 2048 ? 4 : 8
 
 }  // namespace
 
+int lu_tc_launches(const int *order_h, const int *N_h, int S) {
+    int count = 0;
+    for (int i = 0; i < S; ++i)
+        if (i == 0 || cluster_for(N_h[order_h[i]]) != cluster_for(N_h[order_h[i - 1]])) ++count;
+    return count;
+}
+
 void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const double2 *A,
                              float2 *A32, cudaStream_t st) {
     if (S <= 0) return;

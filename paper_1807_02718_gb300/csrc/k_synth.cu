@@ -19,28 +19,33 @@
 // expansion 1/(y - m) = (1/y) sum_r (m/y)^r:
 //   D_p = (2W/M) sin(pi y)/(pi y) sum_r (h/y)^r nu_{p,r},
 //   nu_{p,r} = sum_m (-1)^m (m/h)^r e^{-2 pi i m p / M},
-// truncated once (h/|y|)^r < 2^-54; near windows sum the M terms directly.
+// truncated once (h/|y|)^r < 2^-48 and summed in double-float arithmetic;
+// near windows sum the M terms directly (double-float accumulation).
 #include "fh_internal.h"
 
 namespace fh {
 namespace {
 
-// One CTA per p: phases e^{-2 pi i m p / M} (-1)^m for a chunk of m are staged
-// in shared memory; thread r accumulates sum_m phase_m (m/h)^r, the power by
-// binary exponentiation.
-__device__ __forceinline__ double ipow(double x, int r) {
-    double y = 1.0;
-    while (r) {
-        if (r & 1) y *= x;
-        x *= x;
-        r >>= 1;
+// nu_{p,r} as a contraction: pw[m + h][r] = (m/h)^r (successive products,
+// one thread per m), then one CTA per p stages the phases
+// e^{-2 pi i m p / M} (-1)^m of a chunk of m in shared memory and thread r
+// accumulates sum_m phase_m pw[m + h][r].
+__global__ void far_powers_kernel(int M, double *__restrict__ pw) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= M) return;
+    const int h = M / 2;
+    const double xv = (double)(q - h) / (double)h;
+    double v = 1.0;
+    for (int r = 0; r < kFarTerms; ++r) {
+        pw[(long long)q * kFarTerms + r] = v;
+        v *= xv;
     }
-    return y;
 }
 
-constexpr int kFarChunk = 256;
+constexpr int kFarChunk = 128;
 
-__global__ void __launch_bounds__(256) far_table_kernel(int J, int M, double2 *__restrict__ nu,
+__global__ void __launch_bounds__(192) far_table_kernel(int J, int M, const double *__restrict__ pw,
+                                                       double2 *__restrict__ nu, float4 *__restrict__ nu_f,
                                                        double2 *__restrict__ ph) {
     const int p = blockIdx.x;
     const int r = threadIdx.x;
@@ -71,14 +76,19 @@ __global__ void __launch_bounds__(256) far_table_kernel(int J, int M, double2 *_
         __syncthreads();
         if (r < kFarTerms) {
             const int me = min(kFarChunk, h - m0);
+            const double *col = pw + (long long)(m0 + h) * kFarTerms + r;
             for (int e = 0; e < me; ++e) {
-                const double pw = ipow((double)(m0 + e) / (double)h, r);
-                sr = fma(pw, phs[e].x, sr);
-                si = fma(pw, phs[e].y, si);
+                const double w = col[(long long)e * kFarTerms];
+                sr = fma(w, phs[e].x, sr);
+                si = fma(w, phs[e].y, si);
             }
         }
     }
-    if (r < kFarTerms) nu[(long long)r * J + p] = make_double2(sr, si);
+    if (r < kFarTerms) {
+        if (nu) nu[(long long)r * J + p] = make_double2(sr, si);
+        const float rh = (float)sr, ih = (float)si;   // double-float copy for the far Horner
+        nu_f[(long long)r * J + p] = make_float4(rh, (float)(sr - (double)rh), ih, (float)(si - (double)ih));
+    }
 }
 
 // Double-float (FP32 pair) arithmetic for the near-window sums: FP32 runs at
@@ -105,35 +115,78 @@ __device__ __forceinline__ void df_mac(float &sh, float &sl, dfl a, dfl b) {
     sh = t;
 }
 
+// a * r + v in double-float (r, v double-float; a updated)
+__device__ __forceinline__ void df_horner(float &ah, float &al, dfl r, float vh, float vl) {
+    const float p = ah * r.hi;
+    float e = fmaf(ah, r.hi, -p);
+    e = fmaf(ah, r.lo, e);
+    e = fmaf(al, r.hi, e);
+    const float s = p + vh;
+    const float bb = s - p;
+    float err = (p - (s - bb)) + (vh - bb);
+    err += e + vl;
+    ah = s + err;
+    al = err - (ah - s);
+}
+
+// One CTA per time t, thread p.  The per-window quantities that do not depend
+// on p (y, near or far, sin(pi y), the far ratio h/y and its truncation R)
+// are formed once per CTA.  Near windows: the sinc row uses
+// sin(pi (y - j)) = (-1)^j sin(pi y) and the M-term sums run in double-float;
+// far windows: Horner in double-float over the double-float copy of nu.
 __global__ void __launch_bounds__(256) weights_kernel(
     int J, int M, double W, int K, const double *__restrict__ s, const double2 *__restrict__ B,
-    const double2 *__restrict__ nu, const double2 *__restrict__ ph_g,
+    const float4 *__restrict__ nu_f, const double2 *__restrict__ ph_g,
     const double *__restrict__ T, int n_T, double *__restrict__ Gr, double *__restrict__ Gm) {
-    extern __shared__ float smf[];
-    float2 *phc = reinterpret_cast<float2 *>(smf);          // M: cos (hi, lo)
+    extern __shared__ double smd[];
+    double *wy = smd;                                        // K: y
+    double *wf = wy + K;                                     // K: sin(pi y) (near) or scale sinc(y) (far)
+    float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: h / y as double-float
+    int *wR = reinterpret_cast<int *>(wrho + K);             // K: far terms, 0 = near
+    float2 *phc = reinterpret_cast<float2 *>(wR + ((K + 1) & ~1));   // M: cos (hi, lo)
     float2 *phs = phc + M;                                   // M: sin (hi, lo)
     float2 *sc = phs + M;                                    // M: sinc (hi, lo)
     const int t = blockIdx.x;
     const int p = blockIdx.y * blockDim.x + threadIdx.x;
     const int h = M / 2;
+    const double tt = T[t];
+    const double scale = 2.0 * W / (double)M;
     for (int q = threadIdx.x; q < M; q += blockDim.x) {
         const double2 e = ph_g[q];
         const dfl c = df_split(e.x), sn = df_split(e.y);
         phc[q] = make_float2(c.hi, c.lo);
         phs[q] = make_float2(sn.hi, sn.lo);
     }
-    const double tt = T[t];
-    const double scale = 2.0 * W / (double)M;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double y = W * (tt - s[k]) / kPi;
+        const double sy = sinpi(y);
+        wy[k] = y;
+        if (fabs(y) < 1.25 * (double)h) {
+            wf[k] = sy;
+            wR[k] = 0;
+        } else {
+            const double rho = (double)h / y;
+            const int R = (int)ceil(-48.0 * 0.69314718055994531 / log(fabs(rho)));
+            wR[k] = max(1, min(R, kFarTerms));
+            const dfl rr = df_split(rho);
+            wrho[k] = make_float2(rr.hi, rr.lo);
+            wf[k] = scale * sy / (kPi * y);
+        }
+    }
+    __syncthreads();
     double qr = 0.0, qi = 0.0;
     for (int k = 0; k < K; ++k) {
-        const double y = W * (tt - s[k]) / kPi;
+        const int R = wR[k];
         double dr = 0.0, di = 0.0;
-        if (fabs(y) < 1.25 * (double)h) {
+        if (R == 0) {                 // near window (the same branch in the whole CTA)
+            const double y = wy[k], sy = wf[k];
             __syncthreads();
             for (int m = threadIdx.x; m < M; m += blockDim.x) {
-                const double d = y - (double)(m - h);
-                const dfl v = df_split((d == 0.0) ? 1.0 : sinpi(d) / (kPi * d));
-                sc[m] = make_float2(v.hi, v.lo);
+                const int jj = m - h;
+                const double d = y - (double)jj;
+                const double v = (d == 0.0) ? 1.0 : ((jj & 1) ? -sy : sy) / (kPi * d);
+                const dfl vv = df_split(v);
+                sc[m] = make_float2(vv.hi, vv.lo);
             }
             __syncthreads();
             if (p < J) {
@@ -156,19 +209,17 @@ __global__ void __launch_bounds__(256) weights_kernel(
                 di = scale * ((double)ih + (double)il);
             }
         } else if (p < J) {
-            const double rho = (double)h / y;
-            const double lr = log(fabs(rho));
-            int R = (int)ceil(-54.0 * 0.69314718055994531 / lr);
-            R = max(1, min(R, kFarTerms));
-            double ar = 0.0, ai = 0.0;
+            const float2 r2 = wrho[k];
+            const dfl rho = {r2.x, r2.y};
+            float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
             for (int r = R - 1; r >= 0; --r) {
-                const double2 v = nu[(long long)r * J + p];
-                ar = ar * rho + v.x;
-                ai = ai * rho + v.y;
+                const float4 v = nu_f[(long long)r * J + p];
+                df_horner(ah, al, rho, v.x, v.y);
+                df_horner(bh, bl, rho, v.z, v.w);
             }
-            const double f = scale * sinpi(y) / (kPi * y);
-            dr = f * ar;
-            di = f * ai;
+            const double f = wf[k];
+            dr = f * ((double)ah + (double)al);
+            di = f * ((double)bh + (double)bl);
         }
         if (p < J) {
             const double2 b = B[(long long)k * J + p];
@@ -244,31 +295,113 @@ __global__ void __launch_bounds__(256) contract_kernel(int J, int n_x, int n_T,
     }
 }
 
+// The same contraction in double-float arithmetic (mixed-precision paths):
+// operands are split into FP32 (hi, lo) pairs while staged, each product is
+// formed exactly (FMA residual) plus the hi*lo cross terms, and every output
+// accumulates as a double-float pair (two-sum), ~2^-44 relative per step.
+__global__ void __launch_bounds__(256) contract_df_kernel(int J, int n_x, int n_T,
+                                                          const double2 *__restrict__ V,
+                                                          const double *__restrict__ Gr,
+                                                          const double *__restrict__ Gm,
+                                                          double *__restrict__ u) {
+    __shared__ float2 As[BK][BM];
+    __shared__ float2 Bs[BK][BN + 1];
+    const int x0 = blockIdx.y * BM, t0 = blockIdx.x * BN;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    float sh[4][4], sl[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+    const int K2 = 2 * J;
+    for (int k0 = 0; k0 < K2; k0 += BK) {
+        for (int e = tid; e < BK * BM; e += 256) {
+            const int kk = e / BM, xx = e % BM;
+            const int k = k0 + kk, x = x0 + xx;
+            double v = 0.0;
+            if (k < K2 && x < n_x) {
+                const double2 vv = V[(long long)(k < J ? k : k - J) * n_x + x];
+                v = (k < J) ? vv.x : vv.y;
+            }
+            const float h = (float)v;
+            As[kk][xx] = make_float2(h, (float)(v - (double)h));
+        }
+        for (int e = tid; e < BK * BN; e += 256) {
+            const int kk = e / BN, tt = e % BN;
+            const int k = k0 + kk, t = t0 + tt;
+            double v = 0.0;
+            if (k < K2 && t < n_T) v = (k < J) ? Gr[(long long)k * n_T + t] : Gm[(long long)(k - J) * n_T + t];
+            const float h = (float)v;
+            Bs[kk][tt] = make_float2(h, (float)(v - (double)h));
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float pp = a[i].x * b[j].x;
+                    float pe = fmaf(a[i].x, b[j].x, -pp);
+                    pe = fmaf(a[i].x, b[j].y, pe);
+                    pe = fmaf(a[i].y, b[j].x, pe);
+                    const float t = sh[i][j] + pp;
+                    const float z = t - sh[i][j];
+                    sl[i][j] += ((sh[i][j] - (t - z)) + (pp - z)) + pe;
+                    sh[i][j] = t;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int x = x0 + ty * 4 + i;
+        if (x >= n_x) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int t = t0 + tx * 4 + j;
+            if (t < n_T) u[(long long)x * n_T + t] = (double)sh[i][j] + (double)sl[i][j];
+        }
+    }
+}
+
 }  // namespace
 
-void launch_far_table(int J, int M, double2 *nu, double2 *phase_tab, cudaStream_t st) {
-    far_table_kernel<<<J, 192, 0, st>>>(J, M, nu, phase_tab);
+void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, double2 *phase_tab,
+                      cudaStream_t st) {
+    far_powers_kernel<<<(M + 127) / 128, 128, 0, st>>>(M, pw);
+    far_table_kernel<<<J, 192, 0, st>>>(J, M, pw, nu, nu_f, phase_tab);
 }
 
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
-                          const double2 *nu, const double2 *phase_tab, const double *T,
+                          const float4 *nu_f, const double2 *phase_tab, const double *T,
                           int n_T, double *Gr, double *Gm, cudaStream_t st) {
     if (n_T <= 0) return;
-    const size_t smem = (size_t)M * 3 * sizeof(float2);
+    const size_t smem = (size_t)K * (2 * sizeof(double) + sizeof(float2)) +
+                        (size_t)((K + 1) & ~1) * sizeof(int) + (size_t)M * 3 * sizeof(float2);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
     dim3 grid(n_T, (J + 255) / 256);
-    weights_kernel<<<grid, 256, smem, st>>>(J, M, W, K, s, B, nu, phase_tab, T, n_T, Gr, Gm);
+    weights_kernel<<<grid, 256, smem, st>>>(J, M, W, K, s, B, nu_f, phase_tab, T, n_T, Gr, Gm);
 }
 
 void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,
-                           const double *Gm, double *u, cudaStream_t st) {
+                           const double *Gm, double *u, bool double_float, cudaStream_t st) {
     if (n_x <= 0 || n_T <= 0) return;
     dim3 grid((n_T + BN - 1) / BN, (n_x + BM - 1) / BM);
-    contract_kernel<<<grid, 256, 0, st>>>(J, n_x, n_T, V, Gr, Gm, u);
+    if (double_float)
+        contract_df_kernel<<<grid, 256, 0, st>>>(J, n_x, n_T, V, Gr, Gm, u);
+    else
+        contract_kernel<<<grid, 256, 0, st>>>(J, n_x, n_T, V, Gr, Gm, u);
 }
 
 }  // namespace fh
