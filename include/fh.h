@@ -285,6 +285,14 @@ fh_status fh_get_timings(fh_ctx *ctx, fh_timings *out, int reset);
  * allocates its own device scratch. */
 fh_status fh_eval_bessel(const double *x, int n, double *out);
 
+/* J0, Y0, J1, Y1 at host points x[0..n-1] through the double-float
+ * (FP32-pair) Hankel form used by the mixed-precision kernels for x >= 8
+ * (Sec. 2.3 kernels; Hankel's asymptotic form with binary32 remainder
+ * polynomials); x < 8 uses the FP64 series.  out[4i .. 4i+3] (host,
+ * caller-owned).  Diagnostic entry point; allocates its own device scratch.
+ * Errors: FH_EINVAL (NULL pointers, n < 0), FH_ENOMEM, FH_ECUDA. */
+fh_status fh_eval_bessel_df(const double *x, int n, double *out);
+
 /* Tensor-core (tcgen05) check: C = A B^T for host FP32 arrays A (M x K) and
  * B (N x K), row-major, with the operands taken as BF16 (kind = 1, rounded to
  * nearest) or TF32 (kind = 2) and FP32 accumulation in tensor memory; C is

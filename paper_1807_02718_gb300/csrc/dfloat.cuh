@@ -1,0 +1,176 @@
+// Double-float ("df") arithmetic on the FP32 pipe, and the Hankel-form
+// Bessel functions of orders 0 and 1 at x >= 8 evaluated with it.
+//
+// A df value is hi + lo with |lo| <= ulp(hi) / 2, ~2^-48 relative.  Products
+// use the exact FMA residual (two-product), sums Knuth's two-sum; each
+// operation is accurate to a few 2^-46 relative.  FP32 issues 64 times as
+// many operations per clock as FP64 on this GPU, so a df operation (5-15
+// FP32 instructions) costs a fraction of one FP64 instruction's issue slot.
+//
+// Hankel form (x >= 8, A&S 9.2.5-9.2.6, 9.2.9-9.2.10):
+//   H_nu(x) = sqrt(2/(pi x)) (P_nu + i Q_nu) e^{i (x - (2 nu + 1) pi/4)},
+//   P0 = 1 - 9u/8192 + u^2 G0,   Q0 = (8/x)(-1/64 + 75u/524288 + u^2 G1),
+//   P1 = 1 + 15u/8192 + u^2 G2,  Q1 = (8/x)(3/64 - 105u/524288 + u^2 G3),
+// u = (8/x)^2.  The leading coefficients are exact binary32 numbers; each
+// remainder u^2 G_k (|.| <= 1e-4) is a polynomial whose constant term is a
+// df pair and whose other terms (|.| <= 1e-6) are binary32 (bessel_cheb.h),
+// so the df results carry ~1e-14 absolute error.
+#pragma once
+
+#include "bessel_cheb.h"
+
+namespace fh {
+
+struct dfv {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfv df_make(float hi, float lo) { return {hi, lo}; }
+
+__device__ __forceinline__ dfv df_from(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ double df_to(dfv a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ dfv df_quick(float s, float e) {   // |s| >= |e|
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ dfv df_add(dfv a, dfv b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    return df_quick(s, e);
+}
+
+__device__ __forceinline__ dfv df_add_f(dfv a, float b) {
+    const float s = a.hi + b;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b - bb)) + a.lo;
+    return df_quick(s, e);
+}
+
+__device__ __forceinline__ dfv df_neg(dfv a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dfv df_mul(dfv a, dfv b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_quick(p, e);
+}
+
+__device__ __forceinline__ dfv df_mul_f(dfv a, float b) {
+    const float p = a.hi * b;
+    const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+    return df_quick(p, e);
+}
+
+// a * b + c
+__device__ __forceinline__ dfv df_fma(dfv a, dfv b, dfv c) { return df_add(df_mul(a, b), c); }
+
+__device__ __forceinline__ dfv df_sqrt(dfv a) {
+    const float s = sqrtf(a.hi);
+    const float e = (fmaf(-s, s, a.hi) + a.lo) * (0.5f / s);
+    return df_quick(s, e);
+}
+
+__device__ __forceinline__ dfv df_rcp(dfv a) {
+    const float r = 1.0f / a.hi;
+    const float t = fmaf(-a.hi, r, 1.0f) - a.lo * r;   // 1 - a r
+    return df_quick(r, r * t);
+}
+
+// sin and cos of a df argument |y| <= pi/4 (Taylor series to degree 17 / 16,
+// truncation < 2^-53).
+__device__ __forceinline__ void df_sincos_small(dfv y, dfv &sn, dfv &cs) {
+    const dfv y2 = df_mul(y, y);
+    dfv ps = df_make(kSinDF[16], kSinDF[17]);
+    dfv pc = df_make(kCosDF[16], kCosDF[17]);
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        ps = df_fma(ps, y2, df_make(kSinDF[2 * k], kSinDF[2 * k + 1]));
+        pc = df_fma(pc, y2, df_make(kCosDF[2 * k], kCosDF[2 * k + 1]));
+    }
+    sn = df_mul(ps, y);
+    cs = pc;
+}
+
+// e^{i x} for an FP64 argument 0 <= x < 2^20: quadrant reduction in FP64 (two
+// FMAs with pi/2 split into two doubles), the rest in df.
+__device__ __forceinline__ void df_expi(double x, dfv &c, dfv &s) {
+    constexpr double kPio2Hi = 1.5707963267948966192;
+    constexpr double kPio2Lo = 6.123233995736766036e-17;
+    const double k = rint(x * 0.63661977236758134308);
+    double y = fma(-k, kPio2Hi, x);
+    y = fma(-k, kPio2Lo, y);
+    dfv sn, cs;
+    df_sincos_small(df_from(y), sn, cs);
+    const int q = ((int)k) & 3;
+    if (q == 0) { c = cs; s = sn; }
+    else if (q == 1) { c = df_neg(sn); s = cs; }
+    else if (q == 2) { c = df_neg(cs); s = df_neg(sn); }
+    else { c = sn; s = df_neg(cs); }
+}
+
+// Remainder polynomials staged in shared memory (threads of a warp may fall
+// into different x intervals).
+struct GShared {
+    float c[kPQ_NI * 4 * kG_TERMS];
+    float2 c0[kPQ_NI * 4];          // constant terms as (hi, lo)
+    float uc[kPQ_NI], iuh[kPQ_NI];
+};
+
+__device__ __forceinline__ void g_stage(GShared &tb) {
+    for (int i = threadIdx.x; i < kPQ_NI * 4 * kG_TERMS; i += blockDim.x) tb.c[i] = kG[i];
+    for (int i = threadIdx.x; i < kPQ_NI * 4; i += blockDim.x) tb.c0[i] = make_float2(kG0DF[2 * i], kG0DF[2 * i + 1]);
+    for (int i = threadIdx.x; i < kPQ_NI; i += blockDim.x) {
+        tb.uc[i] = kPQ_UCf[i];
+        tb.iuh[i] = kPQ_IUHf[i];
+    }
+}
+
+// u^2 G(t) in df: G = c0 (df) + t (c1 + c2 t + ...) (binary32).
+__device__ __forceinline__ dfv g_term(const float *c, float2 c0, float t, dfv u2) {
+    float a = c[kG_TERMS - 1];
+#pragma unroll
+    for (int k = kG_TERMS - 2; k >= 1; --k) a = fmaf(a, t, c[k]);
+    return df_mul(u2, df_add_f(df_make(c0.x, c0.y), a * t));
+}
+
+// Hankel-form J0, Y0 (and J1, Y1 when want1) at x = kappa r >= 8.
+//   r8 = 8 / x (df), amp = sqrt(2 / (pi x)) (df), (c, s) = e^{i (x - pi/4)}.
+// J0 = amp (P0 c - Q0 s), Y0 = amp (P0 s + Q0 c); with e^{i (x - 3pi/4)} =
+// (s, -c): J1 = amp (P1 s + Q1 c), Y1 = amp (Q1 s - P1 c).
+template <bool want1>
+__device__ __forceinline__ void df_hankel(const GShared &tb, float xf, dfv r8, dfv amp, dfv c, dfv s,
+                                          dfv &J0, dfv &Y0, dfv &J1, dfv &Y1) {
+    const dfv u = df_mul(r8, r8);
+    const int k = (xf >= 10.f) + (xf >= 13.f) + (xf >= 18.f) + (xf >= 28.f) + (xf >= 60.f);
+    const float t = (u.hi - tb.uc[k]) * tb.iuh[k];
+    const dfv u2 = df_mul(u, u);
+    const float *g = tb.c + k * 4 * kG_TERMS;
+    const float2 *g0 = tb.c0 + k * 4;
+    // delta P0 = P0 - 1, q0 = Q0 / r8
+    const dfv dP0 = df_add(df_mul_f(u, -9.0f / 8192.0f), g_term(g, g0[0], t, u2));
+    const dfv q0 = df_add_f(df_add(df_mul_f(u, 75.0f / 524288.0f), g_term(g + kG_TERMS, g0[1], t, u2)),
+                            -1.0f / 64.0f);
+    const dfv Q0 = df_mul(r8, q0);
+    const dfv P0c = df_add(c, df_mul(dP0, c)), P0s = df_add(s, df_mul(dP0, s));
+    J0 = df_mul(amp, df_add(P0c, df_neg(df_mul(Q0, s))));
+    Y0 = df_mul(amp, df_add(P0s, df_mul(Q0, c)));
+    if (want1) {
+        const dfv dP1 = df_add(df_mul_f(u, 15.0f / 8192.0f), g_term(g + 2 * kG_TERMS, g0[2], t, u2));
+        const dfv q1 = df_add_f(df_add(df_mul_f(u, -105.0f / 524288.0f),
+                                       g_term(g + 3 * kG_TERMS, g0[3], t, u2)), 3.0f / 64.0f);
+        const dfv Q1 = df_mul(r8, q1);
+        const dfv P1s = df_add(s, df_mul(dP1, s)), P1c = df_add(c, df_mul(dP1, c));
+        J1 = df_mul(amp, df_add(P1s, df_mul(Q1, c)));
+        Y1 = df_mul(amp, df_add(df_mul(Q1, s), df_neg(P1c)));
+    }
+}
+
+}  // namespace fh

@@ -548,7 +548,7 @@ fh_status sample_common(fh_ctx *ctx, int q, const double *d_x, int n_x, const do
                                 ctx->d_item_first.as<int>(), ctx->d_solve_j.as<int>(),
                                 ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                 ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_part.as<double2>(),
-                                ctx->d_V.as<double2>(), ctx->stream);
+                                ctx->d_V.as<double2>(), ctx->precision != FH_FP64, ctx->stream);
         FH_TRY(check_launch(ctx, "target field"));
     }
     ctx->n_x_last = n_x;
@@ -1047,6 +1047,26 @@ fh_status fh_eval_bessel(const double *x, int n, double *out) {
         fh::launch_bessel_eval(d, n, d + n, 0);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpy(out, d + n, (size_t)n * 6 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = FH_ECUDA;
+    }
+    cudaFree(d);
+    return st;
+}
+
+fh_status fh_eval_bessel_df(const double *x, int n, double *out) {
+    if (!x || !out || n < 0) return FH_EINVAL;
+    if (n == 0) return FH_OK;
+    double *d = nullptr;
+    if (cudaMalloc(&d, (size_t)n * 5 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return FH_ENOMEM;
+    }
+    fh_status st = FH_OK;
+    if (cudaMemcpy(d, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) st = FH_ECUDA;
+    if (st == FH_OK) {
+        fh::launch_bessel_eval_df(d, n, d + n, 0);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(out, d + n, (size_t)n * 4 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
             st = FH_ECUDA;
     }
     cudaFree(d);

@@ -116,11 +116,14 @@ void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, 
                          const int2 *items, int item_begin, int n_items, const int *item_first,
                          const int *solve_j, const double2 *z, const double2 *dz,
                          const double2 *psi, const double *x, int n_x, double2 *part,
-                         double2 *V, cudaStream_t st);
+                         double2 *V, bool double_float,
+                         cudaStream_t st);
 
 // Kernel Bessel routine on n arguments: out[6i..6i+5] = J0, Y0, J1, Y1 (joint
 // routine) and J0, Y0 (H0-only routine).
 void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st);
+// out[4i..4i+3] = J0, Y0, J1, Y1 through the double-float Hankel form (x >= 8).
+void launch_bessel_eval_df(const double *x, int n, double *out, cudaStream_t st);
 
 // ---- synthesis (k_synth.cu) ----
 // nu[r * J + p] = sum_{m=-h}^{h-1} (-1)^m (m/h)^r e^{-2 pi i m p / M} (nu may

@@ -132,6 +132,72 @@ def pq_table():
     return rows, ucs, uhs
 
 
+# Double-float evaluation (mixed-precision paths) writes each function as its
+# first two Hankel terms, exact in binary32, plus a remainder u^2 G(u):
+#   P0 = 1 - 9u/8192 + u^2 G0,   Q0 = (8/x) (-1/64 + 75u/524288 + u^2 G1),
+#   P1 = 1 + 15u/8192 + u^2 G2,  Q1 = (8/x) (3/64 - 105u/524288 + u^2 G3),
+# u = (8/x)^2 (A&S 9.2.9-9.2.10 with mu = 4 nu^2).  |u^2 G| <= 1e-4 on x >= 8;
+# the constant term of each G piece is kept as a double-float pair and the
+# rest (|.| <= 1e-6) in binary32, which leaves ~1e-14 absolute error.
+LEAD = [(mp.mpf(1), mp.mpf(-9) / 8192), (mp.mpf(-1) / 64, mp.mpf(75) / 524288),
+        (mp.mpf(1), mp.mpf(15) / 8192), (mp.mpf(3) / 64, mp.mpf(-105) / 524288)]
+G_TERMS = 8
+
+
+def g_table():
+    """Horner tables (binary32) of G0..G3 per x interval, variable t as in pq_table."""
+    rows = []
+    bounds = PQ_BREAKS + [mp.inf]
+    for x0, x1 in zip(bounds[:-1], bounds[1:]):
+        u_hi = (mp.mpf(8) / x0) ** 2
+        u_lo = mp.mpf(0) if x1 == mp.inf else (mp.mpf(8) / x1) ** 2
+        uc, uh = (u_hi + u_lo) / 2, (u_hi - u_lo) / 2
+
+        def u_of(t, uc=uc, uh=uh):
+            return uc + uh * t
+
+        def g(t, k, uc=uc, uh=uh):
+            u = u_of(t)
+            if u == 0:
+                u = mp.mpf("1e-30")
+            x = 8 / mp.sqrt(u)
+            v = pq(k // 2, x)[k % 2]
+            if k % 2:
+                v = v * x / 8
+            c0, c1 = LEAD[k]
+            return (v - c0 - c1 * u) / (u * u)
+
+        for k in range(4):
+            c = cheb(lambda t, k=k: g(t, k))
+            # binary32 needs ~1e-8 relative: drop the tail below that
+            scale = max(abs(v) for v in c)
+            c = [v for v in c]
+            while len(c) > 1 and abs(c[-1]) < mp.mpf("1e-9") * scale:
+                c.pop()
+            if len(c) > G_TERMS:
+                raise SystemExit(f"G{k} on [{x0},{x1}) needs {len(c)} terms")
+            c = c + [mp.mpf(0)] * (G_TERMS - len(c))
+            rows.append(cheb_to_monomial(c))
+    return rows
+
+
+def emit_f(name, c):
+    body = ",\n    ".join(repr(float(mp.mpf(v))) + "f" for v in c)
+    return f"static __device__ __constant__ float {name}[{len(c)}] = {{\n    {body}}};\n"
+
+
+def df_consts(name, vals):
+    """Double-float (hi, lo) pairs of the given numbers."""
+    import struct
+    out = []
+    for v in vals:
+        hi = struct.unpack("f", struct.pack("f", float(v)))[0]
+        lo = struct.unpack("f", struct.pack("f", float(v - mp.mpf(hi))))[0]
+        out += [hi, lo]
+    body = ",\n    ".join(repr(x) + "f" for x in out)
+    return f"static __device__ __constant__ float {name}[{len(out)}] = {{\n    {body}}};\n"
+
+
 def emit(name, c):
     body = ",\n    ".join(mp.nstr(v, 20, min_fixed=-1, max_fixed=-1) for v in c)
     return f"constexpr int {name}_N = {len(c)};\nstatic __device__ __constant__ double {name}[{len(c)}] = {{\n    {body}}};\n"
@@ -159,6 +225,17 @@ def main():
     out.append(emit("kPQ", flat))
     out.append(emit("kPQ_UC", ucs))
     out.append(emit("kPQ_UH", uhs))
+    out.append("// binary32 remainder polynomials G0..G3 [interval][function][power of t] (double-float path)")
+    out.append(f"constexpr int kG_TERMS = {G_TERMS};")
+    g_rows = g_table()
+    out.append(emit_f("kG", [v for r in g_rows for v in r]))
+    out.append("// constant terms of G0..G3 as double-float pairs [interval][function][hi, lo]")
+    out.append(df_consts("kG0DF", [r[0] for r in g_rows]))
+    out.append(emit_f("kPQ_UCf", ucs))
+    out.append(emit_f("kPQ_IUHf", [1 / v for v in uhs]))
+    out.append("// (-1)^k / (2k+1)! and (-1)^k / (2k)! as double-float pairs, k = 0..8 (sine and cosine series)")
+    out.append(df_consts("kSinDF", [(-1) ** k / mp.factorial(2 * k + 1) for k in range(9)]))
+    out.append(df_consts("kCosDF", [(-1) ** k / mp.factorial(2 * k) for k in range(9)]))
     print("\n".join(out))
 
 

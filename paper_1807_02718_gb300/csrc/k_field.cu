@@ -9,6 +9,7 @@
 // One CTA per (frequency, 128 targets); source nodes are staged through
 // shared memory with the weights c_i = (pi/n) |z'_i| psi_i / 4 premultiplied.
 #include "bessel.cuh"
+#include "dfloat.cuh"
 #include "fh_internal.h"
 
 namespace fh {
@@ -120,6 +121,140 @@ __global__ void __launch_bounds__(kTgt) field_partial_kernel(
         if (j < cnt) part[((long long)w * kGroup + j) * n_x + it] = acc[j];
 }
 
+// acc += a * b (or -= when neg): exact FP32 product hi*hi with its FMA
+// residual and the cross terms; the running sum is a two-sum pair that is
+// renormalised by the caller.
+__device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool neg) {
+    float p = a.hi * b.hi;
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    if (neg) { p = -p; pe = -pe; }
+    const float t = sh + p;
+    const float z = t - sh;
+    sl += ((sh - (t - z)) + (p - z)) + pe;
+    sh = t;
+}
+
+// Mixed-precision variant of field_partial_kernel: the same sums with the
+// Hankel-form H0 (kappa r >= 8), the phases and the accumulation in
+// double-float arithmetic.  FP64 is kept for the distance, the phase
+// arguments kappa_0 r and dkappa r with their reduction modulo pi/2, and the
+// small-argument series (kappa r < 8).
+__global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
+    SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin,
+    const double2 *__restrict__ z, const double2 *__restrict__ dz,
+    const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
+    double2 *__restrict__ part) {
+    const int w = blockIdx.y;
+    const int2 item = items[item_begin + w];
+    const int g = item.x, i0 = item.y;
+    const int2 sgv = grp.sg[g];
+    const int s0 = sgv.x, cnt = sgv.y;
+    const int N = t.N[s0];
+    const int vo0 = t.vec_off[s0];
+    const double wq = 2.0 * kPi / (double)N * 0.25;   // (pi/n) / 4
+    const double dk = grp.dkappa[g];
+    __shared__ double kap[kGroup];
+    __shared__ float kapf[kGroup], corrf[kGroup];
+    __shared__ dfv ikap[kGroup], isqk[kGroup];
+    __shared__ double2 zs[kChunk];
+    __shared__ float4 ps[kGroup][kChunk];   // (pi/n)|z'|/4 * psi_j as (re hi, re lo, im hi, im lo)
+    __shared__ GShared gt;
+    g_stage(gt);
+    if (threadIdx.x < kGroup) {
+        const int j = threadIdx.x;
+        const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
+        kap[j] = k;
+        kapf[j] = (float)k;
+        ikap[j] = df_from(1.0 / k);
+        isqk[j] = df_from(1.0 / sqrt(k));
+        corrf[j] = (float)(k - ((j < cnt ? t.kappa[s0] : 1.0) + j * dk));
+    }
+    const int ne = min(kChunk, N - i0);
+    for (int e = threadIdx.x; e < kChunk; e += kTgt) {
+        const int i = i0 + e;
+        double2 zz = make_double2(0.0, 0.0);
+        double sp = 0.0;
+        if (e < ne) {
+            const double2 d = dz[vo0 + i];
+            sp = sqrt(d.x * d.x + d.y * d.y) * wq;
+            zz = z[vo0 + i];
+        }
+        zs[e] = zz;
+        for (int j = 0; j < kGroup; ++j) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < ne && j < cnt) {
+                const double2 q = psi[t.vec_off[s0 + j] + i];
+                const dfv re = df_from(q.x * sp), im = df_from(q.y * sp);
+                v = make_float4(re.hi, re.lo, im.hi, im.lo);
+            }
+            ps[j][e] = v;
+        }
+    }
+    __syncthreads();
+    const int it = blockIdx.x * kTgt + threadIdx.x;
+    if (it >= n_x) return;
+    const double px = x[2 * it], py = x[2 * it + 1];
+    const dfv two_over_pi = df_make(0.6366197466850281f, 2.5682552973194106e-08f);   // 2/pi
+    float ah[kGroup][2], al[kGroup][2];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j) ah[j][0] = ah[j][1] = al[j][0] = al[j][1] = 0.f;
+    for (int e = 0; e < ne; ++e) {
+        const double d1 = px - zs[e].x, d2 = py - zs[e].y;
+        const dfv rd = df_sqrt(df_from(fma(d1, d1, d2 * d2)));
+        const double r = df_to(rd);
+        const dfv ir = df_rcp(rd);
+        const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));   // sqrt(2 / (pi r))
+        dfv c, sv, sc, ss;
+        df_expi(kap[0] * r - 0.78539816339744830962, c, sv);   // e^{i (kappa_0 r - pi/4)}
+        df_expi(dk * r, sc, ss);
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+            if (j < cnt) {
+                const float xf = kapf[j] * rd.hi;
+                dfv J0, Y0;
+                if (xf >= 8.0f) {
+                    const float dl = corrf[j] * rd.hi;
+                    const dfv cj = df_add_f(c, -dl * sv.hi), sj = df_add_f(sv, dl * c.hi);
+                    const dfv r8 = df_mul_f(df_mul(ir, ikap[j]), 8.0f);
+                    dfv J1, Y1;
+                    df_hankel<false>(gt, xf, r8, df_mul(amp0, isqk[j]), cj, sj, J0, Y0, J1, Y1);
+                } else {
+                    double j0, y0;
+                    bessel_small0(kap[j] * r, j0, y0);
+                    J0 = df_from(j0);
+                    Y0 = df_from(y0);
+                }
+                const float4 q4 = ps[j][e];
+                const dfv qr = df_make(q4.x, q4.y), qi = df_make(q4.z, q4.w);
+                // acc += (-Y0 qr - J0 qi) + i (-Y0 qi + J0 qr)
+                df_acc(ah[j][0], al[j][0], Y0, qr, true);
+                df_acc(ah[j][0], al[j][0], J0, qi, true);
+                df_acc(ah[j][1], al[j][1], Y0, qi, true);
+                df_acc(ah[j][1], al[j][1], J0, qr, false);
+                const dfv cn = df_add(df_mul(c, sc), df_neg(df_mul(sv, ss)));
+                sv = df_add(df_mul(sv, sc), df_mul(c, ss));
+                c = cn;
+            }
+        }
+        if ((e & 15) == 15)
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const dfv v = df_quick(ah[j][h], al[j][h]);
+                    ah[j][h] = v.hi;
+                    al[j][h] = v.lo;
+                }
+    }
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j)
+        if (j < cnt)
+            part[((long long)w * kGroup + j) * n_x + it] =
+                make_double2((double)ah[j][0] + (double)al[j][0], (double)ah[j][1] + (double)al[j][1]);
+}
+
 // V[solve_j[s0 + j]][x] = sum over the subgroup's items, in item order.
 __global__ void field_reduce_kernel(Subgroups grp, int g_begin, const int *__restrict__ item_first,
                                     int item_begin, const int *__restrict__ solve_j,
@@ -161,22 +296,57 @@ __global__ void bessel_eval_kernel(const double *__restrict__ x, int n, double *
     out[6 * i + 5] = b;
 }
 
+// J0, Y0, J1, Y1 through the double-float Hankel form for x >= 8 (the FP64
+// series below 8), for testing the mixed-precision kernels.
+__global__ void bessel_eval_df_kernel(const double *__restrict__ x, int n, double *__restrict__ out) {
+    __shared__ GShared gt;
+    g_stage(gt);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double xv = x[i];
+    double J0, Y0, J1, Y1;
+    if (xv >= 8.0) {
+        dfv c, s, j0, y0, j1, y1;
+        df_expi(xv - 0.78539816339744830962, c, s);
+        df_hankel<true>(gt, (float)xv, df_from(8.0 / xv), df_from(sqrt(kTwoOverPi / xv)), c, s, j0, y0,
+                        j1, y1);
+        J0 = df_to(j0);
+        Y0 = df_to(y0);
+        J1 = df_to(j1);
+        Y1 = df_to(y1);
+    } else {
+        bessel_j0y0j1y1(xv, J0, Y0, J1, Y1);
+    }
+    out[4 * i + 0] = J0;
+    out[4 * i + 1] = Y0;
+    out[4 * i + 2] = J1;
+    out[4 * i + 3] = Y1;
+}
+
 }  // namespace
 
 void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st) {
     if (n > 0) bessel_eval_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, n, out);
 }
 
+void launch_bessel_eval_df(const double *x, int n, double *out, cudaStream_t st) {
+    if (n > 0) bessel_eval_df_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, n, out);
+}
+
 void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
                          const int2 *items, int item_begin, int n_items, const int *item_first,
                          const int *solve_j, const double2 *z, const double2 *dz,
                          const double2 *psi, const double *x, int n_x, double2 *part,
-                         double2 *V, cudaStream_t st) {
+                         double2 *V, bool double_float, cudaStream_t st) {
     if (n_x <= 0) return;
     field_zero_freq_kernel<<<(n_x + 255) / 256, 256, 0, st>>>(n_x, V);
     if (n_groups <= 0 || n_items <= 0) return;
     dim3 grid((n_x + kTgt - 1) / kTgt, n_items);
-    field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, part);
+    if (double_float)
+        field_partial_df_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, part);
+    else
+        field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, part);
     dim3 g2((n_x + 127) / 128, n_groups);
     field_reduce_kernel<<<g2, 128, 0, st>>>(g, g_begin, item_first, item_begin, solve_j, part, n_x, V);
 }

@@ -32,7 +32,7 @@ EXPORTED = [
     "fh_synthesize", "fh_set_timing", "fh_get_timings", "fh_probe_fma_peak",
     "fh_eval_bessel", "fh_synthesize_static", "fh_discretize_batch", "fh_num_problems",
     "fh_window_spectra_p", "fh_window_spectra_p_dev", "fh_sample_p", "fh_sample_p_dev",
-    "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test",
+    "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test", "fh_eval_bessel_df",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "spectra", "field", "weights", "contract"]
@@ -98,6 +98,7 @@ def load_library(path: str | None = None):
         "fh_get_timings": (C.c_int, [vp, C.POINTER(fh_timings), C.c_int]),
         "fh_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
         "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
+        "fh_eval_bessel_df": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_discretize_batch": (C.c_int, [vp, C.c_int, C.POINTER(fh_curve), _IP, _DP, _IP, _DP, _DP]),
         "fh_num_problems": (C.c_int, [vp, _IP]),
         "fh_window_spectra_p": (C.c_int, [vp, C.c_int, _DP, C.c_int, C.c_double, C.c_double, C.c_double]),
@@ -306,6 +307,16 @@ def fh_eval_bessel(x):
     st = load_library().fh_eval_bessel(_dp(xv), xv.size, _dp(out))
     if st != FH_OK:
         raise FHError(st, "fh_eval_bessel failed")
+    return out
+
+
+def fh_eval_bessel_df(x):
+    """(n, 4) array: J0, Y0, J1, Y1 through the double-float Hankel form (x >= 8)."""
+    xv = _f64(x)
+    out = np.empty((xv.size, 4))
+    st = load_library().fh_eval_bessel_df(_dp(xv), xv.size, _dp(out))
+    if st != FH_OK:
+        raise FHError(st, "fh_eval_bessel_df failed")
     return out
 
 

@@ -44,6 +44,25 @@ def test_bessel_routine_dense_grid():
     assert np.max(np.abs(w * np.pi * x / 2 - 1)) < 5e-13
 
 
+def test_double_float_hankel_form():
+    """The double-float (FP32-pair) Hankel form of the mixed-precision kernels
+    against the FP64 routine and scipy for 8 <= x <= 2000: ~1e-13 absolute,
+    the budget that keeps the mixed path within 1e-10 of the oracle."""
+    x = np.concatenate([np.linspace(8, 8.01, 101), np.linspace(8, 40, 8000),
+                        np.linspace(9.99, 10.01, 51), np.linspace(59.99, 60.01, 51),
+                        np.geomspace(40, 2000, 6000)])
+    out = F.fh_eval_bessel_df(x)
+    ref64 = F.fh_eval_bessel(x)[:, :4]
+    ref = np.stack([special.j0(x), special.y0(x), special.j1(x), special.y1(x)], 1)
+    assert np.max(np.abs(out - ref64)) < 2e-13, np.max(np.abs(out - ref64), axis=0)
+    assert np.max(np.abs(out - ref)) < 2e-13
+    w = out[:, 2] * out[:, 1] - out[:, 0] * out[:, 3]
+    assert np.max(np.abs(w * np.pi * x / 2 - 1)) < 1e-11
+    # below 8 the FP64 series is used unchanged
+    xs = np.linspace(0.1, 7.9, 200)
+    assert np.array_equal(F.fh_eval_bessel_df(xs), F.fh_eval_bessel(xs)[:, :4])
+
+
 def test_fp64_peak_probe_runs():
     v = F.fh_probe_fma_peak(0, True, 256)
     assert v > 0.1
