@@ -682,7 +682,7 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         fh::launch_assemble_groups(t, groups(ctx), ctx->n_groups, ctx->group_tiles,
                                    ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                    ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
-                                   ctx->d_logsin.as<double>(), ctx->d_A.as<double2>(), 0, ctx->stream);
+                                   ctx->d_logsin.as<double>(), ctx->d_A.as<double2>(), 0, ctx->precision != FH_FP64, ctx->stream);
         FH_TRY(check_launch(ctx, "assemble"));
         if (mixed) FH_TRY(ensure(ctx, ctx->d_g, (size_t)ctx->vec_total * sizeof(double2)));
         fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
@@ -916,7 +916,7 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     fh::launch_assemble_groups(t, g1, 1, nt * nt, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
                                ctx->d_logsin.as<double>(), ctx->d_tmpA.as<double2>(), -base,
-                               ctx->stream);
+                               ctx->precision != FH_FP64, ctx->stream);
     FH_TRY(check_launch(ctx, "assemble (single)"));
     fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                    ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),

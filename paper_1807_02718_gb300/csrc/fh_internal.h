@@ -58,7 +58,7 @@ struct Subgroups {
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long n_tiles, const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
-                            double2 *A, long long out_shift, cudaStream_t st);
+                            double2 *A, long long out_shift, bool double_float, cudaStream_t st);
 // Solve s uses the incidence direction pdir[prob[s]].
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
                 const int *prob, const double2 *pdir, double2 *g, cudaStream_t st);

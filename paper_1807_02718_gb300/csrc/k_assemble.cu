@@ -19,6 +19,7 @@
 // offsets tile_off).  Each warp writes 32 consecutive rows of a column:
 // column-major stores of 512 B.
 #include "bessel.cuh"
+#include "dfloat.cuh"
 #include "fh_internal.h"
 
 namespace fh {
@@ -150,6 +151,143 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
     }
 }
 
+// Mixed-precision variant of assemble_group_kernel.  With
+//   k4 = kappa N_il s_l / (4 s_i r),  e4 = eta s_l / 4,
+//   W  = (pi/n) ln(4 sin^2((t_i - t_l)/2)) - R_{i-l},
+// the off-diagonal entry is
+//   Re A = k4 (W/pi J1 - (pi/n) Y1) + (pi/n) e4 J0,
+//   Im A = (pi/n) k4 J1 + e4 ((pi/n) Y0 - W/pi J0),
+// the same combination of M, M1, M2, L, L1, L2 as the FP64 kernel.  For
+// kappa r >= 8 the Bessel values (Hankel form), the phases and this
+// combination run in double-float arithmetic; diagonal entries, kappa r < 8
+// (small-argument series, the near-diagonal band), the Kress weights and the
+// log table stay FP64.
+__global__ void __launch_bounds__(256) assemble_group_df_kernel(
+    SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ z,
+    const double2 *__restrict__ dz, const double2 *__restrict__ ddz,
+    const double *__restrict__ kress, const double *__restrict__ logsin,
+    double2 *__restrict__ A, long long out_shift) {
+    const long long b = blockIdx.x;
+    const int g = find_solve(grp.tile_off, n_groups, b);
+    const int2 sgv = grp.sg[g];
+    const int s0 = sgv.x, cnt = sgv.y;
+    const int N = t.N[s0];
+    const int nt = (N + kTile - 1) / kTile;
+    const long long lt = b - grp.tile_off[g];
+    const int tr = (int)(lt % nt), tc = (int)(lt / nt);
+    __shared__ double kap[kGroup], eta[kGroup];
+    __shared__ float kapf[kGroup], corrf[kGroup];
+    __shared__ dfv kapd[kGroup], etad[kGroup], ikap[kGroup], isqk[kGroup];
+    __shared__ long long moff[kGroup];
+    __shared__ GShared gt;
+    g_stage(gt);
+    const double dk = grp.dkappa[g];
+    if (threadIdx.x < kGroup) {
+        const int j = threadIdx.x;
+        const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
+        const double e = (j < cnt) ? t.eta[s0 + j] : 0.0;
+        kap[j] = k;
+        eta[j] = e;
+        kapf[j] = (float)k;
+        kapd[j] = df_from(k);
+        etad[j] = df_from(e);
+        ikap[j] = df_from(1.0 / k);
+        isqk[j] = df_from(1.0 / sqrt(k));
+        corrf[j] = (float)(k - ((j < cnt ? t.kappa[s0] : 1.0) + j * dk));
+        moff[j] = ((j < cnt) ? t.mat_off[s0 + j] : 0) + out_shift;
+    }
+    __syncthreads();
+    const int i = tr * kTile + (threadIdx.x & 31);
+    if (i >= N) return;
+    const int vo = t.vec_off[s0];
+    const int to = t.tab_off[t.tab[s0]];
+    const double pin = 2.0 * kPi / (double)N;   // pi / n
+    const dfv pind = df_from(pin);
+    const double2 zi = z[vo + i], dzi = dz[vo + i];
+    const double si = sqrt(dzi.x * dzi.x + dzi.y * dzi.y);
+    const dfv isi4 = df_from(0.25 / si);
+    const double inv4pi = 1.0 / (4.0 * kPi);
+    const dfv two_over_pi = df_make(0.6366197466850281f, 2.5682552973194106e-08f);
+
+    for (int q = threadIdx.x >> 5; q < kTile; q += 8) {
+        const int l = tc * kTile + q;
+        if (l >= N) break;
+        int d = i - l;
+        if (d < 0) d += N;
+        const double Rw = kress[to + d];
+        const double2 dzl = dz[vo + l];
+        const double sl = sqrt(dzl.x * dzl.x + dzl.y * dzl.y);
+        const long long e_off = (long long)l * N + i;
+        if (l == i) {
+            const double2 dd = ddz[vo + i];
+            const double M1 = -si * inv4pi;
+            const double L2r = (dd.x * dzi.y - dd.y * dzi.x) * inv4pi / (si * si);
+            for (int j = 0; j < cnt; ++j) {
+                const double M2r = (-kEulerGamma / (2.0 * kPi) - log(kap[j] * si * 0.5) / (2.0 * kPi)) * si;
+                const double M2i = 0.25 * si;
+                const double ar = 0.5 + pin * (L2r + eta[j] * M2i);
+                const double ai = Rw * (-eta[j] * M1) + pin * (0.0 - eta[j] * M2r);
+                A[moff[j] + e_off] = make_double2(ar, ai);
+            }
+            continue;
+        }
+        const double2 zl = z[vo + l];
+        const double d1 = zl.x - zi.x, d2 = zl.y - zi.y;
+        const dfv rd = df_sqrt(df_from(fma(d1, d1, d2 * d2)));
+        const double r = df_to(rd);
+        const dfv ir = df_rcp(rd);
+        const double Nil = dzi.y * d1 - dzi.x * d2;
+        const double ls = logsin[to + d];
+        const dfv Wp = df_from(fma(pin, ls, -Rw) * (1.0 / kPi));           // W / pi
+        const dfv gg4 = df_mul(df_mul(df_from(Nil), df_from(sl)), df_mul(ir, isi4));   // N s_l / (4 s_i r)
+        const dfv sl4 = df_from(0.25 * sl);
+        const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));
+        dfv c, sv, sc, ss;
+        df_expi(kap[0] * r - 0.78539816339744830962, c, sv);
+        df_expi(dk * r, sc, ss);
+        // FP64 quantities for kappa r < 8
+        const double ir64 = df_to(ir);
+        const double gg = Nil * sl * ir64 / si;
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+            if (j < cnt) {
+                const float xf = kapf[j] * rd.hi;
+                if (xf >= 8.0f) {
+                    const float dl = corrf[j] * rd.hi;
+                    const dfv cj = df_add_f(c, -dl * sv.hi), sj = df_add_f(sv, dl * c.hi);
+                    const dfv r8 = df_mul_f(df_mul(ir, ikap[j]), 8.0f);
+                    dfv J0, Y0, J1, Y1;
+                    df_hankel<true>(gt, xf, r8, df_mul(amp0, isqk[j]), cj, sj, J0, Y0, J1, Y1);
+                    const dfv k4 = df_mul(kapd[j], gg4), e4 = df_mul(etad[j], sl4);
+                    const dfv pk4 = df_mul(pind, k4), pe4 = df_mul(pind, e4);
+                    const dfv ar = df_add(df_mul(k4, df_add(df_mul(Wp, J1), df_neg(df_mul(pind, Y1)))),
+                                          df_mul(pe4, J0));
+                    const dfv ai = df_add(df_mul(pk4, J1),
+                                          df_mul(e4, df_add(df_mul(pind, Y0), df_neg(df_mul(Wp, J0)))));
+                    A[moff[j] + e_off] = make_double2(df_to(ar), df_to(ai));
+                } else {
+                    const double kappa = kap[j];
+                    double J0, Y0, J1, Y1;
+                    bessel_small(kappa * r, J0, Y0, J1, Y1);
+                    const double Mr = -0.25 * Y0 * sl, Mi = 0.25 * J0 * sl;
+                    const double M1 = -J0 * sl * inv4pi;
+                    const double M2r = Mr - M1 * ls;
+                    const double Lr = -0.25 * kappa * Y1 * gg, Li = 0.25 * kappa * J1 * gg;
+                    const double L1 = -kappa * inv4pi * J1 * gg;
+                    const double L2r = Lr - L1 * ls;
+                    const double et = eta[j];
+                    const double ar = Rw * L1 + pin * (L2r + et * Mi);
+                    const double ai = Rw * (-et * M1) + pin * (Li - et * M2r);
+                    A[moff[j] + e_off] = make_double2(ar, ai);
+                }
+                const dfv cn = df_add(df_mul(c, sc), df_neg(df_mul(sv, ss)));
+                sv = df_add(df_mul(sv, sc), df_mul(c, ss));
+                c = cn;
+            }
+        }
+    }
+}
+
 // g_i = dB/dn - i eta B = i (kappa p.nu_i - eta) e^{i kappa p.z_i}
 __global__ void rhs_kernel(SolveTables t, const double2 *__restrict__ z,
                            const double2 *__restrict__ dz, const int *__restrict__ prob,
@@ -176,10 +314,14 @@ __global__ void rhs_kernel(SolveTables t, const double2 *__restrict__ z,
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long n_tiles, const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
-                            double2 *A, long long out_shift, cudaStream_t st) {
+                            double2 *A, long long out_shift, bool double_float, cudaStream_t st) {
     if (n_tiles <= 0 || n_groups <= 0) return;
-    assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
-                                                             logsin, A, out_shift);
+    if (double_float)
+        assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
+                                                                    logsin, A, out_shift);
+    else
+        assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
+                                                                 logsin, A, out_shift);
 }
 
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
