@@ -88,7 +88,7 @@ struct fh_ctx {
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_solve_prob, d_order, d_curves, d_pdir;
     DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_nu_f, d_ph, d_omega, d_pw;
-    DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk;
+    DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk, d_Bf;
     int n_rchunk = 0;
     DevBuf d_wa, d_a;
     int n_x_last = 0;
@@ -117,7 +117,7 @@ struct fh_ctx {
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_A32, &d_piv, &d_g, &d_iters,
-                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
+                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
         for (DevBuf *b : all) free_buf(*b);
         free_problems();
@@ -522,9 +522,10 @@ fh_status synth_common(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int
     FH_TRY(ensure(ctx, ctx->d_Gr, (size_t)pb.J * n_T * sizeof(double)));
     FH_TRY(ensure(ctx, ctx->d_Gm, (size_t)pb.J * n_T * sizeof(double)));
     {
-        PhaseScope ps(ctx, FH_PH_WEIGHTS, 1);
+        PhaseScope ps(ctx, FH_PH_WEIGHTS, 2);
+        FH_TRY(ensure(ctx, ctx->d_Bf, (size_t)pb.K * pb.J * sizeof(float4)));
         fh::launch_synth_weights(pb.J, pb.M, pb.W, pb.K, pb.d_s.as<double>(), pb.d_B.as<double2>(),
-                                 ctx->d_nu_f.as<float4>() + pb.nu_off,
+                                 ctx->d_Bf.as<float4>(), ctx->d_nu_f.as<float4>() + pb.nu_off,
                                  ctx->d_ph.as<double2>() + pb.ph_off, d_T, n_T,
                                  ctx->d_Gr.as<double>(), ctx->d_Gm.as<double>(), ctx->stream);
         FH_TRY(check_launch(ctx, "synthesis weights"));

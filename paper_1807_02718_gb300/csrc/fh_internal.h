@@ -133,8 +133,10 @@ constexpr int kFarTerms = 170;
 void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, double2 *phase_tab,
                       cudaStream_t st);
 // Gr/Gm: planes [p][t] with u(x,t) = sum_p Vr[p][x] Gr[p][t] + Vi[p][x] Gm[p][t].
+// Bf: optional scratch of K * J float4 for the double-float copy of B (one
+// extra launch); null splits B on the fly.
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
-                          const float4 *nu_f, const double2 *phase_tab, const double *T,
+                          float4 *Bf, const float4 *nu_f, const double2 *phase_tab, const double *T,
                           int n_T, double *Gr, double *Gm, cudaStream_t st);
 // double_float: operands split into FP32 pairs, products exact, double-float
 // accumulation (mixed-precision paths); else FP64 FMAs.

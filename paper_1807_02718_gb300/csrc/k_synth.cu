@@ -115,6 +115,32 @@ __device__ __forceinline__ void df_mac(float &sh, float &sl, dfl a, dfl b) {
     sh = t;
 }
 
+// a * b in double-float, renormalised
+__device__ __forceinline__ dfl df_mulq(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float h = p + e;
+    return {h, e - (h - p)};
+}
+
+// a + b and 1 / a in double-float, renormalised
+__device__ __forceinline__ dfl df_addq(dfl a, dfl b) {
+    const float sum = a.hi + b.hi;
+    const float bb = sum - a.hi;
+    const float e = ((a.hi - (sum - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    const float h = sum + e;
+    return {h, e - (h - sum)};
+}
+
+__device__ __forceinline__ dfl df_rcpq(dfl a) {
+    const float r = 1.0f / a.hi;
+    const float t = fmaf(-a.hi, r, 1.0f) - a.lo * r;
+    const float h = r + r * t;
+    return {h, r * t - (h - r)};
+}
+
 // a * r + v in double-float (r, v double-float; a updated)
 __device__ __forceinline__ void df_horner(float &ah, float &al, dfl r, float vh, float vl) {
     const float p = ah * r.hi;
@@ -136,13 +162,14 @@ __device__ __forceinline__ void df_horner(float &ah, float &al, dfl r, float vh,
 // far windows: Horner in double-float over the double-float copy of nu.
 __global__ void __launch_bounds__(256) weights_kernel(
     int J, int M, double W, int K, const double *__restrict__ s, const double2 *__restrict__ B,
-    const float4 *__restrict__ nu_f, const double2 *__restrict__ ph_g,
+    const float4 *__restrict__ Bf, const float4 *__restrict__ nu_f, const double2 *__restrict__ ph_g,
     const double *__restrict__ T, int n_T, double *__restrict__ Gr, double *__restrict__ Gm) {
     extern __shared__ double smd[];
     double *wy = smd;                                        // K: y
     double *wf = wy + K;                                     // K: sin(pi y) (near) or scale sinc(y) (far)
-    float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: h / y as double-float
-    int *wR = reinterpret_cast<int *>(wrho + K);             // K: far terms, 0 = near
+    float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: h / y (far) or 2W/M (near), double-float
+    float2 *wfd = wrho + K;                                  // K: scale sinc(y) (far), double-float
+    int *wR = reinterpret_cast<int *>(wfd + K);              // K: far terms, 0 = near
     float2 *phc = reinterpret_cast<float2 *>(wR + ((K + 1) & ~1));   // M: cos (hi, lo)
     float2 *phs = phc + M;                                   // M: sin (hi, lo)
     float2 *sc = phs + M;                                    // M: sinc (hi, lo)
@@ -164,6 +191,8 @@ __global__ void __launch_bounds__(256) weights_kernel(
         if (fabs(y) < 1.25 * (double)h) {
             wf[k] = sy;
             wR[k] = 0;
+            const dfl sd = df_split(scale);
+            wrho[k] = make_float2(sd.hi, sd.lo);
         } else {
             const double rho = (double)h / y;
             const int R = (int)ceil(-48.0 * 0.69314718055994531 / log(fabs(rho)));
@@ -171,42 +200,73 @@ __global__ void __launch_bounds__(256) weights_kernel(
             const dfl rr = df_split(rho);
             wrho[k] = make_float2(rr.hi, rr.lo);
             wf[k] = scale * sy / (kPi * y);
+            const dfl fd = df_split(wf[k]);
+            wfd[k] = make_float2(fd.hi, fd.lo);
         }
     }
     __syncthreads();
-    double qr = 0.0, qi = 0.0;
+    // G accumulates in double-float: q += B_k(w_p) D_p(t - s_k)
+    float qrh = 0.f, qrl = 0.f, qih = 0.f, qil = 0.f;
     for (int k = 0; k < K; ++k) {
         const int R = wR[k];
-        double dr = 0.0, di = 0.0;
+        dfl dr = {0.f, 0.f}, di = {0.f, 0.f};
         if (R == 0) {                 // near window (the same branch in the whole CTA)
-            const double y = wy[k], sy = wf[k];
+            // D_p = (2W/M) [S(y) + (-1)^p S(y+h) + sum_{j=1}^{h-1} (cos_j (S(y-j) + S(y+j))
+            //        + i sin_j (S(y-j) - S(y+j)))], S(v) = sinc(v), (cos_j, sin_j) the phase
+            //        e^{-2 pi i j p / M} (its conjugate pairs -j with j)
+            const double y = wy[k];
+            const dfl sypi = df_split(wf[k] * (1.0 / kPi));   // sin(pi y) / pi
             __syncthreads();
-            for (int m = threadIdx.x; m < M; m += blockDim.x) {
-                const int jj = m - h;
-                const double d = y - (double)jj;
-                const double v = (d == 0.0) ? 1.0 : ((jj & 1) ? -sy : sy) / (kPi * d);
-                const dfl vv = df_split(v);
-                sc[m] = make_float2(vv.hi, vv.lo);
+            for (int jj = threadIdx.x; jj < h + 1; jj += blockDim.x) {
+                // jj = 0: S(y) and S(y + h) into slot 0; jj >= 1: S(y - jj) +- S(y + jj)
+                const int ja = jj == 0 ? 0 : jj, jb = jj == 0 ? h : jj;
+                dfl va, vb;
+                {
+                    const double d = y - (double)ja;
+                    if (d == 0.0) va = {1.f, 0.f};
+                    else {
+                        va = df_mulq(sypi, df_rcpq(df_split(d)));
+                        if (ja & 1) va = {-va.hi, -va.lo};
+                    }
+                }
+                {
+                    const double d = y + (double)jb;
+                    if (d == 0.0) vb = {1.f, 0.f};
+                    else {
+                        vb = df_mulq(sypi, df_rcpq(df_split(d)));
+                        if (jb & 1) vb = {-vb.hi, -vb.lo};
+                    }
+                }
+                if (jj == 0) {
+                    sc[0] = make_float2(va.hi, va.lo);      // S(y)
+                    sc[h] = make_float2(vb.hi, vb.lo);      // S(y + h)
+                } else if (jj < h) {
+                    const dfl sp = df_addq(va, vb), sm = df_addq(va, {-vb.hi, -vb.lo});
+                    sc[jj] = make_float2(sp.hi, sp.lo);
+                    sc[h + jj] = make_float2(sm.hi, sm.lo);
+                }
             }
             __syncthreads();
             if (p < J) {
-                float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-                int q = (int)((((long long)(-h) % M + M) % M) * p % M);
-                for (int m = 0; m < M; ++m) {
-                    const float2 v2 = sc[m];
+                const float2 s0 = sc[0], shh = sc[h];
+                const dfl r0 = df_addq({s0.x, s0.y}, (p & 1) ? dfl{-shh.x, -shh.y} : dfl{shh.x, shh.y});
+                float rh = r0.hi, rl = r0.lo, ih = 0.f, il = 0.f;
+                int q = p;
+                for (int jj = 1; jj < h; ++jj) {
                     const float2 c2 = phc[q], s2 = phs[q];
-                    const dfl v = {v2.x, v2.y};
-                    df_mac(rh, rl, {c2.x, c2.y}, v);
-                    df_mac(ih, il, {s2.x, s2.y}, v);
+                    const float2 a2 = sc[jj], b2 = sc[h + jj];
+                    df_mac(rh, rl, {c2.x, c2.y}, {a2.x, a2.y});
+                    df_mac(ih, il, {s2.x, s2.y}, {b2.x, b2.y});
                     q += p;
                     if (q >= M) q -= M;
-                    if ((m & 31) == 31) {   // renormalise the accumulators
+                    if ((jj & 31) == 31) {   // renormalise the accumulators
                         float tr = rh + rl; rl = rl - (tr - rh); rh = tr;
                         float ti = ih + il; il = il - (ti - ih); ih = ti;
                     }
                 }
-                dr = scale * ((double)rh + (double)rl);
-                di = scale * ((double)ih + (double)il);
+                const float2 sd = wrho[k];   // 2W/M
+                dr = df_mulq({rh, rl}, {sd.x, sd.y});
+                di = df_mulq({ih, il}, {sd.x, sd.y});
             }
         } else if (p < J) {
             const float2 r2 = wrho[k];
@@ -217,22 +277,44 @@ __global__ void __launch_bounds__(256) weights_kernel(
                 df_horner(ah, al, rho, v.x, v.y);
                 df_horner(bh, bl, rho, v.z, v.w);
             }
-            const double f = wf[k];
-            dr = f * ((double)ah + (double)al);
-            di = f * ((double)bh + (double)bl);
+            const float2 f2 = wfd[k];
+            const dfl f = {f2.x, f2.y};
+            dr = df_mulq({ah, al}, f);
+            di = df_mulq({bh, bl}, f);
         }
         if (p < J) {
-            const double2 b = B[(long long)k * J + p];
-            qr += b.x * dr - b.y * di;
-            qi += b.x * di + b.y * dr;
+            dfl br, bi;
+            if (Bf) {
+                const float4 b4 = Bf[(long long)k * J + p];
+                br = {b4.x, b4.y};
+                bi = {b4.z, b4.w};
+            } else {
+                const double2 b = B[(long long)k * J + p];
+                br = df_split(b.x);
+                bi = df_split(b.y);
+            }
+            // q += b * d (complex)
+            df_mac(qrh, qrl, br, dr);
+            df_mac(qrh, qrl, {-bi.hi, -bi.lo}, di);
+            df_mac(qih, qil, br, di);
+            df_mac(qih, qil, bi, dr);
         }
     }
     if (p < J) {
         const double mu = (p == 0 || p == J - 1) ? 1.0 : 2.0;
         const double c = mu / (2.0 * kPi);
-        Gr[(long long)p * n_T + t] = c * qr;
-        Gm[(long long)p * n_T + t] = -c * qi;
+        Gr[(long long)p * n_T + t] = c * ((double)qrh + (double)qrl);
+        Gm[(long long)p * n_T + t] = -c * ((double)qih + (double)qil);
     }
+}
+
+// Split a complex FP64 table into double-float pairs (re hi, re lo, im hi, im lo).
+__global__ void split_df_kernel(const double2 *__restrict__ B, float4 *__restrict__ Bf, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 b = B[i];
+    const dfl r = df_split(b.x), m = df_split(b.y);
+    Bf[i] = make_float4(r.hi, r.lo, m.hi, m.lo);
 }
 
 constexpr int BM = 64, BN = 64, BK = 16;
@@ -380,18 +462,22 @@ void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, doubl
 }
 
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
-                          const float4 *nu_f, const double2 *phase_tab, const double *T,
+                          float4 *Bf, const float4 *nu_f, const double2 *phase_tab, const double *T,
                           int n_T, double *Gr, double *Gm, cudaStream_t st) {
     if (n_T <= 0) return;
-    const size_t smem = (size_t)K * (2 * sizeof(double) + sizeof(float2)) +
+    const size_t smem = (size_t)K * (2 * sizeof(double) + 2 * sizeof(float2)) +
                         (size_t)((K + 1) & ~1) * sizeof(int) + (size_t)M * 3 * sizeof(float2);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
+    if (Bf) {
+        const long long n = (long long)K * J;
+        split_df_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, Bf, n);
+    }
     dim3 grid(n_T, (J + 255) / 256);
-    weights_kernel<<<grid, 256, smem, st>>>(J, M, W, K, s, B, nu_f, phase_tab, T, n_T, Gr, Gm);
+    weights_kernel<<<grid, 256, smem, st>>>(J, M, W, K, s, B, Bf, nu_f, phase_tab, T, n_T, Gr, Gm);
 }
 
 void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,
