@@ -88,8 +88,9 @@ struct fh_ctx {
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_solve_prob, d_order, d_curves, d_pdir;
     DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_nu_f, d_ph, d_omega, d_pw;
-    DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk, d_Bf;
-    int n_rchunk = 0;
+    DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk, d_Bf, d_dblk,
+        d_blk_off, d_dinv;
+    int n_rchunk = 0, n_dblk = 0;
     DevBuf d_wa, d_a;
     int n_x_last = 0;
     DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm;
@@ -117,7 +118,7 @@ struct fh_ctx {
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_A32, &d_piv, &d_g, &d_iters,
-                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
+                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
         for (DevBuf *b : all) free_buf(*b);
         free_problems();
@@ -416,6 +417,15 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
         for (int r0 = 0; r0 < ctx->solve_N[s]; r0 += fh::kResidRows) rchunk.push_back(make_int2(s, r0));
     ctx->n_rchunk = (int)rchunk.size();
     FH_TRY(upload(ctx, ctx->d_rchunk, rchunk));
+    std::vector<int2> dblk;     // (solve, 32-row block) of each diagonal block
+    std::vector<int> blk_off(S);
+    for (int s = 0; s < S; ++s) {
+        blk_off[s] = (int)dblk.size();
+        for (int b = 0; b * 32 < ctx->solve_N[s]; ++b) dblk.push_back(make_int2(s, b));
+    }
+    ctx->n_dblk = (int)dblk.size();
+    FH_TRY(upload(ctx, ctx->d_dblk, dblk));
+    FH_TRY(upload(ctx, ctx->d_blk_off, blk_off));
 
     std::vector<double> omega_v(omega_all, omega_all + jo);
     FH_TRY(upload(ctx, ctx->d_N, ctx->solve_N));
@@ -710,9 +720,10 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         FH_TRY(ensure(ctx, ctx->d_resid, (size_t)ctx->S * sizeof(double)));
         FH_TRY(ensure(ctx, ctx->d_y32, (size_t)ctx->vec_total * sizeof(float2)));
         FH_TRY(ensure(ctx, ctx->d_rstate, fh::refine_state_bytes(ctx->S)));
-        // launches: conversion, one LU launch per cluster size (SIMT: one), and
-        // the refinement's set-up, two kernels per sweep and the verdict
-        PhaseScope ps(ctx, FH_PH_FACTOR, 1 + (tc ? fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S) : 1) +
+        // launches: conversion, one LU launch per cluster size and the
+        // diagonal-block inverses (SIMT: one LU launch), and the refinement's
+        // set-up, two kernels per sweep and the verdict
+        PhaseScope ps(ctx, FH_PH_FACTOR, 1 + (tc ? 1 + fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S) : 1) +
                                              2 + 2 * kRefineMaxIters);
         if (tc) {
             FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
@@ -734,9 +745,12 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
                                       ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
                                       ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
         }
+        if (tc) FH_TRY(ensure(ctx, ctx->d_dinv, (size_t)ctx->n_dblk * 2048 * sizeof(float2)));
         fh::launch_lu_refine(tc, ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                              ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
-                             ctx->d_rchunk.as<int2>(), ctx->n_rchunk, ctx->d_A.as<double2>(),
+                             ctx->d_rchunk.as<int2>(), ctx->n_rchunk, ctx->d_dblk.as<int2>(),
+                             ctx->n_dblk, ctx->d_blk_off.as<int>(), ctx->d_dinv.as<float2>(),
+                             ctx->d_A.as<double2>(),
                              ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_g.as<double2>(),
                              ctx->d_psi.as<double2>(), ctx->d_y32.as<float2>(), ctx->d_rstate.p,
                              kRefineMaxIters, kRefineTol, ctx->d_iters.as<int>(),
@@ -1026,6 +1040,8 @@ fh_status fh_footprint(const int *J, const int *N, int P, int precision, long lo
             const long long n = N[jo + j];
             b += n * n * 16 + n * (16 * 4 + 16 + 8);          // matrix, nodes, density, tables
             if (precision != FH_FP64) b += n * n * 8 + n * (16 + 4 + 8);   // FP32 copy, rhs, perm, FP32 rhs
+            if (precision == FH_MIXED_TF32 || precision == FH_MIXED_BF16)
+                b += (n + 31) / 32 * 2048 * 8;                            // diagonal-block inverses
         }
         b += (long long)fh::kFarTerms * J[q] * 16 + 2LL * (J[q] - 1) * 16;
         jo += J[q];

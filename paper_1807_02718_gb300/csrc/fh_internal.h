@@ -93,9 +93,13 @@ cudaError_t launch_lu_factor_tc(int kind, const int *order, const int *order_h, 
 // refine_state_bytes(S) bytes; y32 one FP32 complex per unknown.
 constexpr int kResidRows = 64;
 size_t refine_state_bytes(int S);
+// Row-major factors: blocks lists (solve, 32-row block) for the diagonal-block
+// inverses, blk_off the first block of each solve, inv 2048 FP32 complex per
+// block (scratch).
 void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
                       const long long *mat_off, const int *vec_off, const int2 *chunks,
-                      int n_chunks, const double2 *A, const float2 *LU32, const int *piv,
+                      int n_chunks, const int2 *blocks, int n_blocks, const int *blk_off,
+                      float2 *inv, const double2 *A, const float2 *LU32, const int *piv,
                       const double2 *g, double2 *x, float2 *y32, void *state, int max_iters,
                       double tol, int *iters, double *resid, int *info, int maxN, cudaStream_t st);
 

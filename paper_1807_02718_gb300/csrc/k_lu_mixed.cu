@@ -276,6 +276,120 @@ __device__ void lu_solve_shared(const float2 *__restrict__ a, int n, float2 *y) 
 #undef AT
 }
 
+// Inverses of the 32 x 32 diagonal blocks of row-major factors, computed once
+// per factorisation: one CTA (two warps) per block; warp 0 inverts the unit
+// lower triangle, warp 1 the upper one, lane j solving for column j; the
+// inverses are stored row-major, L^{-1} then U^{-1}, 2048 values per block.
+// A partial last block is padded with the identity.
+__global__ void __launch_bounds__(64) diag_inverse_kernel(const int2 *__restrict__ blocks,
+                                                          const int *__restrict__ Ns,
+                                                          const long long *__restrict__ mat_off,
+                                                          const int *__restrict__ blk_off,
+                                                          const float2 *__restrict__ LU32,
+                                                          float2 *__restrict__ inv) {
+    const int2 bk = blocks[blockIdx.x];
+    const int s = bk.x, b = bk.y, n = Ns[s], jb = 32 * b, nbv = min(32, n - jb);
+    const float2 *a = LU32 + mat_off[s];
+    __shared__ float2 D[32][33];
+    __shared__ float2 T[2][32][33];
+    const int tid = threadIdx.x, w = tid >> 5, j = tid & 31;
+    for (int e = tid; e < 1024; e += 64) {
+        const int i = e >> 5, q = e & 31;
+        D[i][q] = (i < nbv && q < nbv) ? a[(long long)(jb + i) * n + jb + q]
+                                       : make_float2(i == q ? 1.f : 0.f, 0.f);
+    }
+    __syncthreads();
+    float2 x[32];
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            float2 v = make_float2(i == j ? 1.f : 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < i; ++k) {
+                const float2 l = D[i][k];
+                v.x -= l.x * x[k].x - l.y * x[k].y;
+                v.y -= l.x * x[k].y + l.y * x[k].x;
+            }
+            x[i] = v;
+        }
+    } else {
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {
+            float2 v = make_float2(i == j ? 1.f : 0.f, 0.f);
+#pragma unroll
+            for (int k = i + 1; k < 32; ++k) {
+                const float2 u = D[i][k];
+                v.x -= u.x * x[k].x - u.y * x[k].y;
+                v.y -= u.x * x[k].y + u.y * x[k].x;
+            }
+            const float2 d = D[i][i];
+            const float rd = 1.f / (d.x * d.x + d.y * d.y);
+            x[i] = make_float2((v.x * d.x + v.y * d.y) * rd, (v.y * d.x - v.x * d.y) * rd);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) T[w][i][j] = x[i];
+    __syncthreads();
+    float2 *dst = inv + (long long)(blk_off[s] + b) * 2048;
+    for (int e = tid; e < 2048; e += 64) {
+        const int ww = e >> 10, i = (e >> 5) & 31, q = e & 31;
+        dst[e] = T[ww][i][q];
+    }
+}
+
+// Row-major factors (tensor-core LU): blocked substitution in which each
+// 32-row diagonal step is a product with the precomputed block inverse (one
+// warp, no dependent chain) and the off-diagonal updates use 16-byte loads
+// of the row segments; written for blockDim = 512.
+__device__ void lu_solve_rowmajor(const float2 *__restrict__ a, int n, const float2 *__restrict__ inv,
+                                  float2 *y) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nblk = (n + 31) / 32;
+    for (int pass = 0; pass < 2; ++pass) {           // 0: L (forward), 1: U (backward)
+        for (int bi = 0; bi < nblk; ++bi) {
+            const int b = pass == 0 ? bi : nblk - 1 - bi;
+            const int jb = b * 32, je = min(jb + 32, n);
+            if (tid < 32) {
+                const float4 *row = reinterpret_cast<const float4 *>(inv + (long long)b * 2048 + pass * 1024 + lane * 32);
+                float4 v[16];
+#pragma unroll
+                for (int h = 0; h < 16; ++h) v[h] = row[h];
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < 16; ++h) {
+                    const int q = jb + 2 * h;
+                    if (q < je) {
+                        const float2 y0 = y[q], y1 = y[q + 1];
+                        acc.x += v[h].x * y0.x - v[h].y * y0.y + v[h].z * y1.x - v[h].w * y1.y;
+                        acc.y += v[h].x * y0.y + v[h].y * y0.x + v[h].z * y1.y + v[h].w * y1.x;
+                    }
+                }
+                __syncwarp();
+                if (jb + lane < je) y[jb + lane] = acc;
+            }
+            __syncthreads();
+            const int r0 = pass == 0 ? je : 0, r1 = pass == 0 ? n : jb;
+            for (int i = r0 + tid; i < r1; i += blockDim.x) {
+                float2 yi = y[i];
+                const float4 *src = reinterpret_cast<const float4 *>(a + (long long)i * n + jb);
+                float4 l[16];
+#pragma unroll
+                for (int h = 0; h < 16; ++h)
+                    if (jb + 2 * h < je) l[h] = src[h];
+#pragma unroll
+                for (int h = 0; h < 16; ++h)
+                    if (jb + 2 * h < je) {
+                        const float2 y0 = y[jb + 2 * h], y1 = y[jb + 2 * h + 1];
+                        yi.x -= l[h].x * y0.x - l[h].y * y0.y + l[h].z * y1.x - l[h].w * y1.y;
+                        yi.y -= l[h].x * y0.y + l[h].y * y0.x + l[h].z * y1.y + l[h].w * y1.x;
+                    }
+                y[i] = yi;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __device__ double block_max(double v, double *red) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -299,7 +413,7 @@ __global__ void __launch_bounds__(256) refine_setup_kernel(
     const int *__restrict__ Ns, const int *__restrict__ vec_off, const int *__restrict__ piv,
     const double2 *__restrict__ G, double2 *__restrict__ X, float2 *__restrict__ Y32,
     RefineState *__restrict__ st, int *__restrict__ iters, const int *__restrict__ info) {
-    __shared__ double red[8];
+    __shared__ double red[32];
     const int s = blockIdx.x, n = Ns[s], vo = vec_off[s];
     double gmax = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -323,13 +437,14 @@ __global__ void __launch_bounds__(256) refine_setup_kernel(
 
 // Sweep `it`: stop if sweep it-1 converged; else d = (LU)^{-1} y, x += d.
 template <bool kRowMajor>
-__global__ void __launch_bounds__(256) refine_solve_kernel(
+__global__ void __launch_bounds__(kRowMajor ? 512 : 256) refine_solve_kernel(
     const int *__restrict__ order, const int *__restrict__ Ns, const long long *__restrict__ mat_off,
-    const int *__restrict__ vec_off, const float2 *__restrict__ LU32, double2 *__restrict__ X,
+    const int *__restrict__ vec_off, const float2 *__restrict__ LU32, const float2 *__restrict__ inv,
+    const int *__restrict__ blk_off, double2 *__restrict__ X,
     const float2 *__restrict__ Y32, RefineState *__restrict__ st, int it, double tol,
     int *__restrict__ iters) {
     extern __shared__ float2 ys[];
-    __shared__ double red[8];
+    __shared__ double red[32];
     const int s = order[blockIdx.x];
     RefineState *rs = st + s;
     if (rs->conv) return;
@@ -340,7 +455,8 @@ __global__ void __launch_bounds__(256) refine_solve_kernel(
     const int n = Ns[s], vo = vec_off[s];
     for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = Y32[vo + i];
     __syncthreads();
-    lu_solve_shared<kRowMajor>(LU32 + mat_off[s], n, ys);
+    if (kRowMajor) lu_solve_rowmajor(LU32 + mat_off[s], n, inv + (long long)blk_off[s] * 2048, ys);
+    else lu_solve_shared<false>(LU32 + mat_off[s], n, ys);
     double dmax = 0.0, xmax = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float2 d = ys[i];
@@ -372,7 +488,7 @@ __global__ void __launch_bounds__(256) refine_resid_kernel(
     RefineState *__restrict__ st) {
     extern __shared__ double2 xs[];
     __shared__ double2 part[4][kResidRows];
-    __shared__ double red[8];
+    __shared__ double red[32];
     const int2 ch = chunks[blockIdx.x];
     const int s = ch.x, r0 = ch.y;
     if (st[s].conv) return;
@@ -450,7 +566,8 @@ size_t refine_state_bytes(int S) { return (size_t)S * sizeof(RefineState); }
 
 void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
                       const long long *mat_off, const int *vec_off, const int2 *chunks,
-                      int n_chunks, const double2 *A, const float2 *LU32, const int *piv,
+                      int n_chunks, const int2 *blocks, int n_blocks, const int *blk_off,
+                      float2 *inv, const double2 *A, const float2 *LU32, const int *piv,
                       const double2 *g, double2 *x, float2 *y32, void *state, int max_iters,
                       double tol, int *iters, double *resid, int *info, int maxN, cudaStream_t st) {
     if (S <= 0) return;
@@ -462,14 +579,16 @@ void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
         cudaFuncSetAttribute(refine_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
+    if (row_major)
+        diag_inverse_kernel<<<n_blocks, 64, 0, st>>>(blocks, N, mat_off, blk_off, LU32, inv);
     refine_setup_kernel<<<S, 256, 0, st>>>(N, vec_off, piv, g, x, y32, rs, iters, info);
     for (int it = 1; it <= max_iters; ++it) {
         if (row_major)
-            refine_solve_kernel<true><<<S, 256, (size_t)maxN * sizeof(float2), st>>>(
-                order, N, mat_off, vec_off, LU32, x, y32, rs, it, tol, iters);
+            refine_solve_kernel<true><<<S, 512, (size_t)maxN * sizeof(float2), st>>>(
+                order, N, mat_off, vec_off, LU32, inv, blk_off, x, y32, rs, it, tol, iters);
         else
             refine_solve_kernel<false><<<S, 256, (size_t)maxN * sizeof(float2), st>>>(
-                order, N, mat_off, vec_off, LU32, x, y32, rs, it, tol, iters);
+                order, N, mat_off, vec_off, LU32, inv, blk_off, x, y32, rs, it, tol, iters);
         refine_resid_kernel<<<n_chunks, 256, (size_t)maxN * sizeof(double2), st>>>(
             chunks, N, mat_off, vec_off, A, piv, g, x, y32, rs);
     }
