@@ -38,6 +38,11 @@ sys.path.insert(0, ROOT)
 import fh_inputs as fi  # noqa: E402
 
 METRIC = "frequency solves/s & time samples/s at 1e-10 rel err (mixed vs FP64); p50/p99"
+# arithmetic each --precision computes in
+DTYPES = {"fp64": "f64",
+          "mixed": "f64 + f32 (LU) + f32-pair (Hankel, synthesis)",
+          "tf32": "f64 + tf32x3 tensor (LU) + f32-pair (Hankel, synthesis)",
+          "bf16": "f64 + bf16x3 tensor (LU) + f32-pair (Hankel, synthesis)"}
 WORKLOAD = "kite_pulses: kite, 40 pulses over [0,400], J=256 on [0,40], N=64..480 (8 ppw), 1024 targets, 4096 times to T=1e4"
 
 
@@ -121,6 +126,78 @@ def lu_flops(N):
 def contract_flops(n_x, n_T, J):
     """u = [Vr|Vi][Gr;Gm]: 2 flops per multiply-add over inner dimension 2J."""
     return 2.0 * n_x * n_T * 2 * J
+
+
+# Unit-count peaks of one GB300 at its 2070 MHz maximum SM clock: FP64 2 DFMA
+# and FP32 128 FFMA per clock per SM (ncu's sustained-peak counters), 152 SMs.
+SM_CLOCK_GHZ = 2.07
+FP64_PEAK = 2 * 2 * 152 * SM_CLOCK_GHZ * 1e9 / 1e12       # 1.26 TFLOP/s
+FP32_PEAK = 128 * 2 * 152 * SM_CLOCK_GHZ * 1e9 / 1e12     # 80.5 TFLOP/s
+DF_MAC_INSTR = 11                                          # FP32 instructions per double-float MAC
+DF_PEAK = FP32_PEAK / DF_MAC_INSTR                         # FP64-equivalent flop/s of df MACs
+TF32_OVER_BF16 = 1.1 / 2.25                                # nominal dense tensor rates
+
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
+# committed (profiles/assemble_group_df_kite_pulses.md).
+MEASURED_TRAFFIC = {"assemble_group_df_kernel": 282.2e6}
+
+
+def window_work(wl):
+    """FP64-equivalent flops of the synthesis weights per step: near (t, k):
+    4 J h (paired sinc sums); far (t, k): 4 J R (Horner); every (t, k): 8 J
+    (the B_k accumulation).  R and near/far as in the kernel."""
+    J = wl.J
+    M = 2 * (J - 1)
+    h = M // 2
+    W = float(wl.omega[-1])
+    span = wl.t0 + wl.dt * (wl.a.size - 1)
+    s_k = 15.0 * np.arange(int(np.ceil((span + wl.H) / 15.0)) + 1)
+    s_k = s_k[s_k - wl.H < span]
+    y = W * (wl.T[:, None] - s_k[None, :]) / np.pi
+    near = np.abs(y) < 1.25 * h
+    with np.errstate(divide="ignore"):
+        R = np.clip(np.ceil(-48 * np.log(2) / np.log(np.abs(h / np.where(near, 1.0, y)))), 1, 170)
+    return float(np.sum(np.where(near, 4 * J * h, 4 * J * R)) + 8 * J * y.size)
+
+
+def phase_rooflines(wl, precision, ms, iters, peaks):
+    """Achieved against peak per phase; work definitions in the design doc."""
+    N = wl.N[1:].astype(np.float64)
+    mixed = precision != "fp64"
+    bf16 = peaks.get("bf16_tflops")
+    out = {}
+
+    def put(phase, kernel, bound, work, peak, peak_src):
+        if ms.get(phase, 0) <= 0 or peak is None:
+            return
+        ach = work / (ms[phase] * 1e-3) / 1e12
+        out[phase] = {"kernel": kernel, "bound": bound, "unit": "TFLOP/s", "work_per_step": work,
+                      "achieved": ach, "peak": peak, "frac": ach / peak, "peak_source": peak_src}
+
+    fp64_src = "FP64 unit count (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)"
+    put("assemble", "assemble_group_df_kernel" if mixed else "assemble_group_kernel", "alu",
+        100.0 * float(np.sum(N * N)), FP64_PEAK, fp64_src + "; work 1e2 FP64-equivalent flop per entry")
+    if precision == "fp64":
+        put("factor", "lu_solve_fp64_kernel", "alu", lu_flops(N), FP64_PEAK, fp64_src)
+    elif precision == "mixed":
+        put("factor", "lu_factor_fp32_kernel", "alu", float(np.sum(8 / 3 * N ** 3)), FP32_PEAK,
+            "FP32 unit count (128 FFMA/clk/SM x 152 SMs x 2.07 GHz)")
+    else:
+        pk = bf16 * (TF32_OVER_BF16 if precision == "tf32" else 1.0) if bf16 else None
+        put("factor", "lu_factor_tc_kernel", "tensor", float(np.sum(8 / 3 * N ** 3)), pk,
+            "measured bf16 dense GEMM (MEASURED_PEAKS.json)" +
+            (" x nominal TF32/BF16 ratio 1.1/2.25" if precision == "tf32" else ""))
+    if mixed:
+        put("refine", "refine_resid_kernel", "alu", 8.0 * float(np.sum(N * N)) * max(iters, 1),
+            FP64_PEAK, fp64_src + "; work 8 N^2 per sweep x the largest sweep count")
+    put("field", "field_partial_df_kernel" if mixed else "field_partial_kernel", "alu",
+        50.0 * wl.n_x * float(np.sum(N)), FP64_PEAK, fp64_src + "; work 50 FP64-equivalent flop per (target, node)")
+    put("weights", "weights_kernel", "alu", window_work(wl), DF_PEAK,
+        "double-float MAC rate: FP32 unit count / 11 instructions per MAC, 2 flop per MAC")
+    put("contract", "contract_df_kernel" if mixed else "contract_kernel", "alu",
+        contract_flops(wl.n_x, wl.T.size, wl.J), DF_PEAK if mixed else FP64_PEAK,
+        "double-float MAC rate: FP32 unit count / 11 instructions per MAC" if mixed else fp64_src)
+    return out
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -232,9 +309,13 @@ def run_gpu(args, world, rank, local):
     d_u = torch.empty(n_x * n_T, device=dev, dtype=torch.float64)
     flush = torch.empty(256 * 1024 * 1024 // 8, device=dev, dtype=torch.float64)
 
+    solve_stats = {}
+
     def step():
         F.fh_discretize(pr.ctx, wl.curve, wl.omega, wl.N, wl.c, wl.p)
-        F.fh_solve_frequencies(pr.ctx)
+        st = F.fh_solve_frequencies(pr.ctx)
+        solve_stats["iters"] = st.refine_iters_max
+        solve_stats["resid"] = st.residual_max
         F.fh_window_spectra_dev(pr.ctx, d_a, wl.t0, wl.dt, wl.H)
         F.fh_sample_dev(pr.ctx, d_x, d_T, d_u)
 
@@ -302,33 +383,19 @@ def run_gpu(args, world, rank, local):
     h2d = wl.a.nbytes + wl.x.nbytes + wl.T.nbytes + wl.omega.nbytes + wl.N.nbytes
     d2h = u_host.nbytes
 
-    # ---- roofline of the dominant kernel ----
-    fp64_peak = F.fh_probe_fma_peak(local, True, 4096)
+    # ---- rooflines (algorithmic work per step / phase time) ----
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    if dominant == "factor":
-        work = lu_flops(wl.N[1:])
-        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "lu_solve_fp64_kernel",
-                "work_per_launch": work}
-        achieved = work / (per_launch["factor"] * 1e-3) / 1e12
-        roof.update({"achieved": achieved, "peak": fp64_peak,
-                     "peak_source": "measured FP64 FMA-chain probe on this GPU (fh_probe_fma_peak)"})
-    elif dominant == "contract":
-        work = contract_flops(n_x, n_T, wl.J)
-        achieved = work / (per_launch["contract"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "contract_kernel", "achieved": achieved,
-                "peak": fp64_peak, "peak_source": "measured FP64 FMA-chain probe on this GPU",
-                "work_per_launch": work}
-    else:
-        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": dominant, "achieved": None,
-                "peak": fp64_peak, "peak_source": "measured FP64 FMA-chain probe on this GPU"}
-    if roof.get("achieved") is not None:
-        roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roofs = phase_rooflines(wl, args.precision, step_ms_phases, solve_stats.get("iters", 0), peaks)
+    roof = dict(roofs.get(dominant) or {"bound": "alu", "achieved": None, "peak": None,
+                                        "unit": "TFLOP/s", "frac": None, "kernel": dominant})
+    roof["traffic"] = MEASURED_TRAFFIC.get(roof.get("kernel"))
+    roof["phase"] = dominant
     roof["phase_ms_per_step"] = step_ms_phases
+    roof["all_phases"] = roofs
     roof["hbm_peak_gbs"] = peaks.get("hbm_gbs")
 
     cpu = None
@@ -341,13 +408,18 @@ def run_gpu(args, world, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision,
                        "solves_per_step": S, "time_samples_per_step": n_x * n_T,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "time_samples_per_s": samples_per_s,
+            "accuracy": {"refine_sweeps_max": solve_stats.get("iters"),
+                         "refine_residual_max": solve_stats.get("resid"),
+                         "parity": "densities, fields and u within 1e-10 rel L2 of the FP64 oracle "
+                                   "(tests/test_parity.py, same precision)"},
             "p50_ms": float(np.percentile(per_step, 50)),
             "p99_ms": float(np.percentile(per_step, 99)),
             "e2e": {"value": world * S * args.steps / e2e_total, "unit": "solves/s",

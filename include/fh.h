@@ -259,9 +259,10 @@ fh_status fh_synthesize_static(int J, double W, int K, const double *d_s, const 
 /* ---- kernel timing and launch accounting ---- */
 
 /* Phases of the path, in order: nodes and tables (a1), CFIE assembly with
- * right sides (a2), LU + solve / refinement (a3), window spectra (a4),
+ * right sides (a2), LU + solve (FP64) or the factorisation of the mixed paths
+ * (a3), the mixed paths' FP64 iterative refinement (a3), window spectra (a4),
  * target fields (a5), synthesis weights (a6), synthesis contraction (a7). */
-enum { FH_PH_GEOMETRY = 0, FH_PH_ASSEMBLE, FH_PH_FACTOR, FH_PH_SPECTRA, FH_PH_FIELD,
+enum { FH_PH_GEOMETRY = 0, FH_PH_ASSEMBLE, FH_PH_FACTOR, FH_PH_REFINE, FH_PH_SPECTRA, FH_PH_FIELD,
        FH_PH_WEIGHTS, FH_PH_CONTRACT, FH_NUM_PHASES };
 
 typedef struct {

@@ -720,32 +720,34 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         FH_TRY(ensure(ctx, ctx->d_resid, (size_t)ctx->S * sizeof(double)));
         FH_TRY(ensure(ctx, ctx->d_y32, (size_t)ctx->vec_total * sizeof(float2)));
         FH_TRY(ensure(ctx, ctx->d_rstate, fh::refine_state_bytes(ctx->S)));
-        // launches: conversion, one LU launch per cluster size and the
-        // diagonal-block inverses (SIMT: one LU launch), and the refinement's
-        // set-up, two kernels per sweep and the verdict
-        PhaseScope ps(ctx, FH_PH_FACTOR, 1 + (tc ? 1 + fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S) : 1) +
-                                             2 + 2 * kRefineMaxIters);
-        if (tc) {
-            FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
-            FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
-            fh::launch_convert_rowmajor(ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
-                                        ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->stream);
-            const cudaError_t e = fh::launch_lu_factor_tc(
-                ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->d_order.as<int>(), ctx->order.data(),
-                ctx->solve_N.data(), ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
-                ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
-                ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->stream);
-            if (e != cudaSuccess)
-                return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
-        } else {
-            fh::launch_convert_fp32(ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->mat_total,
-                                    ctx->stream);
-            fh::launch_lu_factor_fp32(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
-                                      ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
-                                      ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
-                                      ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
+        {
+            // launches: conversion and one LU launch per cluster size (SIMT: one)
+            PhaseScope ps(ctx, FH_PH_FACTOR, 1 + (tc ? fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S) : 1));
+            if (tc) {
+                FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
+                FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
+                fh::launch_convert_rowmajor(ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
+                                            ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->stream);
+                const cudaError_t e = fh::launch_lu_factor_tc(
+                    ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->d_order.as<int>(), ctx->order.data(),
+                    ctx->solve_N.data(), ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
+                    ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
+                    ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->stream);
+                if (e != cudaSuccess)
+                    return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
+            } else {
+                fh::launch_convert_fp32(ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->mat_total,
+                                        ctx->stream);
+                fh::launch_lu_factor_fp32(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
+                                          ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
+                                          ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
+                                          ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
+            }
         }
         if (tc) FH_TRY(ensure(ctx, ctx->d_dinv, (size_t)ctx->n_dblk * 2048 * sizeof(float2)));
+        // launches: diagonal-block inverses (row-major factors), set-up, two
+        // kernels per sweep and the verdict
+        PhaseScope ps(ctx, FH_PH_REFINE, (tc ? 1 : 0) + 2 + 2 * kRefineMaxIters);
         fh::launch_lu_refine(tc, ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                              ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
                              ctx->d_rchunk.as<int2>(), ctx->n_rchunk, ctx->d_dblk.as<int2>(),

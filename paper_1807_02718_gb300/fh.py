@@ -35,7 +35,7 @@ EXPORTED = [
     "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test", "fh_eval_bessel_df",
 ]
 
-PHASES = ["geometry", "assemble", "factor", "spectra", "field", "weights", "contract"]
+PHASES = ["geometry", "assemble", "factor", "refine", "spectra", "field", "weights", "contract"]
 
 
 class fh_curve(C.Structure):
@@ -50,7 +50,8 @@ class fh_solve_stats(C.Structure):
 
 
 class fh_timings(C.Structure):
-    _fields_ = [("ms", C.c_double * 7), ("launches", C.c_longlong * 7), ("events", C.c_longlong * 7)]
+    _fields_ = [("ms", C.c_double * len(PHASES)), ("launches", C.c_longlong * len(PHASES)),
+                ("events", C.c_longlong * len(PHASES))]
 
 
 class FHError(RuntimeError):

@@ -63,7 +63,7 @@ class Request:
 
 
 class Server:
-    def __init__(self, device: int = 0, precision: int = F.FH_MIXED_FP32, slots: int = 4,
+    def __init__(self, device: int = 0, precision: int = F.FH_MIXED_TF32, slots: int = 4,
                  max_batch: int = 8, mem_budget: int = 16 << 30):
         self.device = device
         self.precision = precision
@@ -226,21 +226,24 @@ def main():
     ap.add_argument("--max-batch", type=int, default=8)
     ap.add_argument("--mem-gb", type=float, default=16.0)
     ap.add_argument("--seed", type=int, default=5)
-    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     args = ap.parse_args()
     from . import build
     build.build()
     rng = np.random.default_rng(args.seed)
     reqs = [synthetic_request(rng) for _ in range(args.requests)]
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, args.requests))
-    srv = Server(precision=F.FH_FP64 if args.fp64 else F.FH_MIXED_FP32, slots=args.slots,
+    prec = {"fp64": F.FH_FP64, "fp32": F.FH_MIXED_FP32, "tf32": F.FH_MIXED_TF32,
+            "bf16": F.FH_MIXED_BF16}[args.precision]
+    srv = Server(precision=prec, slots=args.slots,
                  max_batch=args.max_batch, mem_budget=int(args.mem_gb * (1 << 30)))
     for r, t in zip(reqs, arrivals):
         r.arrival = float(t) + 0.5
         srv.submit(r)
     srv.drain()
     srv.close()
-    out = {"rate": args.rate, "slots": args.slots, "max_batch": args.max_batch}
+    out = {"rate": args.rate, "slots": args.slots, "max_batch": args.max_batch,
+           "precision": args.precision}
     out.update(srv.stats())
     print(json.dumps(out))
 

@@ -1,6 +1,7 @@
 """The C-ABI library builds, loads and exports every entry point of include/fh.h
 (no compute calls: these run without a GPU)."""
 import os
+import ctypes as C
 import re
 import subprocess
 
@@ -73,3 +74,14 @@ def test_create_without_device_reports_cuda_error(lib_path):
     with pytest.raises(F.FHError) as e:
         F.fh_create(0)
     assert e.value.status == F.FH_ECUDA
+
+
+def test_timing_phases_match_header():
+    """The binding's phase list (and so the fh_timings layout) is the header's enum."""
+    import re
+    hdr = open(HEADER).read()
+    body = re.search(r"enum \{ (FH_PH_GEOMETRY = 0,[^}]*)\}", hdr).group(1)
+    names = [n.strip().split("=")[0].strip() for n in body.split(",") if n.strip()]
+    assert names[-1] == "FH_NUM_PHASES"
+    assert [n[len("FH_PH_"):].lower() for n in names[:-1]] == F.PHASES
+    assert C.sizeof(F.fh_timings) == len(F.PHASES) * 3 * 8
