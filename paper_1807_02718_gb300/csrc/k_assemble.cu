@@ -26,6 +26,7 @@ namespace fh {
 namespace {
 
 constexpr int kTile = 32;
+constexpr int kNearBand = 2;   // off-diagonals whose special functions stay FP64 (mixed paths)
 
 __device__ __forceinline__ int find_solve(const long long *__restrict__ off, int S, long long b) {
     int lo = 0, hi = S;  // off[lo] <= b < off[hi]
@@ -158,10 +159,11 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
 //   Re A = k4 (W/pi J1 - (pi/n) Y1) + (pi/n) e4 J0,
 //   Im A = (pi/n) k4 J1 + e4 ((pi/n) Y0 - W/pi J0),
 // the same combination of M, M1, M2, L, L1, L2 as the FP64 kernel.  For
-// kappa r >= 8 the Bessel values (Hankel form), the phases and this
-// combination run in double-float arithmetic; diagonal entries, kappa r < 8
-// (small-argument series, the near-diagonal band), the Kress weights and the
-// log table stay FP64.
+// kappa r >= 8 off the band |i - l| <= kNearBand, the Bessel values (Hankel
+// form), the phases and this combination run in double-float arithmetic; the
+// diagonal, the band, kappa r < 8 (the small-argument series, whose serial
+// recurrences run faster in FP64 at this kernel's occupancy), the Kress
+// weights and the log table stay FP64.
 __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ z,
     const double2 *__restrict__ dz, const double2 *__restrict__ ddz,
@@ -245,18 +247,19 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
         dfv c, sv, sc, ss;
         df_expi(kap[0] * r - 0.78539816339744830962, c, sv);
         df_expi(dk * r, sc, ss);
-        // FP64 quantities for kappa r < 8
+        // the band |i - l| <= kNearBand keeps FP64 special functions
+        const bool near = d <= kNearBand || d >= N - kNearBand;
         const double ir64 = df_to(ir);
         const double gg = Nil * sl * ir64 / si;
-#pragma unroll
+#pragma unroll 1   // not unrolled: half the registers, twice the occupancy
         for (int j = 0; j < kGroup; ++j) {
             if (j < cnt) {
                 const float xf = kapf[j] * rd.hi;
-                if (xf >= 8.0f) {
+                if (!near && xf >= 8.0f) {
+                    dfv J0, Y0, J1, Y1;
                     const float dl = corrf[j] * rd.hi;
                     const dfv cj = df_add_f(c, -dl * sv.hi), sj = df_add_f(sv, dl * c.hi);
                     const dfv r8 = df_mul_f(df_mul(ir, ikap[j]), 8.0f);
-                    dfv J0, Y0, J1, Y1;
                     df_hankel<true>(gt, xf, r8, df_mul(amp0, isqk[j]), cj, sj, J0, Y0, J1, Y1);
                     const dfv k4 = df_mul(kapd[j], gg4), e4 = df_mul(etad[j], sl4);
                     const dfv pk4 = df_mul(pind, k4), pe4 = df_mul(pind, e4);
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
                 } else {
                     const double kappa = kap[j];
                     double J0, Y0, J1, Y1;
-                    bessel_small(kappa * r, J0, Y0, J1, Y1);
+                    bessel_j0y0j1y1(kappa * r, J0, Y0, J1, Y1);
                     const double Mr = -0.25 * Y0 * sl, Mi = 0.25 * J0 * sl;
                     const double M1 = -J0 * sl * inv4pi;
                     const double M2r = Mr - M1 * ls;

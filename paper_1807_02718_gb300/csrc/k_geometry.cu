@@ -57,17 +57,27 @@ __global__ void geometry_kernel(const CurveParams *__restrict__ curves,
 
 // R_d = -(2 pi / n) sum_{m=1}^{n-1} cos(m pi d / n) / m - (pi / n^2) cos(pi d)
 // and the log kernel ln(4 sin^2(pi d / N)) (d != 0), for d = 0..N-1.
+// cos(pi q / n) for q < N and 1/m for m < n are staged in shared memory; the
+// index m d mod N advances by d per term.
 __global__ void kress_kernel(const int *__restrict__ tab_N, const int *__restrict__ tab_off,
                              double *__restrict__ kress, double *__restrict__ logsin) {
+    extern __shared__ double ksm[];
     const int tb = blockIdx.y;
     const int N = tab_N[tb];
+    const int n = N / 2;
+    if (blockIdx.x * blockDim.x >= N) return;
+    double *ctab = ksm, *inv = ksm + N;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) ctab[q] = cospi((double)q / (double)n);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) inv[m] = m ? 1.0 / (double)m : 0.0;
+    __syncthreads();
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= N) return;
-    const int n = N / 2;
     double acc = 0.0;
+    int q = d;                                   // m d mod N for m = 1
     for (int m = 1; m < n; ++m) {
-        const int q = (int)(((long long)m * d) % N);   // cos(pi m d / n) = cospi(q / n)
-        acc += cospi((double)q / (double)n) / (double)m;
+        acc = fma(ctab[q], inv[m], acc);         // cos(pi m d / n) / m
+        q += d;
+        if (q >= N) q -= N;
     }
     const double sgn = (d & 1) ? -1.0 : 1.0;
     kress[tab_off[tb] + d] = -(2.0 * kPi / n) * acc - (kPi / ((double)n * n)) * sgn;
@@ -92,7 +102,13 @@ void launch_kress_tables(int n_tab, int maxN, const int *tab_N, const int *tab_o
                          double *kress, double *logsin, cudaStream_t st) {
     if (n_tab <= 0) return;
     dim3 grid((maxN + 127) / 128, n_tab);
-    kress_kernel<<<grid, 128, 0, st>>>(tab_N, tab_off, kress, logsin);
+    const size_t smem = (size_t)maxN * 3 / 2 * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(kress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    kress_kernel<<<grid, 128, smem, st>>>(tab_N, tab_off, kress, logsin);
 }
 
 }  // namespace fh
