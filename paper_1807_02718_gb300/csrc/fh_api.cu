@@ -87,6 +87,7 @@ struct fh_ctx {
     DevBuf d_sg, d_sg_tile_off, d_sg_dk, d_tmp_sg, d_items, d_item_first, d_part;
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_solve_prob, d_order, d_curves, d_pdir;
+    DevBuf d_zf, d_dzf, d_sf, d_wpf;
     DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_nu_f, d_ph, d_omega, d_pw;
     DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk, d_Bf, d_dblk,
         d_blk_off, d_dinv;
@@ -116,7 +117,7 @@ struct fh_ctx {
         DevBuf *all[] = {&d_sg, &d_sg_tile_off, &d_sg_dk, &d_tmp_sg, &d_items, &d_item_first,
                          &d_part, &d_N, &d_mat_off, &d_vec_off, &d_tab, &d_tab_off, &d_tab_N,
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
-                         &d_pdir, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
+                         &d_pdir, &d_zf, &d_dzf, &d_sf, &d_wpf, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_A32, &d_piv, &d_g, &d_iters,
                          &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
@@ -450,6 +451,10 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     FH_TRY(ensure(ctx, ctx->d_z, (size_t)vo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_dz, (size_t)vo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_ddz, (size_t)vo * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_zf, (size_t)vo * sizeof(float4)));
+    FH_TRY(ensure(ctx, ctx->d_dzf, (size_t)vo * sizeof(float4)));
+    FH_TRY(ensure(ctx, ctx->d_sf, (size_t)vo * sizeof(float2)));
+    FH_TRY(ensure(ctx, ctx->d_wpf, (size_t)tb * sizeof(float2)));
     FH_TRY(ensure(ctx, ctx->d_psi, (size_t)vo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_kress, (size_t)tb * sizeof(double)));
     FH_TRY(ensure(ctx, ctx->d_logsin, (size_t)tb * sizeof(double)));
@@ -464,10 +469,12 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     PhaseScope ps_(ctx, FH_PH_GEOMETRY, 2 + 2 * P);
     fh::launch_geometry(ctx->d_curves.as<fh::CurveParams>(), ctx->d_solve_prob.as<int>(), S, maxN,
                         ctx->d_N.as<int>(), ctx->d_vec_off.as<int>(), ctx->d_z.as<double2>(),
-                        ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(), ctx->stream);
+                        ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(), ctx->d_zf.as<float4>(),
+                        ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(), ctx->stream);
     FH_TRY(check_launch(ctx, "geometry"));
     fh::launch_kress_tables(ctx->n_tab, maxN, ctx->d_tab_N.as<int>(), ctx->d_tab_off.as<int>(),
-                            ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(), ctx->stream);
+                            ctx->d_kress.as<double>(), ctx->d_logsin.as<double>(),
+                            ctx->d_wpf.as<float2>(), ctx->stream);
     FH_TRY(check_launch(ctx, "kress tables"));
     for (Problem &pb : ctx->probs) {
         fh::launch_far_table(pb.J, pb.M, ctx->d_pw.as<double>(), nullptr,
@@ -558,7 +565,8 @@ fh_status sample_common(fh_ctx *ctx, int q, const double *d_x, int n_x, const do
                                 ctx->d_items.as<int2>(), pb.item_begin, n_items,
                                 ctx->d_item_first.as<int>(), ctx->d_solve_j.as<int>(),
                                 ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                                ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_part.as<double2>(),
+                                ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_zf.as<float4>(),
+                                ctx->d_part.as<double2>(),
                                 ctx->d_V.as<double2>(), ctx->precision != FH_FP64, ctx->stream);
         FH_TRY(check_launch(ctx, "target field"));
     }
@@ -693,7 +701,10 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         fh::launch_assemble_groups(t, groups(ctx), ctx->n_groups, ctx->group_tiles,
                                    ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                    ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
-                                   ctx->d_logsin.as<double>(), ctx->d_A.as<double2>(), 0, ctx->precision != FH_FP64, ctx->stream);
+                                   ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
+                                   ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(),
+                                   ctx->d_wpf.as<float2>(), ctx->d_A.as<double2>(), 0,
+                                   ctx->precision != FH_FP64, ctx->stream);
         FH_TRY(check_launch(ctx, "assemble"));
         if (mixed) FH_TRY(ensure(ctx, ctx->d_g, (size_t)ctx->vec_total * sizeof(double2)));
         fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
@@ -932,8 +943,9 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     const fh::SolveTables t = tables(ctx);
     fh::launch_assemble_groups(t, g1, 1, nt * nt, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
-                               ctx->d_logsin.as<double>(), ctx->d_tmpA.as<double2>(), -base,
-                               ctx->precision != FH_FP64, ctx->stream);
+                               ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
+                               ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(), ctx->d_wpf.as<float2>(),
+                               ctx->d_tmpA.as<double2>(), -base, ctx->precision != FH_FP64, ctx->stream);
     FH_TRY(check_launch(ctx, "assemble (single)"));
     fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                    ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),

@@ -36,10 +36,13 @@ struct SolveTables {
 
 // ---- geometry and quadrature tables (k_geometry.cu) ----
 // Solve s uses curve curves[prob[s]] (device arrays).
+// zf, dzf: double-float copies of z, z' (x hi, x lo, y hi, y lo); sf: |z'|.
 void launch_geometry(const CurveParams *curves, const int *prob, int S, int maxN, const int *N,
-                     const int *vec_off, double2 *z, double2 *dz, double2 *ddz, cudaStream_t st);
+                     const int *vec_off, double2 *z, double2 *dz, double2 *ddz, float4 *zf,
+                     float4 *dzf, float2 *sf, cudaStream_t st);
+// wpf: ((pi/n) ln(4 sin^2(pi d/N)) - R_d) / pi as double-float pairs.
 void launch_kress_tables(int n_tab, int maxN, const int *tab_N, const int *tab_off,
-                         double *kress, double *logsin, cudaStream_t st);
+                         double *kress, double *logsin, float2 *wpf, cudaStream_t st);
 
 // Frequency subgroups: up to kGroup consecutive solves with equal N (hence
 // identical nodes).  Their kernels share the geometry of each node pair and
@@ -58,6 +61,7 @@ struct Subgroups {
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long n_tiles, const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
+                            const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
                             double2 *A, long long out_shift, bool double_float, cudaStream_t st);
 // Solve s uses the incidence direction pdir[prob[s]].
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
@@ -119,7 +123,7 @@ constexpr int kFieldChunk = 64;
 void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
                          const int2 *items, int item_begin, int n_items, const int *item_first,
                          const int *solve_j, const double2 *z, const double2 *dz,
-                         const double2 *psi, const double *x, int n_x, double2 *part,
+                         const double2 *psi, const double *x, int n_x, const float4 *zf, double2 *part,
                          double2 *V, bool double_float,
                          cudaStream_t st);
 

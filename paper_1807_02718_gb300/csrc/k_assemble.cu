@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ z,
     const double2 *__restrict__ dz, const double2 *__restrict__ ddz,
     const double *__restrict__ kress, const double *__restrict__ logsin,
-    double2 *__restrict__ A, long long out_shift) {
+    const float4 *__restrict__ zf, const float4 *__restrict__ dzf, const float2 *__restrict__ sf,
+    const float2 *__restrict__ wpf, double2 *__restrict__ A, long long out_shift) {
     const long long b = blockIdx.x;
     const int g = find_solve(grp.tile_off, n_groups, b);
     const int2 sgv = grp.sg[g];
@@ -210,17 +211,18 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     const dfv isi4 = df_from(0.25 / si);
     const double inv4pi = 1.0 / (4.0 * kPi);
     const dfv two_over_pi = df_make(0.6366197466850281f, 2.5682552973194106e-08f);
+    const float4 zi4 = zf[vo + i], dzi4 = dzf[vo + i];
+    const dfv nzix = df_make(-zi4.x, -zi4.y), nziy = df_make(-zi4.z, -zi4.w);
+    const dfv dzix = df_make(dzi4.x, dzi4.y), dziy = df_make(dzi4.z, dzi4.w);
 
     for (int q = threadIdx.x >> 5; q < kTile; q += 8) {
         const int l = tc * kTile + q;
         if (l >= N) break;
         int d = i - l;
         if (d < 0) d += N;
-        const double Rw = kress[to + d];
-        const double2 dzl = dz[vo + l];
-        const double sl = sqrt(dzl.x * dzl.x + dzl.y * dzl.y);
         const long long e_off = (long long)l * N + i;
         if (l == i) {
+            const double Rw = kress[to + d];
             const double2 dd = ddz[vo + i];
             const double M1 = -si * inv4pi;
             const double L2r = (dd.x * dzi.y - dd.y * dzi.x) * inv4pi / (si * si);
@@ -233,24 +235,34 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
             }
             continue;
         }
-        const double2 zl = z[vo + l];
-        const double d1 = zl.x - zi.x, d2 = zl.y - zi.y;
-        const dfv rd = df_sqrt(df_from(fma(d1, d1, d2 * d2)));
-        const double r = df_to(rd);
+        // pair geometry in double-float from the double-float node tables
+        const float4 zl4 = zf[vo + l];
+        const dfv d1 = df_add(df_make(zl4.x, zl4.y), nzix), d2 = df_add(df_make(zl4.z, zl4.w), nziy);
+        const dfv rd = df_sqrt(df_add(df_mul(d1, d1), df_mul(d2, d2)));
+        const double r = df_to(rd);                 // FP64 only for the phase arguments
         const dfv ir = df_rcp(rd);
-        const double Nil = dzi.y * d1 - dzi.x * d2;
-        const double ls = logsin[to + d];
-        const dfv Wp = df_from(fma(pin, ls, -Rw) * (1.0 / kPi));           // W / pi
-        const dfv gg4 = df_mul(df_mul(df_from(Nil), df_from(sl)), df_mul(ir, isi4));   // N s_l / (4 s_i r)
-        const dfv sl4 = df_from(0.25 * sl);
+        const dfv Nil = df_add(df_mul(dziy, d1), df_neg(df_mul(dzix, d2)));
+        const float2 sl2 = sf[vo + l], wp2 = wpf[to + d];
+        const dfv sl = df_make(sl2.x, sl2.y), Wp = df_make(wp2.x, wp2.y);   // |z'_l|, W / pi
+        const dfv gg4 = df_mul(df_mul(Nil, sl), df_mul(ir, isi4));          // N s_l / (4 s_i r)
+        const dfv sl4 = df_mul_f(sl, 0.25f);
         const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));
         dfv c, sv, sc, ss;
         df_expi(kap[0] * r - 0.78539816339744830962, c, sv);
         df_expi(dk * r, sc, ss);
-        // the band |i - l| <= kNearBand keeps FP64 special functions
+        // the band |i - l| <= kNearBand and kappa r < 8 take the FP64 branch, with
+        // its quantities formed in FP64 from the FP64 tables
         const bool near = d <= kNearBand || d >= N - kNearBand;
-        const double ir64 = df_to(ir);
-        const double gg = Nil * sl * ir64 / si;
+        double Rw = 0.0, ls = 0.0, sl64 = 0.0, gg = 0.0, r64 = 0.0;
+        if (near || kapf[0] * rd.hi < 8.0f) {
+            Rw = kress[to + d];
+            ls = logsin[to + d];
+            const double2 zl = z[vo + l], dzl = dz[vo + l];
+            const double e1 = zl.x - zi.x, e2 = zl.y - zi.y;
+            r64 = sqrt(e1 * e1 + e2 * e2);
+            sl64 = sqrt(dzl.x * dzl.x + dzl.y * dzl.y);
+            gg = (dzi.y * e1 - dzi.x * e2) * sl64 / (si * r64);
+        }
 #pragma unroll 1   // not unrolled: half the registers, twice the occupancy
         for (int j = 0; j < kGroup; ++j) {
             if (j < cnt) {
@@ -271,9 +283,9 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
                 } else {
                     const double kappa = kap[j];
                     double J0, Y0, J1, Y1;
-                    bessel_j0y0j1y1(kappa * r, J0, Y0, J1, Y1);
-                    const double Mr = -0.25 * Y0 * sl, Mi = 0.25 * J0 * sl;
-                    const double M1 = -J0 * sl * inv4pi;
+                    bessel_j0y0j1y1(kappa * r64, J0, Y0, J1, Y1);
+                    const double Mr = -0.25 * Y0 * sl64, Mi = 0.25 * J0 * sl64;
+                    const double M1 = -J0 * sl64 * inv4pi;
                     const double M2r = Mr - M1 * ls;
                     const double Lr = -0.25 * kappa * Y1 * gg, Li = 0.25 * kappa * J1 * gg;
                     const double L1 = -kappa * inv4pi * J1 * gg;
@@ -317,11 +329,13 @@ __global__ void rhs_kernel(SolveTables t, const double2 *__restrict__ z,
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long n_tiles, const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
+                            const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
                             double2 *A, long long out_shift, bool double_float, cudaStream_t st) {
     if (n_tiles <= 0 || n_groups <= 0) return;
     if (double_float)
         assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
-                                                                    logsin, A, out_shift);
+                                                                    logsin, zf, dzf, sf, wpf, A,
+                                                                    out_shift);
     else
         assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
                                                                  logsin, A, out_shift);

@@ -137,15 +137,15 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool 
 }
 
 // Mixed-precision variant of field_partial_kernel: the same sums with the
-// Hankel-form H0 (kappa r >= 8), the phases and the accumulation in
-// double-float arithmetic.  FP64 is kept for the distance, the phase
-// arguments kappa_0 r and dkappa r with their reduction modulo pi/2, and the
-// small-argument series (kappa r < 8).
+// distances, the Hankel-form H0 (kappa r >= 8), the phases and the
+// accumulation in double-float arithmetic.  FP64 is kept for the phase
+// arguments kappa_0 r and dkappa r with their reduction modulo pi/2 and for
+// the small-argument series (kappa r < 8).
 __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
     SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin,
     const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
-    double2 *__restrict__ part) {
+    const float4 *__restrict__ zf, double2 *__restrict__ part) {
     const int w = blockIdx.y;
     const int2 item = items[item_begin + w];
     const int g = item.x, i0 = item.y;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
     __shared__ double kap[kGroup];
     __shared__ float kapf[kGroup], corrf[kGroup];
     __shared__ dfv ikap[kGroup], isqk[kGroup];
-    __shared__ double2 zs[kChunk];
+    __shared__ float4 zs[kChunk];             // node coordinates, double-float
     __shared__ float4 ps[kGroup][kChunk];   // (pi/n)|z'|/4 * psi_j as (re hi, re lo, im hi, im lo)
     __shared__ GShared gt;
     g_stage(gt);
@@ -174,12 +174,12 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
     const int ne = min(kChunk, N - i0);
     for (int e = threadIdx.x; e < kChunk; e += kTgt) {
         const int i = i0 + e;
-        double2 zz = make_double2(0.0, 0.0);
+        float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
         double sp = 0.0;
         if (e < ne) {
             const double2 d = dz[vo0 + i];
             sp = sqrt(d.x * d.x + d.y * d.y) * wq;
-            zz = z[vo0 + i];
+            zz = zf[vo0 + i];
         }
         zs[e] = zz;
         for (int j = 0; j < kGroup; ++j) {
@@ -195,15 +195,16 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
     __syncthreads();
     const int it = blockIdx.x * kTgt + threadIdx.x;
     if (it >= n_x) return;
-    const double px = x[2 * it], py = x[2 * it + 1];
+    const dfv npx = df_neg(df_from(x[2 * it])), npy = df_neg(df_from(x[2 * it + 1]));
     const dfv two_over_pi = df_make(0.6366197466850281f, 2.5682552973194106e-08f);   // 2/pi
     float ah[kGroup][2], al[kGroup][2];
 #pragma unroll
     for (int j = 0; j < kGroup; ++j) ah[j][0] = ah[j][1] = al[j][0] = al[j][1] = 0.f;
     for (int e = 0; e < ne; ++e) {
-        const double d1 = px - zs[e].x, d2 = py - zs[e].y;
-        const dfv rd = df_sqrt(df_from(fma(d1, d1, d2 * d2)));
-        const double r = df_to(rd);
+        const float4 z4 = zs[e];
+        const dfv d1 = df_add(df_make(z4.x, z4.y), npx), d2 = df_add(df_make(z4.z, z4.w), npy);
+        const dfv rd = df_sqrt(df_add(df_mul(d1, d1), df_mul(d2, d2)));
+        const double r = df_to(rd);   // FP64 for the phase arguments and the small-argument series
         const dfv ir = df_rcp(rd);
         const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));   // sqrt(2 / (pi r))
         dfv c, sv, sc, ss;
@@ -337,14 +338,15 @@ void launch_bessel_eval_df(const double *x, int n, double *out, cudaStream_t st)
 void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
                          const int2 *items, int item_begin, int n_items, const int *item_first,
                          const int *solve_j, const double2 *z, const double2 *dz,
-                         const double2 *psi, const double *x, int n_x, double2 *part,
-                         double2 *V, bool double_float, cudaStream_t st) {
+                         const double2 *psi, const double *x, int n_x, const float4 *zf,
+                         double2 *part, double2 *V, bool double_float, cudaStream_t st) {
     if (n_x <= 0) return;
     field_zero_freq_kernel<<<(n_x + 255) / 256, 256, 0, st>>>(n_x, V);
     if (n_groups <= 0 || n_items <= 0) return;
     dim3 grid((n_x + kTgt - 1) / kTgt, n_items);
     if (double_float)
-        field_partial_df_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, part);
+        field_partial_df_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, zf,
+                                                       part);
     else
         field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, part);
     dim3 g2((n_x + 127) / 128, n_groups);
