@@ -271,6 +271,16 @@ typedef struct {
     long long events[FH_NUM_PHASES];    /* timed launch groups per phase         */
 } fh_timings;
 
+/* enable != 0 (the default): fh_solve_frequencies and fh_sample run their
+ * launch sequences as CUDA graphs.  The first call with a given
+ * discretization, buffer set and (for fh_sample) problem, sizes and pointers
+ * launches directly, the second captures the sequence and later calls replay
+ * it; fh_discretize with unchanged inputs keeps its tables and buffers, so the
+ * graphs stay valid across repeated discretize-solve-sample cycles.  The
+ * kernels and their results are the same either way.  Graphs are not used
+ * while kernel timing (fh_set_timing) is on. */
+fh_status fh_set_graphs(fh_ctx *ctx, int enable);
+
 /* enable != 0: bracket every kernel group with CUDA events on the context
  * stream (adds two event records per group).  Launch counts are always kept. */
 fh_status fh_set_timing(fh_ctx *ctx, int enable);

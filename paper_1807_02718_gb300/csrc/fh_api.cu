@@ -65,6 +65,19 @@ struct fh_ctx {
     std::string err;
 
     bool geom = false, solved = false, have_V = false;
+
+    // CUDA graphs of the solve and sample launch sequences, replayed while the
+    // discretization, the buffers and the call's parameters are unchanged
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        long long key = -1, seen = -1;
+        long long launches[FH_NUM_PHASES] = {};
+    };
+    GraphSlot solve_graph, sample_graph;
+    bool graphs = true;
+    cudaStream_t cap = nullptr;            // stream the sequences are captured on
+    unsigned long long disc_hash = 0;
+    long long disc_gen = 0, buf_gen = 0;
     int v_problem = 0;           // problem of the last target fields
     std::vector<Problem> probs;
 
@@ -127,6 +140,9 @@ struct fh_ctx {
             cudaEventDestroy(pe.a);
             cudaEventDestroy(pe.b);
         }
+        for (GraphSlot *g : {&solve_graph, &sample_graph})
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (cap) cudaStreamDestroy(cap);
         if (own) cudaStreamDestroy(own);
     }
 };
@@ -169,6 +185,7 @@ fh_status ensure(fh_ctx *ctx, DevBuf &b, size_t bytes) {
                     "device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
     }
     b.cap = want;
+    ++ctx->buf_gen;
     return FH_OK;
 }
 
@@ -191,6 +208,65 @@ fh_status enter(fh_ctx *ctx) {
 fh_status check_launch(fh_ctx *ctx, const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    return FH_OK;
+}
+
+unsigned long long mix_hash(unsigned long long h, const void *data, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;   // FNV-1a
+    return h;
+}
+
+long long graph_key(fh_ctx *ctx, long long a, long long b, long long c, long long d, long long e) {
+    const long long v[8] = {ctx->disc_gen, ctx->buf_gen, ctx->precision, a, b, c, d, e};
+    return (long long)(mix_hash(1469598103934665603ull, v, sizeof(v)) & 0x7fffffffffffffffull);
+}
+
+// Runs a launch sequence through a CUDA graph: the first call with a key
+// launches directly, the second captures the sequence (on the capture
+// stream) and launches the graph, later calls with the same key replay it on
+// the context stream.  Graphs are off while kernel timing is on.
+template <class Launch>
+fh_status run_captured(fh_ctx *ctx, fh_ctx::GraphSlot &g, long long key, Launch &&launch) {
+    if (!ctx->graphs || ctx->timing) {
+        g.seen = -1;
+        return launch();
+    }
+    if (g.exec && g.key == key) {
+        FH_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
+        for (int i = 0; i < FH_NUM_PHASES; ++i) ctx->launches[i] += g.launches[i];
+        return FH_OK;
+    }
+    if (g.seen != key) {
+        g.seen = key;
+        return launch();
+    }
+    long long before[FH_NUM_PHASES];
+    for (int i = 0; i < FH_NUM_PHASES; ++i) before[i] = ctx->launches[i];
+    cudaStream_t user = ctx->stream;
+    FH_CUDA(ctx, cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = ctx->cap;
+    const fh_status st = launch();
+    ctx->stream = user;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap, &graph);
+    if (st != FH_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st;
+    }
+    if (e != cudaSuccess || !graph)
+        return fail(ctx, FH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+        return fail(ctx, FH_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = exec;
+    g.key = key;
+    for (int i = 0; i < FH_NUM_PHASES; ++i) g.launches[i] = ctx->launches[i] - before[i];
+    FH_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
     return FH_OK;
 }
 
@@ -280,6 +356,8 @@ fh_status check_problem_args(fh_ctx *ctx, const fh_curve *curve, int J, const do
 
 // Builds every per-solve / per-subgroup table of a batch and launches the
 // node, Kress and synthesis-table kernels.
+fh_status discretize_device(fh_ctx *ctx);
+
 fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int *Js,
                            const double *omega_all, const int *N_all, const double *cs,
                            const double *ps) {
@@ -292,6 +370,24 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
                                   cs[q], ps + 2 * q, q));
         jo += Js[q];
     }
+    // the same discretization as the current one: keep its host tables and
+    // buffers (so captured launch sequences stay valid) and rerun its kernels
+    unsigned long long h = mix_hash(1469598103934665603ull, &P, sizeof(P));
+    h = mix_hash(h, curves, sizeof(fh_curve) * P);
+    h = mix_hash(h, Js, sizeof(int) * P);
+    h = mix_hash(h, omega_all, sizeof(double) * jo);
+    const int has_N = N_all != nullptr;
+    h = mix_hash(h, &has_N, sizeof(has_N));
+    if (N_all) h = mix_hash(h, N_all, sizeof(int) * jo);
+    h = mix_hash(h, cs, sizeof(double) * P);
+    h = mix_hash(h, ps, sizeof(double) * 2 * P);
+    if (ctx->geom && h == ctx->disc_hash && (int)ctx->probs.size() == P) {
+        ctx->solved = ctx->have_V = false;
+        for (Problem &pb : ctx->probs) pb.spectra = false;
+        return discretize_device(ctx);
+    }
+    ctx->disc_hash = h;
+    ++ctx->disc_gen;
     ctx->geom = ctx->solved = ctx->have_V = false;
     ctx->free_problems();
     ctx->probs.resize(P);
@@ -466,6 +562,12 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     int maxM = 0;
     for (const Problem &pb : ctx->probs) maxM = std::max(maxM, pb.M);
     FH_TRY(ensure(ctx, ctx->d_pw, (size_t)maxM * fh::kFarTerms * sizeof(double)));
+    return discretize_device(ctx);
+}
+
+// Device part of the discretization: nodes, Kress/log tables, far-field tables.
+fh_status discretize_device(fh_ctx *ctx) {
+    const int P = (int)ctx->probs.size(), S = ctx->S, maxN = ctx->maxN;
     PhaseScope ps_(ctx, FH_PH_GEOMETRY, 2 + 2 * P);
     fh::launch_geometry(ctx->d_curves.as<fh::CurveParams>(), ctx->d_solve_prob.as<int>(), S, maxN,
                         ctx->d_N.as<int>(), ctx->d_vec_off.as<int>(), ctx->d_z.as<double2>(),
@@ -535,12 +637,16 @@ fh_status spectra_common(fh_ctx *ctx, Problem &pb, const double *d_a, int n_samp
     return FH_OK;
 }
 
-fh_status synth_common(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
+fh_status synth_buffers(fh_ctx *ctx, Problem &pb, int n_T) {
     FH_TRY(ensure(ctx, ctx->d_Gr, (size_t)pb.J * n_T * sizeof(double)));
     FH_TRY(ensure(ctx, ctx->d_Gm, (size_t)pb.J * n_T * sizeof(double)));
+    return ensure(ctx, ctx->d_Bf, (size_t)pb.K * pb.J * sizeof(float4));
+}
+
+// Weights G_p(t) and the contraction u = Re sum_p V_p G_p (buffers exist).
+fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
     {
         PhaseScope ps(ctx, FH_PH_WEIGHTS, 2);
-        FH_TRY(ensure(ctx, ctx->d_Bf, (size_t)pb.K * pb.J * sizeof(float4)));
         fh::launch_synth_weights(pb.J, pb.M, pb.W, pb.K, pb.d_s.as<double>(), pb.d_B.as<double2>(),
                                  ctx->d_Bf.as<float4>(), ctx->d_nu_f.as<float4>() + pb.nu_off,
                                  ctx->d_ph.as<double2>() + pb.ph_off, d_T, n_T,
@@ -553,12 +659,15 @@ fh_status synth_common(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int
     return check_launch(ctx, "synthesis contraction");
 }
 
-fh_status sample_common(fh_ctx *ctx, int q, const double *d_x, int n_x, const double *d_T,
-                        int n_T, double *d_u) {
-    Problem &pb = ctx->probs[q];
-    FH_TRY(ensure(ctx, ctx->d_V, (size_t)pb.J * n_x * sizeof(double2)));
+fh_status synth_common(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
+    FH_TRY(synth_buffers(ctx, pb, n_T));
+    return synth_kernels(ctx, pb, n_x, d_T, n_T, d_u);
+}
+
+// Target fields, weights and contraction for one problem (buffers exist).
+fh_status sample_kernels(fh_ctx *ctx, Problem &pb, const double *d_x, int n_x, const double *d_T,
+                         int n_T, double *d_u) {
     const int n_items = pb.item_end - pb.item_begin;
-    FH_TRY(ensure(ctx, ctx->d_part, (size_t)n_items * fh::kGroup * (size_t)n_x * sizeof(double2)));
     {
         PhaseScope ps(ctx, FH_PH_FIELD, pb.S() > 0 ? 3 : 1);
         fh::launch_target_field(tables(ctx), groups(ctx), pb.g_begin, pb.g_end - pb.g_begin,
@@ -570,10 +679,25 @@ fh_status sample_common(fh_ctx *ctx, int q, const double *d_x, int n_x, const do
                                 ctx->d_V.as<double2>(), ctx->precision != FH_FP64, ctx->stream);
         FH_TRY(check_launch(ctx, "target field"));
     }
+    return synth_kernels(ctx, pb, n_x, d_T, n_T, d_u);
+}
+
+fh_status sample_common(fh_ctx *ctx, int q, const double *d_x, int n_x, const double *d_T,
+                        int n_T, double *d_u) {
+    Problem &pb = ctx->probs[q];
+    FH_TRY(ensure(ctx, ctx->d_V, (size_t)pb.J * n_x * sizeof(double2)));
+    const int n_items = pb.item_end - pb.item_begin;
+    FH_TRY(ensure(ctx, ctx->d_part, (size_t)n_items * fh::kGroup * (size_t)n_x * sizeof(double2)));
+    FH_TRY(synth_buffers(ctx, pb, n_T));
+    const long long key = graph_key(ctx, q + ((long long)pb.K << 24), n_x + ((long long)n_T << 32),
+                                    (long long)(uintptr_t)d_x, (long long)(uintptr_t)d_T,
+                                    (long long)(uintptr_t)d_u);
+    FH_TRY(run_captured(ctx, ctx->sample_graph, key,
+                        [&]() { return sample_kernels(ctx, pb, d_x, n_x, d_T, n_T, d_u); }));
     ctx->n_x_last = n_x;
     ctx->v_problem = q;
     ctx->have_V = true;
-    return synth_common(ctx, pb, n_x, d_T, n_T, d_u);
+    return FH_OK;
 }
 
 fh_status check_sample_args(fh_ctx *ctx, int q, int n_x, int n_T) {
@@ -638,7 +762,8 @@ fh_status fh_create(fh_ctx **out, int device, int precision) {
     fh_ctx *ctx = new fh_ctx();
     ctx->device = device;
     ctx->precision = precision;
-    if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
         delete ctx;
         return FH_ECUDA;
     }
@@ -682,20 +807,10 @@ fh_status fh_num_problems(fh_ctx *ctx, int *P) {
     return FH_OK;
 }
 
-fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *stats) {
-    FH_TRY(enter(ctx));
-    if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_solve_frequencies: call fh_discretize first");
-    for (int s = 0; s < ctx->S; ++s) {
-        const Problem &pb = ctx->probs[ctx->solve_prob[s]];
-        const int j = ctx->solve_j[s];
-        const double e = eta ? eta[pb.omega_off + j] : pb.omega[j];
-        if (!is_fin(e)) return fail(ctx, FH_EINVAL, "eta[%lld] is not finite", pb.omega_off + j);
-        ctx->eta_s[s] = e;
-    }
-    ctx->solved = false;
-    FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
+// The kernel sequence of fh_solve_frequencies (assembly, right sides,
+// factorisation, refinement); all buffers exist already.
+fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     const fh::SolveTables t = tables(ctx);
-    const bool mixed = ctx->precision != FH_FP64;
     {
         PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
         fh::launch_assemble_groups(t, groups(ctx), ctx->n_groups, ctx->group_tiles,
@@ -706,7 +821,6 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
                                    ctx->d_wpf.as<float2>(), ctx->d_A.as<double2>(), 0,
                                    ctx->precision != FH_FP64, ctx->stream);
         FH_TRY(check_launch(ctx, "assemble"));
-        if (mixed) FH_TRY(ensure(ctx, ctx->d_g, (size_t)ctx->vec_total * sizeof(double2)));
         fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                        ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
                        mixed ? ctx->d_g.as<double2>() : ctx->d_psi.as<double2>(), ctx->stream);
@@ -721,21 +835,10 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
                                  ctx->d_info.as<int>(), ctx->stream);
         FH_TRY(check_launch(ctx, "lu fp64"));
     } else {
-        const bool tc = ctx->precision == FH_MIXED_TF32 || ctx->precision == FH_MIXED_BF16;
-        if (tc && ctx->maxN > fh::kTcMaxN)
-            return fail(ctx, FH_EINVAL, "tensor-core LU supports N <= %d (largest N is %d)",
-                        fh::kTcMaxN, ctx->maxN);
-        FH_TRY(ensure(ctx, ctx->d_A32, (size_t)ctx->mat_total * sizeof(float2)));
-        FH_TRY(ensure(ctx, ctx->d_piv, (size_t)ctx->vec_total * sizeof(int)));
-        FH_TRY(ensure(ctx, ctx->d_iters, (size_t)ctx->S * sizeof(int)));
-        FH_TRY(ensure(ctx, ctx->d_resid, (size_t)ctx->S * sizeof(double)));
-        FH_TRY(ensure(ctx, ctx->d_y32, (size_t)ctx->vec_total * sizeof(float2)));
-        FH_TRY(ensure(ctx, ctx->d_rstate, fh::refine_state_bytes(ctx->S)));
         {
             // launches: conversion and one LU launch per cluster size (SIMT: one)
             PhaseScope ps(ctx, FH_PH_FACTOR, 1 + (tc ? fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S) : 1));
             if (tc) {
-                FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
                 FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
                 fh::launch_convert_rowmajor(ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
                                             ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->stream);
@@ -755,7 +858,6 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
                                           ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
             }
         }
-        if (tc) FH_TRY(ensure(ctx, ctx->d_dinv, (size_t)ctx->n_dblk * 2048 * sizeof(float2)));
         // launches: diagonal-block inverses (row-major factors), set-up, two
         // kernels per sweep and the verdict
         PhaseScope ps(ctx, FH_PH_REFINE, (tc ? 1 : 0) + 2 + 2 * kRefineMaxIters);
@@ -771,6 +873,42 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
                              ctx->stream);
         FH_TRY(check_launch(ctx, "lu mixed"));
     }
+    return FH_OK;
+}
+
+fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *stats) {
+    FH_TRY(enter(ctx));
+    if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_solve_frequencies: call fh_discretize first");
+    for (int s = 0; s < ctx->S; ++s) {
+        const Problem &pb = ctx->probs[ctx->solve_prob[s]];
+        const int j = ctx->solve_j[s];
+        const double e = eta ? eta[pb.omega_off + j] : pb.omega[j];
+        if (!is_fin(e)) return fail(ctx, FH_EINVAL, "eta[%lld] is not finite", pb.omega_off + j);
+        ctx->eta_s[s] = e;
+    }
+    ctx->solved = false;
+    FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
+    const bool mixed = ctx->precision != FH_FP64;
+    const bool tc = ctx->precision == FH_MIXED_TF32 || ctx->precision == FH_MIXED_BF16;
+    if (tc && ctx->maxN > fh::kTcMaxN)
+        return fail(ctx, FH_EINVAL, "tensor-core LU supports N <= %d (largest N is %d)",
+                    fh::kTcMaxN, ctx->maxN);
+    // every buffer of the launch sequence exists before it is launched or captured
+    if (mixed) {
+        FH_TRY(ensure(ctx, ctx->d_g, (size_t)ctx->vec_total * sizeof(double2)));
+        FH_TRY(ensure(ctx, ctx->d_A32, (size_t)ctx->mat_total * sizeof(float2)));
+        FH_TRY(ensure(ctx, ctx->d_piv, (size_t)ctx->vec_total * sizeof(int)));
+        FH_TRY(ensure(ctx, ctx->d_iters, (size_t)ctx->S * sizeof(int)));
+        FH_TRY(ensure(ctx, ctx->d_resid, (size_t)ctx->S * sizeof(double)));
+        FH_TRY(ensure(ctx, ctx->d_y32, (size_t)ctx->vec_total * sizeof(float2)));
+        FH_TRY(ensure(ctx, ctx->d_rstate, fh::refine_state_bytes(ctx->S)));
+        if (tc) {
+            FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
+            FH_TRY(ensure(ctx, ctx->d_dinv, (size_t)ctx->n_dblk * 2048 * sizeof(float2)));
+        }
+    }
+    const long long key = graph_key(ctx, 0, 0, 0, 0, 0);
+    FH_TRY(run_captured(ctx, ctx->solve_graph, key, [&]() { return solve_kernels(ctx, mixed, tc); }));
     int iters_max = 0;
     double resid_max = 0.0;
     std::vector<int> info(ctx->S), iters;
@@ -1102,6 +1240,13 @@ fh_status fh_eval_bessel_df(const double *x, int n, double *out) {
     }
     cudaFree(d);
     return st;
+}
+
+fh_status fh_set_graphs(fh_ctx *ctx, int enable) {
+    FH_TRY(enter(ctx));
+    ctx->graphs = enable != 0;
+    ctx->solve_graph.seen = ctx->sample_graph.seen = -1;
+    return FH_OK;
 }
 
 fh_status fh_set_timing(fh_ctx *ctx, int enable) {

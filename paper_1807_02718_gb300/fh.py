@@ -32,7 +32,7 @@ EXPORTED = [
     "fh_synthesize", "fh_set_timing", "fh_get_timings", "fh_probe_fma_peak",
     "fh_eval_bessel", "fh_synthesize_static", "fh_discretize_batch", "fh_num_problems",
     "fh_window_spectra_p", "fh_window_spectra_p_dev", "fh_sample_p", "fh_sample_p_dev",
-    "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test", "fh_eval_bessel_df",
+    "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test", "fh_eval_bessel_df", "fh_set_graphs",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "refine", "spectra", "field", "weights", "contract"]
@@ -100,6 +100,7 @@ def load_library(path: str | None = None):
         "fh_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
         "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_eval_bessel_df": (C.c_int, [_DP, C.c_int, _DP]),
+        "fh_set_graphs": (C.c_int, [vp, C.c_int]),
         "fh_discretize_batch": (C.c_int, [vp, C.c_int, C.POINTER(fh_curve), _IP, _DP, _IP, _DP, _DP]),
         "fh_num_problems": (C.c_int, [vp, _IP]),
         "fh_window_spectra_p": (C.c_int, [vp, C.c_int, _DP, C.c_int, C.c_double, C.c_double, C.c_double]),
@@ -280,6 +281,11 @@ def fh_synthesize(ctx, V, T):
     _check(ctx, load_library().fh_synthesize(ctx, Vv.ctypes.data_as(_DP), n_x, _dp(Tv), Tv.size,
                                              _dp(u)))
     return u
+
+
+def fh_set_graphs(ctx, enable: bool):
+    """Run the solve and sample launch sequences as CUDA graphs (default on)."""
+    _check(ctx, load_library().fh_set_graphs(ctx, int(bool(enable))))
 
 
 def fh_set_timing(ctx, enable: bool):
