@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="tf32", choices=["fp64", "mixed", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default schedule instead of running the autotuner at set-up")
     return ap.parse_args()
 
 
@@ -309,6 +311,15 @@ def run_gpu(args, world, rank, local):
     d_u = torch.empty(n_x * n_T, device=dev, dtype=torch.float64)
     flush = torch.empty(256 * 1024 * 1024 // 8, device=dev, dtype=torch.float64)
 
+    # ---- set-up: schedule autotuning on this workload (not timed) ----
+    tuning = {"autotuned": False, "setting": F.fh_get_tuning(pr.ctx)}
+    if not args.no_tune:
+        F.fh_discretize(pr.ctx, wl.curve, wl.omega, wl.N, wl.c, wl.p)
+        t0 = time.perf_counter()
+        chosen, best_ms = F.fh_autotune(pr.ctx, wl.x, reps=3)
+        tuning = {"autotuned": True, "setting": chosen, "best_ms": best_ms,
+                  "tune_s": time.perf_counter() - t0}
+
     solve_stats = {}
 
     def step():
@@ -426,6 +437,7 @@ def run_gpu(args, world, rank, local):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": 1e3 * e2e_total / args.steps},
             "gpu_launches": int(launches),
+            "tuning": tuning,
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -281,6 +281,47 @@ typedef struct {
  * while kernel timing (fh_set_timing) is on. */
 fh_status fh_set_graphs(fh_ctx *ctx, int enable);
 
+/* Schedule parameters of the batched kernels (launch shapes only: every
+ * setting computes the same discrete quantities, equal up to rounding order).
+ *   assemble_group   frequencies of equal N assembled together per CTA tile
+ *                    (1..8; they share the geometry of each node pair)
+ *   field_group      frequencies of equal N per target-field work item (1..8)
+ *   field_chunk      source nodes per target-field work item (16, 32 or 64)
+ *   lu_rows_per_cta  tensor-core LU: a system of order N is factored by the
+ *                    smallest power of two of CTAs, at most 8, that is
+ *                    >= N / lu_rows_per_cta (128, 256 or 512)
+ * Defaults {8, 8, 64, 512}. */
+typedef struct {
+    int assemble_group;
+    int field_group;
+    int field_chunk;
+    int lu_rows_per_cta;
+} fh_tuning;
+
+fh_status fh_get_tuning(const fh_ctx *ctx, fh_tuning *out);
+
+/* Applies t (FH_EINVAL for a value outside the sets above; nothing changes).
+ * With a discretization present its work lists are rebuilt at once; densities,
+ * spectra and target fields already computed stay valid. */
+fh_status fh_set_tuning(fh_ctx *ctx, const fh_tuning *t);
+
+/* Autotuner (schedule selection by measurement): after fh_discretize[_batch],
+ * times each candidate of the assembly (assemble_group 2, 4, 8), the
+ * tensor-core factorisation (lu_rows_per_cta 512, 256, 128; mixed TF32/BF16
+ * only) and the target fields at the n_x targets x (host, 2 n_x interleaved;
+ * field_group 2, 4, 8 x field_chunk 16, 32, 64; skipped when n_x == 0), each
+ * as the fastest of `reps` (>= 1) runs on the context stream, one phase at a
+ * time with the others at their current settings, and applies the fastest.
+ * The runs overwrite the matrices, factors and target-field scratch but not
+ * the densities: a solved context stays solved (densities from the previous
+ * schedule), and target fields are recomputed by the next fh_sample.  Before
+ * the first solve the densities are zeroed for the field runs.  chosen (may
+ * be NULL) receives the applied tuning; ms (may be NULL) receives the best
+ * time of each tuned phase {assembly, factorisation, target fields} in ms
+ * (0 for a phase not tuned).  Blocks until done. */
+fh_status fh_autotune(fh_ctx *ctx, const double *x, int n_x, int reps, fh_tuning *chosen,
+                      double ms[3]);
+
 /* enable != 0: bracket every kernel group with CUDA events on the context
  * stream (adds two event records per group).  Launch counts are always kept. */
 fh_status fh_set_timing(fh_ctx *ctx, int enable);

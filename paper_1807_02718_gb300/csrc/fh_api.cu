@@ -35,8 +35,9 @@ void free_buf(DevBuf &b) {
 }
 
 // One problem of the batch.  Its solves are s_begin .. s_begin + J - 2
-// (frequency j = s - s_begin + 1), its frequency subgroups g_begin .. g_end-1
-// and its field work items item_begin .. item_end-1 (global indices).
+// (frequency j = s - s_begin + 1), its assembly subgroups g_begin .. g_end-1,
+// its target-field subgroups fg_begin .. fg_end-1 and its field work items
+// item_begin .. item_end-1 (global indices).
 struct Problem {
     fh_curve curve{};
     int J = 0, M = 0;
@@ -45,6 +46,7 @@ struct Problem {
     std::vector<int> Nj;
     int s_begin = 0;
     int g_begin = 0, g_end = 0;
+    int fg_begin = 0, fg_end = 0;
     int item_begin = 0, item_end = 0;
     long long nu_off = 0, ph_off = 0, omega_off = 0;   // into the pooled tables
     bool spectra = false;
@@ -88,16 +90,19 @@ struct fh_ctx {
     std::vector<int> solve_prob, solve_j, solve_N, vec_off, tab_of, tab_N, tab_off, order;
     std::vector<long long> mat_off;
     std::vector<double> kappa_s, eta_s;
-    // frequency subgroups (one problem, equal N, at most fh::kGroup solves)
+    // schedule parameters (fh_set_tuning, fh_autotune)
+    fh_tuning tune{fh::kGroup, fh::kGroup, fh::kFieldChunk, 512};
+    // frequency subgroups (one problem, equal N, at most tune.assemble_group
+    // solves for the assembly, tune.field_group for the target fields)
     int n_groups = 0;
     long long group_tiles = 0;
-    std::vector<int2> sg;
+    std::vector<int2> sg, fsg;
     std::vector<long long> sg_tile_off;
-    std::vector<double> sg_dk;
-    std::vector<int2> field_items;      // (subgroup, first node)
-    std::vector<int> item_first;        // first item per subgroup, + end
+    std::vector<double> sg_dk, fsg_dk;
+    std::vector<int2> field_items;      // (field subgroup, first node)
+    std::vector<int> item_first;        // first item per field subgroup, + end
 
-    DevBuf d_sg, d_sg_tile_off, d_sg_dk, d_tmp_sg, d_items, d_item_first, d_part;
+    DevBuf d_sg, d_sg_tile_off, d_sg_dk, d_fsg, d_fsg_dk, d_tmp_sg, d_items, d_item_first, d_part;
     DevBuf d_N, d_mat_off, d_vec_off, d_tab, d_tab_off, d_tab_N, d_kappa, d_eta, d_solve_j,
         d_solve_prob, d_order, d_curves, d_pdir;
     DevBuf d_zf, d_dzf, d_sf, d_wpf;
@@ -107,7 +112,7 @@ struct fh_ctx {
     int n_rchunk = 0, n_dblk = 0;
     DevBuf d_wa, d_a;
     int n_x_last = 0;
-    DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm;
+    DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm, d_Gs, d_Vs;
     DevBuf d_tmpA, d_tmpg, d_tmp_ll, d_tmp_d;
 
     // timing: pending (phase, start, stop) event triples and totals
@@ -127,12 +132,12 @@ struct fh_ctx {
     }
 
     ~fh_ctx() {
-        DevBuf *all[] = {&d_sg, &d_sg_tile_off, &d_sg_dk, &d_tmp_sg, &d_items, &d_item_first,
+        DevBuf *all[] = {&d_sg, &d_sg_tile_off, &d_sg_dk, &d_fsg, &d_fsg_dk, &d_tmp_sg, &d_items, &d_item_first,
                          &d_part, &d_N, &d_mat_off, &d_vec_off, &d_tab, &d_tab_off, &d_tab_N,
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_zf, &d_dzf, &d_sf, &d_wpf, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_A32, &d_piv, &d_g, &d_iters,
-                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm,
+                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_Gs, &d_Vs,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
         for (DevBuf *b : all) free_buf(*b);
         free_problems();
@@ -312,6 +317,92 @@ fh::Subgroups groups(fh_ctx *ctx) {
     return g;
 }
 
+fh::Subgroups field_groups(fh_ctx *ctx) {
+    fh::Subgroups g;
+    g.sg = ctx->d_fsg.as<int2>();
+    g.tile_off = nullptr;
+    g.dkappa = ctx->d_fsg_dk.as<double>();
+    return g;
+}
+
+bool tuning_valid(const fh_tuning &t) {
+    return t.assemble_group >= 1 && t.assemble_group <= fh::kGroup && t.field_group >= 1 &&
+           t.field_group <= fh::kGroup &&
+           (t.field_chunk == 16 || t.field_chunk == 32 || t.field_chunk == 64) &&
+           (t.lu_rows_per_cta == 128 || t.lu_rows_per_cta == 256 || t.lu_rows_per_cta == 512);
+}
+
+// Splits each problem's solves into runs of equal N of at most gmax solves:
+// (first solve, count) and the mean kappa step of each run.
+void split_groups(fh_ctx *ctx, int gmax, std::vector<int2> &sg, std::vector<double> &dk,
+                  std::vector<int> &first, std::vector<int> &end) {
+    sg.clear();
+    dk.clear();
+    first.assign(ctx->probs.size(), 0);
+    end.assign(ctx->probs.size(), 0);
+    for (size_t q = 0; q < ctx->probs.size(); ++q) {
+        const Problem &pb = ctx->probs[q];
+        first[q] = (int)sg.size();
+        const int s_end = pb.s_begin + pb.S();
+        for (int s = pb.s_begin; s < s_end;) {
+            int cnt = 1;
+            while (s + cnt < s_end && cnt < gmax && ctx->solve_N[s + cnt] == ctx->solve_N[s]) ++cnt;
+            sg.push_back(make_int2(s, cnt));
+            dk.push_back(cnt > 1 ? (ctx->kappa_s[s + cnt - 1] - ctx->kappa_s[s]) / (cnt - 1) : 0.0);
+            s += cnt;
+        }
+        end[q] = (int)sg.size();
+    }
+}
+
+// Work lists of the assembly and target-field kernels under ctx->tune
+// (subgroups never cross problems; field items are chunks of field
+// subgroups).  A new schedule is a new launch sequence: disc_gen advances.
+fh_status build_schedules(fh_ctx *ctx) {
+    std::vector<int> first, end;
+    split_groups(ctx, ctx->tune.assemble_group, ctx->sg, ctx->sg_dk, first, end);
+    ctx->sg_tile_off.clear();
+    long long gt = 0;
+    for (const int2 &g : ctx->sg) {
+        ctx->sg_tile_off.push_back(gt);
+        const long long nt = (ctx->solve_N[g.x] + 31) / 32;
+        gt += nt * nt;
+    }
+    ctx->sg_tile_off.push_back(gt);
+    for (size_t q = 0; q < ctx->probs.size(); ++q) {
+        ctx->probs[q].g_begin = first[q];
+        ctx->probs[q].g_end = end[q];
+    }
+    ctx->n_groups = (int)ctx->sg.size();
+    ctx->group_tiles = gt;
+
+    split_groups(ctx, ctx->tune.field_group, ctx->fsg, ctx->fsg_dk, first, end);
+    ctx->field_items.clear();
+    ctx->item_first.clear();
+    for (size_t q = 0; q < ctx->probs.size(); ++q) {
+        Problem &pb = ctx->probs[q];
+        pb.fg_begin = first[q];
+        pb.fg_end = end[q];
+        pb.item_begin = (int)ctx->field_items.size();
+        for (int g = first[q]; g < end[q]; ++g) {
+            ctx->item_first.push_back((int)ctx->field_items.size());
+            for (int i0 = 0; i0 < ctx->solve_N[ctx->fsg[g].x]; i0 += ctx->tune.field_chunk)
+                ctx->field_items.push_back(make_int2(g, i0));
+        }
+        pb.item_end = (int)ctx->field_items.size();
+    }
+    ctx->item_first.push_back((int)ctx->field_items.size());
+    FH_TRY(upload(ctx, ctx->d_sg, ctx->sg));
+    FH_TRY(upload(ctx, ctx->d_sg_tile_off, ctx->sg_tile_off));
+    FH_TRY(upload(ctx, ctx->d_sg_dk, ctx->sg_dk));
+    FH_TRY(upload(ctx, ctx->d_fsg, ctx->fsg));
+    FH_TRY(upload(ctx, ctx->d_fsg_dk, ctx->fsg_dk));
+    FH_TRY(upload(ctx, ctx->d_items, ctx->field_items));
+    FH_TRY(upload(ctx, ctx->d_item_first, ctx->item_first));
+    ++ctx->disc_gen;
+    return FH_OK;
+}
+
 bool is_fin(double v) { return std::isfinite(v); }
 
 // Mixed precision: refinement stops when ||dx||_inf <= kRefineTol ||x||_inf.
@@ -471,39 +562,6 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     ctx->n_tab = (int)ctx->tab_N.size();
     ctx->maxN = maxN;
 
-    // subgroups never cross problems; field items are 64-node chunks of them
-    ctx->sg.clear();
-    ctx->sg_tile_off.clear();
-    ctx->sg_dk.clear();
-    ctx->field_items.clear();
-    ctx->item_first.clear();
-    long long gt = 0;
-    for (int q = 0; q < P; ++q) {
-        Problem &pb = ctx->probs[q];
-        pb.g_begin = (int)ctx->sg.size();
-        pb.item_begin = (int)ctx->field_items.size();
-        const int s_end = pb.s_begin + pb.S();
-        for (int s = pb.s_begin; s < s_end;) {
-            int cnt = 1;
-            while (s + cnt < s_end && cnt < fh::kGroup && ctx->solve_N[s + cnt] == ctx->solve_N[s]) ++cnt;
-            const int g = (int)ctx->sg.size();
-            ctx->sg.push_back(make_int2(s, cnt));
-            ctx->sg_tile_off.push_back(gt);
-            ctx->sg_dk.push_back(cnt > 1 ? (ctx->kappa_s[s + cnt - 1] - ctx->kappa_s[s]) / (cnt - 1) : 0.0);
-            const long long nt = (ctx->solve_N[s] + 31) / 32;
-            gt += nt * nt;
-            ctx->item_first.push_back((int)ctx->field_items.size());
-            for (int i0 = 0; i0 < ctx->solve_N[s]; i0 += fh::kFieldChunk)
-                ctx->field_items.push_back(make_int2(g, i0));
-            s += cnt;
-        }
-        pb.g_end = (int)ctx->sg.size();
-        pb.item_end = (int)ctx->field_items.size();
-    }
-    ctx->sg_tile_off.push_back(gt);
-    ctx->item_first.push_back((int)ctx->field_items.size());
-    ctx->n_groups = (int)ctx->sg.size();
-    ctx->group_tiles = gt;
     ctx->order.resize(S);
     for (int s = 0; s < S; ++s) ctx->order[s] = s;
     std::stable_sort(ctx->order.begin(), ctx->order.end(),
@@ -537,11 +595,7 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     FH_TRY(upload(ctx, ctx->d_solve_prob, ctx->solve_prob));
     FH_TRY(upload(ctx, ctx->d_order, ctx->order));
     FH_TRY(upload(ctx, ctx->d_omega, omega_v));
-    FH_TRY(upload(ctx, ctx->d_sg, ctx->sg));
-    FH_TRY(upload(ctx, ctx->d_sg_tile_off, ctx->sg_tile_off));
-    FH_TRY(upload(ctx, ctx->d_sg_dk, ctx->sg_dk));
-    FH_TRY(upload(ctx, ctx->d_items, ctx->field_items));
-    FH_TRY(upload(ctx, ctx->d_item_first, ctx->item_first));
+    FH_TRY(build_schedules(ctx));
     FH_TRY(upload(ctx, ctx->d_curves, cps));
     FH_TRY(upload(ctx, ctx->d_pdir, pdir));
     FH_TRY(ensure(ctx, ctx->d_z, (size_t)vo * sizeof(double2)));
@@ -637,58 +691,77 @@ fh_status spectra_common(fh_ctx *ctx, Problem &pb, const double *d_a, int n_samp
     return FH_OK;
 }
 
-fh_status synth_buffers(fh_ctx *ctx, Problem &pb, int n_T) {
-    FH_TRY(ensure(ctx, ctx->d_Gr, (size_t)pb.J * n_T * sizeof(double)));
-    FH_TRY(ensure(ctx, ctx->d_Gm, (size_t)pb.J * n_T * sizeof(double)));
+// FP64: weight planes Gr, Gm; mixed: the double-float weights Gs and the
+// double-float copy Vs of the target fields (2J rows each, padded pitch).
+fh_status synth_buffers(fh_ctx *ctx, Problem &pb, int n_x, int n_T) {
+    if (ctx->precision == FH_FP64) {
+        FH_TRY(ensure(ctx, ctx->d_Gr, (size_t)pb.J * n_T * sizeof(double)));
+        FH_TRY(ensure(ctx, ctx->d_Gm, (size_t)pb.J * n_T * sizeof(double)));
+    } else {
+        FH_TRY(ensure(ctx, ctx->d_Gs, (size_t)2 * pb.J * fh::synth_pitch(n_T) * sizeof(float2)));
+        FH_TRY(ensure(ctx, ctx->d_Vs, (size_t)2 * pb.J * fh::synth_pitch(n_x) * sizeof(float2)));
+    }
     return ensure(ctx, ctx->d_Bf, (size_t)pb.K * pb.J * sizeof(float4));
 }
 
 // Weights G_p(t) and the contraction u = Re sum_p V_p G_p (buffers exist).
 fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
+    const bool mixed = ctx->precision != FH_FP64;
     {
         PhaseScope ps(ctx, FH_PH_WEIGHTS, 2);
         fh::launch_synth_weights(pb.J, pb.M, pb.W, pb.K, pb.d_s.as<double>(), pb.d_B.as<double2>(),
                                  ctx->d_Bf.as<float4>(), ctx->d_nu_f.as<float4>() + pb.nu_off,
                                  ctx->d_ph.as<double2>() + pb.ph_off, d_T, n_T,
-                                 ctx->d_Gr.as<double>(), ctx->d_Gm.as<double>(), ctx->stream);
+                                 ctx->d_Gr.as<double>(), ctx->d_Gm.as<double>(),
+                                 mixed ? ctx->d_Gs.as<float2>() : nullptr, ctx->stream);
         FH_TRY(check_launch(ctx, "synthesis weights"));
     }
-    PhaseScope ps(ctx, FH_PH_CONTRACT, 1);
-    fh::launch_synth_contract(pb.J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Gr.as<double>(),
-                              ctx->d_Gm.as<double>(), d_u, ctx->precision != FH_FP64, ctx->stream);
+    PhaseScope ps(ctx, FH_PH_CONTRACT, mixed ? 2 : 1);
+    if (mixed)
+        fh::launch_synth_contract_df(pb.J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Vs.as<float2>(),
+                                     ctx->d_Gs.as<float2>(), d_u, ctx->stream);
+    else
+        fh::launch_synth_contract(pb.J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Gr.as<double>(),
+                                  ctx->d_Gm.as<double>(), d_u, ctx->stream);
     return check_launch(ctx, "synthesis contraction");
 }
 
 fh_status synth_common(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
-    FH_TRY(synth_buffers(ctx, pb, n_T));
+    FH_TRY(synth_buffers(ctx, pb, n_x, n_T));
     return synth_kernels(ctx, pb, n_x, d_T, n_T, d_u);
+}
+
+// Target fields of one problem into d_V (d_V and d_part exist).
+fh_status field_kernels(fh_ctx *ctx, Problem &pb, const double *d_x, int n_x) {
+    PhaseScope ps(ctx, FH_PH_FIELD, pb.S() > 0 ? 3 : 1);
+    fh::launch_target_field(tables(ctx), field_groups(ctx), pb.fg_begin, pb.fg_end - pb.fg_begin,
+                            ctx->d_items.as<int2>(), pb.item_begin, pb.item_end - pb.item_begin,
+                            ctx->tune.field_chunk, ctx->d_item_first.as<int>(), ctx->d_solve_j.as<int>(),
+                            ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(), ctx->d_psi.as<double2>(),
+                            d_x, n_x, ctx->d_zf.as<float4>(), ctx->d_part.as<double2>(),
+                            ctx->d_V.as<double2>(), ctx->precision != FH_FP64, ctx->stream);
+    return check_launch(ctx, "target field");
+}
+
+// Scratch of the target fields of one problem at n_x targets.
+fh_status field_buffers(fh_ctx *ctx, const Problem &pb, int n_x) {
+    FH_TRY(ensure(ctx, ctx->d_V, (size_t)pb.J * n_x * sizeof(double2)));
+    const int n_items = pb.item_end - pb.item_begin;
+    return ensure(ctx, ctx->d_part, (size_t)n_items * fh::kGroup * (size_t)n_x * sizeof(double2));
 }
 
 // Target fields, weights and contraction for one problem (buffers exist).
 fh_status sample_kernels(fh_ctx *ctx, Problem &pb, const double *d_x, int n_x, const double *d_T,
                          int n_T, double *d_u) {
-    const int n_items = pb.item_end - pb.item_begin;
-    {
-        PhaseScope ps(ctx, FH_PH_FIELD, pb.S() > 0 ? 3 : 1);
-        fh::launch_target_field(tables(ctx), groups(ctx), pb.g_begin, pb.g_end - pb.g_begin,
-                                ctx->d_items.as<int2>(), pb.item_begin, n_items,
-                                ctx->d_item_first.as<int>(), ctx->d_solve_j.as<int>(),
-                                ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                                ctx->d_psi.as<double2>(), d_x, n_x, ctx->d_zf.as<float4>(),
-                                ctx->d_part.as<double2>(),
-                                ctx->d_V.as<double2>(), ctx->precision != FH_FP64, ctx->stream);
-        FH_TRY(check_launch(ctx, "target field"));
-    }
+    FH_TRY(field_kernels(ctx, pb, d_x, n_x));
     return synth_kernels(ctx, pb, n_x, d_T, n_T, d_u);
 }
 
 fh_status sample_common(fh_ctx *ctx, int q, const double *d_x, int n_x, const double *d_T,
                         int n_T, double *d_u) {
     Problem &pb = ctx->probs[q];
-    FH_TRY(ensure(ctx, ctx->d_V, (size_t)pb.J * n_x * sizeof(double2)));
-    const int n_items = pb.item_end - pb.item_begin;
-    FH_TRY(ensure(ctx, ctx->d_part, (size_t)n_items * fh::kGroup * (size_t)n_x * sizeof(double2)));
-    FH_TRY(synth_buffers(ctx, pb, n_T));
+    FH_TRY(field_buffers(ctx, pb, n_x));
+    FH_TRY(synth_buffers(ctx, pb, n_x, n_T));
     const long long key = graph_key(ctx, q + ((long long)pb.K << 24), n_x + ((long long)n_T << 32),
                                     (long long)(uintptr_t)d_x, (long long)(uintptr_t)d_T,
                                     (long long)(uintptr_t)d_u);
@@ -807,20 +880,40 @@ fh_status fh_num_problems(fh_ctx *ctx, int *P) {
     return FH_OK;
 }
 
+// All matrices A_s into d_A (column-major, FP64).
+fh_status assemble_kernels(fh_ctx *ctx) {
+    fh::launch_assemble_groups(tables(ctx), groups(ctx), ctx->n_groups, ctx->group_tiles,
+                               ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                               ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
+                               ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
+                               ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(),
+                               ctx->d_wpf.as<float2>(), ctx->d_A.as<double2>(), 0,
+                               ctx->precision != FH_FP64, ctx->stream);
+    return check_launch(ctx, "assemble");
+}
+
+// Row-major FP32 copy of d_A and its tensor-core LU (d_info is cleared by
+// the caller).
+fh_status tc_factor_kernels(fh_ctx *ctx) {
+    FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
+    fh::launch_convert_rowmajor(ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
+                                ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->stream);
+    const cudaError_t e = fh::launch_lu_factor_tc(
+        ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>(),
+        ctx->order.data(), ctx->solve_N.data(), ctx->S, ctx->d_N.as<int>(),
+        ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),
+        ctx->d_vec_off.as<int>(), ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
+    return FH_OK;
+}
+
 // The kernel sequence of fh_solve_frequencies (assembly, right sides,
 // factorisation, refinement); all buffers exist already.
 fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     const fh::SolveTables t = tables(ctx);
     {
         PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
-        fh::launch_assemble_groups(t, groups(ctx), ctx->n_groups, ctx->group_tiles,
-                                   ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                                   ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
-                                   ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
-                                   ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(),
-                                   ctx->d_wpf.as<float2>(), ctx->d_A.as<double2>(), 0,
-                                   ctx->precision != FH_FP64, ctx->stream);
-        FH_TRY(check_launch(ctx, "assemble"));
+        FH_TRY(assemble_kernels(ctx));
         fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                        ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
                        mixed ? ctx->d_g.as<double2>() : ctx->d_psi.as<double2>(), ctx->stream);
@@ -837,18 +930,12 @@ fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     } else {
         {
             // launches: conversion and one LU launch per cluster size (SIMT: one)
-            PhaseScope ps(ctx, FH_PH_FACTOR, 1 + (tc ? fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S) : 1));
+            PhaseScope ps(ctx, FH_PH_FACTOR,
+                          1 + (tc ? fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S,
+                                                       ctx->tune.lu_rows_per_cta)
+                                  : 1));
             if (tc) {
-                FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
-                fh::launch_convert_rowmajor(ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
-                                            ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->stream);
-                const cudaError_t e = fh::launch_lu_factor_tc(
-                    ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->d_order.as<int>(), ctx->order.data(),
-                    ctx->solve_N.data(), ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
-                    ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_vec_off.as<int>(),
-                    ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->stream);
-                if (e != cudaSuccess)
-                    return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
+                FH_TRY(tc_factor_kernels(ctx));
             } else {
                 fh::launch_convert_fp32(ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->mat_total,
                                         ctx->stream);
@@ -1246,6 +1333,175 @@ fh_status fh_set_graphs(fh_ctx *ctx, int enable) {
     FH_TRY(enter(ctx));
     ctx->graphs = enable != 0;
     ctx->solve_graph.seen = ctx->sample_graph.seen = -1;
+    return FH_OK;
+}
+
+fh_status fh_get_tuning(const fh_ctx *ctx, fh_tuning *out) {
+    if (!ctx || !out) return FH_EINVAL;
+    *out = ctx->tune;
+    return FH_OK;
+}
+
+fh_status fh_set_tuning(fh_ctx *ctx, const fh_tuning *t) {
+    FH_TRY(enter(ctx));
+    if (!t || !tuning_valid(*t))
+        return fail(ctx, FH_EINVAL, "tuning out of range (assemble_group, field_group in [1, %d]; "
+                                    "field_chunk 16, 32 or 64; lu_rows_per_cta 128, 256 or 512)",
+                    fh::kGroup);
+    ctx->tune = *t;
+    if (ctx->geom) FH_TRY(build_schedules(ctx));
+    return FH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The fastest of `reps` runs of launch() (CUDA events on the context stream)
+// after one untimed run (module loading, scratch allocation).
+template <class Launch>
+fh_status time_best(fh_ctx *ctx, int reps, double &best, Launch &&launch) {
+    FH_TRY(launch());
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        cudaGetLastError();
+        return fail(ctx, FH_ECUDA, "autotune: event creation failed");
+    }
+    best = HUGE_VAL;
+    fh_status st = FH_OK;
+    for (int r = 0; r < reps && st == FH_OK; ++r) {
+        cudaEventRecord(a, ctx->stream);
+        st = launch();
+        cudaEventRecord(b, ctx->stream);
+        if (st != FH_OK) break;
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) st = fail(ctx, FH_ECUDA, "autotune: %s", cudaGetErrorString(e));
+        else best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+// Tries every value of one tuning field (the others fixed), keeps the
+// fastest and leaves the schedule built for it.
+template <class Launch>
+fh_status tune_field(fh_ctx *ctx, int reps, int fh_tuning::*field, const std::vector<int> &values,
+                     double &best_ms, Launch &&launch) {
+    int best_v = ctx->tune.*field;
+    best_ms = HUGE_VAL;
+    for (int v : values) {
+        ctx->tune.*field = v;
+        FH_TRY(build_schedules(ctx));
+        double ms = 0.0;
+        FH_TRY(time_best(ctx, reps, ms, launch));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_v = v;
+        }
+    }
+    ctx->tune.*field = best_v;
+    return build_schedules(ctx);
+}
+
+fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_out[3]) {
+    const bool tc = ctx->precision == FH_MIXED_TF32 || ctx->precision == FH_MIXED_BF16;
+    // 1. assembly: frequencies per subgroup
+    FH_TRY(ensure(ctx, ctx->d_A, (size_t)ctx->mat_total * sizeof(double2)));
+    FH_TRY(tune_field(ctx, reps, &fh_tuning::assemble_group, {2, 4, 8}, ms_out[0],
+                      [&]() { return assemble_kernels(ctx); }));
+    // 2. tensor-core factorisation of the assembled matrices: CTAs per system
+    if (tc && ctx->maxN <= fh::kTcMaxN) {
+        FH_TRY(ensure(ctx, ctx->d_A32, (size_t)ctx->mat_total * sizeof(float2)));
+        FH_TRY(ensure(ctx, ctx->d_piv, (size_t)ctx->vec_total * sizeof(int)));
+        FH_TRY(ensure(ctx, ctx->d_info, (size_t)ctx->S * sizeof(int)));
+        FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
+        FH_TRY(assemble_kernels(ctx));
+        std::vector<int> info(ctx->S);
+        FH_TRY(tune_field(ctx, reps, &fh_tuning::lu_rows_per_cta, {512, 256, 128}, ms_out[1], [&]() {
+            FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
+            FH_TRY(tc_factor_kernels(ctx));
+            FH_CUDA(ctx, cudaMemcpyAsync(info.data(), ctx->d_info.p, (size_t)ctx->S * sizeof(int),
+                                         cudaMemcpyDeviceToHost, ctx->stream));
+            FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            for (int s = 0; s < ctx->S; ++s)
+                if (info[s] == -2)
+                    return fail(ctx, FH_ETIMEOUT, "autotune: a tensor-core completion wait gave up");
+            return FH_OK;
+        }));
+    }
+    // 3. target fields at the caller's targets: subgroup size x node chunk
+    if (n_x > 0) {
+        FH_TRY(ensure(ctx, ctx->d_x, (size_t)2 * n_x * sizeof(double)));
+        FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_x.p, x, (size_t)2 * n_x * sizeof(double),
+                                     cudaMemcpyHostToDevice, ctx->stream));
+        if (!ctx->solved)
+            FH_CUDA(ctx, cudaMemsetAsync(ctx->d_psi.p, 0, (size_t)ctx->vec_total * sizeof(double2),
+                                         ctx->stream));
+        auto fields = [&]() {
+            for (Problem &pb : ctx->probs) {
+                FH_TRY(field_buffers(ctx, pb, n_x));
+                FH_TRY(field_kernels(ctx, pb, ctx->d_x.as<double>(), n_x));
+            }
+            return FH_OK;
+        };
+        int best_g = ctx->tune.field_group, best_c = ctx->tune.field_chunk;
+        ms_out[2] = HUGE_VAL;
+        for (int g : {2, 4, 8})
+            for (int c : {16, 32, 64}) {
+                ctx->tune.field_group = g;
+                ctx->tune.field_chunk = c;
+                FH_TRY(build_schedules(ctx));
+                double ms = 0.0;
+                FH_TRY(time_best(ctx, reps, ms, fields));
+                if (ms < ms_out[2]) {
+                    ms_out[2] = ms;
+                    best_g = g;
+                    best_c = c;
+                }
+            }
+        ctx->tune.field_group = best_g;
+        ctx->tune.field_chunk = best_c;
+        FH_TRY(build_schedules(ctx));
+        ctx->have_V = false;
+    }
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fh_status fh_autotune(fh_ctx *ctx, const double *x, int n_x, int reps, fh_tuning *chosen,
+                      double ms[3]) {
+    FH_TRY(enter(ctx));
+    if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_autotune: call fh_discretize first");
+    if (n_x < 0 || (n_x > 0 && !x)) return fail(ctx, FH_EINVAL, "x must hold 2 n_x values");
+    if (reps < 1) return fail(ctx, FH_EINVAL, "reps must be >= 1");
+    // tuning runs neither count as launches nor enter the phase timings
+    const bool timing = ctx->timing;
+    long long launches[FH_NUM_PHASES];
+    std::memcpy(launches, ctx->launches, sizeof(launches));
+    ctx->timing = false;
+    double best[3] = {0.0, 0.0, 0.0};
+    const fh_tuning before = ctx->tune;
+    const fh_status st = autotune(ctx, x, n_x, reps, best);
+    ctx->timing = timing;
+    std::memcpy(ctx->launches, launches, sizeof(launches));
+    if (st != FH_OK) {
+        const std::string msg = ctx->err;
+        ctx->tune = before;
+        build_schedules(ctx);
+        ctx->err = msg;
+        return st;
+    }
+    if (chosen) *chosen = ctx->tune;
+    if (ms)
+        for (int i = 0; i < 3; ++i) ms[i] = best[i];
     return FH_OK;
 }
 

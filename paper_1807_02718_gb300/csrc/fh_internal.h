@@ -82,14 +82,18 @@ void launch_lu_factor_fp32(const int *order, int S, const int *N, const long lon
                            cudaStream_t st);
 // Tensor-core LU of the row-major FP32 copy (launch_convert_rowmajor); kind 2:
 // 3xTF32 operands, kind 1: 3xBF16.  order_h / N_h: host copies of order (by
-// decreasing N) and N, used to launch each cluster size (1, 2, 4, 8 CTAs for
-// N <= 512, 1024, 2048, 4096) separately.  err is set and info[s] = -2 if a
+// decreasing N) and N, used to launch each cluster size separately.  A system
+// of order N is factored by the smallest power of two of CTAs, at most 8, that
+// is >= N / rows_per_cta (rows_per_cta 128, 256 or 512; 512 gives 1, 2, 4, 8
+// CTAs for N <= 512, 1024, 2048, 4096).  err is set and info[s] = -2 if a
 // tensor-core completion wait gave up.
 constexpr int kTcMaxN = 4096;
-int lu_tc_launches(const int *order_h, const int *N_h, int S);
+int lu_tc_cluster(int n, int rows_per_cta);
+int lu_tc_launches(const int *order_h, const int *N_h, int S, int rows_per_cta);
 void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const double2 *A,
                              float2 *A32, cudaStream_t st);
-cudaError_t launch_lu_factor_tc(int kind, const int *order, const int *order_h, const int *N_h, int S,
+cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, const int *order_h,
+                                const int *N_h, int S,
                                 const int *N, const long long *mat_off, float2 *A32, int *piv,
                                 const int *vec_off, int *info, int *err, cudaStream_t st);
 // FP64 iterative refinement against the column-major FP64 matrices; chunks
@@ -114,17 +118,17 @@ void launch_window_spectra(const double *a, int n_samples, long long start0, lon
 
 // ---- target fields (k_field.cu) ----
 // V[j * n_x + i] = V(x_i, omega_j); V[0 * n_x + i] = 1 (omega_0 = 0).
-// Work items (subgroup, first node) of kFieldChunk nodes; item_first[g] is
-// the first item of subgroup g (global, one entry past the last subgroup).
-// One problem's subgroups g_begin .. g_begin + n_groups - 1 own the items
-// item_begin .. item_begin + n_items - 1.  part: scratch of
+// Work items (subgroup, first node) of `chunk` <= kFieldChunk nodes;
+// item_first[g] is the first item of subgroup g (global, one entry past the
+// last subgroup).  One problem's subgroups g_begin .. g_begin + n_groups - 1
+// own the items item_begin .. item_begin + n_items - 1.  part: scratch of
 // n_items * kGroup * n_x complex values.
 constexpr int kFieldChunk = 64;
 void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
-                         const int2 *items, int item_begin, int n_items, const int *item_first,
-                         const int *solve_j, const double2 *z, const double2 *dz,
-                         const double2 *psi, const double *x, int n_x, const float4 *zf, double2 *part,
-                         double2 *V, bool double_float,
+                         const int2 *items, int item_begin, int n_items, int chunk,
+                         const int *item_first, const int *solve_j, const double2 *z,
+                         const double2 *dz, const double2 *psi, const double *x, int n_x,
+                         const float4 *zf, double2 *part, double2 *V, bool double_float,
                          cudaStream_t st);
 
 // Kernel Bessel routine on n arguments: out[6i..6i+5] = J0, Y0, J1, Y1 (joint
@@ -141,14 +145,21 @@ constexpr int kFarTerms = 170;
 void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, double2 *phase_tab,
                       cudaStream_t st);
 // Gr/Gm: planes [p][t] with u(x,t) = sum_p Vr[p][x] Gr[p][t] + Vi[p][x] Gm[p][t].
-// Bf: optional scratch of K * J float4 for the double-float copy of B (one
-// extra launch); null splits B on the fly.
+// Gs (optional; then Gr/Gm are not written): the same weights as double-float
+// pairs (hi, lo), rows p = Gr[p] and J + p = Gm[p], row pitch synth_pitch(n_T),
+// for launch_synth_contract_df.  Bf: optional scratch of K * J float4 for the
+// double-float copy of B (one extra launch); null splits B on the fly.
+inline int synth_pitch(int n) { return (n + 3) & ~3; }
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
                           float4 *Bf, const float4 *nu_f, const double2 *phase_tab, const double *T,
-                          int n_T, double *Gr, double *Gm, cudaStream_t st);
-// double_float: operands split into FP32 pairs, products exact, double-float
-// accumulation (mixed-precision paths); else FP64 FMAs.
+                          int n_T, double *Gr, double *Gm, float2 *Gs, cudaStream_t st);
+// FP64 contraction u = [Vr | Vi] [Gr ; Gm] (FP64 FMAs).
 void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,
-                           const double *Gm, double *u, bool double_float, cudaStream_t st);
+                           const double *Gm, double *u, cudaStream_t st);
+// Double-float contraction (mixed-precision paths): V is split into Vs
+// (scratch of 2J rows of synth_pitch(n_x) float2), then u = Vs^T Gs with exact
+// products and double-float accumulation.  Two launches.
+void launch_synth_contract_df(int J, int n_x, int n_T, const double2 *V, float2 *Vs,
+                              const float2 *Gs, double *u, cudaStream_t st);
 
 }  // namespace fh

@@ -16,9 +16,9 @@ namespace fh {
 namespace {
 
 constexpr int kTgt = 128;
-constexpr int kChunk = 64;   // source nodes per work item
+constexpr int kChunk = kFieldChunk;   // largest number of source nodes per work item
 
-// Work item w = (subgroup g, node chunk c).  One CTA per (128 targets, item):
+// Work item w = (subgroup g, chunk of `chunk` <= kChunk nodes).  One CTA per (128 targets, item):
 // for each target-node pair the distance r, 1/r, sqrt(2/(pi r)),
 // e^{i(kappa_0 r - pi/4)} and the step e^{i dkappa r} are formed once; each
 // frequency j of the subgroup then needs only the Horner P0/Q0 series
@@ -28,7 +28,7 @@ constexpr int kChunk = 64;   // source nodes per work item
 // scratch; field_reduce_kernel adds them in a fixed order (the result does
 // not depend on scheduling).
 __global__ void __launch_bounds__(kTgt) field_partial_kernel(
-    SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin,
+    SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin, int chunk,
     const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
     double2 *__restrict__ part) {
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kTgt) field_partial_kernel(
         ikap[j] = 1.0 / k;
         isqk[j] = 1.0 / sqrt(k);
     }
-    const int ne = min(kChunk, N - i0);
+    const int ne = min(chunk, N - i0);
     for (int e = threadIdx.x; e < kChunk; e += kTgt) {
         const int i = i0 + e;
         double2 zz = make_double2(0.0, 0.0);
@@ -142,7 +142,7 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool 
 // arguments kappa_0 r and dkappa r with their reduction modulo pi/2 and for
 // the small-argument series (kappa r < 8).
 __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
-    SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin,
+    SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin, int chunk,
     const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
     const float4 *__restrict__ zf, double2 *__restrict__ part) {
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
         isqk[j] = df_from(1.0 / sqrt(k));
         corrf[j] = (float)(k - ((j < cnt ? t.kappa[s0] : 1.0) + j * dk));
     }
-    const int ne = min(kChunk, N - i0);
+    const int ne = min(chunk, N - i0);
     for (int e = threadIdx.x; e < kChunk; e += kTgt) {
         const int i = i0 + e;
         float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -336,19 +336,21 @@ void launch_bessel_eval_df(const double *x, int n, double *out, cudaStream_t st)
 }
 
 void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
-                         const int2 *items, int item_begin, int n_items, const int *item_first,
-                         const int *solve_j, const double2 *z, const double2 *dz,
-                         const double2 *psi, const double *x, int n_x, const float4 *zf,
-                         double2 *part, double2 *V, bool double_float, cudaStream_t st) {
+                         const int2 *items, int item_begin, int n_items, int chunk,
+                         const int *item_first, const int *solve_j, const double2 *z,
+                         const double2 *dz, const double2 *psi, const double *x, int n_x,
+                         const float4 *zf, double2 *part, double2 *V, bool double_float,
+                         cudaStream_t st) {
     if (n_x <= 0) return;
     field_zero_freq_kernel<<<(n_x + 255) / 256, 256, 0, st>>>(n_x, V);
     if (n_groups <= 0 || n_items <= 0) return;
     dim3 grid((n_x + kTgt - 1) / kTgt, n_items);
     if (double_float)
-        field_partial_df_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, zf,
-                                                       part);
+        field_partial_df_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, chunk, z, dz, psi, x,
+                                                       n_x, zf, part);
     else
-        field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, z, dz, psi, x, n_x, part);
+        field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, chunk, z, dz, psi, x, n_x,
+                                                    part);
     dim3 g2((n_x + 127) / 128, n_groups);
     field_reduce_kernel<<<g2, 128, 0, st>>>(g, g_begin, item_first, item_begin, solve_j, part, n_x, V);
 }

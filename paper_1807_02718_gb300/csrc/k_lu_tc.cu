@@ -13,8 +13,11 @@
 // carries about 2^-21 (TF32) or 2^-16 (BF16) relative accuracy.
 //
 // Layout and parallelism.  The FP32 matrix is row-major.  A system of order n
-// is factored by a cluster of cs = ceil(n / 512) CTAs (1, 2, 4 or 8) of 512
-// threads; thread t of CTA r owns panel row ("slot") 512 r + t.  Per panel of
+// is factored by a cluster of cs >= ceil(n / 512) CTAs (1, 2, 4 or 8; more
+// than the minimum spreads the trailing updates, lu_tc_cluster) of 512
+// threads; thread t of CTA r owns panel row ("slot") 512 r + t, and a CTA
+// whose slots are all past the active rows takes part with empty candidates.
+// Per panel of
 // nb = 32 columns:
 //   1. the panel rows are loaded into registers (32 complex per thread) and
 //      factored column by column: one arg-max per column over the cluster
@@ -611,14 +614,24 @@ cudaError_t launch_group(const int *order, int count, int cs, const int *N, cons
                               A32, piv, info, err);
 }
 
-int cluster_for(int n) { return n <= 512 ? 1 : n <= 1024 ? 2 : n <= 2048 ? 4 : 8; }
-
 }  // namespace
 
-int lu_tc_launches(const int *order_h, const int *N_h, int S) {
+// Every CTA owns kThreads = 512 panel rows, so at least ceil(n / 512) CTAs;
+// smaller rows_per_cta spreads the trailing updates over more CTAs.
+int lu_tc_cluster(int n, int rows_per_cta) {
+    const int rows = rows_per_cta >= kThreads ? kThreads : rows_per_cta >= 256 ? 256 : 128;
+    const int need = (n + rows - 1) / rows;
+    int cs = 1;
+    while (cs < need && cs < 8) cs *= 2;
+    return cs;
+}
+
+int lu_tc_launches(const int *order_h, const int *N_h, int S, int rows_per_cta) {
     int count = 0;
     for (int i = 0; i < S; ++i)
-        if (i == 0 || cluster_for(N_h[order_h[i]]) != cluster_for(N_h[order_h[i - 1]])) ++count;
+        if (i == 0 || lu_tc_cluster(N_h[order_h[i]], rows_per_cta) !=
+                          lu_tc_cluster(N_h[order_h[i - 1]], rows_per_cta))
+            ++count;
     return count;
 }
 
@@ -628,7 +641,8 @@ void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, cons
     convert_rowmajor_kernel<<<dim3(S, 16), dim3(32, 8), 0, st>>>(N, mat_off, A, A32);
 }
 
-cudaError_t launch_lu_factor_tc(int kind, const int *order, const int *order_h, const int *N_h, int S,
+cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, const int *order_h,
+                                const int *N_h, int S,
                                 const int *N, const long long *mat_off, float2 *A32, int *piv,
                                 const int *vec_off, int *info, int *err, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
@@ -644,9 +658,9 @@ cudaError_t launch_lu_factor_tc(int kind, const int *order, const int *order_h, 
     }
     // order is sorted by decreasing N, so each cluster size is a contiguous run
     for (int first = 0; first < S;) {
-        const int cs = cluster_for(N_h[order_h[first]]);
+        const int cs = lu_tc_cluster(N_h[order_h[first]], rows_per_cta);
         int last = first;
-        while (last < S && cluster_for(N_h[order_h[last]]) == cs) ++last;
+        while (last < S && lu_tc_cluster(N_h[order_h[last]], rows_per_cta) == cs) ++last;
         const cudaError_t e = kind == 2
             ? launch_group<2>(order + first, last - first, cs, N, mat_off, A32, piv, vec_off, info, err, st)
             : launch_group<1>(order + first, last - first, cs, N, mat_off, A32, piv, vec_off, info, err, st);

@@ -163,7 +163,8 @@ __device__ __forceinline__ void df_horner(float &ah, float &al, dfl r, float vh,
 __global__ void __launch_bounds__(256) weights_kernel(
     int J, int M, double W, int K, const double *__restrict__ s, const double2 *__restrict__ B,
     const float4 *__restrict__ Bf, const float4 *__restrict__ nu_f, const double2 *__restrict__ ph_g,
-    const double *__restrict__ T, int n_T, double *__restrict__ Gr, double *__restrict__ Gm) {
+    const double *__restrict__ T, int n_T, double *__restrict__ Gr, double *__restrict__ Gm,
+    float2 *__restrict__ Gs, int pitch_T) {
     extern __shared__ double smd[];
     double *wy = smd;                                        // K: y
     double *wf = wy + K;                                     // K: sin(pi y) (near) or scale sinc(y) (far)
@@ -303,8 +304,15 @@ __global__ void __launch_bounds__(256) weights_kernel(
     if (p < J) {
         const double mu = (p == 0 || p == J - 1) ? 1.0 : 2.0;
         const double c = mu / (2.0 * kPi);
-        Gr[(long long)p * n_T + t] = c * ((double)qrh + (double)qrl);
-        Gm[(long long)p * n_T + t] = -c * ((double)qih + (double)qil);
+        const double gr = c * ((double)qrh + (double)qrl), gm = -c * ((double)qih + (double)qil);
+        if (Gs) {
+            const dfl a = df_split(gr), b = df_split(gm);
+            Gs[(long long)p * pitch_T + t] = make_float2(a.hi, a.lo);
+            Gs[(long long)(J + p) * pitch_T + t] = make_float2(b.hi, b.lo);
+        } else {
+            Gr[(long long)p * n_T + t] = gr;
+            Gm[(long long)p * n_T + t] = gm;
+        }
     }
 }
 
@@ -377,54 +385,104 @@ __global__ void __launch_bounds__(256) contract_kernel(int J, int n_x, int n_T,
     }
 }
 
-// The same contraction in double-float arithmetic (mixed-precision paths):
-// operands are split into FP32 (hi, lo) pairs while staged, each product is
-// formed exactly (FMA residual) plus the hi*lo cross terms, and every output
-// accumulates as a double-float pair (two-sum), ~2^-44 relative per step.
-__global__ void __launch_bounds__(256) contract_df_kernel(int J, int n_x, int n_T,
-                                                          const double2 *__restrict__ V,
-                                                          const double *__restrict__ Gr,
-                                                          const double *__restrict__ Gm,
+// V[j][x] (complex FP64) as double-float rows of the contraction's left
+// operand: row j holds the real parts, row J + j the imaginary parts (row
+// pitch px, a multiple of 4).
+__global__ void split_v_kernel(int J, int n_x, int px, const double2 *__restrict__ V,
+                               float2 *__restrict__ Vs) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (x >= px) return;
+    float2 r = make_float2(0.f, 0.f), i = r;
+    if (x < n_x) {
+        const double2 v = V[(long long)j * n_x + x];
+        const dfl a = df_split(v.x), b = df_split(v.y);
+        r = make_float2(a.hi, a.lo);
+        i = make_float2(b.hi, b.lo);
+    }
+    Vs[(long long)j * px + x] = r;
+    Vs[(long long)(J + j) * px + x] = i;
+}
+
+// The contraction in double-float arithmetic (mixed-precision paths):
+//   u[x][t] = sum_{kk < 2J} Vs[kk][x] Gs[kk][t],
+// both operands double-float pairs (hi, lo) with rows along x and t.  Each
+// product is formed exactly (FMA residual) plus the hi*lo cross terms and
+// every output accumulates as a double-float pair (two-sum), ~2^-44 relative
+// per step.  64 x 64 outputs per CTA, 4 x 4 per thread (t in two pairs 32
+// apart, so that shared-memory reads of a warp are contiguous); the next
+// 16-deep slice of both operands is loaded into registers while the current
+// one is consumed from shared memory (two buffers, one barrier per slice).
+// Operand elements past n_x, n_T or 2J are read as zero.
+__global__ void __launch_bounds__(256) contract_df_kernel(int J, int n_x, int n_T, int px, int pt,
+                                                          const float2 *__restrict__ Vs,
+                                                          const float2 *__restrict__ Gs,
                                                           double *__restrict__ u) {
-    __shared__ float2 As[BK][BM];
-    __shared__ float2 Bs[BK][BN + 1];
+    __shared__ __align__(16) float2 As[2][BK][BM];
+    __shared__ __align__(16) float2 Bs[2][BK][BN];
     const int x0 = blockIdx.y * BM, t0 = blockIdx.x * BN;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
+    const int K2 = 2 * J;
     float sh[4][4], sl[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
-    const int K2 = 2 * J;
-    for (int k0 = 0; k0 < K2; k0 += BK) {
-        for (int e = tid; e < BK * BM; e += 256) {
-            const int kk = e / BM, xx = e % BM;
-            const int k = k0 + kk, x = x0 + xx;
-            double v = 0.0;
-            if (k < K2 && x < n_x) {
-                const double2 vv = V[(long long)(k < J ? k : k - J) * n_x + x];
-                v = (k < J) ? vv.x : vv.y;
+
+    // slice loader: element e = tid + 256 h (h = 0, 1) is row e / 32, float2
+    // pair e % 32 of the 16 x 64 slice
+    float4 ra[2], rb[2];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = tid + 256 * h, kk = k0 + (e >> 5), c = 2 * (e & 31);
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (kk < K2) {
+                const int x = x0 + c, t = t0 + c;
+                if (x < n_x) {
+                    a = __ldg(reinterpret_cast<const float4 *>(Vs + (long long)kk * px + x));
+                    if (x + 1 >= n_x) a.z = a.w = 0.f;
+                }
+                if (t < n_T) {
+                    b = __ldg(reinterpret_cast<const float4 *>(Gs + (long long)kk * pt + t));
+                    if (t + 1 >= n_T) b.z = b.w = 0.f;
+                }
             }
-            const float h = (float)v;
-            As[kk][xx] = make_float2(h, (float)(v - (double)h));
+            ra[h] = a;
+            rb[h] = b;
         }
-        for (int e = tid; e < BK * BN; e += 256) {
-            const int kk = e / BN, tt = e % BN;
-            const int k = k0 + kk, t = t0 + tt;
-            double v = 0.0;
-            if (k < K2 && t < n_T) v = (k < J) ? Gr[(long long)k * n_T + t] : Gm[(long long)(k - J) * n_T + t];
-            const float h = (float)v;
-            Bs[kk][tt] = make_float2(h, (float)(v - (double)h));
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = tid + 256 * h, kk = e >> 5, c = 2 * (e & 31);
+            *reinterpret_cast<float4 *>(&As[buf][kk][c]) = ra[h];
+            *reinterpret_cast<float4 *>(&Bs[buf][kk][c]) = rb[h];
         }
-        __syncthreads();
+    };
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < K2; k0 += BK) {
+        const bool more = k0 + BK < K2;
+        if (more) load(k0 + BK);
 #pragma unroll 4
         for (int kk = 0; kk < BK; ++kk) {
             float2 a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+            const float4 a01 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            const float4 a23 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4 + 2]);
+            const float4 b01 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 2]);
+            const float4 b23 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][32 + tx * 2]);
+            a[0] = make_float2(a01.x, a01.y);
+            a[1] = make_float2(a01.z, a01.w);
+            a[2] = make_float2(a23.x, a23.y);
+            a[3] = make_float2(a23.z, a23.w);
+            b[0] = make_float2(b01.x, b01.y);
+            b[1] = make_float2(b01.z, b01.w);
+            b[2] = make_float2(b23.x, b23.y);
+            b[3] = make_float2(b23.z, b23.w);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -439,7 +497,9 @@ __global__ void __launch_bounds__(256) contract_df_kernel(int J, int n_x, int n_
                     sh[i][j] = t;
                 }
         }
+        if (more) store(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -447,7 +507,7 @@ __global__ void __launch_bounds__(256) contract_df_kernel(int J, int n_x, int n_
         if (x >= n_x) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int t = t0 + tx * 4 + j;
+            const int t = t0 + (j < 2 ? tx * 2 + j : 32 + tx * 2 + (j - 2));
             if (t < n_T) u[(long long)x * n_T + t] = (double)sh[i][j] + (double)sl[i][j];
         }
     }
@@ -463,7 +523,7 @@ void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, doubl
 
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
                           float4 *Bf, const float4 *nu_f, const double2 *phase_tab, const double *T,
-                          int n_T, double *Gr, double *Gm, cudaStream_t st) {
+                          int n_T, double *Gr, double *Gm, float2 *Gs, cudaStream_t st) {
     if (n_T <= 0) return;
     const size_t smem = (size_t)K * (2 * sizeof(double) + 2 * sizeof(float2)) +
                         (size_t)((K + 1) & ~1) * sizeof(int) + (size_t)M * 3 * sizeof(float2);
@@ -477,17 +537,24 @@ void launch_synth_weights(int J, int M, double W, int K, const double *s, const 
         split_df_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, Bf, n);
     }
     dim3 grid(n_T, (J + 255) / 256);
-    weights_kernel<<<grid, 256, smem, st>>>(J, M, W, K, s, B, Bf, nu_f, phase_tab, T, n_T, Gr, Gm);
+    weights_kernel<<<grid, 256, smem, st>>>(J, M, W, K, s, B, Bf, nu_f, phase_tab, T, n_T, Gr, Gm, Gs,
+                                            synth_pitch(n_T));
 }
 
 void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,
-                           const double *Gm, double *u, bool double_float, cudaStream_t st) {
+                           const double *Gm, double *u, cudaStream_t st) {
     if (n_x <= 0 || n_T <= 0) return;
     dim3 grid((n_T + BN - 1) / BN, (n_x + BM - 1) / BM);
-    if (double_float)
-        contract_df_kernel<<<grid, 256, 0, st>>>(J, n_x, n_T, V, Gr, Gm, u);
-    else
-        contract_kernel<<<grid, 256, 0, st>>>(J, n_x, n_T, V, Gr, Gm, u);
+    contract_kernel<<<grid, 256, 0, st>>>(J, n_x, n_T, V, Gr, Gm, u);
+}
+
+void launch_synth_contract_df(int J, int n_x, int n_T, const double2 *V, float2 *Vs,
+                              const float2 *Gs, double *u, cudaStream_t st) {
+    if (n_x <= 0 || n_T <= 0) return;
+    const int px = synth_pitch(n_x), pt = synth_pitch(n_T);
+    split_v_kernel<<<dim3((px + 255) / 256, J), 256, 0, st>>>(J, n_x, px, V, Vs);
+    dim3 grid((n_T + BN - 1) / BN, (n_x + BM - 1) / BM);
+    contract_df_kernel<<<grid, 256, 0, st>>>(J, n_x, n_T, px, pt, Vs, Gs, u);
 }
 
 }  // namespace fh

@@ -33,6 +33,7 @@ EXPORTED = [
     "fh_eval_bessel", "fh_synthesize_static", "fh_discretize_batch", "fh_num_problems",
     "fh_window_spectra_p", "fh_window_spectra_p_dev", "fh_sample_p", "fh_sample_p_dev",
     "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test", "fh_eval_bessel_df", "fh_set_graphs",
+    "fh_get_tuning", "fh_set_tuning", "fh_autotune",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "refine", "spectra", "field", "weights", "contract"]
@@ -52,6 +53,11 @@ class fh_solve_stats(C.Structure):
 class fh_timings(C.Structure):
     _fields_ = [("ms", C.c_double * len(PHASES)), ("launches", C.c_longlong * len(PHASES)),
                 ("events", C.c_longlong * len(PHASES))]
+
+
+class fh_tuning(C.Structure):
+    _fields_ = [("assemble_group", C.c_int), ("field_group", C.c_int), ("field_chunk", C.c_int),
+                ("lu_rows_per_cta", C.c_int)]
 
 
 class FHError(RuntimeError):
@@ -101,6 +107,9 @@ def load_library(path: str | None = None):
         "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_eval_bessel_df": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_set_graphs": (C.c_int, [vp, C.c_int]),
+        "fh_get_tuning": (C.c_int, [vp, C.POINTER(fh_tuning)]),
+        "fh_set_tuning": (C.c_int, [vp, C.POINTER(fh_tuning)]),
+        "fh_autotune": (C.c_int, [vp, _DP, C.c_int, C.c_int, C.POINTER(fh_tuning), _DP]),
         "fh_discretize_batch": (C.c_int, [vp, C.c_int, C.POINTER(fh_curve), _IP, _DP, _IP, _DP, _DP]),
         "fh_num_problems": (C.c_int, [vp, _IP]),
         "fh_window_spectra_p": (C.c_int, [vp, C.c_int, _DP, C.c_int, C.c_double, C.c_double, C.c_double]),
@@ -286,6 +295,40 @@ def fh_synthesize(ctx, V, T):
 def fh_set_graphs(ctx, enable: bool):
     """Run the solve and sample launch sequences as CUDA graphs (default on)."""
     _check(ctx, load_library().fh_set_graphs(ctx, int(bool(enable))))
+
+
+TUNING_FIELDS = [f for f, _ in fh_tuning._fields_]
+
+
+def fh_get_tuning(ctx) -> dict:
+    t = fh_tuning()
+    _check(ctx, load_library().fh_get_tuning(ctx, C.byref(t)))
+    return {f: getattr(t, f) for f in TUNING_FIELDS}
+
+
+def fh_set_tuning(ctx, **values):
+    """Set schedule parameters by name (the others keep their values)."""
+    cur = fh_get_tuning(ctx)
+    unknown = set(values) - set(TUNING_FIELDS)
+    if unknown:
+        raise ValueError(f"unknown tuning fields {sorted(unknown)}")
+    cur.update(values)
+    t = fh_tuning(*[int(cur[f]) for f in TUNING_FIELDS])
+    _check(ctx, load_library().fh_set_tuning(ctx, C.byref(t)))
+
+
+def fh_autotune(ctx, x=None, reps: int = 3):
+    """Time the schedule candidates on the current discretization (and the
+    targets x, n_x x 2) and apply the fastest; returns (tuning, best ms of
+    {assemble, factor, field})."""
+    xv = None if x is None else _f64(np.asarray(x, dtype=np.float64).reshape(-1, 2))
+    n_x = 0 if xv is None else xv.shape[0]
+    t = fh_tuning()
+    ms = (C.c_double * 3)()
+    _check(ctx, load_library().fh_autotune(ctx, None if xv is None else _dp(xv), n_x, int(reps),
+                                           C.byref(t), ms))
+    return ({f: getattr(t, f) for f in TUNING_FIELDS},
+            {"assemble": ms[0], "factor": ms[1], "field": ms[2]})
 
 
 def fh_set_timing(ctx, enable: bool):
