@@ -169,11 +169,11 @@ def phase_rooflines(wl, precision, ms, iters, peaks):
     bf16 = peaks.get("bf16_tflops")
     out = {}
 
-    def put(phase, kernel, bound, work, peak, peak_src):
+    def put(phase, kernel, bound, work, peak, peak_src, unit="TFLOP/s"):
         if ms.get(phase, 0) <= 0 or peak is None:
             return
-        ach = work / (ms[phase] * 1e-3) / 1e12
-        out[phase] = {"kernel": kernel, "bound": bound, "unit": "TFLOP/s", "work_per_step": work,
+        ach = work / (ms[phase] * 1e-3) / (1e9 if unit == "GB/s" else 1e12)
+        out[phase] = {"kernel": kernel, "bound": bound, "unit": unit, "work_per_step": work,
                       "achieved": ach, "peak": peak, "frac": ach / peak, "peak_source": peak_src}
 
     fp64_src = "FP64 unit count (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)"
@@ -190,8 +190,10 @@ def phase_rooflines(wl, precision, ms, iters, peaks):
             "measured bf16 dense GEMM (MEASURED_PEAKS.json)" +
             (" x nominal TF32/BF16 ratio 1.1/2.25" if precision == "tf32" else ""))
     if mixed:
-        put("refine", "refine_resid_kernel", "alu", 8.0 * float(np.sum(N * N)) * max(iters, 1),
-            FP64_PEAK, fp64_src + "; work 8 N^2 per sweep x the largest sweep count")
+        put("refine", "refine_resid_kernel", "hbm", 24.0 * float(np.sum(N * N)) * max(iters, 1),
+            peaks.get("hbm_gbs"), "measured copy bandwidth (MEASURED_PEAKS.json); bytes: the "
+            "double-float matrix (16 B/entry, residual) and the FP32 factors (8 B/entry, solves) "
+            "per sweep x the largest sweep count", unit="GB/s")
     put("field", "field_partial_df_kernel" if mixed else "field_partial_kernel", "alu",
         50.0 * wl.n_x * float(np.sum(N)), FP64_PEAK, fp64_src + "; work 50 FP64-equivalent flop per (target, node)")
     put("weights", "weights_kernel", "alu", window_work(wl), DF_PEAK,

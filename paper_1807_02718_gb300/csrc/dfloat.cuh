@@ -34,6 +34,12 @@ __device__ __forceinline__ dfv df_from(double v) {
 
 __device__ __forceinline__ double df_to(dfv a) { return (double)a.hi + (double)a.lo; }
 
+// A complex FP64 value as double-float pairs (re hi, re lo, im hi, im lo).
+__device__ __forceinline__ float4 df_pack(double re, double im) {
+    const dfv r = df_from(re), i = df_from(im);
+    return make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+
 __device__ __forceinline__ dfv df_quick(float s, float e) {   // |s| >= |e|
     const float h = s + e;
     return {h, e - (h - s)};

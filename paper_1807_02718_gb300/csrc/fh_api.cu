@@ -405,9 +405,10 @@ fh_status build_schedules(fh_ctx *ctx) {
 
 bool is_fin(double v) { return std::isfinite(v); }
 
-// Mixed precision: refinement stops when ||dx||_inf <= kRefineTol ||x||_inf.
+// Mixed precision: refinement stops when ||dx||_inf <= kRefineTol ||x||_inf
+// (or when the corrections stall at the residual's rounding level).
 constexpr int kRefineMaxIters = 12;
-constexpr double kRefineTol = 1e-14;
+constexpr double kRefineTol = 1e-12;
 
 fh_status get_problem(fh_ctx *ctx, int problem, Problem **out) {
     if (!ctx->geom) return fail(ctx, FH_ESTATE, "call fh_discretize first");
@@ -880,15 +881,17 @@ fh_status fh_num_problems(fh_ctx *ctx, int *P) {
     return FH_OK;
 }
 
-// All matrices A_s into d_A (column-major, FP64).
+// All matrices A_s into d_A (column-major; FP64 complex, or double-float
+// pairs on the mixed paths).
 fh_status assemble_kernels(fh_ctx *ctx) {
+    const bool mixed = ctx->precision != FH_FP64;
     fh::launch_assemble_groups(tables(ctx), groups(ctx), ctx->n_groups, ctx->group_tiles,
                                ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
                                ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(),
-                               ctx->d_wpf.as<float2>(), ctx->d_A.as<double2>(), 0,
-                               ctx->precision != FH_FP64, ctx->stream);
+                               ctx->d_wpf.as<float2>(), mixed ? nullptr : ctx->d_A.as<double2>(),
+                               mixed ? ctx->d_A.as<float4>() : nullptr, 0, ctx->stream);
     return check_launch(ctx, "assemble");
 }
 
@@ -897,7 +900,7 @@ fh_status assemble_kernels(fh_ctx *ctx) {
 fh_status tc_factor_kernels(fh_ctx *ctx) {
     FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
     fh::launch_convert_rowmajor(ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
-                                ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->stream);
+                                ctx->d_A.as<float4>(), ctx->d_A32.as<float2>(), ctx->stream);
     const cudaError_t e = fh::launch_lu_factor_tc(
         ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>(),
         ctx->order.data(), ctx->solve_N.data(), ctx->S, ctx->d_N.as<int>(),
@@ -937,7 +940,7 @@ fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
             if (tc) {
                 FH_TRY(tc_factor_kernels(ctx));
             } else {
-                fh::launch_convert_fp32(ctx->d_A.as<double2>(), ctx->d_A32.as<float2>(), ctx->mat_total,
+                fh::launch_convert_fp32(ctx->d_A.as<float4>(), ctx->d_A32.as<float2>(), ctx->mat_total,
                                         ctx->stream);
                 fh::launch_lu_factor_fp32(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
                                           ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(),
@@ -952,7 +955,7 @@ fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
                              ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
                              ctx->d_rchunk.as<int2>(), ctx->n_rchunk, ctx->d_dblk.as<int2>(),
                              ctx->n_dblk, ctx->d_blk_off.as<int>(), ctx->d_dinv.as<float2>(),
-                             ctx->d_A.as<double2>(),
+                             ctx->d_A.as<float4>(),
                              ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_g.as<double2>(),
                              ctx->d_psi.as<double2>(), ctx->d_y32.as<float2>(), ctx->d_rstate.p,
                              kRefineMaxIters, kRefineTol, ctx->d_iters.as<int>(),
@@ -1145,6 +1148,7 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     if (!is_fin(eta_j)) return fail(ctx, FH_EINVAL, "eta_j must be finite");
     const int s = pb->s_begin + j - 1, n = ctx->solve_N[s];
     // the subgroup containing s is assembled exactly as in fh_solve_frequencies
+    const bool mixed = ctx->precision != FH_FP64;   // entries as double-float pairs
     int gi = pb->g_begin;
     while (!(ctx->sg[gi].x <= s && s < ctx->sg[gi].x + ctx->sg[gi].y)) ++gi;
     const int2 sgv = ctx->sg[gi];
@@ -1170,7 +1174,8 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
                                ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(), ctx->d_wpf.as<float2>(),
-                               ctx->d_tmpA.as<double2>(), -base, ctx->precision != FH_FP64, ctx->stream);
+                               mixed ? nullptr : ctx->d_tmpA.as<double2>(),
+                               mixed ? ctx->d_tmpA.as<float4>() : nullptr, -base, ctx->stream);
     FH_TRY(check_launch(ctx, "assemble (single)"));
     fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                    ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
@@ -1188,7 +1193,12 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     if (A)
         for (int i = 0; i < n; ++i)
             for (int l = 0; l < n; ++l) {
-                const double2 v = colmajor[(size_t)l * n + i];
+                double2 v = colmajor[(size_t)l * n + i];
+                if (mixed) {   // (re hi, re lo, im hi, im lo) floats in the same 16 bytes
+                    float f[4];
+                    std::memcpy(f, &v, sizeof f);
+                    v = make_double2((double)f[0] + (double)f[1], (double)f[2] + (double)f[3]);
+                }
                 A[2 * ((size_t)i * n + l)] = v.x;
                 A[2 * ((size_t)i * n + l) + 1] = v.y;
             }

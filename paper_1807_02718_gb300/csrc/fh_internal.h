@@ -58,11 +58,13 @@ struct Subgroups {
 // ---- CFIE assembly (k_assemble.cu) ----
 // Matrices are column-major: A_s(i, l) = A[mat_off[s] + l * N_s + i].
 // Grouped assembly: every matrix of subgroup g at A + mat_off[s] + out_shift.
+// Exactly one of A (FP64 complex) and Af (mixed paths: double-float pairs re
+// hi, re lo, im hi, im lo, same 16 bytes per entry) is non-null.
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long n_tiles, const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
-                            double2 *A, long long out_shift, bool double_float, cudaStream_t st);
+                            double2 *A, float4 *Af, long long out_shift, cudaStream_t st);
 // Solve s uses the incidence direction pdir[prob[s]].
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
                 const int *prob, const double2 *pdir, double2 *g, cudaStream_t st);
@@ -74,8 +76,9 @@ void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const d
 void launch_lu_solve_fp64(const int *order, int S, const int *N, const long long *mat_off,
                           const int *vec_off, double2 *A, double2 *b, int *info, cudaStream_t st);
 
-// Mixed precision: FP32 copy of A, FP32 LU, FP64 residual refinement.
-void launch_convert_fp32(const double2 *A, float2 *A32, long long n, cudaStream_t st);
+// Mixed precision: FP32 copy (the hi parts) of the double-float matrices,
+// FP32 LU, double-float residual refinement.
+void launch_convert_fp32(const float4 *Af, float2 *A32, long long n, cudaStream_t st);
 // piv (per system, length N) holds the inverse row permutation on return.
 void launch_lu_factor_fp32(const int *order, int S, const int *N, const long long *mat_off,
                            float2 *A32, int *piv, const int *vec_off, int *info, int maxN,
@@ -90,13 +93,14 @@ void launch_lu_factor_fp32(const int *order, int S, const int *N, const long lon
 constexpr int kTcMaxN = 4096;
 int lu_tc_cluster(int n, int rows_per_cta);
 int lu_tc_launches(const int *order_h, const int *N_h, int S, int rows_per_cta);
-void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const double2 *A,
+void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const float4 *Af,
                              float2 *A32, cudaStream_t st);
 cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, const int *order_h,
                                 const int *N_h, int S,
                                 const int *N, const long long *mat_off, float2 *A32, int *piv,
                                 const int *vec_off, int *info, int *err, cudaStream_t st);
-// FP64 iterative refinement against the column-major FP64 matrices; chunks
+// Iterative refinement against the column-major double-float matrices Af
+// (residuals with exact products and double-float sums); chunks
 // lists (solve, first row) per kResidRows rows; state holds
 // refine_state_bytes(S) bytes; y32 one FP32 complex per unknown.
 constexpr int kResidRows = 64;
@@ -107,7 +111,7 @@ size_t refine_state_bytes(int S);
 void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
                       const long long *mat_off, const int *vec_off, const int2 *chunks,
                       int n_chunks, const int2 *blocks, int n_blocks, const int *blk_off,
-                      float2 *inv, const double2 *A, const float2 *LU32, const int *piv,
+                      float2 *inv, const float4 *Af, const float2 *LU32, const int *piv,
                       const double2 *g, double2 *x, float2 *y32, void *state, int max_iters,
                       double tol, int *iters, double *resid, int *info, int maxN, cudaStream_t st);
 

@@ -163,13 +163,15 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
 // form), the phases and this combination run in double-float arithmetic; the
 // diagonal, the band, kappa r < 8 (the small-argument series, whose serial
 // recurrences run faster in FP64 at this kernel's occupancy), the Kress
-// weights and the log table stay FP64.
+// weights and the log table stay FP64.  Entries are stored as double-float
+// pairs (re hi, re lo, im hi, im lo): the FP32 LU takes the hi parts and the
+// refinement residual uses both.
 __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ z,
     const double2 *__restrict__ dz, const double2 *__restrict__ ddz,
     const double *__restrict__ kress, const double *__restrict__ logsin,
     const float4 *__restrict__ zf, const float4 *__restrict__ dzf, const float2 *__restrict__ sf,
-    const float2 *__restrict__ wpf, double2 *__restrict__ A, long long out_shift) {
+    const float2 *__restrict__ wpf, float4 *__restrict__ A, long long out_shift) {
     const long long b = blockIdx.x;
     const int g = find_solve(grp.tile_off, n_groups, b);
     const int2 sgv = grp.sg[g];
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
                 const double M2i = 0.25 * si;
                 const double ar = 0.5 + pin * (L2r + eta[j] * M2i);
                 const double ai = Rw * (-eta[j] * M1) + pin * (0.0 - eta[j] * M2r);
-                A[moff[j] + e_off] = make_double2(ar, ai);
+                A[moff[j] + e_off] = df_pack(ar, ai);
             }
             continue;
         }
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
                                           df_mul(pe4, J0));
                     const dfv ai = df_add(df_mul(pk4, J1),
                                           df_mul(e4, df_add(df_mul(pind, Y0), df_neg(df_mul(Wp, J0)))));
-                    A[moff[j] + e_off] = make_double2(df_to(ar), df_to(ai));
+                    A[moff[j] + e_off] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
                 } else {
                     const double kappa = kap[j];
                     double J0, Y0, J1, Y1;
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
                     const double et = eta[j];
                     const double ar = Rw * L1 + pin * (L2r + et * Mi);
                     const double ai = Rw * (-et * M1) + pin * (Li - et * M2r);
-                    A[moff[j] + e_off] = make_double2(ar, ai);
+                    A[moff[j] + e_off] = df_pack(ar, ai);
                 }
                 const dfv cn = df_add(df_mul(c, sc), df_neg(df_mul(sv, ss)));
                 sv = df_add(df_mul(sv, sc), df_mul(c, ss));
@@ -330,11 +332,11 @@ void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_grou
                             long long n_tiles, const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
-                            double2 *A, long long out_shift, bool double_float, cudaStream_t st) {
+                            double2 *A, float4 *Af, long long out_shift, cudaStream_t st) {
     if (n_tiles <= 0 || n_groups <= 0) return;
-    if (double_float)
+    if (Af)
         assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
-                                                                    logsin, zf, dzf, sf, wpf, A,
+                                                                    logsin, zf, dzf, sf, wpf, Af,
                                                                     out_shift);
     else
         assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,

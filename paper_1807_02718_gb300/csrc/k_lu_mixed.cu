@@ -1,11 +1,14 @@
 // Step a3, mixed precision: FP32 LU with partial pivoting, then iterative
-// refinement with FP64 residuals r = g - A x against the FP64 matrix.
+// refinement with residuals r = g - A x against the double-float matrix
+// (exact products, double-float sums: ~2^-46 relative per term).
 //
 // The CFIE matrices are well conditioned (second-kind equation), so each
 // refinement sweep contracts the error by ~ cond * N * 2^-24; two or three
-// sweeps bring the FP32 solution to FP64 accuracy.  Refinement stops when the
-// correction is below tol * ||x||_inf (max-norms), or fails with FH_ENOCONV
-// after max_iters sweeps.
+// sweeps bring the FP32 solution to the accuracy of the residual.  Refinement
+// stops when the correction is below tol * ||x||_inf (max-norms), or when it
+// has stopped contracting (no better than half the previous one) below
+// kStallTol * ||x||_inf, the level set by the residual's own rounding; it
+// fails with FH_ENOCONV after max_iters sweeps.
 //
 // Kernels (largest systems first):
 //   lu_factor_fp32_kernel  blocked right-looking LU (panel width 32) of the
@@ -14,9 +17,10 @@
 //                          (d = (LU)^-1 y in FP32, x += d; one CTA per
 //                          system; 32-wide diagonal blocks solved by one warp,
 //                          off-diagonal updates by the CTA), then
-//                          refine_resid_kernel (y = P (g - A x) in FP64, 64
-//                          rows per CTA so the FP64 work of a sweep spreads
-//                          over all SMs).  A system that has converged skips
+//                          refine_resid_kernel (y = P (g - A x), double-float
+//                          products and sums, the difference from g in FP64;
+//                          64 rows per CTA so that a sweep spreads over all
+//                          SMs).  A system that has converged skips
 //                          the remaining sweeps.  The factors may be
 //                          column-major (SIMT LU) or row-major (tensor-core LU).
 #include "fh_internal.h"
@@ -404,9 +408,19 @@ __device__ double block_max(double v, double *red) {
 // Refinement state of one system.
 struct RefineState {
     double gmax, dmax, xmax;
+    double dprev;                 // correction of the sweep before (0 before sweep 2)
     unsigned long long rbits;     // max_i |r_i|_1 as the bits of a non-negative double
     int conv, pad;
 };
+
+// A correction that has stopped contracting is rounding noise of the residual;
+// it is accepted as converged below this fraction of ||x||.
+constexpr double kStallTol = 1e-10;
+
+__device__ __forceinline__ bool refine_done(const RefineState &r, double tol) {
+    if (!(r.dmax > tol * r.xmax) || r.rbits == 0ull) return true;
+    return r.dprev > 0.0 && r.dmax > 0.5 * r.dprev && r.dmax <= kStallTol * r.xmax;
+}
 
 // x = 0, y = P g (FP32), ||g||.
 __global__ void __launch_bounds__(256) refine_setup_kernel(
@@ -426,7 +440,7 @@ __global__ void __launch_bounds__(256) refine_setup_kernel(
     if (threadIdx.x == 0) {
         RefineState r;
         r.gmax = gmax;
-        r.dmax = r.xmax = 0.0;
+        r.dmax = r.xmax = r.dprev = 0.0;
         r.rbits = 0ull;
         r.conv = info[s] != 0;
         r.pad = 0;
@@ -448,7 +462,7 @@ __global__ void __launch_bounds__(kRowMajor ? 512 : 256) refine_solve_kernel(
     const int s = order[blockIdx.x];
     RefineState *rs = st + s;
     if (rs->conv) return;
-    if (it > 1 && (!(rs->dmax > tol * rs->xmax) || rs->rbits == 0ull)) {
+    if (it > 1 && refine_done(*rs, tol)) {
         if (threadIdx.x == 0) rs->conv = 1;
         return;
     }
@@ -470,6 +484,7 @@ __global__ void __launch_bounds__(kRowMajor ? 512 : 256) refine_solve_kernel(
     dmax = block_max(dmax, red);
     xmax = block_max(xmax, red);
     if (threadIdx.x == 0) {
+        rs->dprev = rs->dmax;
         rs->dmax = dmax;
         rs->xmax = xmax;
         rs->rbits = 0ull;
@@ -479,35 +494,53 @@ __global__ void __launch_bounds__(kRowMajor ? 512 : 256) refine_solve_kernel(
 
 
 
-// r = g - A x in FP64 for 64 rows of one system (A column-major); y = P r.
-// Four column phases per row, summed in a fixed order.
+// acc += a * b in double-float (exact product plus cross terms, two-sum)
+__device__ __forceinline__ void dfmac(float &sh, float &sl, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float pe = fmaf(ah, bh, -p);
+    pe = fmaf(ah, bl, pe);
+    pe = fmaf(al, bh, pe);
+    const float t = sh + p;
+    const float z = t - sh;
+    sl += ((sh - (t - z)) + (p - z)) + pe;
+    sh = t;
+}
+
+// r = g - A x for 64 rows of one system (A column-major, double-float pairs);
+// y = P r.  x is split into double-float pairs in shared memory; four column
+// phases per row accumulate in double-float and are summed, then subtracted
+// from g, in FP64 in a fixed order.
 __global__ void __launch_bounds__(256) refine_resid_kernel(
     const int2 *__restrict__ chunks, const int *__restrict__ Ns, const long long *__restrict__ mat_off,
-    const int *__restrict__ vec_off, const double2 *__restrict__ A, const int *__restrict__ piv,
+    const int *__restrict__ vec_off, const float4 *__restrict__ A, const int *__restrict__ piv,
     const double2 *__restrict__ G, const double2 *__restrict__ X, float2 *__restrict__ Y32,
     RefineState *__restrict__ st) {
-    extern __shared__ double2 xs[];
+    extern __shared__ float4 xs[];   // x_l as (re hi, re lo, im hi, im lo)
     __shared__ double2 part[4][kResidRows];
     __shared__ double red[32];
     const int2 ch = chunks[blockIdx.x];
     const int s = ch.x, r0 = ch.y;
     if (st[s].conv) return;
     const int n = Ns[s], vo = vec_off[s];
-    const double2 *a = A + mat_off[s];
-    for (int l = threadIdx.x; l < n; l += blockDim.x) xs[l] = X[vo + l];
+    const float4 *a = A + mat_off[s];
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        const double2 v = X[vo + l];
+        const float rh = (float)v.x, ih = (float)v.y;
+        xs[l] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+    }
     __syncthreads();
     const int ri = threadIdx.x & (kResidRows - 1), ph = threadIdx.x / kResidRows, i = r0 + ri;
-    double rr = 0.0, rim = 0.0;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     if (i < n)
         for (int l = ph; l < n; l += 4) {
-            const double2 al = a[(long long)l * n + i];
-            const double2 xl = xs[l];
-            rr = fma(al.x, xl.x, rr);
-            rr = fma(-al.y, xl.y, rr);
-            rim = fma(al.x, xl.y, rim);
-            rim = fma(al.y, xl.x, rim);
+            const float4 al = __ldcs(a + (long long)l * n + i);
+            const float4 xl = xs[l];
+            dfmac(rh, rl, al.x, al.y, xl.x, xl.y);      // re += ar xr - ai xi
+            dfmac(rh, rl, -al.z, -al.w, xl.z, xl.w);
+            dfmac(ih, il, al.x, al.y, xl.z, xl.w);      // im += ar xi + ai xr
+            dfmac(ih, il, al.z, al.w, xl.x, xl.y);
         }
-    part[ph][ri] = make_double2(rr, rim);
+    part[ph][ri] = make_double2((double)rh + (double)rl, (double)ih + (double)il);
     __syncthreads();
     double m = 0.0;
     if (ph == 0 && i < n) {
@@ -530,21 +563,22 @@ __global__ void refine_final_kernel(int S, const RefineState *__restrict__ st, d
     if (s >= S || info[s] != 0) return;
     const RefineState r = st[s];
     const double rmax = __longlong_as_double((long long)r.rbits);
-    if (!r.conv && r.dmax > tol * r.xmax && r.rbits != 0ull) info[s] = -1;
+    if (!r.conv && !refine_done(r, tol)) info[s] = -1;
     resid[s] = r.gmax > 0.0 ? rmax / r.gmax : 0.0;
 }
 
-__global__ void convert_kernel(const double2 *__restrict__ A, float2 *__restrict__ B, long long n) {
+// FP32 copy: the hi parts of the double-float entries.
+__global__ void convert_kernel(const float4 *__restrict__ A, float2 *__restrict__ B, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double2 v = A[i];
-        B[i] = make_float2((float)v.x, (float)v.y);
+        const float4 v = A[i];
+        B[i] = make_float2(v.x, v.z);
     }
 }
 
 }  // namespace
 
-void launch_convert_fp32(const double2 *A, float2 *A32, long long n, cudaStream_t st) {
+void launch_convert_fp32(const float4 *A, float2 *A32, long long n, cudaStream_t st) {
     if (n <= 0) return;
     convert_kernel<<<152 * 8, 256, 0, st>>>(A, A32, n);
 }
@@ -567,7 +601,7 @@ size_t refine_state_bytes(int S) { return (size_t)S * sizeof(RefineState); }
 void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
                       const long long *mat_off, const int *vec_off, const int2 *chunks,
                       int n_chunks, const int2 *blocks, int n_blocks, const int *blk_off,
-                      float2 *inv, const double2 *A, const float2 *LU32, const int *piv,
+                      float2 *inv, const float4 *A, const float2 *LU32, const int *piv,
                       const double2 *g, double2 *x, float2 *y32, void *state, int max_iters,
                       double tol, int *iters, double *resid, int *info, int maxN, cudaStream_t st) {
     if (S <= 0) return;
@@ -589,7 +623,7 @@ void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
         else
             refine_solve_kernel<false><<<S, 256, (size_t)maxN * sizeof(float2), st>>>(
                 order, N, mat_off, vec_off, LU32, inv, blk_off, x, y32, rs, it, tol, iters);
-        refine_resid_kernel<<<n_chunks, 256, (size_t)maxN * sizeof(double2), st>>>(
+        refine_resid_kernel<<<n_chunks, 256, (size_t)maxN * sizeof(float4), st>>>(
             chunks, N, mat_off, vec_off, A, piv, g, x, y32, rs);
     }
     refine_final_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, rs, tol, resid, info);

@@ -564,14 +564,15 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     if (cs > 1) cg::this_cluster().sync();   // no CTA leaves while its shared memory may be addressed
 }
 
-// Row-major FP32 copy of the column-major FP64 matrices (32 x 32 tiles).
+// Row-major FP32 copy (the hi parts) of the column-major double-float
+// matrices (32 x 32 tiles).
 __global__ void __launch_bounds__(256) convert_rowmajor_kernel(const int *__restrict__ Ns,
                                                                const long long *__restrict__ mat_off,
-                                                               const double2 *__restrict__ A,
+                                                               const float4 *__restrict__ A,
                                                                float2 *__restrict__ A32) {
     __shared__ float2 t[32][33];
     const int s = blockIdx.x, n = Ns[s];
-    const double2 *src = A + mat_off[s];
+    const float4 *src = A + mat_off[s];
     float2 *dst = A32 + mat_off[s];
     const int nt = (n + 31) / 32;
     for (int tile = blockIdx.y; tile < nt * nt; tile += gridDim.y) {
@@ -579,8 +580,8 @@ __global__ void __launch_bounds__(256) convert_rowmajor_kernel(const int *__rest
         for (int k = threadIdx.y; k < 32; k += 8) {
             const int l = tj * 32 + k, i = ti * 32 + threadIdx.x;
             if (l < n && i < n) {
-                const double2 v = src[(long long)l * n + i];
-                t[k][threadIdx.x] = make_float2((float)v.x, (float)v.y);
+                const float4 v = src[(long long)l * n + i];   // (re hi, re lo, im hi, im lo)
+                t[k][threadIdx.x] = make_float2(v.x, v.z);
             }
         }
         __syncthreads();
@@ -635,7 +636,7 @@ int lu_tc_launches(const int *order_h, const int *N_h, int S, int rows_per_cta) 
     return count;
 }
 
-void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const double2 *A,
+void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const float4 *A,
                              float2 *A32, cudaStream_t st) {
     if (S <= 0) return;
     convert_rowmajor_kernel<<<dim3(S, 16), dim3(32, 8), 0, st>>>(N, mat_off, A, A32);

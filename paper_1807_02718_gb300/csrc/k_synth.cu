@@ -19,7 +19,10 @@
 // expansion 1/(y - m) = (1/y) sum_r (m/y)^r:
 //   D_p = (2W/M) sin(pi y)/(pi y) sum_r (h/y)^r nu_{p,r},
 //   nu_{p,r} = sum_m (-1)^m (m/h)^r e^{-2 pi i m p / M},
-// truncated once (h/|y|)^r < 2^-48 and summed in double-float arithmetic;
+// truncated once (h/|y|)^r < 2^-48 and summed by Horner's rule in
+// double-float arithmetic, except the terms past R1 with (h/|y|)^R1 <=
+// 2^-25 / R, which Horner's rule takes in FP32 first (their relative error
+// ~R 2^-24 enters scaled by (h/|y|)^R1, the size of the truncation error);
 // near windows sum the M terms directly (double-float accumulation).
 #include "fh_internal.h"
 
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(256) weights_kernel(
     double *wf = wy + K;                                     // K: sin(pi y) (near) or scale sinc(y) (far)
     float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: h / y (far) or 2W/M (near), double-float
     float2 *wfd = wrho + K;                                  // K: scale sinc(y) (far), double-float
-    int *wR = reinterpret_cast<int *>(wfd + K);              // K: far terms, 0 = near
+    int *wR = reinterpret_cast<int *>(wfd + K);              // K: far terms R | R1 << 16, 0 = near
     float2 *phc = reinterpret_cast<float2 *>(wR + ((K + 1) & ~1));   // M: cos (hi, lo)
     float2 *phs = phc + M;                                   // M: sin (hi, lo)
     float2 *sc = phs + M;                                    // M: sinc (hi, lo)
@@ -196,8 +199,10 @@ __global__ void __launch_bounds__(256) weights_kernel(
             wrho[k] = make_float2(sd.hi, sd.lo);
         } else {
             const double rho = (double)h / y;
-            const int R = (int)ceil(-48.0 * 0.69314718055994531 / log(fabs(rho)));
-            wR[k] = max(1, min(R, kFarTerms));
+            const double lr = -log(fabs(rho));
+            const int R = max(1, min((int)ceil(48.0 * 0.69314718055994531 / lr), kFarTerms));
+            const int R1 = max(1, min((int)ceil((25.0 * 0.69314718055994531 + log((double)R)) / lr), R));
+            wR[k] = R | (R1 << 16);
             const dfl rr = df_split(rho);
             wrho[k] = make_float2(rr.hi, rr.lo);
             wf[k] = scale * sy / (kPi * y);
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(256) weights_kernel(
     // G accumulates in double-float: q += B_k(w_p) D_p(t - s_k)
     float qrh = 0.f, qrl = 0.f, qih = 0.f, qil = 0.f;
     for (int k = 0; k < K; ++k) {
-        const int R = wR[k];
+        const int R = wR[k] & 0xffff, R1 = wR[k] >> 16;
         dfl dr = {0.f, 0.f}, di = {0.f, 0.f};
         if (R == 0) {                 // near window (the same branch in the whole CTA)
             // D_p = (2W/M) [S(y) + (-1)^p S(y+h) + sum_{j=1}^{h-1} (cos_j (S(y-j) + S(y+j))
@@ -272,8 +277,14 @@ __global__ void __launch_bounds__(256) weights_kernel(
         } else if (p < J) {
             const float2 r2 = wrho[k];
             const dfl rho = {r2.x, r2.y};
-            float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
-            for (int r = R - 1; r >= 0; --r) {
+            float ah = 0.f, bh = 0.f;
+            for (int r = R - 1; r >= R1; --r) {     // FP32 tail
+                const float4 v = nu_f[(long long)r * J + p];
+                ah = fmaf(ah, rho.hi, v.x);
+                bh = fmaf(bh, rho.hi, v.z);
+            }
+            float al = 0.f, bl = 0.f;
+            for (int r = R1 - 1; r >= 0; --r) {
                 const float4 v = nu_f[(long long)r * J + p];
                 df_horner(ah, al, rho, v.x, v.y);
                 df_horner(bh, bl, rho, v.z, v.w);
