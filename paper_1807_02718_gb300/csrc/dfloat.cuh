@@ -179,4 +179,73 @@ __device__ __forceinline__ void df_hankel(const GShared &tb, float xf, dfv r8, d
     }
 }
 
+// ---- small arguments (x < 8) ----
+// With t = x^2/32 - 1 (the A&S 9.1.10-9.1.11 ascending series with the
+// logarithmic parts taken out, as in the FP64 routine):
+//   J0 = A0(t),  Y0 = (2/pi) ln(x/2) J0 + A1(t),
+//   J1 = x A2(t), Y1 = (2/pi) ln(x/2) J1 - 2/(pi x) + x A3(t),
+// A_k Chebyshev series in t (bessel_cheb.h).  Clenshaw's recurrence runs in
+// binary32 over the coefficients k >= kChebHead (all below 2^-24 of the
+// largest, |c_k| <= 2e-10) and in double-float over the rest.
+constexpr int kChebHead = 12;
+
+template <int N>
+__device__ __forceinline__ dfv df_clenshaw(const float *c, dfv t) {
+    const float t2f = 2.f * t.hi;
+    float f1 = 0.f, f2 = 0.f;
+#pragma unroll
+    for (int k = N - 1; k >= kChebHead; --k) {
+        const float f0 = fmaf(t2f, f1, c[2 * k] - f2);
+        f2 = f1;
+        f1 = f0;
+    }
+    dfv b1 = df_make(f1, 0.f), b2 = df_make(f2, 0.f);
+    const dfv t2 = df_make(2.f * t.hi, 2.f * t.lo);
+#pragma unroll
+    for (int k = kChebHead - 1; k >= 1; --k) {
+        const dfv b0 = df_add(df_mul(t2, b1), df_add(df_make(c[2 * k], c[2 * k + 1]), df_neg(b2)));
+        b2 = b1;
+        b1 = b0;
+    }
+    return df_add(df_mul(t, b1), df_add(df_make(c[0], c[1]), df_neg(b2)));
+}
+
+// ln a for a double-float a > 0 (normal): a = m 2^e with m in [1/sqrt2, sqrt2),
+// ln m = 2 s sum_k s^2k / (2k+1), s = (m - 1)/(m + 1), |s| <= 0.172; the
+// series to k = 10 (truncation < 1e-17), terms k >= 5 (< 3e-9) in binary32.
+__device__ __forceinline__ dfv df_log(dfv a) {
+    int e;
+    float m = frexpf(a.hi, &e);           // a.hi = m 2^e, m in [1/2, 1)
+    if (m < 0.70710678f) {
+        m *= 2.f;
+        --e;
+    }
+    const dfv mm = df_make(m, ldexpf(a.lo, -e));   // exact power-of-two scaling
+    const dfv s = df_mul(df_add_f(mm, -1.f), df_rcp(df_add_f(mm, 1.f)));
+    const dfv s2 = df_mul(s, s);
+    float pf = kAtanhDF[20];
+#pragma unroll
+    for (int k = 9; k >= 5; --k) pf = fmaf(pf, s2.hi, kAtanhDF[2 * k]);
+    dfv p = df_make(pf, 0.f);
+#pragma unroll
+    for (int k = 4; k >= 0; --k) p = df_add(df_mul(p, s2), df_make(kAtanhDF[2 * k], kAtanhDF[2 * k + 1]));
+    const dfv ln2 = df_make(kLogConstDF[0], kLogConstDF[1]);
+    return df_add(df_mul_f(ln2, (float)e), df_mul(df_make(2.f * s.hi, 2.f * s.lo), p));
+}
+
+// J0, Y0 (and J1, Y1 when want1) at 0 < x < 8 from x and lnh = ln(x/2).
+template <bool want1>
+__device__ __forceinline__ void df_bessel_small(dfv x, dfv lnh, dfv &J0, dfv &Y0, dfv &J1, dfv &Y1) {
+    const dfv x2 = df_mul(x, x);
+    const dfv t = df_add_f(df_make(x2.hi * 0.03125f, x2.lo * 0.03125f), -1.f);
+    const dfv L = df_mul(df_make(kLogConstDF[2], kLogConstDF[3]), lnh);   // (2/pi) ln(x/2)
+    J0 = df_clenshaw<kA0_N>(kA0DF, t);
+    Y0 = df_add(df_mul(L, J0), df_clenshaw<kA1_N>(kA1DF, t));
+    if (want1) {
+        J1 = df_mul(x, df_clenshaw<kA2_N>(kA2DF, t));
+        const dfv tpx = df_mul(df_make(kLogConstDF[2], kLogConstDF[3]), df_rcp(x));   // 2/(pi x)
+        Y1 = df_add(df_add(df_mul(L, J1), df_neg(tpx)), df_mul(x, df_clenshaw<kA3_N>(kA3DF, t)));
+    }
+}
+
 }  // namespace fh

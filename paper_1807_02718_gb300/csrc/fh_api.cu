@@ -885,7 +885,8 @@ fh_status fh_num_problems(fh_ctx *ctx, int *P) {
 // pairs on the mixed paths).
 fh_status assemble_kernels(fh_ctx *ctx) {
     const bool mixed = ctx->precision != FH_FP64;
-    fh::launch_assemble_groups(tables(ctx), groups(ctx), ctx->n_groups, ctx->group_tiles,
+    fh::launch_assemble_groups(tables(ctx), groups(ctx), ctx->n_groups, ctx->group_tiles, 0, ctx->S,
+                               ctx->maxN,
                                ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
@@ -915,7 +916,7 @@ fh_status tc_factor_kernels(fh_ctx *ctx) {
 fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     const fh::SolveTables t = tables(ctx);
     {
-        PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
+        PhaseScope ps(ctx, FH_PH_ASSEMBLE, mixed ? 3 : 2);   // (tiles, band,) right sides
         FH_TRY(assemble_kernels(ctx));
         fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                        ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
@@ -1170,7 +1171,7 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     g1.tile_off = ctx->d_tmp_ll.as<long long>();
     g1.dkappa = ctx->d_tmp_d.as<double>();
     const fh::SolveTables t = tables(ctx);
-    fh::launch_assemble_groups(t, g1, 1, nt * nt, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+    fh::launch_assemble_groups(t, g1, 1, nt * nt, sgv.x, sgv.y, n, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
                                ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(), ctx->d_wpf.as<float2>(),

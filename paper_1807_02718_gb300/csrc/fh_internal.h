@@ -60,8 +60,11 @@ struct Subgroups {
 // Grouped assembly: every matrix of subgroup g at A + mat_off[s] + out_shift.
 // Exactly one of A (FP64 complex) and Af (mixed paths: double-float pairs re
 // hi, re lo, im hi, im lo, same 16 bytes per entry) is non-null.
+// Mixed paths (Af): two launches, the subgroup tiles off the near-diagonal band
+// and the band of solves s_begin .. s_begin + s_count - 1 (largest N maxN).
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
-                            long long n_tiles, const double2 *z, const double2 *dz,
+                            long long n_tiles, int s_begin, int s_count, int maxN,
+                            const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
                             double2 *A, float4 *Af, long long out_shift, cudaStream_t st);

@@ -236,6 +236,13 @@ def main():
     out.append("// (-1)^k / (2k+1)! and (-1)^k / (2k)! as double-float pairs, k = 0..8 (sine and cosine series)")
     out.append(df_consts("kSinDF", [(-1) ** k / mp.factorial(2 * k + 1) for k in range(9)]))
     out.append(df_consts("kCosDF", [(-1) ** k / mp.factorial(2 * k) for k in range(9)]))
+    out.append("// A0..A3 (x < 8) as double-float pairs [hi, lo] for the double-float path")
+    for name, f in (("kA0DF", a0), ("kA1DF", a1), ("kA2DF", a2), ("kA3DF", a3)):
+        out.append(df_consts(name, cheb(f)))
+    out.append("// 1 / (2k + 1), k = 0..10 (ln m = 2 s sum_k s^2k / (2k + 1), s = (m - 1)/(m + 1)),")
+    out.append("// ln 2, 2 / pi and ln(1/2) as double-float pairs")
+    out.append(df_consts("kAtanhDF", [mp.mpf(1) / (2 * k + 1) for k in range(11)]))
+    out.append(df_consts("kLogConstDF", [mp.log(2), 2 / mp.pi, -mp.log(2)]))
     print("\n".join(out))
 
 

@@ -159,17 +159,15 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
 //   Re A = k4 (W/pi J1 - (pi/n) Y1) + (pi/n) e4 J0,
 //   Im A = (pi/n) k4 J1 + e4 ((pi/n) Y0 - W/pi J0),
 // the same combination of M, M1, M2, L, L1, L2 as the FP64 kernel.  For
-// kappa r >= 8 off the band |i - l| <= kNearBand, the Bessel values (Hankel
-// form), the phases and this combination run in double-float arithmetic; the
-// diagonal, the band, kappa r < 8 (the small-argument series, whose serial
-// recurrences run faster in FP64 at this kernel's occupancy), the Kress
-// weights and the log table stay FP64.  Entries are stored as double-float
-// pairs (re hi, re lo, im hi, im lo): the FP32 LU takes the hi parts and the
-// refinement residual uses both.
+// entries off the band |i - l| <= kNearBand, the Bessel values (Hankel form
+// for kappa r >= 8, the small-argument series with ln r formed once per node
+// pair below it), the phases and this combination run in double-float
+// arithmetic; the diagonal and the band (where ln r and the Kress log table
+// nearly cancel), the Kress weights and the log table stay FP64.  Entries are
+// stored as double-float pairs (re hi, re lo, im hi, im lo): the FP32 LU takes
+// the hi parts and the refinement residual uses both.
 __global__ void __launch_bounds__(256) assemble_group_df_kernel(
-    SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ z,
-    const double2 *__restrict__ dz, const double2 *__restrict__ ddz,
-    const double *__restrict__ kress, const double *__restrict__ logsin,
+    SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ dz,
     const float4 *__restrict__ zf, const float4 *__restrict__ dzf, const float2 *__restrict__ sf,
     const float2 *__restrict__ wpf, float4 *__restrict__ A, long long out_shift) {
     const long long b = blockIdx.x;
@@ -180,24 +178,26 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     const int nt = (N + kTile - 1) / kTile;
     const long long lt = b - grp.tile_off[g];
     const int tr = (int)(lt % nt), tc = (int)(lt / nt);
-    __shared__ double kap[kGroup], eta[kGroup];
+    __shared__ double kap[kGroup];
     __shared__ float kapf[kGroup], corrf[kGroup];
-    __shared__ dfv kapd[kGroup], etad[kGroup], ikap[kGroup], isqk[kGroup];
+    __shared__ dfv kapd[kGroup], etad[kGroup], ikap[kGroup], isqk[kGroup], lnk2[kGroup];
     __shared__ long long moff[kGroup];
     __shared__ GShared gt;
     g_stage(gt);
     const double dk = grp.dkappa[g];
+    const dfv dkd = df_from(dk);
+    const float dkf = (float)dk;
     if (threadIdx.x < kGroup) {
         const int j = threadIdx.x;
         const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
         const double e = (j < cnt) ? t.eta[s0 + j] : 0.0;
         kap[j] = k;
-        eta[j] = e;
         kapf[j] = (float)k;
         kapd[j] = df_from(k);
         etad[j] = df_from(e);
         ikap[j] = df_from(1.0 / k);
         isqk[j] = df_from(1.0 / sqrt(k));
+        lnk2[j] = df_from(log(0.5 * k));   // ln(kappa/2): ln(x/2) = ln(kappa/2) + ln r
         corrf[j] = (float)(k - ((j < cnt ? t.kappa[s0] : 1.0) + j * dk));
         moff[j] = ((j < cnt) ? t.mat_off[s0 + j] : 0) + out_shift;
     }
@@ -208,10 +208,9 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     const int to = t.tab_off[t.tab[s0]];
     const double pin = 2.0 * kPi / (double)N;   // pi / n
     const dfv pind = df_from(pin);
-    const double2 zi = z[vo + i], dzi = dz[vo + i];
+    const double2 dzi = dz[vo + i];
     const double si = sqrt(dzi.x * dzi.x + dzi.y * dzi.y);
     const dfv isi4 = df_from(0.25 / si);
-    const double inv4pi = 1.0 / (4.0 * kPi);
     const dfv two_over_pi = df_make(0.6366197466850281f, 2.5682552973194106e-08f);
     const float4 zi4 = zf[vo + i], dzi4 = dzf[vo + i];
     const dfv nzix = df_make(-zi4.x, -zi4.y), nziy = df_make(-zi4.z, -zi4.w);
@@ -223,20 +222,7 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
         int d = i - l;
         if (d < 0) d += N;
         const long long e_off = (long long)l * N + i;
-        if (l == i) {
-            const double Rw = kress[to + d];
-            const double2 dd = ddz[vo + i];
-            const double M1 = -si * inv4pi;
-            const double L2r = (dd.x * dzi.y - dd.y * dzi.x) * inv4pi / (si * si);
-            for (int j = 0; j < cnt; ++j) {
-                const double M2r = (-kEulerGamma / (2.0 * kPi) - log(kap[j] * si * 0.5) / (2.0 * kPi)) * si;
-                const double M2i = 0.25 * si;
-                const double ar = 0.5 + pin * (L2r + eta[j] * M2i);
-                const double ai = Rw * (-eta[j] * M1) + pin * (0.0 - eta[j] * M2r);
-                A[moff[j] + e_off] = df_pack(ar, ai);
-            }
-            continue;
-        }
+        if (d <= kNearBand || d >= N - kNearBand) continue;   // assemble_band_kernel
         // pair geometry in double-float from the double-float node tables
         const float4 zl4 = zf[vo + l];
         const dfv d1 = df_add(df_make(zl4.x, zl4.y), nzix), d2 = df_add(df_make(zl4.z, zl4.w), nziy);
@@ -251,58 +237,93 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
         const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));
         dfv c, sv, sc, ss;
         df_expi(kap[0] * r - 0.78539816339744830962, c, sv);
-        df_expi(dk * r, sc, ss);
-        // the band |i - l| <= kNearBand and kappa r < 8 take the FP64 branch, with
-        // its quantities formed in FP64 from the FP64 tables
-        const bool near = d <= kNearBand || d >= N - kNearBand;
-        double Rw = 0.0, ls = 0.0, sl64 = 0.0, gg = 0.0, r64 = 0.0;
-        if (near || kapf[0] * rd.hi < 8.0f) {
-            Rw = kress[to + d];
-            ls = logsin[to + d];
-            const double2 zl = z[vo + l], dzl = dz[vo + l];
-            const double e1 = zl.x - zi.x, e2 = zl.y - zi.y;
-            r64 = sqrt(e1 * e1 + e2 * e2);
-            sl64 = sqrt(dzl.x * dzl.x + dzl.y * dzl.y);
-            gg = (dzi.y * e1 - dzi.x * e2) * sl64 / (si * r64);
-        }
+        if (dkf * rd.hi < 0.78f) df_sincos_small(df_mul(dkd, rd), ss, sc);   // e^{i dkappa r}, no reduction
+        else df_expi(dk * r, sc, ss);
+        const dfv lnr = kapf[0] * rd.hi < 8.0f ? df_log(rd) : df_make(0.f, 0.f);   // shared by the group
 #pragma unroll 1   // not unrolled: half the registers, twice the occupancy
         for (int j = 0; j < kGroup; ++j) {
             if (j < cnt) {
                 const float xf = kapf[j] * rd.hi;
-                if (!near && xf >= 8.0f) {
-                    dfv J0, Y0, J1, Y1;
+                dfv J0, Y0, J1, Y1;
+                if (xf >= 8.0f) {
                     const float dl = corrf[j] * rd.hi;
                     const dfv cj = df_add_f(c, -dl * sv.hi), sj = df_add_f(sv, dl * c.hi);
                     const dfv r8 = df_mul_f(df_mul(ir, ikap[j]), 8.0f);
                     df_hankel<true>(gt, xf, r8, df_mul(amp0, isqk[j]), cj, sj, J0, Y0, J1, Y1);
-                    const dfv k4 = df_mul(kapd[j], gg4), e4 = df_mul(etad[j], sl4);
-                    const dfv pk4 = df_mul(pind, k4), pe4 = df_mul(pind, e4);
-                    const dfv ar = df_add(df_mul(k4, df_add(df_mul(Wp, J1), df_neg(df_mul(pind, Y1)))),
-                                          df_mul(pe4, J0));
-                    const dfv ai = df_add(df_mul(pk4, J1),
-                                          df_mul(e4, df_add(df_mul(pind, Y0), df_neg(df_mul(Wp, J0)))));
-                    A[moff[j] + e_off] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
                 } else {
-                    const double kappa = kap[j];
-                    double J0, Y0, J1, Y1;
-                    bessel_j0y0j1y1(kappa * r64, J0, Y0, J1, Y1);
-                    const double Mr = -0.25 * Y0 * sl64, Mi = 0.25 * J0 * sl64;
-                    const double M1 = -J0 * sl64 * inv4pi;
-                    const double M2r = Mr - M1 * ls;
-                    const double Lr = -0.25 * kappa * Y1 * gg, Li = 0.25 * kappa * J1 * gg;
-                    const double L1 = -kappa * inv4pi * J1 * gg;
-                    const double L2r = Lr - L1 * ls;
-                    const double et = eta[j];
-                    const double ar = Rw * L1 + pin * (L2r + et * Mi);
-                    const double ai = Rw * (-et * M1) + pin * (Li - et * M2r);
-                    A[moff[j] + e_off] = df_pack(ar, ai);
+                    df_bessel_small<true>(df_mul(kapd[j], rd), df_add(lnr, lnk2[j]), J0, Y0, J1, Y1);
                 }
+                const dfv k4 = df_mul(kapd[j], gg4), e4 = df_mul(etad[j], sl4);
+                const dfv pk4 = df_mul(pind, k4), pe4 = df_mul(pind, e4);
+                const dfv ar = df_add(df_mul(k4, df_add(df_mul(Wp, J1), df_neg(df_mul(pind, Y1)))),
+                                      df_mul(pe4, J0));
+                const dfv ai = df_add(df_mul(pk4, J1),
+                                      df_mul(e4, df_add(df_mul(pind, Y0), df_neg(df_mul(Wp, J0)))));
+                A[moff[j] + e_off] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
                 const dfv cn = df_add(df_mul(c, sc), df_neg(df_mul(sv, ss)));
                 sv = df_add(df_mul(sv, sc), df_mul(c, ss));
                 c = cn;
             }
         }
     }
+}
+
+// The diagonal and the band 0 < |i - l| <= kNearBand (cyclically) of the
+// matrices of solves s_begin .. s_begin + gridDim.y - 1 for the mixed paths, in
+// FP64 with the FP64 kernel's formulas: there r is of the order of the node
+// spacing and ln r nearly cancels against the Kress log table.  One thread
+// per entry, so that no warp of assemble_group_df_kernel runs FP64 Bessel
+// series for a few lanes.
+__global__ void __launch_bounds__(256) assemble_band_kernel(
+    SolveTables t, int s_begin, const double2 *__restrict__ z, const double2 *__restrict__ dz,
+    const double2 *__restrict__ ddz, const double *__restrict__ kress,
+    const double *__restrict__ logsin, float4 *__restrict__ A, long long out_shift) {
+    constexpr int kW = 2 * kNearBand + 1;
+    const int s = s_begin + blockIdx.y;
+    const int N = t.N[s];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * kW) return;
+    const int i = e / kW, o = e % kW - kNearBand;
+    int l = i + o;
+    if (l < 0) l += N;
+    if (l >= N) l -= N;
+    int d = i - l;
+    if (d < 0) d += N;
+    const int vo = t.vec_off[s], to = t.tab_off[t.tab[s]];
+    const double kappa = t.kappa[s], et = t.eta[s];
+    const double pin = 2.0 * kPi / (double)N;   // pi / n
+    const double inv4pi = 1.0 / (4.0 * kPi);
+    const double2 zi = z[vo + i], dzi = dz[vo + i];
+    const double si = sqrt(dzi.x * dzi.x + dzi.y * dzi.y);
+    const double Rw = kress[to + d];
+    double ar, ai;
+    if (l == i) {
+        const double2 dd = ddz[vo + i];
+        const double M1 = -si * inv4pi;
+        const double L2r = (dd.x * dzi.y - dd.y * dzi.x) * inv4pi / (si * si);
+        const double M2r = (-kEulerGamma / (2.0 * kPi) - log(kappa * si * 0.5) / (2.0 * kPi)) * si;
+        const double M2i = 0.25 * si;
+        ar = 0.5 + pin * (L2r + et * M2i);
+        ai = Rw * (-et * M1) + pin * (0.0 - et * M2r);
+    } else {
+        const double ls = logsin[to + d];
+        const double2 zl = z[vo + l], dzl = dz[vo + l];
+        const double e1 = zl.x - zi.x, e2 = zl.y - zi.y;
+        const double r = sqrt(e1 * e1 + e2 * e2);
+        const double sl = sqrt(dzl.x * dzl.x + dzl.y * dzl.y);
+        const double gg = (dzi.y * e1 - dzi.x * e2) * sl / (si * r);
+        double J0, Y0, J1, Y1;
+        bessel_j0y0j1y1(kappa * r, J0, Y0, J1, Y1);
+        const double Mr = -0.25 * Y0 * sl, Mi = 0.25 * J0 * sl;
+        const double M1 = -J0 * sl * inv4pi;
+        const double M2r = Mr - M1 * ls;
+        const double Lr = -0.25 * kappa * Y1 * gg, Li = 0.25 * kappa * J1 * gg;
+        const double L1 = -kappa * inv4pi * J1 * gg;
+        const double L2r = Lr - L1 * ls;
+        ar = Rw * L1 + pin * (L2r + et * Mi);
+        ai = Rw * (-et * M1) + pin * (Li - et * M2r);
+    }
+    A[t.mat_off[s] + out_shift + (long long)l * N + i] = df_pack(ar, ai);
 }
 
 // g_i = dB/dn - i eta B = i (kappa p.nu_i - eta) e^{i kappa p.z_i}
@@ -329,16 +350,18 @@ __global__ void rhs_kernel(SolveTables t, const double2 *__restrict__ z,
 }  // namespace
 
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
-                            long long n_tiles, const double2 *z, const double2 *dz,
+                            long long n_tiles, int s_begin, int s_count, int maxN,
+                            const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
                             double2 *A, float4 *Af, long long out_shift, cudaStream_t st) {
     if (n_tiles <= 0 || n_groups <= 0) return;
-    if (Af)
-        assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
-                                                                    logsin, zf, dzf, sf, wpf, Af,
-                                                                    out_shift);
-    else
+    if (Af) {
+        assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, dz, zf, dzf, sf,
+                                                                    wpf, Af, out_shift);
+        const dim3 grid((maxN * (2 * kNearBand + 1) + 255) / 256, s_count);
+        assemble_band_kernel<<<grid, 256, 0, st>>>(t, s_begin, z, dz, ddz, kress, logsin, Af, out_shift);
+    } else
         assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
                                                                  logsin, A, out_shift);
 }

@@ -137,10 +137,10 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool 
 }
 
 // Mixed-precision variant of field_partial_kernel: the same sums with the
-// distances, the Hankel-form H0 (kappa r >= 8), the phases and the
+// distances, H0 (Hankel form for kappa r >= 8, the small-argument series with
+// ln r formed once per target-node pair below it), the phases and the
 // accumulation in double-float arithmetic.  FP64 is kept for the phase
-// arguments kappa_0 r and dkappa r with their reduction modulo pi/2 and for
-// the small-argument series (kappa r < 8).
+// arguments kappa_0 r and dkappa r with their reduction modulo pi/2.
 __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
     SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin, int chunk,
     const double2 *__restrict__ z, const double2 *__restrict__ dz,
@@ -155,9 +155,11 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
     const int vo0 = t.vec_off[s0];
     const double wq = 2.0 * kPi / (double)N * 0.25;   // (pi/n) / 4
     const double dk = grp.dkappa[g];
+    const dfv dkd = df_from(dk);
+    const float dkf = (float)dk;
     __shared__ double kap[kGroup];
     __shared__ float kapf[kGroup], corrf[kGroup];
-    __shared__ dfv ikap[kGroup], isqk[kGroup];
+    __shared__ dfv ikap[kGroup], isqk[kGroup], kapd[kGroup], lnk2[kGroup];
     __shared__ float4 zs[kChunk];             // node coordinates, double-float
     __shared__ float4 ps[kGroup][kChunk];   // (pi/n)|z'|/4 * psi_j as (re hi, re lo, im hi, im lo)
     __shared__ GShared gt;
@@ -169,6 +171,8 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
         kapf[j] = (float)k;
         ikap[j] = df_from(1.0 / k);
         isqk[j] = df_from(1.0 / sqrt(k));
+        kapd[j] = df_from(k);
+        lnk2[j] = df_from(log(0.5 * k));   // ln(kappa/2): ln(x/2) = ln(kappa/2) + ln r
         corrf[j] = (float)(k - ((j < cnt ? t.kappa[s0] : 1.0) + j * dk));
     }
     const int ne = min(chunk, N - i0);
@@ -204,12 +208,14 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
         const float4 z4 = zs[e];
         const dfv d1 = df_add(df_make(z4.x, z4.y), npx), d2 = df_add(df_make(z4.z, z4.w), npy);
         const dfv rd = df_sqrt(df_add(df_mul(d1, d1), df_mul(d2, d2)));
-        const double r = df_to(rd);   // FP64 for the phase arguments and the small-argument series
+        const double r = df_to(rd);   // FP64 for the phase arguments
         const dfv ir = df_rcp(rd);
         const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));   // sqrt(2 / (pi r))
         dfv c, sv, sc, ss;
         df_expi(kap[0] * r - 0.78539816339744830962, c, sv);   // e^{i (kappa_0 r - pi/4)}
-        df_expi(dk * r, sc, ss);
+        if (dkf * rd.hi < 0.78f) df_sincos_small(df_mul(dkd, rd), ss, sc);   // e^{i dkappa r}, no reduction
+        else df_expi(dk * r, sc, ss);
+        const dfv lnr = kapf[0] * rd.hi < 8.0f ? df_log(rd) : df_make(0.f, 0.f);   // shared by the group
 #pragma unroll
         for (int j = 0; j < kGroup; ++j) {
             if (j < cnt) {
@@ -222,10 +228,8 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
                     dfv J1, Y1;
                     df_hankel<false>(gt, xf, r8, df_mul(amp0, isqk[j]), cj, sj, J0, Y0, J1, Y1);
                 } else {
-                    double j0, y0;
-                    bessel_small0(kap[j] * r, j0, y0);
-                    J0 = df_from(j0);
-                    Y0 = df_from(y0);
+                    dfv J1, Y1;
+                    df_bessel_small<false>(df_mul(kapd[j], rd), df_add(lnr, lnk2[j]), J0, Y0, J1, Y1);
                 }
                 const float4 q4 = ps[j][e];
                 const dfv qr = df_make(q4.x, q4.y), qi = df_make(q4.z, q4.w);
@@ -297,8 +301,9 @@ __global__ void bessel_eval_kernel(const double *__restrict__ x, int n, double *
     out[6 * i + 5] = b;
 }
 
-// J0, Y0, J1, Y1 through the double-float Hankel form for x >= 8 (the FP64
-// series below 8), for testing the mixed-precision kernels.
+// J0, Y0, J1, Y1 through the double-float routines of the mixed-precision
+// kernels (Hankel form for x >= 8, small-argument series with a double-float
+// logarithm below), for testing them.
 __global__ void bessel_eval_df_kernel(const double *__restrict__ x, int n, double *__restrict__ out) {
     __shared__ GShared gt;
     g_stage(gt);
@@ -317,7 +322,14 @@ __global__ void bessel_eval_df_kernel(const double *__restrict__ x, int n, doubl
         J1 = df_to(j1);
         Y1 = df_to(y1);
     } else {
-        bessel_j0y0j1y1(xv, J0, Y0, J1, Y1);
+        const dfv xd = df_from(xv);
+        const dfv lnh = df_add(df_log(xd), df_make(kLogConstDF[4], kLogConstDF[5]));   // ln(x/2)
+        dfv j0, y0, j1, y1;
+        df_bessel_small<true>(xd, lnh, j0, y0, j1, y1);
+        J0 = df_to(j0);
+        Y0 = df_to(y0);
+        J1 = df_to(j1);
+        Y1 = df_to(y1);
     }
     out[4 * i + 0] = J0;
     out[4 * i + 1] = Y0;

@@ -58,9 +58,23 @@ def test_double_float_hankel_form():
     assert np.max(np.abs(out - ref)) < 2e-13
     w = out[:, 2] * out[:, 1] - out[:, 0] * out[:, 3]
     assert np.max(np.abs(w * np.pi * x / 2 - 1)) < 1e-11
-    # below 8 the FP64 series is used unchanged
-    xs = np.linspace(0.1, 7.9, 200)
-    assert np.array_equal(F.fh_eval_bessel_df(xs), F.fh_eval_bessel(xs)[:, :4])
+
+
+def test_double_float_small_argument_series():
+    """Below x = 8 the double-float path sums the same Chebyshev series as the
+    FP64 routine (double-float head, binary32 tail) with a double-float
+    logarithm: within ~1e-13 of the FP64 routine and scipy, relative to
+    max(1, |value|) (Y0, Y1 grow like ln x and 1/x near 0)."""
+    x = np.concatenate([np.geomspace(1e-3, 0.5, 400), np.linspace(0.5, 8.0, 4000, endpoint=False),
+                        np.linspace(7.99, 8.0, 50, endpoint=False), [1.0, 2.0, 4.0, 1 / np.sqrt(2)]])
+    out = F.fh_eval_bessel_df(x)
+    ref64 = F.fh_eval_bessel(x)[:, :4]
+    ref = np.stack([special.j0(x), special.y0(x), special.j1(x), special.y1(x)], 1)
+    scale = np.maximum(1.0, np.abs(ref))
+    assert np.max(np.abs(out - ref64) / scale) < 2e-13, np.max(np.abs(out - ref64) / scale, axis=0)
+    assert np.max(np.abs(out - ref) / scale) < 2e-13, np.max(np.abs(out - ref) / scale, axis=0)
+    w = out[:, 2] * out[:, 1] - out[:, 0] * out[:, 3]     # Wronskian 2 / (pi x)
+    assert np.max(np.abs(w * np.pi * x / 2 - 1)) < 1e-12
 
 
 def test_fp64_peak_probe_runs():
