@@ -122,6 +122,38 @@ __device__ __forceinline__ void df_expi(double x, dfv &c, dfv &s) {
     else { c = sn; s = df_neg(cs); }
 }
 
+// e^{i (x - pi/4)} for x = kappa r, kappa = k1 + k2 + k3 (three binary32
+// pieces, exact for an FP64 kappa), r double-float, 0 <= k1 r.hi < kExpiKrMax.
+// x - pi/4 - q pi/2 is formed without rounding x first (Cody-Waite with pi/2 =
+// C1 + C2 + C3): k1 r.hi - q C1 exactly (FMA residual; q C1 exact and the
+// difference exact by Sterbenz's lemma), the O(2^-24 x) terms k1 r.lo,
+// k2 r.hi, q C2 exactly as double-float pairs, the O(2^-48 x) terms in
+// binary32.  Then the Taylor series on |y| <= pi/4 and the quadrant q.
+constexpr float kExpiKrMax = 6000.f;   // q < 2^12, so that q C1 is exact
+
+__device__ __forceinline__ void df_expi_kr(float k1, float k2, float k3, dfv r, dfv &c, dfv &s) {
+    const float p1 = k1 * r.hi;
+    const float e1 = fmaf(k1, r.hi, -p1);
+    const float qf = rintf((p1 - kPio4DF[0]) * 0.636619772f);
+    const float y0 = fmaf(-qf, kPio2CW[0], p1);
+    const float a = k1 * r.lo, ae = fmaf(k1, r.lo, -a);
+    const float b = k2 * r.hi, be = fmaf(k2, r.hi, -b);
+    const float m = qf * kPio2CW[1], me = fmaf(qf, kPio2CW[1], -m);
+    dfv t = df_add(df_make(a, ae), df_make(b, be));
+    t = df_add(t, df_make(-m, -me));
+    t = df_add(t, df_make(-kPio4DF[0], -kPio4DF[1]));
+    t = df_add_f(t, e1);
+    const float tail = fmaf(k2, r.lo, fmaf(k3, r.hi, -qf * kPio2CW[2]));
+    const dfv y = df_add_f(df_add(df_make(y0, 0.f), t), tail);
+    dfv sn, cs;
+    df_sincos_small(y, sn, cs);
+    const int q = ((int)qf) & 3;
+    if (q == 0) { c = cs; s = sn; }
+    else if (q == 1) { c = df_neg(sn); s = cs; }
+    else if (q == 2) { c = df_neg(cs); s = df_neg(sn); }
+    else { c = sn; s = df_neg(cs); }
+}
+
 // Remainder polynomials staged in shared memory (threads of a warp may fall
 // into different x intervals).
 struct GShared {
@@ -246,6 +278,15 @@ __device__ __forceinline__ void df_bessel_small(dfv x, dfv lnh, dfv &J0, dfv &Y0
         const dfv tpx = df_mul(df_make(kLogConstDF[2], kLogConstDF[3]), df_rcp(x));   // 2/(pi x)
         Y1 = df_add(df_add(df_mul(L, J1), df_neg(tpx)), df_mul(x, df_clenshaw<kA3_N>(kA3DF, t)));
     }
+}
+
+// Out-of-line entry points for the rarely taken branches of the large kernels
+// (their code stays out of the instruction stream of the common path).
+static __device__ __noinline__ void df_expi_cold(double x, dfv &c, dfv &s) { df_expi(x, c, s); }
+
+static __device__ __noinline__ void df_bessel_small0_cold(dfv x, dfv lnh, dfv &J0, dfv &Y0) {
+    dfv J1, Y1;
+    df_bessel_small<false>(x, lnh, J0, Y0, J1, Y1);
 }
 
 }  // namespace fh

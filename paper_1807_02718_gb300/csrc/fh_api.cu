@@ -737,7 +737,8 @@ fh_status field_kernels(fh_ctx *ctx, Problem &pb, const double *d_x, int n_x) {
     PhaseScope ps(ctx, FH_PH_FIELD, pb.S() > 0 ? 3 : 1);
     fh::launch_target_field(tables(ctx), field_groups(ctx), pb.fg_begin, pb.fg_end - pb.fg_begin,
                             ctx->d_items.as<int2>(), pb.item_begin, pb.item_end - pb.item_begin,
-                            ctx->tune.field_chunk, ctx->d_item_first.as<int>(), ctx->d_solve_j.as<int>(),
+                            ctx->tune.field_chunk, ctx->tune.field_group, ctx->d_item_first.as<int>(),
+                            ctx->d_solve_j.as<int>(),
                             ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(), ctx->d_psi.as<double2>(),
                             d_x, n_x, ctx->d_zf.as<float4>(), ctx->d_part.as<double2>(),
                             ctx->d_V.as<double2>(), ctx->precision != FH_FP64, ctx->stream);

@@ -129,13 +129,14 @@ void launch_window_spectra(const double *a, int n_samples, long long start0, lon
 // item_first[g] is the first item of subgroup g (global, one entry past the
 // last subgroup).  One problem's subgroups g_begin .. g_begin + n_groups - 1
 // own the items item_begin .. item_begin + n_items - 1.  part: scratch of
-// n_items * kGroup * n_x complex values.
+// n_items * kGroup * n_x complex values.  group_max: the largest subgroup
+// size (<= kGroup; the double-float kernel is compiled for 4 and kGroup).
 constexpr int kFieldChunk = 64;
 void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
                          const int2 *items, int item_begin, int n_items, int chunk,
-                         const int *item_first, const int *solve_j, const double2 *z,
-                         const double2 *dz, const double2 *psi, const double *x, int n_x,
-                         const float4 *zf, double2 *part, double2 *V, bool double_float,
+                         int group_max, const int *item_first, const int *solve_j,
+                         const double2 *z, const double2 *dz, const double2 *psi, const double *x,
+                         int n_x, const float4 *zf, double2 *part, double2 *V, bool double_float,
                          cudaStream_t st);
 
 // Kernel Bessel routine on n arguments: out[6i..6i+5] = J0, Y0, J1, Y1 (joint

@@ -243,6 +243,16 @@ def main():
     out.append("// ln 2, 2 / pi and ln(1/2) as double-float pairs")
     out.append(df_consts("kAtanhDF", [mp.mpf(1) / (2 * k + 1) for k in range(11)]))
     out.append(df_consts("kLogConstDF", [mp.log(2), 2 / mp.pi, -mp.log(2)]))
+    # Cody-Waite split of pi/2: C1 with 12 significant bits (k C1 exact in
+    # binary32 for k < 2^12), C2 and C3 the next binary32 pieces
+    c1 = mp.floor(mp.pi / 2 * 2 ** 11 + mp.mpf(1) / 2) / 2 ** 11
+    import struct
+    f32 = lambda v: mp.mpf(struct.unpack("f", struct.pack("f", float(v)))[0])
+    c2 = f32(mp.pi / 2 - c1)
+    c3 = f32(mp.pi / 2 - c1 - c2)
+    out.append("// pi/2 = C1 + C2 + C3 (Cody-Waite, C1 with 12 significant bits) and pi/4 as a double-float pair")
+    out.append(emit_f("kPio2CW", [c1, c2, c3]))
+    out.append(df_consts("kPio4DF", [mp.pi / 4]))
     print("\n".join(out))
 
 

@@ -182,11 +182,19 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     __shared__ float kapf[kGroup], corrf[kGroup];
     __shared__ dfv kapd[kGroup], etad[kGroup], ikap[kGroup], isqk[kGroup], lnk2[kGroup];
     __shared__ long long moff[kGroup];
+    __shared__ float k3s[3];   // kappa_0 as three binary32 pieces
     __shared__ GShared gt;
     g_stage(gt);
     const double dk = grp.dkappa[g];
     const dfv dkd = df_from(dk);
     const float dkf = (float)dk;
+    if (threadIdx.x == 0) {
+        const double k0 = t.kappa[s0];
+        const float a = (float)k0, b = (float)(k0 - (double)a);
+        k3s[0] = a;
+        k3s[1] = b;
+        k3s[2] = (float)(k0 - (double)a - (double)b);
+    }
     if (threadIdx.x < kGroup) {
         const int j = threadIdx.x;
         const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
@@ -227,7 +235,6 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
         const float4 zl4 = zf[vo + l];
         const dfv d1 = df_add(df_make(zl4.x, zl4.y), nzix), d2 = df_add(df_make(zl4.z, zl4.w), nziy);
         const dfv rd = df_sqrt(df_add(df_mul(d1, d1), df_mul(d2, d2)));
-        const double r = df_to(rd);                 // FP64 only for the phase arguments
         const dfv ir = df_rcp(rd);
         const dfv Nil = df_add(df_mul(dziy, d1), df_neg(df_mul(dzix, d2)));
         const float2 sl2 = sf[vo + l], wp2 = wpf[to + d];
@@ -236,9 +243,10 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
         const dfv sl4 = df_mul_f(sl, 0.25f);
         const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));
         dfv c, sv, sc, ss;
-        df_expi(kap[0] * r - 0.78539816339744830962, c, sv);
+        if (kapf[0] * rd.hi < kExpiKrMax) df_expi_kr(k3s[0], k3s[1], k3s[2], rd, c, sv);
+        else df_expi_cold(kap[0] * df_to(rd) - 0.78539816339744830962, c, sv);   // e^{i (kappa_0 r - pi/4)}
         if (dkf * rd.hi < 0.78f) df_sincos_small(df_mul(dkd, rd), ss, sc);   // e^{i dkappa r}, no reduction
-        else df_expi(dk * r, sc, ss);
+        else df_expi_cold(dk * df_to(rd), sc, ss);
         const dfv lnr = kapf[0] * rd.hi < 8.0f ? df_log(rd) : df_make(0.f, 0.f);   // shared by the group
 #pragma unroll 1   // not unrolled: half the registers, twice the occupancy
         for (int j = 0; j < kGroup; ++j) {

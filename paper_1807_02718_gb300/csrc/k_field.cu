@@ -141,7 +141,8 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool 
 // ln r formed once per target-node pair below it), the phases and the
 // accumulation in double-float arithmetic.  FP64 is kept for the phase
 // arguments kappa_0 r and dkappa r with their reduction modulo pi/2.
-__global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
+template <int kG>   // largest subgroup size of the launch (<= kGroup)
+__global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
     SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin, int chunk,
     const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
@@ -160,10 +161,18 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
     __shared__ double kap[kGroup];
     __shared__ float kapf[kGroup], corrf[kGroup];
     __shared__ dfv ikap[kGroup], isqk[kGroup], kapd[kGroup], lnk2[kGroup];
+    __shared__ float k3s[3];   // kappa_0 as three binary32 pieces
     __shared__ float4 zs[kChunk];             // node coordinates, double-float
     __shared__ float4 ps[kGroup][kChunk];   // (pi/n)|z'|/4 * psi_j as (re hi, re lo, im hi, im lo)
     __shared__ GShared gt;
     g_stage(gt);
+    if (threadIdx.x == 0) {
+        const double k0 = t.kappa[s0];
+        const float a = (float)k0, b = (float)(k0 - (double)a);
+        k3s[0] = a;
+        k3s[1] = b;
+        k3s[2] = (float)(k0 - (double)a - (double)b);
+    }
     if (threadIdx.x < kGroup) {
         const int j = threadIdx.x;
         const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
             zz = zf[vo0 + i];
         }
         zs[e] = zz;
-        for (int j = 0; j < kGroup; ++j) {
+        for (int j = 0; j < kG; ++j) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (e < ne && j < cnt) {
                 const double2 q = psi[t.vec_off[s0 + j] + i];
@@ -201,23 +210,23 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
     if (it >= n_x) return;
     const dfv npx = df_neg(df_from(x[2 * it])), npy = df_neg(df_from(x[2 * it + 1]));
     const dfv two_over_pi = df_make(0.6366197466850281f, 2.5682552973194106e-08f);   // 2/pi
-    float ah[kGroup][2], al[kGroup][2];
+    float ah[kG][2], al[kG][2];
 #pragma unroll
-    for (int j = 0; j < kGroup; ++j) ah[j][0] = ah[j][1] = al[j][0] = al[j][1] = 0.f;
+    for (int j = 0; j < kG; ++j) ah[j][0] = ah[j][1] = al[j][0] = al[j][1] = 0.f;
     for (int e = 0; e < ne; ++e) {
         const float4 z4 = zs[e];
         const dfv d1 = df_add(df_make(z4.x, z4.y), npx), d2 = df_add(df_make(z4.z, z4.w), npy);
         const dfv rd = df_sqrt(df_add(df_mul(d1, d1), df_mul(d2, d2)));
-        const double r = df_to(rd);   // FP64 for the phase arguments
         const dfv ir = df_rcp(rd);
         const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));   // sqrt(2 / (pi r))
         dfv c, sv, sc, ss;
-        df_expi(kap[0] * r - 0.78539816339744830962, c, sv);   // e^{i (kappa_0 r - pi/4)}
+        if (kapf[0] * rd.hi < kExpiKrMax) df_expi_kr(k3s[0], k3s[1], k3s[2], rd, c, sv);
+        else df_expi_cold(kap[0] * df_to(rd) - 0.78539816339744830962, c, sv);   // e^{i (kappa_0 r - pi/4)}
         if (dkf * rd.hi < 0.78f) df_sincos_small(df_mul(dkd, rd), ss, sc);   // e^{i dkappa r}, no reduction
-        else df_expi(dk * r, sc, ss);
+        else df_expi_cold(dk * df_to(rd), sc, ss);
         const dfv lnr = kapf[0] * rd.hi < 8.0f ? df_log(rd) : df_make(0.f, 0.f);   // shared by the group
 #pragma unroll
-        for (int j = 0; j < kGroup; ++j) {
+        for (int j = 0; j < kG; ++j) {
             if (j < cnt) {
                 const float xf = kapf[j] * rd.hi;
                 dfv J0, Y0;
@@ -228,8 +237,7 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
                     dfv J1, Y1;
                     df_hankel<false>(gt, xf, r8, df_mul(amp0, isqk[j]), cj, sj, J0, Y0, J1, Y1);
                 } else {
-                    dfv J1, Y1;
-                    df_bessel_small<false>(df_mul(kapd[j], rd), df_add(lnr, lnk2[j]), J0, Y0, J1, Y1);
+                    df_bessel_small0_cold(df_mul(kapd[j], rd), df_add(lnr, lnk2[j]), J0, Y0);
                 }
                 const float4 q4 = ps[j][e];
                 const dfv qr = df_make(q4.x, q4.y), qi = df_make(q4.z, q4.w);
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
         }
         if ((e & 15) == 15)
 #pragma unroll
-            for (int j = 0; j < kGroup; ++j)
+            for (int j = 0; j < kG; ++j)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const dfv v = df_quick(ah[j][h], al[j][h]);
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(kTgt) field_partial_df_kernel(
                 }
     }
 #pragma unroll
-    for (int j = 0; j < kGroup; ++j)
+    for (int j = 0; j < kG; ++j)
         if (j < cnt)
             part[((long long)w * kGroup + j) * n_x + it] =
                 make_double2((double)ah[j][0] + (double)al[j][0], (double)ah[j][1] + (double)al[j][1]);
@@ -349,17 +357,20 @@ void launch_bessel_eval_df(const double *x, int n, double *out, cudaStream_t st)
 
 void launch_target_field(const SolveTables &t, const Subgroups &g, int g_begin, int n_groups,
                          const int2 *items, int item_begin, int n_items, int chunk,
-                         const int *item_first, const int *solve_j, const double2 *z,
-                         const double2 *dz, const double2 *psi, const double *x, int n_x,
-                         const float4 *zf, double2 *part, double2 *V, bool double_float,
+                         int group_max, const int *item_first, const int *solve_j,
+                         const double2 *z, const double2 *dz, const double2 *psi, const double *x,
+                         int n_x, const float4 *zf, double2 *part, double2 *V, bool double_float,
                          cudaStream_t st) {
     if (n_x <= 0) return;
     field_zero_freq_kernel<<<(n_x + 255) / 256, 256, 0, st>>>(n_x, V);
     if (n_groups <= 0 || n_items <= 0) return;
     dim3 grid((n_x + kTgt - 1) / kTgt, n_items);
-    if (double_float)
-        field_partial_df_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, chunk, z, dz, psi, x,
-                                                       n_x, zf, part);
+    if (double_float && group_max <= 4)
+        field_partial_df_kernel<4><<<grid, kTgt, 0, st>>>(t, g, items, item_begin, chunk, z, dz, psi, x,
+                                                          n_x, zf, part);
+    else if (double_float)
+        field_partial_df_kernel<kGroup><<<grid, kTgt, 0, st>>>(t, g, items, item_begin, chunk, z, dz, psi,
+                                                               x, n_x, zf, part);
     else
         field_partial_kernel<<<grid, kTgt, 0, st>>>(t, g, items, item_begin, chunk, z, dz, psi, x, n_x,
                                                     part);
