@@ -164,21 +164,46 @@ __device__ __forceinline__ void stage_a(const float2 *__restrict__ a, int n, int
     }
 }
 
-// B operand for complex columns j0 .. j0+63 of U12: row 2jj gives Re, row
-// 2jj+1 gives Im of output column j0+jj.
+// B operand for complex columns j0 .. j0+TCC-1 of U12: row 2jj gives Re, row
+// 2jj+1 gives Im of output column j0+jj.  load_b reads this thread's
+// kBElems elements (qpc complex values each) into registers, store_b splits
+// them into the K-major hi and lo tiles, so that the loads of the next tile
+// can be in flight during the current tile's epilogue.
 template <int kKind>
-__device__ __forceinline__ void stage_b(const float2 *__restrict__ a, int n, int k0, int nb, int j0,
-                                        uint8_t *sh, uint8_t *sl) {
-    constexpr int qpc = Op<kKind>::qpc, kChunks = NB / qpc, kRowB = 2 * NB * Op<kKind>::esize;
-    for (int e = threadIdx.x; e < 2 * TCC * kChunks; e += kThreads) {
+struct BRegs {
+    static constexpr int qpc = Op<kKind>::qpc, kChunks = NB / qpc;
+    static constexpr int kElems = 2 * TCC * kChunks / kThreads;
+    float2 u[kElems][qpc];
+};
+
+template <int kKind>
+__device__ __forceinline__ void load_b(const float2 *__restrict__ a, int n, int k0, int nb, int j0,
+                                       BRegs<kKind> &rb) {
+    constexpr int qpc = Op<kKind>::qpc;
+#pragma unroll
+    for (int m = 0; m < BRegs<kKind>::kElems; ++m) {
+        const int e = threadIdx.x + m * kThreads;
         const int b = e & (2 * TCC - 1), c = e / (2 * TCC);
         const int j = j0 + (b >> 1), q0 = c * qpc;
+#pragma unroll
+        for (int h = 0; h < qpc; ++h)
+            rb.u[m][h] = (j < n && q0 + h < nb) ? __ldcg(a + (long long)(k0 + q0 + h) * n + j)
+                                                : make_float2(0.f, 0.f);
+    }
+}
+
+template <int kKind>
+__device__ __forceinline__ void store_b(const BRegs<kKind> &rb, uint8_t *sh, uint8_t *sl) {
+    constexpr int qpc = Op<kKind>::qpc, kRowB = 2 * NB * Op<kKind>::esize;
+#pragma unroll
+    for (int m = 0; m < BRegs<kKind>::kElems; ++m) {
+        const int e = threadIdx.x + m * kThreads;
+        const int b = e & (2 * TCC - 1), c = e / (2 * TCC);
         const bool im = b & 1;
         float v[2 * qpc];
 #pragma unroll
         for (int h = 0; h < qpc; ++h) {
-            float2 u = make_float2(0.f, 0.f);
-            if (j < n && q0 + h < nb) u = __ldcg(a + (long long)(k0 + q0 + h) * n + j);
+            const float2 u = rb.u[m][h];
             v[2 * h] = im ? u.y : u.x;
             v[2 * h + 1] = im ? u.x : -u.y;
         }
@@ -500,16 +525,17 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             const int nrt = (m2 + TR - 1) / TR, nct = (m2 + TCC - 1) / TCC;
             for (int rt = rank; rt < nrt; rt += cs) {
                 const int i0 = r0 + rt * TR;
+                BRegs<kKind> rb;
+                load_b<kKind>(a, n, k0, nb, r0, rb);            // first column tile
                 stage_a<kKind>(a, n, k0, nb, i0, sAh, sAl);
                 int prev = -1, prev_j0 = 0;
+                float4 cprev[4], ccur[4];
                 for (int ct = 0; ct <= nct; ++ct) {
                     const int b = bsel;
                     const int j0 = r0 + ct * TCC;
-                    float4 cpre[4];
-                    if (prev >= 0) epi_load(a, n, i0, prev_j0, cpre);   // overlaps staging and the MMA
                     if (ct < nct) {
                         uint8_t *bh = sB + 2 * b * kBTile, *bl = bh + kBTile;
-                        stage_b<kKind>(a, n, k0, nb, j0, bh, bl);
+                        store_b<kKind>(rb, bh, bl);
                         tc::fence_async_smem();
                         tc::tc_fence_before();
                         __syncthreads();
@@ -520,6 +546,10 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                                              tc::smem_u32(bh), tc::smem_u32(bl), &ps.bar[b]);
                         pending[b] = issue;
                         bsel ^= 1;
+                        // in flight while this tile multiplies and the previous one is
+                        // written back: the next tile's B and this tile's C
+                        if (ct + 1 < nct) load_b<kKind>(a, n, k0, nb, j0 + TCC, rb);
+                        epi_load(a, n, i0, j0, ccur);
                     }
                     if (prev >= 0) {   // epilogue of the previous tile while this one multiplies
                         bool got = true;
@@ -530,9 +560,11 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         }
                         tc::tc_fence_after();
                         if (!__syncthreads_and(got)) failed = true;
-                        if (!failed) epi_store(a, n, i0, prev_j0, taddr + (uint32_t)(prev * 2 * TCC), sX, cpre);
+                        if (!failed) epi_store(a, n, i0, prev_j0, taddr + (uint32_t)(prev * 2 * TCC), sX, cprev);
                         tc::tc_fence_before();
                     }
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) cprev[p] = ccur[p];
                     prev = b;
                     prev_j0 = j0;
                 }
