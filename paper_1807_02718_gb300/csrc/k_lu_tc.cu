@@ -132,6 +132,7 @@ struct PanelShared {
     int mv_cnt;
     uint64_t bar[2];
     uint32_t tslot;
+    int wait_failed;                            // a completion wait of this CTA gave up
 };
 
 // Arg-max of packed keys over a warp; returns (hi, lo) of the best.
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     if (tid == 0) {
         tc::mbar_init(&ps.bar[0], 1);
         tc::mbar_init(&ps.bar[1], 1);
+        ps.wait_failed = 0;
     }
     if (rank == 0)   // pv: factored position -> original row, while factoring
         for (int i = tid; i < n; i += kThreads) pv[i] = i;
@@ -540,6 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         tc::tc_fence_before();
                         __syncthreads();
                         tc::tc_fence_after();
+                        if (ps.wait_failed) failed = true;   // the same verdict in every thread
                         const bool issue = !failed;
                         if (tid == 0 && issue)
                             issue_mma<kKind>(taddr + (uint32_t)(b * 2 * TCC), tc::smem_u32(sAh), tc::smem_u32(sAl),
@@ -552,6 +555,10 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         epi_load(a, n, i0, j0, ccur);
                     }
                     if (prev >= 0) {   // epilogue of the previous tile while this one multiplies
+                        // every thread waits for the completion itself (no barrier): its
+                        // accumulator reads and the reuse of the tile's B buffer two tiles
+                        // later follow its own wait; a give-up is shared through
+                        // ps.wait_failed at the next barrier
                         bool got = true;
                         if (pending[prev]) {
                             got = tc::mbar_wait(&ps.bar[prev], phase[prev], kWaitLimit);
@@ -559,7 +566,10 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                             pending[prev] = false;
                         }
                         tc::tc_fence_after();
-                        if (!__syncthreads_and(got)) failed = true;
+                        if (!got) {
+                            failed = true;
+                            ps.wait_failed = 1;
+                        }
                         if (!failed) epi_store(a, n, i0, prev_j0, taddr + (uint32_t)(prev * 2 * TCC), sX, cprev);
                         tc::tc_fence_before();
                     }
@@ -573,6 +583,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         sys_sync(cs, true);
     }
 
+    __syncthreads();
+    if (ps.wait_failed) failed = true;
     // after a failed wait, let any MMA still in flight finish before freeing
     for (int b = 0; b < 2; ++b)
         if (pending[b]) {
