@@ -290,12 +290,18 @@ fh_status fh_set_graphs(fh_ctx *ctx, int enable);
  *   lu_rows_per_cta  tensor-core LU: a system of order N is factored by the
  *                    smallest power of two of CTAs, at most 8, that is
  *                    >= N / lu_rows_per_cta (128, 256 or 512)
- * Defaults {8, 8, 64, 512}. */
+ *   lu_early         tensor-core LU: the largest systems, at least this
+ *                    percentage of them (0..50, whole assembly subgroups), are
+ *                    assembled and factored on a second stream while the
+ *                    others are assembled (0: one sequence).  Kernel timing
+ *                    (fh_set_timing) runs the single sequence.
+ * Defaults {8, 8, 64, 512, 0}. */
 typedef struct {
     int assemble_group;
     int field_group;
     int field_chunk;
     int lu_rows_per_cta;
+    int lu_early;
 } fh_tuning;
 
 fh_status fh_get_tuning(const fh_ctx *ctx, fh_tuning *out);
@@ -307,8 +313,9 @@ fh_status fh_set_tuning(fh_ctx *ctx, const fh_tuning *t);
 
 /* Autotuner (schedule selection by measurement): after fh_discretize[_batch],
  * times each candidate of the assembly (assemble_group 2, 4, 8), the
- * tensor-core factorisation (lu_rows_per_cta 512, 256, 128; mixed TF32/BF16
- * only) and the target fields at the n_x targets x (host, 2 n_x interleaved;
+ * tensor-core factorisation (lu_rows_per_cta 512, 256, 128, then lu_early 0,
+ * 10, 20, 35 over assembly plus factorisation; mixed TF32/BF16 only) and the
+ * target fields at the n_x targets x (host, 2 n_x interleaved;
  * field_group 2, 4, 8 x field_chunk 16, 32, 64; skipped when n_x == 0), each
  * as the fastest of `reps` (>= 1) runs on the context stream, one phase at a
  * time with the others at their current settings, and applies the fastest.
@@ -317,10 +324,11 @@ fh_status fh_set_tuning(fh_ctx *ctx, const fh_tuning *t);
  * schedule), and target fields are recomputed by the next fh_sample.  Before
  * the first solve the densities are zeroed for the field runs.  chosen (may
  * be NULL) receives the applied tuning; ms (may be NULL) receives the best
- * time of each tuned phase {assembly, factorisation, target fields} in ms
- * (0 for a phase not tuned).  Blocks until done. */
+ * time of each tuned stage {assembly, factorisation, target fields, assembly
+ * plus factorisation with lu_early} in ms (0 for a stage not tuned).  Blocks
+ * until done. */
 fh_status fh_autotune(fh_ctx *ctx, const double *x, int n_x, int reps, fh_tuning *chosen,
-                      double ms[3]);
+                      double ms[4]);
 
 /* enable != 0: bracket every kernel group with CUDA events on the context
  * stream (adds two event records per group).  Launch counts are always kept. */

@@ -35,9 +35,9 @@ void free_buf(DevBuf &b) {
 }
 
 // One problem of the batch.  Its solves are s_begin .. s_begin + J - 2
-// (frequency j = s - s_begin + 1), its assembly subgroups g_begin .. g_end-1,
-// its target-field subgroups fg_begin .. fg_end-1 and its field work items
-// item_begin .. item_end-1 (global indices).
+// (frequency j = s - s_begin + 1), its target-field subgroups fg_begin ..
+// fg_end-1 and its field work items item_begin .. item_end-1 (global
+// indices).  Assembly subgroups are ordered by decreasing N over all problems.
 struct Problem {
     fh_curve curve{};
     int J = 0, M = 0;
@@ -45,7 +45,6 @@ struct Problem {
     std::vector<double> omega;
     std::vector<int> Nj;
     int s_begin = 0;
-    int g_begin = 0, g_end = 0;
     int fg_begin = 0, fg_end = 0;
     int item_begin = 0, item_end = 0;
     long long nu_off = 0, ph_off = 0, omega_off = 0;   // into the pooled tables
@@ -91,7 +90,12 @@ struct fh_ctx {
     std::vector<long long> mat_off;
     std::vector<double> kappa_s, eta_s;
     // schedule parameters (fh_set_tuning, fh_autotune)
-    fh_tuning tune{fh::kGroup, fh::kGroup, fh::kFieldChunk, 512};
+    fh_tuning tune{fh::kGroup, fh::kGroup, fh::kFieldChunk, 512, 0};
+    // lu_early: the first early_groups assembly subgroups (early_solves solves,
+    // the largest) are assembled and factored on the side stream
+    int early_groups = 0, early_solves = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // frequency subgroups (one problem, equal N, at most tune.assemble_group
     // solves for the assembly, tune.field_group for the target fields)
     int n_groups = 0;
@@ -113,7 +117,7 @@ struct fh_ctx {
     DevBuf d_wa, d_a;
     int n_x_last = 0;
     DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm, d_Gs, d_Vs;
-    DevBuf d_tmpA, d_tmpg, d_tmp_ll, d_tmp_d;
+    DevBuf d_tmpA, d_tmpg, d_tmp_ll, d_tmp_d, d_tmp_i;
 
     // timing: pending (phase, start, stop) event triples and totals
     bool timing = false;
@@ -138,7 +142,7 @@ struct fh_ctx {
                          &d_pdir, &d_zf, &d_dzf, &d_sf, &d_wpf, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_A32, &d_piv, &d_g, &d_iters,
                          &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_Gs, &d_Vs,
-                         &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d};
+                         &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d, &d_tmp_i};
         for (DevBuf *b : all) free_buf(*b);
         free_problems();
         for (auto &pe : pending) {
@@ -148,6 +152,9 @@ struct fh_ctx {
         for (GraphSlot *g : {&solve_graph, &sample_graph})
             if (g->exec) cudaGraphExecDestroy(g->exec);
         if (cap) cudaStreamDestroy(cap);
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (own) cudaStreamDestroy(own);
     }
 };
@@ -329,7 +336,8 @@ bool tuning_valid(const fh_tuning &t) {
     return t.assemble_group >= 1 && t.assemble_group <= fh::kGroup && t.field_group >= 1 &&
            t.field_group <= fh::kGroup &&
            (t.field_chunk == 16 || t.field_chunk == 32 || t.field_chunk == 64) &&
-           (t.lu_rows_per_cta == 128 || t.lu_rows_per_cta == 256 || t.lu_rows_per_cta == 512);
+           (t.lu_rows_per_cta == 128 || t.lu_rows_per_cta == 256 || t.lu_rows_per_cta == 512) &&
+           t.lu_early >= 0 && t.lu_early <= 50;
 }
 
 // Splits each problem's solves into runs of equal N of at most gmax solves:
@@ -360,21 +368,43 @@ void split_groups(fh_ctx *ctx, int gmax, std::vector<int2> &sg, std::vector<doub
 // subgroups).  A new schedule is a new launch sequence: disc_gen advances.
 fh_status build_schedules(fh_ctx *ctx) {
     std::vector<int> first, end;
-    split_groups(ctx, ctx->tune.assemble_group, ctx->sg, ctx->sg_dk, first, end);
+    {
+        // assembly subgroups by decreasing N (stable); the factorisation order
+        // lists their solves in the same order, so that a prefix of subgroups
+        // is a prefix of the order (largest systems first)
+        std::vector<int2> sg;
+        std::vector<double> dk;
+        split_groups(ctx, ctx->tune.assemble_group, sg, dk, first, end);
+        std::vector<int> perm(sg.size());
+        for (size_t g = 0; g < sg.size(); ++g) perm[g] = (int)g;
+        std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+            return ctx->solve_N[sg[a].x] > ctx->solve_N[sg[b].x];
+        });
+        ctx->sg.resize(sg.size());
+        ctx->sg_dk.resize(sg.size());
+        for (size_t g = 0; g < sg.size(); ++g) {
+            ctx->sg[g] = sg[perm[g]];
+            ctx->sg_dk[g] = dk[perm[g]];
+        }
+    }
     ctx->sg_tile_off.clear();
+    ctx->order.clear();
     long long gt = 0;
     for (const int2 &g : ctx->sg) {
         ctx->sg_tile_off.push_back(gt);
         const long long nt = (ctx->solve_N[g.x] + 31) / 32;
         gt += nt * nt;
+        for (int j = 0; j < g.y; ++j) ctx->order.push_back(g.x + j);
     }
     ctx->sg_tile_off.push_back(gt);
-    for (size_t q = 0; q < ctx->probs.size(); ++q) {
-        ctx->probs[q].g_begin = first[q];
-        ctx->probs[q].g_end = end[q];
-    }
     ctx->n_groups = (int)ctx->sg.size();
     ctx->group_tiles = gt;
+    ctx->early_groups = ctx->early_solves = 0;
+    if (ctx->tune.lu_early > 0) {
+        const long long want = ((long long)ctx->S * ctx->tune.lu_early + 99) / 100;
+        while (ctx->early_groups < ctx->n_groups && ctx->early_solves < want)
+            ctx->early_solves += ctx->sg[ctx->early_groups++].y;
+    }
 
     split_groups(ctx, ctx->tune.field_group, ctx->fsg, ctx->fsg_dk, first, end);
     ctx->field_items.clear();
@@ -397,6 +427,7 @@ fh_status build_schedules(fh_ctx *ctx) {
     FH_TRY(upload(ctx, ctx->d_sg_dk, ctx->sg_dk));
     FH_TRY(upload(ctx, ctx->d_fsg, ctx->fsg));
     FH_TRY(upload(ctx, ctx->d_fsg_dk, ctx->fsg_dk));
+    FH_TRY(upload(ctx, ctx->d_order, ctx->order));
     FH_TRY(upload(ctx, ctx->d_items, ctx->field_items));
     FH_TRY(upload(ctx, ctx->d_item_first, ctx->item_first));
     ++ctx->disc_gen;
@@ -563,10 +594,6 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     ctx->n_tab = (int)ctx->tab_N.size();
     ctx->maxN = maxN;
 
-    ctx->order.resize(S);
-    for (int s = 0; s < S; ++s) ctx->order[s] = s;
-    std::stable_sort(ctx->order.begin(), ctx->order.end(),
-                     [&](int a, int b) { return ctx->solve_N[a] > ctx->solve_N[b]; });
 
     std::vector<int2> rchunk;   // (solve, first row) of each refinement residual chunk
     for (int s = 0; s < S; ++s)
@@ -594,7 +621,6 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
     FH_TRY(upload(ctx, ctx->d_solve_j, ctx->solve_j));
     FH_TRY(upload(ctx, ctx->d_solve_prob, ctx->solve_prob));
-    FH_TRY(upload(ctx, ctx->d_order, ctx->order));
     FH_TRY(upload(ctx, ctx->d_omega, omega_v));
     FH_TRY(build_schedules(ctx));
     FH_TRY(upload(ctx, ctx->d_curves, cps));
@@ -838,7 +864,10 @@ fh_status fh_create(fh_ctx **out, int device, int precision) {
     ctx->device = device;
     ctx->precision = precision;
     if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return FH_ECUDA;
     }
@@ -884,10 +913,12 @@ fh_status fh_num_problems(fh_ctx *ctx, int *P) {
 
 // All matrices A_s into d_A (column-major; FP64 complex, or double-float
 // pairs on the mixed paths).
-fh_status assemble_kernels(fh_ctx *ctx) {
+// Subgroups g0 .. g1-1 (their solves are order[s0 .. s1-1]).
+fh_status assemble_range(fh_ctx *ctx, int g0, int g1, int s0, int s1) {
     const bool mixed = ctx->precision != FH_FP64;
-    fh::launch_assemble_groups(tables(ctx), groups(ctx), ctx->n_groups, ctx->group_tiles, 0, ctx->S,
-                               ctx->maxN,
+    const long long t0 = ctx->sg_tile_off[g0], t1 = ctx->sg_tile_off[g1];
+    fh::launch_assemble_groups(tables(ctx), groups(ctx), ctx->n_groups, t0, t1 - t0,
+                               ctx->d_order.as<int>() + s0, s1 - s0, ctx->maxN,
                                ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
@@ -897,18 +928,70 @@ fh_status assemble_kernels(fh_ctx *ctx) {
     return check_launch(ctx, "assemble");
 }
 
-// Row-major FP32 copy of d_A and its tensor-core LU (d_info is cleared by
-// the caller).
-fh_status tc_factor_kernels(fh_ctx *ctx) {
-    FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
-    fh::launch_convert_rowmajor(ctx->S, ctx->d_N.as<int>(), ctx->d_mat_off.as<long long>(),
-                                ctx->d_A.as<float4>(), ctx->d_A32.as<float2>(), ctx->stream);
+fh_status assemble_kernels(fh_ctx *ctx) { return assemble_range(ctx, 0, ctx->n_groups, 0, ctx->S); }
+
+// Row-major FP32 copies and tensor-core LU of the solves order[s0 .. s1-1]
+// (d_info and d_tcerr are cleared by the caller).
+fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1) {
+    fh::launch_convert_rowmajor(ctx->d_order.as<int>() + s0, s1 - s0, ctx->d_N.as<int>(),
+                                ctx->d_mat_off.as<long long>(), ctx->d_A.as<float4>(),
+                                ctx->d_A32.as<float2>(), ctx->stream);
     const cudaError_t e = fh::launch_lu_factor_tc(
-        ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>(),
-        ctx->order.data(), ctx->solve_N.data(), ctx->S, ctx->d_N.as<int>(),
+        ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>() + s0,
+        ctx->order.data() + s0, ctx->solve_N.data(), s1 - s0, ctx->d_N.as<int>(),
         ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),
         ctx->d_vec_off.as<int>(), ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->stream);
     if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
+    return FH_OK;
+}
+
+fh_status tc_factor_kernels(fh_ctx *ctx) {
+    FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
+    return tc_factor_range(ctx, 0, ctx->S);
+}
+
+// Runs the enclosed launches on another stream of the context.
+struct OnStream {
+    fh_ctx *ctx;
+    cudaStream_t saved;
+    OnStream(fh_ctx *c, cudaStream_t st) : ctx(c), saved(c->stream) { ctx->stream = st; }
+    ~OnStream() { ctx->stream = saved; }
+};
+
+int tc_launches(fh_ctx *ctx, int s0, int s1) {
+    return 1 + fh::lu_tc_launches(ctx->order.data() + s0, ctx->solve_N.data(), s1 - s0,
+                                  ctx->tune.lu_rows_per_cta);
+}
+
+// Tensor-core path with lu_early: the largest systems (subgroups 0 ..
+// early_groups-1) are assembled and factored on the side stream while the
+// rest is assembled on the context stream; the streams join before the
+// refinement.  d_info and d_tcerr are cleared first.
+fh_status split_front(fh_ctx *ctx) {
+    const int gL = ctx->early_groups, SL = ctx->early_solves, S = ctx->S;
+    FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)S * sizeof(int), ctx->stream));
+    FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
+    FH_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    FH_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    {
+        OnStream on(ctx, ctx->side);
+        {
+            PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
+            FH_TRY(assemble_range(ctx, 0, gL, 0, SL));
+        }
+        PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, 0, SL));
+        FH_TRY(tc_factor_range(ctx, 0, SL));
+    }
+    FH_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+    {
+        PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
+        FH_TRY(assemble_range(ctx, gL, ctx->n_groups, SL, S));
+    }
+    {
+        PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, SL, S));
+        FH_TRY(tc_factor_range(ctx, SL, S));
+    }
+    FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     return FH_OK;
 }
 
@@ -916,15 +999,23 @@ fh_status tc_factor_kernels(fh_ctx *ctx) {
 // factorisation, refinement); all buffers exist already.
 fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     const fh::SolveTables t = tables(ctx);
-    {
+    const bool split = tc && !ctx->timing && ctx->early_solves > 0 && ctx->early_solves < ctx->S;
+    if (split) {
+        FH_TRY(split_front(ctx));
+        PhaseScope ps(ctx, FH_PH_ASSEMBLE, 1);
+        fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                       ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(), ctx->d_g.as<double2>(),
+                       ctx->stream);
+        FH_TRY(check_launch(ctx, "rhs"));
+    } else {
         PhaseScope ps(ctx, FH_PH_ASSEMBLE, mixed ? 3 : 2);   // (tiles, band,) right sides
         FH_TRY(assemble_kernels(ctx));
         fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                        ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
                        mixed ? ctx->d_g.as<double2>() : ctx->d_psi.as<double2>(), ctx->stream);
         FH_TRY(check_launch(ctx, "rhs"));
+        FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
     }
-    FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
     if (!mixed) {
         PhaseScope ps(ctx, FH_PH_FACTOR, 1);
         fh::launch_lu_solve_fp64(ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
@@ -935,11 +1026,10 @@ fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     } else {
         {
             // launches: conversion and one LU launch per cluster size (SIMT: one)
-            PhaseScope ps(ctx, FH_PH_FACTOR,
-                          1 + (tc ? fh::lu_tc_launches(ctx->order.data(), ctx->solve_N.data(), ctx->S,
-                                                       ctx->tune.lu_rows_per_cta)
-                                  : 1));
-            if (tc) {
+            PhaseScope ps(ctx, FH_PH_FACTOR, split ? 0 : tc ? tc_launches(ctx, 0, ctx->S) : 2);
+            if (split) {
+                // factored above
+            } else if (tc) {
                 FH_TRY(tc_factor_kernels(ctx));
             } else {
                 fh::launch_convert_fp32(ctx->d_A.as<float4>(), ctx->d_A32.as<float2>(), ctx->mat_total,
@@ -1151,7 +1241,7 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     const int s = pb->s_begin + j - 1, n = ctx->solve_N[s];
     // the subgroup containing s is assembled exactly as in fh_solve_frequencies
     const bool mixed = ctx->precision != FH_FP64;   // entries as double-float pairs
-    int gi = pb->g_begin;
+    int gi = 0;
     while (!(ctx->sg[gi].x <= s && s < ctx->sg[gi].x + ctx->sg[gi].y)) ++gi;
     const int2 sgv = ctx->sg[gi];
     const long long nt = (n + 31) / 32;
@@ -1164,6 +1254,9 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     FH_TRY(upload(ctx, ctx->d_tmp_sg, sg1));
     FH_TRY(upload(ctx, ctx->d_tmp_ll, to1));
     FH_TRY(upload(ctx, ctx->d_tmp_d, dk1));
+    std::vector<int> list1(sgv.y);
+    for (int q = 0; q < sgv.y; ++q) list1[q] = sgv.x + q;
+    FH_TRY(upload(ctx, ctx->d_tmp_i, list1));
     const long long base = ctx->mat_off[sgv.x];
     FH_TRY(ensure(ctx, ctx->d_tmpA, (size_t)sgv.y * n * n * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_tmpg, (size_t)ctx->vec_total * sizeof(double2)));
@@ -1172,7 +1265,8 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     g1.tile_off = ctx->d_tmp_ll.as<long long>();
     g1.dkappa = ctx->d_tmp_d.as<double>();
     const fh::SolveTables t = tables(ctx);
-    fh::launch_assemble_groups(t, g1, 1, nt * nt, sgv.x, sgv.y, n, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+    fh::launch_assemble_groups(t, g1, 1, 0, nt * nt, ctx->d_tmp_i.as<int>(), sgv.y, n,
+                               ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
                                ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(), ctx->d_wpf.as<float2>(),
@@ -1419,7 +1513,7 @@ fh_status tune_field(fh_ctx *ctx, int reps, int fh_tuning::*field, const std::ve
     return build_schedules(ctx);
 }
 
-fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_out[3]) {
+fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_out[4]) {
     const bool tc = ctx->precision == FH_MIXED_TF32 || ctx->precision == FH_MIXED_BF16;
     // 1. assembly: frequencies per subgroup
     FH_TRY(ensure(ctx, ctx->d_A, (size_t)ctx->mat_total * sizeof(double2)));
@@ -1436,6 +1530,23 @@ fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_ou
         FH_TRY(tune_field(ctx, reps, &fh_tuning::lu_rows_per_cta, {512, 256, 128}, ms_out[1], [&]() {
             FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
             FH_TRY(tc_factor_kernels(ctx));
+            FH_CUDA(ctx, cudaMemcpyAsync(info.data(), ctx->d_info.p, (size_t)ctx->S * sizeof(int),
+                                         cudaMemcpyDeviceToHost, ctx->stream));
+            FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            for (int s = 0; s < ctx->S; ++s)
+                if (info[s] == -2)
+                    return fail(ctx, FH_ETIMEOUT, "autotune: a tensor-core completion wait gave up");
+            return FH_OK;
+        }));
+        // 2b. assembly + factorisation with the largest systems started early
+        FH_TRY(tune_field(ctx, reps, &fh_tuning::lu_early, {0, 10, 20, 35}, ms_out[3], [&]() {
+            if (ctx->early_solves > 0 && ctx->early_solves < ctx->S) {
+                FH_TRY(split_front(ctx));
+            } else {
+                FH_TRY(assemble_kernels(ctx));
+                FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
+                FH_TRY(tc_factor_kernels(ctx));
+            }
             FH_CUDA(ctx, cudaMemcpyAsync(info.data(), ctx->d_info.p, (size_t)ctx->S * sizeof(int),
                                          cudaMemcpyDeviceToHost, ctx->stream));
             FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1489,7 +1600,7 @@ fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_ou
 extern "C" {
 
 fh_status fh_autotune(fh_ctx *ctx, const double *x, int n_x, int reps, fh_tuning *chosen,
-                      double ms[3]) {
+                      double ms[4]) {
     FH_TRY(enter(ctx));
     if (!ctx->geom) return fail(ctx, FH_ESTATE, "fh_autotune: call fh_discretize first");
     if (n_x < 0 || (n_x > 0 && !x)) return fail(ctx, FH_EINVAL, "x must hold 2 n_x values");
@@ -1499,7 +1610,7 @@ fh_status fh_autotune(fh_ctx *ctx, const double *x, int n_x, int reps, fh_tuning
     long long launches[FH_NUM_PHASES];
     std::memcpy(launches, ctx->launches, sizeof(launches));
     ctx->timing = false;
-    double best[3] = {0.0, 0.0, 0.0};
+    double best[4] = {0.0, 0.0, 0.0, 0.0};
     const fh_tuning before = ctx->tune;
     const fh_status st = autotune(ctx, x, n_x, reps, best);
     ctx->timing = timing;
@@ -1513,7 +1624,7 @@ fh_status fh_autotune(fh_ctx *ctx, const double *x, int n_x, int reps, fh_tuning
     }
     if (chosen) *chosen = ctx->tune;
     if (ms)
-        for (int i = 0; i < 3; ++i) ms[i] = best[i];
+        for (int i = 0; i < 4; ++i) ms[i] = best[i];
     return FH_OK;
 }
 

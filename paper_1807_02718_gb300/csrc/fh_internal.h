@@ -60,10 +60,13 @@ struct Subgroups {
 // Grouped assembly: every matrix of subgroup g at A + mat_off[s] + out_shift.
 // Exactly one of A (FP64 complex) and Af (mixed paths: double-float pairs re
 // hi, re lo, im hi, im lo, same 16 bytes per entry) is non-null.
-// Mixed paths (Af): two launches, the subgroup tiles off the near-diagonal band
-// and the band of solves s_begin .. s_begin + s_count - 1 (largest N maxN).
+// Launches the tiles tile_base .. tile_base + n_tiles - 1 of the subgroup
+// table g (n_groups subgroups, tile offsets over the whole table).  Mixed
+// paths (Af): also the near-diagonal band of the band_count solves in the
+// device list band_list (largest N maxN), a second launch.
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
-                            long long n_tiles, int s_begin, int s_count, int maxN,
+                            long long tile_base, long long n_tiles, const int *band_list,
+                            int band_count, int maxN,
                             const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
@@ -96,8 +99,9 @@ void launch_lu_factor_fp32(const int *order, int S, const int *N, const long lon
 constexpr int kTcMaxN = 4096;
 int lu_tc_cluster(int n, int rows_per_cta);
 int lu_tc_launches(const int *order_h, const int *N_h, int S, int rows_per_cta);
-void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const float4 *Af,
-                             float2 *A32, cudaStream_t st);
+// Row-major FP32 copies of the count solves in the device list list.
+void launch_convert_rowmajor(const int *list, int count, const int *N, const long long *mat_off,
+                             const float4 *Af, float2 *A32, cudaStream_t st);
 cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, const int *order_h,
                                 const int *N_h, int S,
                                 const int *N, const long long *mat_off, float2 *A32, int *piv,

@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
     SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ z,
     const double2 *__restrict__ dz, const double2 *__restrict__ ddz,
     const double *__restrict__ kress, const double *__restrict__ logsin,
-    double2 *__restrict__ A, long long out_shift) {
-    const long long b = blockIdx.x;
+    double2 *__restrict__ A, long long out_shift, long long tile_base) {
+    const long long b = tile_base + blockIdx.x;
     const int g = find_solve(grp.tile_off, n_groups, b);
     const int2 sgv = grp.sg[g];
     const int s0 = sgv.x, cnt = sgv.y;
@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
 __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ dz,
     const float4 *__restrict__ zf, const float4 *__restrict__ dzf, const float2 *__restrict__ sf,
-    const float2 *__restrict__ wpf, float4 *__restrict__ A, long long out_shift) {
-    const long long b = blockIdx.x;
+    const float2 *__restrict__ wpf, float4 *__restrict__ A, long long out_shift, long long tile_base) {
+    const long long b = tile_base + blockIdx.x;
     const int g = find_solve(grp.tile_off, n_groups, b);
     const int2 sgv = grp.sg[g];
     const int s0 = sgv.x, cnt = sgv.y;
@@ -277,17 +277,17 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
 }
 
 // The diagonal and the band 0 < |i - l| <= kNearBand (cyclically) of the
-// matrices of solves s_begin .. s_begin + gridDim.y - 1 for the mixed paths, in
+// matrices of solves list[0 .. gridDim.y - 1] for the mixed paths, in
 // FP64 with the FP64 kernel's formulas: there r is of the order of the node
 // spacing and ln r nearly cancels against the Kress log table.  One thread
 // per entry, so that no warp of assemble_group_df_kernel runs FP64 Bessel
 // series for a few lanes.
 __global__ void __launch_bounds__(256) assemble_band_kernel(
-    SolveTables t, int s_begin, const double2 *__restrict__ z, const double2 *__restrict__ dz,
+    SolveTables t, const int *__restrict__ list, const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ ddz, const double *__restrict__ kress,
     const double *__restrict__ logsin, float4 *__restrict__ A, long long out_shift) {
     constexpr int kW = 2 * kNearBand + 1;
-    const int s = s_begin + blockIdx.y;
+    const int s = list[blockIdx.y];
     const int N = t.N[s];
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N * kW) return;
@@ -358,7 +358,8 @@ __global__ void rhs_kernel(SolveTables t, const double2 *__restrict__ z,
 }  // namespace
 
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
-                            long long n_tiles, int s_begin, int s_count, int maxN,
+                            long long tile_base, long long n_tiles, const int *band_list,
+                            int band_count, int maxN,
                             const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
@@ -366,12 +367,14 @@ void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_grou
     if (n_tiles <= 0 || n_groups <= 0) return;
     if (Af) {
         assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, dz, zf, dzf, sf,
-                                                                    wpf, Af, out_shift);
-        const dim3 grid((maxN * (2 * kNearBand + 1) + 255) / 256, s_count);
-        assemble_band_kernel<<<grid, 256, 0, st>>>(t, s_begin, z, dz, ddz, kress, logsin, Af, out_shift);
+                                                                    wpf, Af, out_shift, tile_base);
+        if (band_count > 0) {
+            const dim3 grid((maxN * (2 * kNearBand + 1) + 255) / 256, band_count);
+            assemble_band_kernel<<<grid, 256, 0, st>>>(t, band_list, z, dz, ddz, kress, logsin, Af, out_shift);
+        }
     } else
         assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
-                                                                 logsin, A, out_shift);
+                                                                 logsin, A, out_shift, tile_base);
 }
 
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,

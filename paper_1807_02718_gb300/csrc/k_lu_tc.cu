@@ -610,12 +610,13 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
 
 // Row-major FP32 copy (the hi parts) of the column-major double-float
 // matrices (32 x 32 tiles).
-__global__ void __launch_bounds__(256) convert_rowmajor_kernel(const int *__restrict__ Ns,
+__global__ void __launch_bounds__(256) convert_rowmajor_kernel(const int *__restrict__ list,
+                                                               const int *__restrict__ Ns,
                                                                const long long *__restrict__ mat_off,
                                                                const float4 *__restrict__ A,
                                                                float2 *__restrict__ A32) {
     __shared__ float2 t[32][33];
-    const int s = blockIdx.x, n = Ns[s];
+    const int s = list[blockIdx.x], n = Ns[s];
     const float4 *src = A + mat_off[s];
     float2 *dst = A32 + mat_off[s];
     const int nt = (n + 31) / 32;
@@ -680,10 +681,10 @@ int lu_tc_launches(const int *order_h, const int *N_h, int S, int rows_per_cta) 
     return count;
 }
 
-void launch_convert_rowmajor(int S, const int *N, const long long *mat_off, const float4 *A,
-                             float2 *A32, cudaStream_t st) {
-    if (S <= 0) return;
-    convert_rowmajor_kernel<<<dim3(S, 16), dim3(32, 8), 0, st>>>(N, mat_off, A, A32);
+void launch_convert_rowmajor(const int *list, int count, const int *N, const long long *mat_off,
+                             const float4 *A, float2 *A32, cudaStream_t st) {
+    if (count <= 0) return;
+    convert_rowmajor_kernel<<<dim3(count, 16), dim3(32, 8), 0, st>>>(list, N, mat_off, A, A32);
 }
 
 cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, const int *order_h,

@@ -57,7 +57,7 @@ class fh_timings(C.Structure):
 
 class fh_tuning(C.Structure):
     _fields_ = [("assemble_group", C.c_int), ("field_group", C.c_int), ("field_chunk", C.c_int),
-                ("lu_rows_per_cta", C.c_int)]
+                ("lu_rows_per_cta", C.c_int), ("lu_early", C.c_int)]
 
 
 class FHError(RuntimeError):
@@ -320,15 +320,15 @@ def fh_set_tuning(ctx, **values):
 def fh_autotune(ctx, x=None, reps: int = 3):
     """Time the schedule candidates on the current discretization (and the
     targets x, n_x x 2) and apply the fastest; returns (tuning, best ms of
-    {assemble, factor, field})."""
+    {assemble, factor, field, assemble_factor})."""
     xv = None if x is None else _f64(np.asarray(x, dtype=np.float64).reshape(-1, 2))
     n_x = 0 if xv is None else xv.shape[0]
     t = fh_tuning()
-    ms = (C.c_double * 3)()
+    ms = (C.c_double * 4)()
     _check(ctx, load_library().fh_autotune(ctx, None if xv is None else _dp(xv), n_x, int(reps),
                                            C.byref(t), ms))
     return ({f: getattr(t, f) for f in TUNING_FIELDS},
-            {"assemble": ms[0], "factor": ms[1], "field": ms[2]})
+            {"assemble": ms[0], "factor": ms[1], "field": ms[2], "assemble_factor": ms[3]})
 
 
 def fh_set_timing(ctx, enable: bool):

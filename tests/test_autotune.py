@@ -93,9 +93,10 @@ def test_invalid_settings_are_rejected():
     pr = F.Problem(0, F.FH_MIXED_TF32)
     before = F.fh_get_tuning(pr.ctx)
     assert before == {"assemble_group": 8, "field_group": 8, "field_chunk": 64,
-                      "lu_rows_per_cta": 512}
+                      "lu_rows_per_cta": 512, "lu_early": 0}
     for bad in (dict(assemble_group=0), dict(assemble_group=9), dict(field_group=0),
-                dict(field_chunk=48), dict(field_chunk=128), dict(lu_rows_per_cta=1024)):
+                dict(field_chunk=48), dict(field_chunk=128), dict(lu_rows_per_cta=1024),
+                dict(lu_early=-1), dict(lu_early=51)):
         with pytest.raises(F.FHError) as e:
             F.fh_set_tuning(pr.ctx, **bad)
         assert e.value.status == F.FH_EINVAL
@@ -118,8 +119,10 @@ def test_autotune_choice_equals_the_same_setting_by_hand(prec, oracle_runs):
     assert ms["assemble"] > 0 and ms["field"] > 0
     if prec == F.FH_MIXED_TF32:
         assert chosen["lu_rows_per_cta"] in (128, 256, 512) and ms["factor"] > 0
+        assert chosen["lu_early"] in (0, 10, 20, 35) and ms["assemble_factor"] > 0
     else:
         assert chosen["lu_rows_per_cta"] == 512 and ms["factor"] == 0
+        assert chosen["lu_early"] == 0 and ms["assemble_factor"] == 0
     # tuning runs are not counted as launches of the path
     assert all(v["launches"] == 0 for v in F.fh_get_timings(tuned.ctx, reset=True).values())
     by_hand = F.Problem(0, prec)
@@ -144,3 +147,23 @@ def test_autotune_after_solve_keeps_the_solution(oracle_runs):
         assert np.array_equal(x, y)
     u = pr.sample(wl.x, wl.T)
     assert rel(u, ref["u"]) < TOL
+
+
+@pytest.mark.parametrize("early", [10, 35, 50])
+@pytest.mark.parametrize("graphs", [False, True])
+def test_largest_systems_started_early(early, graphs, oracle_runs):
+    """lu_early runs the largest systems' assembly and factorisation on a second
+    stream: the same kernels on the same data, so bitwise the same densities,
+    fields and u as the single sequence (direct launches and graph replay)."""
+    wl, ref = oracle_runs
+    one = F.Problem(0, F.FH_MIXED_TF32)
+    two = F.Problem(0, F.FH_MIXED_TF32)
+    F.fh_set_tuning(two.ctx, lu_early=early)
+    F.fh_set_graphs(two.ctx, graphs)
+    a = cycle(one, wl)
+    for _ in range(3 if graphs else 1):     # direct, capture, replay
+        b = cycle(two, wl)
+        for x, y in zip(a[0], b[0]):
+            assert np.array_equal(x, y)
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert rel(b[2], ref["u"]) < TOL
