@@ -341,12 +341,86 @@ __global__ void __launch_bounds__(64) diag_inverse_kernel(const int2 *__restrict
     }
 }
 
+// Software-pipelined form of lu_solve_rowmajor for n <= blockDim.x - 32:
+// thread t < n keeps row t and the last warp (which owns no row) does the
+// diagonal-block products.  The loads a step needs (the last warp: the next
+// block inverse; a row thread: its row's segment of the next block) are
+// issued as soon as the current step has consumed the register buffer, so
+// that they are in flight across the barriers and the other warps' work
+// rather than on the critical path of each step.  Same arithmetic, in the
+// same order, as the blocked form.
+__device__ void lu_solve_rowmajor_pipe(const float2 *__restrict__ a, int n,
+                                       const float2 *__restrict__ inv, float2 *y) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool dw = tid >= (int)blockDim.x - 32;   // the diagonal warp
+    const int nblk = (n + 31) / 32, steps = 2 * nblk;
+    float4 r[16];   // next block inverse row (diagonal warp) or next row segment
+    // step k: pass 0 (L, forward) over blocks 0 .. nblk-1, then pass 1 (U,
+    // backward) over blocks nblk-1 .. 0; rows updated: below (L) or above (U)
+    auto block_of = [&](int k) { return k < nblk ? k : steps - 1 - k; };
+    auto active = [&](int k) {
+        const int b = block_of(k), jb = 32 * b, je = min(jb + 32, n);
+        return !dw && (k < nblk ? (tid >= je && tid < n) : (tid < jb));
+    };
+    auto load_inv = [&](int k) {
+        const int pass = k < nblk ? 0 : 1, b = block_of(k);
+        const float4 *row = reinterpret_cast<const float4 *>(inv + (long long)b * 2048 + pass * 1024 + lane * 32);
+#pragma unroll
+        for (int h = 0; h < 16; ++h) r[h] = row[h];
+    };
+    auto load_row = [&](int k) {
+        const int jb = 32 * block_of(k), je = min(jb + 32, n);
+        const float4 *src = reinterpret_cast<const float4 *>(a + (long long)tid * n + jb);
+#pragma unroll
+        for (int h = 0; h < 16; ++h)
+            if (jb + 2 * h < je) r[h] = src[h];
+    };
+    if (dw) load_inv(0);
+    else if (active(0)) load_row(0);
+    for (int k = 0; k < steps; ++k) {
+        const int jb = 32 * block_of(k), je = min(jb + 32, n);
+        if (dw) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int h = 0; h < 16; ++h) {
+                const int q = jb + 2 * h;
+                if (q < je) {
+                    const float2 y0 = y[q], y1 = y[q + 1];
+                    acc.x += r[h].x * y0.x - r[h].y * y0.y + r[h].z * y1.x - r[h].w * y1.y;
+                    acc.y += r[h].x * y0.y + r[h].y * y0.x + r[h].z * y1.y + r[h].w * y1.x;
+                }
+            }
+            if (k + 1 < steps) load_inv(k + 1);
+            __syncwarp();
+            if (jb + lane < je) y[jb + lane] = acc;
+        }
+        __syncthreads();
+        if (active(k)) {
+            float2 yi = y[tid];
+#pragma unroll
+            for (int h = 0; h < 16; ++h)
+                if (jb + 2 * h < je) {
+                    const float2 y0 = y[jb + 2 * h], y1 = y[jb + 2 * h + 1];
+                    yi.x -= r[h].x * y0.x - r[h].y * y0.y + r[h].z * y1.x - r[h].w * y1.y;
+                    yi.y -= r[h].x * y0.y + r[h].y * y0.x + r[h].z * y1.y + r[h].w * y1.x;
+                }
+            y[tid] = yi;
+        }
+        if (k + 1 < steps && active(k + 1)) load_row(k + 1);
+        __syncthreads();
+    }
+}
+
 // Row-major factors (tensor-core LU): blocked substitution in which each
 // 32-row diagonal step is a product with the precomputed block inverse (one
 // warp, no dependent chain) and the off-diagonal updates use 16-byte loads
 // of the row segments; written for blockDim = 512.
 __device__ void lu_solve_rowmajor(const float2 *__restrict__ a, int n, const float2 *__restrict__ inv,
                                   float2 *y) {
+    if (n <= (int)blockDim.x - 32) {
+        lu_solve_rowmajor_pipe(a, n, inv, y);
+        return;
+    }
     const int tid = threadIdx.x, lane = tid & 31;
     const int nblk = (n + 31) / 32;
     for (int pass = 0; pass < 2; ++pass) {           // 0: L (forward), 1: U (backward)
