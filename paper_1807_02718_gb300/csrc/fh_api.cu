@@ -638,7 +638,7 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     FH_TRY(ensure(ctx, ctx->d_A, (size_t)mo * sizeof(double2)));
     FH_TRY(ensure(ctx, ctx->d_info, (size_t)S * sizeof(int)));
     FH_TRY(ensure(ctx, ctx->d_nu_f, (size_t)nu_off * sizeof(float4)));
-    FH_TRY(ensure(ctx, ctx->d_ph, (size_t)ph_off * sizeof(double2)));
+    FH_TRY(ensure(ctx, ctx->d_ph, (size_t)ph_off * sizeof(float4)));
 
     int maxM = 0;
     for (const Problem &pb : ctx->probs) maxM = std::max(maxM, pb.M);
@@ -662,7 +662,7 @@ fh_status discretize_device(fh_ctx *ctx) {
     for (Problem &pb : ctx->probs) {
         fh::launch_far_table(pb.J, pb.M, ctx->d_pw.as<double>(), nullptr,
                              ctx->d_nu_f.as<float4>() + pb.nu_off,
-                             ctx->d_ph.as<double2>() + pb.ph_off, ctx->stream);
+                             ctx->d_ph.as<float4>() + pb.ph_off, ctx->stream);
         FH_TRY(check_launch(ctx, "far table"));
     }
     ctx->geom = true;
@@ -738,7 +738,7 @@ fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, in
         PhaseScope ps(ctx, FH_PH_WEIGHTS, 2);
         fh::launch_synth_weights(pb.J, pb.M, pb.W, pb.K, pb.d_s.as<double>(), pb.d_B.as<double2>(),
                                  ctx->d_Bf.as<float4>(), ctx->d_nu_f.as<float4>() + pb.nu_off,
-                                 ctx->d_ph.as<double2>() + pb.ph_off, d_T, n_T,
+                                 ctx->d_ph.as<float4>() + pb.ph_off, d_T, n_T,
                                  ctx->d_Gr.as<double>(), ctx->d_Gm.as<double>(),
                                  mixed ? ctx->d_Gs.as<float2>() : nullptr, ctx->stream);
         FH_TRY(check_launch(ctx, "synthesis weights"));

@@ -154,7 +154,7 @@ void launch_bessel_eval_df(const double *x, int n, double *out, cudaStream_t st)
 // be null), and nu_f the same as double-float pairs (re hi, re lo, im hi,
 // im lo); pw is scratch of M * kFarTerms doubles.
 constexpr int kFarTerms = 170;
-void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, double2 *phase_tab,
+void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, float4 *phase_tab,
                       cudaStream_t st);
 // Gr/Gm: planes [p][t] with u(x,t) = sum_p Vr[p][x] Gr[p][t] + Vi[p][x] Gm[p][t].
 // Gs (optional; then Gr/Gm are not written): the same weights as double-float
@@ -163,7 +163,7 @@ void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, doubl
 // double-float copy of B (one extra launch); null splits B on the fly.
 inline int synth_pitch(int n) { return (n + 3) & ~3; }
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
-                          float4 *Bf, const float4 *nu_f, const double2 *phase_tab, const double *T,
+                          float4 *Bf, const float4 *nu_f, const float4 *phase_tab, const double *T,
                           int n_T, double *Gr, double *Gm, float2 *Gs, cudaStream_t st);
 // FP64 contraction u = [Vr | Vi] [Gr ; Gm] (FP64 FMAs).
 void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,

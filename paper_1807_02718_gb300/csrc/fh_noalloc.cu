@@ -69,7 +69,7 @@ extern "C" fh_status fh_synthesize_static(int J, double W, int K, const double *
     double *Gm = Gr + (size_t)J * n_T;
     double *pw = scratch;   // power table of the far-field table; G is written after it is used
     float4 *nu_f = reinterpret_cast<float4 *>(scratch + 2 * (size_t)kMaxGridPoints);
-    double2 *ph = reinterpret_cast<double2 *>(nu_f + (size_t)fh::kFarTerms * kMaxJ);
+    float4 *ph = nu_f + (size_t)fh::kFarTerms * kMaxJ;   // phase table, double-float
     fh::launch_far_table(J, M, pw, nullptr, nu_f, ph, stream);
     fh::launch_synth_weights(J, M, W, K, d_s, reinterpret_cast<const double2 *>(d_B), nullptr, nu_f, ph, d_T,
                              n_T, Gr, Gm, nullptr, stream);

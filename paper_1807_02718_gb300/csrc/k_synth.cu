@@ -49,7 +49,7 @@ constexpr int kFarChunk = 128;
 
 __global__ void __launch_bounds__(192) far_table_kernel(int J, int M, const double *__restrict__ pw,
                                                        double2 *__restrict__ nu, float4 *__restrict__ nu_f,
-                                                       double2 *__restrict__ ph) {
+                                                       float4 *__restrict__ ph) {
     const int p = blockIdx.x;
     const int r = threadIdx.x;
     const int h = M / 2;
@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(192) far_table_kernel(int J, int M, const doub
         for (int q = r; q < M; q += blockDim.x) {
             double sn, cs;
             sincospi(-2.0 * (double)q / (double)M, &sn, &cs);
-            ph[q] = make_double2(cs, sn);
+            const float ch = (float)cs, sh = (float)sn;   // double-float (cos, sin)
+            ph[q] = make_float4(ch, (float)(cs - (double)ch), sh, (float)(sn - (double)sh));
         }
     double sr = 0.0, si = 0.0;
     for (int m0 = -h; m0 < h; m0 += kFarChunk) {
@@ -165,29 +166,23 @@ __device__ __forceinline__ void df_horner(float &ah, float &al, dfl r, float vh,
 // far windows: Horner in double-float over the double-float copy of nu.
 __global__ void __launch_bounds__(256) weights_kernel(
     int J, int M, double W, int K, const double *__restrict__ s, const double2 *__restrict__ B,
-    const float4 *__restrict__ Bf, const float4 *__restrict__ nu_f, const double2 *__restrict__ ph_g,
+    const float4 *__restrict__ Bf, const float4 *__restrict__ nu_f, const float4 *__restrict__ ph_g,
     const double *__restrict__ T, int n_T, double *__restrict__ Gr, double *__restrict__ Gm,
     float2 *__restrict__ Gs, int pitch_T) {
-    extern __shared__ double smd[];
+    extern __shared__ __align__(16) double smd[];
     double *wy = smd;                                        // K: y
     double *wf = wy + K;                                     // K: sin(pi y) (near) or scale sinc(y) (far)
     float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: h / y (far) or 2W/M (near), double-float
     float2 *wfd = wrho + K;                                  // K: scale sinc(y) (far), double-float
     int *wR = reinterpret_cast<int *>(wfd + K);              // K: far terms R | R1 << 16, 0 = near
-    float2 *phc = reinterpret_cast<float2 *>(wR + ((K + 1) & ~1));   // M: cos (hi, lo)
-    float2 *phs = phc + M;                                   // M: sin (hi, lo)
-    float2 *sc = phs + M;                                    // M: sinc (hi, lo)
+    float4 *ph4 = reinterpret_cast<float4 *>(wR + ((K + 3) & ~3));   // M: (cos hi, lo, sin hi, lo)
+    float4 *sc4 = ph4 + M;   // h: [0] = (S(y), S(y+h)), [j] = (S(y-j) + S(y+j), S(y-j) - S(y+j))
     const int t = blockIdx.x;
     const int p = blockIdx.y * blockDim.x + threadIdx.x;
     const int h = M / 2;
     const double tt = T[t];
     const double scale = 2.0 * W / (double)M;
-    for (int q = threadIdx.x; q < M; q += blockDim.x) {
-        const double2 e = ph_g[q];
-        const dfl c = df_split(e.x), sn = df_split(e.y);
-        phc[q] = make_float2(c.hi, c.lo);
-        phs[q] = make_float2(sn.hi, sn.lo);
-    }
+    for (int q = threadIdx.x; q < M; q += blockDim.x) ph4[q] = ph_g[q];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const double y = W * (tt - s[k]) / kPi;
         const double sy = sinpi(y);
@@ -244,25 +239,23 @@ __global__ void __launch_bounds__(256) weights_kernel(
                     }
                 }
                 if (jj == 0) {
-                    sc[0] = make_float2(va.hi, va.lo);      // S(y)
-                    sc[h] = make_float2(vb.hi, vb.lo);      // S(y + h)
+                    sc4[0] = make_float4(va.hi, va.lo, vb.hi, vb.lo);   // S(y), S(y + h)
                 } else if (jj < h) {
                     const dfl sp = df_addq(va, vb), sm = df_addq(va, {-vb.hi, -vb.lo});
-                    sc[jj] = make_float2(sp.hi, sp.lo);
-                    sc[h + jj] = make_float2(sm.hi, sm.lo);
+                    sc4[jj] = make_float4(sp.hi, sp.lo, sm.hi, sm.lo);
                 }
             }
             __syncthreads();
             if (p < J) {
-                const float2 s0 = sc[0], shh = sc[h];
-                const dfl r0 = df_addq({s0.x, s0.y}, (p & 1) ? dfl{-shh.x, -shh.y} : dfl{shh.x, shh.y});
+                const float4 s0 = sc4[0];
+                const dfl r0 = df_addq({s0.x, s0.y}, (p & 1) ? dfl{-s0.z, -s0.w} : dfl{s0.z, s0.w});
                 float rh = r0.hi, rl = r0.lo, ih = 0.f, il = 0.f;
                 int q = p;
                 for (int jj = 1; jj < h; ++jj) {
-                    const float2 c2 = phc[q], s2 = phs[q];
-                    const float2 a2 = sc[jj], b2 = sc[h + jj];
-                    df_mac(rh, rl, {c2.x, c2.y}, {a2.x, a2.y});
-                    df_mac(ih, il, {s2.x, s2.y}, {b2.x, b2.y});
+                    const float4 e = ph4[q];     // one 16-byte gather: cos and sin
+                    const float4 v = sc4[jj];    // one 16-byte broadcast: both sinc sums
+                    df_mac(rh, rl, {e.x, e.y}, {v.x, v.y});
+                    df_mac(ih, il, {e.z, e.w}, {v.z, v.w});
                     q += p;
                     if (q >= M) q -= M;
                     if ((jj & 31) == 31) {   // renormalise the accumulators
@@ -526,18 +519,18 @@ __global__ void __launch_bounds__(256) contract_df_kernel(int J, int n_x, int n_
 
 }  // namespace
 
-void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, double2 *phase_tab,
+void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, float4 *phase_tab,
                       cudaStream_t st) {
     far_powers_kernel<<<(M + 127) / 128, 128, 0, st>>>(M, pw);
     far_table_kernel<<<J, 192, 0, st>>>(J, M, pw, nu, nu_f, phase_tab);
 }
 
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
-                          float4 *Bf, const float4 *nu_f, const double2 *phase_tab, const double *T,
+                          float4 *Bf, const float4 *nu_f, const float4 *phase_tab, const double *T,
                           int n_T, double *Gr, double *Gm, float2 *Gs, cudaStream_t st) {
     if (n_T <= 0) return;
     const size_t smem = (size_t)K * (2 * sizeof(double) + 2 * sizeof(float2)) +
-                        (size_t)((K + 1) & ~1) * sizeof(int) + (size_t)M * 3 * sizeof(float2);
+                        (size_t)((K + 3) & ~3) * sizeof(int) + (size_t)(M + M / 2) * sizeof(float4);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
