@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default schedule instead of running the autotuner at set-up")
+    ap.add_argument("--tuning", default=None,
+                    help="schedule given explicitly instead of autotuned, e.g. "
+                         "assemble_group=8,field_group=4,field_chunk=64,lu_rows_per_cta=512,lu_early=20")
     return ap.parse_args()
 
 
@@ -139,9 +142,13 @@ DF_MAC_INSTR = 11                                          # FP32 instructions p
 DF_PEAK = FP32_PEAK / DF_MAC_INSTR                         # FP64-equivalent flop/s of df MACs
 TF32_OVER_BF16 = 1.1 / 2.25                                # nominal dense tensor rates
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
-# committed (profiles/assemble_group_df_kite_pulses.md).
-MEASURED_TRAFFIC = {"assemble_group_df_kernel": 278.7e6}
+# DRAM bytes (read + write) per step of the kernel as committed, from one ncu
+# capture of the bench command with the autotuned schedule
+# (profiles/launches_kite_pulses_tf32.md): both launches where the schedule
+# splits a phase into the early and the remaining systems.
+MEASURED_TRAFFIC = {"field_partial_df_kernel": 2.27e6, "lu_factor_tc_kernel": 384.8e6,
+                    "assemble_group_df_kernel": 215.9e6, "weights_kernel": 0.85e6,
+                    "contract_df_kernel": 36.6e6}
 
 
 def window_work(wl):
@@ -319,7 +326,10 @@ def run_gpu(args, world, rank, local):
 
     # ---- set-up: schedule autotuning on this workload (not timed) ----
     tuning = {"autotuned": False, "setting": F.fh_get_tuning(pr.ctx)}
-    if not args.no_tune:
+    if args.tuning:
+        F.fh_set_tuning(pr.ctx, **{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
+        tuning = {"autotuned": False, "setting": F.fh_get_tuning(pr.ctx)}
+    elif not args.no_tune:
         F.fh_discretize(pr.ctx, wl.curve, wl.omega, wl.N, wl.c, wl.p)
         t0 = time.perf_counter()
         chosen, best_ms = F.fh_autotune(pr.ctx, wl.x, reps=3)
