@@ -169,7 +169,10 @@ def window_work(wl):
     return float(np.sum(np.where(near, 4 * J * h, 4 * J * R)) + 8 * J * y.size)
 
 
-def phase_rooflines(wl, precision, ms, iters, peaks):
+OZAKI_PAIRS = 28   # slice pairs (i, j), i + j < 7, of the tensor-core contraction
+
+
+def phase_rooflines(wl, precision, ms, iters, peaks, contract_tc=False):
     """Achieved against peak per phase; work definitions in the design doc."""
     N = wl.N[1:].astype(np.float64)
     mixed = precision != "fp64"
@@ -209,9 +212,14 @@ def phase_rooflines(wl, precision, ms, iters, peaks):
         50.0 * wl.n_x * float(np.sum(N)), DF_PEAK if mixed else FP64_PEAK,
         (df_src if mixed else fp64_src) + "; work 50 FP64-equivalent flop per (target, node)")
     put("weights", "weights_kernel", "alu", window_work(wl), DF_PEAK, df_src)
-    put("contract", "contract_df_kernel" if mixed else "contract_kernel", "alu",
-        contract_flops(wl.n_x, wl.T.size, wl.J), DF_PEAK if mixed else FP64_PEAK,
-        "double-float MAC rate: FP32 unit count / 11 instructions per MAC" if mixed else fp64_src)
+    if contract_tc:
+        put("contract", "contract_tc_kernel", "tensor", OZAKI_PAIRS * contract_flops(wl.n_x, wl.T.size, wl.J),
+            bf16, "measured bf16 dense GEMM (MEASURED_PEAKS.json); work 28 BF16 slice-pair products of "
+            "2 n_x n_T (2J) flop (FP64-class result from exact slices)")
+    else:
+        put("contract", "contract_df_kernel" if mixed else "contract_kernel", "alu",
+            contract_flops(wl.n_x, wl.T.size, wl.J), DF_PEAK if mixed else FP64_PEAK,
+            "double-float MAC rate: FP32 unit count / 11 instructions per MAC" if mixed else fp64_src)
     return out
 
 
@@ -416,7 +424,10 @@ def run_gpu(args, world, rank, local):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    roofs = phase_rooflines(wl, args.precision, step_ms_phases, solve_stats.get("iters", 0), peaks)
+    contract_tc = (args.precision != "fp64" and bool(tuning["setting"].get("contract_tc"))
+                   and 2 * wl.J <= 576)
+    roofs = phase_rooflines(wl, args.precision, step_ms_phases, solve_stats.get("iters", 0), peaks,
+                            contract_tc)
     roof = dict(roofs.get(dominant) or {"bound": "alu", "achieved": None, "peak": None,
                                         "unit": "TFLOP/s", "frac": None, "kernel": dominant})
     roof["traffic"] = MEASURED_TRAFFIC.get(roof.get("kernel"))

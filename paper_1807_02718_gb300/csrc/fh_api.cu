@@ -90,7 +90,7 @@ struct fh_ctx {
     std::vector<long long> mat_off;
     std::vector<double> kappa_s, eta_s;
     // schedule parameters (fh_set_tuning, fh_autotune)
-    fh_tuning tune{fh::kGroup, fh::kGroup, fh::kFieldChunk, 512, 0};
+    fh_tuning tune{fh::kGroup, fh::kGroup, fh::kFieldChunk, 512, 0, 1};
     // lu_early: the first early_groups assembly subgroups (early_solves solves,
     // the largest) are assembled and factored on the side stream
     int early_groups = 0, early_solves = 0;
@@ -116,7 +116,8 @@ struct fh_ctx {
     int n_rchunk = 0, n_dblk = 0;
     DevBuf d_wa, d_a;
     int n_x_last = 0;
-    DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm, d_Gs, d_Vs;
+    DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm, d_Gs, d_Vs, d_ctc, d_ctc_err;
+    bool ctc_pending = false;   // a tensor-core contraction ran since its flag was last read
     DevBuf d_tmpA, d_tmpg, d_tmp_ll, d_tmp_d, d_tmp_i;
 
     // timing: pending (phase, start, stop) event triples and totals
@@ -141,7 +142,7 @@ struct fh_ctx {
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_zf, &d_dzf, &d_sf, &d_wpf, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_A32, &d_piv, &d_g, &d_iters,
-                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_Gs, &d_Vs,
+                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_Gs, &d_Vs, &d_ctc, &d_ctc_err,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d, &d_tmp_i};
         for (DevBuf *b : all) free_buf(*b);
         free_problems();
@@ -337,7 +338,7 @@ bool tuning_valid(const fh_tuning &t) {
            t.field_group <= fh::kGroup &&
            (t.field_chunk == 16 || t.field_chunk == 32 || t.field_chunk == 64) &&
            (t.lu_rows_per_cta == 128 || t.lu_rows_per_cta == 256 || t.lu_rows_per_cta == 512) &&
-           t.lu_early >= 0 && t.lu_early <= 50;
+           t.lu_early >= 0 && t.lu_early <= 50 && (t.contract_tc == 0 || t.contract_tc == 1);
 }
 
 // Splits each problem's solves into runs of equal N of at most gmax solves:
@@ -720,10 +721,20 @@ fh_status spectra_common(fh_ctx *ctx, Problem &pb, const double *d_a, int n_samp
 
 // FP64: weight planes Gr, Gm; mixed: the double-float weights Gs and the
 // double-float copy Vs of the target fields (2J rows each, padded pitch).
+// The mixed paths contract on the tensor cores when the schedule asks for it
+// and 2J fits the exact-accumulation bound.
+bool use_contract_tc(const fh_ctx *ctx, const Problem &pb) {
+    return ctx->precision != FH_FP64 && ctx->tune.contract_tc && fh::contract_tc_ok(pb.J);
+}
+
 fh_status synth_buffers(fh_ctx *ctx, Problem &pb, int n_x, int n_T) {
-    if (ctx->precision == FH_FP64) {
+    if (ctx->precision == FH_FP64 || use_contract_tc(ctx, pb)) {
         FH_TRY(ensure(ctx, ctx->d_Gr, (size_t)pb.J * n_T * sizeof(double)));
         FH_TRY(ensure(ctx, ctx->d_Gm, (size_t)pb.J * n_T * sizeof(double)));
+        if (ctx->precision != FH_FP64) {
+            FH_TRY(ensure(ctx, ctx->d_ctc, fh::contract_tc_scratch_bytes(pb.J, n_x, n_T)));
+            FH_TRY(ensure(ctx, ctx->d_ctc_err, sizeof(int)));
+        }
     } else {
         FH_TRY(ensure(ctx, ctx->d_Gs, (size_t)2 * pb.J * fh::synth_pitch(n_T) * sizeof(float2)));
         FH_TRY(ensure(ctx, ctx->d_Vs, (size_t)2 * pb.J * fh::synth_pitch(n_x) * sizeof(float2)));
@@ -733,7 +744,8 @@ fh_status synth_buffers(fh_ctx *ctx, Problem &pb, int n_x, int n_T) {
 
 // Weights G_p(t) and the contraction u = Re sum_p V_p G_p (buffers exist).
 fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
-    const bool mixed = ctx->precision != FH_FP64;
+    const bool tcc = use_contract_tc(ctx, pb);
+    const bool mixed = ctx->precision != FH_FP64 && !tcc;   // double-float weights and contraction
     {
         PhaseScope ps(ctx, FH_PH_WEIGHTS, 2);
         fh::launch_synth_weights(pb.J, pb.M, pb.W, pb.K, pb.d_s.as<double>(), pb.d_B.as<double2>(),
@@ -743,7 +755,16 @@ fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, in
                                  mixed ? ctx->d_Gs.as<float2>() : nullptr, ctx->stream);
         FH_TRY(check_launch(ctx, "synthesis weights"));
     }
-    PhaseScope ps(ctx, FH_PH_CONTRACT, mixed ? 2 : 1);
+    PhaseScope ps(ctx, FH_PH_CONTRACT, tcc ? 5 : mixed ? 2 : 1);
+    if (tcc) {
+        FH_CUDA(ctx, cudaMemsetAsync(ctx->d_ctc_err.p, 0, sizeof(int), ctx->stream));
+        const cudaError_t e = fh::launch_contract_tc(pb.J, n_x, n_T, ctx->d_V.as<double2>(),
+                                                     ctx->d_Gr.as<double>(), ctx->d_Gm.as<double>(), d_u,
+                                                     ctx->d_ctc.p, ctx->d_ctc_err.as<int>(), ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "tensor-core contraction: %s", cudaGetErrorString(e));
+        ctx->ctc_pending = true;
+        return FH_OK;
+    }
     if (mixed)
         fh::launch_synth_contract_df(pb.J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Vs.as<float2>(),
                                      ctx->d_Gs.as<float2>(), d_u, ctx->stream);
@@ -810,6 +831,18 @@ fh_status check_sample_args(fh_ctx *ctx, int q, int n_x, int n_T) {
     return FH_OK;
 }
 
+// Waits for a host-pointer sample; reports a tensor-core contraction that gave
+// up waiting (its flag is read with the result).
+fh_status finish_sample(fh_ctx *ctx) {
+    int ctc_err = 0;
+    if (ctx->ctc_pending)
+        FH_CUDA(ctx, cudaMemcpyAsync(&ctc_err, ctx->d_ctc_err.p, sizeof(int), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctc_err) return fail(ctx, FH_ETIMEOUT, "a tensor-core completion wait of the contraction gave up");
+    return FH_OK;
+}
+
 fh_status sample_host(fh_ctx *ctx, int q, const double *x, int n_x, const double *T, int n_T,
                       double *u_out) {
     FH_TRY(check_sample_args(ctx, q, n_x, n_T));
@@ -826,8 +859,7 @@ fh_status sample_host(fh_ctx *ctx, int q, const double *x, int n_x, const double
                          ctx->d_u.as<double>()));
     FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
                                  cudaMemcpyDeviceToHost, ctx->stream));
-    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return FH_OK;
+    return finish_sample(ctx);
 }
 
 fh_status spectra_host(fh_ctx *ctx, int q, const double *a, int n_samples, double t0, double dt,
@@ -1372,8 +1404,7 @@ fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, 
     FH_TRY(synth_common(ctx, *pb, n_x, ctx->d_T.as<double>(), n_T, ctx->d_u.as<double>()));
     FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
                                  cudaMemcpyDeviceToHost, ctx->stream));
-    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return FH_OK;
+    return finish_sample(ctx);
 }
 
 fh_status fh_footprint(const int *J, const int *N, int P, int precision, long long *bytes) {

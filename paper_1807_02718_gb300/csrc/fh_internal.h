@@ -168,6 +168,19 @@ void launch_synth_weights(int J, int M, double W, int K, const double *s, const 
 // FP64 contraction u = [Vr | Vi] [Gr ; Gm] (FP64 FMAs).
 void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,
                            const double *Gm, double *u, cudaStream_t st);
+// Tensor-core contraction (mixed-precision paths, 2J <= kContractTcMaxK): the
+// operands cut into seven 6-bit slices held exactly in BF16, every slice
+// product summed exactly in FP32 per level, levels combined in double-float.
+// scratch: contract_tc_scratch_bytes(J, n_x, n_T) bytes; err set if an MMA
+// completion wait gave up.  Six launches.
+constexpr int kContractTcMaxK = 576;
+bool contract_tc_ok(int J);
+size_t contract_tc_scratch_bytes(int J, int n_x, int n_T);
+cudaError_t launch_contract_tc(int J, int n_x, int n_T, const double2 *V, const double *Gr,
+                               const double *Gm, double *u, void *scratch, int *err, cudaStream_t st);
+int contract_tc_kpad(int J);
+int contract_tc_rows(int n);
+int contract_tc_cols(int n);
 // Double-float contraction (mixed-precision paths): V is split into Vs
 // (scratch of 2J rows of synth_pitch(n_x) float2), then u = Vs^T Gs with exact
 // products and double-float accumulation.  Two launches.

@@ -57,7 +57,7 @@ class fh_timings(C.Structure):
 
 class fh_tuning(C.Structure):
     _fields_ = [("assemble_group", C.c_int), ("field_group", C.c_int), ("field_chunk", C.c_int),
-                ("lu_rows_per_cta", C.c_int), ("lu_early", C.c_int)]
+                ("lu_rows_per_cta", C.c_int), ("lu_early", C.c_int), ("contract_tc", C.c_int)]
 
 
 class FHError(RuntimeError):

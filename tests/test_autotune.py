@@ -93,10 +93,10 @@ def test_invalid_settings_are_rejected():
     pr = F.Problem(0, F.FH_MIXED_TF32)
     before = F.fh_get_tuning(pr.ctx)
     assert before == {"assemble_group": 8, "field_group": 8, "field_chunk": 64,
-                      "lu_rows_per_cta": 512, "lu_early": 0}
+                      "lu_rows_per_cta": 512, "lu_early": 0, "contract_tc": 1}
     for bad in (dict(assemble_group=0), dict(assemble_group=9), dict(field_group=0),
                 dict(field_chunk=48), dict(field_chunk=128), dict(lu_rows_per_cta=1024),
-                dict(lu_early=-1), dict(lu_early=51)):
+                dict(lu_early=-1), dict(lu_early=51), dict(contract_tc=2)):
         with pytest.raises(F.FHError) as e:
             F.fh_set_tuning(pr.ctx, **bad)
         assert e.value.status == F.FH_EINVAL
