@@ -169,7 +169,7 @@ def window_work(wl):
     return float(np.sum(np.where(near, 4 * J * h, 4 * J * R)) + 8 * J * y.size)
 
 
-OZAKI_PAIRS = 28   # slice pairs (i, j), i + j < 7, of the tensor-core contraction
+OZAKI_PAIRS = 36   # slice pairs (i, j), i + j < 8, of the tensor-core contraction
 
 
 def phase_rooflines(wl, precision, ms, iters, peaks, contract_tc=False):
@@ -214,7 +214,7 @@ def phase_rooflines(wl, precision, ms, iters, peaks, contract_tc=False):
     put("weights", "weights_kernel", "alu", window_work(wl), DF_PEAK, df_src)
     if contract_tc:
         put("contract", "contract_tc_kernel", "tensor", OZAKI_PAIRS * contract_flops(wl.n_x, wl.T.size, wl.J),
-            bf16, "measured bf16 dense GEMM (MEASURED_PEAKS.json); work 28 BF16 slice-pair products of "
+            bf16, "measured bf16 dense GEMM (MEASURED_PEAKS.json); work 36 BF16 slice-pair products of "
             "2 n_x n_T (2J) flop (FP64-class result from exact slices)")
     else:
         put("contract", "contract_df_kernel" if mixed else "contract_kernel", "alu",
@@ -425,7 +425,7 @@ def run_gpu(args, world, rank, local):
     except Exception:
         pass
     contract_tc = (args.precision != "fp64" and bool(tuning["setting"].get("contract_tc"))
-                   and 2 * wl.J <= 576)
+                   and 2 * wl.J <= 512)
     roofs = phase_rooflines(wl, args.precision, step_ms_phases, solve_stats.get("iters", 0), peaks,
                             contract_tc)
     roof = dict(roofs.get(dominant) or {"bound": "alu", "achieved": None, "peak": None,

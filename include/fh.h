@@ -295,10 +295,10 @@ fh_status fh_set_graphs(fh_ctx *ctx, int enable);
  *                    assembled and factored on a second stream while the
  *                    others are assembled (0: one sequence).  Kernel timing
  *                    (fh_set_timing) runs the single sequence.
- *   contract_tc      mixed paths, 2J <= 576: 1 contracts u = [Vr | Vi][Gr ; Gm]
- *                    on the tensor cores (operands cut into seven 6-bit
+ *   contract_tc      mixed paths, 2J <= 512: 1 contracts u = [Vr | Vi][Gr ; Gm]
+ *                    on the tensor cores (operands cut into eight 6-bit
  *                    slices held exactly in BF16, exact FP32 sums per slice
- *                    level, levels combined in double-float; ~2^-42 of
+ *                    level, levels combined in double-float; ~2^-48 of
  *                    max|row| max|column| per term), 0 in double-float on the
  *                    FP32 pipe.  fh_sample and fh_synthesize (host pointers)
  *                    report a tensor-core completion wait that gave up as

@@ -4,16 +4,16 @@
 // of the operands, the "Ozaki scheme").
 //
 // Each row x of A is scaled by a power of two sa_x >= max_kk |A[x][kk]| and
-// cut into kSlices slices of kSliceBits bits, A[x][kk] / sa_x = sum_i
-// a_i 2^-(kSliceBits (i + 1)) + O(2^-42), a_i integers with |a_i| <= 2^6;
+// cut into kSlices = 8 slices of kSliceBits = 6 bits, A[x][kk] / sa_x =
+// sum_i a_i 2^-(6 (i + 1)) + O(2^-49), a_i integers with |a_i| <= 2^6;
 // likewise each column t of B with sb_t.  Integers of 7 bits are exact in
 // BF16, their products (<= 2^12) are exact in the FP32 accumulator, and a
-// level d = i + j sums at most kSlices pairs over K <= kMaxK terms below 2^24,
-// so every level is an exact integer sum: TMEM holds one FP32 accumulator per
-// level (kSlices x 64 columns).  The epilogue combines the levels, scaled by
+// level d = i + j sums at most kSlices pairs over K <= 512 terms below 2^24
+// (8 x 512 x 2^12 = 2^24), so every level is an exact integer sum: TMEM holds
+// one FP32 accumulator per level (kSlices x 64 = 512 columns, all of it).  The epilogue combines the levels, scaled by
 // 2^-(kSliceBits (d + 2)), in double-float and multiplies by sa_x sb_t.  The
 // result differs from the exact product by the dropped slice pairs (i + j >=
-// kSlices) and the remainders, ~K 2^-42 sa_x sb_t at worst.
+// kSlices) and the remainders, ~K 2^-48 sa_x sb_t at worst.
 //
 // Kernels: ozaki_scale_kernel (the power-of-two scale of each row of A and
 // each column of B), ozaki_slice_kernel (slices, written K-major in BF16
@@ -30,7 +30,7 @@
 namespace fh {
 namespace {
 
-constexpr int kSlices = 7;
+constexpr int kSlices = 8;
 constexpr int kSliceBits = 6;
 constexpr int kTM = 128;                 // output rows (x) per CTA = TMEM lanes
 constexpr int kTN = 64;                  // output columns (t) per CTA
@@ -85,10 +85,10 @@ __global__ void __launch_bounds__(kThr) ozaki_scale_kernel(Src src, int K, int *
 
 // Slices of a 64-row x 32-column block: out[s][r][kk] (row pitch kpad, BF16).
 // In integer arithmetic on the FP64 bit pattern: V = round(src 2^(42 - e[r]))
-// (|V| <= 2^42) = sum_s a_s 2^(36 - 6 s) with balanced digits, each the
+// (|V| <= 2^48) = sum_s a_s 2^(42 - 6 s) with balanced digits, each the
 // nearest multiple of the remainder (a_0 in [-64, 64], a_s in [-32, 32]), so
 // that the dropped slice products carry no common sign: src / 2^e[r] =
-// sum_s a_s 2^-(6 (s + 1)) to within 2^-43.
+// sum_s a_s 2^-(6 (s + 1)) to within 2^-49.
 __global__ void __launch_bounds__(kThr) ozaki_slice_kernel(Src src, const int *__restrict__ e,
                                                            int kpad, long long slice_stride,
                                                            __nv_bfloat16 *__restrict__ out) {
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThr) ozaki_slice_kernel(Src src, const int *_
         const int bexp = (int)((bits >> 52) & 0x7FF);
         const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (bexp ? (1ull << 52) : 0ull);
         // |src| = mant 2^(E), E = bexp - 1075 (1 - 1075 for subnormals); V = mant 2^(E + 42 - e)
-        const int sh = (bexp ? bexp : 1) - 1075 + kSlices * kSliceBits - e[r];   // <= -11
+        const int sh = (bexp ? bexp : 1) - 1075 + kSlices * kSliceBits - e[r];   // <= -5
         long long V = 0;
         if (sh > -64) {
             const int rs = -sh;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kThr) ozaki_slice_kernel(Src src, const int *_
         if (bits >> 63) V = -V;
 #pragma unroll
         for (int s = 0; s < kSlices; ++s) {
-            const int p = kSliceBits * (kSlices - 1 - s);   // 36, 30, ..., 0
+            const int p = kSliceBits * (kSlices - 1 - s);   // 42, 36, ..., 0
             const long long a = p ? (V + (1ll << (p - 1))) >> p : V;   // nearest, ties up
             V -= a << p;                                    // |V| <= 2^(p - 1)
             t[s][kk][rr] = __float2bfloat16_rn((float)a);   // |a| <= 64: exact
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kThr, 1) contract_tc_kernel(
             // The B slices of a stage are consecutive 64-row blocks of one K-major
             // operand, so A slice i against B slices j0 .. j0 + n - 1 (N = 64 n <=
             // 256) writes the products a_i b_j to accumulator columns 64 (i + j):
-            // the level of each pair.  Ten MMAs cover the 28 pairs.
+            // the level of each pair.  Twelve MMAs cover the 36 pairs.
             const uint64_t ds = desc0 + (uint64_t)((s * kStage) >> 4);
 #pragma unroll
             for (int i = 0; i < kSlices; ++i) {

@@ -1,7 +1,8 @@
 """The tensor-core contraction u = [Vr | Vi] [Gr ; Gm] (operands cut into exact
 BF16 slices, exact FP32 sums per slice level): against the oracle's synthesis,
 the double-float contraction and the FP64 path, on ragged tile counts, on rows
-and columns with a wide dynamic range, and its fall-back above 2J = 576."""
+and columns with a wide dynamic range, at the largest exact size (2J = 512) and
+its fall-back above it."""
 import numpy as np
 import pytest
 
@@ -92,11 +93,25 @@ def test_zero_rows_and_columns():
     assert rel(u, u_64) < 1e-11
 
 
+def test_largest_exact_size():
+    """2J = 512 (the bench workload's K): eight levels of 512 terms still sum
+    exactly, and u agrees with the double-float and FP64 contractions."""
+    wl = fi.small_kite(J=256, W=30.0)
+    wl.N = np.full(256, 64, dtype=np.int32)
+    V = fields(wl.J, 150, 5)
+    T = np.linspace(0.0, 60.0, 100)
+    u_tc = synth(wl, F.FH_MIXED_TF32, V, T)
+    u_df = synth(wl, F.FH_MIXED_TF32, V, T, contract_tc=0)
+    u_64 = synth(wl, F.FH_FP64, V, T)
+    assert rel(u_tc, u_64) < 1e-12, rel(u_tc, u_64)
+    assert rel(u_df, u_64) < 1e-12
+
+
 def test_falls_back_above_the_exact_bound():
-    """2J = 602 > 576: the tensor-core setting runs the double-float kernel,
+    """2J = 514 > 512: the tensor-core setting runs the double-float kernel,
     bit for bit."""
-    wl = fi.small_kite(J=301, W=30.0)
-    wl.N = np.full(301, 64, dtype=np.int32)
+    wl = fi.small_kite(J=257, W=30.0)
+    wl.N = np.full(257, 64, dtype=np.int32)
     V = fields(wl.J, 70, 4)
     T = np.linspace(0.0, 60.0, 40)
     a = synth(wl, F.FH_MIXED_TF32, V, T)
