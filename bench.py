@@ -147,13 +147,13 @@ TF32_OVER_BF16 = 1.1 / 2.25                                # nominal dense tenso
 # (profiles/launches_kite_pulses_tf32.md): both launches where the schedule
 # splits a phase into the early and the remaining systems.
 MEASURED_TRAFFIC = {"field_partial_df_kernel": 2.27e6, "lu_factor_tc_kernel": 384.8e6,
-                    "assemble_group_df_kernel": 215.9e6, "weights_kernel": 0.85e6,
-                    "contract_df_kernel": 36.6e6}
+                    "assemble_group_df_kernel": 215.9e6, "contract_df_kernel": 36.6e6}
 
 
 def window_work(wl):
     """FP64-equivalent flops of the synthesis weights per step: near (t, k):
-    4 J h (paired sinc sums); far (t, k): 4 J R (Horner); every (t, k): 8 J
+    4 J x 42 (interpolation from the sampled near sums, J <= 1025) or 4 J h
+    (direct paired sinc sums); far (t, k): 4 J R (Horner); every (t, k): 8 J
     (the B_k accumulation).  R and near/far as in the kernel."""
     J = wl.J
     M = 2 * (J - 1)
@@ -166,7 +166,11 @@ def window_work(wl):
     near = np.abs(y) < 1.25 * h
     with np.errstate(divide="ignore"):
         R = np.clip(np.ceil(-48 * np.log(2) / np.log(np.abs(h / np.where(near, 1.0, y)))), 1, 170)
-    return float(np.sum(np.where(near, 4 * J * h, 4 * J * R)) + 8 * J * y.size)
+    per_near = 4 * J * (SINC_POINTS if J <= SINC_TAB_MAX_J else h)
+    return float(np.sum(np.where(near, per_near, 4 * J * R)) + 8 * J * y.size)
+
+
+SINC_POINTS, SINC_TAB_MAX_J = 42, 1025   # samples per near sum; largest J with the sampled table
 
 
 OZAKI_PAIRS = 36   # slice pairs (i, j), i + j < 8, of the tensor-core contraction

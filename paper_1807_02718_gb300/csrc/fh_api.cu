@@ -48,6 +48,7 @@ struct Problem {
     int fg_begin = 0, fg_end = 0;
     int item_begin = 0, item_end = 0;
     long long nu_off = 0, ph_off = 0, omega_off = 0;   // into the pooled tables
+    long long stab_off = -1;                            // sampled near sums (-1: direct sums)
     bool spectra = false;
     int K = 0;
     double H = 10.0;
@@ -111,6 +112,7 @@ struct fh_ctx {
         d_solve_prob, d_order, d_curves, d_pdir;
     DevBuf d_zf, d_dzf, d_sf, d_wpf;
     DevBuf d_z, d_dz, d_ddz, d_kress, d_logsin, d_A, d_psi, d_info, d_nu, d_nu_f, d_ph, d_omega, d_pw;
+    DevBuf d_stab;
     DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk, d_Bf, d_dblk,
         d_blk_off, d_dinv;
     int n_rchunk = 0, n_dblk = 0;
@@ -141,7 +143,7 @@ struct fh_ctx {
                          &d_part, &d_N, &d_mat_off, &d_vec_off, &d_tab, &d_tab_off, &d_tab_N,
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_zf, &d_dzf, &d_sf, &d_wpf, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
-                         &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_A32, &d_piv, &d_g, &d_iters,
+                         &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_stab, &d_A32, &d_piv, &d_g, &d_iters,
                          &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_Gs, &d_Vs, &d_ctc, &d_ctc_err,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d, &d_tmp_i};
         for (DevBuf *b : all) free_buf(*b);
@@ -526,7 +528,7 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     ctx->tab_N.clear();
     ctx->tab_off.clear();
     std::map<int, int> tab_index;
-    long long mo = 0, nu_off = 0, ph_off = 0;
+    long long mo = 0, nu_off = 0, ph_off = 0, stab_off = 0;
     int vo = 0, tb = 0, maxN = 0;
     std::vector<fh::CurveParams> cps(P);
     std::vector<double2> pdir(P);
@@ -552,6 +554,9 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
         pb.ph_off = ph_off;
         nu_off += (long long)fh::kFarTerms * J;
         ph_off += pb.M;
+        const long long n_stab = fh::sinc_tab_entries(J);
+        pb.stab_off = n_stab ? stab_off : -1;
+        stab_off += n_stab;
         for (int j = 1; j < J; ++j) {
             const int n = pb.Nj[j];
             ctx->solve_prob.push_back(q);
@@ -640,6 +645,7 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     FH_TRY(ensure(ctx, ctx->d_info, (size_t)S * sizeof(int)));
     FH_TRY(ensure(ctx, ctx->d_nu_f, (size_t)nu_off * sizeof(float4)));
     FH_TRY(ensure(ctx, ctx->d_ph, (size_t)ph_off * sizeof(float4)));
+    if (stab_off) FH_TRY(ensure(ctx, ctx->d_stab, (size_t)stab_off * sizeof(float4)));
 
     int maxM = 0;
     for (const Problem &pb : ctx->probs) maxM = std::max(maxM, pb.M);
@@ -650,7 +656,9 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
 // Device part of the discretization: nodes, Kress/log tables, far-field tables.
 fh_status discretize_device(fh_ctx *ctx) {
     const int P = (int)ctx->probs.size(), S = ctx->S, maxN = ctx->maxN;
-    PhaseScope ps_(ctx, FH_PH_GEOMETRY, 2 + 2 * P);
+    int n_stab = 0;
+    for (const Problem &pb : ctx->probs) n_stab += pb.stab_off >= 0;
+    PhaseScope ps_(ctx, FH_PH_GEOMETRY, 2 + 2 * P + n_stab);
     fh::launch_geometry(ctx->d_curves.as<fh::CurveParams>(), ctx->d_solve_prob.as<int>(), S, maxN,
                         ctx->d_N.as<int>(), ctx->d_vec_off.as<int>(), ctx->d_z.as<double2>(),
                         ctx->d_dz.as<double2>(), ctx->d_ddz.as<double2>(), ctx->d_zf.as<float4>(),
@@ -665,6 +673,11 @@ fh_status discretize_device(fh_ctx *ctx) {
                              ctx->d_nu_f.as<float4>() + pb.nu_off,
                              ctx->d_ph.as<float4>() + pb.ph_off, ctx->stream);
         FH_TRY(check_launch(ctx, "far table"));
+        if (pb.stab_off >= 0) {
+            fh::launch_sinc_table(pb.J, pb.M, ctx->d_ph.as<float4>() + pb.ph_off,
+                                  ctx->d_stab.as<float4>() + pb.stab_off, ctx->stream);
+            FH_TRY(check_launch(ctx, "near-sum table"));
+        }
     }
     ctx->geom = true;
     return FH_OK;
@@ -750,7 +763,8 @@ fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, in
         PhaseScope ps(ctx, FH_PH_WEIGHTS, 2);
         fh::launch_synth_weights(pb.J, pb.M, pb.W, pb.K, pb.d_s.as<double>(), pb.d_B.as<double2>(),
                                  ctx->d_Bf.as<float4>(), ctx->d_nu_f.as<float4>() + pb.nu_off,
-                                 ctx->d_ph.as<float4>() + pb.ph_off, d_T, n_T,
+                                 ctx->d_ph.as<float4>() + pb.ph_off,
+                                 pb.stab_off >= 0 ? ctx->d_stab.as<float4>() + pb.stab_off : nullptr, d_T, n_T,
                                  ctx->d_Gr.as<double>(), ctx->d_Gm.as<double>(),
                                  mixed ? ctx->d_Gs.as<float2>() : nullptr, ctx->stream);
         FH_TRY(check_launch(ctx, "synthesis weights"));
@@ -1419,7 +1433,7 @@ fh_status fh_footprint(const int *J, const int *N, int P, int precision, long lo
             if (precision == FH_MIXED_TF32 || precision == FH_MIXED_BF16)
                 b += (n + 31) / 32 * 2048 * 8;                            // diagonal-block inverses
         }
-        b += (long long)fh::kFarTerms * J[q] * 16 + 2LL * (J[q] - 1) * 16;
+        b += (long long)fh::kFarTerms * J[q] * 16 + 2LL * (J[q] - 1) * 16 + fh::sinc_tab_entries(J[q]) * 16;
         jo += J[q];
     }
     *bytes = b;

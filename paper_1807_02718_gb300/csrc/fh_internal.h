@@ -163,8 +163,32 @@ void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, float
 // double-float copy of B (one extra launch); null splits B on the fly.
 inline int synth_pitch(int n) { return (n + 3) & ~3; }
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
-                          float4 *Bf, const float4 *nu_f, const float4 *phase_tab, const double *T,
-                          int n_T, double *Gr, double *Gm, float2 *Gs, cudaStream_t st);
+                          float4 *Bf, const float4 *nu_f, const float4 *phase_tab,
+                          const float4 *sinc_tab, const double *T, int n_T, double *Gr, double *Gm,
+                          float2 *Gs, cudaStream_t st);
+// Near-window sums by interpolation.  The near sums
+//   D_p(y) = sum_{m=-h}^{h-1} e^{-2 pi i m p / M} sinc(y - m)
+// are, as functions of y, band-limited to [-pi, pi]; sampled on the
+// half-integer grid y_g = g / 2 (oversampling 2) they are recovered by
+//   D_p(y) = sum_g D_p(y_g) sinc(2 (y - y_g)) E(y - y_g),
+// E(u) = exp(beta (sqrt(1 - (u / U)^2) - 1)) for |u| < U (the "exponential of
+// semicircle" window), with U = 10.5 and beta = 32.5: 42 samples per y; the
+// window's Fourier transform is flat to 1.4e-15 on [-pi, pi] and its aliases
+// from [3 pi, inf) sum below 1.1e-15.  The table holds D_p(y_g) for |g| <= G =
+// ceil(2.5 h) + 24 (every near y, |y| < 1.25 h, with its 42 samples) as
+// double-float pairs (re hi, re lo, im hi, im lo), row g + G, column p:
+// integer rows are the phases themselves, half-integer rows the direct sums
+// in double-float.  Built for J <= kSincTabMaxJ (table size (2G + 1) J).
+constexpr int kSincTabMaxJ = 1025;
+constexpr int kSincPts = 42;
+constexpr double kSincU = 10.5;
+constexpr double kSincBeta = 32.5;
+inline int sinc_tab_half(int J) { return J >= 2 && J <= kSincTabMaxJ ? (5 * (J - 1) + 1) / 2 + 24 : 0; }
+inline long long sinc_tab_entries(int J) {
+    const int G = sinc_tab_half(J);
+    return G ? (2LL * G + 1) * J : 0;
+}
+void launch_sinc_table(int J, int M, const float4 *phase_tab, float4 *tab, cudaStream_t st);
 // FP64 contraction u = [Vr | Vi] [Gr ; Gm] (FP64 FMAs).
 void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const double *Gr,
                            const double *Gm, double *u, cudaStream_t st);

@@ -71,8 +71,8 @@ extern "C" fh_status fh_synthesize_static(int J, double W, int K, const double *
     float4 *nu_f = reinterpret_cast<float4 *>(scratch + 2 * (size_t)kMaxGridPoints);
     float4 *ph = nu_f + (size_t)fh::kFarTerms * kMaxJ;   // phase table, double-float
     fh::launch_far_table(J, M, pw, nullptr, nu_f, ph, stream);
-    fh::launch_synth_weights(J, M, W, K, d_s, reinterpret_cast<const double2 *>(d_B), nullptr, nu_f, ph, d_T,
-                             n_T, Gr, Gm, nullptr, stream);
+    fh::launch_synth_weights(J, M, W, K, d_s, reinterpret_cast<const double2 *>(d_B), nullptr, nu_f, ph,
+                             nullptr, d_T, n_T, Gr, Gm, nullptr, stream);   // direct near sums
     fh::launch_synth_contract(J, n_x, n_T, reinterpret_cast<const double2 *>(d_V), Gr, Gm, d_u, stream);
     return cudaGetLastError() == cudaSuccess ? FH_OK : FH_ECUDA;
 }

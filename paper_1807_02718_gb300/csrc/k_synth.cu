@@ -159,17 +159,107 @@ __device__ __forceinline__ void df_horner(float &ah, float &al, dfl r, float vh,
     al = err - (ah - s);
 }
 
+// Direct near-window sum, unscaled, for the thread's p (all threads of the CTA
+// call it; it begins and ends with a barrier):
+//   (rh + rl) + i (ih + il) = sum_{m=-h}^{h-1} e^{-2 pi i m p / M} sinc(y - m)
+//   = S(y) + (-1)^p S(y+h) + sum_{j=1}^{h-1} (cos_j (S(y-j) + S(y+j))
+//     + i sin_j (S(y-j) - S(y+j))),
+// S(v) = sinc(v), (cos_j, sin_j) the phase e^{-2 pi i j p / M} (its conjugate
+// pairs -j with j).  The sinc row uses sin(pi (y - j)) = (-1)^j sin(pi y);
+// sypi = sin(pi y) / pi.  ph4: M phases (shared), sc4: h + 1 float4 (shared).
+__device__ void near_sum(double y, dfl sypi, int h, int M, int p, int J, const float4 *ph4,
+                         float4 *sc4, float &rh, float &rl, float &ih, float &il) {
+    __syncthreads();
+    for (int jj = threadIdx.x; jj < h + 1; jj += blockDim.x) {
+        // jj = 0: S(y) and S(y + h) into slot 0; jj >= 1: S(y - jj) +- S(y + jj)
+        const int ja = jj == 0 ? 0 : jj, jb = jj == 0 ? h : jj;
+        dfl va, vb;
+        {
+            const double d = y - (double)ja;
+            if (d == 0.0) va = {1.f, 0.f};
+            else {
+                va = df_mulq(sypi, df_rcpq(df_split(d)));
+                if (ja & 1) va = {-va.hi, -va.lo};
+            }
+        }
+        {
+            const double d = y + (double)jb;
+            if (d == 0.0) vb = {1.f, 0.f};
+            else {
+                vb = df_mulq(sypi, df_rcpq(df_split(d)));
+                if (jb & 1) vb = {-vb.hi, -vb.lo};
+            }
+        }
+        if (jj == 0) {
+            sc4[0] = make_float4(va.hi, va.lo, vb.hi, vb.lo);   // S(y), S(y + h)
+        } else if (jj < h) {
+            const dfl sp = df_addq(va, vb), sm = df_addq(va, {-vb.hi, -vb.lo});
+            sc4[jj] = make_float4(sp.hi, sp.lo, sm.hi, sm.lo);
+        }
+    }
+    __syncthreads();
+    rh = rl = ih = il = 0.f;
+    if (p < J) {
+        const float4 s0 = sc4[0];
+        const dfl r0 = df_addq({s0.x, s0.y}, (p & 1) ? dfl{-s0.z, -s0.w} : dfl{s0.z, s0.w});
+        rh = r0.hi;
+        rl = r0.lo;
+        int q = p;
+        for (int jj = 1; jj < h; ++jj) {
+            const float4 e = ph4[q];     // one 16-byte gather: cos and sin
+            const float4 v = sc4[jj];    // one 16-byte broadcast: both sinc sums
+            df_mac(rh, rl, {e.x, e.y}, {v.x, v.y});
+            df_mac(ih, il, {e.z, e.w}, {v.z, v.w});
+            q += p;
+            if (q >= M) q -= M;
+            if ((jj & 31) == 31) {   // renormalise the accumulators
+                float tr = rh + rl; rl = rl - (tr - rh); rh = tr;
+                float ti = ih + il; il = il - (ti - ih); ih = ti;
+            }
+        }
+    }
+}
+
+// The sampled near sums: one CTA per row g (y_g = g / 2) and 256 columns p.
+// Even rows: D_p(n) = e^{-2 pi i n p / M} for -h <= n < h, else 0 (sinc(n - m)
+// vanishes off m = n); odd rows: the direct sum, sin(pi g / 2) = +-1.
+__global__ void __launch_bounds__(256) sinc_table_kernel(int J, int M, int G,
+                                                         const float4 *__restrict__ ph_g,
+                                                         float4 *__restrict__ tab) {
+    extern __shared__ __align__(16) float4 sm4[];
+    float4 *ph4 = sm4;        // M phases
+    float4 *sc4 = sm4 + M;    // h + 1 sinc sums
+    const int g = (int)blockIdx.x - G;
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    const int h = M / 2;
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if ((g & 1) == 0) {       // the same branch in the whole CTA
+        const int n = g / 2;
+        if (p < J && n >= -h && n < h) out = ph_g[(long long)(n + M) * p % M];
+    } else {
+        for (int q = threadIdx.x; q < M; q += blockDim.x) ph4[q] = ph_g[q];
+        const double sy = (g & 3) == 1 ? 1.0 : -1.0;   // sin(pi g / 2)
+        float rh, rl, ih, il;
+        near_sum(0.5 * (double)g, df_split(sy / kPi), h, M, p, J, ph4, sc4, rh, rl, ih, il);
+        const float tr = rh + rl, ti = ih + il;
+        out = make_float4(tr, rl - (tr - rh), ti, il - (ti - ih));
+    }
+    if (p < J) tab[(long long)blockIdx.x * J + p] = out;
+}
+
 // One CTA per time t, thread p.  The per-window quantities that do not depend
 // on p (y, near or far, sin(pi y), the far ratio h/y and its truncation R)
-// are formed once per CTA.  Near windows: the sinc row uses
-// sin(pi (y - j)) = (-1)^j sin(pi y) and the M-term sums run in double-float;
-// far windows: Horner in double-float over the double-float copy of nu.
+// are formed once per CTA.  Near windows: with the sampled table, 42 samples
+// around y weighted by sinc(2u) E(u) (weights formed once per window, FP64,
+// then split); without it, the direct M-term sums (near_sum).  Far windows:
+// Horner in double-float over the double-float copy of nu.
 __global__ void __launch_bounds__(256) weights_kernel(
     int J, int M, double W, int K, const double *__restrict__ s, const double2 *__restrict__ B,
     const float4 *__restrict__ Bf, const float4 *__restrict__ nu_f, const float4 *__restrict__ ph_g,
-    const double *__restrict__ T, int n_T, double *__restrict__ Gr, double *__restrict__ Gm,
-    float2 *__restrict__ Gs, int pitch_T) {
+    const float4 *__restrict__ tab, int G, const double *__restrict__ T, int n_T,
+    double *__restrict__ Gr, double *__restrict__ Gm, float2 *__restrict__ Gs, int pitch_T) {
     extern __shared__ __align__(16) double smd[];
+    __shared__ float2 swt[kSincPts];                          // interpolation weights, double-float
     double *wy = smd;                                        // K: y
     double *wf = wy + K;                                     // K: sin(pi y) (near) or scale sinc(y) (far)
     float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: h / y (far) or 2W/M (near), double-float
@@ -182,7 +272,8 @@ __global__ void __launch_bounds__(256) weights_kernel(
     const int h = M / 2;
     const double tt = T[t];
     const double scale = 2.0 * W / (double)M;
-    for (int q = threadIdx.x; q < M; q += blockDim.x) ph4[q] = ph_g[q];
+    if (!tab)   // phases for the direct near sums
+        for (int q = threadIdx.x; q < M; q += blockDim.x) ph4[q] = ph_g[q];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const double y = W * (tt - s[k]) / kPi;
         const double sy = sinpi(y);
@@ -211,58 +302,42 @@ __global__ void __launch_bounds__(256) weights_kernel(
     for (int k = 0; k < K; ++k) {
         const int R = wR[k] & 0xffff, R1 = wR[k] >> 16;
         dfl dr = {0.f, 0.f}, di = {0.f, 0.f};
-        if (R == 0) {                 // near window (the same branch in the whole CTA)
-            // D_p = (2W/M) [S(y) + (-1)^p S(y+h) + sum_{j=1}^{h-1} (cos_j (S(y-j) + S(y+j))
-            //        + i sin_j (S(y-j) - S(y+j)))], S(v) = sinc(v), (cos_j, sin_j) the phase
-            //        e^{-2 pi i j p / M} (its conjugate pairs -j with j)
+        if (R == 0 && tab) {          // near window, sampled (the same branch in the whole CTA)
             const double y = wy[k];
-            const dfl sypi = df_split(wf[k] * (1.0 / kPi));   // sin(pi y) / pi
-            __syncthreads();
-            for (int jj = threadIdx.x; jj < h + 1; jj += blockDim.x) {
-                // jj = 0: S(y) and S(y + h) into slot 0; jj >= 1: S(y - jj) +- S(y + jj)
-                const int ja = jj == 0 ? 0 : jj, jb = jj == 0 ? h : jj;
-                dfl va, vb;
-                {
-                    const double d = y - (double)ja;
-                    if (d == 0.0) va = {1.f, 0.f};
-                    else {
-                        va = df_mulq(sypi, df_rcpq(df_split(d)));
-                        if (ja & 1) va = {-va.hi, -va.lo};
-                    }
+            const int g0 = (int)floor(2.0 * y) - (kSincPts / 2 - 1);
+            __syncthreads();          // previous window's weights read
+            if (threadIdx.x < kSincPts) {
+                const int g = g0 + (int)threadIdx.x;
+                const double u = y - 0.5 * (double)g;
+                double w = 1.0;
+                if (u != 0.0) {   // sinc(2u) E(u), sin(2 pi u) = (-1)^g sin(2 pi y)
+                    const double z = u * (1.0 / kSincU);
+                    const double e = fabs(z) < 1.0 ? exp(kSincBeta * (sqrt(1.0 - z * z) - 1.0)) : 0.0;
+                    const double s2 = sinpi(2.0 * y);
+                    w = ((g & 1) ? -s2 : s2) * e / (2.0 * kPi * u);
                 }
-                {
-                    const double d = y + (double)jb;
-                    if (d == 0.0) vb = {1.f, 0.f};
-                    else {
-                        vb = df_mulq(sypi, df_rcpq(df_split(d)));
-                        if (jb & 1) vb = {-vb.hi, -vb.lo};
-                    }
-                }
-                if (jj == 0) {
-                    sc4[0] = make_float4(va.hi, va.lo, vb.hi, vb.lo);   // S(y), S(y + h)
-                } else if (jj < h) {
-                    const dfl sp = df_addq(va, vb), sm = df_addq(va, {-vb.hi, -vb.lo});
-                    sc4[jj] = make_float4(sp.hi, sp.lo, sm.hi, sm.lo);
-                }
+                const dfl wd = df_split(w);
+                swt[threadIdx.x] = make_float2(wd.hi, wd.lo);
             }
             __syncthreads();
             if (p < J) {
-                const float4 s0 = sc4[0];
-                const dfl r0 = df_addq({s0.x, s0.y}, (p & 1) ? dfl{-s0.z, -s0.w} : dfl{s0.z, s0.w});
-                float rh = r0.hi, rl = r0.lo, ih = 0.f, il = 0.f;
-                int q = p;
-                for (int jj = 1; jj < h; ++jj) {
-                    const float4 e = ph4[q];     // one 16-byte gather: cos and sin
-                    const float4 v = sc4[jj];    // one 16-byte broadcast: both sinc sums
-                    df_mac(rh, rl, {e.x, e.y}, {v.x, v.y});
-                    df_mac(ih, il, {e.z, e.w}, {v.z, v.w});
-                    q += p;
-                    if (q >= M) q -= M;
-                    if ((jj & 31) == 31) {   // renormalise the accumulators
-                        float tr = rh + rl; rl = rl - (tr - rh); rh = tr;
-                        float ti = ih + il; il = il - (ti - ih); ih = ti;
-                    }
+                const float4 *col = tab + (long long)(g0 + G) * J + p;
+                float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll 6
+                for (int i = 0; i < kSincPts; ++i) {
+                    const float4 v = col[(long long)i * J];
+                    const float2 w = swt[i];
+                    df_mac(rh, rl, {w.x, w.y}, {v.x, v.y});
+                    df_mac(ih, il, {w.x, w.y}, {v.z, v.w});
                 }
+                const float2 sd = wrho[k];   // 2W/M
+                dr = df_mulq({rh, rl}, {sd.x, sd.y});
+                di = df_mulq({ih, il}, {sd.x, sd.y});
+            }
+        } else if (R == 0) {          // near window, direct sums
+            float rh, rl, ih, il;
+            near_sum(wy[k], df_split(wf[k] * (1.0 / kPi)), h, M, p, J, ph4, sc4, rh, rl, ih, il);
+            if (p < J) {
                 const float2 sd = wrho[k];   // 2W/M
                 dr = df_mulq({rh, rl}, {sd.x, sd.y});
                 di = df_mulq({ih, il}, {sd.x, sd.y});
@@ -525,12 +600,26 @@ void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, float
     far_table_kernel<<<J, 192, 0, st>>>(J, M, pw, nu, nu_f, phase_tab);
 }
 
+void launch_sinc_table(int J, int M, const float4 *phase_tab, float4 *tab, cudaStream_t st) {
+    const int G = sinc_tab_half(J);
+    if (!G) return;
+    const size_t smem = (size_t)(M + M / 2 + 1) * sizeof(float4);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(sinc_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr_set = true;
+    }
+    sinc_table_kernel<<<dim3(2 * G + 1, (J + 255) / 256), 256, smem, st>>>(J, M, G, phase_tab, tab);
+}
+
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
-                          float4 *Bf, const float4 *nu_f, const float4 *phase_tab, const double *T,
-                          int n_T, double *Gr, double *Gm, float2 *Gs, cudaStream_t st) {
+                          float4 *Bf, const float4 *nu_f, const float4 *phase_tab,
+                          const float4 *sinc_tab, const double *T, int n_T, double *Gr, double *Gm,
+                          float2 *Gs, cudaStream_t st) {
     if (n_T <= 0) return;
     const size_t smem = (size_t)K * (2 * sizeof(double) + 2 * sizeof(float2)) +
-                        (size_t)((K + 3) & ~3) * sizeof(int) + (size_t)(M + M / 2) * sizeof(float4);
+                        (size_t)((K + 3) & ~3) * sizeof(int) +
+                        (sinc_tab ? 0 : (size_t)(M + M / 2) * sizeof(float4));
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -541,7 +630,8 @@ void launch_synth_weights(int J, int M, double W, int K, const double *s, const 
         split_df_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, Bf, n);
     }
     dim3 grid(n_T, (J + 255) / 256);
-    weights_kernel<<<grid, 256, smem, st>>>(J, M, W, K, s, B, Bf, nu_f, phase_tab, T, n_T, Gr, Gm, Gs,
+    weights_kernel<<<grid, 256, smem, st>>>(J, M, W, K, s, B, Bf, nu_f, phase_tab, sinc_tab,
+                                            sinc_tab ? sinc_tab_half(J) : 0, T, n_T, Gr, Gm, Gs,
                                             synth_pitch(n_T));
 }
 
