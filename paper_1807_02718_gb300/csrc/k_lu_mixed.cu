@@ -5,10 +5,14 @@
 // The CFIE matrices are well conditioned (second-kind equation), so each
 // refinement sweep contracts the error by ~ cond * N * 2^-24; two or three
 // sweeps bring the FP32 solution to the accuracy of the residual.  Refinement
-// stops when the correction is below tol * ||x||_inf (max-norms), or when it
-// has stopped contracting (no better than half the previous one) below
-// kStallTol * ||x||_inf, the level set by the residual's own rounding; it
-// fails with FH_ENOCONV after max_iters sweeps.
+// stops when the correction is below tol * ||x||_inf (max-norms); when the
+// corrections contract steadily (ratio rho = ||d_k|| / ||d_(k-1)|| <= 1/2),
+// the error left after adding d_k is about ||d_k|| rho / (1 - rho), and the
+// sweep that would only confirm it is skipped once that estimate is below
+// kEstTol * ||x||_inf; when the correction has stopped contracting (no better
+// than half the previous one) below kStallTol * ||x||_inf, the level set by
+// the residual's own rounding, it stops too.  It fails with FH_ENOCONV after
+// max_iters sweeps.
 //
 // Kernels (largest systems first):
 //   lu_factor_fp32_kernel  blocked right-looking LU (panel width 32) of the
@@ -490,10 +494,19 @@ struct RefineState {
 // A correction that has stopped contracting is rounding noise of the residual;
 // it is accepted as converged below this fraction of ||x||.
 constexpr double kStallTol = 1e-10;
+// Steady contraction: converged once the estimated remaining error is below
+// this fraction of ||x|| (two orders below the correction tolerance, at the
+// rounding level of the double-float residual).
+constexpr double kEstTol = 1e-14;
 
 __device__ __forceinline__ bool refine_done(const RefineState &r, double tol) {
     if (!(r.dmax > tol * r.xmax) || r.rbits == 0ull) return true;
-    return r.dprev > 0.0 && r.dmax > 0.5 * r.dprev && r.dmax <= kStallTol * r.xmax;
+    if (!(r.dprev > 0.0)) return false;
+    if (r.dmax <= 0.5 * r.dprev) {
+        const double rho = r.dmax / r.dprev;
+        return r.dmax * rho <= kEstTol * (1.0 - rho) * r.xmax;
+    }
+    return r.dmax <= kStallTol * r.xmax;
 }
 
 // x = 0, y = P g (FP32), ||g||.
