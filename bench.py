@@ -153,7 +153,8 @@ MEASURED_TRAFFIC = {"field_partial_df_kernel": 2.27e6, "lu_factor_tc_kernel": 38
 def window_work(wl):
     """FP64-equivalent flops of the synthesis weights per step: near (t, k):
     4 J x 42 (interpolation from the sampled near sums, J <= 1025) or 4 J h
-    (direct paired sinc sums); far (t, k): 4 J R (Horner); every (t, k): 8 J
+    (direct paired sinc sums); far (t, k): 4 J R (Horner in the Chebyshev
+    ratio); every (t, k): 8 J
     (the B_k accumulation).  R and near/far as in the kernel."""
     J = wl.J
     M = 2 * (J - 1)
@@ -164,8 +165,9 @@ def window_work(wl):
     s_k = s_k[s_k - wl.H < span]
     y = W * (wl.T[:, None] - s_k[None, :]) / np.pi
     near = np.abs(y) < 1.25 * h
-    with np.errstate(divide="ignore"):
-        R = np.clip(np.ceil(-48 * np.log(2) / np.log(np.abs(h / np.where(near, 1.0, y)))), 1, 170)
+    a = np.abs(np.where(near, 2.0 * h, y)) / h
+    rho = 1.0 / (a + np.sqrt((a - 1.0) * (a + 1.0)))     # Chebyshev ratio of the far expansion
+    R = np.clip(np.ceil(-48 * np.log(2) / np.log(rho)), 1, 64)
     per_near = 4 * J * (SINC_POINTS if J <= SINC_TAB_MAX_J else h)
     return float(np.sum(np.where(near, per_near, 4 * J * R)) + 8 * J * y.size)
 

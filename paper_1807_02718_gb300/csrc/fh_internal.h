@@ -150,10 +150,11 @@ void launch_bessel_eval(const double *x, int n, double *out, cudaStream_t st);
 void launch_bessel_eval_df(const double *x, int n, double *out, cudaStream_t st);
 
 // ---- synthesis (k_synth.cu) ----
-// nu[r * J + p] = sum_{m=-h}^{h-1} (-1)^m (m/h)^r e^{-2 pi i m p / M} (nu may
-// be null), and nu_f the same as double-float pairs (re hi, re lo, im hi,
-// im lo); pw is scratch of M * kFarTerms doubles.
-constexpr int kFarTerms = 170;
+// nu[r * J + p] = sum_{m=-h}^{h-1} (-1)^m T_r(m/h) e^{-2 pi i m p / M} (T_r
+// the Chebyshev polynomials, the r = 0 row halved; nu may be null), and nu_f
+// the same as double-float pairs (re hi, re lo, im hi, im lo); pw is scratch
+// of M * kFarTerms doubles.  Far windows (|y| >= 1.25 h) need at most 48 terms.
+constexpr int kFarTerms = 64;
 void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, float4 *phase_tab,
                       cudaStream_t st);
 // Gr/Gm: planes [p][t] with u(x,t) = sum_p Vr[p][x] Gr[p][t] + Vi[p][x] Gm[p][t].

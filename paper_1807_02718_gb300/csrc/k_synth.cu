@@ -15,39 +15,48 @@
 // the targets (the O(1)-in-T part); the contraction over p is a real GEMM
 // u = [Vr | Vi] [Gr ; -Gi] with inner dimension 2J.
 //
-// D_p for windows far from t (|y| >= 1.25 h, y = W tau/pi) uses the convergent
-// expansion 1/(y - m) = (1/y) sum_r (m/y)^r:
-//   D_p = (2W/M) sin(pi y)/(pi y) sum_r (h/y)^r nu_{p,r},
-//   nu_{p,r} = sum_m (-1)^m (m/h)^r e^{-2 pi i m p / M},
-// truncated once (h/|y|)^r < 2^-48 and summed by Horner's rule in
-// double-float arithmetic, except the terms past R1 with (h/|y|)^R1 <=
-// 2^-25 / R, which Horner's rule takes in FP32 first (their relative error
-// ~R 2^-24 enters scaled by (h/|y|)^R1, the size of the truncation error);
-// near windows sum the M terms directly (double-float accumulation).
+// D_p for windows far from t (|y| >= 1.25 h, y = W tau/pi) uses the Chebyshev
+// expansion of 1/(y - m) in x = m/h on [-1, 1]: with a = y/h,
+// s = sign(a) sqrt(a^2 - 1) and rho = 1/(a + s) (|rho| <= 1/2 for |a| >= 1.25),
+//   1/(a - x) = (2/s) [1/2 + sum_{r>=1} rho^r T_r(x)]
+// (the generating function of the Chebyshev polynomials), so that
+//   D_p = (2W/M) (sin(pi y)/pi) (2/(h s)) sum_r rho^r nu_{p,r},
+//   nu_{p,r} = sum_m (-1)^m T_r(m/h) e^{-2 pi i m p / M}  (r = 0 halved),
+// truncated once |rho|^r < 2^-48 (|nu_{p,r}| <= M) and summed by Horner's
+// rule in double-float arithmetic, except the terms past R1 with
+// |rho|^R1 <= 2^-25 / R, which Horner's rule takes in FP32 first (their
+// relative error ~R 2^-24 enters scaled by |rho|^R1, the size of the
+// truncation error).  Its ratio |rho| is below the Taylor ratio h/|y| (0.5
+// against 0.8 at |y| = 1.25 h), hence fewer terms.  Near windows interpolate a
+// table of the direct sums or sum the M terms directly.
 #include "fh_internal.h"
 
 namespace fh {
 namespace {
 
-// nu_{p,r} as a contraction: pw[m + h][r] = (m/h)^r (successive products,
-// one thread per m), then one CTA per p stages the phases
-// e^{-2 pi i m p / M} (-1)^m of a chunk of m in shared memory and thread r
-// accumulates sum_m phase_m pw[m + h][r].
+// nu_{p,r} as a contraction: pw[m + h][r] = T_r(m/h) (three-term recurrence
+// T_{r+1} = 2x T_r - T_{r-1}, stable on [-1, 1]; T_0 halved; one thread per
+// m), then one CTA per p stages the phases e^{-2 pi i m p / M} (-1)^m of a
+// chunk of m in shared memory and thread r accumulates
+// sum_m phase_m pw[m + h][r].
 __global__ void far_powers_kernel(int M, double *__restrict__ pw) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= M) return;
     const int h = M / 2;
     const double xv = (double)(q - h) / (double)h;
-    double v = 1.0;
-    for (int r = 0; r < kFarTerms; ++r) {
-        pw[(long long)q * kFarTerms + r] = v;
-        v *= xv;
+    double t0 = 1.0, t1 = xv;
+    pw[(long long)q * kFarTerms] = 0.5;
+    for (int r = 1; r < kFarTerms; ++r) {
+        pw[(long long)q * kFarTerms + r] = t1;
+        const double t2 = 2.0 * xv * t1 - t0;
+        t0 = t1;
+        t1 = t2;
     }
 }
 
 constexpr int kFarChunk = 128;
 
-__global__ void __launch_bounds__(192) far_table_kernel(int J, int M, const double *__restrict__ pw,
+__global__ void __launch_bounds__(128) far_table_kernel(int J, int M, const double *__restrict__ pw,
                                                        double2 *__restrict__ nu, float4 *__restrict__ nu_f,
                                                        float4 *__restrict__ ph) {
     const int p = blockIdx.x;
@@ -167,9 +176,7 @@ __device__ __forceinline__ void df_horner(float &ah, float &al, dfl r, float vh,
 // S(v) = sinc(v), (cos_j, sin_j) the phase e^{-2 pi i j p / M} (its conjugate
 // pairs -j with j).  The sinc row uses sin(pi (y - j)) = (-1)^j sin(pi y);
 // sypi = sin(pi y) / pi.  ph4: M phases (shared), sc4: h + 1 float4 (shared).
-__device__ void near_sum(double y, dfl sypi, int h, int M, int p, int J, const float4 *ph4,
-                         float4 *sc4, float &rh, float &rl, float &ih, float &il) {
-    __syncthreads();
+__device__ void stage_sinc_row(double y, dfl sypi, int h, float4 *sc4) {
     for (int jj = threadIdx.x; jj < h + 1; jj += blockDim.x) {
         // jj = 0: S(y) and S(y + h) into slot 0; jj >= 1: S(y - jj) +- S(y + jj)
         const int ja = jj == 0 ? 0 : jj, jb = jj == 0 ? h : jj;
@@ -197,6 +204,12 @@ __device__ void near_sum(double y, dfl sypi, int h, int M, int p, int J, const f
             sc4[jj] = make_float4(sp.hi, sp.lo, sm.hi, sm.lo);
         }
     }
+}
+
+__device__ void near_sum(double y, dfl sypi, int h, int M, int p, int J, const float4 *ph4,
+                         float4 *sc4, float &rh, float &rl, float &ih, float &il) {
+    __syncthreads();
+    stage_sinc_row(y, sypi, h, sc4);
     __syncthreads();
     rh = rl = ih = il = 0.f;
     if (p < J) {
@@ -220,31 +233,89 @@ __device__ void near_sum(double y, dfl sypi, int h, int M, int p, int J, const f
     }
 }
 
-// The sampled near sums: one CTA per row g (y_g = g / 2) and 256 columns p.
-// Even rows: D_p(n) = e^{-2 pi i n p / M} for -h <= n < h, else 0 (sinc(n - m)
-// vanishes off m = n); odd rows: the direct sum, sin(pi g / 2) = +-1.
-__global__ void __launch_bounds__(256) sinc_table_kernel(int J, int M, int G,
-                                                         const float4 *__restrict__ ph_g,
-                                                         float4 *__restrict__ tab) {
+// The sampled near sums.  Odd rows (direct sums, sin(pi g / 2) = +-1): one
+// CTA per kTabRows consecutive odd rows and kTabThreads columns p, so that
+// each phase gathered from shared memory serves kTabRows rows.  Even rows:
+// D_p(n) = e^{-2 pi i n p / M} for -h <= n < h, else 0 (sinc(n - m) vanishes
+// off m = n), written by the CTAs past the odd ones (grid-stride, blockIdx.y
+// 0 only).
+constexpr int kTabRows = 4;
+constexpr int kTabThreads = 128;
+
+__global__ void __launch_bounds__(kTabThreads) sinc_table_kernel(int J, int M, int G, int odd_ctas,
+                                                                 const float4 *__restrict__ ph_g,
+                                                                 float4 *__restrict__ tab) {
+    const int h = M / 2;
+    if ((int)blockIdx.x >= odd_ctas) {
+        if (blockIdx.y != 0) return;
+        const int e_first = (G & 1) ? 1 - G : -G;           // first even row
+        const long long n_even = (long long)((G - e_first) / 2 + 1) * J;
+        const int nb = gridDim.x - odd_ctas;
+        for (long long idx = (long long)(blockIdx.x - odd_ctas) * blockDim.x + threadIdx.x; idx < n_even;
+             idx += (long long)nb * blockDim.x) {
+            const int pp = (int)(idx % J);
+            const int g = e_first + 2 * (int)(idx / J);
+            const int n = g / 2;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (n >= -h && n < h) v = ph_g[(long long)(n + M) * pp % M];
+            tab[(long long)(g + G) * J + pp] = v;
+        }
+        return;
+    }
     extern __shared__ __align__(16) float4 sm4[];
     float4 *ph4 = sm4;        // M phases
-    float4 *sc4 = sm4 + M;    // h + 1 sinc sums
-    const int g = (int)blockIdx.x - G;
-    const int p = blockIdx.y * blockDim.x + threadIdx.x;
-    const int h = M / 2;
-    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-    if ((g & 1) == 0) {       // the same branch in the whole CTA
-        const int n = g / 2;
-        if (p < J && n >= -h && n < h) out = ph_g[(long long)(n + M) * p % M];
-    } else {
-        for (int q = threadIdx.x; q < M; q += blockDim.x) ph4[q] = ph_g[q];
-        const double sy = (g & 3) == 1 ? 1.0 : -1.0;   // sin(pi g / 2)
-        float rh, rl, ih, il;
-        near_sum(0.5 * (double)g, df_split(sy / kPi), h, M, p, J, ph4, sc4, rh, rl, ih, il);
-        const float tr = rh + rl, ti = ih + il;
-        out = make_float4(tr, rl - (tr - rh), ti, il - (ti - ih));
+    float4 *sc4 = sm4 + M;    // kTabRows rows of h sinc sums
+    const int o_first = (G & 1) ? -G : 1 - G;            // first odd row
+    const int g0 = o_first + 2 * kTabRows * (int)blockIdx.x;
+    const int p = blockIdx.y * kTabThreads + threadIdx.x;
+    for (int q = threadIdx.x; q < M; q += blockDim.x) ph4[q] = ph_g[q];
+#pragma unroll 1
+    for (int r = 0; r < kTabRows; ++r) {
+        const int g = g0 + 2 * r;
+        if (g <= G) {
+            const double sy = (g & 3) == 1 ? 1.0 : -1.0;   // sin(pi g / 2)
+            stage_sinc_row(0.5 * (double)g, df_split(sy / kPi), h, sc4 + r * h);
+        } else {
+            for (int jj = threadIdx.x; jj < h; jj += blockDim.x) sc4[r * h + jj] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
-    if (p < J) tab[(long long)blockIdx.x * J + p] = out;
+    __syncthreads();
+    if (p >= J) return;
+    float ac[kTabRows][4];
+#pragma unroll
+    for (int r = 0; r < kTabRows; ++r) {
+        const float4 s0 = sc4[r * h];
+        const dfl r0 = df_addq({s0.x, s0.y}, (p & 1) ? dfl{-s0.z, -s0.w} : dfl{s0.z, s0.w});
+        ac[r][0] = r0.hi;
+        ac[r][1] = r0.lo;
+        ac[r][2] = ac[r][3] = 0.f;
+    }
+    int q = p;
+    for (int jj = 1; jj < h; ++jj) {
+        const float4 e = ph4[q];
+#pragma unroll
+        for (int r = 0; r < kTabRows; ++r) {
+            const float4 v = sc4[r * h + jj];
+            df_mac(ac[r][0], ac[r][1], {e.x, e.y}, {v.x, v.y});
+            df_mac(ac[r][2], ac[r][3], {e.z, e.w}, {v.z, v.w});
+        }
+        q += p;
+        if (q >= M) q -= M;
+        if ((jj & 31) == 31) {   // renormalise the accumulators
+#pragma unroll
+            for (int r = 0; r < kTabRows; ++r) {
+                float t0 = ac[r][0] + ac[r][1]; ac[r][1] = ac[r][1] - (t0 - ac[r][0]); ac[r][0] = t0;
+                float t1 = ac[r][2] + ac[r][3]; ac[r][3] = ac[r][3] - (t1 - ac[r][2]); ac[r][2] = t1;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kTabRows; ++r) {
+        const int g = g0 + 2 * r;
+        if (g > G) break;
+        const float tr = ac[r][0] + ac[r][1], ti = ac[r][2] + ac[r][3];
+        tab[(long long)(g + G) * J + p] = make_float4(tr, ac[r][1] - (tr - ac[r][0]), ti, ac[r][3] - (ti - ac[r][2]));
+    }
 }
 
 // One CTA per time t, thread p.  The per-window quantities that do not depend
@@ -261,9 +332,9 @@ __global__ void __launch_bounds__(256) weights_kernel(
     extern __shared__ __align__(16) double smd[];
     __shared__ float2 swt[kSincPts];                          // interpolation weights, double-float
     double *wy = smd;                                        // K: y
-    double *wf = wy + K;                                     // K: sin(pi y) (near) or scale sinc(y) (far)
-    float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: h / y (far) or 2W/M (near), double-float
-    float2 *wfd = wrho + K;                                  // K: scale sinc(y) (far), double-float
+    double *wf = wy + K;                                     // K: sin(pi y) (near) or the far prefactor
+    float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: rho (far) or 2W/M (near), double-float
+    float2 *wfd = wrho + K;                                  // K: far prefactor, double-float
     int *wR = reinterpret_cast<int *>(wfd + K);              // K: far terms R | R1 << 16, 0 = near
     float4 *ph4 = reinterpret_cast<float4 *>(wR + ((K + 3) & ~3));   // M: (cos hi, lo, sin hi, lo)
     float4 *sc4 = ph4 + M;   // h: [0] = (S(y), S(y+h)), [j] = (S(y-j) + S(y+j), S(y-j) - S(y+j))
@@ -284,14 +355,16 @@ __global__ void __launch_bounds__(256) weights_kernel(
             const dfl sd = df_split(scale);
             wrho[k] = make_float2(sd.hi, sd.lo);
         } else {
-            const double rho = (double)h / y;
+            const double a = y / (double)h;
+            const double sq = copysign(sqrt((a - 1.0) * (a + 1.0)), a);
+            const double rho = 1.0 / (a + sq);
             const double lr = -log(fabs(rho));
             const int R = max(1, min((int)ceil(48.0 * 0.69314718055994531 / lr), kFarTerms));
             const int R1 = max(1, min((int)ceil((25.0 * 0.69314718055994531 + log((double)R)) / lr), R));
             wR[k] = R | (R1 << 16);
             const dfl rr = df_split(rho);
             wrho[k] = make_float2(rr.hi, rr.lo);
-            wf[k] = scale * sy / (kPi * y);
+            wf[k] = scale * sy * 2.0 / (kPi * (double)h * sq);
             const dfl fd = df_split(wf[k]);
             wfd[k] = make_float2(fd.hi, fd.lo);
         }
@@ -597,19 +670,22 @@ __global__ void __launch_bounds__(256) contract_df_kernel(int J, int n_x, int n_
 void launch_far_table(int J, int M, double *pw, double2 *nu, float4 *nu_f, float4 *phase_tab,
                       cudaStream_t st) {
     far_powers_kernel<<<(M + 127) / 128, 128, 0, st>>>(M, pw);
-    far_table_kernel<<<J, 192, 0, st>>>(J, M, pw, nu, nu_f, phase_tab);
+    far_table_kernel<<<J, 128, 0, st>>>(J, M, pw, nu, nu_f, phase_tab);
 }
 
 void launch_sinc_table(int J, int M, const float4 *phase_tab, float4 *tab, cudaStream_t st) {
     const int G = sinc_tab_half(J);
     if (!G) return;
-    const size_t smem = (size_t)(M + M / 2 + 1) * sizeof(float4);
+    const size_t smem = (size_t)(M + kTabRows * (M / 2)) * sizeof(float4);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(sinc_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(sinc_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    sinc_table_kernel<<<dim3(2 * G + 1, (J + 255) / 256), 256, smem, st>>>(J, M, G, phase_tab, tab);
+    const int o_first = (G & 1) ? -G : 1 - G, o_last = (G & 1) ? G : G - 1;
+    const int odd_ctas = ((o_last - o_first) / 2 + 1 + kTabRows - 1) / kTabRows;
+    sinc_table_kernel<<<dim3(odd_ctas + 64, (J + kTabThreads - 1) / kTabThreads), kTabThreads, smem, st>>>(
+        J, M, G, odd_ctas, phase_tab, tab);
 }
 
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
