@@ -168,6 +168,60 @@ __device__ __forceinline__ void df_horner(float &ah, float &al, dfl r, float vh,
     al = err - (ah - s);
 }
 
+__device__ __forceinline__ dfl df_negq(dfl a) { return {-a.hi, -a.lo}; }
+
+// sqrt(a) in double-float (a > 0): s = sqrt(a.hi) in binary32, corrected by
+// (a - s^2) / (2 s) with s^2 exact through the FMA residual.
+__device__ __forceinline__ dfl df_sqrtq(dfl a) {
+    const float s = sqrtf(a.hi);
+    const float r = (fmaf(-s, s, a.hi) + a.lo) / (2.f * s);
+    const float h = s + r;
+    return {h, r - (h - s)};
+}
+
+// e^x in double-float for -88 < x <= 0: x = k ln2 + r with |r| <= ln2 / 2,
+// ln2 = L1 + L2 where L1 holds 16 significant bits (k L1 exact for |k| < 2^8);
+// e^r by its Taylor series at 0, the terms n = 8 .. 13 (below 6e-9 for
+// |r| <= 0.347) in binary32 and the rest in double-float; then e^x = 2^k e^r.
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr float kLn2A = 0.693145751953125f;
+constexpr float kLn2B = (float)(kLn2 - 0.693145751953125);
+constexpr float kLn2C = (float)(kLn2 - 0.693145751953125 - (double)kLn2B);
+// 1/n! for n = 3 .. 7 as double-float pairs (1/0!, 1/1!, 1/2! are exact)
+#define FH_INV_FACT(n, v) \
+    constexpr float kIF##n##h = (float)(v); \
+    constexpr float kIF##n##l = (float)((v) - (double)(float)(v));
+FH_INV_FACT(3, 1.0 / 6.0)
+FH_INV_FACT(4, 1.0 / 24.0)
+FH_INV_FACT(5, 1.0 / 120.0)
+FH_INV_FACT(6, 1.0 / 720.0)
+FH_INV_FACT(7, 1.0 / 5040.0)
+#undef FH_INV_FACT
+
+__device__ __forceinline__ dfl df_expq(dfl x) {
+    const float k = rintf(x.hi * 1.4426950408889634f);
+    // r = x - k ln2: x.hi - k L1 is exact (Sterbenz), k L2 exact as a pair
+    const float kb = k * kLn2B, kbe = fmaf(k, kLn2B, -kb);
+    dfl r = df_addq({x.hi - k * kLn2A, x.lo}, {-kb, -fmaf(k, kLn2C, kbe)});
+    float tail = 1.f / 6227020800.f;   // 1/13!
+    tail = fmaf(tail, r.hi, 1.f / 479001600.f);
+    tail = fmaf(tail, r.hi, 1.f / 39916800.f);
+    tail = fmaf(tail, r.hi, 1.f / 3628800.f);
+    tail = fmaf(tail, r.hi, 1.f / 362880.f);
+    tail = fmaf(tail, r.hi, 1.f / 40320.f);
+    dfl q = {tail, 0.f};
+    q = df_addq(df_mulq(q, r), {kIF7h, kIF7l});
+    q = df_addq(df_mulq(q, r), {kIF6h, kIF6l});
+    q = df_addq(df_mulq(q, r), {kIF5h, kIF5l});
+    q = df_addq(df_mulq(q, r), {kIF4h, kIF4l});
+    q = df_addq(df_mulq(q, r), {kIF3h, kIF3l});
+    q = df_addq(df_mulq(q, r), {0.5f, 0.f});
+    q = df_addq(df_mulq(q, r), {1.f, 0.f});
+    q = df_addq(df_mulq(q, r), {1.f, 0.f});
+    const int ki = (int)k;
+    return {ldexpf(q.hi, ki), ldexpf(q.lo, ki)};
+}
+
 // Direct near-window sum, unscaled, for the thread's p (all threads of the CTA
 // call it; it begins and ends with a barrier):
 //   (rh + rl) + i (ih + il) = sum_{m=-h}^{h-1} e^{-2 pi i m p / M} sinc(y - m)
@@ -318,6 +372,19 @@ __global__ void __launch_bounds__(kTabThreads) sinc_table_kernel(int J, int M, i
     }
 }
 
+// Bytes of the per-window arrays of weights_kernel (y, sin(pi y) or the far
+// prefactor, three double-float and three int arrays), rounded to 16.
+__host__ __device__ inline size_t weights_smem_head(int K) {
+    return ((size_t)K * (2 * sizeof(double) + 3 * sizeof(float2) + 3 * sizeof(int)) + 15) & ~(size_t)15;
+}
+
+constexpr float kBetaUHi = (float)(kSincBeta / kSincU);
+constexpr float kBetaULo = (float)(kSincBeta / kSincU - (double)kBetaUHi);
+constexpr float k2PiHi = (float)(2.0 * kPi);
+constexpr float k2PiLo = (float)(2.0 * kPi - (double)k2PiHi);
+constexpr float kInv2PiHi = (float)(0.5 / kPi);
+constexpr float kInv2PiLo = (float)(0.5 / kPi - (double)kInv2PiHi);
+
 // One CTA per time t, thread p.  The per-window quantities that do not depend
 // on p (y, near or far, sin(pi y), the far ratio h/y and its truncation R)
 // are formed once per CTA.  Near windows: with the sampled table, 42 samples
@@ -334,9 +401,12 @@ __global__ void __launch_bounds__(256) weights_kernel(
     double *wy = smd;                                        // K: y
     double *wf = wy + K;                                     // K: sin(pi y) (near) or the far prefactor
     float2 *wrho = reinterpret_cast<float2 *>(wf + K);       // K: rho (far) or 2W/M (near), double-float
-    float2 *wfd = wrho + K;                                  // K: far prefactor, double-float
-    int *wR = reinterpret_cast<int *>(wfd + K);              // K: far terms R | R1 << 16, 0 = near
-    float4 *ph4 = reinterpret_cast<float4 *>(wR + ((K + 3) & ~3));   // M: (cos hi, lo, sin hi, lo)
+    float2 *wfd = wrho + K;                                  // K: far prefactor or sin(2 pi y), double-float
+    float2 *wu = wfd + K;                                    // K: u_c = y - g_c / 2 (near, table)
+    int *wR = reinterpret_cast<int *>(wu + K);               // K: far terms R | R1 << 16, 0 = near
+    int *wg = wR + K;                                        // K: first sample row g0 (near, table)
+    int *wgc = wg + K;                                       // K: nearest sample row g_c (near, table)
+    float4 *ph4 = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smd) + weights_smem_head(K));
     float4 *sc4 = ph4 + M;   // h: [0] = (S(y), S(y+h)), [j] = (S(y-j) + S(y+j), S(y-j) - S(y+j))
     const int t = blockIdx.x;
     const int p = blockIdx.y * blockDim.x + threadIdx.x;
@@ -346,21 +416,36 @@ __global__ void __launch_bounds__(256) weights_kernel(
     if (!tab)   // phases for the direct near sums
         for (int q = threadIdx.x; q < M; q += blockDim.x) ph4[q] = ph_g[q];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const double y = W * (tt - s[k]) / kPi;
-        const double sy = sinpi(y);
+        const double y = W * (tt - s[k]) * (1.0 / kPi);
         wy[k] = y;
         if (fabs(y) < 1.25 * (double)h) {
-            wf[k] = sy;
             wR[k] = 0;
             const dfl sd = df_split(scale);
             wrho[k] = make_float2(sd.hi, sd.lo);
+            if (tab) {   // samples g0 .. g0 + 41 around y, sin(2 pi y)
+                // offsets from the nearest sample g_c: u_c = y - g_c / 2 is exact in FP64
+                // (|u_c| <= 1/4), so that sin(2 pi u) / u stays accurate as u -> 0
+                const int gc = (int)rint(2.0 * y);
+                const dfl uc = df_split(y - 0.5 * (double)gc);
+                double sn, cs;
+                sincospi(y, &sn, &cs);
+                const dfl s2 = df_split(2.0 * sn * cs);
+                wg[k] = (int)floor(2.0 * y) - (kSincPts / 2 - 1);
+                wgc[k] = gc;
+                wu[k] = make_float2(uc.hi, uc.lo);
+                wfd[k] = make_float2(s2.hi, s2.lo);
+            } else {
+                wf[k] = sinpi(y);
+            }
         } else {
+            const double sy = sinpi(y);
             const double a = y / (double)h;
             const double sq = copysign(sqrt((a - 1.0) * (a + 1.0)), a);
             const double rho = 1.0 / (a + sq);
-            const double lr = -log(fabs(rho));
-            const int R = max(1, min((int)ceil(48.0 * 0.69314718055994531 / lr), kFarTerms));
-            const int R1 = max(1, min((int)ceil((25.0 * 0.69314718055994531 + log((double)R)) / lr), R));
+            // truncation from binary32 logarithms (a term count, not a value)
+            const float lr = -logf(fabsf((float)rho));
+            const int R = max(1, min((int)ceilf(48.f * 0.693147181f / lr), kFarTerms));
+            const int R1 = max(1, min((int)ceilf((25.f * 0.693147181f + logf((float)R)) / lr), R));
             wR[k] = R | (R1 << 16);
             const dfl rr = df_split(rho);
             wrho[k] = make_float2(rr.hi, rr.lo);
@@ -376,21 +461,27 @@ __global__ void __launch_bounds__(256) weights_kernel(
         const int R = wR[k] & 0xffff, R1 = wR[k] >> 16;
         dfl dr = {0.f, 0.f}, di = {0.f, 0.f};
         if (R == 0 && tab) {          // near window, sampled (the same branch in the whole CTA)
-            const double y = wy[k];
-            const int g0 = (int)floor(2.0 * y) - (kSincPts / 2 - 1);
+            const int g0 = wg[k];
             __syncthreads();          // previous window's weights read
             if (threadIdx.x < kSincPts) {
-                const int g = g0 + (int)threadIdx.x;
-                const double u = y - 0.5 * (double)g;
-                double w = 1.0;
-                if (u != 0.0) {   // sinc(2u) E(u), sin(2 pi u) = (-1)^g sin(2 pi y)
-                    const double z = u * (1.0 / kSincU);
-                    const double e = fabs(z) < 1.0 ? exp(kSincBeta * (sqrt(1.0 - z * z) - 1.0)) : 0.0;
-                    const double s2 = sinpi(2.0 * y);
-                    w = ((g & 1) ? -s2 : s2) * e / (2.0 * kPi * u);
+                // sinc(2u) E(u) at u = y - g/2 = u_c + (g_c - g)/2 in double-float:
+                // sin(2 pi u) = (-1)^g sin(2 pi y), E(u) = exp((beta/U) sqrt(U^2 - u^2) - beta)
+                const int i = (int)threadIdx.x;
+                const float2 uc2 = wu[k];
+                const dfl u = df_addq({uc2.x, uc2.y}, {0.5f * (float)(wgc[k] - g0 - i), 0.f});
+                dfl w = {1.f, 0.f};
+                if (u.hi != 0.f || u.lo != 0.f) {
+                    const dfl w2 = df_addq({(float)(kSincU * kSincU), 0.f}, df_negq(df_mulq(u, u)));
+                    w = {0.f, 0.f};
+                    if (w2.hi > 0.f) {
+                        const dfl arg = df_addq(df_mulq(df_sqrtq(w2), {kBetaUHi, kBetaULo}),
+                                                {(float)-kSincBeta, 0.f});
+                        const float2 s22 = wfd[k];
+                        const dfl s2 = ((g0 + i) & 1) ? dfl{-s22.x, -s22.y} : dfl{s22.x, s22.y};
+                        w = df_mulq(df_mulq(s2, df_expq(arg)), df_rcpq(df_mulq(u, {k2PiHi, k2PiLo})));
+                    }
                 }
-                const dfl wd = df_split(w);
-                swt[threadIdx.x] = make_float2(wd.hi, wd.lo);
+                swt[i] = make_float2(w.hi, w.lo);
             }
             __syncthreads();
             if (p < J) {
@@ -453,17 +544,16 @@ __global__ void __launch_bounds__(256) weights_kernel(
             df_mac(qih, qil, bi, dr);
         }
     }
-    if (p < J) {
-        const double mu = (p == 0 || p == J - 1) ? 1.0 : 2.0;
-        const double c = mu / (2.0 * kPi);
-        const double gr = c * ((double)qrh + (double)qrl), gm = -c * ((double)qih + (double)qil);
+    if (p < J) {   // G = (mu_p / 2 pi) q, mu_p / 2 pi = 1/(2 pi) or 1/pi, in double-float
+        const bool edge = p == 0 || p == J - 1;
+        const dfl c = edge ? dfl{kInv2PiHi, kInv2PiLo} : dfl{2.f * kInv2PiHi, 2.f * kInv2PiLo};
+        const dfl a = df_mulq({qrh, qrl}, c), b = df_negq(df_mulq({qih, qil}, c));
         if (Gs) {
-            const dfl a = df_split(gr), b = df_split(gm);
             Gs[(long long)p * pitch_T + t] = make_float2(a.hi, a.lo);
             Gs[(long long)(J + p) * pitch_T + t] = make_float2(b.hi, b.lo);
         } else {
-            Gr[(long long)p * n_T + t] = gr;
-            Gm[(long long)p * n_T + t] = gm;
+            Gr[(long long)p * n_T + t] = (double)a.hi + (double)a.lo;
+            Gm[(long long)p * n_T + t] = (double)b.hi + (double)b.lo;
         }
     }
 }
@@ -693,9 +783,7 @@ void launch_synth_weights(int J, int M, double W, int K, const double *s, const 
                           const float4 *sinc_tab, const double *T, int n_T, double *Gr, double *Gm,
                           float2 *Gs, cudaStream_t st) {
     if (n_T <= 0) return;
-    const size_t smem = (size_t)K * (2 * sizeof(double) + 2 * sizeof(float2)) +
-                        (size_t)((K + 3) & ~3) * sizeof(int) +
-                        (sinc_tab ? 0 : (size_t)(M + M / 2) * sizeof(float4));
+    const size_t smem = weights_smem_head(K) + (sinc_tab ? 0 : (size_t)(M + M / 2) * sizeof(float4));
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
