@@ -97,6 +97,10 @@ struct fh_ctx {
     int early_groups = 0, early_solves = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // near-diagonal band of the mixed-path assembly: its own (high-priority)
+    // stream, forked and joined around each tile launch
+    cudaStream_t band = nullptr;
+    cudaEvent_t ev_band0 = nullptr, ev_band1 = nullptr;
     // frequency subgroups (one problem, equal N, at most tune.assemble_group
     // solves for the assembly, tune.field_group for the target fields)
     int n_groups = 0;
@@ -158,6 +162,9 @@ struct fh_ctx {
         if (side) cudaStreamDestroy(side);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        if (band) cudaStreamDestroy(band);
+        if (ev_band0) cudaEventDestroy(ev_band0);
+        if (ev_band1) cudaEventDestroy(ev_band1);
         if (own) cudaStreamDestroy(own);
     }
 };
@@ -909,11 +916,16 @@ fh_status fh_create(fh_ctx **out, int device, int precision) {
     fh_ctx *ctx = new fh_ctx();
     ctx->device = device;
     ctx->precision = precision;
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->band, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_band0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_band1, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return FH_ECUDA;
     }
@@ -963,6 +975,10 @@ fh_status fh_num_problems(fh_ctx *ctx, int *P) {
 fh_status assemble_range(fh_ctx *ctx, int g0, int g1, int s0, int s1) {
     const bool mixed = ctx->precision != FH_FP64;
     const long long t0 = ctx->sg_tile_off[g0], t1 = ctx->sg_tile_off[g1];
+    if (mixed) {   // the band kernel runs on the band stream beside the tiles
+        FH_CUDA(ctx, cudaEventRecord(ctx->ev_band0, ctx->stream));
+        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->band, ctx->ev_band0, 0));
+    }
     fh::launch_assemble_groups(tables(ctx), groups(ctx), ctx->n_groups, t0, t1 - t0,
                                ctx->d_order.as<int>() + s0, s1 - s0, ctx->maxN,
                                ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
@@ -970,7 +986,12 @@ fh_status assemble_range(fh_ctx *ctx, int g0, int g1, int s0, int s1) {
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
                                ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(),
                                ctx->d_wpf.as<float2>(), mixed ? nullptr : ctx->d_A.as<double2>(),
-                               mixed ? ctx->d_A.as<float4>() : nullptr, 0, ctx->stream);
+                               mixed ? ctx->d_A.as<float4>() : nullptr, 0, ctx->stream,
+                               mixed ? ctx->band : ctx->stream);
+    if (mixed) {
+        FH_CUDA(ctx, cudaEventRecord(ctx->ev_band1, ctx->band));
+        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_band1, 0));
+    }
     return check_launch(ctx, "assemble");
 }
 
@@ -1317,7 +1338,7 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
                                ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(), ctx->d_wpf.as<float2>(),
                                mixed ? nullptr : ctx->d_tmpA.as<double2>(),
-                               mixed ? ctx->d_tmpA.as<float4>() : nullptr, -base, ctx->stream);
+                               mixed ? ctx->d_tmpA.as<float4>() : nullptr, -base, ctx->stream, ctx->stream);
     FH_TRY(check_launch(ctx, "assemble (single)"));
     fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                    ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),

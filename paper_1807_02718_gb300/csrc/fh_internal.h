@@ -63,14 +63,17 @@ struct Subgroups {
 // Launches the tiles tile_base .. tile_base + n_tiles - 1 of the subgroup
 // table g (n_groups subgroups, tile offsets over the whole table).  Mixed
 // paths (Af): also the near-diagonal band of the band_count solves in the
-// device list band_list (largest N maxN), a second launch.
+// device list band_list (largest N maxN), a second launch, issued first on
+// band_st (which may be st; the two kernels write disjoint entries, so that on
+// another stream the FP64-bound band overlaps the FP32-bound tiles).
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long tile_base, long long n_tiles, const int *band_list,
                             int band_count, int maxN,
                             const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
-                            double2 *A, float4 *Af, long long out_shift, cudaStream_t st);
+                            double2 *A, float4 *Af, long long out_shift, cudaStream_t st,
+                            cudaStream_t band_st);
 // Solve s uses the incidence direction pdir[prob[s]].
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,
                 const int *prob, const double2 *pdir, double2 *g, cudaStream_t st);

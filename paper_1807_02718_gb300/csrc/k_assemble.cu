@@ -363,15 +363,17 @@ void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_grou
                             const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
-                            double2 *A, float4 *Af, long long out_shift, cudaStream_t st) {
+                            double2 *A, float4 *Af, long long out_shift, cudaStream_t st,
+                            cudaStream_t band_st) {
     if (n_tiles <= 0 || n_groups <= 0) return;
     if (Af) {
-        assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, dz, zf, dzf, sf,
-                                                                    wpf, Af, out_shift, tile_base);
         if (band_count > 0) {
             const dim3 grid((maxN * (2 * kNearBand + 1) + 255) / 256, band_count);
-            assemble_band_kernel<<<grid, 256, 0, st>>>(t, band_list, z, dz, ddz, kress, logsin, Af, out_shift);
+            assemble_band_kernel<<<grid, 256, 0, band_st>>>(t, band_list, z, dz, ddz, kress, logsin, Af,
+                                                            out_shift);
         }
+        assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, dz, zf, dzf, sf,
+                                                                    wpf, Af, out_shift, tile_base);
     } else
         assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
                                                                  logsin, A, out_shift, tile_base);
