@@ -8,7 +8,8 @@
 // by the trapezoidal rule on tau_q = -H + q dt (the integrand vanishes at
 // both ends).  Pass 1 forms the windowed samples wa[k][q]; pass 2 gives one
 // CTA per frequency, which stages e^{i omega tau_q} for a chunk of q in
-// shared memory and lets each warp reduce one window's dot product.
+// shared memory once for all windows; each warp reduces the dot products of
+// four windows in FP64.
 #include "fh_internal.h"
 
 namespace fh {
@@ -40,6 +41,11 @@ __global__ void windowed_samples_kernel(const double *__restrict__ a, int n_samp
 
 constexpr int kChunk = 1024;
 
+// One CTA per frequency: for each chunk of 1024 samples the phases
+// e^{i omega tau_q} are formed once, as the product of e^{i omega tau_{q0 + 32a}}
+// (FP64 sincos, 32 per chunk) and e^{i omega dt b} (b < 32, once per CTA);
+// warp w accumulates the FP64 dot products of windows kb + w, kb + w + 8, ...
+// (four per warp, blocks of 32 windows), so that each phase serves every window.
 __global__ void __launch_bounds__(256) spectra_kernel(const double *__restrict__ wa, int Q,
                                                       double dt, double H, int K, int J,
                                                       const double *__restrict__ omega,
@@ -48,33 +54,50 @@ __global__ void __launch_bounds__(256) spectra_kernel(const double *__restrict__
     const double w = omega[j];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ double2 ph[kChunk];
-    for (int kg = 0; kg < K; kg += 8) {
-        const int k = kg + warp;
-        double sr = 0.0, si = 0.0;
+    __shared__ double2 e0[32], e1[kChunk / 32];
+    if (threadIdx.x < 32) {
+        double sn, cs;
+        sincos(w * (dt * (double)threadIdx.x), &sn, &cs);
+        e0[threadIdx.x] = make_double2(cs, sn);
+    }
+    for (int kb = 0; kb < K; kb += 32) {
+        double sr[4] = {0.0, 0.0, 0.0, 0.0}, si[4] = {0.0, 0.0, 0.0, 0.0};
         for (int q0 = 0; q0 <= Q; q0 += kChunk) {
             __syncthreads();
-            for (int e = threadIdx.x; e < kChunk; e += 256) {
-                const int q = q0 + e;
-                double sn = 0.0, cs = 0.0;
-                if (q <= Q) sincos(w * (-H + dt * q), &sn, &cs);
-                ph[e] = make_double2(cs, sn);
+            if (threadIdx.x < kChunk / 32) {
+                double sn, cs;
+                sincos(w * (-H + dt * (double)(q0 + 32 * (int)threadIdx.x)), &sn, &cs);
+                e1[threadIdx.x] = make_double2(cs, sn);
             }
             __syncthreads();
-            if (k < K) {
-                const double *row = wa + (long long)k * (Q + 1);
-                const int qe = min(kChunk, Q + 1 - q0);
+            for (int e = threadIdx.x; e < kChunk; e += 256) {
+                const double2 a = e1[e >> 5], b = e0[e & 31];
+                ph[e] = q0 + e <= Q ? make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x)
+                                    : make_double2(0.0, 0.0);
+            }
+            __syncthreads();
+            const int qe = min(kChunk, Q + 1 - q0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int k = kb + warp + 8 * s;
+                if (k >= K) continue;
+                const double *row = wa + (long long)k * (Q + 1) + q0;
                 for (int e = lane; e < qe; e += 32) {
-                    const double v = row[q0 + e];
-                    sr += v * ph[e].x;
-                    si += v * ph[e].y;
+                    const double v = row[e];
+                    sr[s] += v * ph[e].x;
+                    si[s] += v * ph[e].y;
                 }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_down_sync(0xffffffffu, sr, o);
-            si += __shfl_down_sync(0xffffffffu, si, o);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            for (int o = 16; o > 0; o >>= 1) {
+                sr[s] += __shfl_down_sync(0xffffffffu, sr[s], o);
+                si[s] += __shfl_down_sync(0xffffffffu, si[s], o);
+            }
+            const int k = kb + warp + 8 * s;
+            if (lane == 0 && k < K) B[(long long)k * J + j] = make_double2(dt * sr[s], dt * si[s]);
         }
-        if (lane == 0 && k < K) B[(long long)k * J + j] = make_double2(dt * sr, dt * si);
     }
 }
 
