@@ -762,8 +762,16 @@ fh_status synth_buffers(fh_ctx *ctx, Problem &pb, int n_x, int n_T) {
     return ensure(ctx, ctx->d_Bf, (size_t)pb.K * pb.J * sizeof(float4));
 }
 
-// Weights G_p(t) and the contraction u = Re sum_p V_p G_p (buffers exist).
-fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
+// Runs the enclosed launches on another stream of the context.
+struct OnStream {
+    fh_ctx *ctx;
+    cudaStream_t saved;
+    OnStream(fh_ctx *c, cudaStream_t st) : ctx(c), saved(c->stream) { ctx->stream = st; }
+    ~OnStream() { ctx->stream = saved; }
+};
+
+// Weights G_p(t) (buffers exist); contract_kernels: u = Re sum_p V_p G_p.
+fh_status weights_kernels(fh_ctx *ctx, Problem &pb, const double *d_T, int n_T) {
     const bool tcc = use_contract_tc(ctx, pb);
     const bool mixed = ctx->precision != FH_FP64 && !tcc;   // double-float weights and contraction
     {
@@ -776,6 +784,12 @@ fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, in
                                  mixed ? ctx->d_Gs.as<float2>() : nullptr, ctx->stream);
         FH_TRY(check_launch(ctx, "synthesis weights"));
     }
+    return FH_OK;
+}
+
+fh_status contract_kernels(fh_ctx *ctx, Problem &pb, int n_x, int n_T, double *d_u) {
+    const bool tcc = use_contract_tc(ctx, pb);
+    const bool mixed = ctx->precision != FH_FP64 && !tcc;
     PhaseScope ps(ctx, FH_PH_CONTRACT, tcc ? 5 : mixed ? 2 : 1);
     if (tcc) {
         FH_CUDA(ctx, cudaMemsetAsync(ctx->d_ctc_err.p, 0, sizeof(int), ctx->stream));
@@ -793,6 +807,11 @@ fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, in
         fh::launch_synth_contract(pb.J, n_x, n_T, ctx->d_V.as<double2>(), ctx->d_Gr.as<double>(),
                                   ctx->d_Gm.as<double>(), d_u, ctx->stream);
     return check_launch(ctx, "synthesis contraction");
+}
+
+fh_status synth_kernels(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
+    FH_TRY(weights_kernels(ctx, pb, d_T, n_T));
+    return contract_kernels(ctx, pb, n_x, n_T, d_u);
 }
 
 fh_status synth_common(fh_ctx *ctx, Problem &pb, int n_x, const double *d_T, int n_T, double *d_u) {
@@ -823,8 +842,23 @@ fh_status field_buffers(fh_ctx *ctx, const Problem &pb, int n_x) {
 // Target fields, weights and contraction for one problem (buffers exist).
 fh_status sample_kernels(fh_ctx *ctx, Problem &pb, const double *d_x, int n_x, const double *d_T,
                          int n_T, double *d_u) {
+    if (ctx->timing) {   // one sequence, so that the phase times add up
+        FH_TRY(field_kernels(ctx, pb, d_x, n_x));
+        return synth_kernels(ctx, pb, n_x, d_T, n_T, d_u);
+    }
+    // The weights do not depend on the targets: they run on the side stream
+    // beside the target fields (filling the SMs the field grid's last wave
+    // leaves idle); the streams join before the contraction.
+    FH_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    FH_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    {
+        OnStream on(ctx, ctx->side);
+        FH_TRY(weights_kernels(ctx, pb, d_T, n_T));
+    }
     FH_TRY(field_kernels(ctx, pb, d_x, n_x));
-    return synth_kernels(ctx, pb, n_x, d_T, n_T, d_u);
+    FH_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+    FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    return contract_kernels(ctx, pb, n_x, n_T, d_u);
 }
 
 fh_status sample_common(fh_ctx *ctx, int q, const double *d_x, int n_x, const double *d_T,
@@ -1016,14 +1050,6 @@ fh_status tc_factor_kernels(fh_ctx *ctx) {
     FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
     return tc_factor_range(ctx, 0, ctx->S);
 }
-
-// Runs the enclosed launches on another stream of the context.
-struct OnStream {
-    fh_ctx *ctx;
-    cudaStream_t saved;
-    OnStream(fh_ctx *c, cudaStream_t st) : ctx(c), saved(c->stream) { ctx->stream = st; }
-    ~OnStream() { ctx->stream = saved; }
-};
 
 int tc_launches(fh_ctx *ctx, int s0, int s1) {
     return 1 + fh::lu_tc_launches(ctx->order.data() + s0, ctx->solve_N.data(), s1 - s0,
