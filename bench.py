@@ -10,7 +10,8 @@ wavelength (64..480), 1024 targets on r = 3, 4096 times up to T = 1e4):
 
 Headline `value`: frequency solves/s of whole steps with inputs resident in
 HBM (device-pointer entry points).  `e2e`: the same through the host-pointer
-C-ABI calls, host<->device copies included.  Also reported: time samples/s,
+C-ABI calls, host<->device copies (from and to page-locked host buffers)
+included.  Also reported: time samples/s,
 per-step p50/p99 latency, the dominant kernel against its roofline, the
 oracle timed on the host cores, and SM clocks sampled during the timed
 region.  L2 is flushed (256 MiB write) between timed steps.
@@ -406,17 +407,20 @@ def run_gpu(args, world, rank, local):
     step_ms_phases = {n: v["ms"] / reps for n, v in phases.items()}
     dominant = max(step_ms_phases, key=step_ms_phases.get)
 
-    # ---- end to end through the host-pointer API ----
-    u_host = np.empty((n_x, n_T))
+    # ---- end to end through the host-pointer API (inputs and u in page-locked host memory) ----
+    def pinned(arr):
+        return torch.from_numpy(np.ascontiguousarray(arr)).pin_memory().numpy()
+    a_p, x_p, T_p, om_p = pinned(wl.a), pinned(wl.x), pinned(wl.T), pinned(wl.omega)
+    u_host = torch.empty(n_x * n_T, dtype=torch.float64).pin_memory().numpy()
     e2e_times = []
     for k in range(args.steps):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        F.fh_discretize(pr.ctx, wl.curve, wl.omega, wl.N, wl.c, wl.p)
+        F.fh_discretize(pr.ctx, wl.curve, om_p, wl.N, wl.c, wl.p)
         F.fh_solve_frequencies(pr.ctx)
-        F.fh_window_spectra(pr.ctx, wl.a, wl.t0, wl.dt, wl.H)
-        u_host = F.fh_sample(pr.ctx, wl.x, wl.T)
+        F.fh_window_spectra(pr.ctx, a_p, wl.t0, wl.dt, wl.H)
+        F.fh_sample(pr.ctx, x_p, T_p, out=u_host)
         e2e_times.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_times)
     e2e_total = max_over_ranks(e2e_total, world, dev)

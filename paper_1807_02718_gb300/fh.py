@@ -218,10 +218,17 @@ def fh_window_spectra_dev(ctx, d_a, t0: float, dt: float, H: float = 10.0):
                                                      float(dt), float(H)))
 
 
-def fh_sample(ctx, x, T):
+def fh_sample(ctx, x, T, out=None):
+    """u(x, T) into a new array, or into `out` (C-contiguous float64 of n_x * n_T
+    elements, e.g. a view of page-locked host memory for full-speed copies)."""
     xv, Tv = _f64(x), _f64(T)
     n_x, n_T = xv.size // 2, Tv.size
-    u = np.empty((n_x, n_T), dtype=np.float64)
+    if out is None:
+        u = np.empty((n_x, n_T), dtype=np.float64)
+    else:
+        if out.dtype != np.float64 or out.size != n_x * n_T or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous float64 array of n_x * n_T elements")
+        u = out.reshape(n_x, n_T)
     _check(ctx, load_library().fh_sample(ctx, _dp(xv), n_x, _dp(Tv), n_T, _dp(u)))
     return u
 

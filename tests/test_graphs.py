@@ -61,3 +61,22 @@ def test_changed_discretization_after_replays():
     _, u3 = cycle(pr, wl2)           # capture with the new shape
     _, u4 = cycle(pr, wl2)           # replay
     assert np.array_equal(u3, u2) and np.array_equal(u4, u2)
+
+
+def test_sample_into_page_locked_buffer():
+    """The host-pointer sample writing into a caller's page-locked buffer (the
+    bench's end-to-end leg) gives bitwise the array it returns otherwise, on
+    direct launches and on graph replays."""
+    import torch
+    wl = fi.small_kite()
+    pr = F.Problem(0, F.FH_MIXED_TF32)
+    pr.discretize(wl.curve, wl.omega, wl.N, wl.c, wl.p)
+    pr.solve()
+    pr.window_spectra(wl.a, wl.t0, wl.dt, wl.H)
+    ref = F.fh_sample(pr.ctx, wl.x, wl.T)
+    buf = torch.full((ref.size,), float("nan"), dtype=torch.float64).pin_memory().numpy()
+    for _ in range(3):
+        out = F.fh_sample(pr.ctx, wl.x, wl.T, out=buf)
+        assert np.array_equal(out, ref) and np.shares_memory(out, buf)
+    with pytest.raises(ValueError):
+        F.fh_sample(pr.ctx, wl.x, wl.T, out=np.empty(ref.size + 1))
