@@ -93,7 +93,8 @@ struct fh_ctx {
     // schedule parameters (fh_set_tuning, fh_autotune)
     fh_tuning tune{fh::kGroup, fh::kGroup, fh::kFieldChunk, 512, 0, 1};
     // lu_early: the first early_groups assembly subgroups (early_solves solves,
-    // the largest) are assembled and factored on the side stream
+    // the largest) are assembled, factored and refined on the side stream
+    // (high priority, so that their CTAs are dispatched ahead of the rest's)
     int early_groups = 0, early_solves = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -120,6 +121,7 @@ struct fh_ctx {
     DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk, d_Bf, d_dblk,
         d_blk_off, d_dinv;
     int n_rchunk = 0, n_dblk = 0;
+    int n_rchunk_early = 0, n_dblk_early = 0;   // entries of the lu_early systems (listed first)
     DevBuf d_wa, d_a;
     int n_x_last = 0;
     DevBuf d_x, d_T, d_u, d_V, d_Gr, d_Gm, d_Gs, d_Vs, d_ctc, d_ctc_err;
@@ -415,6 +417,32 @@ fh_status build_schedules(fh_ctx *ctx) {
         while (ctx->early_groups < ctx->n_groups && ctx->early_solves < want)
             ctx->early_solves += ctx->sg[ctx->early_groups++].y;
     }
+    {
+        // refinement work lists in factorisation order, so that the lu_early
+        // systems' entries come first: residual chunks (solve, first row) and
+        // diagonal blocks (solve, 32-row block); blk_off[s]: first block of s
+        std::vector<int2> rchunk, dblk;
+        std::vector<int> blk_off(ctx->S);
+        for (int i = 0; i < ctx->S; ++i) {
+            const int s = ctx->order[i];
+            if (i == ctx->early_solves) {
+                ctx->n_rchunk_early = (int)rchunk.size();
+                ctx->n_dblk_early = (int)dblk.size();
+            }
+            for (int r0 = 0; r0 < ctx->solve_N[s]; r0 += fh::kResidRows) rchunk.push_back(make_int2(s, r0));
+            blk_off[s] = (int)dblk.size();
+            for (int b = 0; b * 32 < ctx->solve_N[s]; ++b) dblk.push_back(make_int2(s, b));
+        }
+        if (ctx->early_solves == 0 || ctx->early_solves >= ctx->S) {
+            ctx->n_rchunk_early = ctx->early_solves ? (int)rchunk.size() : 0;
+            ctx->n_dblk_early = ctx->early_solves ? (int)dblk.size() : 0;
+        }
+        ctx->n_rchunk = (int)rchunk.size();
+        ctx->n_dblk = (int)dblk.size();
+        FH_TRY(upload(ctx, ctx->d_rchunk, rchunk));
+        FH_TRY(upload(ctx, ctx->d_dblk, dblk));
+        FH_TRY(upload(ctx, ctx->d_blk_off, blk_off));
+    }
 
     split_groups(ctx, ctx->tune.field_group, ctx->fsg, ctx->fsg_dk, first, end);
     ctx->field_items.clear();
@@ -447,9 +475,8 @@ fh_status build_schedules(fh_ctx *ctx) {
 bool is_fin(double v) { return std::isfinite(v); }
 
 // Mixed precision: refinement stops when ||dx||_inf <= kRefineTol ||x||_inf
-// (or when the corrections stall at the residual's rounding level).
-constexpr int kRefineMaxIters = 12;
-constexpr double kRefineTol = 1e-12;
+// (or when the corrections stall at the residual's rounding level); the
+// constants sit beside refine_range.
 
 fh_status get_problem(fh_ctx *ctx, int problem, Problem **out) {
     if (!ctx->geom) return fail(ctx, FH_ESTATE, "call fh_discretize first");
@@ -608,20 +635,6 @@ fh_status discretize_batch(fh_ctx *ctx, int P, const fh_curve *curves, const int
     ctx->maxN = maxN;
 
 
-    std::vector<int2> rchunk;   // (solve, first row) of each refinement residual chunk
-    for (int s = 0; s < S; ++s)
-        for (int r0 = 0; r0 < ctx->solve_N[s]; r0 += fh::kResidRows) rchunk.push_back(make_int2(s, r0));
-    ctx->n_rchunk = (int)rchunk.size();
-    FH_TRY(upload(ctx, ctx->d_rchunk, rchunk));
-    std::vector<int2> dblk;     // (solve, 32-row block) of each diagonal block
-    std::vector<int> blk_off(S);
-    for (int s = 0; s < S; ++s) {
-        blk_off[s] = (int)dblk.size();
-        for (int b = 0; b * 32 < ctx->solve_N[s]; ++b) dblk.push_back(make_int2(s, b));
-    }
-    ctx->n_dblk = (int)dblk.size();
-    FH_TRY(upload(ctx, ctx->d_dblk, dblk));
-    FH_TRY(upload(ctx, ctx->d_blk_off, blk_off));
 
     std::vector<double> omega_v(omega_all, omega_all + jo);
     FH_TRY(upload(ctx, ctx->d_N, ctx->solve_N));
@@ -954,7 +967,7 @@ fh_status fh_create(fh_ctx **out, int device, int precision) {
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->band, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -1056,14 +1069,46 @@ int tc_launches(fh_ctx *ctx, int s0, int s1) {
                                   ctx->tune.lu_rows_per_cta);
 }
 
+constexpr int kRefineMaxIters = 12;
+constexpr double kRefineTol = 1e-12;
+
+// Refinement of the solves order[i0 .. i1-1]: their residual chunks and
+// diagonal blocks are the list entries [c0, c1) and [b0, b1).
+fh_status refine_range(fh_ctx *ctx, bool tc, int i0, int i1, int c0, int c1, int b0, int b1) {
+    // every buffer the refinement writes is allocated by fh_solve_frequencies first
+    if (!ctx->d_g.p || !ctx->d_psi.p || !ctx->d_y32.p || !ctx->d_rstate.p || !ctx->d_iters.p ||
+        !ctx->d_resid.p || !ctx->d_info.p || (tc && !ctx->d_dinv.p))
+        return fail(ctx, FH_ESTATE, "refinement launched before its buffers exist");
+    PhaseScope ps(ctx, FH_PH_REFINE, (tc ? 1 : 0) + 2 + 2 * kRefineMaxIters);
+    fh::launch_lu_refine(tc, ctx->d_order.as<int>() + i0, i1 - i0, ctx->d_N.as<int>(),
+                         ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
+                         ctx->d_rchunk.as<int2>() + c0, c1 - c0, ctx->d_dblk.as<int2>() + b0, b1 - b0,
+                         ctx->d_blk_off.as<int>(), ctx->d_dinv.as<float2>(), ctx->d_A.as<float4>(),
+                         ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_g.as<double2>(),
+                         ctx->d_psi.as<double2>(), ctx->d_y32.as<float2>(), ctx->d_rstate.p,
+                         kRefineMaxIters, kRefineTol, ctx->d_iters.as<int>(), ctx->d_resid.as<double>(),
+                         ctx->d_info.as<int>(), ctx->maxN, ctx->stream);
+    return check_launch(ctx, "lu mixed");
+}
+
 // Tensor-core path with lu_early: the largest systems (subgroups 0 ..
-// early_groups-1) are assembled and factored on the side stream while the
-// rest is assembled on the context stream; the streams join before the
-// refinement.  d_info and d_tcerr are cleared first.
-fh_status split_front(fh_ctx *ctx) {
+// early_groups-1) are assembled, factored and refined on the side stream
+// while the rest is assembled, factored and refined on the context stream;
+// the streams join at the end.  d_info and d_tcerr are cleared and the right
+// sides formed first.  refine = false (the autotuner's assembly + factorisation
+// timing) leaves out the right sides and the refinement.
+fh_status split_front(fh_ctx *ctx, bool refine) {
     const int gL = ctx->early_groups, SL = ctx->early_solves, S = ctx->S;
     FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)S * sizeof(int), ctx->stream));
     FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
+    if (refine) {
+        if (!ctx->d_g.p) return fail(ctx, FH_ESTATE, "right sides launched before their buffer exists");
+        PhaseScope ps(ctx, FH_PH_ASSEMBLE, 1);
+        fh::launch_rhs(tables(ctx), ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
+                       ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(), ctx->d_g.as<double2>(),
+                       ctx->stream);
+        FH_TRY(check_launch(ctx, "rhs"));
+    }
     FH_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
     FH_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
     {
@@ -1072,8 +1117,11 @@ fh_status split_front(fh_ctx *ctx) {
             PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
             FH_TRY(assemble_range(ctx, 0, gL, 0, SL));
         }
-        PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, 0, SL));
-        FH_TRY(tc_factor_range(ctx, 0, SL));
+        {
+            PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, 0, SL));
+            FH_TRY(tc_factor_range(ctx, 0, SL));
+        }
+        if (refine) FH_TRY(refine_range(ctx, true, 0, SL, 0, ctx->n_rchunk_early, 0, ctx->n_dblk_early));
     }
     FH_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
     {
@@ -1084,6 +1132,8 @@ fh_status split_front(fh_ctx *ctx) {
         PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, SL, S));
         FH_TRY(tc_factor_range(ctx, SL, S));
     }
+    if (refine)
+        FH_TRY(refine_range(ctx, true, SL, S, ctx->n_rchunk_early, ctx->n_rchunk, ctx->n_dblk_early, ctx->n_dblk));
     FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     return FH_OK;
 }
@@ -1093,14 +1143,8 @@ fh_status split_front(fh_ctx *ctx) {
 fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     const fh::SolveTables t = tables(ctx);
     const bool split = tc && !ctx->timing && ctx->early_solves > 0 && ctx->early_solves < ctx->S;
-    if (split) {
-        FH_TRY(split_front(ctx));
-        PhaseScope ps(ctx, FH_PH_ASSEMBLE, 1);
-        fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
-                       ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(), ctx->d_g.as<double2>(),
-                       ctx->stream);
-        FH_TRY(check_launch(ctx, "rhs"));
-    } else {
+    if (split) return split_front(ctx, true);   // assembly, factorisation and refinement
+    {
         PhaseScope ps(ctx, FH_PH_ASSEMBLE, mixed ? 3 : 2);   // (tiles, band,) right sides
         FH_TRY(assemble_kernels(ctx));
         fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
@@ -1119,10 +1163,8 @@ fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     } else {
         {
             // launches: conversion and one LU launch per cluster size (SIMT: one)
-            PhaseScope ps(ctx, FH_PH_FACTOR, split ? 0 : tc ? tc_launches(ctx, 0, ctx->S) : 2);
-            if (split) {
-                // factored above
-            } else if (tc) {
+            PhaseScope ps(ctx, FH_PH_FACTOR, tc ? tc_launches(ctx, 0, ctx->S) : 2);
+            if (tc) {
                 FH_TRY(tc_factor_kernels(ctx));
             } else {
                 fh::launch_convert_fp32(ctx->d_A.as<float4>(), ctx->d_A32.as<float2>(), ctx->mat_total,
@@ -1135,18 +1177,7 @@ fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
         }
         // launches: diagonal-block inverses (row-major factors), set-up, two
         // kernels per sweep and the verdict
-        PhaseScope ps(ctx, FH_PH_REFINE, (tc ? 1 : 0) + 2 + 2 * kRefineMaxIters);
-        fh::launch_lu_refine(tc, ctx->d_order.as<int>(), ctx->S, ctx->d_N.as<int>(),
-                             ctx->d_mat_off.as<long long>(), ctx->d_vec_off.as<int>(),
-                             ctx->d_rchunk.as<int2>(), ctx->n_rchunk, ctx->d_dblk.as<int2>(),
-                             ctx->n_dblk, ctx->d_blk_off.as<int>(), ctx->d_dinv.as<float2>(),
-                             ctx->d_A.as<float4>(),
-                             ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(), ctx->d_g.as<double2>(),
-                             ctx->d_psi.as<double2>(), ctx->d_y32.as<float2>(), ctx->d_rstate.p,
-                             kRefineMaxIters, kRefineTol, ctx->d_iters.as<int>(),
-                             ctx->d_resid.as<double>(), ctx->d_info.as<int>(), ctx->maxN,
-                             ctx->stream);
-        FH_TRY(check_launch(ctx, "lu mixed"));
+        FH_TRY(refine_range(ctx, tc, 0, ctx->S, 0, ctx->n_rchunk, 0, ctx->n_dblk));
     }
     return FH_OK;
 }
@@ -1633,7 +1664,7 @@ fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_ou
         // 2b. assembly + factorisation with the largest systems started early
         FH_TRY(tune_field(ctx, reps, &fh_tuning::lu_early, {0, 10, 20, 35}, ms_out[3], [&]() {
             if (ctx->early_solves > 0 && ctx->early_solves < ctx->S) {
-                FH_TRY(split_front(ctx));
+                FH_TRY(split_front(ctx, false));
             } else {
                 FH_TRY(assemble_kernels(ctx));
                 FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));

@@ -511,11 +511,12 @@ __device__ __forceinline__ bool refine_done(const RefineState &r, double tol) {
 
 // x = 0, y = P g (FP32), ||g||.
 __global__ void __launch_bounds__(256) refine_setup_kernel(
-    const int *__restrict__ Ns, const int *__restrict__ vec_off, const int *__restrict__ piv,
+    const int *__restrict__ order, const int *__restrict__ Ns, const int *__restrict__ vec_off,
+    const int *__restrict__ piv,
     const double2 *__restrict__ G, double2 *__restrict__ X, float2 *__restrict__ Y32,
     RefineState *__restrict__ st, int *__restrict__ iters, const int *__restrict__ info) {
     __shared__ double red[32];
-    const int s = blockIdx.x, n = Ns[s], vo = vec_off[s];
+    const int s = order[blockIdx.x], n = Ns[s], vo = vec_off[s];
     double gmax = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double2 gi = G[vo + i];
@@ -644,10 +645,12 @@ __global__ void __launch_bounds__(256) refine_resid_kernel(
 }
 
 // After the last sweep: convergence verdict and relative residual.
-__global__ void refine_final_kernel(int S, const RefineState *__restrict__ st, double tol,
-                                    double *__restrict__ resid, int *__restrict__ info) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S || info[s] != 0) return;
+__global__ void refine_final_kernel(const int *__restrict__ order, int S, const RefineState *__restrict__ st,
+                                    double tol, double *__restrict__ resid, int *__restrict__ info) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    const int s = order[i];
+    if (info[s] != 0) return;
     const RefineState r = st[s];
     const double rmax = __longlong_as_double((long long)r.rbits);
     if (!r.conv && !refine_done(r, tol)) info[s] = -1;
@@ -702,7 +705,7 @@ void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
     }
     if (row_major)
         diag_inverse_kernel<<<n_blocks, 64, 0, st>>>(blocks, N, mat_off, blk_off, LU32, inv);
-    refine_setup_kernel<<<S, 256, 0, st>>>(N, vec_off, piv, g, x, y32, rs, iters, info);
+    refine_setup_kernel<<<S, 256, 0, st>>>(order, N, vec_off, piv, g, x, y32, rs, iters, info);
     for (int it = 1; it <= max_iters; ++it) {
         if (row_major)
             refine_solve_kernel<true><<<S, 512, (size_t)maxN * sizeof(float2), st>>>(
@@ -713,7 +716,7 @@ void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
         refine_resid_kernel<<<n_chunks, 256, (size_t)maxN * sizeof(float4), st>>>(
             chunks, N, mat_off, vec_off, A, piv, g, x, y32, rs);
     }
-    refine_final_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, rs, tol, resid, info);
+    refine_final_kernel<<<(S + 255) / 256, 256, 0, st>>>(order, S, rs, tol, resid, info);
 }
 
 }  // namespace fh
