@@ -1092,9 +1092,9 @@ fh_status refine_range(fh_ctx *ctx, bool tc, int i0, int i1, int c0, int c1, int
 }
 
 // Tensor-core path with lu_early: the largest systems (subgroups 0 ..
-// early_groups-1) are assembled, factored and refined on the side stream
-// while the rest is assembled, factored and refined on the context stream;
-// the streams join at the end.  d_info and d_tcerr are cleared and the right
+// early_groups-1) are assembled first, then factored and refined on the side
+// stream while the rest is assembled, factored and refined on the context
+// stream; the streams join at the end.  d_info and d_tcerr are cleared and the right
 // sides formed first.  refine = false (the autotuner's assembly + factorisation
 // timing) leaves out the right sides and the refinement.
 fh_status split_front(fh_ctx *ctx, bool refine) {
@@ -1109,14 +1109,16 @@ fh_status split_front(fh_ctx *ctx, bool refine) {
                        ctx->stream);
         FH_TRY(check_launch(ctx, "rhs"));
     }
+    // the largest systems are assembled first, alone, so that their LU CTAs
+    // (a whole SM each) find empty SMs when the rest's assembly starts
+    {
+        PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
+        FH_TRY(assemble_range(ctx, 0, gL, 0, SL));
+    }
     FH_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
     FH_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
     {
         OnStream on(ctx, ctx->side);
-        {
-            PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
-            FH_TRY(assemble_range(ctx, 0, gL, 0, SL));
-        }
         {
             PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, 0, SL));
             FH_TRY(tc_factor_range(ctx, 0, SL));
