@@ -330,9 +330,13 @@ def run_gpu(args, world, rank, local):
     S = wl.J - 1
     n_x, n_T = wl.n_x, wl.T.size
     pr = F.Problem(local, prec)
-    stream = torch.cuda.current_stream()
-    F.fh_set_stream(pr.ctx, stream.cuda_stream)
     dev = torch.device("cuda", local)
+    # One explicit stream for the library, the L2 flush and the timing events
+    # (torch's default stream has the NULL handle, which would leave the
+    # library on its own stream, unordered with the events).
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    F.fh_set_stream(pr.ctx, stream.cuda_stream)
     d_a = torch.tensor(wl.a, device=dev, dtype=torch.float64)
     d_x = torch.tensor(wl.x, device=dev, dtype=torch.float64)
     d_T = torch.tensor(wl.T, device=dev, dtype=torch.float64)
