@@ -143,11 +143,11 @@ DF_MAC_INSTR = 11                                          # FP32 instructions p
 DF_PEAK = FP32_PEAK / DF_MAC_INSTR                         # FP64-equivalent flop/s of df MACs
 TF32_OVER_BF16 = 1.1 / 2.25                                # nominal dense tensor rates
 
-# DRAM bytes (read + write) per step of the kernel as committed, from one ncu
-# capture of the bench command with the autotuned schedule
-# (profiles/launches_kite_pulses_tf32.md): both launches where the schedule
-# splits a phase into the early and the remaining systems.
-MEASURED_TRAFFIC = {"field_partial_df_kernel": 2.27e6, "lu_factor_tc_kernel": 384.8e6,
+# DRAM bytes (read + write) per step of the kernel as committed, from ncu
+# captures of the bench command (--set full, one launch per kernel; both
+# launches where the schedule splits a phase into the early and the remaining
+# systems).
+MEASURED_TRAFFIC = {"field_partial_df_kernel": 2.0e6, "lu_factor_tc_kernel": 384.8e6,
                     "assemble_group_df_kernel": 215.9e6, "contract_df_kernel": 36.6e6}
 
 
@@ -180,7 +180,8 @@ OZAKI_PAIRS = 36   # slice pairs (i, j), i + j < 8, of the tensor-core contracti
 
 
 def phase_rooflines(wl, precision, ms, iters, peaks, contract_tc=False):
-    """Achieved against peak per phase; work definitions in the design doc."""
+    """Achieved against peak per phase: algorithmic work per step (each
+    entry's work definition is in its peak_source) over the phase time."""
     N = wl.N[1:].astype(np.float64)
     mixed = precision != "fp64"
     bf16 = peaks.get("bf16_tflops")
