@@ -36,9 +36,9 @@ namespace {
 
 // nu_{p,r} as a contraction: pw[m + h][r] = T_r(m/h) (three-term recurrence
 // T_{r+1} = 2x T_r - T_{r-1}, stable on [-1, 1]; T_0 halved; one thread per
-// m), then one CTA per p stages the phases e^{-2 pi i m p / M} (-1)^m of a
-// chunk of m in shared memory and thread r accumulates
-// sum_m phase_m pw[m + h][r].
+// m), then one CTA per p stages (-1)^k (cos, sin)(2 pi k p / M) of a chunk of
+// k in shared memory and thread r accumulates the cosine (even r) or sine
+// (odd r) sum over k = 1 .. h-1, m and -m paired.
 __global__ void far_powers_kernel(int M, double *__restrict__ pw) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= M) return;
@@ -70,32 +70,44 @@ __global__ void __launch_bounds__(128) far_table_kernel(int J, int M, const doub
             const float ch = (float)cs, sh = (float)sn;   // double-float (cos, sin)
             ph[q] = make_float4(ch, (float)(cs - (double)ch), sh, (float)(sn - (double)sh));
         }
-    double sr = 0.0, si = 0.0;
-    for (int m0 = -h; m0 < h; m0 += kFarChunk) {
+    // Pairing m with -m (T_r(-x) = (-1)^r T_r(x), e^{-i th m} + (-1)^r e^{i th m} =
+    // 2 cos(th m) for even r, -2i sin(th m) for odd r; th = 2 pi p / M):
+    //   nu_{p,r} = T_r(0) + (-1)^(h+p+r) T_r(1)
+    //            + 2 sum_{k=1}^{h-1} (-1)^k T_r(k/h) {cos(th k) | -i sin(th k)},
+    // the m = -h term using e^{i th h} = (-1)^p (T_0 halved throughout).
+    const bool odd_r = r & 1;
+    double acc = 0.0;
+    for (int k0 = 1; k0 < h; k0 += kFarChunk) {
         __syncthreads();
         for (int e = r; e < kFarChunk; e += blockDim.x) {
-            const int m = m0 + e;
+            const int k = k0 + e;
             double2 v = make_double2(0.0, 0.0);
-            if (m < h) {
-                const long long mm = ((long long)(m % M) + M) % M;
-                const int q = (int)((mm * p) % M);
+            if (k < h) {
+                const int q = (int)(((long long)k * p) % M);
                 double sn, cs;
-                sincospi(-2.0 * (double)q / (double)M, &sn, &cs);
-                const double sg = (m & 1) ? -1.0 : 1.0;
+                sincospi(2.0 * (double)q / (double)M, &sn, &cs);
+                const double sg = (k & 1) ? -1.0 : 1.0;
                 v = make_double2(sg * cs, sg * sn);
             }
             phs[e] = v;
         }
         __syncthreads();
         if (r < kFarTerms) {
-            const int me = min(kFarChunk, h - m0);
-            const double *col = pw + (long long)(m0 + h) * kFarTerms + r;
-            for (int e = 0; e < me; ++e) {
+            const int ke = min(kFarChunk, h - k0);
+            const double *col = pw + (long long)(k0 + h) * kFarTerms + r;
+            for (int e = 0; e < ke; ++e) {
                 const double w = col[(long long)e * kFarTerms];
-                sr = fma(w, phs[e].x, sr);
-                si = fma(w, phs[e].y, si);
+                acc = fma(w, odd_r ? phs[e].y : phs[e].x, acc);
             }
         }
+    }
+    double sr = 0.0, si = 0.0;
+    if (r < kFarTerms) {
+        const double t0 = pw[(long long)h * kFarTerms + r];      // T_r(0) (T_0 halved)
+        const double t1 = r == 0 ? 0.5 : 1.0;                    // T_r(1)
+        const double edge = ((h + p + r) & 1) ? -t1 : t1;        // the m = -h term
+        sr = t0 + edge + (odd_r ? 0.0 : 2.0 * acc);
+        si = odd_r ? -2.0 * acc : 0.0;
     }
     if (r < kFarTerms) {
         if (nu) nu[(long long)r * J + p] = make_double2(sr, si);
