@@ -300,8 +300,10 @@ __device__ void near_sum(double y, dfl sypi, int h, int M, int p, int J, const f
 }
 
 // The sampled near sums.  Odd rows (direct sums, sin(pi g / 2) = +-1): one
-// CTA per kTabRows consecutive odd rows and kTabThreads columns p, so that
-// each phase gathered from shared memory serves kTabRows rows.  Even rows:
+// CTA per kTabRows consecutive positive odd rows and kTabThreads columns p,
+// so that each phase gathered from shared memory serves kTabRows rows; the
+// negative odd rows follow from the positive ones by a conjugation and a
+// real end-term correction.  Even rows:
 // D_p(n) = e^{-2 pi i n p / M} for -h <= n < h, else 0 (sinc(n - m) vanishes
 // off m = n), written by the CTAs past the odd ones (grid-stride, blockIdx.y
 // 0 only).
@@ -331,8 +333,7 @@ __global__ void __launch_bounds__(kTabThreads) sinc_table_kernel(int J, int M, i
     extern __shared__ __align__(16) float4 sm4[];
     float4 *ph4 = sm4;        // M phases
     float4 *sc4 = sm4 + M;    // kTabRows rows of h sinc sums
-    const int o_first = (G & 1) ? -G : 1 - G;            // first odd row
-    const int g0 = o_first + 2 * kTabRows * (int)blockIdx.x;
+    const int g0 = 1 + 2 * kTabRows * (int)blockIdx.x;   // positive odd rows; -g from g
     const int p = blockIdx.y * kTabThreads + threadIdx.x;
     for (int q = threadIdx.x; q < M; q += blockDim.x) ph4[q] = ph_g[q];
 #pragma unroll 1
@@ -380,7 +381,16 @@ __global__ void __launch_bounds__(kTabThreads) sinc_table_kernel(int J, int M, i
         const int g = g0 + 2 * r;
         if (g > G) break;
         const float tr = ac[r][0] + ac[r][1], ti = ac[r][2] + ac[r][3];
-        tab[(long long)(g + G) * J + p] = make_float4(tr, ac[r][1] - (tr - ac[r][0]), ti, ac[r][3] - (ti - ac[r][2]));
+        const dfl re = {tr, ac[r][1] - (tr - ac[r][0])}, im = {ti, ac[r][3] - (ti - ac[r][2])};
+        tab[(long long)(g + G) * J + p] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        // D_p(-y) = conj(D_p(y)) + (-1)^p (sinc(y - h) - sinc(y + h)): m and -m
+        // swap, c_{-m} = conj(c_m), and the end terms m = -h, h differ; at
+        // y = g/2, sinc(y -+ h) = (-1)^h sin(pi y) / (pi (y -+ h))
+        const double y = 0.5 * (double)g, sy = (g & 3) == 1 ? 1.0 : -1.0;
+        const double corr = ((h & 1) ? -sy : sy) * 2.0 * (double)h / (kPi * (y * y - (double)h * (double)h));
+        const dfl c = df_split((p & 1) ? -corr : corr);
+        const dfl rn = df_addq(re, c);
+        tab[(long long)(G - g) * J + p] = make_float4(rn.hi, rn.lo, -im.hi, -im.lo);
     }
 }
 
@@ -784,8 +794,7 @@ void launch_sinc_table(int J, int M, const float4 *phase_tab, float4 *tab, cudaS
         cudaFuncSetAttribute(sinc_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    const int o_first = (G & 1) ? -G : 1 - G, o_last = (G & 1) ? G : G - 1;
-    const int odd_ctas = ((o_last - o_first) / 2 + 1 + kTabRows - 1) / kTabRows;
+    const int odd_ctas = ((G + 1) / 2 + kTabRows - 1) / kTabRows;   // positive odd rows 1 .. G
     sinc_table_kernel<<<dim3(odd_ctas + 64, (J + kTabThreads - 1) / kTabThreads), kTabThreads, smem, st>>>(
         J, M, G, odd_ctas, phase_tab, tab);
 }
