@@ -117,6 +117,45 @@ def test_cfie_kite_reciprocity(kappa):
     assert abs(Ua - Ub) / abs(Ua) < 1e-11
 
 
+@pytest.mark.parametrize("seed", [4, 19])
+def test_star_geometry_matches_spectral_derivatives(seed):
+    """Star branch of the node tables: z against the shape definition of the
+    inputs module, z' and z'' against exact spectral differentiation of the
+    sampled curve.  A star with five harmonics is a trigonometric polynomial
+    of degree 6 in t, so differentiation by FFT on 2n >= 14 nodes is exact
+    up to rounding; a wrong sign or factor in r', r'' fails this."""
+    rng = np.random.default_rng(seed)
+    cur = fi.random_star(rng, n_harm=5, amp_max=0.3)
+    cur.center = (0.3, -0.2)
+    for n in (16, 45):
+        t, z, dz, ddz = O.discretize(cur, n)
+        zp = cur.point(t)
+        assert np.max(np.abs(z - zp)) < 1e-14
+        k = np.fft.fftfreq(2 * n, 1.0 / (2 * n))
+        k[n] = 0.0                        # Nyquist mode: zero for degree < n
+        for c in range(2):
+            Z = np.fft.fft(zp[c])
+            d1 = np.real(np.fft.ifft(1j * k * Z))
+            d2 = np.real(np.fft.ifft(-(k ** 2) * Z))
+            assert np.max(np.abs(dz[c] - d1)) < 1e-12
+            assert np.max(np.abs(ddz[c] - d2)) < 1e-11
+
+
+@pytest.mark.parametrize("kappa", [3.0, 8.0])
+def test_cfie_star_reciprocity(kappa):
+    """Point-source reciprocity U_y(x) = U_x(y) on a star obstacle: the whole
+    CFIE (including the curvature diagonal L2(t,t), which uses z'') through
+    the star branch of the geometry."""
+    rng = np.random.default_rng(23)
+    cur = fi.random_star(rng, n_harm=5, amp_max=0.15)
+    n = 128
+    xa = np.array([2.2, 1.4])
+    xb = np.array([-2.0, -1.7])
+    Ua = O.target_field(cur, n, kappa, _point_source_density(cur, n, kappa, xa), xb)[0]
+    Ub = O.target_field(cur, n, kappa, _point_source_density(cur, n, kappa, xb), xa)[0]
+    assert abs(Ua - Ub) / abs(Ua) < 1e-11
+
+
 def test_cfie_kite_spectral_convergence():
     """Far field from N = 192 and N = 384 agree to near machine precision."""
     cur = fi.kite()
