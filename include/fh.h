@@ -135,7 +135,10 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
  *   a          n_samples real samples a(t0 + q dt) (host); a = 0 outside them
  *   t0, dt     sample grid; H/dt and (H + t0)/dt must be integers (1e-9)
  *   H          window half-width (the paper uses H = 10)
- * Requires fh_discretize.  Spectra stay resident on the device. */
+ * Requires fh_discretize.  Spectra stay resident on the device.  FH_EINVAL if
+ * the signal spans more windows than the synthesis weights hold in shared
+ * memory (52 K bytes, plus 24 (2J - 2) bytes when J > 1025, at most 204800:
+ * K <= 3938 for J <= 1025). */
 fh_status fh_window_spectra(fh_ctx *ctx, const double *a, int n_samples, double t0,
                             double dt, double H);
 
@@ -245,7 +248,11 @@ fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, 
  *            is the omega = 0 value (1 for the 2D low-frequency limit)
  *   d_T      n_T sample times (device);  d_u  n_x*n_T doubles, u[i*n_T + l] (device)
  *   stream   cudaStream_t to launch on (NULL: legacy default stream)
- * Limits: J*n_T <= 524288.  Larger sizes return FH_EINVAL; nothing is launched.
+ * Limits: J*n_T <= 524288, and 52 K + 24 M <= 204800 (M = 2(J-1): the weights
+ * kernel's per-window and phase arrays in shared memory; K <= 2048 at J = 2049).
+ * Larger sizes return FH_EINVAL; nothing is launched.  A CUDA error left
+ * pending by earlier work on the calling thread is returned as FH_ECUDA before
+ * anything is launched, and left in place for its owner. 
  * The first call on a device looks up the device address of the static array
  * (cudaGetSymbolAddress) with that device current; make it before any stream
  * capture.  Every call reuses the same array, whose contents are whatever the

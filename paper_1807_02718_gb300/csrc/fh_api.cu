@@ -703,6 +703,13 @@ fh_status discretize_device(fh_ctx *ctx) {
     return FH_OK;
 }
 
+// Largest window count whose synthesis-weights arrays fit in shared memory.
+int max_windows(const Problem &pb) {
+    int K = 1;
+    while (fh::synth_weights_smem(pb.J, K + 1, pb.stab_off >= 0) <= fh::kWeightsMaxSmem) ++K;
+    return K;
+}
+
 fh_status spectra_common(fh_ctx *ctx, Problem &pb, const double *d_a, int n_samples, double t0,
                          double dt, double H) {
     if (n_samples < 1) return fail(ctx, FH_EINVAL, "n_samples must be >= 1 (got %d)", n_samples);
@@ -724,6 +731,9 @@ fh_status spectra_common(fh_ctx *ctx, Problem &pb, const double *d_a, int n_samp
         if (K > 1000000) return fail(ctx, FH_EINVAL, "too many windows");
     }
     K = std::max(K, 1);
+    if (fh::synth_weights_smem(pb.J, K, pb.stab_off >= 0) > fh::kWeightsMaxSmem)
+        return fail(ctx, FH_EINVAL, "the signal spans %d windows; the synthesis weights support "
+                    "at most %d at J = %d", K, max_windows(pb), pb.J);
     std::vector<double> s(K);
     long long start0 = 0;
     for (int k = 0; k < K; ++k) {

@@ -6,9 +6,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "fh.h"
 
 namespace fh {
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device.  The attribute lives in each device's context, so
+// a process with contexts on several GPUs needs it on every one; `done` holds
+// one bit per device (devices beyond 63 set it on every call).  Concurrent
+// first calls from several host threads only repeat the (idempotent) call.
+inline cudaError_t ensure_smem_attr(const void *fn, int bytes,
+                                    std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kEulerGamma = 0.57721566490153286061;
@@ -170,6 +189,12 @@ void launch_synth_weights(int J, int M, double W, int K, const double *s, const 
                           float4 *Bf, const float4 *nu_f, const float4 *phase_tab,
                           const float4 *sinc_tab, const double *T, int n_T, double *Gr, double *Gm,
                           float2 *Gs, cudaStream_t st);
+// Dynamic shared memory launch_synth_weights needs for J frequencies and K
+// windows, with (`table`) or without the near-sum table; at most
+// kWeightsMaxSmem bytes are available (so K and J are bounded; callers
+// reject larger problems before launching).
+constexpr size_t kWeightsMaxSmem = 200 * 1024;
+size_t synth_weights_smem(int J, int K, bool table);
 // Near-window sums by interpolation.  The near sums
 //   D_p(y) = sum_{m=-h}^{h-1} e^{-2 pi i m p / M} sinc(y - m)
 // are, as functions of y, band-limited to [-pi, pi]; sampled on the

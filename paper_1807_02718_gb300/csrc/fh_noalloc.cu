@@ -58,8 +58,13 @@ extern "C" fh_status fh_synthesize_static(int J, double W, int K, const double *
                                           void *cuda_stream) {
     if (J < 2 || J > kMaxJ || K < 1 || n_x < 0 || n_T < 0 || !(W > 0.0)) return FH_EINVAL;
     if ((long long)J * n_T > kMaxGridPoints) return FH_EINVAL;
+    // the weights kernel keeps per-window arrays and the phase rows in shared memory
+    if (fh::synth_weights_smem(J, K, false) > fh::kWeightsMaxSmem) return FH_EINVAL;
     if (n_x == 0 || n_T == 0) return FH_OK;
     if (!d_s || !d_B || !d_V || !d_T || !d_u) return FH_EINVAL;
+    // An error left pending by earlier, unrelated work belongs to its owner:
+    // report it without launching and without clearing it.
+    if (cudaPeekAtLastError() != cudaSuccess) return FH_ECUDA;
     double *scratch = nullptr;
     const fh_status st = scratch_address(&scratch);
     if (st != FH_OK) return st;

@@ -291,11 +291,10 @@ size_t contract_tc_scratch_bytes(int J, int n_x, int n_T) {
 cudaError_t launch_contract_tc(int J, int n_x, int n_T, const double2 *V, const double *Gr,
                                const double *Gm, double *u, void *scratch, int *err, cudaStream_t st) {
     if (n_x <= 0 || n_T <= 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    static std::atomic<unsigned long long> attr{0};
+    {
+        const cudaError_t e = ensure_smem_attr((const void *)contract_tc_kernel, kSmem, attr);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int kp = contract_tc_kpad(J), rx = contract_tc_rows(n_x), rt = contract_tc_cols(n_T);
     __nv_bfloat16 *As = static_cast<__nv_bfloat16 *>(scratch);

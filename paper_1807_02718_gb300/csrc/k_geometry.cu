@@ -122,11 +122,8 @@ void launch_kress_tables(int n_tab, int maxN, const int *tab_N, const int *tab_o
     if (n_tab <= 0) return;
     dim3 grid((maxN + 127) / 128, n_tab);
     const size_t smem = (size_t)maxN * 3 / 2 * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(kress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    ensure_smem_attr((const void *)kress_kernel, 200 * 1024, attr);
     kress_kernel<<<grid, 128, smem, st>>>(tab_N, tab_off, kress, logsin, wpf);
 }
 

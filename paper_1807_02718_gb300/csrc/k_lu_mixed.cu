@@ -677,11 +677,8 @@ void launch_lu_factor_fp32(const int *order, int S, const int *N, const long lon
                            float2 *A32, int *piv, const int *vec_off, int *info, int maxN,
                            cudaStream_t st) {
     if (S <= 0) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(lu_factor_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    ensure_smem_attr((const void *)lu_factor_fp32_kernel, 64 * 1024, attr);
     lu_factor_fp32_kernel<<<S, 256, maxN * sizeof(int), st>>>(order, N, mat_off, vec_off, A32, piv,
                                                               info);
 }
@@ -696,13 +693,10 @@ void launch_lu_refine(bool row_major, const int *order, int S, const int *N,
                       double tol, int *iters, double *resid, int *info, int maxN, cudaStream_t st) {
     if (S <= 0) return;
     RefineState *rs = static_cast<RefineState *>(state);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(refine_resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(refine_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(refine_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr[3] = {{0}, {0}, {0}};
+    ensure_smem_attr((const void *)refine_resid_kernel, 200 * 1024, attr[0]);
+    ensure_smem_attr((const void *)refine_solve_kernel<true>, 200 * 1024, attr[1]);
+    ensure_smem_attr((const void *)refine_solve_kernel<false>, 200 * 1024, attr[2]);
     if (row_major)
         diag_inverse_kernel<<<n_blocks, 64, 0, st>>>(blocks, N, mat_off, blk_off, LU32, inv);
     refine_setup_kernel<<<S, 256, 0, st>>>(order, N, vec_off, piv, g, x, y32, rs, iters, info);

@@ -692,15 +692,14 @@ cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, co
                                 const int *N, const long long *mat_off, float2 *A32, int *piv,
                                 const int *vec_off, int *info, int *err, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
-    static bool attr[3] = {false, false, false};
-    if (!attr[kind]) {
+    static std::atomic<unsigned long long> attr[4] = {{0}, {0}, {0}, {0}};
+    {
         const void *fns[4] = {(const void *)lu_factor_tc_kernel<2, false>, (const void *)lu_factor_tc_kernel<2, true>,
                               (const void *)lu_factor_tc_kernel<1, false>, (const void *)lu_factor_tc_kernel<1, true>};
         for (int f = kind == 2 ? 0 : 2, e0 = f + 2; f < e0; ++f) {
-            const cudaError_t e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+            const cudaError_t e = ensure_smem_attr(fns[f], kDynSmem, attr[f]);
             if (e != cudaSuccess) return e;
         }
-        attr[kind] = true;
     }
     // order is sorted by decreasing N, so each cluster size is a contiguous run
     for (int first = 0; first < S;) {

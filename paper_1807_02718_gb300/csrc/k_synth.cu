@@ -789,14 +789,16 @@ void launch_sinc_table(int J, int M, const float4 *phase_tab, float4 *tab, cudaS
     const int G = sinc_tab_half(J);
     if (!G) return;
     const size_t smem = (size_t)(M + kTabRows * (M / 2)) * sizeof(float4);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(sinc_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    ensure_smem_attr((const void *)sinc_table_kernel, 200 * 1024, attr);
     const int odd_ctas = ((G + 1) / 2 + kTabRows - 1) / kTabRows;   // positive odd rows 1 .. G
     sinc_table_kernel<<<dim3(odd_ctas + 64, (J + kTabThreads - 1) / kTabThreads), kTabThreads, smem, st>>>(
         J, M, G, odd_ctas, phase_tab, tab);
+}
+
+size_t synth_weights_smem(int J, int K, bool table) {
+    const int M = 2 * (J - 1);
+    return weights_smem_head(K) + (table ? 0 : (size_t)(M + M / 2) * sizeof(float4));
 }
 
 void launch_synth_weights(int J, int M, double W, int K, const double *s, const double2 *B,
@@ -804,12 +806,9 @@ void launch_synth_weights(int J, int M, double W, int K, const double *s, const 
                           const float4 *sinc_tab, const double *T, int n_T, double *Gr, double *Gm,
                           float2 *Gs, cudaStream_t st) {
     if (n_T <= 0) return;
-    const size_t smem = weights_smem_head(K) + (sinc_tab ? 0 : (size_t)(M + M / 2) * sizeof(float4));
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    const size_t smem = synth_weights_smem(J, K, sinc_tab != nullptr);
+    static std::atomic<unsigned long long> attr{0};
+    ensure_smem_attr((const void *)weights_kernel, (int)kWeightsMaxSmem, attr);
     if (Bf) {
         const long long n = (long long)K * J;
         split_df_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, Bf, n);

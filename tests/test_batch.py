@@ -36,7 +36,7 @@ def test_footprint_counts_matrices_and_tables():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", [F.FH_FP64, F.FH_MIXED_FP32])
+@pytest.mark.parametrize("precision", [F.FH_FP64, F.FH_MIXED_FP32, F.FH_MIXED_TF32, F.FH_MIXED_BF16])
 def test_batch_equals_each_problem_alone(precision):
     from paper_1807_02718_gb300 import build
     build.build()
@@ -71,4 +71,47 @@ def test_batch_equals_each_problem_alone(precision):
     wl = fi.Workload("batch2", cur, om, N, 1.0, pdir, a, t0, dt, 10.0, x, T)
     ref = O.run(wl)["u"]
     assert np.linalg.norm(u_batch[2] - ref) / np.linalg.norm(ref) < TOL
+    F.fh_destroy(ctx)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [F.FH_MIXED_TF32, F.FH_MIXED_BF16])
+def test_batch_tensor_core_vs_oracle(precision):
+    """Three star problems of uneven sizes (N up to ~300) in one batch on the
+    tensor-core LU, with the largest systems split onto the second stream
+    (lu_early) and the tensor-core contraction: every problem's densities and
+    u(x, T) within 1e-10 of the oracle, each after graph replay."""
+    from paper_1807_02718_gb300 import build
+    build.build()
+    rng = np.random.default_rng(8)
+    probs = []
+    for q in range(3):
+        cur = fi.random_star(rng)
+        J = int(rng.integers(20, 40))
+        om = fi.frequency_mesh(J, float(rng.uniform(10.0, 30.0)))
+        ang = float(rng.uniform(0, 2 * np.pi))
+        probs.append((cur, om, fi.boundary_sizes(cur, om), (np.cos(ang), np.sin(ang))))
+    sig = fi.pulse_train(9, n=6, span=60.0, fmin=4.0, fmax=12.0)
+    t0, dt = -10.0, 0.01
+    a = fi.sample_signal(sig, t0, dt, int(np.ceil((sig.t_end - t0) / dt)) + 1)
+    x = fi.targets_on_circle(9, 2.6, center=(-0.1, 0.05))
+    T = np.concatenate([np.linspace(0, 120, 97), [777.0, 1e4]])
+    ctx = F.fh_create(0, precision)
+    F.fh_set_tuning(ctx, lu_early=20, contract_tc=1)
+    for _ in range(3):                      # direct launches, capture, replay
+        F.fh_discretize_batch(ctx, [p[0] for p in probs], [p[1] for p in probs],
+                              [p[2] for p in probs], ps=[p[3] for p in probs])
+        st = F.fh_solve_frequencies(ctx)
+        u_batch = []
+        for q in range(3):
+            F.fh_window_spectra_p(ctx, q, a, t0, dt)
+            u_batch.append(F.fh_sample_p(ctx, q, x, T))
+    assert st.residual_max < 1e-12
+    for q, (cur, om, N, pdir) in enumerate(probs):
+        wl = fi.Workload(f"batch{q}", cur, om, N, 1.0, pdir, a, t0, dt, 10.0, x, T)
+        ref = O.run(wl)
+        for j in range(1, len(om)):
+            psi = F.fh_get_density_p(ctx, q, j, int(N[j]))
+            assert np.linalg.norm(psi - ref["psi"][j]) / np.linalg.norm(ref["psi"][j]) < TOL
+        assert np.linalg.norm(u_batch[q] - ref["u"]) / np.linalg.norm(ref["u"]) < TOL
     F.fh_destroy(ctx)

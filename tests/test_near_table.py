@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import fh_inputs as fi
+import oracle as O
 from paper_1807_02718_gb300 import fh as F
 
 pytestmark = pytest.mark.gpu
@@ -76,3 +77,40 @@ def test_direct_sums_above_the_table_bound():
     bit those of the allocation-free entry point."""
     u_ctx, u_dir = both(1026, 60.0, n_x=8)
     assert np.array_equal(u_ctx, u_dir)
+
+
+@pytest.mark.parametrize("J", [12, 1025])
+def test_table_rows_against_oracle(J):
+    """Every half-integer row of the near-sum table, negative rows included
+    (those are derived from the positive ones by conjugation and an end-term
+    correction), read through the synthesis: with a single window, a time at
+    y = W (T - s_1) / pi = g/2 puts the 42-point interpolation exactly on
+    sample g (weight 1 there, 0 on the others), so u at that time is the
+    table row contracted with B and V.  Compared pointwise with the oracle's
+    direct sum (1e-13 of the largest |u|), for every g with |g/2| < 1.25 h."""
+    W = 6.0 if J == 12 else 60.0
+    om = fi.frequency_mesh(J, W)
+    t0, dt = -10.0, 0.01
+    t = t0 + dt * np.arange(1500)                 # one window (K = 1, s_1 = 0)
+    a = np.exp(-((t - 1.0) / 1.5) ** 2) * np.sin(2.0 * t)
+    h = J - 1
+    g_max = int(math.floor(2 * 1.25 * h - 1e-9))
+    g = np.arange(-g_max, g_max + 1)
+    if J > 100:                                   # all negative rows, a spread of positive ones
+        g = np.concatenate([g[g < 0], g[g >= 0][::17]])
+    T = (g / 2.0) * math.pi / W
+    pr = F.Problem()
+    pr.discretize(fi.circle(1.0), om, np.full(J, 16, dtype=np.int32))
+    pr.window_spectra(a, t0, dt, 10.0)
+    assert F.fh_get_num_windows(pr.ctx) == 1
+    rng = np.random.default_rng(J + 1)
+    V = rng.standard_normal((3, J)) + 1j * rng.standard_normal((3, J))
+    V[:, 0] = 1.0
+    u = F.fh_synthesize(pr.ctx, V, T)
+    pr.close()
+    s, B = O.window_spectra(a, t0, dt, 10.0, om)
+    uo = O.synthesize(B, s, om, V, T)
+    scale = np.max(np.abs(uo))
+    neg = g < 0
+    assert np.max(np.abs(u[:, neg] - uo[:, neg])) < 1e-13 * scale
+    assert np.max(np.abs(u[:, ~neg] - uo[:, ~neg])) < 1e-13 * scale

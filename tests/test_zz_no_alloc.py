@@ -23,11 +23,20 @@ def rel(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
 
 
-def test_static_scratch_synthesis_matches_context_path():
+# (J, n_T): a small mesh; J > 1025 (direct near sums, weights shared memory
+# above 48 KB); the largest J; and J * n_T at the scratch limit 2^19, where
+# the far table's power table, aliased with the weight planes, is largest.
+SIZES = [(96, 360), (1100, 524288 // 1100), (2049, 524288 // 2049)]
+
+
+@pytest.mark.parametrize("J,n_T", SIZES)
+def test_static_scratch_synthesis_matches_context_path(J, n_T):
     import torch
     from paper_1807_02718_gb300 import build
     build.build()
-    wl = fi.kite_pulses(J=96, W=20.0, n_x=40, n_near=300, n_far=60)
+    W = 20.0 * (J - 1) / 95.0
+    wl = fi.kite_pulses(J=J, W=W, n_x=40, n_near=n_T - n_T // 6, n_far=n_T // 6)
+    assert wl.T.size == n_T
     pr = F.Problem()
     pr.discretize(wl.curve, wl.omega, wl.N)
     pr.window_spectra(wl.a, wl.t0, wl.dt, wl.H)
@@ -65,6 +74,15 @@ def test_static_scratch_rejects_oversize():
     d_V = torch.zeros(2 * J, device=dev, dtype=torch.float64)
     d_T = torch.zeros(n_T, device=dev, dtype=torch.float64)
     d_u = torch.zeros(n_T, device=dev, dtype=torch.float64)
+    with pytest.raises(F.FHError) as e:
+        F.fh_synthesize_static(J, 10.0, d_s, d_B, d_V, d_T, d_u)
+    assert e.value.status == F.FH_EINVAL
+    # too many windows for the weights kernel's shared memory at J = 2049
+    K = 2049
+    d_s = torch.zeros(K, device=dev, dtype=torch.float64)
+    d_B = torch.zeros(2 * K * J, device=dev, dtype=torch.float64)
+    d_T = torch.zeros(10, device=dev, dtype=torch.float64)
+    d_u = torch.zeros(10, device=dev, dtype=torch.float64)
     with pytest.raises(F.FHError) as e:
         F.fh_synthesize_static(J, 10.0, d_s, d_B, d_V, d_T, d_u)
     assert e.value.status == F.FH_EINVAL
