@@ -384,6 +384,15 @@ fh_status fh_tc_gemm_test(int kind, int M, int N, int K, const float *A, const f
  * which the ALU-bound kernels are reported. */
 fh_status fh_probe_fma_peak(int device, int fp64, int iters, double *tflops);
 
+/* Measured dense tensor-core throughput of device `device` in TFLOP/s: one
+ * CTA per SM issues `iters` (>= 2) back-to-back tcgen05 MMAs of 128 x 256
+ * outputs and one K step from operands resident in shared memory, FP32
+ * accumulation in tensor memory; kind 1 = BF16 operands (kind::f16), 2 = TF32
+ * (kind::tf32).  Best of two timed runs.  Not part of the scattering path: it
+ * is the peak against which the tensor-core LU and contraction are reported.
+ * FH_ETIMEOUT if the bounded completion wait gave up. */
+fh_status fh_probe_mma_peak(int device, int kind, int iters, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -357,6 +357,15 @@ def fh_probe_fma_peak(device: int = 0, fp64: bool = True, iters: int = 4096) -> 
     return v.value
 
 
+def fh_probe_mma_peak(device: int = 0, kind: int = 2, iters: int = 20000) -> float:
+    """Dense tcgen05 throughput in TFLOP/s (kind 1 = BF16, 2 = TF32)."""
+    v = C.c_double()
+    st = load_library().fh_probe_mma_peak(int(device), int(kind), int(iters), C.byref(v))
+    if st != FH_OK:
+        raise FHError(st, "fh_probe_mma_peak failed")
+    return v.value
+
+
 def fh_eval_bessel(x):
     """(n, 6) array: J0, Y0, J1, Y1 (joint routine), J0, Y0 (H0 routine)."""
     xv = _f64(x)
