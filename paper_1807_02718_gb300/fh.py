@@ -33,7 +33,7 @@ EXPORTED = [
     "fh_eval_bessel", "fh_synthesize_static", "fh_discretize_batch", "fh_num_problems",
     "fh_window_spectra_p", "fh_window_spectra_p_dev", "fh_sample_p", "fh_sample_p_dev",
     "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test", "fh_eval_bessel_df", "fh_set_graphs",
-    "fh_get_tuning", "fh_set_tuning", "fh_autotune",
+    "fh_get_tuning", "fh_set_tuning", "fh_autotune", "fh_probe_mma_peak",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "refine", "spectra", "field", "weights", "contract"]
@@ -104,6 +104,7 @@ def load_library(path: str | None = None):
         "fh_set_timing": (C.c_int, [vp, C.c_int]),
         "fh_get_timings": (C.c_int, [vp, C.POINTER(fh_timings), C.c_int]),
         "fh_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
+        "fh_probe_mma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
         "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_eval_bessel_df": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_set_graphs": (C.c_int, [vp, C.c_int]),
