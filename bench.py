@@ -281,6 +281,12 @@ def _oracle_jobs(out_path, jobs):
     before the parent touches the GPU) while the GPU legs run.  Writes an .npz
     of results and timings."""
     sys.path.insert(0, ROOT)
+    try:    # leave the first two cores to the process driving the GPU
+        cores = sorted(os.sched_getaffinity(0))
+        if len(cores) > 4:
+            os.sched_setaffinity(0, cores[2:])
+    except (AttributeError, OSError):
+        pass
     import oracle as O
     res = {}
     if "kite_pulses_full" in jobs:
@@ -323,22 +329,33 @@ def _oracle_jobs(out_path, jobs):
 
 
 def start_oracle(jobs):
-    """Spawn the oracle process (before any CUDA call in this process)."""
+    """Spawn the oracle process (before any CUDA call in this process).  It
+    runs on all host cores but the first two (BLAS threads set to match), so
+    that the thread launching the GPU work is not starved."""
     fd, path = tempfile.mkstemp(suffix=".npz")
     os.close(fd)
+    n = max(1, cpu_cores() - 2) if cpu_cores() > 4 else cpu_cores()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ.update(OMP_NUM_THREADS=str(n), OPENBLAS_NUM_THREADS=str(n))
     ctx = mp.get_context("spawn")
     p = ctx.Process(target=_oracle_jobs, args=(path, jobs), daemon=True)
     p.start()
-    return p, path
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    return p, path, n
 
 
-def finish_oracle(p, path, timeout=900):
+def finish_oracle(p, path, threads, timeout=900):
     p.join(timeout)
     if p.is_alive():
         p.terminate()
         return None
     try:
         d = dict(np.load(path))
+        d["threads"] = threads
     except Exception:
         d = None
     try:
@@ -349,11 +366,15 @@ def finish_oracle(p, path, timeout=900):
 
 
 def n3_fit(N, t):
-    """Least-squares t = c3 N^3 + c2 N^2 over the sampled solves."""
+    """Non-negative least squares t = c0 + c2 N^2 + c3 N^3 over the sampled
+    solves (assembly ~ N^2, LU ~ N^3, a fixed per-solve cost); returns
+    (c0, c2, c3)."""
+    from scipy.optimize import nnls
     N = np.asarray(N, dtype=float)
-    A = np.stack([N ** 3, N ** 2], 1)
-    c, *_ = np.linalg.lstsq(A, np.asarray(t, dtype=float), rcond=None)
-    return c
+    A = np.stack([np.ones_like(N), N ** 2, N ** 3], 1)
+    sc = A.max(axis=0)
+    c, _ = nnls(A / sc, np.asarray(t, dtype=float))
+    return c / sc
 
 
 def oracle_solve_sample(wl, stride, offset):
@@ -717,15 +738,15 @@ def run_gpu(args, world, rank, local):
                 # cpu_baseline: the oracle's solves of the sampled frequencies
                 c = n3_fit(od["kw_N"], od["kw_t"])
                 Nw = wl.N[1:].astype(float)
-                est_solves = float(np.sum(c[0] * Nw ** 3 + c[1] * Nw ** 2))
+                est_solves = float(np.sum(c[0] + c[1] * Nw ** 2 + c[2] * Nw ** 3))
                 est_step = est_solves + float(od["kw_t_synth16"]) * n_x / 16
                 cpu = {"value": len(od["kw_t"]) / float(np.sum(od["kw_t"])), "unit": "solves/s",
-                       "cores": cpu_cores(), "kind": "oracle",
+                       "cores": int(od["threads"]), "kind": "oracle",
                        "sample": (f"oracle solves at {len(od['kw_t'])} frequencies j in "
                                   f"{list(map(int, od['kw_j']))} (N {int(min(od['kw_N']))}.."
                                   f"{int(max(od['kw_N']))}), {float(np.sum(od['kw_t'])):.1f} s, run "
                                   "in a process beside the GPU legs; solves/s = solves done / time"),
-                       "n3_fit_s": {"c3": float(c[0]), "c2": float(c[1])},
+                       "n3_fit_s": {"c0": float(c[0]), "c2": float(c[1]), "c3": float(c[2])},
                        "est_full_step_s": est_step,
                        "est_full_step_note": "N^3 fit over the sampled solves for all 511 solves + "
                                              "spectra and synthesis timed for 16 targets x 4096 "
@@ -738,7 +759,7 @@ def run_gpu(args, world, rank, local):
                                     "targets, synthesis at 4096 times), timed once"}
                 if cpu is None:
                     cpu = {"value": cpu_full["solves_per_s"], "unit": "solves/s",
-                           "cores": cpu_cores(), "kind": "oracle", "sample": cpu_full["note"]}
+                           "cores": int(od["threads"]), "kind": "oracle", "sample": cpu_full["note"]}
                 cpu["full_step_kite_pulses"] = cpu_full
 
     if rank == 0:
