@@ -120,6 +120,12 @@ struct fh_ctx {
     DevBuf d_stab;
     DevBuf d_A32, d_piv, d_g, d_iters, d_resid, d_tcerr, d_y32, d_rstate, d_rchunk, d_Bf, d_dblk,
         d_blk_off, d_dinv;
+    // tensor-core LU work space: tensor maps of the FP32 matrices, staged
+    // operand tiles and their offsets; valid for (lu_key_ptr, lu_key_gen)
+    DevBuf d_lu_maps, d_lu_opnd, d_lu_aoff, d_lu_boff;
+    void *lu_key_ptr = nullptr;
+    long long lu_key_gen = -1;
+    int lu_key_kind = 0;
     int n_rchunk = 0, n_dblk = 0;
     int n_rchunk_early = 0, n_dblk_early = 0;   // entries of the lu_early systems (listed first)
     DevBuf d_wa, d_a;
@@ -150,7 +156,8 @@ struct fh_ctx {
                          &d_kappa, &d_eta, &d_solve_j, &d_solve_prob, &d_order, &d_curves,
                          &d_pdir, &d_zf, &d_dzf, &d_sf, &d_wpf, &d_z, &d_dz, &d_ddz, &d_kress, &d_logsin, &d_A, &d_psi,
                          &d_info, &d_nu, &d_nu_f, &d_ph, &d_omega, &d_pw, &d_stab, &d_A32, &d_piv, &d_g, &d_iters,
-                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_Gs, &d_Vs, &d_ctc, &d_ctc_err,
+                         &d_resid, &d_tcerr, &d_y32, &d_rstate, &d_rchunk, &d_Bf, &d_dblk, &d_blk_off, &d_dinv,
+                         &d_lu_maps, &d_lu_opnd, &d_lu_aoff, &d_lu_boff, &d_wa, &d_a, &d_x, &d_T, &d_u, &d_V, &d_Gr, &d_Gm, &d_Gs, &d_Vs, &d_ctc, &d_ctc_err,
                          &d_tmpA, &d_tmpg, &d_tmp_ll, &d_tmp_d, &d_tmp_i};
         for (DevBuf *b : all) free_buf(*b);
         free_problems();
@@ -1054,6 +1061,31 @@ fh_status assemble_range(fh_ctx *ctx, int g0, int g1, int s0, int s1) {
 
 fh_status assemble_kernels(fh_ctx *ctx) { return assemble_range(ctx, 0, ctx->n_groups, 0, ctx->S); }
 
+// Tensor maps of the row-major FP32 matrices and the staged-operand buffer
+// of the tensor-core LU, rebuilt when the matrices move or the
+// discretization changes (before any launch sequence is captured).
+fh_status ensure_tc_work(fh_ctx *ctx) {
+    const int kind = ctx->precision == FH_MIXED_TF32 ? 2 : 1;
+    if (ctx->lu_key_ptr == ctx->d_A32.p && ctx->lu_key_gen == ctx->disc_gen && ctx->lu_key_kind == kind &&
+        ctx->d_lu_maps.p)
+        return FH_OK;
+    std::vector<long long> aoff(ctx->S), boff(ctx->S);
+    const size_t bytes = fh::lu_tc_opnd_bytes(kind, ctx->solve_N.data(), ctx->S, aoff.data(), boff.data());
+    FH_TRY(ensure(ctx, ctx->d_lu_opnd, bytes));
+    std::vector<unsigned char> maps(fh::lu_tc_map_bytes(ctx->S));
+    const cudaError_t e = fh::lu_tc_encode_maps(ctx->solve_N.data(), ctx->mat_off.data(), ctx->S,
+                                                ctx->d_A32.as<float2>(), maps.data());
+    if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "tensor map encoding failed: %s", cudaGetErrorString(e));
+    FH_TRY(upload(ctx, ctx->d_lu_maps, maps));
+    FH_TRY(upload(ctx, ctx->d_lu_aoff, aoff));
+    FH_TRY(upload(ctx, ctx->d_lu_boff, boff));
+    FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the host staging vectors go out of scope
+    ctx->lu_key_ptr = ctx->d_A32.p;
+    ctx->lu_key_gen = ctx->disc_gen;
+    ctx->lu_key_kind = kind;
+    return FH_OK;
+}
+
 // Row-major FP32 copies and tensor-core LU of the solves order[s0 .. s1-1]
 // (d_info and d_tcerr are cleared by the caller).
 fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1) {
@@ -1064,7 +1096,10 @@ fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1) {
         ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>() + s0,
         ctx->order.data() + s0, ctx->solve_N.data(), s1 - s0, ctx->d_N.as<int>(),
         ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),
-        ctx->d_vec_off.as<int>(), ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(), ctx->stream);
+        ctx->d_vec_off.as<int>(), ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(),
+        fh::LuTcWork{ctx->d_lu_maps.p, ctx->d_lu_opnd.as<uint8_t>(), ctx->d_lu_aoff.as<long long>(),
+                     ctx->d_lu_boff.as<long long>()},
+        ctx->stream);
     if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
     return FH_OK;
 }
@@ -1223,6 +1258,7 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         if (tc) {
             FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
             FH_TRY(ensure(ctx, ctx->d_dinv, (size_t)ctx->n_dblk * 2048 * sizeof(float2)));
+            FH_TRY(ensure_tc_work(ctx));
         }
     }
     const long long key = graph_key(ctx, 0, 0, 0, 0, 0);
@@ -1660,6 +1696,7 @@ fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_ou
         FH_TRY(ensure(ctx, ctx->d_piv, (size_t)ctx->vec_total * sizeof(int)));
         FH_TRY(ensure(ctx, ctx->d_info, (size_t)ctx->S * sizeof(int)));
         FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
+        FH_TRY(ensure_tc_work(ctx));
         FH_TRY(assemble_kernels(ctx));
         std::vector<int> info(ctx->S);
         FH_TRY(tune_field(ctx, reps, &fh_tuning::lu_rows_per_cta, {512, 256, 128}, ms_out[1], [&]() {

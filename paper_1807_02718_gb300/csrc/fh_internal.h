@@ -124,10 +124,26 @@ int lu_tc_launches(const int *order_h, const int *N_h, int S, int rows_per_cta);
 // Row-major FP32 copies of the count solves in the device list list.
 void launch_convert_rowmajor(const int *list, int count, const int *N, const long long *mat_off,
                              const float4 *Af, float2 *A32, cudaStream_t st);
+// Work space of the tensor-core LU (indexed by solve, like N and mat_off):
+// maps: S tensor maps of the row-major FP32 matrices (lu_tc_encode_maps,
+// copied to the device); opnd: the staged operand tiles of every system,
+// system s's L21 tiles at byte a_off[s] and U12 tiles at b_off[s]
+// (lu_tc_opnd_bytes fills host copies of the offsets and returns the size).
+struct LuTcWork {
+    const void *maps;
+    uint8_t *opnd;
+    const long long *a_off, *b_off;
+};
+size_t lu_tc_opnd_bytes(int kind, const int *N_h, int S, long long *a_off_h, long long *b_off_h);
+size_t lu_tc_map_bytes(int S);
+// Host: encodes the tensor maps of systems 0..S-1 (matrix s at A32 +
+// mat_off_h[s], order N_h[s]) into maps_h (lu_tc_map_bytes(S) bytes).
+cudaError_t lu_tc_encode_maps(const int *N_h, const long long *mat_off_h, int S, float2 *A32, void *maps_h);
 cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, const int *order_h,
                                 const int *N_h, int S,
                                 const int *N, const long long *mat_off, float2 *A32, int *piv,
-                                const int *vec_off, int *info, int *err, cudaStream_t st);
+                                const int *vec_off, int *info, int *err, const LuTcWork &w,
+                                cudaStream_t st);
 // Iterative refinement against the column-major double-float matrices Af
 // (residuals with exact products and double-float sums); chunks
 // lists (solve, first row) per kResidRows rows; state holds

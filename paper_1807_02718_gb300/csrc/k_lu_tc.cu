@@ -30,14 +30,25 @@
 //      each CTA over its own column range, through shared memory;
 //   3. U12 = L11^{-1} A12 by forward substitution, one column per thread, over
 //      the same column ranges;
-//   4. A22 -= L21 U12: 128-row tiles are dealt round-robin to the CTAs; per
-//      row tile the A operand is staged once and 64-column B tiles are
-//      double-buffered, so that staging and the epilogue of one tile overlap
-//      the MMAs of the next (two 128-column TMEM accumulators).
+//   4. A22 -= L21 U12: 128-row tiles are dealt round-robin to the CTAs and
+//      processed by three warp roles over a two-stage pipeline: one thread
+//      (the producer) brings in the operand tiles with the TMA engine -- the
+//      split L21 rows (bulk copy, once per row tile) and the split U12
+//      columns (bulk copy, per 32-column tile), both written in the MMA's
+//      shared-memory layout by steps 2 and 3, and the C tile of the row-major
+//      matrix (tiled tensor load, 128-byte swizzle) -- one thread issues the
+//      MMAs into one of two TMEM accumulators, and eight epilogue warps
+//      subtract the accumulator from the C tile in shared memory and write it
+//      back with a tiled tensor store.  Stages are handed over through
+//      mbarriers (bounded waits).
 // Cluster barriers separate the steps; a cluster of one uses __syncthreads.
 #include <climits>
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <mutex>
 
 #include "fh_internal.h"
 #include "tc_gemm.cuh"
@@ -56,10 +67,16 @@ constexpr int kMaxCluster = 8;
 constexpr int kMaxMoved = 2 * NB;
 constexpr int kATile = TR * 2 * NB * 4;        // A operand (hi or lo) at 4 bytes per element: 32 KiB
 constexpr int kBTile = 2 * TCC * 2 * NB * 4;   // B operand (hi or lo): 16 KiB
-constexpr int kXPitch = 5;                     // float4 per row of an epilogue transpose buffer
-constexpr int kXBytes = kWarps * 32 * kXPitch * 16;   // 40 KiB
-constexpr int kDynSmem = 1024 + 2 * kATile + 4 * kBTile + kXBytes;
+constexpr int kCBox = TR * 32 * 4;             // one 128 x 32-float box of a C tile: 16 KiB
+constexpr int kDynSmem = 1024 + 2 * kATile + 4 * kBTile + 4 * kCBox;
 constexpr long long kWaitLimit = 1LL << 22;
+constexpr int kEpiWarp0 = 4, kEpiWarps = 8;    // epilogue warps 4 .. 11
+constexpr int kEpiThreads = 32 * kEpiWarps;
+
+// Bytes of one operand tile (hi or lo) of each kind: A is 128 L21 rows, B 64
+// rows (32 complex columns x {Re, Im}) of the 2 NB-long K dimension.
+template <int kKind> __host__ __device__ constexpr int a_tile_bytes() { return TR * 2 * NB * (kKind == 2 ? 4 : 2); }
+template <int kKind> __host__ __device__ constexpr int b_tile_bytes() { return 2 * TCC * 2 * NB * (kKind == 2 ? 4 : 2); }
 
 template <int kKind> struct Op;
 template <> struct Op<2> {              // TF32
@@ -141,82 +158,55 @@ __device__ __forceinline__ void key_max(uint32_t h, uint32_t l, uint32_t &mh, ui
     ml = __reduce_max_sync(0xffffffffu, h == mh ? l : 0u);
 }
 
-// A operand: rows i0 .. i0+127 of L21 (panel columns k0 .. k0+nb-1), K-major.
+// Step 2: row `r` (0..127) of L21 tile `tile` in the MMA operand layout
+// (K-major core matrices, hi tile then lo tile), from the 32 complex panel
+// values of that row.
 template <int kKind>
-__device__ __forceinline__ void stage_a(const float2 *__restrict__ a, int n, int k0, int nb, int i0,
-                                        uint8_t *sh, uint8_t *sl) {
-    constexpr int qpc = Op<kKind>::qpc, kChunks = NB / qpc, kRowB = 2 * NB * Op<kKind>::esize;
-    for (int e = threadIdx.x; e < TR * kChunks; e += kThreads) {
-        const int r = e & (TR - 1), c = e / TR;
-        const int i = i0 + r, q0 = c * qpc;
-        float v[2 * qpc];
+__device__ __forceinline__ void put_a_row(uint8_t *tiles, int tile, int r, const float2 (&v)[NB]) {
+    constexpr int qpc = Op<kKind>::qpc, kRowB = 2 * NB * Op<kKind>::esize, kT = a_tile_bytes<kKind>();
+    uint8_t *hi = tiles + (size_t)tile * 2 * kT, *lo = hi + kT;
 #pragma unroll
-        for (int h = 0; h < qpc / 2; ++h) {
-            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < n && q0 + 2 * h < nb)
-                t = __ldcg(reinterpret_cast<const float4 *>(a + (long long)i * n + k0 + q0 + 2 * h));
-            v[4 * h] = t.x;
-            v[4 * h + 1] = t.y;
-            v[4 * h + 2] = t.z;
-            v[4 * h + 3] = t.w;
-        }
-        const uint32_t off = tc::kmajor_offset(r, c * 16, kRowB);
-        split_store<kKind>(v, sh + off, sl + off);
-    }
-}
-
-// B operand for complex columns j0 .. j0+TCC-1 of U12: row 2jj gives Re, row
-// 2jj+1 gives Im of output column j0+jj.  load_b reads this thread's
-// kBElems elements (qpc complex values each) into registers, store_b splits
-// them into the K-major hi and lo tiles, so that the loads of the next tile
-// can be in flight during the current tile's epilogue.
-template <int kKind>
-struct BRegs {
-    static constexpr int qpc = Op<kKind>::qpc, kChunks = NB / qpc;
-    static constexpr int kElems = 2 * TCC * kChunks / kThreads;
-    float2 u[kElems][qpc];
-};
-
-template <int kKind>
-__device__ __forceinline__ void load_b(const float2 *__restrict__ a, int n, int k0, int nb, int j0,
-                                       BRegs<kKind> &rb) {
-    constexpr int qpc = Op<kKind>::qpc;
-#pragma unroll
-    for (int m = 0; m < BRegs<kKind>::kElems; ++m) {
-        const int e = threadIdx.x + m * kThreads;
-        const int b = e & (2 * TCC - 1), c = e / (2 * TCC);
-        const int j = j0 + (b >> 1), q0 = c * qpc;
-#pragma unroll
-        for (int h = 0; h < qpc; ++h)
-            rb.u[m][h] = (j < n && q0 + h < nb) ? __ldcg(a + (long long)(k0 + q0 + h) * n + j)
-                                                : make_float2(0.f, 0.f);
-    }
-}
-
-template <int kKind>
-__device__ __forceinline__ void store_b(const BRegs<kKind> &rb, uint8_t *sh, uint8_t *sl) {
-    constexpr int qpc = Op<kKind>::qpc, kRowB = 2 * NB * Op<kKind>::esize;
-#pragma unroll
-    for (int m = 0; m < BRegs<kKind>::kElems; ++m) {
-        const int e = threadIdx.x + m * kThreads;
-        const int b = e & (2 * TCC - 1), c = e / (2 * TCC);
-        const bool im = b & 1;
-        float v[2 * qpc];
+    for (int c = 0; c < NB / qpc; ++c) {
+        float w[2 * qpc];
 #pragma unroll
         for (int h = 0; h < qpc; ++h) {
-            const float2 u = rb.u[m][h];
-            v[2 * h] = im ? u.y : u.x;
-            v[2 * h + 1] = im ? u.x : -u.y;
+            w[2 * h] = v[c * qpc + h].x;
+            w[2 * h + 1] = v[c * qpc + h].y;
         }
-        const uint32_t off = tc::kmajor_offset(b, c * 16, kRowB);
-        split_store<kKind>(v, sh + off, sl + off);
+        const uint32_t off = tc::kmajor_offset(r, c * 16, kRowB);
+        split_store<kKind>(w, hi + off, lo + off);
     }
 }
 
-// One 128 x 64 complex tile: hi*hi + hi*lo + lo*hi over the panel's K.
+// Step 3: the two B rows of U12 column `jj` (local to the trailing block):
+// row 2 (jj % 32) gives Re, row 2 (jj % 32) + 1 gives Im of output column jj,
+// in B tile jj / 32.  u[q] = U12(q, jj).
+template <int kKind>
+__device__ __forceinline__ void put_b_col(uint8_t *tiles, int jj, const float2 *u) {
+    constexpr int qpc = Op<kKind>::qpc, kRowB = 2 * NB * Op<kKind>::esize, kT = b_tile_bytes<kKind>();
+    uint8_t *hi = tiles + (size_t)(jj / TCC) * 2 * kT, *lo = hi + kT;
+    const int b = 2 * (jj % TCC);
+#pragma unroll
+    for (int c = 0; c < NB / qpc; ++c) {
+        float re[2 * qpc], im[2 * qpc];
+#pragma unroll
+        for (int h = 0; h < qpc; ++h) {
+            const float2 x = u[c * qpc + h];
+            re[2 * h] = x.x;
+            re[2 * h + 1] = -x.y;
+            im[2 * h] = x.y;
+            im[2 * h + 1] = x.x;
+        }
+        const uint32_t o0 = tc::kmajor_offset(b, c * 16, kRowB), o1 = tc::kmajor_offset(b + 1, c * 16, kRowB);
+        split_store<kKind>(re, hi + o0, lo + o0);
+        split_store<kKind>(im, hi + o1, lo + o1);
+    }
+}
+
+// One 128 x 32-complex tile: hi*hi + hi*lo + lo*hi over the panel's K.
 template <int kKind>
 __device__ __forceinline__ void issue_mma(uint32_t tacc, uint32_t ah, uint32_t al, uint32_t bh,
-                                          uint32_t bl, uint64_t *bar) {
+                                          uint32_t bl) {
     constexpr int kRowB = 2 * NB * Op<kKind>::esize;
     constexpr uint32_t sbo = (kRowB / 16) * 128;
     constexpr int ksteps = kRowB / 32;          // 32 bytes of K per MMA
@@ -230,50 +220,14 @@ __device__ __forceinline__ void issue_mma(uint32_t tacc, uint32_t ah, uint32_t a
         tc::mma<kKind>(tacc, dah, dbl, idesc, 1u);
         tc::mma<kKind>(tacc, dal, dbh, idesc, 1u);
     }
-    tc::mma_commit(bar);
 }
 
-// C(i0.., j0..) -= accumulator.  Warp w owns TMEM lanes 32 (w % 4) .. and
-// accumulator columns 16 (w / 4) .. (8 complex columns of each of its 32
-// rows).  C is read eight rows at a time, four lanes covering the 64
-// contiguous bytes of a row (epi_load, issued before the MMA wait); the
-// accumulator is passed through the warp's shared-memory buffer into the same
-// lane pattern (epi_store).
-__device__ __forceinline__ void epi_load(const float2 *__restrict__ a, int n, int i0, int j0, float4 (&c)[4]) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wq = warp & 3, wc = warp >> 2;
-    const int j = j0 + 8 * wc + 2 * (lane & 3);
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int i = i0 + 32 * wq + 8 * p + (lane >> 2);
-        c[p] = (i < n && j < n) ? __ldcg(reinterpret_cast<const float4 *>(a + (long long)i * n + j))
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
-
-__device__ __forceinline__ void epi_store(float2 *__restrict__ a, int n, int i0, int j0, uint32_t tacc,
-                                          float4 *sX, const float4 (&c)[4]) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wq = warp & 3, wc = warp >> 2;
-    float d[16];
-    tc::tmem_ld16(tacc + ((uint32_t)(32 * wq) << 16) + (uint32_t)(wc * 16), d);
-    float4 *buf = sX + warp * 32 * kXPitch;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        buf[lane * kXPitch + k] = make_float4(d[4 * k], d[4 * k + 1], d[4 * k + 2], d[4 * k + 3]);
-    __syncwarp();
-    const int k = lane & 3, j = j0 + 8 * wc + 2 * k;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int rr = 8 * p + (lane >> 2), i = i0 + 32 * wq + rr;
-        if (i < n && j < n) {
-            const float4 dv = buf[rr * kXPitch + k];
-            __stcg(reinterpret_cast<float4 *>(a + (long long)i * n + j),
-                   make_float4(c[p].x - dv.x, c[p].y - dv.y, c[p].z - dv.z, c[p].w - dv.w));
-        }
-    }
-    __syncwarp();
-}
+// Pipeline state of the trailing update, kept in shared memory: stage s of
+// the B and C buffers and of the TMEM accumulators is used by items s, s+2, ...
+struct Pipe {
+    uint64_t a_full, a_empty;
+    uint64_t b_full[2], b_empty[2], c_full[2], c_empty[2], acc_full[2], acc_empty[2];
+};
 
 // Pointer into the shared memory of CTA r of this system's cluster.
 template <typename T>
@@ -283,20 +237,26 @@ __device__ __forceinline__ T *at_rank(T *p, int cs, int r) {
 
 // Blocks [cs * c, cs * c + cs) factor system order[c].  On return piv holds
 // the inverse row permutation (original row i is row piv[i] of the factors).
+// tmaps[s]: tensor map of system s's row-major FP32 matrix (2n floats x n
+// rows, 32 x 128 boxes, 128-byte swizzle); opnd + a_off[s] / b_off[s]: the
+// system's staged L21 and U12 operand tiles (rewritten every panel).
 template <int kKind, bool kMulti>
 __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     const int *__restrict__ order, int cs_arg, const int *__restrict__ Ns,
     const long long *__restrict__ mat_off, const int *__restrict__ vec_off,
     float2 *__restrict__ A32, int *__restrict__ piv, int *__restrict__ info,
-    int *__restrict__ err) {
+    int *__restrict__ err, const CUtensorMap *__restrict__ tmaps, uint8_t *__restrict__ opnd,
+    const long long *__restrict__ a_off, const long long *__restrict__ b_off) {
     extern __shared__ uint8_t dsm[];
     __shared__ __align__(16) PanelShared ps;
+    __shared__ __align__(8) Pipe pp;
+    constexpr int kAT = a_tile_bytes<kKind>(), kBT = b_tile_bytes<kKind>();
     uint8_t *stage = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sAh = stage, *sAl = stage + kATile;
-    uint8_t *sB = stage + 2 * kATile;                                   // 2 x (hi, lo)
-    float4 *sX = reinterpret_cast<float4 *>(sB + 4 * kBTile);           // epilogue transposes
-    float4 *gbuf = reinterpret_cast<float4 *>(sB);                      // row gather (B + X)
-    constexpr int kGather = (4 * kBTile + kXBytes) / 16;                // float4 in gbuf
+    uint8_t *sA = stage;                                                // hi, lo
+    uint8_t *sB = stage + 2 * kATile;                                   // 2 stages x (hi, lo)
+    uint8_t *sC = sB + 4 * kBTile;                                      // 2 stages x 2 boxes (1 KiB aligned)
+    float4 *gbuf = reinterpret_cast<float4 *>(sB);                      // row gather (B + C)
+    constexpr int kGather = (4 * kBTile + 4 * kCBox) / 16;              // float4 in gbuf
 
     const int cs = kMulti ? cs_arg : 1;
     const int rank = kMulti ? (int)cg::this_cluster().block_rank() : 0;
@@ -304,13 +264,23 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     const int n = Ns[s];
     float2 *a = A32 + mat_off[s];
     int *pv = piv + vec_off[s];
+    const CUtensorMap *tmap = tmaps + s;
+    uint8_t *atiles = opnd + a_off[s], *btiles = opnd + b_off[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int myslot = rank * kThreads + tid;
 
     if (warp == 0) tc::tmem_alloc(&ps.tslot, 4 * TCC);
     if (tid == 0) {
-        tc::mbar_init(&ps.bar[0], 1);
-        tc::mbar_init(&ps.bar[1], 1);
+        tc::mbar_init(&pp.a_full, 1);
+        tc::mbar_init(&pp.a_empty, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&pp.b_full[b], 1);
+            tc::mbar_init(&pp.b_empty[b], 1);
+            tc::mbar_init(&pp.c_full[b], 1);
+            tc::mbar_init(&pp.c_empty[b], 1);
+            tc::mbar_init(&pp.acc_full[b], 1);
+            tc::mbar_init(&pp.acc_empty[b], kEpiWarps);
+        }
         ps.wait_failed = 0;
     }
     if (rank == 0)   // pv: factored position -> original row, while factoring
@@ -322,10 +292,12 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     const uint32_t taddr = ps.tslot;
     if (cs > 1) cg::this_cluster().sync();   // every CTA running before shared memory is addressed remotely
 
-    uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {false, false};
+    // pipeline counters: items (row tile, column tile) and row tiles this
+    // CTA has processed, over all panels; the producer also counts the loads
+    // it armed on each full barrier and the MMA thread its commits
+    long long n_item = 0, n_rowt = 0;
+    int armed_a = 0, armed_b[2] = {0, 0}, armed_c[2] = {0, 0}, commits[2] = {0, 0}, commits_a = 0;
     bool failed = false, bad = false;
-    int bsel = 0;
 
     for (int k0 = 0; k0 < n; k0 += NB) {
         const int nb = min(NB, n - k0), m = n - k0;
@@ -426,12 +398,15 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         }
         if (bad) break;
 
-        // 2. panel to its final rows; L11 and the moved rows to every CTA
+        // 2. panel to its final rows (and the L21 rows to the staged A
+        // operand); L11 and the moved rows to every CTA
         if (own) {
             float4 *dst = reinterpret_cast<float4 *>(a + (long long)(k0 + mypos) * n + k0);
 #pragma unroll
             for (int h = 0; h < NB / 2; ++h)
                 if (2 * h < nb) __stcg(dst + h, make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y));
+            if (mypos >= nb && nb == NB)
+                put_a_row<kKind>(atiles, (mypos - NB) / TR, (mypos - NB) % TR, v);
             if (mypos < nb)
                 for (int r = 0; r < cs; ++r) {
                     float2 *l = at_rank(&ps.l11[mypos][0], cs, r);
@@ -518,85 +493,183 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 for (int e = 0; e < 8; ++e)
                     if (8 * B + e < nb) col[(long long)(8 * B + e) * n] = xb[e];
             }
+            if (nb == NB) {   // the finished column to the staged B operand
+                float2 u[NB];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) u[q] = col[(long long)q * n];
+                put_b_col<kKind>(btiles, c - k0, u);
+            }
         }
+        // the swaps, U12 and the staged operands (generic stores to global
+        // memory) are read by the TMA engine below, which also overwrites the
+        // shared-memory gather buffer of the swaps
+        tc::fence_async_all();
         sys_sync(cs, true);
 
         // 4. A22 -= L21 U12 on the tensor cores
         const int r0 = k0 + nb, m2 = n - r0;
         if (m2 > 0) {
             const int nrt = (m2 + TR - 1) / TR, nct = (m2 + TCC - 1) / TCC;
-            for (int rt = rank; rt < nrt; rt += cs) {
-                const int i0 = r0 + rt * TR;
-                BRegs<kKind> rb;
-                load_b<kKind>(a, n, k0, nb, r0, rb);            // first column tile
-                stage_a<kKind>(a, n, k0, nb, i0, sAh, sAl);
-                int prev = -1, prev_j0 = 0;
-                float4 cprev[4], ccur[4];
-                for (int ct = 0; ct <= nct; ++ct) {
-                    const int b = bsel;
-                    const int j0 = r0 + ct * TCC;
-                    if (ct < nct) {
-                        uint8_t *bh = sB + 2 * b * kBTile, *bl = bh + kBTile;
-                        store_b<kKind>(rb, bh, bl);
-                        tc::fence_async_smem();
-                        tc::tc_fence_before();
-                        __syncthreads();
-                        tc::tc_fence_after();
-                        if (ps.wait_failed) failed = true;   // the same verdict in every thread
-                        const bool issue = !failed;
-                        if (tid == 0 && issue)
-                            issue_mma<kKind>(taddr + (uint32_t)(b * 2 * TCC), tc::smem_u32(sAh), tc::smem_u32(sAl),
-                                             tc::smem_u32(bh), tc::smem_u32(bl), &ps.bar[b]);
-                        pending[b] = issue;
-                        bsel ^= 1;
-                        // in flight while this tile multiplies and the previous one is
-                        // written back: the next tile's B and this tile's C
-                        if (ct + 1 < nct) load_b<kKind>(a, n, k0, nb, j0 + TCC, rb);
-                        epi_load(a, n, i0, j0, ccur);
+            const int my_rt = rank < nrt ? (nrt - 1 - rank) / cs + 1 : 0;   // row tiles of this CTA
+            if (tid == 0) {
+                // producer: A once per row tile, B and C per item
+                long long it = n_item, rtc = n_rowt;
+                for (int q = 0; q < my_rt && !failed; ++q, ++rtc) {
+                    const int rt = rank + q * cs, i0 = r0 + rt * TR;
+                    if (rtc > 0 && !tc::mbar_wait(&pp.a_empty, (uint32_t)((rtc - 1) & 1), kWaitLimit)) {
+                        failed = true;
+                        break;
                     }
-                    if (prev >= 0) {   // epilogue of the previous tile while this one multiplies
-                        // every thread waits for the completion itself (no barrier): its
-                        // accumulator reads and the reuse of the tile's B buffer two tiles
-                        // later follow its own wait; a give-up is shared through
-                        // ps.wait_failed at the next barrier
-                        bool got = true;
-                        if (pending[prev]) {
-                            got = tc::mbar_wait(&ps.bar[prev], phase[prev], kWaitLimit);
-                            phase[prev] ^= 1u;
-                            pending[prev] = false;
-                        }
-                        tc::tc_fence_after();
-                        if (!got) {
+                    tc::mbar_arrive_tx(&pp.a_full, 2 * kAT);
+                    tc::bulk_load(sA, atiles + (size_t)rt * 2 * kAT, 2 * kAT, &pp.a_full);
+                    ++armed_a;
+                    for (int ct = 0; ct < nct; ++ct, ++it) {
+                        const int st = (int)(it & 1);
+                        const long long u = it >> 1;
+                        if (u > 0 && (!tc::mbar_wait(&pp.b_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit) ||
+                                      !tc::mbar_wait(&pp.c_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
                             failed = true;
-                            ps.wait_failed = 1;
+                            break;
                         }
-                        if (!failed) epi_store(a, n, i0, prev_j0, taddr + (uint32_t)(prev * 2 * TCC), sX, cprev);
-                        tc::tc_fence_before();
+                        uint8_t *bdst = sB + st * 2 * kBTile, *cdst = sC + st * 2 * kCBox;
+                        tc::mbar_arrive_tx(&pp.b_full[st], 2 * kBT);
+                        tc::bulk_load(bdst, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[st]);
+                        ++armed_b[st];
+                        const int x = 2 * (r0 + ct * TCC);
+                        tc::mbar_arrive_tx(&pp.c_full[st], 2 * kCBox);
+                        tc::tma_load_2d(cdst, tmap, x, i0, &pp.c_full[st]);
+                        tc::tma_load_2d(cdst + kCBox, tmap, x + 32, i0, &pp.c_full[st]);
+                        ++armed_c[st];
                     }
+                }
+                if (failed) ps.wait_failed = 1;
+            } else if (tid == 32) {
+                // MMA issuer
+                long long it = n_item, rtc = n_rowt;
+                for (int q = 0; q < my_rt && !failed; ++q, ++rtc) {
+                    if (!tc::mbar_wait(&pp.a_full, (uint32_t)(rtc & 1), kWaitLimit)) {
+                        failed = true;
+                        break;
+                    }
+                    for (int ct = 0; ct < nct; ++ct, ++it) {
+                        const int st = (int)(it & 1);
+                        const long long u = it >> 1;
+                        if (!tc::mbar_wait(&pp.b_full[st], (uint32_t)(u & 1), kWaitLimit) ||
+                            (u > 0 && !tc::mbar_wait(&pp.acc_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
+                            failed = true;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t bh = tc::smem_u32(sB + st * 2 * kBTile);
+                        issue_mma<kKind>(taddr + (uint32_t)(st * 2 * TCC), tc::smem_u32(sA),
+                                         tc::smem_u32(sA) + kAT, bh, bh + kBT);
+                        tc::mma_commit(&pp.acc_full[st]);
+                        tc::mma_commit(&pp.b_empty[st]);
+                        ++commits[st];
+                        if (ct == nct - 1) {
+                            tc::mma_commit(&pp.a_empty);
+                            ++commits_a;
+                        }
+                    }
+                    if (failed) break;
+                }
+                if (failed) ps.wait_failed = 1;
+            } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
+                // epilogue: C -= accumulator in shared memory, tiled store
+                const int ew = warp - kEpiWarp0;
+                const int lg = warp & 3, half = ew >> 2;      // TMEM lane group, column half (box)
+                const int r = 32 * lg + lane;                 // tile row
+                long long it = n_item;
+                bool stop = false;
+                for (int q = 0; q < my_rt && !stop && !failed; ++q) {
+                    const int rt = rank + q * cs, i0 = r0 + rt * TR;
+                    for (int ct = 0; ct < nct; ++ct, ++it) {
+                        const int st = (int)(it & 1);
+                        const uint32_t par = (uint32_t)((it >> 1) & 1);
+                        bool got = tc::mbar_wait(&pp.acc_full[st], par, kWaitLimit);
+                        got = got && tc::mbar_wait(&pp.c_full[st], par, kWaitLimit);
+                        if (tc::bar_or(1, kEpiThreads, !got)) {   // the same verdict in every epilogue thread
+                            stop = true;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        float d[32];
+                        const uint32_t tacc = taddr + (uint32_t)(st * 2 * TCC) + ((uint32_t)(32 * lg) << 16) +
+                                              (uint32_t)(32 * half);
+                        tc::tmem_ld16(tacc, *reinterpret_cast<float(*)[16]>(d));
+                        tc::tmem_ld16(tacc + 16, *reinterpret_cast<float(*)[16]>(d + 16));
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&pp.acc_empty[st]);
+                        float4 *row = reinterpret_cast<float4 *>(sC + st * 2 * kCBox + half * kCBox + r * 128);
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) cprev[p] = ccur[p];
-                    prev = b;
-                    prev_j0 = j0;
+                        for (int c = 0; c < 8; ++c) {
+                            float4 *pc = row + (c ^ (r & 7));     // 128-byte swizzle of the box
+                            float4 x = *pc;
+                            x.x -= d[4 * c];
+                            x.y -= d[4 * c + 1];
+                            x.z -= d[4 * c + 2];
+                            x.w -= d[4 * c + 3];
+                            *pc = x;
+                        }
+                        tc::fence_async_smem();
+                        tc::bar_named(1, kEpiThreads);
+                        if (ew == 0 && lane == 0) {
+                            const int x = 2 * (r0 + ct * TCC);
+                            uint8_t *src = sC + st * 2 * kCBox;
+                            tc::tma_store_2d(tmap, x, i0, src);
+                            tc::tma_store_2d(tmap, x + 32, i0, src + kCBox);
+                            tc::bulk_commit();
+                            tc::bulk_wait_read();
+                            tc::mbar_arrive(&pp.c_empty[st]);
+                        }
+                    }
+                }
+                if (stop) {
+                    failed = true;
+                    if (ew == 0 && lane == 0) ps.wait_failed = 1;
+                }
+                if (ew == 0 && lane == 0) {   // the stores are in global memory before the next panel reads them
+                    tc::bulk_wait_all();
+                    tc::fence_async_global();
                 }
             }
+            // every thread advances the counters identically
+            n_item += (long long)my_rt * nct;
+            n_rowt += my_rt;
+            // drain: the producer's loads and the MMAs have landed (a no-op
+            // unless a wait gave up) before the buffers are reused
+            if (tid == 0) {
+                if (armed_a) tc::mbar_wait(&pp.a_full, (uint32_t)((armed_a - 1) & 1), kWaitLimit);
+                for (int b = 0; b < 2; ++b) {
+                    if (armed_b[b]) tc::mbar_wait(&pp.b_full[b], (uint32_t)((armed_b[b] - 1) & 1), kWaitLimit);
+                    if (armed_c[b]) tc::mbar_wait(&pp.c_full[b], (uint32_t)((armed_c[b] - 1) & 1), kWaitLimit);
+                }
+            } else if (tid == 32) {
+                for (int b = 0; b < 2; ++b)
+                    if (commits[b]) {
+                        tc::mbar_wait(&pp.acc_full[b], (uint32_t)((commits[b] - 1) & 1), kWaitLimit);
+                        tc::mbar_wait(&pp.b_empty[b], (uint32_t)((commits[b] - 1) & 1), kWaitLimit);
+                    }
+                if (commits_a) tc::mbar_wait(&pp.a_empty, (uint32_t)((commits_a - 1) & 1), kWaitLimit);
+            }
+            tc::fence_async_smem();   // the staging buffers are reused by generic accesses next
+            tc::tc_fence_before();
+            __syncthreads();
+            tc::tc_fence_after();
+            if (ps.wait_failed) failed = true;
         }
         sys_sync(cs, true);
     }
 
     __syncthreads();
     if (ps.wait_failed) failed = true;
-    // after a failed wait, let any MMA still in flight finish before freeing
-    for (int b = 0; b < 2; ++b)
-        if (pending[b]) {
-            tc::mbar_wait(&ps.bar[b], phase[b], kWaitLimit);
-            pending[b] = false;
-        }
     if (failed && tid == 0) {
         atomicOr(err, 1);
         info[s] = -2;
     }
     if (!bad && rank == 0) {   // position -> row  into  row -> position
-        int *perm = reinterpret_cast<int *>(sAh);
+        int *perm = reinterpret_cast<int *>(sA);
         __syncthreads();
         for (int i = tid; i < n; i += kThreads) perm[i] = pv[i];
         __syncthreads();
@@ -640,7 +713,8 @@ __global__ void __launch_bounds__(256) convert_rowmajor_kernel(const int *__rest
 
 template <int kKind>
 cudaError_t launch_group(const int *order, int count, int cs, const int *N, const long long *mat_off,
-                         float2 *A32, int *piv, const int *vec_off, int *info, int *err, cudaStream_t st) {
+                         float2 *A32, int *piv, const int *vec_off, int *info, int *err,
+                         const LuTcWork &w, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(count * cs));
     cfg.blockDim = dim3(kThreads);
@@ -653,11 +727,12 @@ cudaError_t launch_group(const int *order, int count, int cs, const int *N, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    const CUtensorMap *maps = static_cast<const CUtensorMap *>(w.maps);
     if (cs == 1)
         return cudaLaunchKernelEx(&cfg, lu_factor_tc_kernel<kKind, false>, order, cs, N, mat_off,
-                                  vec_off, A32, piv, info, err);
+                                  vec_off, A32, piv, info, err, maps, w.opnd, w.a_off, w.b_off);
     return cudaLaunchKernelEx(&cfg, lu_factor_tc_kernel<kKind, true>, order, cs, N, mat_off, vec_off,
-                              A32, piv, info, err);
+                              A32, piv, info, err, maps, w.opnd, w.a_off, w.b_off);
 }
 
 }  // namespace
@@ -687,10 +762,60 @@ void launch_convert_rowmajor(const int *list, int count, const int *N, const lon
     convert_rowmajor_kernel<<<dim3(count, 16), dim3(32, 8), 0, st>>>(list, N, mat_off, A, A32);
 }
 
+size_t lu_tc_opnd_bytes(int kind, const int *N_h, int S, long long *a_off_h, long long *b_off_h) {
+    const size_t at = kind == 2 ? a_tile_bytes<2>() : a_tile_bytes<1>();
+    const size_t bt = kind == 2 ? b_tile_bytes<2>() : b_tile_bytes<1>();
+    size_t off = 0;
+    for (int s = 0; s < S; ++s) {
+        const int m2 = std::max(N_h[s] - NB, 0);
+        if (a_off_h) a_off_h[s] = (long long)off;
+        off += (size_t)((m2 + TR - 1) / TR) * 2 * at;
+        if (b_off_h) b_off_h[s] = (long long)off;
+        off += (size_t)((m2 + TCC - 1) / TCC) * 2 * bt;
+    }
+    return std::max(off, (size_t)16);
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+}  // namespace
+
+size_t lu_tc_map_bytes(int S) { return (size_t)std::max(S, 1) * sizeof(CUtensorMap); }
+
+cudaError_t lu_tc_encode_maps(const int *N_h, const long long *mat_off_h, int S, float2 *A32, void *maps_h) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap *m = static_cast<CUtensorMap *>(maps_h);
+    for (int s = 0; s < S; ++s) {
+        const cuuint64_t n = (cuuint64_t)N_h[s];
+        const cuuint64_t dims[2] = {2 * n, n};                   // floats per row, rows
+        const cuuint64_t strides[1] = {2 * n * sizeof(float)};   // bytes between rows
+        const cuuint32_t box[2] = {32, (cuuint32_t)TR};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = enc(&m[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, A32 + mat_off_h[s], dims, strides,
+                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, const int *order_h,
                                 const int *N_h, int S,
                                 const int *N, const long long *mat_off, float2 *A32, int *piv,
-                                const int *vec_off, int *info, int *err, cudaStream_t st) {
+                                const int *vec_off, int *info, int *err, const LuTcWork &w,
+                                cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     static std::atomic<unsigned long long> attr[4] = {{0}, {0}, {0}, {0}};
     {
@@ -707,8 +832,8 @@ cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, co
         int last = first;
         while (last < S && lu_tc_cluster(N_h[order_h[last]], rows_per_cta) == cs) ++last;
         const cudaError_t e = kind == 2
-            ? launch_group<2>(order + first, last - first, cs, N, mat_off, A32, piv, vec_off, info, err, st)
-            : launch_group<1>(order + first, last - first, cs, N, mat_off, A32, piv, vec_off, info, err, st);
+            ? launch_group<2>(order + first, last - first, cs, N, mat_off, A32, piv, vec_off, info, err, w, st)
+            : launch_group<1>(order + first, last - first, cs, N, mat_off, A32, piv, vec_off, info, err, w, st);
         if (e != cudaSuccess) return e;
         first = last;
     }
