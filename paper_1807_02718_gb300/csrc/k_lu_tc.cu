@@ -457,48 +457,28 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             }
         }
 
-        // 3. U12 = L11^{-1} A12 over this CTA's columns right of the panel
-        // (blocks of 8 rows; finished blocks are re-read from memory, which
-        // keeps the register footprint at 8 complex values)
+        // 3. U12 = L11^{-1} A12 over this CTA's columns right of the panel:
+        // one column per thread, all nb values in registers (one round of
+        // loads), forward substitution with L11 from shared memory, then the
+        // column to the matrix and to the staged B operand
         for (int c = max(c_lo, k0) + tid; c < c_hi; c += kThreads) {
             float2 *col = a + (long long)k0 * n + c + nb;
+            float2 x[NB];
 #pragma unroll
-            for (int B = 0; B < NB / 8; ++B) {
-                if (8 * B >= nb) continue;
-                float2 xb[8];
+            for (int e = 0; e < NB; ++e)
+                x[e] = e < nb ? __ldcg(col + (long long)e * n) : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    xb[e] = 8 * B + e < nb ? __ldcg(col + (long long)(8 * B + e) * n) : make_float2(0.f, 0.f);
+            for (int q = 0; q < NB - 1; ++q)
 #pragma unroll
-                for (int C = 0; C < B; ++C)
+                for (int e = q + 1; e < NB; ++e) {
+                    const float2 l = ps.l11[e][q];
+                    x[e].x -= l.x * x[q].x - l.y * x[q].y;
+                    x[e].y -= l.x * x[q].y + l.y * x[q].x;
+                }
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float2 xq = col[(long long)(8 * C + q) * n];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const float2 l = ps.l11[8 * B + e][8 * C + q];
-                            xb[e].x -= l.x * xq.x - l.y * xq.y;
-                            xb[e].y -= l.x * xq.y + l.y * xq.x;
-                        }
-                    }
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-#pragma unroll
-                    for (int e = q + 1; e < 8; ++e) {
-                        const float2 l = ps.l11[8 * B + e][8 * B + q];
-                        xb[e].x -= l.x * xb[q].x - l.y * xb[q].y;
-                        xb[e].y -= l.x * xb[q].y + l.y * xb[q].x;
-                    }
-#pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    if (8 * B + e < nb) col[(long long)(8 * B + e) * n] = xb[e];
-            }
-            if (nb == NB) {   // the finished column to the staged B operand
-                float2 u[NB];
-#pragma unroll
-                for (int q = 0; q < NB; ++q) u[q] = col[(long long)q * n];
-                put_b_col<kKind>(btiles, c - k0, u);
-            }
+            for (int e = 0; e < NB; ++e)
+                if (e < nb) __stcg(col + (long long)e * n, x[e]);
+            if (nb == NB) put_b_col<kKind>(btiles, c - k0, x);
         }
         // the swaps, U12 and the staged operands (generic stores to global
         // memory) are read by the TMA engine below, which also overwrites the
@@ -615,13 +595,17 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         tc::fence_async_smem();
                         tc::bar_named(1, kEpiThreads);
                         if (ew == 0 && lane == 0) {
+                            // store this tile; the previous tile's store has read its
+                            // buffer once at most one group is outstanding
                             const int x = 2 * (r0 + ct * TCC);
                             uint8_t *src = sC + st * 2 * kCBox;
                             tc::tma_store_2d(tmap, x, i0, src);
                             tc::tma_store_2d(tmap, x + 32, i0, src + kCBox);
                             tc::bulk_commit();
-                            tc::bulk_wait_read();
-                            tc::mbar_arrive(&pp.c_empty[st]);
+                            if (it > n_item) {
+                                tc::bulk_wait_read1();
+                                tc::mbar_arrive(&pp.c_empty[st ^ 1]);
+                            }
                         }
                     }
                 }
@@ -629,8 +613,11 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     failed = true;
                     if (ew == 0 && lane == 0) ps.wait_failed = 1;
                 }
-                if (ew == 0 && lane == 0) {   // the stores are in global memory before the next panel reads them
+                if (ew == 0 && lane == 0) {
+                    // the last tile's buffer is released, and the stores are in
+                    // global memory before the next panel reads them
                     tc::bulk_wait_all();
+                    if (it > n_item) tc::mbar_arrive(&pp.c_empty[(int)((it - 1) & 1)]);
                     tc::fence_async_global();
                 }
             }
