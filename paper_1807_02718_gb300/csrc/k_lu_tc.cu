@@ -63,14 +63,21 @@ constexpr int kWarps = kThreads / 32;
 constexpr int NB = 32;                  // panel width (complex columns)
 constexpr int TR = 128;                 // rows per tile (TMEM lanes)
 constexpr int TCC = 32;                 // complex columns per tile (64 accumulator columns)
+constexpr int kStages = 2;              // pipeline depth of the trailing update (B, C, accumulators)
 constexpr int kMaxCluster = 8;
 constexpr int kMaxMoved = 2 * NB;
 constexpr int kATile = TR * 2 * NB * 4;        // A operand (hi or lo) at 4 bytes per element: 32 KiB
 constexpr int kBTile = 2 * TCC * 2 * NB * 4;   // B operand (hi or lo): 16 KiB
-constexpr int kCBox = TR * 32 * 4;             // one 128 x 32-float box of a C tile: 16 KiB
-constexpr int kDynSmem = 1024 + 2 * kATile + 4 * kBTile + 4 * kCBox;
+constexpr int kCBox = TR * 32 * 4;             // one 128 x 32-float box (tensor map box): 16 KiB
+constexpr int kCBoxes = 2 * TCC / 32;          // boxes per C tile
+constexpr int kCTile = kCBoxes * kCBox;
+constexpr int kDynSmem = 1024 + 2 * kATile + kStages * (2 * kBTile + kCTile);
 constexpr long long kWaitLimit = 1LL << 22;
 constexpr int kEpiWarp0 = 4, kEpiWarps = 8;    // epilogue warps 4 .. 11
+constexpr int kStoreTid = 64;                  // issues the tile stores (warp 2)
+constexpr int kTmemCols = kStages * 2 * TCC < 32 ? 32 : kStages * 2 * TCC;   // accumulators (a power of two)
+static_assert((kTmemCols & (kTmemCols - 1)) == 0, "TMEM allocation is a power of two");
+static_assert(TCC == 16 || TCC == 32, "a C tile is one or two tensor-map boxes");
 constexpr int kEpiThreads = 32 * kEpiWarps;
 
 // Bytes of one operand tile (hi or lo) of each kind: A is 128 L21 rows, B 64
@@ -226,7 +233,8 @@ __device__ __forceinline__ void issue_mma(uint32_t tacc, uint32_t ah, uint32_t a
 // the B and C buffers and of the TMEM accumulators is used by items s, s+2, ...
 struct Pipe {
     uint64_t a_full, a_empty;
-    uint64_t b_full[2], b_empty[2], c_full[2], c_empty[2], acc_full[2], acc_empty[2];
+    uint64_t b_full[kStages], b_empty[kStages], c_full[kStages], c_empty[kStages];
+    uint64_t acc_full[kStages], acc_empty[kStages], c_written[kStages];
 };
 
 // Pointer into the shared memory of CTA r of this system's cluster.
@@ -253,10 +261,10 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     constexpr int kAT = a_tile_bytes<kKind>(), kBT = b_tile_bytes<kKind>();
     uint8_t *stage = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = stage;                                                // hi, lo
-    uint8_t *sB = stage + 2 * kATile;                                   // 2 stages x (hi, lo)
-    uint8_t *sC = sB + 4 * kBTile;                                      // 2 stages x 2 boxes (1 KiB aligned)
+    uint8_t *sB = stage + 2 * kATile;                                   // stages x (hi, lo)
+    uint8_t *sC = sB + kStages * 2 * kBTile;                            // stages x C tile (1 KiB aligned)
     float4 *gbuf = reinterpret_cast<float4 *>(sB);                      // row gather (B + C)
-    constexpr int kGather = (4 * kBTile + 4 * kCBox) / 16;              // float4 in gbuf
+    constexpr int kGather = kStages * (2 * kBTile + kCTile) / 16;       // float4 in gbuf
 
     const int cs = kMulti ? cs_arg : 1;
     const int rank = kMulti ? (int)cg::this_cluster().block_rank() : 0;
@@ -269,17 +277,18 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int myslot = rank * kThreads + tid;
 
-    if (warp == 0) tc::tmem_alloc(&ps.tslot, 4 * TCC);
+    if (warp == 0) tc::tmem_alloc(&ps.tslot, kTmemCols);
     if (tid == 0) {
         tc::mbar_init(&pp.a_full, 1);
         tc::mbar_init(&pp.a_empty, 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kStages; ++b) {
             tc::mbar_init(&pp.b_full[b], 1);
             tc::mbar_init(&pp.b_empty[b], 1);
             tc::mbar_init(&pp.c_full[b], 1);
             tc::mbar_init(&pp.c_empty[b], 1);
             tc::mbar_init(&pp.acc_full[b], 1);
             tc::mbar_init(&pp.acc_empty[b], kEpiWarps);
+            tc::mbar_init(&pp.c_written[b], kEpiWarps);
         }
         ps.wait_failed = 0;
     }
@@ -296,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     // CTA has processed, over all panels; the producer also counts the loads
     // it armed on each full barrier and the MMA thread its commits
     long long n_item = 0, n_rowt = 0;
-    int armed_a = 0, armed_b[2] = {0, 0}, armed_c[2] = {0, 0}, commits[2] = {0, 0}, commits_a = 0;
+    int armed_a = 0, armed_b[kStages] = {}, armed_c[kStages] = {}, commits[kStages] = {}, commits_a = 0;
     bool failed = false, bad = false;
 
     for (int k0 = 0; k0 < n; k0 += NB) {
@@ -504,21 +513,22 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     tc::bulk_load(sA, atiles + (size_t)rt * 2 * kAT, 2 * kAT, &pp.a_full);
                     ++armed_a;
                     for (int ct = 0; ct < nct; ++ct, ++it) {
-                        const int st = (int)(it & 1);
-                        const long long u = it >> 1;
+                        const int st = (int)(it % kStages);
+                        const long long u = it / kStages;
                         if (u > 0 && (!tc::mbar_wait(&pp.b_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit) ||
                                       !tc::mbar_wait(&pp.c_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
                             failed = true;
                             break;
                         }
-                        uint8_t *bdst = sB + st * 2 * kBTile, *cdst = sC + st * 2 * kCBox;
+                        uint8_t *bdst = sB + st * 2 * kBTile, *cdst = sC + st * kCTile;
                         tc::mbar_arrive_tx(&pp.b_full[st], 2 * kBT);
                         tc::bulk_load(bdst, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[st]);
                         ++armed_b[st];
                         const int x = 2 * (r0 + ct * TCC);
-                        tc::mbar_arrive_tx(&pp.c_full[st], 2 * kCBox);
-                        tc::tma_load_2d(cdst, tmap, x, i0, &pp.c_full[st]);
-                        tc::tma_load_2d(cdst + kCBox, tmap, x + 32, i0, &pp.c_full[st]);
+                        tc::mbar_arrive_tx(&pp.c_full[st], kCTile);
+#pragma unroll
+                        for (int bx = 0; bx < kCBoxes; ++bx)
+                            tc::tma_load_2d(cdst + bx * kCBox, tmap, x + 32 * bx, i0, &pp.c_full[st]);
                         ++armed_c[st];
                     }
                 }
@@ -532,8 +542,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         break;
                     }
                     for (int ct = 0; ct < nct; ++ct, ++it) {
-                        const int st = (int)(it & 1);
-                        const long long u = it >> 1;
+                        const int st = (int)(it % kStages);
+                        const long long u = it / kStages;
                         if (!tc::mbar_wait(&pp.b_full[st], (uint32_t)(u & 1), kWaitLimit) ||
                             (u > 0 && !tc::mbar_wait(&pp.acc_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
                             failed = true;
@@ -555,17 +565,16 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 }
                 if (failed) ps.wait_failed = 1;
             } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
-                // epilogue: C -= accumulator in shared memory, tiled store
+                // epilogue: C -= accumulator in the shared-memory C tile
                 const int ew = warp - kEpiWarp0;
                 const int lg = warp & 3, half = ew >> 2;      // TMEM lane group, column half (box)
                 const int r = 32 * lg + lane;                 // tile row
                 long long it = n_item;
                 bool stop = false;
                 for (int q = 0; q < my_rt && !stop && !failed; ++q) {
-                    const int rt = rank + q * cs, i0 = r0 + rt * TR;
                     for (int ct = 0; ct < nct; ++ct, ++it) {
-                        const int st = (int)(it & 1);
-                        const uint32_t par = (uint32_t)((it >> 1) & 1);
+                        const int st = (int)(it % kStages);
+                        const uint32_t par = (uint32_t)((it / kStages) & 1);
                         bool got = tc::mbar_wait(&pp.acc_full[st], par, kWaitLimit);
                         got = got && tc::mbar_wait(&pp.c_full[st], par, kWaitLimit);
                         if (tc::bar_or(1, kEpiThreads, !got)) {   // the same verdict in every epilogue thread
@@ -573,18 +582,21 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                             break;
                         }
                         tc::tc_fence_after();
-                        float d[32];
+                        // this thread: accumulator columns [TCC half, TCC half + TCC) of row r
+                        float d[TCC];
                         const uint32_t tacc = taddr + (uint32_t)(st * 2 * TCC) + ((uint32_t)(32 * lg) << 16) +
-                                              (uint32_t)(32 * half);
-                        tc::tmem_ld16(tacc, *reinterpret_cast<float(*)[16]>(d));
-                        tc::tmem_ld16(tacc + 16, *reinterpret_cast<float(*)[16]>(d + 16));
+                                              (uint32_t)(TCC * half);
+#pragma unroll
+                        for (int q = 0; q < TCC / 16; ++q)
+                            tc::tmem_ld16(tacc + 16 * q, *reinterpret_cast<float(*)[16]>(d + 16 * q));
                         tc::tc_fence_before();
                         __syncwarp();
                         if (lane == 0) tc::mbar_arrive(&pp.acc_empty[st]);
-                        float4 *row = reinterpret_cast<float4 *>(sC + st * 2 * kCBox + half * kCBox + r * 128);
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            float4 *pc = row + (c ^ (r & 7));     // 128-byte swizzle of the box
+                        for (int c = 0; c < TCC / 4; ++c) {
+                            const int f = TCC * half + 4 * c;             // float column within the tile
+                            float4 *row = reinterpret_cast<float4 *>(sC + st * kCTile + (f / 32) * kCBox + r * 128);
+                            float4 *pc = row + (((f % 32) / 4) ^ (r & 7));  // 128-byte swizzle of the box
                             float4 x = *pc;
                             x.x -= d[4 * c];
                             x.y -= d[4 * c + 1];
@@ -592,34 +604,42 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                             x.w -= d[4 * c + 3];
                             *pc = x;
                         }
-                        tc::fence_async_smem();
-                        tc::bar_named(1, kEpiThreads);
-                        if (ew == 0 && lane == 0) {
-                            // store this tile; the previous tile's store has read its
-                            // buffer once at most one group is outstanding
-                            const int x = 2 * (r0 + ct * TCC);
-                            uint8_t *src = sC + st * 2 * kCBox;
-                            tc::tma_store_2d(tmap, x, i0, src);
-                            tc::tma_store_2d(tmap, x + 32, i0, src + kCBox);
-                            tc::bulk_commit();
-                            if (it > n_item) {
-                                tc::bulk_wait_read1();
-                                tc::mbar_arrive(&pp.c_empty[st ^ 1]);
-                            }
-                        }
+                        tc::fence_async_smem();   // the tile store (async proxy) reads these writes
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&pp.c_written[st]);
                     }
                 }
                 if (stop) {
                     failed = true;
                     if (ew == 0 && lane == 0) ps.wait_failed = 1;
                 }
-                if (ew == 0 && lane == 0) {
-                    // the last tile's buffer is released, and the stores are in
-                    // global memory before the next panel reads them
-                    tc::bulk_wait_all();
-                    if (it > n_item) tc::mbar_arrive(&pp.c_empty[(int)((it - 1) & 1)]);
-                    tc::fence_async_global();
+            } else if (tid == kStoreTid) {
+                // tile stores: each C tile goes back to the matrix once its
+                // eight epilogue warps have written it; its buffer is released
+                // when the store has read it
+                long long it = n_item;
+                for (int q = 0; q < my_rt && !failed; ++q) {
+                    const int rt = rank + q * cs, i0 = r0 + rt * TR;
+                    for (int ct = 0; ct < nct; ++ct, ++it) {
+                        const int st = (int)(it % kStages);
+                        if (!tc::mbar_wait(&pp.c_written[st], (uint32_t)((it / kStages) & 1), kWaitLimit)) {
+                            failed = true;
+                            break;
+                        }
+                        const int x = 2 * (r0 + ct * TCC);
+                        uint8_t *src = sC + st * kCTile;
+#pragma unroll
+                        for (int bx = 0; bx < kCBoxes; ++bx)
+                            tc::tma_store_2d(tmap, x + 32 * bx, i0, src + bx * kCBox);
+                        tc::bulk_commit();
+                        tc::bulk_wait_read();
+                        tc::mbar_arrive(&pp.c_empty[st]);
+                    }
                 }
+                if (failed) ps.wait_failed = 1;
+                // the stores are in global memory before the next panel reads them
+                tc::bulk_wait_all();
+                tc::fence_async_global();
             }
             // every thread advances the counters identically
             n_item += (long long)my_rt * nct;
@@ -628,12 +648,12 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             // unless a wait gave up) before the buffers are reused
             if (tid == 0) {
                 if (armed_a) tc::mbar_wait(&pp.a_full, (uint32_t)((armed_a - 1) & 1), kWaitLimit);
-                for (int b = 0; b < 2; ++b) {
+                for (int b = 0; b < kStages; ++b) {
                     if (armed_b[b]) tc::mbar_wait(&pp.b_full[b], (uint32_t)((armed_b[b] - 1) & 1), kWaitLimit);
                     if (armed_c[b]) tc::mbar_wait(&pp.c_full[b], (uint32_t)((armed_c[b] - 1) & 1), kWaitLimit);
                 }
             } else if (tid == 32) {
-                for (int b = 0; b < 2; ++b)
+                for (int b = 0; b < kStages; ++b)
                     if (commits[b]) {
                         tc::mbar_wait(&pp.acc_full[b], (uint32_t)((commits[b] - 1) & 1), kWaitLimit);
                         tc::mbar_wait(&pp.b_empty[b], (uint32_t)((commits[b] - 1) & 1), kWaitLimit);
@@ -664,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     }
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_free(taddr, 4 * TCC);
+    if (warp == 0) tc::tmem_free(taddr, kTmemCols);
     if (cs > 1) cg::this_cluster().sync();   // no CTA leaves while its shared memory may be addressed
 }
 
