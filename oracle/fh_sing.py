@@ -95,18 +95,21 @@ def fcc_interval(fvals: np.ndarray, a: float, b: float, t: np.ndarray) -> np.nda
     interpolating polynomial p(x) = sum_n a_n T_n(x), w = delta + h x
     (delta = (a+b)/2, h = (b-a)/2), is integrated against e^{-iwt} exactly:
       h e^{-i delta t} int_{-1}^{1} p(x) e^{-i h t x} dx,
-    the last integral by Gauss-Legendre with 40 + h|t| nodes (exact to
-    rounding for the degree-(Nq-1) polynomial times the entire function)."""
+    the last integral by composite 24-point Gauss-Legendre on 1 + h|t|/6
+    equal panels (at most 12 radians of phase per panel: exact to rounding for
+    the degree-(Nq-1) polynomial times the exponential)."""
     t = np.atleast_1d(np.asarray(t, dtype=np.float64))
     coef = cheb_interp_coeffs(np.asarray(fvals, dtype=np.complex128))
     delta, h = 0.5 * (a + b), 0.5 * (b - a)
+    xg, wg = np.polynomial.legendre.leggauss(24)
     out = np.empty(t.size, dtype=np.complex128)
     for i, ti in enumerate(t):
         kap = h * ti
-        ng = int(40 + 1.2 * abs(kap))
-        xg, wg = np.polynomial.legendre.leggauss(ng)
-        p = np.polynomial.chebyshev.chebval(xg, coef)
-        out[i] = h * np.exp(-1j * delta * ti) * np.sum(wg * p * np.exp(-1j * kap * xg))
+        edges = np.linspace(-1.0, 1.0, int(abs(kap) / 6.0) + 2)
+        x = (0.5 * np.diff(edges)[:, None] * xg[None, :] + 0.5 * (edges[1:] + edges[:-1])[:, None]).ravel()
+        w = (0.5 * np.diff(edges)[:, None] * wg[None, :]).ravel()
+        p = np.polynomial.chebyshev.chebval(x, coef)
+        out[i] = h * np.exp(-1j * delta * ti) * np.sum(w * p * np.exp(-1j * kap * x))
     return out
 
 
