@@ -263,6 +263,58 @@ fh_status fh_synthesize_static(int J, double W, int K, const double *d_s, const 
                                const double *d_V, int n_x, const double *d_T, int n_T,
                                double *d_u, void *stream);
 
+/* ---- 2D synthesis with the low-frequency split; scaled convolutions ---- */
+
+/* The frequency set F^sing of the singular quadrature (Sec. 4.2, eqs.
+ * gradedmesh, gradedmeshIntRule): on the graded mesh mu_j = omega_c (j/4)^9.1,
+ * j = 1..4, the 8 Clenshaw-Curtis points (a+b)/2 + (b-a)/2 cos(pi c/7), c =
+ * 0..7, of each subinterval [a, b] = [mu_{j-1}, mu_j], j = 2..4, interval by
+ * interval: out receives 24 doubles (host; shared end points appear twice).
+ * Errors: FH_EINVAL (omega_c not positive and finite, NULL out). */
+fh_status fh_sing_frequencies(double omega_c, double *out);
+
+/* Steps T1b-T2d and T5 (Sec. 5) for the 2D case: u(x_i, T_l) = sum_k (1/pi)
+ * Re[ I_{w_c}^{W}[F_k](T_l - s_k) + I_0^{w_c}[F_k](T_l - s_k) ], F_k(w) =
+ * B_k^slow(w) V(x_i, w) (eq. fourier_sing_decomp with F(-w) = conj F(w)).
+ * The smooth piece on [w_c, W] (w_c = j_c W/(J-1)) is the term-wise integral
+ * (eq. approx) of the FC(Gram) Fourier continuation (Remark Fourier-FC; d = 10
+ * matching and C = 31 continuation points) of the samples at omega_j, j =
+ * j_c .. J-1; the singular piece on (0, w_c] is the Filon-Clenshaw-Curtis rule
+ * on the points of fh_sing_frequencies(w_c).
+ *   J, W       uniform mesh omega_j = j W/(J-1); n = J - j_c >= 20 and n + 31 even
+ *   j_c        index of w_c (>= 1)
+ *   K, d_s     window centres (device, K doubles)
+ *   d_B        B_k^slow(omega_j), K*J complex, B[k*J + j] (device)
+ *   d_Bs       B_k^slow at the 24 singular frequencies, K*24 complex (device)
+ *   d_V        V(x_i, omega_j), J*n_x complex, V[j*n_x + i] (device)
+ *   d_Vs       V(x_i, .) at the singular frequencies, 24*n_x complex (device)
+ *   d_T, d_u   n_T times; u as n_x*n_T doubles, u[i*n_T + l] (device)
+ *   stream     cudaStream_t (NULL: legacy default stream); work is stream-ordered
+ * Work space is taken from the device's stream-ordered allocator and returned
+ * on the same stream.  FH_EINVAL (sizes), FH_ENOMEM, FH_ECUDA (also for a
+ * CUDA error pending from earlier work, which is left in place). */
+fh_status fh_synthesize_sing(int J, double W, int j_c, int K, const double *d_s, const double *d_B,
+                             const double *d_Bs, const double *d_V, const double *d_Vs, int n_x,
+                             const double *d_T, int n_T, double *d_u, void *stream);
+
+/* Sec. 4.1.2, eqs. conv_sum, conv_sum_2, approx_conv_sum: for each of `batch`
+ * coefficient vectors c (M complex, c_m for m = -M/2 .. M/2-1; device,
+ * consecutive) the scaled convolution d_n = sum_m c_m b(beta n - gamma m) with
+ * b(q) = 2A sinc(2A q / P) (eq. discConv; normalised sinc), approximated by
+ * (1/L) sum_p C_p^{(gamma)} B_p e^{2 pi i beta n p / L} for n = n0 - L/2 ..
+ * n0 + L/2 - 1: C^{(gamma)} the gamma-fractional DFT of c zero-padded to L, B
+ * the DFT of b at the integers -L/2 .. L/2-1, each fractional DFT by the chirp
+ * factorisation as a circular convolution of radix-2 FFTs.  d_d receives
+ * batch*L complex (device).  L even, M <= L <= 2^24.  Work space as for
+ * fh_synthesize_sing.  The error of the approximation is O(L^-2) for P > 2A. */
+fh_status fh_scaled_convolution(const double *d_c, int M, int batch, double beta, double gamma,
+                                long long n0, int L, double A, double P, double *d_d, void *stream);
+
+/* Window count and spectra of problem `problem` of a batch: as
+ * fh_get_num_windows and fh_get_window_spectra (s: K doubles, B: K*J complex). */
+fh_status fh_get_num_windows_p(fh_ctx *ctx, int problem, int *K);
+fh_status fh_get_window_spectra_p(fh_ctx *ctx, int problem, double *s, double *B);
+
 /* ---- kernel timing and launch accounting ---- */
 
 /* Phases of the path, in order: nodes and tables (a1), CFIE assembly with

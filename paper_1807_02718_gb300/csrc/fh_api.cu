@@ -1377,9 +1377,23 @@ fh_status fh_get_num_windows(fh_ctx *ctx, int *K) {
 }
 
 fh_status fh_get_window_spectra(fh_ctx *ctx, double *s, double *B) {
+    return fh_get_window_spectra_p(ctx, 0, s, B);
+}
+
+fh_status fh_get_num_windows_p(fh_ctx *ctx, int problem, int *K) {
+    FH_TRY(enter(ctx));
+    if (!K) return fail(ctx, FH_EINVAL, "K must be non-NULL");
+    Problem *pb;
+    FH_TRY(get_problem(ctx, problem, &pb));
+    if (!pb->spectra) return fail(ctx, FH_ESTATE, "no window spectra yet");
+    *K = pb->K;
+    return FH_OK;
+}
+
+fh_status fh_get_window_spectra_p(fh_ctx *ctx, int problem, double *s, double *B) {
     FH_TRY(enter(ctx));
     Problem *pb;
-    FH_TRY(get_problem(ctx, 0, &pb));
+    FH_TRY(get_problem(ctx, problem, &pb));
     if (!pb->spectra) return fail(ctx, FH_ESTATE, "no window spectra yet");
     if (s) std::memcpy(s, pb->s.data(), pb->s.size() * sizeof(double));
     if (B) {

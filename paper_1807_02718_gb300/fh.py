@@ -34,6 +34,8 @@ EXPORTED = [
     "fh_window_spectra_p", "fh_window_spectra_p_dev", "fh_sample_p", "fh_sample_p_dev",
     "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test", "fh_eval_bessel_df", "fh_set_graphs",
     "fh_get_tuning", "fh_set_tuning", "fh_autotune", "fh_probe_mma_peak",
+    "fh_sing_frequencies", "fh_synthesize_sing", "fh_scaled_convolution", "fh_get_window_spectra_p",
+    "fh_get_num_windows_p",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "refine", "spectra", "field", "weights", "contract"]
@@ -105,6 +107,13 @@ def load_library(path: str | None = None):
         "fh_get_timings": (C.c_int, [vp, C.POINTER(fh_timings), C.c_int]),
         "fh_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
         "fh_probe_mma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, _DP]),
+        "fh_sing_frequencies": (C.c_int, [C.c_double, _DP]),
+        "fh_synthesize_sing": (C.c_int, [C.c_int, C.c_double, C.c_int, C.c_int, vp, vp, vp, vp, vp, C.c_int,
+                                         vp, C.c_int, vp, vp]),
+        "fh_scaled_convolution": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_longlong,
+                                            C.c_int, C.c_double, C.c_double, vp, vp]),
+        "fh_get_window_spectra_p": (C.c_int, [vp, C.c_int, _DP, _DP]),
+        "fh_get_num_windows_p": (C.c_int, [vp, C.c_int, _IP]),
         "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_eval_bessel_df": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_set_graphs": (C.c_int, [vp, C.c_int]),
@@ -254,6 +263,55 @@ def fh_get_window_spectra(ctx, J: int):
     B = np.empty((K, J), dtype=np.complex128)
     _check(ctx, load_library().fh_get_window_spectra(ctx, _dp(s), B.ctypes.data_as(_DP)))
     return s, B
+
+
+def fh_get_num_windows_p(ctx, problem: int) -> int:
+    K = C.c_int()
+    _check(ctx, load_library().fh_get_num_windows_p(ctx, int(problem), C.byref(K)))
+    return K.value
+
+
+def fh_get_window_spectra_p(ctx, problem: int, J: int):
+    """(s, B) of problem `problem` of a batch (its J frequencies)."""
+    lib = load_library()
+    K = C.c_int()
+    _check(ctx, lib.fh_get_num_windows_p(ctx, int(problem), C.byref(K)))
+    s = np.empty(K.value)
+    B = np.empty((K.value, J), dtype=np.complex128)
+    _check(ctx, lib.fh_get_window_spectra_p(ctx, int(problem), _dp(s), B.ctypes.data_as(_DP)))
+    return s, B
+
+
+def fh_sing_frequencies(omega_c: float) -> np.ndarray:
+    """The 24 frequencies of the singular (Filon-Clenshaw-Curtis) quadrature on (0, omega_c]."""
+    out = np.empty(24)
+    st = load_library().fh_sing_frequencies(float(omega_c), _dp(out))
+    if st != FH_OK:
+        raise FHError(st, "fh_sing_frequencies failed")
+    return out
+
+
+def fh_synthesize_sing(J: int, W: float, j_c: int, d_s, d_B, d_Bs, d_V, d_Vs, d_T, d_u, stream=None):
+    """Split 2D synthesis into d_u (float64 CUDA tensors; complex arrays as
+    interleaved doubles: d_B K*J, d_Bs K*24, d_V J*n_x, d_Vs 24*n_x)."""
+    K = d_s.numel()
+    n_x = d_V.numel() // (2 * J)
+    st = load_library().fh_synthesize_sing(int(J), float(W), int(j_c), K, _dev_ptr(d_s), _dev_ptr(d_B),
+                                           _dev_ptr(d_Bs), _dev_ptr(d_V), _dev_ptr(d_Vs), n_x, _dev_ptr(d_T),
+                                           d_T.numel(), _dev_ptr(d_u), C.c_void_p(stream or 0))
+    if st != FH_OK:
+        raise FHError(st, "fh_synthesize_sing failed")
+
+
+def fh_scaled_convolution(d_c, M: int, beta: float, gamma: float, n0: int, L: int, A: float, P: float,
+                          d_d, stream=None):
+    """Scaled convolutions of the batch of coefficient rows in d_c (batch*M
+    complex as doubles) into d_d (batch*L complex as doubles)."""
+    batch = d_c.numel() // (2 * M)
+    st = load_library().fh_scaled_convolution(_dev_ptr(d_c), int(M), batch, float(beta), float(gamma), int(n0),
+                                              int(L), float(A), float(P), _dev_ptr(d_d), C.c_void_p(stream or 0))
+    if st != FH_OK:
+        raise FHError(st, "fh_scaled_convolution failed")
 
 
 def fh_get_geometry(ctx, j: int, N: int):
