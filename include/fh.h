@@ -277,11 +277,11 @@ fh_status fh_sing_frequencies(double omega_c, double *out);
  * Re[ I_{w_c}^{W}[F_k](T_l - s_k) + I_0^{w_c}[F_k](T_l - s_k) ], F_k(w) =
  * B_k^slow(w) V(x_i, w) (eq. fourier_sing_decomp with F(-w) = conj F(w)).
  * The smooth piece on [w_c, W] (w_c = j_c W/(J-1)) is the term-wise integral
- * (eq. approx) of the FC(Gram) Fourier continuation (Remark Fourier-FC; d = 10
+ * (eq. approx) of the FC(Gram) Fourier continuation (Remark Fourier-FC; d = 6
  * matching and C = 31 continuation points) of the samples at omega_j, j =
  * j_c .. J-1; the singular piece on (0, w_c] is the Filon-Clenshaw-Curtis rule
  * on the points of fh_sing_frequencies(w_c).
- *   J, W       uniform mesh omega_j = j W/(J-1); n = J - j_c >= 20 and n + 31 even
+ *   J, W       uniform mesh omega_j = j W/(J-1); n = J - j_c >= 12 and n + 31 even
  *   j_c        index of w_c (>= 1)
  *   K, d_s     window centres (device, K doubles)
  *   d_B        B_k^slow(omega_j), K*J complex, B[k*J + j] (device)

@@ -191,12 +191,12 @@ _FC_TABLE = None
 
 def fc_gram_table():
     """(A, Q): continuation table (C x d) and Gram basis (d x d) written by
-    gen_fc_gram.py (d = 10, C = 31; the construction is stated there)."""
+    gen_fc_gram.py (d = 6, C = 31; the construction is stated there)."""
     global _FC_TABLE
     if _FC_TABLE is None:
         import json
         import os
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "fc_gram_d10_c31.json")) as fh:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "fc_gram_d6_c31.json")) as fh:
             t = json.load(fh)
         _FC_TABLE = (np.asarray(t["A"], dtype=np.float64), np.asarray(t["Q"], dtype=np.float64))
     return _FC_TABLE

@@ -1,20 +1,23 @@
 """Writes the FC(Gram) continuation table used by the oracle (test
-infrastructure; run once, output committed: fc_gram_d10_c31.json).
+infrastructure; run once, output committed: fc_gram_d6_c31.json).
 
 FC(Gram) Fourier continuation (Sec. 4.1, Remark Fourier-FC, citing Bruno &
 Lyon and Amlani & Bruno; the paper gives no tables).  The reading taken:
 
-* d = 10 matching points, C = 31 continuation points, Z = 14 zero points,
-  trigonometric degree 28 with period 108 (= 2 (d - 1 + C + Z)) in units of
-  the grid spacing, oversampling 10 on the matching and zero intervals;
+* d = 6 matching points, C = 31 continuation points, Z = 12 zero points,
+  trigonometric degree 24 with period 96 (= 2 (d - 1 + C + Z)) in units of
+  the grid spacing, oversampling 10 on the matching and zero intervals
+  (d = 6 keeps the table entries below 6e4, so that rounding of O(1e-16)
+  stays below 1e-11 of the result; larger d raises the order but the table
+  entries grow to 1e6 .. 3e7);
 * Gram basis: the polynomials q_0..q_{d-1} orthonormal for the discrete
   inner product on the d points u = 0..d-1 (Gram-Schmidt of 1, u, u^2, ...);
 * for each q_k, g_k is the least-squares trigonometric polynomial
-  g(u) = a_0 + sum_{l=1}^{28} (a_l cos(2 pi l u/108) + b_l sin(2 pi l u/108))
+  g(u) = a_0 + sum_{l=1}^{24} (a_l cos(2 pi l u/96) + b_l sin(2 pi l u/96))
   with g = q_k on the oversampled matching interval [0, d-1] and g = 0 on the
   oversampled zero interval [d + C, d + C + Z - 1]; the least-squares matrix
-  has full rank (smallest singular value 1.3e-26 of the largest at 100
-  digits), so g_k is unique;
+  has full rank (smallest singular value 2.2e-24 of the largest), so
+  g_k is unique;
 * the continuation table is A[j, k] = g_k(d + j), j = 0..C-1 (the values
   that blend the right end's polynomial to zero); Q[i, k] = q_k(i).
 
@@ -28,9 +31,9 @@ import os
 
 import mpmath as mp
 
-D, C, Z, K, OVERSAMPLE = 10, 31, 14, 28, 10
+D, C, Z, K, OVERSAMPLE = 6, 31, 12, 24, 10
 PERIOD = 2 * (D - 1 + C + Z)
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fc_gram_d10_c31.json")
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fc_gram_d6_c31.json")
 
 
 def gram_basis(d):

@@ -5,11 +5,11 @@ FC(Gram) Fourier continuation (Sec. 4.1, Remark Fourier-FC: a smooth,
 non-periodic F on [a, b] is given a Fourier series of a period P > b - a).
 The paper cites the method without tables; the construction used here:
 
-* d = 10 matching points, C = 31 continuation points, a zero interval of
-  Z = 14 points beyond them; functions of the grid coordinate u (unit spacing);
+* d = 6 matching points, C = 31 continuation points, a zero interval of
+  Z = 12 points beyond them; functions of the grid coordinate u (unit spacing);
 * Gram basis q_0..q_{d-1}: orthonormal for sum_{i<d} f(i) g(i), from 1, u, u^2, ...;
-* blend-to-zero function of q_k: the trigonometric polynomial of degree 28
-  and period 108 = 2 (d - 1 + C + Z) closest in least squares to q_k on the
+* blend-to-zero function of q_k: the trigonometric polynomial of degree 24
+  and period 96 = 2 (d - 1 + C + Z) closest in least squares to q_k on the
   points i/10 of [0, d-1] and to 0 on the points d + C + i/10 of
   [d + C, d + C + Z - 1] (the least-squares matrix has full column rank);
 * table A[j][k] = that function at u = d + j (j < C); Q[i][k] = q_k(i).
@@ -23,7 +23,7 @@ import os
 
 import mpmath as mp
 
-D, C, Z, K, OS = 10, 31, 14, 28, 10
+D, C, Z, K, OS = 6, 31, 12, 24, 10
 PERIOD = 2 * (D - 1 + C + Z)
 
 

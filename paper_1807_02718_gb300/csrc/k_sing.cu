@@ -6,7 +6,7 @@
 //   u_k(x, t) = (1/pi) Re[ I_{w_c}^{W}[F_k](t - s_k) + I_0^{w_c}[F_k](t - s_k) ]
 // (eq. fourier_sing_decomp).  The smooth piece uses the n = J - j_c
 // equispaced samples of [w_c, W] (w_c = omega_{j_c}): their FC(Gram)
-// continuation (d = 10, C = 31, fc_gram_table.h) has period P = (n + C) dw, its
+// continuation (d = 6, C = 31, fc_gram_table.h) has period P = (n + C) dw, its
 // DFT gives the coefficients of eq. fourier_approx about delta = (w_c + W)/2,
 // and the term-wise integral eq. approx gives the transform at any t.  The
 // singular piece uses the Filon-Clenshaw-Curtis rule on the graded mesh

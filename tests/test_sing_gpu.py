@@ -66,29 +66,43 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("fields", ["oracle", "random"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_split_synthesis_from_oracle_inputs(name):
-    """Oracle spectra and (random) target fields in: u matches the oracle's
-    split synthesis at ordinary and large times (T up to 1e4, negative T)."""
+def test_split_synthesis_from_oracle_inputs(name, fields):
+    """Oracle spectra and target fields in: u matches the oracle's split
+    synthesis at ordinary and large times (T up to 1e4, negative T).
+    With the oracle's own target fields (smooth in w) the bar is 1e-10.  With
+    random fields the FC(Gram) Gram coefficients of every order are O(1), and
+    the continuation table's entries (up to 6e4 for d = 6) turn rounding
+    differences of order 1e-16 into up to ~1e-11 of the result; that case is
+    held to 1e-9."""
     mk, j_c = CASES[name]
     wl = mk()
     s, B = O.window_spectra(wl.a, wl.t0, wl.dt, wl.H, wl.omega)
     osg = S.sing_frequencies(wl.omega[j_c])
     _, Bs = O.window_spectra(wl.a, wl.t0, wl.dt, wl.H, osg)
-    rng = np.random.default_rng(len(name))
-    V = rng.standard_normal((wl.n_x, wl.J)) + 1j * rng.standard_normal((wl.n_x, wl.J))
-    Vs = rng.standard_normal((wl.n_x, osg.size)) + 1j * rng.standard_normal((wl.n_x, osg.size))
+    if fields == "oracle":
+        V = O.target_fields(wl, O.solve_all(wl))
+        n = int(wl.N[-1]) // 2
+        Vs = np.stack([O.target_field(wl.curve, n, w, O.solve_density(wl.curve, n, w, wl.c, wl.p), wl.x, wl.c)
+                       for w in osg], 1)
+        tol = TOL
+    else:
+        rng = np.random.default_rng(len(name))
+        V = rng.standard_normal((wl.n_x, wl.J)) + 1j * rng.standard_normal((wl.n_x, wl.J))
+        Vs = rng.standard_normal((wl.n_x, osg.size)) + 1j * rng.standard_normal((wl.n_x, osg.size))
+        tol = 1e-9
     T = np.concatenate([wl.T, [-7.0, 333.3, 2.5e3, 1.0e4]])
     u = gpu_sing(wl.J, float(wl.omega[-1]), j_c, s, B, Bs, V, Vs, T)
     uo = S.synthesize_sing(B, Bs, s, wl.omega, j_c, V, Vs, T)
     assert np.all(np.isfinite(u))
-    assert rel(u, uo) < TOL, rel(u, uo)
+    assert rel(u, uo) < tol, rel(u, uo)
 
 
 def test_split_synthesis_rejects_bad_meshes():
     import torch
     z = torch.zeros(64, device="cuda", dtype=torch.float64)
-    for J, j_c in ((64, 4), (20, 3), (64, 0)):      # n + 31 odd; n < 20; j_c < 1
+    for J, j_c in ((64, 4), (12, 3), (64, 0)):      # n + 31 odd; n < 12; j_c < 1
         with pytest.raises(F.FHError) as e:
             F.fh_synthesize_sing(J, 10.0, j_c, z[:1], z, z, z, z, z[:4], z[:4])
         assert e.value.status == F.FH_EINVAL
@@ -101,7 +115,7 @@ def test_split_synthesis_end_to_end_circle(prec):
     the uniform mesh from one context, those of the 24 singular frequencies
     from a batch of one-frequency problems, spectra of both, then the split
     synthesis.  Against the oracle run on the same inputs, and within the
-    oracle's own bound of the exact time-domain answer (5e-9)."""
+    oracle's own bound of the exact time-domain answer."""
     cur = fi.circle(1.0)
     W, J, j_c = 20.0, 256, 5
     om = np.linspace(0, W, J)
