@@ -189,6 +189,17 @@ fh_status fh_sample_p(fh_ctx *ctx, int problem, const double *x, int n_x, const 
 fh_status fh_sample_p_dev(fh_ctx *ctx, int problem, const double *d_x, int n_x,
                           const double *d_T, int n_T, double *d_u);
 
+/* Time samples on resident target fields (no fresh step F5): u(x_i, T_l)
+ * for the targets of the last fh_sample* call of problem `problem` (or of the
+ * last fh_synthesize for problem 0), whose V(x_i, omega_j) stay on the device,
+ * at new times T (host / device; u as in fh_sample, n_x of that call).  Only
+ * the synthesis weights and the contraction run (Sec. 5 T0-T6), so the cost
+ * per time sample does not include the target-field evaluation; fields from
+ * before a later fh_discretize*, fh_solve_frequencies, fh_set_densities or
+ * fh_autotune are not resident (FH_ESTATE). */
+fh_status fh_resample_p(fh_ctx *ctx, int problem, const double *T, int n_T, double *u_out);
+fh_status fh_resample_p_dev(fh_ctx *ctx, int problem, const double *d_T, int n_T, double *d_u);
+
 /* Density psi_j (N_j complex) of frequency j of problem `problem`. */
 fh_status fh_get_density_p(fh_ctx *ctx, int problem, int j, double *psi);
 
@@ -197,6 +208,11 @@ fh_status fh_get_density_p(fh_ctx *ctx, int problem, int j, double *psi);
  * per-call sampling work space (about 16 (J + n_items) n_x + 16 J n_T bytes).
  * Used for admission by memory footprint.  No device is touched. */
 fh_status fh_footprint(const int *J, const int *N, int P, int precision, long long *bytes);
+
+/* Free and total device memory of CUDA device `device` now (cudaMemGetInfo),
+ * for admission against what the device actually has.  FH_ECUDA if the
+ * device cannot be queried. */
+fh_status fh_device_memory(int device, long long *free_bytes, long long *total_bytes);
 
 /* ---- inspection of resident state (host buffers; used by parity tests) ---- */
 

@@ -1240,6 +1240,7 @@ fh_status fh_solve_frequencies(fh_ctx *ctx, const double *eta, fh_solve_stats *s
         ctx->eta_s[s] = e;
     }
     ctx->solved = false;
+    ctx->have_V = false;   // target fields of earlier densities
     FH_TRY(upload(ctx, ctx->d_eta, ctx->eta_s));
     const bool mixed = ctx->precision != FH_FP64;
     const bool tc = ctx->precision == FH_MIXED_TF32 || ctx->precision == FH_MIXED_BF16;
@@ -1364,6 +1365,42 @@ fh_status fh_sample_p_dev(fh_ctx *ctx, int problem, const double *d_x, int n_x,
     if (n_x == 0 || n_T == 0) return FH_OK;
     if (!d_x || !d_T || !d_u) return fail(ctx, FH_EINVAL, "d_x, d_T and d_u must be non-NULL");
     return sample_common(ctx, problem, d_x, n_x, d_T, n_T, d_u);
+}
+
+// Time side only (weights and contraction) on the resident target fields of
+// problem `problem` (the last fh_sample* of that problem, or fh_synthesize).
+fh_status check_resample(fh_ctx *ctx, int problem, int n_T) {
+    Problem *pb;
+    FH_TRY(get_problem(ctx, problem, &pb));
+    if (!ctx->have_V || ctx->v_problem != problem)
+        return fail(ctx, FH_ESTATE, "no resident target fields of problem %d: call fh_sample first", problem);
+    if (!pb->spectra) return fail(ctx, FH_ESTATE, "fh_resample: call fh_window_spectra first");
+    if (n_T < 0) return fail(ctx, FH_EINVAL, "n_T must be >= 0");
+    return FH_OK;
+}
+
+fh_status fh_resample_p_dev(fh_ctx *ctx, int problem, const double *d_T, int n_T, double *d_u) {
+    FH_TRY(enter(ctx));
+    FH_TRY(check_resample(ctx, problem, n_T));
+    if (n_T == 0 || ctx->n_x_last == 0) return FH_OK;
+    if (!d_T || !d_u) return fail(ctx, FH_EINVAL, "d_T and d_u must be non-NULL");
+    return synth_common(ctx, ctx->probs[problem], ctx->n_x_last, d_T, n_T, d_u);
+}
+
+fh_status fh_resample_p(fh_ctx *ctx, int problem, const double *T, int n_T, double *u_out) {
+    FH_TRY(enter(ctx));
+    FH_TRY(check_resample(ctx, problem, n_T));
+    const int n_x = ctx->n_x_last;
+    if (n_T == 0 || n_x == 0) return FH_OK;
+    if (!T || !u_out) return fail(ctx, FH_EINVAL, "T and u_out must be non-NULL");
+    FH_TRY(ensure(ctx, ctx->d_T, (size_t)n_T * sizeof(double)));
+    FH_TRY(ensure(ctx, ctx->d_u, (size_t)n_x * n_T * sizeof(double)));
+    FH_CUDA(ctx, cudaMemcpyAsync(ctx->d_T.p, T, (size_t)n_T * sizeof(double), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    FH_TRY(synth_common(ctx, ctx->probs[problem], n_x, ctx->d_T.as<double>(), n_T, ctx->d_u.as<double>()));
+    FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    return finish_sample(ctx);
 }
 
 fh_status fh_get_num_windows(fh_ctx *ctx, int *K) {
@@ -1513,6 +1550,7 @@ fh_status fh_set_densities(fh_ctx *ctx, const double *psi_all) {
                                  cudaMemcpyHostToDevice, ctx->stream));
     FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->solved = true;
+    ctx->have_V = false;
     return FH_OK;
 }
 
@@ -1559,6 +1597,25 @@ fh_status fh_synthesize(fh_ctx *ctx, const double *V, int n_x, const double *T, 
     FH_CUDA(ctx, cudaMemcpyAsync(u_out, ctx->d_u.p, (size_t)n_x * n_T * sizeof(double),
                                  cudaMemcpyDeviceToHost, ctx->stream));
     return finish_sample(ctx);
+}
+
+fh_status fh_device_memory(int device, long long *free_bytes, long long *total_bytes) {
+    if (!free_bytes || !total_bytes) return FH_EINVAL;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return FH_ECUDA;
+    }
+    size_t f = 0, t = 0;
+    const cudaError_t e = cudaMemGetInfo(&f, &t);
+    cudaSetDevice(cur);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FH_ECUDA;
+    }
+    *free_bytes = (long long)f;
+    *total_bytes = (long long)t;
+    return FH_OK;
 }
 
 fh_status fh_footprint(const int *J, const int *N, int P, int precision, long long *bytes) {

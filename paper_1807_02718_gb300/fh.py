@@ -35,7 +35,7 @@ EXPORTED = [
     "fh_get_density_p", "fh_footprint", "fh_tc_gemm_test", "fh_eval_bessel_df", "fh_set_graphs",
     "fh_get_tuning", "fh_set_tuning", "fh_autotune", "fh_probe_mma_peak",
     "fh_sing_frequencies", "fh_synthesize_sing", "fh_scaled_convolution", "fh_get_window_spectra_p",
-    "fh_get_num_windows_p",
+    "fh_get_num_windows_p", "fh_resample_p", "fh_resample_p_dev", "fh_device_memory",
 ]
 
 PHASES = ["geometry", "assemble", "factor", "refine", "spectra", "field", "weights", "contract"]
@@ -114,6 +114,9 @@ def load_library(path: str | None = None):
                                             C.c_int, C.c_double, C.c_double, vp, vp]),
         "fh_get_window_spectra_p": (C.c_int, [vp, C.c_int, _DP, _DP]),
         "fh_get_num_windows_p": (C.c_int, [vp, C.c_int, _IP]),
+        "fh_resample_p": (C.c_int, [vp, C.c_int, _DP, C.c_int, _DP]),
+        "fh_device_memory": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "fh_resample_p_dev": (C.c_int, [vp, C.c_int, vp, C.c_int, vp]),
         "fh_eval_bessel": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_eval_bessel_df": (C.c_int, [_DP, C.c_int, _DP]),
         "fh_set_graphs": (C.c_int, [vp, C.c_int]),
@@ -263,6 +266,27 @@ def fh_get_window_spectra(ctx, J: int):
     B = np.empty((K, J), dtype=np.complex128)
     _check(ctx, load_library().fh_get_window_spectra(ctx, _dp(s), B.ctypes.data_as(_DP)))
     return s, B
+
+
+def fh_device_memory(device: int = 0):
+    """(free, total) device bytes now."""
+    f, t = C.c_longlong(), C.c_longlong()
+    st = load_library().fh_device_memory(int(device), C.byref(f), C.byref(t))
+    if st != FH_OK:
+        raise FHError(st, "fh_device_memory failed")
+    return f.value, t.value
+
+
+def fh_resample_p(ctx, problem: int, T, n_x: int, out=None):
+    """u at new times T on the resident target fields (n_x targets of the last sample)."""
+    Tv = _f64(T)
+    u = np.empty((n_x, Tv.size), dtype=np.float64) if out is None else out.reshape(n_x, Tv.size)
+    _check(ctx, load_library().fh_resample_p(ctx, int(problem), _dp(Tv), Tv.size, _dp(u)))
+    return u
+
+
+def fh_resample_p_dev(ctx, problem: int, d_T, d_u):
+    _check(ctx, load_library().fh_resample_p_dev(ctx, int(problem), _dev_ptr(d_T), d_T.numel(), _dev_ptr(d_u)))
 
 
 def fh_get_num_windows_p(ctx, problem: int) -> int:

@@ -1,17 +1,21 @@
 """Continuous-batching server for fast-hybrid scattering requests.
 
 A request is one scattering problem (obstacle, frequency mesh, incidence
-direction, incident signal) followed by sample queries (targets x, times T).
-The server keeps a FIFO of arrived requests and a fixed number of slots.  Each
-slot is a worker thread that owns one libfh context on its own CUDA stream:
-it takes as many waiting requests as fit (batch size and device memory
-budget, counted with fh_footprint), discretises and solves them in shared
+direction, incident signal), one set of targets x and a list of sample
+queries (times T).  The server keeps a FIFO of arrived requests and a fixed
+number of slots.  Each slot is a worker thread that owns one libfh context on
+its own CUDA stream: it takes as many waiting requests as fit (batch size and
+device memory: the footprint of the batch, counted with fh_footprint, within
+the budget, which is a fraction of the device's free memory at start-up
+(fh_device_memory) unless given), discretises and solves them in shared
 launches (fh_discretize_batch / fh_solve_frequencies), keeps their densities
-and window spectra resident while it answers every query of the batch
-(fh_sample_p: no re-solve, any T), then takes the next batch into the same
-context (its buffers are reused).  Requests that arrive while other slots are busy are admitted as
-soon as a slot and memory are free; the slots' kernels run concurrently on the
-device.  Every result is computed by the same kernels with the same per-problem
+and window spectra resident, and answers every query of the batch: the first
+query of a request evaluates its target fields (fh_sample_p), the later ones
+reuse them (fh_resample_p: the time side only, any T, no re-solve).  Then it
+takes the next batch into the same context (its buffers are reused).
+Requests that arrive while other slots are busy are admitted as soon as a
+slot and memory are free; the slots' kernels run concurrently on the device.
+Every result is computed by the same kernels with the same per-problem
 arithmetic whatever the batch, so it is the same alone and in the mix.
 
     python -m paper_1807_02718_gb300.serve --rate 50 --requests 64 --slots 4
@@ -38,7 +42,8 @@ class Request:
     a: np.ndarray
     t0: float
     dt: float
-    queries: list                      # [(x interleaved, T)]
+    x: np.ndarray                      # targets, interleaved
+    queries: list                      # [T], sample times per query
     H: float = 10.0
     arrival: float = 0.0               # seconds after server start
     rid: int = -1
@@ -51,23 +56,29 @@ class Request:
     def solves(self) -> int:
         return len(self.omega) - 1
 
+    @property
+    def samples(self) -> int:
+        return len(self.x) // 2 * sum(len(T) for T in self.queries)
+
     def footprint(self, precision: int) -> int:
         base = F.fh_footprint([len(self.omega)], [self.N], precision)
         n_items = int(np.sum(np.ceil(np.asarray(self.N[1:]) / 64.0)))
-        work = 0
-        for x, T in self.queries:
-            n_x, n_T = len(x) // 2, len(T)
-            work = max(work, 16 * (len(self.omega) + 8 * n_items) * n_x + 16 * len(self.omega) * n_T
-                       + 8 * n_x * n_T)
+        n_x = len(self.x) // 2
+        n_T = max((len(T) for T in self.queries), default=0)
+        work = (16 * (len(self.omega) + 8 * n_items) * n_x + 16 * len(self.omega) * n_T
+                + 8 * n_x * n_T)
         return base + work
 
 
 class Server:
     def __init__(self, device: int = 0, precision: int = F.FH_MIXED_TF32, slots: int = 4,
-                 max_batch: int = 8, mem_budget: int = 16 << 30):
+                 max_batch: int = 8, mem_budget: int | None = None, mem_fraction: float = 0.8):
         self.device = device
         self.precision = precision
         self.max_batch = max_batch
+        if mem_budget is None:   # what the device has free now, less a margin
+            free, _ = F.fh_device_memory(device)
+            mem_budget = int(mem_fraction * free)
         self.mem_budget = mem_budget
         self.mem_used = 0
         self.mem_peak = 0
@@ -165,8 +176,11 @@ class Server:
                 F.fh_solve_frequencies(ctx)
                 for q, r in enumerate(batch):
                     F.fh_window_spectra_p(ctx, q, r.a, r.t0, r.dt, r.H)
-                    for x, T in r.queries:
-                        r.results.append(F.fh_sample_p(ctx, q, x, T))
+                    for i, T in enumerate(r.queries):
+                        if i == 0:   # target fields of the request, then resident
+                            r.results.append(F.fh_sample_p(ctx, q, r.x, T))
+                        else:
+                            r.results.append(F.fh_resample_p(ctx, q, T, len(r.x) // 2))
                     r.done = self.now()
             except F.FHError as e:
                 for r in batch:
@@ -187,7 +201,7 @@ class Server:
         lat = np.array([r.done - r.arrival for r in ok]) if ok else np.zeros(1)
         span = max((r.done for r in ok), default=0.0) - min((r.arrival for r in ok), default=0.0)
         solves = sum(r.solves for r in ok)
-        samples = sum(len(x) // 2 * len(T) for r in ok for x, T in r.queries)
+        samples = sum(r.samples for r in ok)
         return {"requests": len(ok), "errors": len(self.finished) - len(ok),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "solves_per_s": solves / span if span > 0 else 0.0,
@@ -195,9 +209,14 @@ class Server:
                 "peak_concurrent_batches": self.peak_active}
 
 
-def synthetic_request(rng: np.random.Generator, wmax_lo=10.0, wmax_hi=120.0, J=32, n_cap=512,
-                      n_queries=(1, 4), n_targets=(256, 1024), n_times=64, t_max=1.0e4) -> Request:
-    """A star obstacle with a random pulse-train or linear-chirp signal and random queries."""
+def synthetic_request(rng: np.random.Generator, wmax_lo=10.0, wmax_hi=120.0, J=128, n_cap=2048,
+                      n_queries=(1, 100), n_targets=(256, 4096), n_times=16, t_max=1.0e4) -> Request:
+    """A serving request of the paper's shapes: a random star obstacle
+    r = 1 + sum_{k<=5} a_k cos(k t + phi_k), J frequencies on [0, w_max],
+    w_max ~ U(wmax_lo, wmax_hi), N by 8 points per wavelength (capped at
+    n_cap), a random pulse-train or linear-chirp signal, n_targets ~ U targets
+    on a circle of radius 3, and n_queries ~ U queries of n_times random times
+    in [0, t_max]."""
     import fh_inputs as fi
     cur = fi.random_star(rng)
     W = float(rng.uniform(wmax_lo, wmax_hi))
@@ -211,11 +230,28 @@ def synthetic_request(rng: np.random.Generator, wmax_lo=10.0, wmax_hi=120.0, J=3
         sig = fi.Chirp(0.0, float(rng.uniform(30, 80)), 5.0)
     t0, dt = -10.0, 0.01
     a = fi.sample_signal(sig, t0, dt, int(np.ceil((sig.t_end - t0) / dt)) + 1)
-    queries = []
-    for _ in range(int(rng.integers(n_queries[0], n_queries[1] + 1))):
-        nx = int(rng.integers(n_targets[0], n_targets[1] + 1))
-        queries.append((fi.targets_on_circle(nx, 3.0), np.sort(rng.uniform(0.0, t_max, n_times))))
-    return Request(cur, om, N, (np.cos(ang), np.sin(ang)), a, t0, dt, queries)
+    nx = int(rng.integers(n_targets[0], n_targets[1] + 1))
+    queries = [np.sort(rng.uniform(0.0, t_max, n_times))
+               for _ in range(int(rng.integers(n_queries[0], n_queries[1] + 1)))]
+    return Request(cur, om, N, (np.cos(ang), np.sin(ang)), a, t0, dt, fi.targets_on_circle(nx, 3.0), queries)
+
+
+def run_stream(rate: float, n_requests: int, seed: int = 5, slots: int = 4, max_batch: int = 8,
+               precision: int = F.FH_MIXED_TF32, **request_kw) -> dict:
+    """Serve n_requests synthetic requests arriving as a Poisson process of
+    the given rate; returns the server's statistics."""
+    rng = np.random.default_rng(seed)
+    reqs = [synthetic_request(rng, **request_kw) for _ in range(n_requests)]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    srv = Server(precision=precision, slots=slots, max_batch=max_batch)
+    for r, t in zip(reqs, arrivals):
+        r.arrival = float(t) + 0.2
+        srv.submit(r)
+    srv.drain()
+    srv.close()
+    out = {"rate": rate, "slots": slots, "max_batch": max_batch}
+    out.update(srv.stats())
+    return out
 
 
 def main():
@@ -224,27 +260,15 @@ def main():
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--max-batch", type=int, default=8)
-    ap.add_argument("--mem-gb", type=float, default=16.0)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     args = ap.parse_args()
     from . import build
     build.build()
-    rng = np.random.default_rng(args.seed)
-    reqs = [synthetic_request(rng) for _ in range(args.requests)]
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, args.requests))
     prec = {"fp64": F.FH_FP64, "fp32": F.FH_MIXED_FP32, "tf32": F.FH_MIXED_TF32,
             "bf16": F.FH_MIXED_BF16}[args.precision]
-    srv = Server(precision=prec, slots=args.slots,
-                 max_batch=args.max_batch, mem_budget=int(args.mem_gb * (1 << 30)))
-    for r, t in zip(reqs, arrivals):
-        r.arrival = float(t) + 0.5
-        srv.submit(r)
-    srv.drain()
-    srv.close()
-    out = {"rate": args.rate, "slots": args.slots, "max_batch": args.max_batch,
-           "precision": args.precision}
-    out.update(srv.stats())
+    out = run_stream(args.rate, args.requests, args.seed, args.slots, args.max_batch, prec)
+    out["precision"] = args.precision
     print(json.dumps(out))
 
 

@@ -405,3 +405,25 @@ def test_tensor_core_lu_clusters(prec):
     psi_o = O.solve_all(wl)
     for j in (1, 2, 3):
         assert rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) < TOL
+
+
+def test_resample_on_resident_target_fields():
+    """fh_resample_p: new times on the target fields left by the last sample
+    (no fresh step F5) equal a fresh fh_sample at those times bit for bit, and
+    the oracle within 1e-10; fields stop being resident after a re-solve."""
+    wl = fi.small_kite()
+    pr = make(wl)
+    pr.solve()
+    pr.window_spectra(wl.a, wl.t0, wl.dt, wl.H)
+    with pytest.raises(F.FHError) as e:
+        F.fh_resample_p(pr.ctx, 0, wl.T, wl.n_x)
+    assert e.value.status == F.FH_ESTATE
+    pr.sample(wl.x, wl.T[:5])
+    T2 = np.concatenate([wl.T[::-1], [7.7e3]])
+    u = F.fh_resample_p(pr.ctx, 0, T2, wl.n_x)
+    assert np.array_equal(u, pr.sample(wl.x, T2))
+    assert rel(u, O.run(wl, T=T2)["u"]) < TOL
+    pr.solve()
+    with pytest.raises(F.FHError) as e:
+        F.fh_resample_p(pr.ctx, 0, T2, wl.n_x)
+    assert e.value.status == F.FH_ESTATE
