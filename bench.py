@@ -539,6 +539,22 @@ class Leg:
         h2d = wl.a.nbytes + wl.x.nbytes + wl.T.nbytes + wl.omega.nbytes + wl.N.nbytes
         return times, int(h2d), int(u_host.nbytes)
 
+    def resample_timed(self, steps, flush):
+        """Time samples on the resident target fields (no fresh step F5):
+        fh_resample_p_dev at the workload's times, per call ms."""
+        torch = self.torch
+        ev = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            self.F.fh_resample_p_dev(self.pr.ctx, 0, self.d_T, self.d_u)
+            e1.record(self.stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
     def u(self):
         self.stream.synchronize()
         return self.d_u.cpu().numpy().reshape(self.wl.n_x, self.wl.T.size)
@@ -615,6 +631,79 @@ def batch_leg(F, torch, local, stream, flush, steps, warmup):
     return out
 
 
+def split_synthesis_leg(F, torch, local, stream, steps):
+    """The 2D synthesis with the low-frequency split (FCC on (0, w_c], FC(Gram)
+    on [w_c, W]) on the 256-frequency kite: densities and target fields of
+    the mesh and of the 24 singular frequencies from the solver, then
+    fh_synthesize_sing for 1024 targets x 4096 times, timed with CUDA events."""
+    wl = fi.kite_pulses()
+    j_c = 5
+    dev = torch.device("cuda", local)
+    pr = F.Problem(local, F.FH_MIXED_TF32)
+    F.fh_set_stream(pr.ctx, stream.cuda_stream)
+    pr.discretize(wl.curve, wl.omega, wl.N, wl.c, wl.p)
+    pr.solve()
+    pr.window_spectra(wl.a, wl.t0, wl.dt, wl.H)
+    pr.sample(wl.x, wl.T[:2])
+    V = F.fh_get_target_field(pr.ctx, wl.n_x, wl.J)
+    s, B = F.fh_get_window_spectra(pr.ctx, wl.J)
+    pr.close()
+    osg = F.fh_sing_frequencies(wl.omega[j_c])
+    ctx = F.fh_create(local, F.FH_MIXED_TF32)
+    P = osg.size
+    F.fh_discretize_batch(ctx, [wl.curve] * P, [np.array([0.0, w]) for w in osg],
+                          [np.array([64, 64], dtype=np.int32)] * P, ps=[wl.p] * P)
+    F.fh_solve_frequencies(ctx)
+    Vs = np.empty((wl.n_x, P), dtype=np.complex128)
+    Bs = np.empty((B.shape[0], P), dtype=np.complex128)
+    for q in range(P):
+        F.fh_window_spectra_p(ctx, q, wl.a, wl.t0, wl.dt, wl.H)
+        F.fh_sample_p(ctx, q, wl.x, wl.T[:2])
+        Vs[:, q] = F.fh_get_target_field(ctx, wl.n_x, 2)[:, 1]
+        Bs[:, q] = F.fh_get_window_spectra_p(ctx, q, 2)[1][:, 1]
+    F.fh_destroy(ctx)
+
+    def d(a):
+        a = np.ascontiguousarray(a)
+        return torch.tensor((a.view(np.float64) if np.iscomplexobj(a) else a).ravel(), device=dev)
+    d_s, d_B, d_Bs = d(s), d(B), d(Bs)
+    d_V, d_Vs, d_T = d(V.T), d(Vs.T), d(wl.T)
+    d_u = torch.empty(wl.n_x * wl.T.size, device=dev, dtype=torch.float64)
+    torch.cuda.synchronize()
+    F.fh_synthesize_sing(wl.J, float(wl.omega[-1]), j_c, d_s, d_B, d_Bs, d_V, d_Vs, d_T, d_u,
+                         stream.cuda_stream)
+    ev = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        F.fh_synthesize_sing(wl.J, float(wl.omega[-1]), j_c, d_s, d_B, d_Bs, d_V, d_Vs, d_T, d_u,
+                             stream.cuda_stream)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(per) / len(per)
+    assert bool(torch.isfinite(d_u).all())
+    return {"workload": WORKLOADS["kite_pulses"][1] + f"; w_c = omega_{j_c}, 24 singular frequencies",
+            "ms_per_call": ms, "time_samples_per_s": wl.n_x * wl.T.size / (ms * 1e-3),
+            "calls": len(per), "extra_solves": P}
+
+
+def serving_leg(rates, n_requests):
+    """Continuous-batching server at the serving configuration's shape (star
+    obstacles, 128 frequencies on [0, w_max], w_max ~ U(10, 120), pulse or
+    chirp signals, 256-4096 targets and 1-100 queries of 16 times in [0, 1e4]
+    per request), Poisson arrivals, TF32: p50/p99 request latency and
+    throughput per arrival rate."""
+    from paper_1807_02718_gb300 import serve as SV
+    out = []
+    for i, rate in enumerate(rates):
+        st = SV.run_stream(rate, n_requests, seed=11 + i)
+        out.append(st)
+    return out
+
+
 def run_gpu(args, world, rank, local):
     extra = not args.no_extra and world == 1 and rank == 0
     oracle_proc = None
@@ -653,6 +742,11 @@ def run_gpu(args, world, rank, local):
     value = world * S * args.steps / (total_ms / 1e3)
     samples_per_s = world * n_x * n_T * args.steps / (total_ms / 1e3)
     u_mixed = leg.u()
+    res = leg.resample_timed(max(3, args.steps // 2), flush)
+    resident = {"ms_per_call": sum(res) / len(res),
+                "time_samples_per_s": n_x * n_T * len(res) / (sum(res) / 1e3),
+                "note": "fh_resample_p_dev: weights + contraction on the resident target fields of "
+                        "the timed steps (no fresh target-field step)"}
     phase_ms = leg.phases(max(2, min(args.steps, 3)), flush)
     dominant = max(phase_ms, key=phase_ms.get)
     e2e_times, h2d, d2h = leg.e2e(args.steps, flush)
@@ -711,6 +805,10 @@ def run_gpu(args, world, rank, local):
         # ---- batching configuration ----
         other = other or {}
         other["star_batch"] = batch_leg(F, torch, local, stream, flush, max(3, args.steps // 4), 2)
+        # ---- 2D split synthesis (low-frequency quadrature) ----
+        other["split_synthesis"] = split_synthesis_leg(F, torch, local, stream, 3)
+        # ---- serving ----
+        other["serving"] = serving_leg([20.0, 100.0], 24)
 
     cpu = None
     if oracle_proc is not None:
@@ -773,6 +871,8 @@ def run_gpu(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision], "data": "synthetic", "config": cfg,
             "time_samples_per_s": samples_per_s,
+            "time_samples_per_s_resident_fields": resident["time_samples_per_s"],
+            "resident_fields": resident,
             "p50_ms": float(np.percentile(per_step, 50)),
             "p99_ms": float(np.percentile(per_step, 99)),
             "e2e": {"value": world * S * args.steps / e2e_total, "unit": "solves/s",
