@@ -146,12 +146,15 @@ __device__ __forceinline__ void sys_sync(int cs, bool with_global) {
 // Pivot candidates are packed keys: hi = bits of |a|_1 (monotone for
 // non-negative floats; NaN and Inf sort above every finite value), lo = ~row
 // position (the smaller position wins a tie); an inactive row has key 0.
+struct __align__(16) Cand {                 // one CTA's pivot candidate: key, then its row
+    uint32_t kh, kl, pad[2];
+    float2 row[NB];
+};
 struct PanelShared {
     uint32_t kh[2][kWarps], kl[2][kWarps];      // per-warp best keys
     float2 wrow[2][kWarps][NB];                 // cluster of one: warp winners' rows
-    uint32_t ckh[2][kMaxCluster], ckl[2][kMaxCluster];
-    float2 crow[2][kMaxCluster][NB];            // cluster: CTA winners' rows
-    float2 l11[NB][NB + 1];                     // unit lower L11 of the current panel
+    Cand cand[2][kMaxCluster];                  // cluster: every CTA's candidate
+    float2 l11[NB + 16][NB + 1];                // unit lower L11 of the current panel; rows NB.. stay zero
     int mv_dst[kMaxMoved], mv_src[kMaxMoved];
     int mv_cnt;
     uint64_t bar[2];
@@ -210,6 +213,59 @@ __device__ __forceinline__ void put_b_col(uint8_t *tiles, int jj, const float2 *
     }
 }
 
+// Step 3, one group of four rows: the B-operand chunks of U12 rows
+// [4 g, 4 g + 4) of column `jj` (as put_b_col, for that slice of K).
+template <int kKind>
+__device__ __forceinline__ void put_b_group(uint8_t *tiles, int jj, int g, const float2 *u) {
+    constexpr int qpc = Op<kKind>::qpc, kRowB = 2 * NB * Op<kKind>::esize, kT = b_tile_bytes<kKind>();
+    uint8_t *hi = tiles + (size_t)(jj / TCC) * 2 * kT, *lo = hi + kT;
+    const int b = 2 * (jj % TCC);
+#pragma unroll
+    for (int cc = 0; cc < 4 / qpc; ++cc) {
+        const int c = g * (4 / qpc) + cc;
+        float re[2 * qpc], im[2 * qpc];
+#pragma unroll
+        for (int h = 0; h < qpc; ++h) {
+            const float2 x = u[cc * qpc + h];
+            re[2 * h] = x.x;
+            re[2 * h + 1] = -x.y;
+            im[2 * h] = x.y;
+            im[2 * h + 1] = x.x;
+        }
+        const uint32_t o0 = tc::kmajor_offset(b, c * 16, kRowB), o1 = tc::kmajor_offset(b + 1, c * 16, kRowB);
+        split_store<kKind>(re, hi + o0, lo + o0);
+        split_store<kKind>(im, hi + o1, lo + o1);
+    }
+}
+
+// Step 3 for one column, rows in groups of four: x[0..3] are rows q0..q0+3,
+// eliminated into x[4..kRows) (rows q0 + 4 ..), stored, then the column
+// shifts down by four.  Two instances (kRows = 32 while q0 < 16, 16 after)
+// keep the loop bodies short enough to stay in the instruction cache.
+template <int kKind, int kRows>
+__device__ __forceinline__ void trsm_groups(float2 (&x)[NB], int g0, int g1, const float2 (*l11)[NB + 1],
+                                            float2 *col, long long n, int nb, uint8_t *btiles, int jj) {
+#pragma unroll 1
+    for (int g = g0; g < g1; ++g) {
+        const int q0 = 4 * g;
+        const float2 (*L)[NB + 1] = reinterpret_cast<const float2 (*)[NB + 1]>(&l11[q0][q0]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int e = i + 1; e < kRows; ++e) {   // rows past the panel read zero rows of l11
+                const float2 l = L[e][i];
+                x[e].x -= l.x * x[i].x - l.y * x[i].y;
+                x[e].y -= l.x * x[i].y + l.y * x[i].x;
+            }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (q0 + i < nb) __stcg(col + (long long)(q0 + i) * n, x[i]);
+        if (nb == NB) put_b_group<kKind>(btiles, jj, g, x);
+#pragma unroll
+        for (int e = 0; e + 4 < kRows; ++e) x[e] = x[e + 4];
+    }
+}
+
 // One 128 x 32-complex tile: hi*hi + hi*lo + lo*hi over the panel's K.
 template <int kKind>
 __device__ __forceinline__ void issue_mma(uint32_t tacc, uint32_t ah, uint32_t al, uint32_t bh,
@@ -235,6 +291,10 @@ struct Pipe {
     uint64_t a_full, a_empty;
     uint64_t b_full[kStages], b_empty[kStages], c_full[kStages], c_empty[kStages];
     uint64_t acc_full[kStages], acc_empty[kStages], c_written[kStages];
+    // items (row tile, column tile) and row tiles processed over all panels;
+    // the loads the producer armed on each full barrier, the MMA thread's commits
+    long long n_item, n_rowt;
+    int armed_a, armed_b[kStages], armed_c[kStages], commits[kStages], commits_a;
 };
 
 // Pointer into the shared memory of CTA r of this system's cluster.
@@ -291,7 +351,11 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             tc::mbar_init(&pp.c_written[b], kEpiWarps);
         }
         ps.wait_failed = 0;
+        pp.n_item = pp.n_rowt = 0;
+        pp.armed_a = pp.commits_a = 0;
+        for (int b = 0; b < kStages; ++b) pp.armed_b[b] = pp.armed_c[b] = pp.commits[b] = 0;
     }
+    for (int i = tid; i < 16 * (NB + 1); i += kThreads) ps.l11[NB + i / (NB + 1)][i % (NB + 1)] = make_float2(0.f, 0.f);
     if (rank == 0)   // pv: factored position -> original row, while factoring
         for (int i = tid; i < n; i += kThreads) pv[i] = i;
     tc::fence_async_smem();
@@ -301,11 +365,6 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     const uint32_t taddr = ps.tslot;
     if (cs > 1) cg::this_cluster().sync();   // every CTA running before shared memory is addressed remotely
 
-    // pipeline counters: items (row tile, column tile) and row tiles this
-    // CTA has processed, over all panels; the producer also counts the loads
-    // it armed on each full barrier and the MMA thread its commits
-    long long n_item = 0, n_rowt = 0;
-    int armed_a = 0, armed_b[kStages] = {}, armed_c[kStages] = {}, commits[kStages] = {}, commits_a = 0;
     bool failed = false, bad = false;
 
     for (int k0 = 0; k0 < n; k0 += NB) {
@@ -357,26 +416,38 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 const uint32_t h2 = lane < kWarps ? ps.kh[pb][lane] : 0u;
                 const uint32_t l2 = lane < kWarps ? ps.kl[pb][lane] : 0u;
                 key_max(h2, l2, mh, ml);
-                if (active && khi == mh && klo == ml)     // this CTA's best row, to every CTA
-                    for (int r = 0; r < cs; ++r) {
-                        *at_rank(&ps.ckh[pb][rank], cs, r) = mh;
-                        *at_rank(&ps.ckl[pb][rank], cs, r) = ml;
-                        float4 *dst = reinterpret_cast<float4 *>(at_rank(&ps.crow[pb][rank][0], cs, r));
+                // this CTA's candidate to every CTA: the winning thread (or, when no
+                // row of this CTA is left, warp 0 with an empty key) fills this
+                // CTA's slot, then its warp copies the slot to the other CTAs, one
+                // 16-byte chunk per lane and step (the key and the row from column cl)
+                const bool none = mh == 0u && ml == 0u;
+                const bool win = active && khi == mh && klo == ml;
+                if (none ? warp == 0 : __ballot_sync(0xffffffffu, win) != 0u) {
+                    Cand &mine = ps.cand[pb][rank];
+                    float4 *m4 = reinterpret_cast<float4 *>(&mine);
+                    if (win) {
+                        m4[0] = make_float4(__uint_as_float(mh), __uint_as_float(ml), 0.f, 0.f);
 #pragma unroll
                         for (int h = cl / 2; h < NB / 2; ++h)
-                            dst[h] = make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
+                            m4[1 + h] = make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
+                    } else if (none && lane == 0) {
+                        m4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                if (mh == 0u && ml == 0u && tid == 0)    // no row of this CTA is left: empty candidate
-                    for (int r = 0; r < cs; ++r) {
-                        *at_rank(&ps.ckh[pb][rank], cs, r) = 0u;
-                        *at_rank(&ps.ckl[pb][rank], cs, r) = 0u;
+                    __syncwarp();
+                    const int h0 = cl / 2, per = none ? 1 : 1 + NB / 2 - h0;
+                    for (int i = lane; i < (cs - 1) * per; i += 32) {
+                        const int rr = i / per, j = i - rr * per;
+                        const int f = j == 0 ? 0 : h0 + j;
+                        float4 *dst = reinterpret_cast<float4 *>(at_rank(&mine, cs, rr < rank ? rr : rr + 1));
+                        dst[f] = m4[f];
                     }
+                }
                 sys_sync(cs, false);
-                const uint32_t h3 = lane < cs ? ps.ckh[pb][lane] : 0u;
-                const uint32_t l3 = lane < cs ? ps.ckl[pb][lane] : 0u;
+                const uint32_t h3 = lane < cs ? ps.cand[pb][lane].kh : 0u;
+                const uint32_t l3 = lane < cs ? ps.cand[pb][lane].kl : 0u;
                 key_max(h3, l3, mh, ml);
                 const uint32_t hit = __ballot_sync(0xffffffffu, lane < cs && h3 == mh && l3 == ml);
-                row = ps.crow[pb][__ffs(hit) - 1];
+                row = ps.cand[pb][__ffs(hit) - 1].row;
             }
             // zero or non-finite pivot, or no row left: the same verdict in every CTA
             if (ml == 0u || mh == 0u || mh >= 0x7F800000u) {
@@ -434,31 +505,36 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         }
         sys_sync(cs, true);
 
-        // column range of this CTA outside the panel: c in [0, n - nb), column
-        // c < k0 ? c : c + nb
-        const int ncs = n - nb;
-        const int W = (((ncs + cs - 1) / cs) + 1) & ~1;
-        const int c_lo = min(ncs, rank * W), c_hi = min(ncs, c_lo + W);
+        // column ranges of this CTA outside the panel: an even share of the
+        // columns left of it, [lc_lo, lc_hi), and of those right of it, columns
+        // nb + [rc_lo, rc_hi) (the swaps and U12 of one column stay in one CTA)
+        const int ncs = n - nb, nr = ncs - k0;
+        const int WL = (((k0 + cs - 1) / cs) + 1) & ~1, WR = (((nr + cs - 1) / cs) + 1) & ~1;
+        const int lc_lo = min(k0, rank * WL), lc_hi = min(k0, lc_lo + WL);
+        const int rc_lo = k0 + min(nr, rank * WR), rc_hi = k0 + min(nr, rank * WR + WR);
         const int nmv = min(ps.mv_cnt, kMaxMoved);
         if (nmv > 0) {
             int t_perm = 0;
             if (rank == 0 && tid < nmv) t_perm = pv[k0 + ps.mv_src[tid]];
             const int CW2 = kGather / nmv;      // float4 (two columns) per moved row and chunk
-            for (int cb = c_lo; cb < c_hi; cb += 2 * CW2) {
-                const int cw2 = min(2 * CW2, c_hi - cb) / 2;
-                const int tot = nmv * cw2;
-                for (int e = tid; e < tot; e += kThreads) {
-                    const int p = e / cw2, c = cb + 2 * (e - p * cw2);
-                    const int j = c < k0 ? c : c + nb;
-                    gbuf[e] = __ldcg(reinterpret_cast<const float4 *>(a + (long long)(k0 + ps.mv_src[p]) * n + j));
+            for (int side = 0; side < 2; ++side) {
+                const int c_lo = side == 0 ? lc_lo : rc_lo, c_hi = side == 0 ? lc_hi : rc_hi;
+                for (int cb = c_lo; cb < c_hi; cb += 2 * CW2) {
+                    const int cw2 = min(2 * CW2, c_hi - cb) / 2;
+                    const int tot = nmv * cw2;
+                    for (int e = tid; e < tot; e += kThreads) {
+                        const int p = e / cw2, c = cb + 2 * (e - p * cw2);
+                        const int j = c < k0 ? c : c + nb;
+                        gbuf[e] = __ldcg(reinterpret_cast<const float4 *>(a + (long long)(k0 + ps.mv_src[p]) * n + j));
+                    }
+                    __syncthreads();
+                    for (int e = tid; e < tot; e += kThreads) {
+                        const int p = e / cw2, c = cb + 2 * (e - p * cw2);
+                        const int j = c < k0 ? c : c + nb;
+                        __stcg(reinterpret_cast<float4 *>(a + (long long)(k0 + ps.mv_dst[p]) * n + j), gbuf[e]);
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
-                for (int e = tid; e < tot; e += kThreads) {
-                    const int p = e / cw2, c = cb + 2 * (e - p * cw2);
-                    const int j = c < k0 ? c : c + nb;
-                    __stcg(reinterpret_cast<float4 *>(a + (long long)(k0 + ps.mv_dst[p]) * n + j), gbuf[e]);
-                }
-                __syncthreads();
             }
             if (rank == 0) {
                 __syncthreads();
@@ -470,24 +546,14 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         // one column per thread, all nb values in registers (one round of
         // loads), forward substitution with L11 from shared memory, then the
         // column to the matrix and to the staged B operand
-        for (int c = max(c_lo, k0) + tid; c < c_hi; c += kThreads) {
+        for (int c = rc_lo + tid; c < rc_hi; c += kThreads) {
             float2 *col = a + (long long)k0 * n + c + nb;
             float2 x[NB];
 #pragma unroll
             for (int e = 0; e < NB; ++e)
                 x[e] = e < nb ? __ldcg(col + (long long)e * n) : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < NB - 1; ++q)
-#pragma unroll
-                for (int e = q + 1; e < NB; ++e) {
-                    const float2 l = ps.l11[e][q];
-                    x[e].x -= l.x * x[q].x - l.y * x[q].y;
-                    x[e].y -= l.x * x[q].y + l.y * x[q].x;
-                }
-#pragma unroll
-            for (int e = 0; e < NB; ++e)
-                if (e < nb) __stcg(col + (long long)e * n, x[e]);
-            if (nb == NB) put_b_col<kKind>(btiles, c - k0, x);
+            trsm_groups<kKind, NB>(x, 0, NB / 8, ps.l11, col, n, nb, btiles, c - k0);
+            trsm_groups<kKind, NB / 2>(x, NB / 8, NB / 4, ps.l11, col, n, nb, btiles, c - k0);
         }
         // the swaps, U12 and the staged operands (generic stores to global
         // memory) are read by the TMA engine below, which also overwrites the
@@ -502,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             const int my_rt = rank < nrt ? (nrt - 1 - rank) / cs + 1 : 0;   // row tiles of this CTA
             if (tid == 0) {
                 // producer: A once per row tile, B and C per item
-                long long it = n_item, rtc = n_rowt;
+                long long it = pp.n_item, rtc = pp.n_rowt;
                 for (int q = 0; q < my_rt && !failed; ++q, ++rtc) {
                     const int rt = rank + q * cs, i0 = r0 + rt * TR;
                     if (rtc > 0 && !tc::mbar_wait(&pp.a_empty, (uint32_t)((rtc - 1) & 1), kWaitLimit)) {
@@ -511,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     }
                     tc::mbar_arrive_tx(&pp.a_full, 2 * kAT);
                     tc::bulk_load(sA, atiles + (size_t)rt * 2 * kAT, 2 * kAT, &pp.a_full);
-                    ++armed_a;
+                    ++pp.armed_a;
                     for (int ct = 0; ct < nct; ++ct, ++it) {
                         const int st = (int)(it % kStages);
                         const long long u = it / kStages;
@@ -523,19 +589,19 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         uint8_t *bdst = sB + st * 2 * kBTile, *cdst = sC + st * kCTile;
                         tc::mbar_arrive_tx(&pp.b_full[st], 2 * kBT);
                         tc::bulk_load(bdst, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[st]);
-                        ++armed_b[st];
+                        ++pp.armed_b[st];
                         const int x = 2 * (r0 + ct * TCC);
                         tc::mbar_arrive_tx(&pp.c_full[st], kCTile);
 #pragma unroll
                         for (int bx = 0; bx < kCBoxes; ++bx)
                             tc::tma_load_2d(cdst + bx * kCBox, tmap, x + 32 * bx, i0, &pp.c_full[st]);
-                        ++armed_c[st];
+                        ++pp.armed_c[st];
                     }
                 }
                 if (failed) ps.wait_failed = 1;
             } else if (tid == 32) {
                 // MMA issuer
-                long long it = n_item, rtc = n_rowt;
+                long long it = pp.n_item, rtc = pp.n_rowt;
                 for (int q = 0; q < my_rt && !failed; ++q, ++rtc) {
                     if (!tc::mbar_wait(&pp.a_full, (uint32_t)(rtc & 1), kWaitLimit)) {
                         failed = true;
@@ -555,10 +621,10 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                                          tc::smem_u32(sA) + kAT, bh, bh + kBT);
                         tc::mma_commit(&pp.acc_full[st]);
                         tc::mma_commit(&pp.b_empty[st]);
-                        ++commits[st];
+                        ++pp.commits[st];
                         if (ct == nct - 1) {
                             tc::mma_commit(&pp.a_empty);
-                            ++commits_a;
+                            ++pp.commits_a;
                         }
                     }
                     if (failed) break;
@@ -569,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 const int ew = warp - kEpiWarp0;
                 const int lg = warp & 3, half = ew >> 2;      // TMEM lane group, column half (box)
                 const int r = 32 * lg + lane;                 // tile row
-                long long it = n_item;
+                long long it = pp.n_item;
                 bool stop = false;
                 for (int q = 0; q < my_rt && !stop && !failed; ++q) {
                     for (int ct = 0; ct < nct; ++ct, ++it) {
@@ -617,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 // tile stores: each C tile goes back to the matrix once its
                 // eight epilogue warps have written it; its buffer is released
                 // when the store has read it
-                long long it = n_item;
+                long long it = pp.n_item;
                 for (int q = 0; q < my_rt && !failed; ++q) {
                     const int rt = rank + q * cs, i0 = r0 + rt * TR;
                     for (int ct = 0; ct < nct; ++ct, ++it) {
@@ -641,30 +707,31 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 tc::bulk_wait_all();
                 tc::fence_async_global();
             }
-            // every thread advances the counters identically
-            n_item += (long long)my_rt * nct;
-            n_rowt += my_rt;
             // drain: the producer's loads and the MMAs have landed (a no-op
             // unless a wait gave up) before the buffers are reused
             if (tid == 0) {
-                if (armed_a) tc::mbar_wait(&pp.a_full, (uint32_t)((armed_a - 1) & 1), kWaitLimit);
+                if (pp.armed_a) tc::mbar_wait(&pp.a_full, (uint32_t)((pp.armed_a - 1) & 1), kWaitLimit);
                 for (int b = 0; b < kStages; ++b) {
-                    if (armed_b[b]) tc::mbar_wait(&pp.b_full[b], (uint32_t)((armed_b[b] - 1) & 1), kWaitLimit);
-                    if (armed_c[b]) tc::mbar_wait(&pp.c_full[b], (uint32_t)((armed_c[b] - 1) & 1), kWaitLimit);
+                    if (pp.armed_b[b]) tc::mbar_wait(&pp.b_full[b], (uint32_t)((pp.armed_b[b] - 1) & 1), kWaitLimit);
+                    if (pp.armed_c[b]) tc::mbar_wait(&pp.c_full[b], (uint32_t)((pp.armed_c[b] - 1) & 1), kWaitLimit);
                 }
             } else if (tid == 32) {
                 for (int b = 0; b < kStages; ++b)
-                    if (commits[b]) {
-                        tc::mbar_wait(&pp.acc_full[b], (uint32_t)((commits[b] - 1) & 1), kWaitLimit);
-                        tc::mbar_wait(&pp.b_empty[b], (uint32_t)((commits[b] - 1) & 1), kWaitLimit);
+                    if (pp.commits[b]) {
+                        tc::mbar_wait(&pp.acc_full[b], (uint32_t)((pp.commits[b] - 1) & 1), kWaitLimit);
+                        tc::mbar_wait(&pp.b_empty[b], (uint32_t)((pp.commits[b] - 1) & 1), kWaitLimit);
                     }
-                if (commits_a) tc::mbar_wait(&pp.a_empty, (uint32_t)((commits_a - 1) & 1), kWaitLimit);
+                if (pp.commits_a) tc::mbar_wait(&pp.a_empty, (uint32_t)((pp.commits_a - 1) & 1), kWaitLimit);
             }
             tc::fence_async_smem();   // the staging buffers are reused by generic accesses next
             tc::tc_fence_before();
             __syncthreads();
             tc::tc_fence_after();
             if (ps.wait_failed) failed = true;
+            if (tid == 0) {   // read again at the next panel's update, after its barriers
+                pp.n_item += (long long)my_rt * nct;
+                pp.n_rowt += my_rt;
+            }
         }
         sys_sync(cs, true);
     }
