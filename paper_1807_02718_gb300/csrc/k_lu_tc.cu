@@ -49,6 +49,7 @@
 #include <cuda_bf16.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "fh_internal.h"
 #include "tc_gemm.cuh"
@@ -63,20 +64,15 @@ constexpr int kWarps = kThreads / 32;
 constexpr int NB = 32;                  // panel width (complex columns)
 constexpr int TR = 128;                 // rows per tile (TMEM lanes)
 constexpr int TCC = 32;                 // complex columns per tile (64 accumulator columns)
-constexpr int kStages = 2;              // pipeline depth of the trailing update (B, C, accumulators)
+constexpr int kMaxStages = 3;           // pipeline depth of the trailing update (B, C, accumulators)
 constexpr int kMaxCluster = 8;
 constexpr int kMaxMoved = 2 * NB;
-constexpr int kATile = TR * 2 * NB * 4;        // A operand (hi or lo) at 4 bytes per element: 32 KiB
-constexpr int kBTile = 2 * TCC * 2 * NB * 4;   // B operand (hi or lo): 16 KiB
 constexpr int kCBox = TR * 32 * 4;             // one 128 x 32-float box (tensor map box): 16 KiB
 constexpr int kCBoxes = 2 * TCC / 32;          // boxes per C tile
 constexpr int kCTile = kCBoxes * kCBox;
-constexpr int kDynSmem = 1024 + 2 * kATile + kStages * (2 * kBTile + kCTile);
 constexpr long long kWaitLimit = 1LL << 22;
 constexpr int kEpiWarp0 = 4, kEpiWarps = 8;    // epilogue warps 4 .. 11
 constexpr int kStoreTid = 64;                  // issues the tile stores (warp 2)
-constexpr int kTmemCols = kStages * 2 * TCC < 32 ? 32 : kStages * 2 * TCC;   // accumulators (a power of two)
-static_assert((kTmemCols & (kTmemCols - 1)) == 0, "TMEM allocation is a power of two");
 static_assert(TCC == 16 || TCC == 32, "a C tile is one or two tensor-map boxes");
 constexpr int kEpiThreads = 32 * kEpiWarps;
 
@@ -84,6 +80,17 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 // rows (32 complex columns x {Re, Im}) of the 2 NB-long K dimension.
 template <int kKind> __host__ __device__ constexpr int a_tile_bytes() { return TR * 2 * NB * (kKind == 2 ? 4 : 2); }
 template <int kKind> __host__ __device__ constexpr int b_tile_bytes() { return 2 * TCC * 2 * NB * (kKind == 2 ? 4 : 2); }
+
+// Shared-memory staging of each kind: the split A operand of one row tile,
+// then per pipeline stage the split B operand of one column tile and the C
+// tile.  The half-size BF16 operands leave room for a third stage.
+template <int kKind> struct Layout {
+    static constexpr int kAT = a_tile_bytes<kKind>(), kBT = b_tile_bytes<kKind>();
+    static constexpr int kStages = kKind == 2 ? 2 : 3;
+    static constexpr int kDyn = 1024 + 2 * kAT + kStages * (2 * kBT + TR * 2 * TCC * 4);
+    static constexpr int kTmemCols = kStages * 2 * TCC <= 128 ? 128 : 256;   // accumulators (a power of two)
+    static_assert(kStages <= kMaxStages && kStages * 2 * TCC <= kTmemCols, "stages fit the barriers and TMEM");
+};
 
 template <int kKind> struct Op;
 template <> struct Op<2> {              // TF32
@@ -289,12 +296,12 @@ __device__ __forceinline__ void issue_mma(uint32_t tacc, uint32_t ah, uint32_t a
 // the B and C buffers and of the TMEM accumulators is used by items s, s+2, ...
 struct Pipe {
     uint64_t a_full, a_empty;
-    uint64_t b_full[kStages], b_empty[kStages], c_full[kStages], c_empty[kStages];
-    uint64_t acc_full[kStages], acc_empty[kStages], c_written[kStages];
+    uint64_t b_full[kMaxStages], b_empty[kMaxStages], c_full[kMaxStages], c_empty[kMaxStages];
+    uint64_t acc_full[kMaxStages], acc_empty[kMaxStages], c_written[kMaxStages];
     // items (row tile, column tile) and row tiles processed over all panels;
     // the loads the producer armed on each full barrier, the MMA thread's commits
     long long n_item, n_rowt;
-    int armed_a, armed_b[kStages], armed_c[kStages], commits[kStages], commits_a;
+    int armed_a, armed_b[kMaxStages], armed_c[kMaxStages], commits[kMaxStages], commits_a;
 };
 
 // Pointer into the shared memory of CTA r of this system's cluster.
@@ -318,13 +325,14 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     extern __shared__ uint8_t dsm[];
     __shared__ __align__(16) PanelShared ps;
     __shared__ __align__(8) Pipe pp;
-    constexpr int kAT = a_tile_bytes<kKind>(), kBT = b_tile_bytes<kKind>();
+    constexpr int kAT = Layout<kKind>::kAT, kBT = Layout<kKind>::kBT, kStages = Layout<kKind>::kStages;
+    constexpr int kTmemCols = Layout<kKind>::kTmemCols;
     uint8_t *stage = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = stage;                                                // hi, lo
-    uint8_t *sB = stage + 2 * kATile;                                   // stages x (hi, lo)
-    uint8_t *sC = sB + kStages * 2 * kBTile;                            // stages x C tile (1 KiB aligned)
+    uint8_t *sB = stage + 2 * kAT;                                      // stages x (hi, lo)
+    uint8_t *sC = sB + kStages * 2 * kBT;                               // stages x C tile (1 KiB aligned)
     float4 *gbuf = reinterpret_cast<float4 *>(sB);                      // row gather (B + C)
-    constexpr int kGather = kStages * (2 * kBTile + kCTile) / 16;       // float4 in gbuf
+    constexpr int kGather = kStages * (2 * kBT + kCTile) / 16;          // float4 in gbuf
 
     const int cs = kMulti ? cs_arg : 1;
     const int rank = kMulti ? (int)cg::this_cluster().block_rank() : 0;
@@ -384,7 +392,117 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         int mypos = myslot;
         bool active = own;
 
-        // 1. panel factorisation in registers
+        // 1. panel factorisation in registers, four columns per step of a
+        // short rolled loop: v rotates left by four after each step, so that
+        // v[i] is column q0 + i of the step and v[e] column q0 + e (e < 32 - q0;
+        // the finished columns wrap to the end and come back in place after
+        // the eighth step).  Two loop bodies, all 32 entries while q0 < 16 and
+        // the first 16 after, keep the code small enough for the instruction
+        // cache; the entries past the panel are skipped by predicate.
+        if constexpr (kMulti) {
+            auto panel_step = [&](auto rows_c, auto group_c, const int q0) {
+                constexpr int kRows = decltype(rows_c)::value, kGroup = decltype(group_c)::value;
+                {
+    #pragma unroll
+                    for (int i = 0; i < kGroup; ++i) {
+                        const int cl = q0 + i;
+                        if (cl >= nb || bad) continue;
+                        const int pb = cl & 1;
+                        const uint32_t khi = active ? __float_as_uint(fabsf(v[i].x) + fabsf(v[i].y)) : 0u;
+                        const uint32_t klo = active ? ~(uint32_t)mypos : 0u;
+                        uint32_t mh, ml;
+                        key_max(khi, klo, mh, ml);
+                        if (lane == 0) {
+                            ps.kh[pb][warp] = mh;
+                            ps.kl[pb][warp] = ml;
+                        }
+                        const float2 *row;
+                        {
+                            __syncthreads();
+                            const uint32_t h2 = lane < kWarps ? ps.kh[pb][lane] : 0u;
+                            const uint32_t l2 = lane < kWarps ? ps.kl[pb][lane] : 0u;
+                            key_max(h2, l2, mh, ml);
+                            // this CTA's candidate to every CTA: the winning thread (or, when no
+                            // row of this CTA is left, warp 0 with an empty key) fills this
+                            // CTA's slot, then its warp copies the slot to the other CTAs, one
+                            // 16-byte chunk per lane and step (the key and the row from column cl)
+                            const bool none = mh == 0u && ml == 0u;
+                            const bool win = active && khi == mh && klo == ml;
+                            if (none ? warp == 0 : __ballot_sync(0xffffffffu, win) != 0u) {
+                                Cand &mine = ps.cand[pb][rank];
+                                float4 *m4 = reinterpret_cast<float4 *>(&mine);
+                                if (win) {
+                                    m4[0] = make_float4(__uint_as_float(mh), __uint_as_float(ml), 0.f, 0.f);
+    #pragma unroll
+                                    for (int e = i & ~1; e < kRows; e += 2)
+                                        if (q0 + e < NB)
+                                            m4[1 + (q0 + e) / 2] = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
+                                } else if (none && lane == 0) {
+                                    m4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                }
+                                __syncwarp();
+                                const int h0 = cl / 2, per = none ? 1 : 1 + NB / 2 - h0;
+                                for (int t = lane; t < (cs - 1) * per; t += 32) {
+                                    const int rr = t / per, j = t - rr * per;
+                                    const int f = j == 0 ? 0 : h0 + j;
+                                    float4 *dst = reinterpret_cast<float4 *>(at_rank(&mine, cs, rr < rank ? rr : rr + 1));
+                                    dst[f] = m4[f];
+                                }
+                            }
+                            sys_sync(cs, false);
+                            const uint32_t h3 = lane < cs ? ps.cand[pb][lane].kh : 0u;
+                            const uint32_t l3 = lane < cs ? ps.cand[pb][lane].kl : 0u;
+                            key_max(h3, l3, mh, ml);
+                            const uint32_t hit = __ballot_sync(0xffffffffu, lane < cs && h3 == mh && l3 == ml);
+                            row = ps.cand[pb][__ffs(hit) - 1].row;
+                        }
+                        // zero or non-finite pivot, or no row left: the same verdict in every CTA
+                        if (ml == 0u || mh == 0u || mh >= 0x7F800000u) {
+                            if (rank == 0 && tid == 0) info[s] = k0 + cl + 1;
+                            bad = true;
+                            continue;
+                        }
+                        const int wpos = (int)~ml;
+                        const float2 pvt = row[cl];
+                        const float rd = 1.f / (pvt.x * pvt.x + pvt.y * pvt.y);
+                        const float2 pinv = make_float2(pvt.x * rd, -pvt.y * rd);
+                        if (active && mypos == wpos) {
+                            mypos = cl;
+                            active = false;
+                        } else if (active && mypos == cl) {
+                            mypos = wpos;        // swapped with the pivot row's position
+                        }
+                        if (active) {
+                            const float2 l = cmul(v[i], pinv);
+                            v[i] = l;
+    #pragma unroll
+                            for (int e = i + 1; e < kRows; ++e)
+                                if (q0 + e < NB) {
+                                    const float2 u = row[q0 + e];
+                                    v[e].x -= l.x * u.x - l.y * u.y;
+                                    v[e].y -= l.x * u.y + l.y * u.x;
+                                }
+                        }
+                    }
+                    if constexpr (kGroup < NB) {
+                        float2 t[kGroup];
+    #pragma unroll
+                        for (int e = 0; e < kGroup; ++e) t[e] = v[e];
+    #pragma unroll
+                        for (int e = 0; e + kGroup < NB; ++e) v[e] = v[e + kGroup];
+    #pragma unroll
+                        for (int e = 0; e < kGroup; ++e) v[NB - kGroup + e] = t[e];
+                    }
+                }
+            };
+#pragma unroll 1
+            for (int q0 = 0; q0 < NB / 2; q0 += 4)
+                panel_step(std::integral_constant<int, NB>{}, std::integral_constant<int, 4>{}, q0);
+#pragma unroll 1
+            for (int q0 = NB / 2; q0 < NB; q0 += 4)
+                panel_step(std::integral_constant<int, NB / 2>{}, std::integral_constant<int, 4>{}, q0);
+        } else {
+            // a cluster of one: fully unrolled (the column work dominates here)
 #pragma unroll
         for (int cl = 0; cl < NB; ++cl) {
             if (cl >= nb || bad) continue;
@@ -475,6 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     v[q].y -= l.x * u.y + l.y * u.x;
                 }
             }
+        }
         }
         if (bad) break;
 
@@ -586,7 +705,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                             failed = true;
                             break;
                         }
-                        uint8_t *bdst = sB + st * 2 * kBTile, *cdst = sC + st * kCTile;
+                        uint8_t *bdst = sB + st * 2 * kBT, *cdst = sC + st * kCTile;
                         tc::mbar_arrive_tx(&pp.b_full[st], 2 * kBT);
                         tc::bulk_load(bdst, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[st]);
                         ++pp.armed_b[st];
@@ -616,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                             break;
                         }
                         tc::tc_fence_after();
-                        const uint32_t bh = tc::smem_u32(sB + st * 2 * kBTile);
+                        const uint32_t bh = tc::smem_u32(sB + st * 2 * kBT);
                         issue_mma<kKind>(taddr + (uint32_t)(st * 2 * TCC), tc::smem_u32(sA),
                                          tc::smem_u32(sA) + kAT, bh, bh + kBT);
                         tc::mma_commit(&pp.acc_full[st]);
@@ -792,7 +911,7 @@ cudaError_t launch_group(const int *order, int count, int cs, const int *N, cons
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(count * cs));
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = kDynSmem;
+    cfg.dynamicSmemBytes = Layout<kKind>::kDyn;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -896,7 +1015,7 @@ cudaError_t launch_lu_factor_tc(int kind, int rows_per_cta, const int *order, co
         const void *fns[4] = {(const void *)lu_factor_tc_kernel<2, false>, (const void *)lu_factor_tc_kernel<2, true>,
                               (const void *)lu_factor_tc_kernel<1, false>, (const void *)lu_factor_tc_kernel<1, true>};
         for (int f = kind == 2 ? 0 : 2, e0 = f + 2; f < e0; ++f) {
-            const cudaError_t e = ensure_smem_attr(fns[f], kDynSmem, attr[f]);
+            const cudaError_t e = ensure_smem_attr(fns[f], f < 2 ? Layout<2>::kDyn : Layout<1>::kDyn, attr[f]);
             if (e != cudaSuccess) return e;
         }
     }
