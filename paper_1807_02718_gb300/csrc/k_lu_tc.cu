@@ -31,16 +31,16 @@
 //   3. U12 = L11^{-1} A12 by forward substitution, one column per thread, over
 //      the same column ranges;
 //   4. A22 -= L21 U12: 128-row tiles are dealt round-robin to the CTAs and
-//      processed by three warp roles over a two-stage pipeline: one thread
-//      (the producer) brings in the operand tiles with the TMA engine -- the
-//      split L21 rows (bulk copy, once per row tile) and the split U12
-//      columns (bulk copy, per 32-column tile), both written in the MMA's
-//      shared-memory layout by steps 2 and 3, and the C tile of the row-major
-//      matrix (tiled tensor load, 128-byte swizzle) -- one thread issues the
-//      MMAs into one of two TMEM accumulators, and eight epilogue warps
-//      subtract the accumulator from the C tile in shared memory and write it
-//      back with a tiled tensor store.  Stages are handed over through
-//      mbarriers (bounded waits).
+//      processed by warp roles over a pipeline of two (TF32) or three (BF16)
+//      stages: one thread (the producer) brings in the operand tiles with the
+//      TMA engine -- the split L21 rows (bulk copy, once per row tile) and
+//      the split U12 columns (bulk copy, per 32-column tile), both written in
+//      the MMA's shared-memory layout by steps 2 and 3 -- one thread issues
+//      the MMAs into the stage's TMEM accumulator, eight epilogue warps write
+//      the negated accumulator into the stage's shared-memory tile (128-byte
+//      swizzle), and one thread adds that tile into the row-major matrix with
+//      a tiled tensor reduction (FP32 add at L2), so that C is never loaded
+//      into the SM.  Stages are handed over through mbarriers (bounded waits).
 // Cluster barriers separate the steps; a cluster of one uses __syncthreads.
 #include <climits>
 #include <cooperative_groups.h>
@@ -296,12 +296,12 @@ __device__ __forceinline__ void issue_mma(uint32_t tacc, uint32_t ah, uint32_t a
 // the B and C buffers and of the TMEM accumulators is used by items s, s+2, ...
 struct Pipe {
     uint64_t a_full, a_empty;
-    uint64_t b_full[kMaxStages], b_empty[kMaxStages], c_full[kMaxStages], c_empty[kMaxStages];
+    uint64_t b_full[kMaxStages], b_empty[kMaxStages], c_empty[kMaxStages];
     uint64_t acc_full[kMaxStages], acc_empty[kMaxStages], c_written[kMaxStages];
     // items (row tile, column tile) and row tiles processed over all panels;
     // the loads the producer armed on each full barrier, the MMA thread's commits
     long long n_item, n_rowt;
-    int armed_a, armed_b[kMaxStages], armed_c[kMaxStages], commits[kMaxStages], commits_a;
+    int armed_a, armed_b[kMaxStages], commits[kMaxStages], commits_a;
 };
 
 // Pointer into the shared memory of CTA r of this system's cluster.
@@ -352,7 +352,6 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         for (int b = 0; b < kStages; ++b) {
             tc::mbar_init(&pp.b_full[b], 1);
             tc::mbar_init(&pp.b_empty[b], 1);
-            tc::mbar_init(&pp.c_full[b], 1);
             tc::mbar_init(&pp.c_empty[b], 1);
             tc::mbar_init(&pp.acc_full[b], 1);
             tc::mbar_init(&pp.acc_empty[b], kEpiWarps);
@@ -361,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         ps.wait_failed = 0;
         pp.n_item = pp.n_rowt = 0;
         pp.armed_a = pp.commits_a = 0;
-        for (int b = 0; b < kStages; ++b) pp.armed_b[b] = pp.armed_c[b] = pp.commits[b] = 0;
+        for (int b = 0; b < kStages; ++b) pp.armed_b[b] = pp.commits[b] = 0;
     }
     for (int i = tid; i < 16 * (NB + 1); i += kThreads) ps.l11[NB + i / (NB + 1)][i % (NB + 1)] = make_float2(0.f, 0.f);
     if (rank == 0)   // pv: factored position -> original row, while factoring
@@ -686,7 +685,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             const int nrt = (m2 + TR - 1) / TR, nct = (m2 + TCC - 1) / TCC;
             const int my_rt = rank < nrt ? (nrt - 1 - rank) / cs + 1 : 0;   // row tiles of this CTA
             if (tid == 0) {
-                // producer: A once per row tile, B and C per item
+                // producer: A once per row tile, B per item
                 long long it = pp.n_item, rtc = pp.n_rowt;
                 for (int q = 0; q < my_rt && !failed; ++q, ++rtc) {
                     const int rt = rank + q * cs, i0 = r0 + rt * TR;
@@ -700,21 +699,13 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     for (int ct = 0; ct < nct; ++ct, ++it) {
                         const int st = (int)(it % kStages);
                         const long long u = it / kStages;
-                        if (u > 0 && (!tc::mbar_wait(&pp.b_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit) ||
-                                      !tc::mbar_wait(&pp.c_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
+                        if (u > 0 && !tc::mbar_wait(&pp.b_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit)) {
                             failed = true;
                             break;
                         }
-                        uint8_t *bdst = sB + st * 2 * kBT, *cdst = sC + st * kCTile;
                         tc::mbar_arrive_tx(&pp.b_full[st], 2 * kBT);
-                        tc::bulk_load(bdst, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[st]);
+                        tc::bulk_load(sB + st * 2 * kBT, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[st]);
                         ++pp.armed_b[st];
-                        const int x = 2 * (r0 + ct * TCC);
-                        tc::mbar_arrive_tx(&pp.c_full[st], kCTile);
-#pragma unroll
-                        for (int bx = 0; bx < kCBoxes; ++bx)
-                            tc::tma_load_2d(cdst + bx * kCBox, tmap, x + 32 * bx, i0, &pp.c_full[st]);
-                        ++pp.armed_c[st];
                     }
                 }
                 if (failed) ps.wait_failed = 1;
@@ -750,7 +741,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 }
                 if (failed) ps.wait_failed = 1;
             } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
-                // epilogue: C -= accumulator in the shared-memory C tile
+                // epilogue: the negated accumulator into the shared-memory tile
+                // of the stage, once the reduction of its previous item has read it
                 const int ew = warp - kEpiWarp0;
                 const int lg = warp & 3, half = ew >> 2;      // TMEM lane group, column half (box)
                 const int r = 32 * lg + lane;                 // tile row
@@ -761,7 +753,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         const int st = (int)(it % kStages);
                         const uint32_t par = (uint32_t)((it / kStages) & 1);
                         bool got = tc::mbar_wait(&pp.acc_full[st], par, kWaitLimit);
-                        got = got && tc::mbar_wait(&pp.c_full[st], par, kWaitLimit);
+                        if (it >= kStages)
+                            got = got && tc::mbar_wait(&pp.c_empty[st], par ^ 1u, kWaitLimit);
                         if (tc::bar_or(1, kEpiThreads, !got)) {   // the same verdict in every epilogue thread
                             stop = true;
                             break;
@@ -782,14 +775,9 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                             const int f = TCC * half + 4 * c;             // float column within the tile
                             float4 *row = reinterpret_cast<float4 *>(sC + st * kCTile + (f / 32) * kCBox + r * 128);
                             float4 *pc = row + (((f % 32) / 4) ^ (r & 7));  // 128-byte swizzle of the box
-                            float4 x = *pc;
-                            x.x -= d[4 * c];
-                            x.y -= d[4 * c + 1];
-                            x.z -= d[4 * c + 2];
-                            x.w -= d[4 * c + 3];
-                            *pc = x;
+                            *pc = make_float4(-d[4 * c], -d[4 * c + 1], -d[4 * c + 2], -d[4 * c + 3]);
                         }
-                        tc::fence_async_smem();   // the tile store (async proxy) reads these writes
+                        tc::fence_async_smem();   // the tile reduction (async proxy) reads these writes
                         __syncwarp();
                         if (lane == 0) tc::mbar_arrive(&pp.c_written[st]);
                     }
@@ -799,9 +787,9 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     if (ew == 0 && lane == 0) ps.wait_failed = 1;
                 }
             } else if (tid == kStoreTid) {
-                // tile stores: each C tile goes back to the matrix once its
-                // eight epilogue warps have written it; its buffer is released
-                // when the store has read it
+                // tile reductions: each tile is added into the matrix (C +=
+                // -L21 U12, at L2) once its eight epilogue warps have written
+                // it; its buffer is released when the reduction has read it
                 long long it = pp.n_item;
                 for (int q = 0; q < my_rt && !failed; ++q) {
                     const int rt = rank + q * cs, i0 = r0 + rt * TR;
@@ -815,14 +803,14 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         uint8_t *src = sC + st * kCTile;
 #pragma unroll
                         for (int bx = 0; bx < kCBoxes; ++bx)
-                            tc::tma_store_2d(tmap, x + 32 * bx, i0, src + bx * kCBox);
+                            tc::tma_reduce_add_2d(tmap, x + 32 * bx, i0, src + bx * kCBox);
                         tc::bulk_commit();
                         tc::bulk_wait_read();
                         tc::mbar_arrive(&pp.c_empty[st]);
                     }
                 }
                 if (failed) ps.wait_failed = 1;
-                // the stores are in global memory before the next panel reads them
+                // the reductions are in global memory before the next panel reads them
                 tc::bulk_wait_all();
                 tc::fence_async_global();
             }
@@ -830,10 +818,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             // unless a wait gave up) before the buffers are reused
             if (tid == 0) {
                 if (pp.armed_a) tc::mbar_wait(&pp.a_full, (uint32_t)((pp.armed_a - 1) & 1), kWaitLimit);
-                for (int b = 0; b < kStages; ++b) {
+                for (int b = 0; b < kStages; ++b)
                     if (pp.armed_b[b]) tc::mbar_wait(&pp.b_full[b], (uint32_t)((pp.armed_b[b] - 1) & 1), kWaitLimit);
-                    if (pp.armed_c[b]) tc::mbar_wait(&pp.c_full[b], (uint32_t)((pp.armed_c[b] - 1) & 1), kWaitLimit);
-                }
             } else if (tid == 32) {
                 for (int b = 0; b < kStages; ++b)
                     if (pp.commits[b]) {

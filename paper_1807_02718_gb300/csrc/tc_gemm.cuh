@@ -136,6 +136,13 @@ __device__ __forceinline__ void tma_store_2d(const void *tmap, int x, int y, con
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
                  ::"l"(tmap), "r"(x), "r"(y), "r"(smem_u32(src)) : "memory");
 }
+// Tiled tensor reduction: adds the shared-memory box to the tensor at (x, y)
+// in global memory (element-wise FP32 add performed at L2); elements outside
+// the tensor are not touched.
+__device__ __forceinline__ void tma_reduce_add_2d(const void *tmap, int x, int y, const void *src) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(tmap), "r"(x), "r"(y), "r"(smem_u32(src)) : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Wait until the committed bulk stores have read their shared-memory source.
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
