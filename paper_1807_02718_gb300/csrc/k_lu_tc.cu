@@ -31,16 +31,18 @@
 //   3. U12 = L11^{-1} A12 by forward substitution, one column per thread, over
 //      the same column ranges;
 //   4. A22 -= L21 U12: 128-row tiles are dealt round-robin to the CTAs and
-//      processed by warp roles over a pipeline of two (TF32) or three (BF16)
-//      stages: one thread (the producer) brings in the operand tiles with the
-//      TMA engine -- the split L21 rows (bulk copy, once per row tile) and
-//      the split U12 columns (bulk copy, per 32-column tile), both written in
-//      the MMA's shared-memory layout by steps 2 and 3 -- one thread issues
-//      the MMAs into the stage's TMEM accumulator, eight epilogue warps write
-//      the negated accumulator into the stage's shared-memory tile (128-byte
-//      swizzle), and one thread adds that tile into the row-major matrix with
-//      a tiled tensor reduction (FP32 add at L2), so that C is never loaded
-//      into the SM.  Stages are handed over through mbarriers (bounded waits).
+//      processed by warp roles over a two-stage pipeline (TMEM accumulators
+//      and output tiles) fed by a ring of two (TF32) or six (BF16) B tiles:
+//      one thread (the producer) brings in the operand tiles with the TMA
+//      engine -- the split L21 rows (bulk copy, once per row tile) and the
+//      split U12 columns (bulk copy, per 32-column tile), both written in the
+//      MMA's shared-memory layout by steps 2 and 3 -- one thread issues the
+//      MMAs into the stage's accumulator, one group of four epilogue warps per
+//      stage writes the negated accumulator into the stage's shared-memory
+//      tile (128-byte swizzle), and one thread adds that tile into the
+//      row-major matrix with a tiled tensor reduction (FP32 add at L2), so
+//      that C is never loaded into the SM.  Stages are handed over through
+//      mbarriers (bounded waits).
 // Cluster barriers separate the steps; a cluster of one uses __syncthreads.
 #include <climits>
 #include <cooperative_groups.h>
@@ -64,32 +66,34 @@ constexpr int kWarps = kThreads / 32;
 constexpr int NB = 32;                  // panel width (complex columns)
 constexpr int TR = 128;                 // rows per tile (TMEM lanes)
 constexpr int TCC = 32;                 // complex columns per tile (64 accumulator columns)
-constexpr int kMaxStages = 3;           // pipeline depth of the trailing update (B, C, accumulators)
+constexpr int kMaxStages = 3;           // pipeline depth of the trailing update (C tiles, accumulators)
+constexpr int kMaxBStages = 6;          // depth of the ring of B operand tiles
 constexpr int kMaxCluster = 8;
 constexpr int kMaxMoved = 2 * NB;
 constexpr int kCBox = TR * 32 * 4;             // one 128 x 32-float box (tensor map box): 16 KiB
 constexpr int kCBoxes = 2 * TCC / 32;          // boxes per C tile
 constexpr int kCTile = kCBoxes * kCBox;
 constexpr long long kWaitLimit = 1LL << 22;
-constexpr int kEpiWarp0 = 4, kEpiWarps = 8;    // epilogue warps 4 .. 11
+constexpr int kEpiWarp0 = 4;                   // epilogue warps from 4: one group of four per stage
 constexpr int kStoreTid = 64;                  // issues the tile stores (warp 2)
 static_assert(TCC == 16 || TCC == 32, "a C tile is one or two tensor-map boxes");
-constexpr int kEpiThreads = 32 * kEpiWarps;
 
 // Bytes of one operand tile (hi or lo) of each kind: A is 128 L21 rows, B 64
 // rows (32 complex columns x {Re, Im}) of the 2 NB-long K dimension.
 template <int kKind> __host__ __device__ constexpr int a_tile_bytes() { return TR * 2 * NB * (kKind == 2 ? 4 : 2); }
 template <int kKind> __host__ __device__ constexpr int b_tile_bytes() { return 2 * TCC * 2 * NB * (kKind == 2 ? 4 : 2); }
 
-// Shared-memory staging of each kind: the split A operand of one row tile,
-// then per pipeline stage the split B operand of one column tile and the C
-// tile.  The half-size BF16 operands leave room for a third stage.
+// Shared-memory staging of each kind: the split A operand of one row tile, a
+// ring of split B operand tiles (one per column tile) and per pipeline stage
+// the output tile.  The ring is as deep as the space allows: the half-size
+// BF16 operands leave room for six B tiles.
 template <int kKind> struct Layout {
     static constexpr int kAT = a_tile_bytes<kKind>(), kBT = b_tile_bytes<kKind>();
-    static constexpr int kStages = kKind == 2 ? 2 : 3;
-    static constexpr int kDyn = 1024 + 2 * kAT + kStages * (2 * kBT + TR * 2 * TCC * 4);
+    static constexpr int kStages = 2, kBStages = kKind == 2 ? 2 : 6;
+    static constexpr int kDyn = 1024 + 2 * kAT + kBStages * 2 * kBT + kStages * TR * 2 * TCC * 4;
     static constexpr int kTmemCols = kStages * 2 * TCC <= 128 ? 128 : 256;   // accumulators (a power of two)
-    static_assert(kStages <= kMaxStages && kStages * 2 * TCC <= kTmemCols, "stages fit the barriers and TMEM");
+    static_assert(kStages <= kMaxStages && kBStages <= kMaxBStages && kStages * 2 * TCC <= kTmemCols,
+                  "stages fit the barriers and TMEM");
 };
 
 template <int kKind> struct Op;
@@ -296,12 +300,12 @@ __device__ __forceinline__ void issue_mma(uint32_t tacc, uint32_t ah, uint32_t a
 // the B and C buffers and of the TMEM accumulators is used by items s, s+2, ...
 struct Pipe {
     uint64_t a_full, a_empty;
-    uint64_t b_full[kMaxStages], b_empty[kMaxStages], c_empty[kMaxStages];
+    uint64_t b_full[kMaxBStages], b_empty[kMaxBStages], c_empty[kMaxStages];
     uint64_t acc_full[kMaxStages], acc_empty[kMaxStages], c_written[kMaxStages];
     // items (row tile, column tile) and row tiles processed over all panels;
     // the loads the producer armed on each full barrier, the MMA thread's commits
     long long n_item, n_rowt;
-    int armed_a, armed_b[kMaxStages], commits[kMaxStages], commits_a;
+    int armed_a, armed_b[kMaxBStages], commits[kMaxStages], commits_b[kMaxBStages], commits_a;
 };
 
 // Pointer into the shared memory of CTA r of this system's cluster.
@@ -326,13 +330,14 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     __shared__ __align__(16) PanelShared ps;
     __shared__ __align__(8) Pipe pp;
     constexpr int kAT = Layout<kKind>::kAT, kBT = Layout<kKind>::kBT, kStages = Layout<kKind>::kStages;
+    constexpr int kBStages = Layout<kKind>::kBStages;
     constexpr int kTmemCols = Layout<kKind>::kTmemCols;
     uint8_t *stage = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = stage;                                                // hi, lo
     uint8_t *sB = stage + 2 * kAT;                                      // stages x (hi, lo)
-    uint8_t *sC = sB + kStages * 2 * kBT;                               // stages x C tile (1 KiB aligned)
+    uint8_t *sC = sB + kBStages * 2 * kBT;                              // stages x C tile (1 KiB aligned)
     float4 *gbuf = reinterpret_cast<float4 *>(sB);                      // row gather (B + C)
-    constexpr int kGather = kStages * (2 * kBT + kCTile) / 16;          // float4 in gbuf
+    constexpr int kGather = (kBStages * 2 * kBT + kStages * kCTile) / 16;   // float4 in gbuf
 
     const int cs = kMulti ? cs_arg : 1;
     const int rank = kMulti ? (int)cg::this_cluster().block_rank() : 0;
@@ -349,18 +354,21 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     if (tid == 0) {
         tc::mbar_init(&pp.a_full, 1);
         tc::mbar_init(&pp.a_empty, 1);
-        for (int b = 0; b < kStages; ++b) {
+        for (int b = 0; b < kBStages; ++b) {
             tc::mbar_init(&pp.b_full[b], 1);
             tc::mbar_init(&pp.b_empty[b], 1);
+            pp.armed_b[b] = pp.commits_b[b] = 0;
+        }
+        for (int b = 0; b < kStages; ++b) {
             tc::mbar_init(&pp.c_empty[b], 1);
             tc::mbar_init(&pp.acc_full[b], 1);
-            tc::mbar_init(&pp.acc_empty[b], kEpiWarps);
-            tc::mbar_init(&pp.c_written[b], kEpiWarps);
+            tc::mbar_init(&pp.acc_empty[b], 4);
+            tc::mbar_init(&pp.c_written[b], 4);
         }
         ps.wait_failed = 0;
         pp.n_item = pp.n_rowt = 0;
         pp.armed_a = pp.commits_a = 0;
-        for (int b = 0; b < kStages; ++b) pp.armed_b[b] = pp.commits[b] = 0;
+        for (int b = 0; b < kStages; ++b) pp.commits[b] = 0;
     }
     for (int i = tid; i < 16 * (NB + 1); i += kThreads) ps.l11[NB + i / (NB + 1)][i % (NB + 1)] = make_float2(0.f, 0.f);
     if (rank == 0)   // pv: factored position -> original row, while factoring
@@ -688,7 +696,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 // producer: A once per row tile, B per item
                 long long it = pp.n_item, rtc = pp.n_rowt;
                 for (int q = 0; q < my_rt && !failed; ++q, ++rtc) {
-                    const int rt = rank + q * cs, i0 = r0 + rt * TR;
+                    const int rt = rank + q * cs;
                     if (rtc > 0 && !tc::mbar_wait(&pp.a_empty, (uint32_t)((rtc - 1) & 1), kWaitLimit)) {
                         failed = true;
                         break;
@@ -697,15 +705,15 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     tc::bulk_load(sA, atiles + (size_t)rt * 2 * kAT, 2 * kAT, &pp.a_full);
                     ++pp.armed_a;
                     for (int ct = 0; ct < nct; ++ct, ++it) {
-                        const int st = (int)(it % kStages);
-                        const long long u = it / kStages;
-                        if (u > 0 && !tc::mbar_wait(&pp.b_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit)) {
+                        const int bs = (int)(it % kBStages);
+                        const long long ub = it / kBStages;
+                        if (ub > 0 && !tc::mbar_wait(&pp.b_empty[bs], (uint32_t)((ub - 1) & 1), kWaitLimit)) {
                             failed = true;
                             break;
                         }
-                        tc::mbar_arrive_tx(&pp.b_full[st], 2 * kBT);
-                        tc::bulk_load(sB + st * 2 * kBT, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[st]);
-                        ++pp.armed_b[st];
+                        tc::mbar_arrive_tx(&pp.b_full[bs], 2 * kBT);
+                        tc::bulk_load(sB + bs * 2 * kBT, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[bs]);
+                        ++pp.armed_b[bs];
                     }
                 }
                 if (failed) ps.wait_failed = 1;
@@ -718,20 +726,21 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         break;
                     }
                     for (int ct = 0; ct < nct; ++ct, ++it) {
-                        const int st = (int)(it % kStages);
+                        const int st = (int)(it % kStages), bs = (int)(it % kBStages);
                         const long long u = it / kStages;
-                        if (!tc::mbar_wait(&pp.b_full[st], (uint32_t)(u & 1), kWaitLimit) ||
+                        if (!tc::mbar_wait(&pp.b_full[bs], (uint32_t)((it / kBStages) & 1), kWaitLimit) ||
                             (u > 0 && !tc::mbar_wait(&pp.acc_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
                             failed = true;
                             break;
                         }
                         tc::tc_fence_after();
-                        const uint32_t bh = tc::smem_u32(sB + st * 2 * kBT);
+                        const uint32_t bh = tc::smem_u32(sB + bs * 2 * kBT);
                         issue_mma<kKind>(taddr + (uint32_t)(st * 2 * TCC), tc::smem_u32(sA),
                                          tc::smem_u32(sA) + kAT, bh, bh + kBT);
                         tc::mma_commit(&pp.acc_full[st]);
-                        tc::mma_commit(&pp.b_empty[st]);
+                        tc::mma_commit(&pp.b_empty[bs]);
                         ++pp.commits[st];
+                        ++pp.commits_b[bs];
                         if (ct == nct - 1) {
                             tc::mma_commit(&pp.a_empty);
                             ++pp.commits_a;
@@ -740,57 +749,59 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     if (failed) break;
                 }
                 if (failed) ps.wait_failed = 1;
-            } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
-                // epilogue: the negated accumulator into the shared-memory tile
-                // of the stage, once the reduction of its previous item has read it
-                const int ew = warp - kEpiWarp0;
-                const int lg = warp & 3, half = ew >> 2;      // TMEM lane group, column half (box)
-                const int r = 32 * lg + lane;                 // tile row
+            } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4 * kStages) {
+                // epilogue, one group of four warps per stage (the groups work on
+                // consecutive items at once): the negated accumulator into the
+                // stage's shared-memory tile, once the reduction of the stage's
+                // previous item has read it; thread: row r, all 2 TCC columns
+                const int g = (warp - kEpiWarp0) >> 2, lg = warp & 3;   // group (= stage), TMEM lane group
+                const int r = 32 * lg + lane;                           // tile row
                 long long it = pp.n_item;
                 bool stop = false;
                 for (int q = 0; q < my_rt && !stop && !failed; ++q) {
                     for (int ct = 0; ct < nct; ++ct, ++it) {
-                        const int st = (int)(it % kStages);
+                        if ((int)(it % kStages) != g) continue;
                         const uint32_t par = (uint32_t)((it / kStages) & 1);
-                        bool got = tc::mbar_wait(&pp.acc_full[st], par, kWaitLimit);
-                        if (it >= kStages)
-                            got = got && tc::mbar_wait(&pp.c_empty[st], par ^ 1u, kWaitLimit);
-                        if (tc::bar_or(1, kEpiThreads, !got)) {   // the same verdict in every epilogue thread
+                        bool got = tc::mbar_wait(&pp.acc_full[g], par, kWaitLimit);
+                        if (it >= kStages) got = got && tc::mbar_wait(&pp.c_empty[g], par ^ 1u, kWaitLimit);
+                        if (tc::bar_or(1 + g, 128, !got)) {   // the same verdict in the whole group
                             stop = true;
                             break;
                         }
                         tc::tc_fence_after();
-                        // this thread: accumulator columns [TCC half, TCC half + TCC) of row r
-                        float d[TCC];
-                        const uint32_t tacc = taddr + (uint32_t)(st * 2 * TCC) + ((uint32_t)(32 * lg) << 16) +
-                                              (uint32_t)(TCC * half);
+                        const uint32_t tacc = taddr + (uint32_t)(g * 2 * TCC) + ((uint32_t)(32 * lg) << 16);
 #pragma unroll
-                        for (int q = 0; q < TCC / 16; ++q)
-                            tc::tmem_ld16(tacc + 16 * q, *reinterpret_cast<float(*)[16]>(d + 16 * q));
-                        tc::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&pp.acc_empty[st]);
+                        for (int bx = 0; bx < kCBoxes; ++bx) {   // one 32-column box at a time
+                            float d[32];
+                            tc::tmem_ld16(tacc + 32 * bx, *reinterpret_cast<float(*)[16]>(d));
+                            tc::tmem_ld16(tacc + 32 * bx + 16, *reinterpret_cast<float(*)[16]>(d + 16));
+                            if (bx == kCBoxes - 1) {   // the accumulator is read
+                                tc::tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) tc::mbar_arrive(&pp.acc_empty[g]);
+                            }
+                            float4 *row = reinterpret_cast<float4 *>(sC + g * kCTile + bx * kCBox + r * 128);
 #pragma unroll
-                        for (int c = 0; c < TCC / 4; ++c) {
-                            const int f = TCC * half + 4 * c;             // float column within the tile
-                            float4 *row = reinterpret_cast<float4 *>(sC + st * kCTile + (f / 32) * kCBox + r * 128);
-                            float4 *pc = row + (((f % 32) / 4) ^ (r & 7));  // 128-byte swizzle of the box
-                            *pc = make_float4(-d[4 * c], -d[4 * c + 1], -d[4 * c + 2], -d[4 * c + 3]);
+                            for (int c = 0; c < 8; ++c)   // 128-byte swizzle of the box
+                                row[c ^ (r & 7)] = make_float4(-d[4 * c], -d[4 * c + 1], -d[4 * c + 2], -d[4 * c + 3]);
                         }
                         tc::fence_async_smem();   // the tile reduction (async proxy) reads these writes
                         __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&pp.c_written[st]);
+                        if (lane == 0) tc::mbar_arrive(&pp.c_written[g]);
                     }
                 }
                 if (stop) {
                     failed = true;
-                    if (ew == 0 && lane == 0) ps.wait_failed = 1;
+                    if (lg == 0 && lane == 0) ps.wait_failed = 1;
                 }
             } else if (tid == kStoreTid) {
                 // tile reductions: each tile is added into the matrix (C +=
-                // -L21 U12, at L2) once its eight epilogue warps have written
+                // -L21 U12, at L2) once its four epilogue warps have written
                 // it; its buffer is released when the reduction has read it
+                // (two reductions in flight: an item's buffer is released once
+                // the next item's reduction has been issued)
                 long long it = pp.n_item;
+                int prev = -1;   // stage of the previous item, its buffer not yet released
                 for (int q = 0; q < my_rt && !failed; ++q) {
                     const int rt = rank + q * cs, i0 = r0 + rt * TR;
                     for (int ct = 0; ct < nct; ++ct, ++it) {
@@ -805,9 +816,16 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                         for (int bx = 0; bx < kCBoxes; ++bx)
                             tc::tma_reduce_add_2d(tmap, x + 32 * bx, i0, src + bx * kCBox);
                         tc::bulk_commit();
-                        tc::bulk_wait_read();
-                        tc::mbar_arrive(&pp.c_empty[st]);
+                        if (prev >= 0) {
+                            tc::bulk_wait_read1();
+                            tc::mbar_arrive(&pp.c_empty[prev]);
+                        }
+                        prev = st;
                     }
+                }
+                if (prev >= 0) {
+                    tc::bulk_wait_read();
+                    tc::mbar_arrive(&pp.c_empty[prev]);
                 }
                 if (failed) ps.wait_failed = 1;
                 // the reductions are in global memory before the next panel reads them
@@ -818,14 +836,13 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             // unless a wait gave up) before the buffers are reused
             if (tid == 0) {
                 if (pp.armed_a) tc::mbar_wait(&pp.a_full, (uint32_t)((pp.armed_a - 1) & 1), kWaitLimit);
-                for (int b = 0; b < kStages; ++b)
+                for (int b = 0; b < kBStages; ++b)
                     if (pp.armed_b[b]) tc::mbar_wait(&pp.b_full[b], (uint32_t)((pp.armed_b[b] - 1) & 1), kWaitLimit);
             } else if (tid == 32) {
                 for (int b = 0; b < kStages; ++b)
-                    if (pp.commits[b]) {
-                        tc::mbar_wait(&pp.acc_full[b], (uint32_t)((pp.commits[b] - 1) & 1), kWaitLimit);
-                        tc::mbar_wait(&pp.b_empty[b], (uint32_t)((pp.commits[b] - 1) & 1), kWaitLimit);
-                    }
+                    if (pp.commits[b]) tc::mbar_wait(&pp.acc_full[b], (uint32_t)((pp.commits[b] - 1) & 1), kWaitLimit);
+                for (int b = 0; b < kBStages; ++b)
+                    if (pp.commits_b[b]) tc::mbar_wait(&pp.b_empty[b], (uint32_t)((pp.commits_b[b] - 1) & 1), kWaitLimit);
                 if (pp.commits_a) tc::mbar_wait(&pp.a_empty, (uint32_t)((pp.commits_a - 1) & 1), kWaitLimit);
             }
             tc::fence_async_smem();   // the staging buffers are reused by generic accesses next
