@@ -30,8 +30,8 @@
 //      each CTA over its own column range, through shared memory;
 //   3. U12 = L11^{-1} A12 by forward substitution, one column per thread, over
 //      the same column ranges;
-//   4. A22 -= L21 U12: 128-row tiles are dealt round-robin to the CTAs and
-//      processed by warp roles over a two-stage pipeline (TMEM accumulators
+//   4. A22 -= L21 U12: the items (128-row tile, 32-column tile) are split
+//      evenly over the CTAs in row-tile order and processed by warp roles over a two-stage pipeline (TMEM accumulators
 //      and output tiles) fed by a ring of two (TF32) or six (BF16) B tiles:
 //      one thread (the producer) brings in the operand tiles with the TMA
 //      engine -- the split L21 rows (bulk copy, once per row tile) and the
@@ -691,62 +691,66 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         const int r0 = k0 + nb, m2 = n - r0;
         if (m2 > 0) {
             const int nrt = (m2 + TR - 1) / TR, nct = (m2 + TCC - 1) / TCC;
-            const int my_rt = rank < nrt ? (nrt - 1 - rank) / cs + 1 : 0;   // row tiles of this CTA
+            // this CTA's items: an even share of the (row tile, column tile)
+            // sequence in row-tile order, i.e. up to two partial row tiles
+            // ("segments") besides whole ones
+            const long long n_items = (long long)nrt * nct;
+            const int t_lo = (int)(n_items * rank / cs), t_hi = (int)(n_items * (rank + 1) / cs);
+            const int n_seg = t_hi > t_lo ? (t_hi - 1) / nct - t_lo / nct + 1 : 0;
             if (tid == 0) {
-                // producer: A once per row tile, B per item
+                // producer: A once per segment, B per item
                 long long it = pp.n_item, rtc = pp.n_rowt;
-                for (int q = 0; q < my_rt && !failed; ++q, ++rtc) {
-                    const int rt = rank + q * cs;
-                    if (rtc > 0 && !tc::mbar_wait(&pp.a_empty, (uint32_t)((rtc - 1) & 1), kWaitLimit)) {
-                        failed = true;
-                        break;
-                    }
-                    tc::mbar_arrive_tx(&pp.a_full, 2 * kAT);
-                    tc::bulk_load(sA, atiles + (size_t)rt * 2 * kAT, 2 * kAT, &pp.a_full);
-                    ++pp.armed_a;
-                    for (int ct = 0; ct < nct; ++ct, ++it) {
-                        const int bs = (int)(it % kBStages);
-                        const long long ub = it / kBStages;
-                        if (ub > 0 && !tc::mbar_wait(&pp.b_empty[bs], (uint32_t)((ub - 1) & 1), kWaitLimit)) {
+                for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
+                    const int rt = t / nct, ct = t - rt * nct;
+                    if (t == t_lo || ct == 0) {
+                        if (rtc > 0 && !tc::mbar_wait(&pp.a_empty, (uint32_t)((rtc - 1) & 1), kWaitLimit)) {
                             failed = true;
                             break;
                         }
-                        tc::mbar_arrive_tx(&pp.b_full[bs], 2 * kBT);
-                        tc::bulk_load(sB + bs * 2 * kBT, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[bs]);
-                        ++pp.armed_b[bs];
+                        tc::mbar_arrive_tx(&pp.a_full, 2 * kAT);
+                        tc::bulk_load(sA, atiles + (size_t)rt * 2 * kAT, 2 * kAT, &pp.a_full);
+                        ++pp.armed_a;
+                        ++rtc;
                     }
+                    const int bs = (int)(it % kBStages);
+                    const long long ub = it / kBStages;
+                    if (ub > 0 && !tc::mbar_wait(&pp.b_empty[bs], (uint32_t)((ub - 1) & 1), kWaitLimit)) {
+                        failed = true;
+                        break;
+                    }
+                    tc::mbar_arrive_tx(&pp.b_full[bs], 2 * kBT);
+                    tc::bulk_load(sB + bs * 2 * kBT, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[bs]);
+                    ++pp.armed_b[bs];
                 }
                 if (failed) ps.wait_failed = 1;
             } else if (tid == 32) {
                 // MMA issuer
                 long long it = pp.n_item, rtc = pp.n_rowt;
-                for (int q = 0; q < my_rt && !failed; ++q, ++rtc) {
-                    if (!tc::mbar_wait(&pp.a_full, (uint32_t)(rtc & 1), kWaitLimit)) {
+                for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
+                    const int ct = t % nct;
+                    if ((t == t_lo || ct == 0) && !tc::mbar_wait(&pp.a_full, (uint32_t)((rtc++) & 1), kWaitLimit)) {
                         failed = true;
                         break;
                     }
-                    for (int ct = 0; ct < nct; ++ct, ++it) {
-                        const int st = (int)(it % kStages), bs = (int)(it % kBStages);
-                        const long long u = it / kStages;
-                        if (!tc::mbar_wait(&pp.b_full[bs], (uint32_t)((it / kBStages) & 1), kWaitLimit) ||
-                            (u > 0 && !tc::mbar_wait(&pp.acc_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
-                            failed = true;
-                            break;
-                        }
-                        tc::tc_fence_after();
-                        const uint32_t bh = tc::smem_u32(sB + bs * 2 * kBT);
-                        issue_mma<kKind>(taddr + (uint32_t)(st * 2 * TCC), tc::smem_u32(sA),
-                                         tc::smem_u32(sA) + kAT, bh, bh + kBT);
-                        tc::mma_commit(&pp.acc_full[st]);
-                        tc::mma_commit(&pp.b_empty[bs]);
-                        ++pp.commits[st];
-                        ++pp.commits_b[bs];
-                        if (ct == nct - 1) {
-                            tc::mma_commit(&pp.a_empty);
-                            ++pp.commits_a;
-                        }
+                    const int st = (int)(it % kStages), bs = (int)(it % kBStages);
+                    const long long u = it / kStages;
+                    if (!tc::mbar_wait(&pp.b_full[bs], (uint32_t)((it / kBStages) & 1), kWaitLimit) ||
+                        (u > 0 && !tc::mbar_wait(&pp.acc_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
+                        failed = true;
+                        break;
                     }
-                    if (failed) break;
+                    tc::tc_fence_after();
+                    const uint32_t bh = tc::smem_u32(sB + bs * 2 * kBT);
+                    issue_mma<kKind>(taddr + (uint32_t)(st * 2 * TCC), tc::smem_u32(sA),
+                                     tc::smem_u32(sA) + kAT, bh, bh + kBT);
+                    tc::mma_commit(&pp.acc_full[st]);
+                    tc::mma_commit(&pp.b_empty[bs]);
+                    ++pp.commits[st];
+                    ++pp.commits_b[bs];
+                    if (t == t_hi - 1 || ct == nct - 1) {   // the segment's A tile is read
+                        tc::mma_commit(&pp.a_empty);
+                        ++pp.commits_a;
+                    }
                 }
                 if (failed) ps.wait_failed = 1;
             } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4 * kStages) {
@@ -758,8 +762,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 const int r = 32 * lg + lane;                           // tile row
                 long long it = pp.n_item;
                 bool stop = false;
-                for (int q = 0; q < my_rt && !stop && !failed; ++q) {
-                    for (int ct = 0; ct < nct; ++ct, ++it) {
+                for (int t = t_lo; t < t_hi && !stop && !failed; ++t, ++it) {
+                    {
                         if ((int)(it % kStages) != g) continue;
                         const uint32_t par = (uint32_t)((it / kStages) & 1);
                         bool got = tc::mbar_wait(&pp.acc_full[g], par, kWaitLimit);
@@ -802,9 +806,9 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                 // the next item's reduction has been issued)
                 long long it = pp.n_item;
                 int prev = -1;   // stage of the previous item, its buffer not yet released
-                for (int q = 0; q < my_rt && !failed; ++q) {
-                    const int rt = rank + q * cs, i0 = r0 + rt * TR;
-                    for (int ct = 0; ct < nct; ++ct, ++it) {
+                for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
+                    const int rt = t / nct, ct = t - rt * nct, i0 = r0 + rt * TR;
+                    {
                         const int st = (int)(it % kStages);
                         if (!tc::mbar_wait(&pp.c_written[st], (uint32_t)((it / kStages) & 1), kWaitLimit)) {
                             failed = true;
@@ -851,8 +855,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             tc::tc_fence_after();
             if (ps.wait_failed) failed = true;
             if (tid == 0) {   // read again at the next panel's update, after its barriers
-                pp.n_item += (long long)my_rt * nct;
-                pp.n_rowt += my_rt;
+                pp.n_item += t_hi - t_lo;
+                pp.n_rowt += n_seg;
             }
         }
         sys_sync(cs, true);
