@@ -85,12 +85,16 @@ template <int kKind> __host__ __device__ constexpr int b_tile_bytes() { return 2
 
 // Shared-memory staging of each kind: the split A operand of one row tile, a
 // ring of split B operand tiles (one per column tile) and per pipeline stage
-// the output tile.  The ring is as deep as the space allows: the half-size
-// BF16 operands leave room for six B tiles.
+// the output tile.  With the half-size BF16 operands the tiles have room for
+// two panels in K (kPair): the trailing matrix is then updated once per pair
+// of panels, which halves its traffic.
 template <int kKind> struct Layout {
     static constexpr int kAT = a_tile_bytes<kKind>(), kBT = b_tile_bytes<kKind>();
-    static constexpr int kStages = 2, kBStages = kKind == 2 ? 2 : 6;
-    static constexpr int kDyn = 1024 + 2 * kAT + kBStages * 2 * kBT + kStages * TR * 2 * TCC * 4;
+    static constexpr bool kPair = kKind == 1;
+    static constexpr int kSlots = kPair ? 2 : 1;
+    static constexpr int kASpace = 2 * kSlots * kAT, kBSlot = 2 * kSlots * kBT;   // A (hi, lo); one ring slot
+    static constexpr int kStages = 2, kBStages = 2;
+    static constexpr int kDyn = 1024 + kASpace + kBStages * kBSlot + kStages * TR * 2 * TCC * 4;
     static constexpr int kTmemCols = kStages * 2 * TCC <= 128 ? 128 : 256;   // accumulators (a power of two)
     static_assert(kStages <= kMaxStages && kBStages <= kMaxBStages && kStages * 2 * TCC <= kTmemCols,
                   "stages fit the barriers and TMEM");
@@ -179,12 +183,17 @@ __device__ __forceinline__ void key_max(uint32_t h, uint32_t l, uint32_t &mh, ui
     ml = __reduce_max_sync(0xffffffffu, h == mh ? l : 0u);
 }
 
+// Operand tiles hold kSlots panels side by side in K (one panel, or two for
+// the combined update of a pair of panels); slot `slot` of a row holds the
+// 2 NB K values of one panel.
+
 // Step 2: row `r` (0..127) of L21 tile `tile` in the MMA operand layout
-// (K-major core matrices, hi tile then lo tile), from the 32 complex panel
-// values of that row.
-template <int kKind>
-__device__ __forceinline__ void put_a_row(uint8_t *tiles, int tile, int r, const float2 (&v)[NB]) {
-    constexpr int qpc = Op<kKind>::qpc, kRowB = 2 * NB * Op<kKind>::esize, kT = a_tile_bytes<kKind>();
+// (K-major core matrices, hi tile then lo tile), slot `slot`, from the 32
+// complex panel values of that row.
+template <int kKind, int kSlots>
+__device__ __forceinline__ void put_a_row(uint8_t *tiles, int tile, int r, const float2 (&v)[NB], int slot) {
+    constexpr int qpc = Op<kKind>::qpc, kPanB = 2 * NB * Op<kKind>::esize, kRowB = kSlots * kPanB;
+    constexpr int kT = kSlots * a_tile_bytes<kKind>();
     uint8_t *hi = tiles + (size_t)tile * 2 * kT, *lo = hi + kT;
 #pragma unroll
     for (int c = 0; c < NB / qpc; ++c) {
@@ -194,41 +203,19 @@ __device__ __forceinline__ void put_a_row(uint8_t *tiles, int tile, int r, const
             w[2 * h] = v[c * qpc + h].x;
             w[2 * h + 1] = v[c * qpc + h].y;
         }
-        const uint32_t off = tc::kmajor_offset(r, c * 16, kRowB);
+        const uint32_t off = tc::kmajor_offset(r, slot * kPanB + c * 16, kRowB);
         split_store<kKind>(w, hi + off, lo + off);
     }
 }
 
-// Step 3: the two B rows of U12 column `jj` (local to the trailing block):
-// row 2 (jj % 32) gives Re, row 2 (jj % 32) + 1 gives Im of output column jj,
-// in B tile jj / 32.  u[q] = U12(q, jj).
-template <int kKind>
-__device__ __forceinline__ void put_b_col(uint8_t *tiles, int jj, const float2 *u) {
-    constexpr int qpc = Op<kKind>::qpc, kRowB = 2 * NB * Op<kKind>::esize, kT = b_tile_bytes<kKind>();
-    uint8_t *hi = tiles + (size_t)(jj / TCC) * 2 * kT, *lo = hi + kT;
-    const int b = 2 * (jj % TCC);
-#pragma unroll
-    for (int c = 0; c < NB / qpc; ++c) {
-        float re[2 * qpc], im[2 * qpc];
-#pragma unroll
-        for (int h = 0; h < qpc; ++h) {
-            const float2 x = u[c * qpc + h];
-            re[2 * h] = x.x;
-            re[2 * h + 1] = -x.y;
-            im[2 * h] = x.y;
-            im[2 * h + 1] = x.x;
-        }
-        const uint32_t o0 = tc::kmajor_offset(b, c * 16, kRowB), o1 = tc::kmajor_offset(b + 1, c * 16, kRowB);
-        split_store<kKind>(re, hi + o0, lo + o0);
-        split_store<kKind>(im, hi + o1, lo + o1);
-    }
-}
-
 // Step 3, one group of four rows: the B-operand chunks of U12 rows
-// [4 g, 4 g + 4) of column `jj` (as put_b_col, for that slice of K).
-template <int kKind>
-__device__ __forceinline__ void put_b_group(uint8_t *tiles, int jj, int g, const float2 *u) {
-    constexpr int qpc = Op<kKind>::qpc, kRowB = 2 * NB * Op<kKind>::esize, kT = b_tile_bytes<kKind>();
+// [4 g, 4 g + 4) of column `jj` (local to the trailing block): row 2 (jj %
+// 32) gives Re, row 2 (jj % 32) + 1 gives Im of output column jj, in B tile
+// jj / 32, slot `slot`.
+template <int kKind, int kSlots>
+__device__ __forceinline__ void put_b_group(uint8_t *tiles, int jj, int g, const float2 *u, int slot) {
+    constexpr int qpc = Op<kKind>::qpc, kPanB = 2 * NB * Op<kKind>::esize, kRowB = kSlots * kPanB;
+    constexpr int kT = kSlots * b_tile_bytes<kKind>();
     uint8_t *hi = tiles + (size_t)(jj / TCC) * 2 * kT, *lo = hi + kT;
     const int b = 2 * (jj % TCC);
 #pragma unroll
@@ -243,11 +230,20 @@ __device__ __forceinline__ void put_b_group(uint8_t *tiles, int jj, int g, const
             im[2 * h] = x.y;
             im[2 * h + 1] = x.x;
         }
-        const uint32_t o0 = tc::kmajor_offset(b, c * 16, kRowB), o1 = tc::kmajor_offset(b + 1, c * 16, kRowB);
+        const uint32_t o0 = tc::kmajor_offset(b, slot * kPanB + c * 16, kRowB);
+        const uint32_t o1 = tc::kmajor_offset(b + 1, slot * kPanB + c * 16, kRowB);
         split_store<kKind>(re, hi + o0, lo + o0);
         split_store<kKind>(im, hi + o1, lo + o1);
     }
 }
+
+// Where step 3 stages the B operand of column jj: columns jj < split into
+// the one-panel tiles bt1 (column jj), the others into slot `slot` of the
+// two-panel tiles bt2 (column jj - split).
+struct BDest {
+    uint8_t *bt1, *bt2;
+    int split, slot;
+};
 
 // Step 3 for one column, rows in groups of four: x[0..3] are rows q0..q0+3,
 // eliminated into x[4..kRows) (rows q0 + 4 ..), stored, then the column
@@ -255,7 +251,7 @@ __device__ __forceinline__ void put_b_group(uint8_t *tiles, int jj, int g, const
 // keep the loop bodies short enough to stay in the instruction cache.
 template <int kKind, int kRows>
 __device__ __forceinline__ void trsm_groups(float2 (&x)[NB], int g0, int g1, const float2 (*l11)[NB + 1],
-                                            float2 *col, long long n, int nb, uint8_t *btiles, int jj) {
+                                            float2 *col, long long n, int nb, const BDest &bd, int jj) {
 #pragma unroll 1
     for (int g = g0; g < g1; ++g) {
         const int q0 = 4 * g;
@@ -271,17 +267,20 @@ __device__ __forceinline__ void trsm_groups(float2 (&x)[NB], int g0, int g1, con
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             if (q0 + i < nb) __stcg(col + (long long)(q0 + i) * n, x[i]);
-        if (nb == NB) put_b_group<kKind>(btiles, jj, g, x);
+        if (nb == NB) {
+            if (jj < bd.split) put_b_group<kKind, 1>(bd.bt1, jj, g, x, 0);
+            else put_b_group<kKind, 2>(bd.bt2, jj - bd.split, g, x, bd.slot);
+        }
 #pragma unroll
         for (int e = 0; e + 4 < kRows; ++e) x[e] = x[e + 4];
     }
 }
 
-// One 128 x 32-complex tile: hi*hi + hi*lo + lo*hi over the panel's K.
-template <int kKind>
+// One 128 x 32-complex tile: hi*hi + hi*lo + lo*hi over the K of kSlots panels.
+template <int kKind, int kSlots>
 __device__ __forceinline__ void issue_mma(uint32_t tacc, uint32_t ah, uint32_t al, uint32_t bh,
                                           uint32_t bl) {
-    constexpr int kRowB = 2 * NB * Op<kKind>::esize;
+    constexpr int kRowB = kSlots * 2 * NB * Op<kKind>::esize;
     constexpr uint32_t sbo = (kRowB / 16) * 128;
     constexpr int ksteps = kRowB / 32;          // 32 bytes of K per MMA
     constexpr uint32_t idesc = tc::instr_desc(kKind == 2 ? 2u : 1u, TR, 2 * TCC);
@@ -329,15 +328,19 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     extern __shared__ uint8_t dsm[];
     __shared__ __align__(16) PanelShared ps;
     __shared__ __align__(8) Pipe pp;
-    constexpr int kAT = Layout<kKind>::kAT, kBT = Layout<kKind>::kBT, kStages = Layout<kKind>::kStages;
-    constexpr int kBStages = Layout<kKind>::kBStages;
-    constexpr int kTmemCols = Layout<kKind>::kTmemCols;
+    using LT = Layout<kKind>;
+    constexpr int kAT = LT::kAT, kBT = LT::kBT, kStages = LT::kStages, kBStages = LT::kBStages;
+    constexpr int kTmemCols = LT::kTmemCols;
     uint8_t *stage = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = stage;                                                // hi, lo
-    uint8_t *sB = stage + 2 * kAT;                                      // stages x (hi, lo)
-    uint8_t *sC = sB + kBStages * 2 * kBT;                              // stages x C tile (1 KiB aligned)
+    uint8_t *sB = stage + LT::kASpace;                                  // ring of B tiles (hi, lo)
+    uint8_t *sC = sB + kBStages * LT::kBSlot;                           // stages x C tile (1 KiB aligned)
     float4 *gbuf = reinterpret_cast<float4 *>(sB);                      // row gather (B + C)
-    constexpr int kGather = (kBStages * 2 * kBT + kStages * kCTile) / 16;   // float4 in gbuf
+    constexpr int kGather = (kBStages * LT::kBSlot + kStages * kCTile) / 16;   // float4 in gbuf
+    // second panel of a pair: L21 of the first panel in the rows of the
+    // second's pivots (32 x 32), kept in the A space between the updates
+    float2 (*lpq)[NB + 2] = reinterpret_cast<float2 (*)[NB + 2]>(sA);
+    static_assert(NB * (NB + 2) * 8 <= LT::kASpace, "the pair's L block fits the A space");
 
     const int cs = kMulti ? cs_arg : 1;
     const int rank = kMulti ? (int)cg::this_cluster().block_rank() : 0;
@@ -347,6 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     int *pv = piv + vec_off[s];
     const CUtensorMap *tmap = tmaps + s;
     uint8_t *atiles = opnd + a_off[s], *btiles = opnd + b_off[s];
+    // two-panel B tiles after the one-panel ones (lu_tc_opnd_bytes)
+    uint8_t *b2tiles = btiles + (size_t)((max(n - NB, 0) + TCC - 1) / TCC) * 2 * kBT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int myslot = rank * kThreads + tid;
 
@@ -381,8 +386,13 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     if (cs > 1) cg::this_cluster().sync();   // every CTA running before shared memory is addressed remotely
 
     bool failed = false, bad = false;
+    // role of the panel: 0 alone, 1 first of a pair (its update reaches only
+    // the second panel's columns), 2 second of a pair (one update of the
+    // trailing matrix with both panels' K)
+    int role = 0;
 
     for (int k0 = 0; k0 < n; k0 += NB) {
+        role = role == 1 ? 2 : (LT::kPair && n - k0 > 2 * NB ? 1 : 0);
         const int nb = min(NB, n - k0), m = n - k0;
         if (tid == 0) ps.mv_cnt = 0;
         const bool own = myslot < m;
@@ -611,8 +621,12 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
 #pragma unroll
             for (int h = 0; h < NB / 2; ++h)
                 if (2 * h < nb) __stcg(dst + h, make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y));
-            if (mypos >= nb && nb == NB)
-                put_a_row<kKind>(atiles, (mypos - NB) / TR, (mypos - NB) % TR, v);
+            if (role != 2) {
+                if (mypos >= nb && nb == NB)
+                    put_a_row<kKind, 1>(atiles, (mypos - NB) / TR, (mypos - NB) % TR, v, 0);
+            } else if (mypos >= NB) {
+                put_a_row<kKind, 2>(atiles, (mypos - NB) / TR, (mypos - NB) % TR, v, 1);
+            }
             if (mypos < nb)
                 for (int r = 0; r < cs; ++r) {
                     float2 *l = at_rank(&ps.l11[mypos][0], cs, r);
@@ -620,6 +634,29 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
                     for (int q = 0; q < NB; ++q)
                         if (q < mypos) l[q] = v[q];
                 }
+            if (role == 2) {
+                // the row's L21 of the first panel (v is done with), from its
+                // place before the swaps of this panel: into slot 0 of the
+                // two-panel A tiles, or for a pivot row into row mypos of lpq
+                // at every CTA
+                const float4 *lp = reinterpret_cast<const float4 *>(a + (long long)(k0 + myslot) * n + (k0 - NB));
+#pragma unroll
+                for (int h = 0; h < NB / 2; ++h) {
+                    const float4 t = __ldcg(lp + h);
+                    v[2 * h] = make_float2(t.x, t.y);
+                    v[2 * h + 1] = make_float2(t.z, t.w);
+                }
+                if (mypos >= NB) {
+                    put_a_row<kKind, 2>(atiles, (mypos - NB) / TR, (mypos - NB) % TR, v, 0);
+                } else {
+                    for (int r = 0; r < cs; ++r) {
+                        float4 *dst = reinterpret_cast<float4 *>(at_rank(&lpq[mypos][0], cs, r));
+#pragma unroll
+                        for (int h = 0; h < NB / 2; ++h)
+                            dst[h] = make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
+                    }
+                }
+            }
             if (mypos != myslot)
                 for (int r = 0; r < cs; ++r) {
                     const int idx = atomicAdd(at_rank(&ps.mv_cnt, cs, r), 1);
@@ -672,14 +709,42 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         // one column per thread, all nb values in registers (one round of
         // loads), forward substitution with L11 from shared memory, then the
         // column to the matrix and to the staged B operand
+        // (second panel of a pair: first A12 -= L21(first panel) U12(first
+        // panel) in these rows, the update the first panel left out)
+        const BDest bd{btiles, b2tiles, role == 0 ? INT_MAX : role == 1 ? NB : 0, role == 2 ? 1 : 0};
+        // (U12 of the first panel over this CTA's columns, rows k0 - NB ..,
+        // into the gather space with coalesced loads: up[q][c - rc_lo])
+        float2 *up = reinterpret_cast<float2 *>(gbuf);
+        const int ncol = rc_hi - rc_lo;
+        // (at most 512 columns: a CTA owns 512 rows, so cs >= n / 512)
+        if (role == 2 && NB * ncol > 2 * kGather) failed = true;
+        if (role == 2 && !failed) {
+            for (int e = tid; e < NB * ncol; e += kThreads) {
+                const int q = e / ncol, c = e - q * ncol;
+                up[e] = __ldcg(a + (long long)(k0 - NB + q) * n + rc_lo + c + nb);
+            }
+            __syncthreads();
+        }
         for (int c = rc_lo + tid; c < rc_hi; c += kThreads) {
             float2 *col = a + (long long)k0 * n + c + nb;
             float2 x[NB];
 #pragma unroll
             for (int e = 0; e < NB; ++e)
                 x[e] = e < nb ? __ldcg(col + (long long)e * n) : make_float2(0.f, 0.f);
-            trsm_groups<kKind, NB>(x, 0, NB / 8, ps.l11, col, n, nb, btiles, c - k0);
-            trsm_groups<kKind, NB / 2>(x, NB / 8, NB / 4, ps.l11, col, n, nb, btiles, c - k0);
+            if (role == 2 && !failed) {
+#pragma unroll 2
+                for (int q = 0; q < NB; ++q) {
+                    const float2 u = up[q * ncol + (c - rc_lo)];
+#pragma unroll
+                    for (int e = 0; e < NB; ++e) {
+                        const float2 l = lpq[e][q];
+                        x[e].x -= l.x * u.x - l.y * u.y;
+                        x[e].y -= l.x * u.y + l.y * u.x;
+                    }
+                }
+            }
+            trsm_groups<kKind, NB>(x, 0, NB / 8, ps.l11, col, n, nb, bd, c - k0);
+            trsm_groups<kKind, NB / 2>(x, NB / 8, NB / 4, ps.l11, col, n, nb, bd, c - k0);
         }
         // the swaps, U12 and the staged operands (generic stores to global
         // memory) are read by the TMA engine below, which also overwrites the
@@ -687,177 +752,183 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         tc::fence_async_all();
         sys_sync(cs, true);
 
-        // 4. A22 -= L21 U12 on the tensor cores
+        // 4. A22 -= L21 U12 on the tensor cores: rows and columns from r0,
+        // nct column tiles; at / bt: the staged A and B tiles (kS panels in K)
         const int r0 = k0 + nb, m2 = n - r0;
-        if (m2 > 0) {
-            const int nrt = (m2 + TR - 1) / TR, nct = (m2 + TCC - 1) / TCC;
-            // this CTA's items: an even share of the (row tile, column tile)
-            // sequence in row-tile order, i.e. up to two partial row tiles
-            // ("segments") besides whole ones
-            const long long n_items = (long long)nrt * nct;
-            const int t_lo = (int)(n_items * rank / cs), t_hi = (int)(n_items * (rank + 1) / cs);
-            const int n_seg = t_hi > t_lo ? (t_hi - 1) / nct - t_lo / nct + 1 : 0;
-            if (tid == 0) {
-                // producer: A once per segment, B per item
-                long long it = pp.n_item, rtc = pp.n_rowt;
-                for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
-                    const int rt = t / nct, ct = t - rt * nct;
-                    if (t == t_lo || ct == 0) {
-                        if (rtc > 0 && !tc::mbar_wait(&pp.a_empty, (uint32_t)((rtc - 1) & 1), kWaitLimit)) {
+        auto update = [&](auto slots_c, const int nct, const uint8_t *at, const uint8_t *bt) {
+                constexpr int kS = decltype(slots_c)::value;   // panels in K
+                const int nrt = (m2 + TR - 1) / TR;
+                // this CTA's items: an even share of the (row tile, column tile)
+                // sequence in row-tile order, i.e. up to two partial row tiles
+                // ("segments") besides whole ones
+                const long long n_items = (long long)nrt * nct;
+                const int t_lo = (int)(n_items * rank / cs), t_hi = (int)(n_items * (rank + 1) / cs);
+                const int n_seg = t_hi > t_lo ? (t_hi - 1) / nct - t_lo / nct + 1 : 0;
+                if (tid == 0) {
+                    // producer: A once per segment, B per item
+                    long long it = pp.n_item, rtc = pp.n_rowt;
+                    for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
+                        const int rt = t / nct, ct = t - rt * nct;
+                        if (t == t_lo || ct == 0) {
+                            if (rtc > 0 && !tc::mbar_wait(&pp.a_empty, (uint32_t)((rtc - 1) & 1), kWaitLimit)) {
+                                failed = true;
+                                break;
+                            }
+                            tc::mbar_arrive_tx(&pp.a_full, 2 * kS * kAT);
+                            tc::bulk_load(sA, at + (size_t)rt * 2 * kS * kAT, 2 * kS * kAT, &pp.a_full);
+                            ++pp.armed_a;
+                            ++rtc;
+                        }
+                        const int bs = (int)(it % kBStages);
+                        const long long ub = it / kBStages;
+                        if (ub > 0 && !tc::mbar_wait(&pp.b_empty[bs], (uint32_t)((ub - 1) & 1), kWaitLimit)) {
                             failed = true;
                             break;
                         }
-                        tc::mbar_arrive_tx(&pp.a_full, 2 * kAT);
-                        tc::bulk_load(sA, atiles + (size_t)rt * 2 * kAT, 2 * kAT, &pp.a_full);
-                        ++pp.armed_a;
-                        ++rtc;
+                        tc::mbar_arrive_tx(&pp.b_full[bs], 2 * kS * kBT);
+                        tc::bulk_load(sB + bs * LT::kBSlot, bt + (size_t)ct * 2 * kS * kBT, 2 * kS * kBT, &pp.b_full[bs]);
+                        ++pp.armed_b[bs];
                     }
-                    const int bs = (int)(it % kBStages);
-                    const long long ub = it / kBStages;
-                    if (ub > 0 && !tc::mbar_wait(&pp.b_empty[bs], (uint32_t)((ub - 1) & 1), kWaitLimit)) {
-                        failed = true;
-                        break;
-                    }
-                    tc::mbar_arrive_tx(&pp.b_full[bs], 2 * kBT);
-                    tc::bulk_load(sB + bs * 2 * kBT, btiles + (size_t)ct * 2 * kBT, 2 * kBT, &pp.b_full[bs]);
-                    ++pp.armed_b[bs];
-                }
-                if (failed) ps.wait_failed = 1;
-            } else if (tid == 32) {
-                // MMA issuer
-                long long it = pp.n_item, rtc = pp.n_rowt;
-                for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
-                    const int ct = t % nct;
-                    if ((t == t_lo || ct == 0) && !tc::mbar_wait(&pp.a_full, (uint32_t)((rtc++) & 1), kWaitLimit)) {
-                        failed = true;
-                        break;
-                    }
-                    const int st = (int)(it % kStages), bs = (int)(it % kBStages);
-                    const long long u = it / kStages;
-                    if (!tc::mbar_wait(&pp.b_full[bs], (uint32_t)((it / kBStages) & 1), kWaitLimit) ||
-                        (u > 0 && !tc::mbar_wait(&pp.acc_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
-                        failed = true;
-                        break;
-                    }
-                    tc::tc_fence_after();
-                    const uint32_t bh = tc::smem_u32(sB + bs * 2 * kBT);
-                    issue_mma<kKind>(taddr + (uint32_t)(st * 2 * TCC), tc::smem_u32(sA),
-                                     tc::smem_u32(sA) + kAT, bh, bh + kBT);
-                    tc::mma_commit(&pp.acc_full[st]);
-                    tc::mma_commit(&pp.b_empty[bs]);
-                    ++pp.commits[st];
-                    ++pp.commits_b[bs];
-                    if (t == t_hi - 1 || ct == nct - 1) {   // the segment's A tile is read
-                        tc::mma_commit(&pp.a_empty);
-                        ++pp.commits_a;
-                    }
-                }
-                if (failed) ps.wait_failed = 1;
-            } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4 * kStages) {
-                // epilogue, one group of four warps per stage (the groups work on
-                // consecutive items at once): the negated accumulator into the
-                // stage's shared-memory tile, once the reduction of the stage's
-                // previous item has read it; thread: row r, all 2 TCC columns
-                const int g = (warp - kEpiWarp0) >> 2, lg = warp & 3;   // group (= stage), TMEM lane group
-                const int r = 32 * lg + lane;                           // tile row
-                long long it = pp.n_item;
-                bool stop = false;
-                for (int t = t_lo; t < t_hi && !stop && !failed; ++t, ++it) {
-                    {
-                        if ((int)(it % kStages) != g) continue;
-                        const uint32_t par = (uint32_t)((it / kStages) & 1);
-                        bool got = tc::mbar_wait(&pp.acc_full[g], par, kWaitLimit);
-                        if (it >= kStages) got = got && tc::mbar_wait(&pp.c_empty[g], par ^ 1u, kWaitLimit);
-                        if (tc::bar_or(1 + g, 128, !got)) {   // the same verdict in the whole group
-                            stop = true;
+                    if (failed) ps.wait_failed = 1;
+                } else if (tid == 32) {
+                    // MMA issuer
+                    long long it = pp.n_item, rtc = pp.n_rowt;
+                    for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
+                        const int ct = t % nct;
+                        if ((t == t_lo || ct == 0) && !tc::mbar_wait(&pp.a_full, (uint32_t)((rtc++) & 1), kWaitLimit)) {
+                            failed = true;
+                            break;
+                        }
+                        const int st = (int)(it % kStages), bs = (int)(it % kBStages);
+                        const long long u = it / kStages;
+                        if (!tc::mbar_wait(&pp.b_full[bs], (uint32_t)((it / kBStages) & 1), kWaitLimit) ||
+                            (u > 0 && !tc::mbar_wait(&pp.acc_empty[st], (uint32_t)((u - 1) & 1), kWaitLimit))) {
+                            failed = true;
                             break;
                         }
                         tc::tc_fence_after();
-                        const uint32_t tacc = taddr + (uint32_t)(g * 2 * TCC) + ((uint32_t)(32 * lg) << 16);
-#pragma unroll
-                        for (int bx = 0; bx < kCBoxes; ++bx) {   // one 32-column box at a time
-                            float d[32];
-                            tc::tmem_ld16(tacc + 32 * bx, *reinterpret_cast<float(*)[16]>(d));
-                            tc::tmem_ld16(tacc + 32 * bx + 16, *reinterpret_cast<float(*)[16]>(d + 16));
-                            if (bx == kCBoxes - 1) {   // the accumulator is read
-                                tc::tc_fence_before();
-                                __syncwarp();
-                                if (lane == 0) tc::mbar_arrive(&pp.acc_empty[g]);
+                        const uint32_t bh = tc::smem_u32(sB + bs * LT::kBSlot);
+                        issue_mma<kKind, kS>(taddr + (uint32_t)(st * 2 * TCC), tc::smem_u32(sA),
+                                             tc::smem_u32(sA) + kS * kAT, bh, bh + kS * kBT);
+                        tc::mma_commit(&pp.acc_full[st]);
+                        tc::mma_commit(&pp.b_empty[bs]);
+                        ++pp.commits[st];
+                        ++pp.commits_b[bs];
+                        if (t == t_hi - 1 || ct == nct - 1) {   // the segment's A tile is read
+                            tc::mma_commit(&pp.a_empty);
+                            ++pp.commits_a;
+                        }
+                    }
+                    if (failed) ps.wait_failed = 1;
+                } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4 * kStages) {
+                    // epilogue, one group of four warps per stage (the groups work on
+                    // consecutive items at once): the negated accumulator into the
+                    // stage's shared-memory tile, once the reduction of the stage's
+                    // previous item has read it; thread: row r, all 2 TCC columns
+                    const int g = (warp - kEpiWarp0) >> 2, lg = warp & 3;   // group (= stage), TMEM lane group
+                    const int r = 32 * lg + lane;                           // tile row
+                    long long it = pp.n_item;
+                    bool stop = false;
+                    for (int t = t_lo; t < t_hi && !stop && !failed; ++t, ++it) {
+                        {
+                            if ((int)(it % kStages) != g) continue;
+                            const uint32_t par = (uint32_t)((it / kStages) & 1);
+                            bool got = tc::mbar_wait(&pp.acc_full[g], par, kWaitLimit);
+                            if (it >= kStages) got = got && tc::mbar_wait(&pp.c_empty[g], par ^ 1u, kWaitLimit);
+                            if (tc::bar_or(1 + g, 128, !got)) {   // the same verdict in the whole group
+                                stop = true;
+                                break;
                             }
-                            float4 *row = reinterpret_cast<float4 *>(sC + g * kCTile + bx * kCBox + r * 128);
-#pragma unroll
-                            for (int c = 0; c < 8; ++c)   // 128-byte swizzle of the box
-                                row[c ^ (r & 7)] = make_float4(-d[4 * c], -d[4 * c + 1], -d[4 * c + 2], -d[4 * c + 3]);
+                            tc::tc_fence_after();
+                            const uint32_t tacc = taddr + (uint32_t)(g * 2 * TCC) + ((uint32_t)(32 * lg) << 16);
+    #pragma unroll
+                            for (int bx = 0; bx < kCBoxes; ++bx) {   // one 32-column box at a time
+                                float d[32];
+                                tc::tmem_ld16(tacc + 32 * bx, *reinterpret_cast<float(*)[16]>(d));
+                                tc::tmem_ld16(tacc + 32 * bx + 16, *reinterpret_cast<float(*)[16]>(d + 16));
+                                if (bx == kCBoxes - 1) {   // the accumulator is read
+                                    tc::tc_fence_before();
+                                    __syncwarp();
+                                    if (lane == 0) tc::mbar_arrive(&pp.acc_empty[g]);
+                                }
+                                float4 *row = reinterpret_cast<float4 *>(sC + g * kCTile + bx * kCBox + r * 128);
+    #pragma unroll
+                                for (int c = 0; c < 8; ++c)   // 128-byte swizzle of the box
+                                    row[c ^ (r & 7)] = make_float4(-d[4 * c], -d[4 * c + 1], -d[4 * c + 2], -d[4 * c + 3]);
+                            }
+                            tc::fence_async_smem();   // the tile reduction (async proxy) reads these writes
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(&pp.c_written[g]);
                         }
-                        tc::fence_async_smem();   // the tile reduction (async proxy) reads these writes
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&pp.c_written[g]);
                     }
-                }
-                if (stop) {
-                    failed = true;
-                    if (lg == 0 && lane == 0) ps.wait_failed = 1;
-                }
-            } else if (tid == kStoreTid) {
-                // tile reductions: each tile is added into the matrix (C +=
-                // -L21 U12, at L2) once its four epilogue warps have written
-                // it; its buffer is released when the reduction has read it
-                // (two reductions in flight: an item's buffer is released once
-                // the next item's reduction has been issued)
-                long long it = pp.n_item;
-                int prev = -1;   // stage of the previous item, its buffer not yet released
-                for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
-                    const int rt = t / nct, ct = t - rt * nct, i0 = r0 + rt * TR;
-                    {
-                        const int st = (int)(it % kStages);
-                        if (!tc::mbar_wait(&pp.c_written[st], (uint32_t)((it / kStages) & 1), kWaitLimit)) {
-                            failed = true;
-                            break;
-                        }
-                        const int x = 2 * (r0 + ct * TCC);
-                        uint8_t *src = sC + st * kCTile;
-#pragma unroll
-                        for (int bx = 0; bx < kCBoxes; ++bx)
-                            tc::tma_reduce_add_2d(tmap, x + 32 * bx, i0, src + bx * kCBox);
-                        tc::bulk_commit();
-                        if (prev >= 0) {
-                            tc::bulk_wait_read1();
-                            tc::mbar_arrive(&pp.c_empty[prev]);
-                        }
-                        prev = st;
+                    if (stop) {
+                        failed = true;
+                        if (lg == 0 && lane == 0) ps.wait_failed = 1;
                     }
+                } else if (tid == kStoreTid) {
+                    // tile reductions: each tile is added into the matrix (C +=
+                    // -L21 U12, at L2) once its four epilogue warps have written
+                    // it; its buffer is released when the reduction has read it
+                    // (two reductions in flight: an item's buffer is released once
+                    // the next item's reduction has been issued)
+                    long long it = pp.n_item;
+                    int prev = -1;   // stage of the previous item, its buffer not yet released
+                    for (int t = t_lo; t < t_hi && !failed; ++t, ++it) {
+                        const int rt = t / nct, ct = t - rt * nct, i0 = r0 + rt * TR;
+                        {
+                            const int st = (int)(it % kStages);
+                            if (!tc::mbar_wait(&pp.c_written[st], (uint32_t)((it / kStages) & 1), kWaitLimit)) {
+                                failed = true;
+                                break;
+                            }
+                            const int x = 2 * (r0 + ct * TCC);
+                            uint8_t *src = sC + st * kCTile;
+    #pragma unroll
+                            for (int bx = 0; bx < kCBoxes; ++bx)
+                                tc::tma_reduce_add_2d(tmap, x + 32 * bx, i0, src + bx * kCBox);
+                            tc::bulk_commit();
+                            if (prev >= 0) {
+                                tc::bulk_wait_read1();
+                                tc::mbar_arrive(&pp.c_empty[prev]);
+                            }
+                            prev = st;
+                        }
+                    }
+                    if (prev >= 0) {
+                        tc::bulk_wait_read();
+                        tc::mbar_arrive(&pp.c_empty[prev]);
+                    }
+                    if (failed) ps.wait_failed = 1;
+                    // the reductions are in global memory before the next panel reads them
+                    tc::bulk_wait_all();
+                    tc::fence_async_global();
                 }
-                if (prev >= 0) {
-                    tc::bulk_wait_read();
-                    tc::mbar_arrive(&pp.c_empty[prev]);
+                // drain: the producer's loads and the MMAs have landed (a no-op
+                // unless a wait gave up) before the buffers are reused
+                if (tid == 0) {
+                    if (pp.armed_a) tc::mbar_wait(&pp.a_full, (uint32_t)((pp.armed_a - 1) & 1), kWaitLimit);
+                    for (int b = 0; b < kBStages; ++b)
+                        if (pp.armed_b[b]) tc::mbar_wait(&pp.b_full[b], (uint32_t)((pp.armed_b[b] - 1) & 1), kWaitLimit);
+                } else if (tid == 32) {
+                    for (int b = 0; b < kStages; ++b)
+                        if (pp.commits[b]) tc::mbar_wait(&pp.acc_full[b], (uint32_t)((pp.commits[b] - 1) & 1), kWaitLimit);
+                    for (int b = 0; b < kBStages; ++b)
+                        if (pp.commits_b[b]) tc::mbar_wait(&pp.b_empty[b], (uint32_t)((pp.commits_b[b] - 1) & 1), kWaitLimit);
+                    if (pp.commits_a) tc::mbar_wait(&pp.a_empty, (uint32_t)((pp.commits_a - 1) & 1), kWaitLimit);
                 }
-                if (failed) ps.wait_failed = 1;
-                // the reductions are in global memory before the next panel reads them
-                tc::bulk_wait_all();
-                tc::fence_async_global();
-            }
-            // drain: the producer's loads and the MMAs have landed (a no-op
-            // unless a wait gave up) before the buffers are reused
-            if (tid == 0) {
-                if (pp.armed_a) tc::mbar_wait(&pp.a_full, (uint32_t)((pp.armed_a - 1) & 1), kWaitLimit);
-                for (int b = 0; b < kBStages; ++b)
-                    if (pp.armed_b[b]) tc::mbar_wait(&pp.b_full[b], (uint32_t)((pp.armed_b[b] - 1) & 1), kWaitLimit);
-            } else if (tid == 32) {
-                for (int b = 0; b < kStages; ++b)
-                    if (pp.commits[b]) tc::mbar_wait(&pp.acc_full[b], (uint32_t)((pp.commits[b] - 1) & 1), kWaitLimit);
-                for (int b = 0; b < kBStages; ++b)
-                    if (pp.commits_b[b]) tc::mbar_wait(&pp.b_empty[b], (uint32_t)((pp.commits_b[b] - 1) & 1), kWaitLimit);
-                if (pp.commits_a) tc::mbar_wait(&pp.a_empty, (uint32_t)((pp.commits_a - 1) & 1), kWaitLimit);
-            }
-            tc::fence_async_smem();   // the staging buffers are reused by generic accesses next
-            tc::tc_fence_before();
-            __syncthreads();
-            tc::tc_fence_after();
-            if (ps.wait_failed) failed = true;
-            if (tid == 0) {   // read again at the next panel's update, after its barriers
-                pp.n_item += t_hi - t_lo;
-                pp.n_rowt += n_seg;
-            }
+                tc::fence_async_smem();   // the staging buffers are reused by generic accesses next
+                tc::tc_fence_before();
+                __syncthreads();
+                tc::tc_fence_after();
+                if (ps.wait_failed) failed = true;
+                if (tid == 0) {   // read again at the next panel's update, after its barriers
+                    pp.n_item += t_hi - t_lo;
+                    pp.n_rowt += n_seg;
+                }
+        };
+        if (m2 > 0) {
+            if (role == 2) update(std::integral_constant<int, 2>{}, (m2 + TCC - 1) / TCC, atiles, b2tiles);
+            else update(std::integral_constant<int, 1>{}, role == 1 ? 1 : (m2 + TCC - 1) / TCC, atiles, btiles);
         }
         sys_sync(cs, true);
     }
@@ -965,13 +1036,20 @@ void launch_convert_rowmajor(const int *list, int count, const int *N, const lon
 size_t lu_tc_opnd_bytes(int kind, const int *N_h, int S, long long *a_off_h, long long *b_off_h) {
     const size_t at = kind == 2 ? a_tile_bytes<2>() : a_tile_bytes<1>();
     const size_t bt = kind == 2 ? b_tile_bytes<2>() : b_tile_bytes<1>();
+    // per system: the A tiles (one-panel rows below the first panel, or for
+    // BF16 the larger two-panel tiles below a pair), then the one-panel B
+    // tiles and for BF16 the two-panel B tiles
+    const bool pair = kind != 2;
     size_t off = 0;
     for (int s = 0; s < S; ++s) {
-        const int m2 = std::max(N_h[s] - NB, 0);
+        const int m2 = std::max(N_h[s] - NB, 0), m3 = std::max(N_h[s] - 2 * NB, 0);
         if (a_off_h) a_off_h[s] = (long long)off;
-        off += (size_t)((m2 + TR - 1) / TR) * 2 * at;
+        size_t a_sz = (size_t)((m2 + TR - 1) / TR) * 2 * at;
+        if (pair) a_sz = std::max(a_sz, (size_t)((m3 + TR - 1) / TR) * 4 * at);
+        off += a_sz;
         if (b_off_h) b_off_h[s] = (long long)off;
         off += (size_t)((m2 + TCC - 1) / TCC) * 2 * bt;
+        if (pair) off += (size_t)((m3 + TCC - 1) / TCC) * 4 * bt;
     }
     return std::max(off, (size_t)16);
 }
