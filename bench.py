@@ -11,12 +11,12 @@ configuration): kite obstacle, 40-pulse incident train over [0, 400], 512
 frequencies on [0, 160] (511 solves), N_j by 8 points per wavelength
 (64..1920), 1024 targets on r = 3, 4096 times up to T = 1e4.  `value` is
 frequency solves/s of whole steps with inputs resident in HBM in the
-mixed precision (`--precision`, default TF32 tensor-core LU + FP64-class
+mixed precision (`--precision`, default BF16 tensor-core LU + FP64-class
 refinement); `e2e` the same through the host-pointer C-ABI calls with the
 host<->device copies inside the timed region.  Beside it, in the same run:
 
 * the plain FP64 GPU path on the same workload (fewer steps), its solves/s
-  and the mixed/FP64 ratio;
+  and the mixed/FP64 ratio; the TF32 tensor-core LU on the same workload;
 * the measured error of the timed output: u against the FP64 GPU u at all
   targets and times, densities and target fields against the FP64 oracle at
   sampled frequencies;
@@ -77,7 +77,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["fp64", "mixed", "tf32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "mixed", "tf32", "bf16"])
     ap.add_argument("--workload", default="kite_wide", choices=list(WORKLOADS))
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="timed steps of the FP64 leg on the headline workload")
@@ -576,11 +576,14 @@ def summary(per_step, units):
             "steps": len(per_step)}
 
 
-def batch_leg(F, torch, local, stream, flush, steps, warmup):
+PRECISIONS = None   # name -> fh precision code, filled once the binding is loaded
+
+
+def batch_leg(F, torch, local, stream, flush, steps, warmup, precision):
     """32 star obstacles x 128 frequencies on [0, w_max], w_max ~ U(20, 100),
     N by 8 points per wavelength (64 .. ~900), all in one batched context
-    (one launch per kernel for all problems), TF32; 256 targets x 512 times
-    per problem.  solves/s of whole batched steps."""
+    (one launch per kernel for all problems), in the bench's precision; 256
+    targets x 512 times per problem.  solves/s of whole batched steps."""
     probs = fi.star_batch()
     sig = fi.pulse_train(3, n=8, span=80.0, fmin=4.0, fmax=16.0)
     t0s, dt = -10.0, 0.01
@@ -593,7 +596,7 @@ def batch_leg(F, torch, local, stream, flush, steps, warmup):
     d_T = torch.tensor(T, device=dev, dtype=torch.float64)
     d_u = torch.empty(x.size // 2 * T.size, device=dev, dtype=torch.float64)
     torch.cuda.synchronize()
-    ctx = F.fh_create(local, F.FH_MIXED_TF32)
+    ctx = F.fh_create(local, PRECISIONS[precision])
     F.fh_set_stream(ctx, stream.cuda_stream)
     curves, oms, Ns = [p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs]
     F.fh_discretize_batch(ctx, curves, oms, Ns)
@@ -626,12 +629,12 @@ def batch_leg(F, torch, local, stream, flush, steps, warmup):
     out.update({"workload": "star_batch: 32 stars r=1+sum_{k<=5} a_k cos(kt+phi_k), a~U(0,0.1), "
                             "128 freqs each on [0,w_max], w_max~U(20,100), N 8 ppw "
                             f"({int(Nall.min())}..{int(Nall.max())}); 256 targets x 512 times per problem",
-                "precision": "tf32", "solves_per_step": S, "tuning": tuning,
+                "precision": precision, "solves_per_step": S, "tuning": tuning,
                 "time_samples_per_s": len(probs) * x.size // 2 * T.size * len(per) / (sum(per) / 1e3)})
     return out
 
 
-def split_synthesis_leg(F, torch, local, stream, steps):
+def split_synthesis_leg(F, torch, local, stream, steps, precision):
     """The 2D synthesis with the low-frequency split (FCC on (0, w_c], FC(Gram)
     on [w_c, W]) on the 256-frequency kite: densities and target fields of
     the mesh and of the 24 singular frequencies from the solver, then
@@ -639,7 +642,7 @@ def split_synthesis_leg(F, torch, local, stream, steps):
     wl = fi.kite_pulses()
     j_c = 5
     dev = torch.device("cuda", local)
-    pr = F.Problem(local, F.FH_MIXED_TF32)
+    pr = F.Problem(local, PRECISIONS[precision])
     F.fh_set_stream(pr.ctx, stream.cuda_stream)
     pr.discretize(wl.curve, wl.omega, wl.N, wl.c, wl.p)
     pr.solve()
@@ -649,7 +652,7 @@ def split_synthesis_leg(F, torch, local, stream, steps):
     s, B = F.fh_get_window_spectra(pr.ctx, wl.J)
     pr.close()
     osg = F.fh_sing_frequencies(wl.omega[j_c])
-    ctx = F.fh_create(local, F.FH_MIXED_TF32)
+    ctx = F.fh_create(local, PRECISIONS[precision])
     P = osg.size
     F.fh_discretize_batch(ctx, [wl.curve] * P, [np.array([0.0, w]) for w in osg],
                           [np.array([64, 64], dtype=np.int32)] * P, ps=[wl.p] * P)
@@ -690,16 +693,16 @@ def split_synthesis_leg(F, torch, local, stream, steps):
             "calls": len(per), "extra_solves": P}
 
 
-def serving_leg(rates, n_requests):
+def serving_leg(rates, n_requests, precision):
     """Continuous-batching server at the serving configuration's shape (star
     obstacles, 128 frequencies on [0, w_max], w_max ~ U(10, 120), pulse or
     chirp signals, 256-4096 targets and 1-100 queries of 16 times in [0, 1e4]
-    per request), Poisson arrivals, TF32: p50/p99 request latency and
-    throughput per arrival rate."""
+    per request), Poisson arrivals, in the bench's precision: p50/p99 request
+    latency and throughput per arrival rate."""
     from paper_1807_02718_gb300 import serve as SV
     out = []
     for i, rate in enumerate(rates):
-        st = SV.run_stream(rate, n_requests, seed=11 + i)
+        st = SV.run_stream(rate, n_requests, seed=11 + i, precision=PRECISIONS[precision])
         out.append(st)
     return out
 
@@ -717,6 +720,8 @@ def run_gpu(args, world, rank, local):
     from paper_1807_02718_gb300 import fh as F
 
     build.build()
+    global PRECISIONS
+    PRECISIONS = {"fp64": F.FH_FP64, "mixed": F.FH_MIXED_FP32, "tf32": F.FH_MIXED_TF32, "bf16": F.FH_MIXED_BF16}
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     # One explicit stream for the library, the L2 flush and the timing events
@@ -769,7 +774,7 @@ def run_gpu(args, world, rank, local):
     tuning = leg.tuning
     leg.close()
 
-    fp64 = other = None
+    fp64 = other = other_prec = None
     if extra and args.precision != "fp64":
         # ---- the plain FP64 GPU path on the same workload ----
         leg64 = Leg(F, torch, local, stream, wl, "fp64", args)
@@ -784,6 +789,18 @@ def run_gpu(args, world, rank, local):
         accuracy["u_rel_l2_vs_fp64_gpu"] = rel(u_mixed, u64)
         accuracy["u_max_abs_diff_vs_fp64_gpu"] = float(np.max(np.abs(u_mixed - u64)))
         accuracy["u_compared"] = f"all {n_x} targets x {n_T} times"
+
+        # ---- the other tensor-core precision on the same workload ----
+        alt = "tf32" if args.precision == "bf16" else "bf16" if args.precision == "tf32" else None
+        if alt:
+            la = Leg(F, torch, local, stream, wl, alt, args)
+            pa, _, _ = la.timed(max(3, args.steps // 2), 2, flush)
+            other_prec = {alt: summary(pa, S)}
+            other_prec[alt]["phase_ms_per_step"] = la.phases(1, flush)
+            other_prec[alt]["tuning"] = la.tuning["setting"]
+            other_prec[alt]["refine_iters"] = la.stats.get("iters")
+            other_prec[alt]["u_rel_l2_vs_fp64_gpu"] = rel(la.u(), u64)
+            la.close()
 
         # ---- the other kite workload, both precisions ----
         if args.workload == "kite_wide":
@@ -804,11 +821,11 @@ def run_gpu(args, world, rank, local):
             other = {"kite_pulses": kp}
         # ---- batching configuration ----
         other = other or {}
-        other["star_batch"] = batch_leg(F, torch, local, stream, flush, max(3, args.steps // 4), 2)
+        other["star_batch"] = batch_leg(F, torch, local, stream, flush, max(3, args.steps // 4), 2, args.precision)
         # ---- 2D split synthesis (low-frequency quadrature) ----
-        other["split_synthesis"] = split_synthesis_leg(F, torch, local, stream, 3)
+        other["split_synthesis"] = split_synthesis_leg(F, torch, local, stream, 3, args.precision)
         # ---- serving ----
-        other["serving"] = serving_leg([20.0, 100.0], 24)
+        other["serving"] = serving_leg([20.0, 100.0], 24, args.precision)
 
     cpu = None
     if oracle_proc is not None:
@@ -882,6 +899,7 @@ def run_gpu(args, world, rank, local):
             "accuracy": accuracy,
             "fp64": fp64,
             "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+            "other_precisions": other_prec,
             "other_workloads": other,
             "peaks": peaks,
             "tuning": tuning,

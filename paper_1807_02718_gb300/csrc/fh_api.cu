@@ -1627,8 +1627,12 @@ fh_status fh_footprint(const int *J, const int *N, int P, int precision, long lo
             const long long n = N[jo + j];
             b += n * n * 16 + n * (16 * 4 + 16 + 8);          // matrix, nodes, density, tables
             if (precision != FH_FP64) b += n * n * 8 + n * (16 + 4 + 8);   // FP32 copy, rhs, perm, FP32 rhs
-            if (precision == FH_MIXED_TF32 || precision == FH_MIXED_BF16)
+            if (precision == FH_MIXED_TF32 || precision == FH_MIXED_BF16) {
                 b += (n + 31) / 32 * 2048 * 8;                            // diagonal-block inverses
+                const int ni = (int)n;                                    // staged operands, tensor map
+                b += (long long)fh::lu_tc_opnd_bytes(precision == FH_MIXED_TF32 ? 2 : 1, &ni, 1, nullptr, nullptr) +
+                     (long long)fh::lu_tc_map_bytes(1);
+            }
         }
         b += (long long)fh::kFarTerms * J[q] * 16 + 2LL * (J[q] - 1) * 16 + fh::sinc_tab_entries(J[q]) * 16;
         jo += J[q];

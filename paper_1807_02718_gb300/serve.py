@@ -71,7 +71,7 @@ class Request:
 
 
 class Server:
-    def __init__(self, device: int = 0, precision: int = F.FH_MIXED_TF32, slots: int = 4,
+    def __init__(self, device: int = 0, precision: int = F.FH_MIXED_BF16, slots: int = 4,
                  max_batch: int = 8, mem_budget: int | None = None, mem_fraction: float = 0.8):
         self.device = device
         self.precision = precision
@@ -237,7 +237,7 @@ def synthetic_request(rng: np.random.Generator, wmax_lo=10.0, wmax_hi=120.0, J=1
 
 
 def run_stream(rate: float, n_requests: int, seed: int = 5, slots: int = 4, max_batch: int = 8,
-               precision: int = F.FH_MIXED_TF32, **request_kw) -> dict:
+               precision: int = F.FH_MIXED_BF16, **request_kw) -> dict:
     """Serve n_requests synthetic requests arriving as a Poisson process of
     the given rate; returns the server's statistics."""
     rng = np.random.default_rng(seed)
@@ -261,7 +261,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--max-batch", type=int, default=8)
     ap.add_argument("--seed", type=int, default=5)
-    ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
     args = ap.parse_args()
     from . import build
     build.build()
