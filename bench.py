@@ -216,7 +216,7 @@ def phase_rooflines(wl, precision, ms, iters, peaks, contract_tc=False):
              "ms_per_step": ms[phase]}
         if peak:
             d.update(peak=peak, frac=ach / peak, peak_source=peak_src)
-        if kernel in NCU_PIPE:
+        if kernel in NCU_PIPE and precision == "bf16":
             d["ncu"] = NCU_PIPE[kernel]
         if extra:
             d.update(extra)
@@ -766,7 +766,8 @@ def run_gpu(args, world, rank, local):
                             contract_tc)
     roof = dict(roofs.get(dominant) or {"bound": "alu", "achieved": None, "peak": None,
                                         "unit": None, "frac": None, "kernel": dominant})
-    roof["traffic"] = MEASURED_TRAFFIC.get(roof.get("kernel"))
+    # (the capture is of the BF16 kernel; the TF32 one updates once per panel)
+    roof["traffic"] = MEASURED_TRAFFIC.get(roof.get("kernel")) if args.precision == "bf16" else None
     roof["phase"] = dominant
     roof["phase_ms_per_step"] = phase_ms
     roof["all_phases"] = roofs
