@@ -105,6 +105,22 @@ __device__ __forceinline__ void df_sincos_small(dfv y, dfv &sn, dfv &cs) {
     cs = pc;
 }
 
+// e^{i y} for a double-float 0 <= y < 3.1 without FP64: the Taylor series at
+// y / 2^h with y / 2^h <= 0.78 (h = 0, 1 or 2; halving is exact), then h
+// double-angle steps cos 2a = 1 - 2 sin^2 a, sin 2a = 2 sin a cos a.  The
+// frequency step e^{i dkappa r} of the wide-band fields reaches y ~ 1.6.
+__device__ __forceinline__ void df_sincos_mid(dfv y, dfv &sn, dfv &cs) {
+    const int h = (y.hi >= 0.78f) + (y.hi >= 1.56f);
+    const float sc = h == 0 ? 1.f : h == 1 ? 0.5f : 0.25f;
+    df_sincos_small(df_make(y.hi * sc, y.lo * sc), sn, cs);
+    for (int k = 0; k < h; ++k) {
+        const dfv s2 = df_mul(sn, sn);
+        const dfv c2 = df_add_f(df_mul_f(s2, -2.f), 1.f);
+        sn = df_mul_f(df_mul(sn, cs), 2.f);
+        cs = c2;
+    }
+}
+
 // e^{i x} for an FP64 argument 0 <= x < 2^20: quadrant reduction in FP64 (two
 // FMAs with pi/2 split into two doubles), the rest in df.
 __device__ __forceinline__ void df_expi(double x, dfv &c, dfv &s) {

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
         dfv c, sv, sc, ss;
         if (kapf[0] * rd.hi < kExpiKrMax) df_expi_kr(k3s[0], k3s[1], k3s[2], rd, c, sv);
         else df_expi_cold(kap[0] * df_to(rd) - 0.78539816339744830962, c, sv);   // e^{i (kappa_0 r - pi/4)}
-        if (dkf * rd.hi < 0.78f) df_sincos_small(df_mul(dkd, rd), ss, sc);   // e^{i dkappa r}, no reduction
+        if (dkf * rd.hi < 3.1f) df_sincos_mid(df_mul(dkd, rd), ss, sc);   // e^{i dkappa r}, no FP64 reduction
         else df_expi_cold(dk * df_to(rd), sc, ss);
         const dfv lnr = kapf[0] * rd.hi < 8.0f ? df_log(rd) : df_make(0.f, 0.f);   // shared by the group
 #pragma unroll
