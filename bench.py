@@ -761,7 +761,7 @@ def run_gpu(args, world, rank, local):
     e2e_times, h2d, d2h = leg.e2e(args.steps, flush)
     e2e_total = max_over_ranks(sum(e2e_times), world, dev)
     contract_tc = (args.precision != "fp64" and bool(leg.tuning["setting"].get("contract_tc"))
-                   and 2 * wl.J <= 512)
+                   and 2 * wl.J <= 8192)
     roofs = phase_rooflines(wl, args.precision, phase_ms, leg.stats.get("iters", 0), peaks,
                             contract_tc)
     roof = dict(roofs.get(dominant) or {"bound": "alu", "achieved": None, "peak": None,

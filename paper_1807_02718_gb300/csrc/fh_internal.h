@@ -239,10 +239,11 @@ void launch_synth_contract(int J, int n_x, int n_T, const double2 *V, const doub
                            const double *Gm, double *u, cudaStream_t st);
 // Tensor-core contraction (mixed-precision paths, 2J <= kContractTcMaxK): the
 // operands cut into eight 6-bit slices held exactly in BF16, every slice
-// product summed exactly in FP32 per level, levels combined in double-float.
+// product summed exactly in FP32 per level over K segments of 512, levels and
+// segments combined in double-float.
 // scratch: contract_tc_scratch_bytes(J, n_x, n_T) bytes; err set if an MMA
 // completion wait gave up.  Six launches.
-constexpr int kContractTcMaxK = 512;
+constexpr int kContractTcMaxK = 8192;
 bool contract_tc_ok(int J);
 size_t contract_tc_scratch_bytes(int J, int n_x, int n_T);
 cudaError_t launch_contract_tc(int J, int n_x, int n_T, const double2 *V, const double *Gr,

@@ -8,23 +8,29 @@
 // sum_i a_i 2^-(6 (i + 1)) + O(2^-49), a_i integers with |a_i| <= 2^6;
 // likewise each column t of B with sb_t.  Integers of 7 bits are exact in
 // BF16, their products (<= 2^12) are exact in the FP32 accumulator, and a
-// level d = i + j sums at most kSlices pairs over K <= 512 terms below 2^24
-// (8 x 512 x 2^12 = 2^24), so every level is an exact integer sum: TMEM holds
-// one FP32 accumulator per level (kSlices x 64 = 512 columns, all of it).  The epilogue combines the levels, scaled by
-// 2^-(kSliceBits (d + 2)), in double-float and multiplies by sa_x sb_t.  The
-// result differs from the exact product by the dropped slice pairs (i + j >=
-// kSlices) and the remainders, ~K 2^-48 sa_x sb_t at worst.
+// level d = i + j sums at most kSlices pairs over a K segment of kSegK = 512
+// terms below 2^24 (8 x 512 x 2^12 = 2^24), so every level is an exact
+// integer sum: TMEM holds one FP32 accumulator per level (kSlices x 64 = 512
+// columns, all of it).  After each K segment the epilogue combines the
+// levels, scaled by 2^-(kSliceBits (d + 2)), into double-float sums (one per
+// output) and the next segment starts its levels afresh; at the end the sums
+// are multiplied by sa_x sb_t.  The result differs from the exact product by
+// the dropped slice pairs (i + j >= kSlices) and the remainders, ~K 2^-48
+// sa_x sb_t at worst.
 //
 // Kernels: ozaki_scale_kernel (the power-of-two scale of each row of A and
-// each column of B), ozaki_slice_kernel (slices, written K-major in BF16
-// through a shared-memory transpose), contract_tc_kernel (one CTA per 128 x 64
-// output tile; K in chunks of 64: all slices of the chunk staged in shared
-// memory in the canonical no-swizzle K-major layout, one thread issues the
-// kind::f16 MMAs of every pair into its level's accumulator, bounded mbarrier
-// wait; then the double-float epilogue).
+// each column of B), ozaki_slice_kernel (slices in BF16, written directly in
+// the MMA's shared-memory layout: per 128-row (A) or 64-row (B) tile and K
+// chunk of 16, the eight slices' K-major core matrices in one contiguous
+// block), contract_tc_kernel (one CTA per 128 x 64 output tile, warp
+// specialised over a four-stage pipeline: one thread bulk-copies each chunk's
+// A and B blocks (48 KB), one thread issues the kind::f16 MMAs of every slice
+// pair into its level's accumulator, eight epilogue warps combine the levels
+// after each segment; mbarriers with bounded waits hand the stages over).
 #include <cuda_bf16.h>
 
 #include "fh_internal.h"
+#include "dfloat.cuh"
 #include "tc_gemm.cuh"
 
 namespace fh {
@@ -40,9 +46,12 @@ constexpr int kKPad = 64;                // K padding of the slice arrays
 constexpr int kThr = 256;
 constexpr int kASlice = kTM * kKBytes;   // bytes of one A slice chunk (4 KiB)
 constexpr int kBSlice = kTN * kKBytes;   // bytes of one B slice chunk (2 KiB)
-constexpr int kStage = kSlices * (kASlice + kBSlice);   // 42 KiB
-constexpr int kStages = 4;                              // chunks k+1 .. k+3 in flight
+constexpr int kABlock = kSlices * kASlice, kBBlock = kSlices * kBSlice;   // 32 + 16 KiB per chunk
+constexpr int kStage = kABlock + kBBlock;                                 // 48 KiB
+constexpr int kStages = 4;
 constexpr int kSmem = 1024 + kStages * kStage;
+constexpr int kSegK = 512;                  // K per exact segment
+constexpr int kCtaThreads = 384;            // producer (warp 0), MMA (warp 1), epilogue (warps 4 .. 11)
 constexpr long long kWaitLimit = 1LL << 22;
 
 // Element (r, kk) of the operand whose rows are r: A rows are targets x (from
@@ -83,14 +92,19 @@ __global__ void __launch_bounds__(kThr) ozaki_scale_kernel(Src src, int K, int *
     }
 }
 
-// Slices of a 64-row x 32-column block: out[s][r][kk] (row pitch kpad, BF16).
+// Slices of a 64-row x 32-column block, in BF16, written into the tiled
+// layout the contraction copies in bulk: for tile rows tr (128 for A, 64 for
+// B) and K chunks of 16, block (r / tr) * nkc + kk / 16 holds the eight slices
+// one after the other, each tr rows of 32 bytes as K-major core matrices
+// (8 rows x 16 bytes; the two 16-byte halves of K 128 bytes apart, 8-row
+// groups 256 bytes apart).
 // In integer arithmetic on the FP64 bit pattern: V = round(src 2^(42 - e[r]))
 // (|V| <= 2^48) = sum_s a_s 2^(42 - 6 s) with balanced digits, each the
 // nearest multiple of the remainder (a_0 in [-64, 64], a_s in [-32, 32]), so
 // that the dropped slice products carry no common sign: src / 2^e[r] =
 // sum_s a_s 2^-(6 (s + 1)) to within 2^-49.
 __global__ void __launch_bounds__(kThr) ozaki_slice_kernel(Src src, const int *__restrict__ e,
-                                                           int kpad, long long slice_stride,
+                                                           int kpad, int tr,
                                                            __nv_bfloat16 *__restrict__ out) {
     __shared__ __nv_bfloat16 t[kSlices][32][64 + 8];   // [slice][kk][r], padded rows
     const int r0 = blockIdx.y * 64, k0 = blockIdx.x * 32;
@@ -117,161 +131,165 @@ __global__ void __launch_bounds__(kThr) ozaki_slice_kernel(Src src, const int *_
         }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < kSlices * 64 * 32; idx += kThr) {
-        const int kk = idx & 31, rr = (idx >> 5) & 63, s = idx >> 11;   // consecutive threads: consecutive kk
-        out[s * slice_stride + (long long)(r0 + rr) * kpad + k0 + kk] = t[s][kk][rr];
-    }
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Every slice of K chunk k0 .. k0 + kKC - 1 into one stage: 16-byte rows of
-// 8-row core matrices, copied asynchronously (in flight during the MMAs of
-// the chunks before).  Thread t copies 16-byte chunk t % 2 of A row t / 2
-// and, for t < 128, of B row t / 2, for every slice.  Always commits a
-// group (empty past the last chunk), so that group counting stays uniform.
-__device__ __forceinline__ void stage_chunk(const __nv_bfloat16 *__restrict__ a_row,
-                                            const __nv_bfloat16 *__restrict__ b_row, long long a_stride,
-                                            long long b_stride, bool has_b, int k0, bool live,
-                                            uint32_t stage, uint32_t dA, uint32_t dB) {
-    if (live) {
+    // 16-byte pieces: 8 consecutive K of one row and slice
+    const int nkc = kpad / kKC;
+    uint8_t *ob = reinterpret_cast<uint8_t *>(out);
+    for (int idx = threadIdx.x; idx < kSlices * 64 * 4; idx += kThr) {
+        const int rr = idx & 63, k8 = (idx >> 6) & 3, s = idx >> 8;
+        const int r = r0 + rr, kk = k0 + 8 * k8;
+        __align__(16) __nv_bfloat16 w[8];
 #pragma unroll
-        for (int sl = 0; sl < kSlices; ++sl) {
-            cp_async16(stage + sl * kASlice + dA, a_row + sl * a_stride + k0);
-            if (has_b) cp_async16(stage + kSlices * kASlice + sl * kBSlice + dB, b_row + sl * b_stride + k0);
-        }
+        for (int q = 0; q < 8; ++q) w[q] = t[s][8 * k8 + q][rr];
+        const size_t blk = ((size_t)(r / tr) * nkc + kk / kKC) * kSlices + s;
+        const uint32_t off = tc::kmajor_offset(r % tr, (kk % kKC) * 2, kKBytes);
+        *reinterpret_cast<uint4 *>(ob + blk * (size_t)tr * kKBytes + off) = *reinterpret_cast<const uint4 *>(w);
     }
-    cp_async_commit();
 }
 
-__global__ void __launch_bounds__(kThr, 1) contract_tc_kernel(
-    const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__restrict__ Bs, long long a_stride,
-    long long b_stride, int kpad, const int *__restrict__ ea, const int *__restrict__ eb, int n_x,
-    int n_T, double *__restrict__ u, int *__restrict__ err) {
+__global__ void __launch_bounds__(kCtaThreads, 1) contract_tc_kernel(
+    const uint8_t *__restrict__ As, const uint8_t *__restrict__ Bs, int kpad, const int *__restrict__ ea,
+    const int *__restrict__ eb, int n_x, int n_T, double *__restrict__ u, int *__restrict__ err) {
     extern __shared__ uint8_t dsm[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bar[kStages];
+    __shared__ uint64_t full[kStages], empty[kStages], lv_full, lv_empty;
     __shared__ uint32_t tslot;
+    __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int x0 = blockIdx.y * kTM, t0 = blockIdx.x * kTN;
+    const int nkc = kpad / kKC, nseg = (kpad + kSegK - 1) / kSegK;
     if (warp == 0) tc::tmem_alloc(&tslot, 512);
-    if (tid == 0)
-        for (int s = 0; s < kStages; ++s) tc::mbar_init(&bar[s], 1);
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&lv_full, 1);
+        tc::mbar_init(&lv_empty, 8);
+        failed = 0;
+    }
     tc::fence_async_smem();
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t taddr = tslot;
-    const uint32_t st0 = tc::smem_u32(sm);
-    constexpr uint32_t sbo = (kKBytes / 16) * 128;
-    const int nk = kpad / kKC;
-    // this thread's copies: 16-byte chunk tid % 2 of A row tid / 2 (and of B row tid / 2)
-    const int crow = tid >> 1, cch = tid & 1;
-    const bool has_b = crow < kTN;
-    const __nv_bfloat16 *a_row = As + (long long)(x0 + crow) * kpad + cch * 8;
-    const __nv_bfloat16 *b_row = Bs + (long long)(t0 + (has_b ? crow : 0)) * kpad + cch * 8;
-    const uint32_t dA = tc::kmajor_offset(crow, cch * 16, kKBytes), dB = dA;
-    // MMA descriptors differ only in the start address field (address / 16)
-    const uint64_t desc0 = tc::smem_desc(st0, 128, sbo);
-    bool ok = true;
-    uint32_t phase[kStages] = {};
-    bool pending[kStages] = {};
-    for (int k = 0; k < kStages - 1; ++k)
-        stage_chunk(a_row, b_row, a_stride, b_stride, has_b, k * kKC, k < nk, st0 + k * kStage, dA, dB);
-    for (int k = 0; k < nk; ++k) {
-        const int s = k % kStages;
-        cp_async_wait<kStages - 2>();   // chunk k has landed (k+1, k+2 may be in flight)
-        tc::fence_async_smem();
-        tc::tc_fence_before();
-        ok = __syncthreads_and(ok) != 0;
-        tc::tc_fence_after();
-        if (!ok) break;
-        if (tid == 0) {   // queued behind the previous chunks' MMAs
-            // The B slices of a stage are consecutive 64-row blocks of one K-major
-            // operand, so A slice i against B slices j0 .. j0 + n - 1 (N = 64 n <=
-            // 256) writes the products a_i b_j to accumulator columns 64 (i + j):
-            // the level of each pair.  Twelve MMAs cover the 36 pairs.
-            const uint64_t ds = desc0 + (uint64_t)((s * kStage) >> 4);
+    const uint8_t *ablk = As + (size_t)blockIdx.y * nkc * kABlock;   // this tile's chunks, in K order
+    const uint8_t *bblk = Bs + (size_t)blockIdx.x * nkc * kBBlock;
+    if (tid == 0) {
+        // producer: chunk k's A and B blocks into stage k % kStages
+        for (int k = 0; k < nkc; ++k) {
+            const int st = k % kStages;
+            if (k >= kStages && !tc::mbar_wait(&empty[st], (uint32_t)(((k / kStages) - 1) & 1), kWaitLimit)) {
+                failed = 1;
+                break;
+            }
+            tc::mbar_arrive_tx(&full[st], kStage);
+            tc::bulk_load(sm + st * kStage, ablk + (size_t)k * kABlock, kABlock, &full[st]);
+            tc::bulk_load(sm + st * kStage + kABlock, bblk + (size_t)k * kBBlock, kBBlock, &full[st]);
+        }
+    } else if (tid == 32) {
+        // MMA issuer.  The B slices of a stage are consecutive 64-row blocks of
+        // one K-major operand, so A slice i against B slices j0 .. j0 + n - 1
+        // (N = 64 n <= 256) writes the products a_i b_j to accumulator columns
+        // 64 (i + j): the level of each pair.  Twelve MMAs cover the 36 pairs.
+        constexpr uint32_t sbo = (kKBytes / 16) * 128;
+        const uint64_t desc0 = tc::smem_desc(tc::smem_u32(sm), 128, sbo);
+        for (int k = 0; k < nkc && !failed; ++k) {
+            const int st = k % kStages, kin = k % (kSegK / kKC);
+            if (!tc::mbar_wait(&full[st], (uint32_t)((k / kStages) & 1), kWaitLimit) ||
+                (kin == 0 && k > 0 && !tc::mbar_wait(&lv_empty, (uint32_t)(((k / (kSegK / kKC)) - 1) & 1), kWaitLimit))) {
+                failed = 1;
+                break;
+            }
+            tc::tc_fence_after();
+            const uint64_t ds = desc0 + (uint64_t)((st * kStage) >> 4);
 #pragma unroll
             for (int i = 0; i < kSlices; ++i) {
                 const uint64_t da = ds + (uint64_t)((i * kASlice) >> 4);
 #pragma unroll
                 for (int j0 = 0; j0 < kSlices - i; j0 += 4) {
                     const int n = (kSlices - i - j0) < 4 ? (kSlices - i - j0) : 4;   // slices of B
-                    const uint64_t db = ds + (uint64_t)((kSlices * kASlice + j0 * kBSlice) >> 4);
+                    const uint64_t db = ds + (uint64_t)((kABlock + j0 * kBSlice) >> 4);
                     const uint32_t id = tc::instr_desc(1u, kTM, kTN * n);
-                    tc::mma<1>(taddr + (uint32_t)((i + j0) * kTN), da, db, id, (k == 0 && i == 0) ? 0u : 1u);
+                    tc::mma<1>(taddr + (uint32_t)((i + j0) * kTN), da, db, id, (kin == 0 && i == 0) ? 0u : 1u);
                 }
             }
-            tc::mma_commit(&bar[s]);
+            tc::mma_commit(&empty[st]);
+            if (kin == kSegK / kKC - 1 || k == nkc - 1) tc::mma_commit(&lv_full);   // a segment's levels
         }
-        pending[s] = true;
-        // refill the stage of chunk k - 1 with chunk k + kStages - 1 once that
-        // chunk's MMAs (ahead of chunk k's in the tensor pipe) are done
-        const int sp = (k + kStages - 1) % kStages;
-        if (pending[sp]) {
-            if (!tc::mbar_wait(&bar[sp], phase[sp], kWaitLimit)) ok = false;
-            phase[sp] ^= 1u;
-            pending[sp] = false;
-        }
-        const int kn = k + kStages - 1;
-        stage_chunk(a_row, b_row, a_stride, b_stride, has_b, kn * kKC, ok && kn < nk, st0 + sp * kStage,
-                    dA, dB);   // after a give-up the stage may still be read: nothing copied
-    }
-    cp_async_wait<0>();
-    // the last chunk's MMAs (the MMAs of one thread complete in issue order)
-    bool got = true;
-    for (int s = 0; s < kStages; ++s)
-        if (pending[s]) {
-            const bool g = tc::mbar_wait(&bar[s], phase[s], kWaitLimit);
-            phase[s] ^= 1u;
-            got = got && g;
-        }
-    tc::tc_fence_after();
-    ok = __syncthreads_and(ok && got) != 0;
-    if (!ok) {
-        if (tid == 0) atomicOr(err, 1);
-    } else {
-        // warp w: TMEM lanes 32 (w % 4) .. (rows), columns 32 (w / 4) .. of each level
-        const int q = warp & 3, ch = warp >> 2;
+    } else if (warp >= 4) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows), columns
+        // 32 ((w - 4) / 4) .. of each level; double-float sums across segments
+        const int q = warp & 3, ch = (warp - 4) >> 2;
         const int x = x0 + 32 * q + lane;
-        const int ex = x < n_x ? ea[x] : 0;
-#pragma unroll 1
-        for (int g = 0; g < 2; ++g) {
-            const int c0 = 32 * ch + 16 * g;
-            float hi[16], lo[16];
+        float hi[2][16], lo[2][16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) hi[k] = lo[k] = 0.f;
-#pragma unroll 1
-            for (int d = kSlices - 1; d >= 0; --d) {   // smallest levels first
-                float v[16];
-                tc::tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * kTN + c0), v);
-                const float sc = ldexpf(1.f, -kSliceBits * d);   // level d relative to level 0
+        for (int g = 0; g < 2; ++g)
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {          // (hi, lo) += v sc, two-sum
-                    const float p = v[k] * sc;           // exact: integer times a power of two
-                    const float t = hi[k] + p, bb = t - hi[k];
-                    lo[k] += (hi[k] - (t - bb)) + (p - bb);
-                    hi[k] = t;
+            for (int c = 0; c < 16; ++c) hi[g][c] = lo[g][c] = 0.f;
+        bool ok = true;
+        for (int sg = 0; sg < nseg && ok; ++sg) {
+            ok = tc::mbar_wait(&lv_full, (uint32_t)(sg & 1), kWaitLimit);
+            if (tc::bar_or(1, 256, !ok)) {   // the same verdict in every epilogue thread
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const int c0 = 32 * ch + 16 * g;
+                float h2[16], l2[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) h2[c] = l2[c] = 0.f;
+#pragma unroll 1
+                for (int d = kSlices - 1; d >= 0; --d) {   // smallest levels first
+                    float v[16];
+                    tc::tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * kTN + c0), v);
+                    const float sc = ldexpf(1.f, -kSliceBits * d);   // level d relative to level 0
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {          // (h2, l2) += v sc, two-sum
+                        const float p = v[c] * sc;           // exact: integer times a power of two
+                        const float t = h2[c] + p, bb = t - h2[c];
+                        l2[c] += (h2[c] - (t - bb)) + (p - bb);
+                        h2[c] = t;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {   // segment sum into the running sum
+                    const dfv r = df_add(df_make(hi[g][c], lo[g][c]), df_make(h2[c], l2[c]));
+                    hi[g][c] = r.hi;
+                    lo[g][c] = r.lo;
                 }
             }
-            if (x < n_x)
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&lv_empty);   // the levels may be overwritten
+        }
+        if (!ok && lane == 0) failed = 1;
+        if (ok && x < n_x) {
+            const int ex = ea[x];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const int t = t0 + c0 + k;
+            for (int g = 0; g < 2; ++g)
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int t = t0 + 32 * ch + 16 * g + c;
                     if (t < n_T)
                         u[(long long)x * n_T + t] =
-                            ldexp((double)hi[k] + (double)lo[k], ex + eb[t] - 2 * kSliceBits);
+                            ldexp((double)hi[g][c] + (double)lo[g][c], ex + eb[t] - 2 * kSliceBits);
                 }
         }
+    }
+    // drain: loads and MMAs in flight have landed before the CTA ends (a
+    // no-op unless a wait gave up)
+    if (tid == 0) {
+        for (int k = max(0, nkc - kStages); k < nkc; ++k)
+            tc::mbar_wait(&full[k % kStages], (uint32_t)((k / kStages) & 1), kWaitLimit);
+    } else if (tid == 32) {
+        for (int k = max(0, nkc - kStages); k < nkc; ++k)
+            tc::mbar_wait(&empty[k % kStages], (uint32_t)((k / kStages) & 1), kWaitLimit);
     }
     tc::tc_fence_before();
     __syncthreads();
+    if (failed && tid == 0) atomicOr(err, 1);
     if (warp == 0) tc::tmem_free(taddr, 512);
 }
 
@@ -305,11 +323,10 @@ cudaError_t launch_contract_tc(int J, int n_x, int n_T, const double2 *V, const 
     const Src sbt{nullptr, Gr, Gm, J, n_T, n_T};
     ozaki_scale_kernel<<<rx / 32, kThr, 0, st>>>(sa, 2 * J, ea);
     ozaki_scale_kernel<<<rt / 32, kThr, 0, st>>>(sbt, 2 * J, eb);
-    ozaki_slice_kernel<<<dim3(kp / 32, rx / 64), kThr, 0, st>>>(sa, ea, kp, (long long)rx * kp, As);
-    ozaki_slice_kernel<<<dim3(kp / 32, rt / 64), kThr, 0, st>>>(sbt, eb, kp, (long long)rt * kp, Bs);
-    contract_tc_kernel<<<dim3(rt / kTN, rx / kTM), kThr, kSmem, st>>>(As, Bs, (long long)rx * kp,
-                                                                    (long long)rt * kp, kp, ea, eb,
-                                                                    n_x, n_T, u, err);
+    ozaki_slice_kernel<<<dim3(kp / 32, rx / 64), kThr, 0, st>>>(sa, ea, kp, kTM, As);
+    ozaki_slice_kernel<<<dim3(kp / 32, rt / 64), kThr, 0, st>>>(sbt, eb, kp, kTN, Bs);
+    contract_tc_kernel<<<dim3(rt / kTN, rx / kTM), kCtaThreads, kSmem, st>>>(
+        reinterpret_cast<const uint8_t *>(As), reinterpret_cast<const uint8_t *>(Bs), kp, ea, eb, n_x, n_T, u, err);
     return cudaGetLastError();
 }
 

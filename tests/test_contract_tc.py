@@ -1,8 +1,8 @@
 """The tensor-core contraction u = [Vr | Vi] [Gr ; Gm] (operands cut into exact
 BF16 slices, exact FP32 sums per slice level): against the oracle's synthesis,
 the double-float contraction and the FP64 path, on ragged tile counts, on rows
-and columns with a wide dynamic range, at the largest exact size (2J = 512) and
-its fall-back above it."""
+and columns with a wide dynamic range, at the largest size of one exact K
+segment (2J = 512) and with two segments (2J = 514, 1024)."""
 import numpy as np
 import pytest
 
@@ -107,13 +107,17 @@ def test_largest_exact_size():
     assert rel(u_df, u_64) < 1e-12
 
 
-def test_falls_back_above_the_exact_bound():
-    """2J = 514 > 512: the tensor-core setting runs the double-float kernel,
-    bit for bit."""
-    wl = fi.small_kite(J=257, W=30.0)
-    wl.N = np.full(257, 64, dtype=np.int32)
-    V = fields(wl.J, 70, 4)
-    T = np.linspace(0.0, 60.0, 40)
-    a = synth(wl, F.FH_MIXED_TF32, V, T)
-    b = synth(wl, F.FH_MIXED_TF32, V, T, contract_tc=0)
-    assert np.array_equal(a, b)
+@pytest.mark.parametrize("J", [257, 512])
+def test_k_segments(J):
+    """2J = 514 and 1024 (the wide-band workload's K): the levels are exact
+    integer sums over K segments of 512, combined in double-float; u agrees
+    with the double-float and FP64 contractions."""
+    wl = fi.small_kite(J=J, W=30.0)
+    wl.N = np.full(J, 64, dtype=np.int32)
+    V = fields(wl.J, 150, 4)
+    T = np.linspace(0.0, 60.0, 100)
+    u_tc = synth(wl, F.FH_MIXED_TF32, V, T)
+    u_df = synth(wl, F.FH_MIXED_TF32, V, T, contract_tc=0)
+    u_64 = synth(wl, F.FH_FP64, V, T)
+    assert rel(u_tc, u_64) < 1e-12, rel(u_tc, u_64)
+    assert rel(u_df, u_64) < 1e-12
