@@ -78,6 +78,34 @@ __device__ __forceinline__ dfv df_mul_f(dfv a, float b) {
 // a * b + c
 __device__ __forceinline__ dfv df_fma(dfv a, dfv b, dfv c) { return df_add(df_mul(a, b), c); }
 
+// a * b + c with one renormalisation: the exact product of the hi parts (FMA
+// residual) and the cross terms, the sum of the two leading parts by two-sum,
+// every small part added into one error term.
+__device__ __forceinline__ dfv df_mad(dfv a, dfv b, dfv c) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = p + c.hi;
+    const float bb = s - p;
+    return df_quick(s, ((p - (s - bb)) + (c.hi - bb)) + (e + c.lo));
+}
+
+// a * b + c * d with one renormalisation (two exact products, one two-sum).
+__device__ __forceinline__ dfv df_dot2(dfv a, dfv b, dfv c, dfv d) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float q = c.hi * d.hi;
+    float f = fmaf(c.hi, d.hi, -q);
+    f = fmaf(c.hi, d.lo, f);
+    f = fmaf(c.lo, d.hi, f);
+    const float s = p + q;
+    const float bb = s - p;
+    return df_quick(s, ((p - (s - bb)) + (q - bb)) + (e + f));
+}
+
 __device__ __forceinline__ dfv df_sqrt(dfv a) {
     const float s = sqrtf(a.hi);
     const float e = (fmaf(-s, s, a.hi) + a.lo) * (0.5f / s);
@@ -91,15 +119,22 @@ __device__ __forceinline__ dfv df_rcp(dfv a) {
 }
 
 // sin and cos of a df argument |y| <= pi/4 (Taylor series to degree 17 / 16,
-// truncation < 2^-53).
+// truncation < 2^-53).  Horner in y^2; the coefficients of y^12 and beyond
+// (<= 1/12! = 2.1e-9, times y^12 <= 0.055) need only binary32, the rest are
+// df multiply-adds.
 __device__ __forceinline__ void df_sincos_small(dfv y, dfv &sn, dfv &cs) {
     const dfv y2 = df_mul(y, y);
-    dfv ps = df_make(kSinDF[16], kSinDF[17]);
-    dfv pc = df_make(kCosDF[16], kCosDF[17]);
+    float ts = kSinDF[16], tc = kCosDF[16];
 #pragma unroll
-    for (int k = 7; k >= 0; --k) {
-        ps = df_fma(ps, y2, df_make(kSinDF[2 * k], kSinDF[2 * k + 1]));
-        pc = df_fma(pc, y2, df_make(kCosDF[2 * k], kCosDF[2 * k + 1]));
+    for (int k = 7; k >= 6; --k) {
+        ts = fmaf(ts, y2.hi, kSinDF[2 * k]);
+        tc = fmaf(tc, y2.hi, kCosDF[2 * k]);
+    }
+    dfv ps = df_make(ts, 0.f), pc = df_make(tc, 0.f);
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+        ps = df_mad(ps, y2, df_make(kSinDF[2 * k], kSinDF[2 * k + 1]));
+        pc = df_mad(pc, y2, df_make(kCosDF[2 * k], kCosDF[2 * k + 1]));
     }
     sn = df_mul(ps, y);
     cs = pc;
@@ -187,43 +222,60 @@ __device__ __forceinline__ void g_stage(GShared &tb) {
     }
 }
 
-// u^2 G(t) in df: G = c0 (df) + t (c1 + c2 t + ...) (binary32).
-__device__ __forceinline__ dfv g_term(const float *c, float2 c0, float t, dfv u2) {
+// The binary32 part of a remainder polynomial: G - c0 = t (c1 + c2 t + ...).
+__device__ __forceinline__ float g_poly(const float *c, float t) {
     float a = c[kG_TERMS - 1];
 #pragma unroll
     for (int k = kG_TERMS - 2; k >= 1; --k) a = fmaf(a, t, c[k]);
-    return df_mul(u2, df_add_f(df_make(c0.x, c0.y), a * t));
+    return a * t;
 }
 
-// Hankel-form J0, Y0 (and J1, Y1 when want1) at x = kappa r >= 8.
-//   r8 = 8 / x (df), amp = sqrt(2 / (pi x)) (df), (c, s) = e^{i (x - pi/4)}.
-// J0 = amp (P0 c - Q0 s), Y0 = amp (P0 s + Q0 c); with e^{i (x - 3pi/4)} =
-// (s, -c): J1 = amp (P1 s + Q1 c), Y1 = amp (Q1 s - P1 c).
+// u k + u^2 G with G = c0 + at (c0 a df pair, at binary32, k an exact
+// binary32 coefficient): the Hankel terms of P or Q after the constant one,
+// summed with one renormalisation.
+__device__ __forceinline__ dfv pq_rem(dfv u, float k, dfv u2, float2 c0, float at) {
+    const dfv G = df_add_f(df_make(c0.x, c0.y), at);
+    const float p = u.hi * k;
+    const float e = fmaf(u.lo, k, fmaf(u.hi, k, -p));
+    const float q = u2.hi * G.hi;
+    float f = fmaf(u2.hi, G.hi, -q);
+    f = fmaf(u2.hi, G.lo, f);
+    f = fmaf(u2.lo, G.hi, f);
+    const float sm = p + q;
+    const float bb = sm - p;
+    return df_quick(sm, ((p - (sm - bb)) + (q - bb)) + (e + f));
+}
+
+// Hankel-form J0, Y0 (and J1, Y1 when want1) at x = kappa r >= 8, scaled by
+// the amplitude that the caller carries in the phase:
+//   r8 = 8 / x (df), (c, s) = a e^{i (x - pi/4)} for any real a;
+//   J0 = a' (P0 c - Q0 s), Y0 = a' (P0 s + Q0 c), and with e^{i (x - 3pi/4)}
+//   = (s, -c): J1 = a' (P1 s + Q1 c), Y1 = a' (Q1 s - P1 c), where
+//   a' = sqrt(2 / (pi x)) / a (a = sqrt(2 / (pi x)) gives J and Y themselves).
+// P = 1 + dP: each value is the phase component plus one two-product dot
+// product of the small corrections (|dP| <= 1.2e-3, |Q| <= 0.05).
 template <bool want1>
-__device__ __forceinline__ void df_hankel(const GShared &tb, float xf, dfv r8, dfv amp, dfv c, dfv s,
-                                          dfv &J0, dfv &Y0, dfv &J1, dfv &Y1) {
+__device__ __forceinline__ void df_hankel(const GShared &tb, float xf, dfv r8, dfv c, dfv s, dfv &J0,
+                                          dfv &Y0, dfv &J1, dfv &Y1) {
     const dfv u = df_mul(r8, r8);
     const int k = (xf >= 10.f) + (xf >= 13.f) + (xf >= 18.f) + (xf >= 28.f) + (xf >= 60.f);
     const float t = (u.hi - tb.uc[k]) * tb.iuh[k];
     const dfv u2 = df_mul(u, u);
     const float *g = tb.c + k * 4 * kG_TERMS;
     const float2 *g0 = tb.c0 + k * 4;
-    // delta P0 = P0 - 1, q0 = Q0 / r8
-    const dfv dP0 = df_add(df_mul_f(u, -9.0f / 8192.0f), g_term(g, g0[0], t, u2));
-    const dfv q0 = df_add_f(df_add(df_mul_f(u, 75.0f / 524288.0f), g_term(g + kG_TERMS, g0[1], t, u2)),
-                            -1.0f / 64.0f);
-    const dfv Q0 = df_mul(r8, q0);
-    const dfv P0c = df_add(c, df_mul(dP0, c)), P0s = df_add(s, df_mul(dP0, s));
-    J0 = df_mul(amp, df_add(P0c, df_neg(df_mul(Q0, s))));
-    Y0 = df_mul(amp, df_add(P0s, df_mul(Q0, c)));
+    // dP0 = P0 - 1, Q0 = r8 (-1/64 + 75 u / 524288 + u^2 G1)
+    const dfv dP0 = pq_rem(u, -9.0f / 8192.0f, u2, g0[0], g_poly(g, t));
+    const dfv Q0 = df_mul(r8, df_add_f(pq_rem(u, 75.0f / 524288.0f, u2, g0[1], g_poly(g + kG_TERMS, t)),
+                                       -1.0f / 64.0f));
+    J0 = df_add(c, df_dot2(dP0, c, df_neg(Q0), s));
+    Y0 = df_add(s, df_dot2(dP0, s, Q0, c));
     if (want1) {
-        const dfv dP1 = df_add(df_mul_f(u, 15.0f / 8192.0f), g_term(g + 2 * kG_TERMS, g0[2], t, u2));
-        const dfv q1 = df_add_f(df_add(df_mul_f(u, -105.0f / 524288.0f),
-                                       g_term(g + 3 * kG_TERMS, g0[3], t, u2)), 3.0f / 64.0f);
-        const dfv Q1 = df_mul(r8, q1);
-        const dfv P1s = df_add(s, df_mul(dP1, s)), P1c = df_add(c, df_mul(dP1, c));
-        J1 = df_mul(amp, df_add(P1s, df_mul(Q1, c)));
-        Y1 = df_mul(amp, df_add(df_mul(Q1, s), df_neg(P1c)));
+        const dfv dP1 = pq_rem(u, 15.0f / 8192.0f, u2, g0[2], g_poly(g + 2 * kG_TERMS, t));
+        const dfv Q1 = df_mul(r8, df_add_f(pq_rem(u, -105.0f / 524288.0f, u2, g0[3],
+                                                  g_poly(g + 3 * kG_TERMS, t)),
+                                           3.0f / 64.0f));
+        J1 = df_add(s, df_dot2(dP1, s, Q1, c));
+        Y1 = df_add(df_neg(c), df_dot2(Q1, s, df_neg(dP1), c));
     }
 }
 

@@ -165,7 +165,14 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
 // arithmetic; the diagonal and the band (where ln r and the Kress log table
 // nearly cancel), the Kress weights and the log table stay FP64.  Entries are
 // stored as double-float pairs (re hi, re lo, im hi, im lo): the FP32 LU takes
-// the hi parts and the refinement residual uses both.
+// the hi parts and the refinement residual uses both.  Per node pair the
+// amplitude sqrt(2 / (pi r)) rides on the phase and the geometry factors are
+// combined once,
+//   A1 = g4 W/pi, B1 = g4 pi/n, C1 = s4 pi/n, D1 = s4 W/pi
+//   (g4 = N_il s_l / (4 s_i r), s4 = s_l / 4),
+// so that with J' = sqrt(kappa_j) J (what the Hankel form returns)
+//   Re A = sqrt(kappa) (A1 J1' - B1 Y1') + (eta / sqrt(kappa)) C1 J0',
+//   Im A = sqrt(kappa) B1 J1' + (eta / sqrt(kappa)) (C1 Y0' - D1 J0').
 __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ dz,
     const float4 *__restrict__ zf, const float4 *__restrict__ dzf, const float2 *__restrict__ sf,
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     const int tr = (int)(lt % nt), tc = (int)(lt / nt);
     __shared__ double kap[kGroup];
     __shared__ float kapf[kGroup], corrf[kGroup];
-    __shared__ dfv kapd[kGroup], etad[kGroup], ikap[kGroup], isqk[kGroup], lnk2[kGroup];
+    __shared__ dfv kapd[kGroup], ikap8[kGroup], sqk[kGroup], eqk[kGroup], lnk2[kGroup];
     __shared__ long long moff[kGroup];
     __shared__ float k3s[3];   // kappa_0 as three binary32 pieces
     __shared__ GShared gt;
@@ -202,9 +209,9 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
         kap[j] = k;
         kapf[j] = (float)k;
         kapd[j] = df_from(k);
-        etad[j] = df_from(e);
-        ikap[j] = df_from(1.0 / k);
-        isqk[j] = df_from(1.0 / sqrt(k));
+        ikap8[j] = df_from(8.0 / k);
+        sqk[j] = df_from(sqrt(k));
+        eqk[j] = df_from(e / sqrt(k));
         lnk2[j] = df_from(log(0.5 * k));   // ln(kappa/2): ln(x/2) = ln(kappa/2) + ln r
         corrf[j] = (float)(k - ((j < cnt ? t.kappa[s0] : 1.0) + j * dk));
         moff[j] = ((j < cnt) ? t.mat_off[s0 + j] : 0) + out_shift;
@@ -241,35 +248,39 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
         const dfv sl = df_make(sl2.x, sl2.y), Wp = df_make(wp2.x, wp2.y);   // |z'_l|, W / pi
         const dfv gg4 = df_mul(df_mul(Nil, sl), df_mul(ir, isi4));          // N s_l / (4 s_i r)
         const dfv sl4 = df_mul_f(sl, 0.25f);
+        const dfv A1 = df_mul(gg4, Wp), B1 = df_mul(gg4, pind), C1 = df_mul(sl4, pind), D1 = df_mul(sl4, Wp);
         const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));
         dfv c, sv, sc, ss;
         if (kapf[0] * rd.hi < kExpiKrMax) df_expi_kr(k3s[0], k3s[1], k3s[2], rd, c, sv);
         else df_expi_cold(kap[0] * df_to(rd) - 0.78539816339744830962, c, sv);   // e^{i (kappa_0 r - pi/4)}
         if (dkf * rd.hi < 3.1f) df_sincos_mid(df_mul(dkd, rd), ss, sc);   // e^{i dkappa r}, no FP64 reduction
         else df_expi_cold(dk * df_to(rd), sc, ss);
+        c = df_mul(c, amp0);
+        sv = df_mul(sv, amp0);
         const dfv lnr = kapf[0] * rd.hi < 8.0f ? df_log(rd) : df_make(0.f, 0.f);   // shared by the group
 #pragma unroll 1   // not unrolled: half the registers, twice the occupancy
         for (int j = 0; j < kGroup; ++j) {
             if (j < cnt) {
                 const float xf = kapf[j] * rd.hi;
-                dfv J0, Y0, J1, Y1;
+                dfv J0, Y0, J1, Y1;   // each times sqrt(kappa_j)
                 if (xf >= 8.0f) {
                     const float dl = corrf[j] * rd.hi;
                     const dfv cj = df_add_f(c, -dl * sv.hi), sj = df_add_f(sv, dl * c.hi);
-                    const dfv r8 = df_mul_f(df_mul(ir, ikap[j]), 8.0f);
-                    df_hankel<true>(gt, xf, r8, df_mul(amp0, isqk[j]), cj, sj, J0, Y0, J1, Y1);
+                    df_hankel<true>(gt, xf, df_mul(ir, ikap8[j]), cj, sj, J0, Y0, J1, Y1);
                 } else {
                     df_bessel_small<true>(df_mul(kapd[j], rd), df_add(lnr, lnk2[j]), J0, Y0, J1, Y1);
+                    const dfv q = sqk[j];
+                    J0 = df_mul(J0, q);
+                    Y0 = df_mul(Y0, q);
+                    J1 = df_mul(J1, q);
+                    Y1 = df_mul(Y1, q);
                 }
-                const dfv k4 = df_mul(kapd[j], gg4), e4 = df_mul(etad[j], sl4);
-                const dfv pk4 = df_mul(pind, k4), pe4 = df_mul(pind, e4);
-                const dfv ar = df_add(df_mul(k4, df_add(df_mul(Wp, J1), df_neg(df_mul(pind, Y1)))),
-                                      df_mul(pe4, J0));
-                const dfv ai = df_add(df_mul(pk4, J1),
-                                      df_mul(e4, df_add(df_mul(pind, Y0), df_neg(df_mul(Wp, J0)))));
+                const dfv sq = sqk[j], eq = eqk[j];
+                const dfv ar = df_dot2(sq, df_dot2(A1, J1, df_neg(B1), Y1), eq, df_mul(C1, J0));
+                const dfv ai = df_dot2(sq, df_mul(B1, J1), eq, df_dot2(C1, Y0, df_neg(D1), J0));
                 A[moff[j] + e_off] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
-                const dfv cn = df_add(df_mul(c, sc), df_neg(df_mul(sv, ss)));
-                sv = df_add(df_mul(sv, sc), df_mul(c, ss));
+                const dfv cn = df_dot2(c, sc, df_neg(sv), ss);
+                sv = df_dot2(sv, sc, c, ss);
                 c = cn;
             }
         }

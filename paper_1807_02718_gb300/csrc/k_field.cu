@@ -139,8 +139,11 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool 
 // Mixed-precision variant of field_partial_kernel: the same sums with the
 // distances, H0 (Hankel form for kappa r >= 8, the small-argument series with
 // ln r formed once per target-node pair below it), the phases and the
-// accumulation in double-float arithmetic.  FP64 is kept for the phase
-// arguments kappa_0 r and dkappa r with their reduction modulo pi/2.
+// accumulation in double-float arithmetic (the phases e^{i kappa_0 r} and
+// e^{i dkappa r} reduced in binary32 pieces, FP64 only for kappa_0 r >= 6000).
+// The amplitude sqrt(2 / (pi r)) rides on the phase of each target-node pair
+// and 1 / sqrt(kappa_j) on the staged densities, so that the Hankel form
+// returns sqrt(kappa_j) H0 and needs no amplitude product per frequency.
 template <int kG>   // largest subgroup size of the launch (<= kGroup)
 __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
     SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin, int chunk,
@@ -160,10 +163,11 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
     const float dkf = (float)dk;
     __shared__ double kap[kGroup];
     __shared__ float kapf[kGroup], corrf[kGroup];
-    __shared__ dfv ikap[kGroup], isqk[kGroup], kapd[kGroup], lnk2[kGroup];
+    __shared__ dfv ikap8[kGroup], sqk[kGroup], kapd[kGroup], lnk2[kGroup];
+    __shared__ double isqd[kGroup];
     __shared__ float k3s[3];   // kappa_0 as three binary32 pieces
     __shared__ float4 zs[kChunk];             // node coordinates, double-float
-    __shared__ float4 ps[kGroup][kChunk];   // (pi/n)|z'|/4 * psi_j as (re hi, re lo, im hi, im lo)
+    __shared__ float4 ps[kGroup][kChunk];   // (pi/n)|z'|/4 psi_j / sqrt(kappa_j) as (re hi, re lo, im hi, im lo)
     __shared__ GShared gt;
     g_stage(gt);
     if (threadIdx.x == 0) {
@@ -178,12 +182,14 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
         const double k = (j < cnt) ? t.kappa[s0 + j] : 1.0;
         kap[j] = k;
         kapf[j] = (float)k;
-        ikap[j] = df_from(1.0 / k);
-        isqk[j] = df_from(1.0 / sqrt(k));
+        ikap8[j] = df_from(8.0 / k);
+        sqk[j] = df_from(sqrt(k));
+        isqd[j] = 1.0 / sqrt(k);
         kapd[j] = df_from(k);
         lnk2[j] = df_from(log(0.5 * k));   // ln(kappa/2): ln(x/2) = ln(kappa/2) + ln r
         corrf[j] = (float)(k - ((j < cnt ? t.kappa[s0] : 1.0) + j * dk));
     }
+    __syncthreads();
     const int ne = min(chunk, N - i0);
     for (int e = threadIdx.x; e < kChunk; e += kTgt) {
         const int i = i0 + e;
@@ -199,7 +205,8 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (e < ne && j < cnt) {
                 const double2 q = psi[t.vec_off[s0 + j] + i];
-                const dfv re = df_from(q.x * sp), im = df_from(q.y * sp);
+                const double spj = sp * isqd[j];
+                const dfv re = df_from(q.x * spj), im = df_from(q.y * spj);
                 v = make_float4(re.hi, re.lo, im.hi, im.lo);
             }
             ps[j][e] = v;
@@ -224,20 +231,23 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
         else df_expi_cold(kap[0] * df_to(rd) - 0.78539816339744830962, c, sv);   // e^{i (kappa_0 r - pi/4)}
         if (dkf * rd.hi < 3.1f) df_sincos_mid(df_mul(dkd, rd), ss, sc);   // e^{i dkappa r}, no FP64 reduction
         else df_expi_cold(dk * df_to(rd), sc, ss);
+        c = df_mul(c, amp0);
+        sv = df_mul(sv, amp0);
         const dfv lnr = kapf[0] * rd.hi < 8.0f ? df_log(rd) : df_make(0.f, 0.f);   // shared by the group
 #pragma unroll
         for (int j = 0; j < kG; ++j) {
             if (j < cnt) {
                 const float xf = kapf[j] * rd.hi;
-                dfv J0, Y0;
+                dfv J0, Y0;   // sqrt(kappa_j) J0, sqrt(kappa_j) Y0
                 if (xf >= 8.0f) {
                     const float dl = corrf[j] * rd.hi;
                     const dfv cj = df_add_f(c, -dl * sv.hi), sj = df_add_f(sv, dl * c.hi);
-                    const dfv r8 = df_mul_f(df_mul(ir, ikap[j]), 8.0f);
                     dfv J1, Y1;
-                    df_hankel<false>(gt, xf, r8, df_mul(amp0, isqk[j]), cj, sj, J0, Y0, J1, Y1);
+                    df_hankel<false>(gt, xf, df_mul(ir, ikap8[j]), cj, sj, J0, Y0, J1, Y1);
                 } else {
                     df_bessel_small0_cold(df_mul(kapd[j], rd), df_add(lnr, lnk2[j]), J0, Y0);
+                    J0 = df_mul(J0, sqk[j]);
+                    Y0 = df_mul(Y0, sqk[j]);
                 }
                 const float4 q4 = ps[j][e];
                 const dfv qr = df_make(q4.x, q4.y), qi = df_make(q4.z, q4.w);
@@ -246,8 +256,8 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
                 df_acc(ah[j][0], al[j][0], J0, qi, true);
                 df_acc(ah[j][1], al[j][1], Y0, qi, true);
                 df_acc(ah[j][1], al[j][1], J0, qr, false);
-                const dfv cn = df_add(df_mul(c, sc), df_neg(df_mul(sv, ss)));
-                sv = df_add(df_mul(sv, sc), df_mul(c, ss));
+                const dfv cn = df_dot2(c, sc, df_neg(sv), ss);
+                sv = df_dot2(sv, sc, c, ss);
                 c = cn;
             }
         }
@@ -323,8 +333,8 @@ __global__ void bessel_eval_df_kernel(const double *__restrict__ x, int n, doubl
     if (xv >= 8.0) {
         dfv c, s, j0, y0, j1, y1;
         df_expi(xv - 0.78539816339744830962, c, s);
-        df_hankel<true>(gt, (float)xv, df_from(8.0 / xv), df_from(sqrt(kTwoOverPi / xv)), c, s, j0, y0,
-                        j1, y1);
+        const dfv amp = df_from(sqrt(kTwoOverPi / xv));   // carried by the phase
+        df_hankel<true>(gt, (float)xv, df_from(8.0 / xv), df_mul(c, amp), df_mul(s, amp), j0, y0, j1, y1);
         J0 = df_to(j0);
         Y0 = df_to(y0);
         J1 = df_to(j1);
