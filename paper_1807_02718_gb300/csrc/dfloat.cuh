@@ -207,11 +207,12 @@ __device__ __forceinline__ void df_expi_kr(float k1, float k2, float k3, dfv r, 
 
 // Remainder polynomials staged in shared memory (threads of a warp may fall
 // into different x intervals).
-struct GShared {
-    float c[kPQ_NI * 4 * kG_TERMS];
+struct __align__(16) GShared {
+    float c[kPQ_NI * 4 * kG_TERMS];   // read as float4 pairs (kG_TERMS = 8)
     float2 c0[kPQ_NI * 4];          // constant terms as (hi, lo)
     float uc[kPQ_NI], iuh[kPQ_NI];
 };
+static_assert(kG_TERMS == 8, "g_poly reads each remainder polynomial as two float4");
 
 __device__ __forceinline__ void g_stage(GShared &tb) {
     for (int i = threadIdx.x; i < kPQ_NI * 4 * kG_TERMS; i += blockDim.x) tb.c[i] = kG[i];
@@ -222,11 +223,16 @@ __device__ __forceinline__ void g_stage(GShared &tb) {
     }
 }
 
-// The binary32 part of a remainder polynomial: G - c0 = t (c1 + c2 t + ...).
+// The binary32 part of a remainder polynomial: G - c0 = t (c1 + c2 t + ...
+// + c7 t^6), its eight coefficients (c0 unused) as two 16-byte loads.
 __device__ __forceinline__ float g_poly(const float *c, float t) {
-    float a = c[kG_TERMS - 1];
-#pragma unroll
-    for (int k = kG_TERMS - 2; k >= 1; --k) a = fmaf(a, t, c[k]);
+    const float4 lo = reinterpret_cast<const float4 *>(c)[0], hi = reinterpret_cast<const float4 *>(c)[1];
+    float a = fmaf(hi.w, t, hi.z);
+    a = fmaf(a, t, hi.y);
+    a = fmaf(a, t, hi.x);
+    a = fmaf(a, t, lo.w);
+    a = fmaf(a, t, lo.z);
+    a = fmaf(a, t, lo.y);
     return a * t;
 }
 
@@ -262,16 +268,18 @@ __device__ __forceinline__ void df_hankel(const GShared &tb, float xf, dfv r8, d
     const float t = (u.hi - tb.uc[k]) * tb.iuh[k];
     const dfv u2 = df_mul(u, u);
     const float *g = tb.c + k * 4 * kG_TERMS;
-    const float2 *g0 = tb.c0 + k * 4;
+    const float4 g01 = reinterpret_cast<const float4 *>(tb.c0)[2 * k];
     // dP0 = P0 - 1, Q0 = r8 (-1/64 + 75 u / 524288 + u^2 G1)
-    const dfv dP0 = pq_rem(u, -9.0f / 8192.0f, u2, g0[0], g_poly(g, t));
-    const dfv Q0 = df_mul(r8, df_add_f(pq_rem(u, 75.0f / 524288.0f, u2, g0[1], g_poly(g + kG_TERMS, t)),
+    const dfv dP0 = pq_rem(u, -9.0f / 8192.0f, u2, make_float2(g01.x, g01.y), g_poly(g, t));
+    const dfv Q0 = df_mul(r8, df_add_f(pq_rem(u, 75.0f / 524288.0f, u2, make_float2(g01.z, g01.w),
+                                              g_poly(g + kG_TERMS, t)),
                                        -1.0f / 64.0f));
     J0 = df_add(c, df_dot2(dP0, c, df_neg(Q0), s));
     Y0 = df_add(s, df_dot2(dP0, s, Q0, c));
     if (want1) {
-        const dfv dP1 = pq_rem(u, 15.0f / 8192.0f, u2, g0[2], g_poly(g + 2 * kG_TERMS, t));
-        const dfv Q1 = df_mul(r8, df_add_f(pq_rem(u, -105.0f / 524288.0f, u2, g0[3],
+        const float4 g23 = reinterpret_cast<const float4 *>(tb.c0)[2 * k + 1];
+        const dfv dP1 = pq_rem(u, 15.0f / 8192.0f, u2, make_float2(g23.x, g23.y), g_poly(g + 2 * kG_TERMS, t));
+        const dfv Q1 = df_mul(r8, df_add_f(pq_rem(u, -105.0f / 524288.0f, u2, make_float2(g23.z, g23.w),
                                                   g_poly(g + 3 * kG_TERMS, t)),
                                            3.0f / 64.0f));
         J1 = df_add(s, df_dot2(dP1, s, Q1, c));

@@ -382,6 +382,14 @@ void split_groups(fh_ctx *ctx, int gmax, std::vector<int2> &sg, std::vector<doub
     }
 }
 
+// Assembly CTAs of one matrix order n (tiles of 32 x 32): all nt^2 tiles for
+// the FP64 kernel, the nt (nt + 1) / 2 tiles of the upper triangle for the
+// double-float kernel (which writes both entries of each node pair).
+long long assembly_tiles(const fh_ctx *ctx, int n) {
+    const long long nt = (n + 31) / 32;
+    return ctx->precision == FH_FP64 ? nt * nt : nt * (nt + 1) / 2;
+}
+
 // Work lists of the assembly and target-field kernels under ctx->tune
 // (subgroups never cross problems; field items are chunks of field
 // subgroups).  A new schedule is a new launch sequence: disc_gen advances.
@@ -411,8 +419,7 @@ fh_status build_schedules(fh_ctx *ctx) {
     long long gt = 0;
     for (const int2 &g : ctx->sg) {
         ctx->sg_tile_off.push_back(gt);
-        const long long nt = (ctx->solve_N[g.x] + 31) / 32;
-        gt += nt * nt;
+        gt += assembly_tiles(ctx, ctx->solve_N[g.x]);
         for (int j = 0; j < g.y; ++j) ctx->order.push_back(g.x + j);
     }
     ctx->sg_tile_off.push_back(gt);
@@ -1467,12 +1474,11 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     int gi = 0;
     while (!(ctx->sg[gi].x <= s && s < ctx->sg[gi].x + ctx->sg[gi].y)) ++gi;
     const int2 sgv = ctx->sg[gi];
-    const long long nt = (n + 31) / 32;
     std::vector<double> eta = ctx->eta_s;
     eta[s] = eta_j;
     FH_TRY(upload(ctx, ctx->d_eta, eta));
     std::vector<int2> sg1 = {sgv};
-    std::vector<long long> to1 = {0, nt * nt};
+    std::vector<long long> to1 = {0, assembly_tiles(ctx, n)};
     std::vector<double> dk1 = {ctx->sg_dk[gi]};
     FH_TRY(upload(ctx, ctx->d_tmp_sg, sg1));
     FH_TRY(upload(ctx, ctx->d_tmp_ll, to1));
@@ -1488,7 +1494,7 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
     g1.tile_off = ctx->d_tmp_ll.as<long long>();
     g1.dkappa = ctx->d_tmp_d.as<double>();
     const fh::SolveTables t = tables(ctx);
-    fh::launch_assemble_groups(t, g1, 1, 0, nt * nt, ctx->d_tmp_i.as<int>(), sgv.y, n,
+    fh::launch_assemble_groups(t, g1, 1, 0, to1[1], ctx->d_tmp_i.as<int>(), sgv.y, n,
                                ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                                ctx->d_ddz.as<double2>(), ctx->d_kress.as<double>(),
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),

@@ -80,7 +80,9 @@ struct Subgroups {
 // Exactly one of A (FP64 complex) and Af (mixed paths: double-float pairs re
 // hi, re lo, im hi, im lo, same 16 bytes per entry) is non-null.
 // Launches the tiles tile_base .. tile_base + n_tiles - 1 of the subgroup
-// table g (n_groups subgroups, tile offsets over the whole table).  Mixed
+// table g (n_groups subgroups, tile offsets over the whole table; a matrix of
+// order n has ceil(n/32)^2 tiles for A, the ceil(n/32) (ceil(n/32) + 1) / 2
+// tiles of its upper triangle for Af).  Mixed
 // paths (Af): also the near-diagonal band of the band_count solves in the
 // device list band_list (largest N maxN), a second launch, issued first on
 // band_st (which may be st; the two kernels write disjoint entries, so that on

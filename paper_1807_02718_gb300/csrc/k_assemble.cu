@@ -17,7 +17,8 @@
 // One CTA assembles one 32 x 32 tile for up to kGroup frequencies; tiles of
 // all frequencies (of all problems of a batch) form one flat launch (prefix
 // offsets tile_off).  Each warp writes 32 consecutive rows of a column:
-// column-major stores of 512 B.
+// column-major stores of 512 B (the double-float kernel also writes the
+// transposed entries, 16 B per row, which meet in L2).
 #include "bessel.cuh"
 #include "dfloat.cuh"
 #include "fh_internal.h"
@@ -173,7 +174,12 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
 // so that with J' = sqrt(kappa_j) J (what the Hankel form returns)
 //   Re A = sqrt(kappa) (A1 J1' - B1 Y1') + (eta / sqrt(kappa)) C1 J0',
 //   Im A = sqrt(kappa) B1 J1' + (eta / sqrt(kappa)) (C1 Y0' - D1 J0').
-__global__ void __launch_bounds__(256) assemble_group_df_kernel(
+// r, the Bessel values, the phases and the Kress log weight (even in i - l)
+// are the same for A(i, l) and A(l, i): a CTA takes a tile (tr, tc) of the
+// upper triangle (flat index tc (tc + 1) / 2 + tr within the subgroup) and
+// writes both entries of every node pair (i < l on a diagonal tile), the
+// second one with its own geometry factors (N_li, s_i, s_l swapped).
+__global__ void __launch_bounds__(256, 3) assemble_group_df_kernel(
     SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ dz,
     const float4 *__restrict__ zf, const float4 *__restrict__ dzf, const float2 *__restrict__ sf,
     const float2 *__restrict__ wpf, float4 *__restrict__ A, long long out_shift, long long tile_base) {
@@ -182,9 +188,11 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     const int2 sgv = grp.sg[g];
     const int s0 = sgv.x, cnt = sgv.y;
     const int N = t.N[s0];
-    const int nt = (N + kTile - 1) / kTile;
     const long long lt = b - grp.tile_off[g];
-    const int tr = (int)(lt % nt), tc = (int)(lt / nt);
+    int tc = (int)((sqrtf(8.f * (float)lt + 1.f) - 1.f) * 0.5f);
+    while (tc > 0 && (long long)tc * (tc + 1) / 2 > lt) --tc;
+    while ((long long)(tc + 1) * (tc + 2) / 2 <= lt) ++tc;
+    const int tr = (int)(lt - (long long)tc * (tc + 1) / 2);   // 0 <= tr <= tc < ceil(N / 32)
     __shared__ double kap[kGroup];
     __shared__ float kapf[kGroup], corrf[kGroup];
     __shared__ dfv kapd[kGroup], ikap8[kGroup], sqk[kGroup], eqk[kGroup], lnk2[kGroup];
@@ -230,25 +238,34 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
     const float4 zi4 = zf[vo + i], dzi4 = dzf[vo + i];
     const dfv nzix = df_make(-zi4.x, -zi4.y), nziy = df_make(-zi4.z, -zi4.w);
     const dfv dzix = df_make(dzi4.x, dzi4.y), dziy = df_make(dzi4.z, dzi4.w);
+    const float2 si2 = sf[vo + i];
+    const dfv si4 = df_mul_f(df_make(si2.x, si2.y), 0.25f);   // s_i / 4
+    const dfv C2 = df_mul(si4, pind);
 
     for (int q = threadIdx.x >> 5; q < kTile; q += 8) {
         const int l = tc * kTile + q;
         if (l >= N) break;
+        if (tr == tc && l <= i) continue;   // each pair once on a diagonal tile
         int d = i - l;
         if (d < 0) d += N;
-        const long long e_off = (long long)l * N + i;
         if (d <= kNearBand || d >= N - kNearBand) continue;   // assemble_band_kernel
+        const long long e_il = (long long)l * N + i, e_li = (long long)i * N + l;
         // pair geometry in double-float from the double-float node tables
-        const float4 zl4 = zf[vo + l];
+        const float4 zl4 = zf[vo + l], dzl4 = dzf[vo + l];
         const dfv d1 = df_add(df_make(zl4.x, zl4.y), nzix), d2 = df_add(df_make(zl4.z, zl4.w), nziy);
         const dfv rd = df_sqrt(df_add(df_mul(d1, d1), df_mul(d2, d2)));
         const dfv ir = df_rcp(rd);
         const dfv Nil = df_add(df_mul(dziy, d1), df_neg(df_mul(dzix, d2)));
-        const float2 sl2 = sf[vo + l], wp2 = wpf[to + d];
-        const dfv sl = df_make(sl2.x, sl2.y), Wp = df_make(wp2.x, wp2.y);   // |z'_l|, W / pi
-        const dfv gg4 = df_mul(df_mul(Nil, sl), df_mul(ir, isi4));          // N s_l / (4 s_i r)
+        // N_li = z2'_l (z1_i - z1_l) - z1'_l (z2_i - z2_l)
+        const dfv Nli = df_dot2(df_make(dzl4.x, dzl4.y), d2, df_make(-dzl4.z, -dzl4.w), d1);
+        const float2 sl2 = sf[vo + l], wp2 = wpf[to + d], wq2 = wpf[to + N - d];
+        const dfv sl = df_make(sl2.x, sl2.y), Wp = df_make(wp2.x, wp2.y);   // |z'_l|, W / pi at i - l
+        const dfv Wq = df_make(wq2.x, wq2.y);                                // W / pi at l - i
+        const dfv gg4 = df_mul(df_mul(Nil, sl), df_mul(ir, isi4));          // N_il s_l / (4 s_i r)
+        const dfv gq4 = df_mul(df_mul(Nli, si4), df_mul(ir, df_rcp(sl)));   // N_li s_i / (4 s_l r)
         const dfv sl4 = df_mul_f(sl, 0.25f);
         const dfv A1 = df_mul(gg4, Wp), B1 = df_mul(gg4, pind), C1 = df_mul(sl4, pind), D1 = df_mul(sl4, Wp);
+        const dfv A2 = df_mul(gq4, Wq), B2 = df_mul(gq4, pind), D2 = df_mul(si4, Wq);
         const dfv amp0 = df_sqrt(df_mul(ir, two_over_pi));
         dfv c, sv, sc, ss;
         if (kapf[0] * rd.hi < kExpiKrMax) df_expi_kr(k3s[0], k3s[1], k3s[2], rd, c, sv);
@@ -276,9 +293,17 @@ __global__ void __launch_bounds__(256) assemble_group_df_kernel(
                     Y1 = df_mul(Y1, q);
                 }
                 const dfv sq = sqk[j], eq = eqk[j];
-                const dfv ar = df_dot2(sq, df_dot2(A1, J1, df_neg(B1), Y1), eq, df_mul(C1, J0));
-                const dfv ai = df_dot2(sq, df_mul(B1, J1), eq, df_dot2(C1, Y0, df_neg(D1), J0));
-                A[moff[j] + e_off] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+                const long long mo = moff[j];
+                {
+                    const dfv ar = df_dot2(sq, df_dot2(A1, J1, df_neg(B1), Y1), eq, df_mul(C1, J0));
+                    const dfv ai = df_dot2(sq, df_mul(B1, J1), eq, df_dot2(C1, Y0, df_neg(D1), J0));
+                    A[mo + e_il] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+                }
+                {
+                    const dfv br = df_dot2(sq, df_dot2(A2, J1, df_neg(B2), Y1), eq, df_mul(C2, J0));
+                    const dfv bi = df_dot2(sq, df_mul(B2, J1), eq, df_dot2(C2, Y0, df_neg(D2), J0));
+                    A[mo + e_li] = make_float4(br.hi, br.lo, bi.hi, bi.lo);
+                }
                 const dfv cn = df_dot2(c, sc, df_neg(sv), ss);
                 sv = df_dot2(sv, sc, c, ss);
                 c = cn;
