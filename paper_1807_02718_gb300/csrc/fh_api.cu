@@ -1042,9 +1042,12 @@ fh_status fh_num_problems(fh_ctx *ctx, int *P) {
 
 // All matrices A_s into d_A (column-major; FP64 complex, or double-float
 // pairs on the mixed paths).
-// Subgroups g0 .. g1-1 (their solves are order[s0 .. s1-1]).
-fh_status assemble_range(fh_ctx *ctx, int g0, int g1, int s0, int s1) {
+// Subgroups g0 .. g1-1 (their solves are order[s0 .. s1-1]).  a32 (mixed
+// paths): the hi parts also into the row-major FP32 copy d_A32 that the
+// tensor-core LU factors in place, so that its conversion is skipped.
+fh_status assemble_range(fh_ctx *ctx, int g0, int g1, int s0, int s1, bool a32) {
     const bool mixed = ctx->precision != FH_FP64;
+    if (a32 && (!mixed || !ctx->d_A32.p)) return fail(ctx, FH_ESTATE, "row-major FP32 copy requested without its buffer");
     const long long t0 = ctx->sg_tile_off[g0], t1 = ctx->sg_tile_off[g1];
     if (mixed) {   // the band kernel runs on the band stream beside the tiles
         FH_CUDA(ctx, cudaEventRecord(ctx->ev_band0, ctx->stream));
@@ -1057,8 +1060,8 @@ fh_status assemble_range(fh_ctx *ctx, int g0, int g1, int s0, int s1) {
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
                                ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(),
                                ctx->d_wpf.as<float2>(), mixed ? nullptr : ctx->d_A.as<double2>(),
-                               mixed ? ctx->d_A.as<float4>() : nullptr, 0, ctx->stream,
-                               mixed ? ctx->band : ctx->stream);
+                               mixed ? ctx->d_A.as<float4>() : nullptr, a32 ? ctx->d_A32.as<float2>() : nullptr,
+                               0, ctx->stream, mixed ? ctx->band : ctx->stream);
     if (mixed) {
         FH_CUDA(ctx, cudaEventRecord(ctx->ev_band1, ctx->band));
         FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_band1, 0));
@@ -1066,7 +1069,7 @@ fh_status assemble_range(fh_ctx *ctx, int g0, int g1, int s0, int s1) {
     return check_launch(ctx, "assemble");
 }
 
-fh_status assemble_kernels(fh_ctx *ctx) { return assemble_range(ctx, 0, ctx->n_groups, 0, ctx->S); }
+fh_status assemble_kernels(fh_ctx *ctx, bool a32) { return assemble_range(ctx, 0, ctx->n_groups, 0, ctx->S, a32); }
 
 // Tensor maps of the row-major FP32 matrices and the staged-operand buffer
 // of the tensor-core LU, rebuilt when the matrices move or the
@@ -1093,12 +1096,14 @@ fh_status ensure_tc_work(fh_ctx *ctx) {
     return FH_OK;
 }
 
-// Row-major FP32 copies and tensor-core LU of the solves order[s0 .. s1-1]
-// (d_info and d_tcerr are cleared by the caller).
-fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1) {
-    fh::launch_convert_rowmajor(ctx->d_order.as<int>() + s0, s1 - s0, ctx->d_N.as<int>(),
-                                ctx->d_mat_off.as<long long>(), ctx->d_A.as<float4>(),
-                                ctx->d_A32.as<float2>(), ctx->stream);
+// Tensor-core LU of the solves order[s0 .. s1-1] (d_info and d_tcerr are
+// cleared by the caller), after their row-major FP32 copies when convert
+// (the assembly wrote them otherwise).
+fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1, bool convert) {
+    if (convert)
+        fh::launch_convert_rowmajor(ctx->d_order.as<int>() + s0, s1 - s0, ctx->d_N.as<int>(),
+                                    ctx->d_mat_off.as<long long>(), ctx->d_A.as<float4>(),
+                                    ctx->d_A32.as<float2>(), ctx->stream);
     const cudaError_t e = fh::launch_lu_factor_tc(
         ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>() + s0,
         ctx->order.data() + s0, ctx->solve_N.data(), s1 - s0, ctx->d_N.as<int>(),
@@ -1111,13 +1116,13 @@ fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1) {
     return FH_OK;
 }
 
-fh_status tc_factor_kernels(fh_ctx *ctx) {
+fh_status tc_factor_kernels(fh_ctx *ctx, bool convert) {
     FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
-    return tc_factor_range(ctx, 0, ctx->S);
+    return tc_factor_range(ctx, 0, ctx->S, convert);
 }
 
-int tc_launches(fh_ctx *ctx, int s0, int s1) {
-    return 1 + fh::lu_tc_launches(ctx->order.data() + s0, ctx->solve_N.data(), s1 - s0,
+int tc_launches(fh_ctx *ctx, int s0, int s1, bool convert) {
+    return (convert ? 1 : 0) + fh::lu_tc_launches(ctx->order.data() + s0, ctx->solve_N.data(), s1 - s0,
                                   ctx->tune.lu_rows_per_cta);
 }
 
@@ -1165,26 +1170,26 @@ fh_status split_front(fh_ctx *ctx, bool refine) {
     // (a whole SM each) find empty SMs when the rest's assembly starts
     {
         PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
-        FH_TRY(assemble_range(ctx, 0, gL, 0, SL));
+        FH_TRY(assemble_range(ctx, 0, gL, 0, SL, true));
     }
     FH_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
     FH_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
     {
         OnStream on(ctx, ctx->side);
         {
-            PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, 0, SL));
-            FH_TRY(tc_factor_range(ctx, 0, SL));
+            PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, 0, SL, false));
+            FH_TRY(tc_factor_range(ctx, 0, SL, false));
         }
         if (refine) FH_TRY(refine_range(ctx, true, 0, SL, 0, ctx->n_rchunk_early, 0, ctx->n_dblk_early));
     }
     FH_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
     {
         PhaseScope ps(ctx, FH_PH_ASSEMBLE, 2);
-        FH_TRY(assemble_range(ctx, gL, ctx->n_groups, SL, S));
+        FH_TRY(assemble_range(ctx, gL, ctx->n_groups, SL, S, true));
     }
     {
-        PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, SL, S));
-        FH_TRY(tc_factor_range(ctx, SL, S));
+        PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, SL, S, false));
+        FH_TRY(tc_factor_range(ctx, SL, S, false));
     }
     if (refine)
         FH_TRY(refine_range(ctx, true, SL, S, ctx->n_rchunk_early, ctx->n_rchunk, ctx->n_dblk_early, ctx->n_dblk));
@@ -1200,7 +1205,7 @@ fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
     if (split) return split_front(ctx, true);   // assembly, factorisation and refinement
     {
         PhaseScope ps(ctx, FH_PH_ASSEMBLE, mixed ? 3 : 2);   // (tiles, band,) right sides
-        FH_TRY(assemble_kernels(ctx));
+        FH_TRY(assemble_kernels(ctx, tc));   // tensor-core paths: with the row-major FP32 copy
         fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                        ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
                        mixed ? ctx->d_g.as<double2>() : ctx->d_psi.as<double2>(), ctx->stream);
@@ -1216,10 +1221,10 @@ fh_status solve_kernels(fh_ctx *ctx, bool mixed, bool tc) {
         FH_TRY(check_launch(ctx, "lu fp64"));
     } else {
         {
-            // launches: conversion and one LU launch per cluster size (SIMT: one)
-            PhaseScope ps(ctx, FH_PH_FACTOR, tc ? tc_launches(ctx, 0, ctx->S) : 2);
+            // launches: one LU launch per cluster size (SIMT: conversion and LU)
+            PhaseScope ps(ctx, FH_PH_FACTOR, tc ? tc_launches(ctx, 0, ctx->S, false) : 2);
             if (tc) {
-                FH_TRY(tc_factor_kernels(ctx));
+                FH_TRY(tc_factor_kernels(ctx, false));
             } else {
                 fh::launch_convert_fp32(ctx->d_A.as<float4>(), ctx->d_A32.as<float2>(), ctx->mat_total,
                                         ctx->stream);
@@ -1500,7 +1505,8 @@ fh_status fh_assemble_matrix(fh_ctx *ctx, int j, double eta_j, double *A, double
                                ctx->d_logsin.as<double>(), ctx->d_zf.as<float4>(),
                                ctx->d_dzf.as<float4>(), ctx->d_sf.as<float2>(), ctx->d_wpf.as<float2>(),
                                mixed ? nullptr : ctx->d_tmpA.as<double2>(),
-                               mixed ? ctx->d_tmpA.as<float4>() : nullptr, -base, ctx->stream, ctx->stream);
+                               mixed ? ctx->d_tmpA.as<float4>() : nullptr, nullptr, -base, ctx->stream,
+                               ctx->stream);
     FH_TRY(check_launch(ctx, "assemble (single)"));
     fh::launch_rhs(t, ctx->S, ctx->maxN, ctx->d_z.as<double2>(), ctx->d_dz.as<double2>(),
                    ctx->d_solve_prob.as<int>(), ctx->d_pdir.as<double2>(),
@@ -1770,7 +1776,7 @@ fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_ou
     // 1. assembly: frequencies per subgroup
     FH_TRY(ensure(ctx, ctx->d_A, (size_t)ctx->mat_total * sizeof(double2)));
     FH_TRY(tune_field(ctx, reps, &fh_tuning::assemble_group, {2, 4, 8}, ms_out[0],
-                      [&]() { return assemble_kernels(ctx); }));
+                      [&]() { return assemble_kernels(ctx, false); }));
     // 2. tensor-core factorisation of the assembled matrices: CTAs per system
     if (tc && ctx->maxN <= fh::kTcMaxN) {
         FH_TRY(ensure(ctx, ctx->d_A32, (size_t)ctx->mat_total * sizeof(float2)));
@@ -1778,11 +1784,11 @@ fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_ou
         FH_TRY(ensure(ctx, ctx->d_info, (size_t)ctx->S * sizeof(int)));
         FH_TRY(ensure(ctx, ctx->d_tcerr, sizeof(int)));
         FH_TRY(ensure_tc_work(ctx));
-        FH_TRY(assemble_kernels(ctx));
+        FH_TRY(assemble_kernels(ctx, false));
         std::vector<int> info(ctx->S);
         FH_TRY(tune_field(ctx, reps, &fh_tuning::lu_rows_per_cta, {512, 256, 128}, ms_out[1], [&]() {
             FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
-            FH_TRY(tc_factor_kernels(ctx));
+            FH_TRY(tc_factor_kernels(ctx, true));   // each repetition factors a fresh copy
             FH_CUDA(ctx, cudaMemcpyAsync(info.data(), ctx->d_info.p, (size_t)ctx->S * sizeof(int),
                                          cudaMemcpyDeviceToHost, ctx->stream));
             FH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1796,9 +1802,9 @@ fh_status autotune(fh_ctx *ctx, const double *x, int n_x, int reps, double ms_ou
             if (ctx->early_solves > 0 && ctx->early_solves < ctx->S) {
                 FH_TRY(split_front(ctx, false));
             } else {
-                FH_TRY(assemble_kernels(ctx));
+                FH_TRY(assemble_kernels(ctx, true));
                 FH_CUDA(ctx, cudaMemsetAsync(ctx->d_info.p, 0, (size_t)ctx->S * sizeof(int), ctx->stream));
-                FH_TRY(tc_factor_kernels(ctx));
+                FH_TRY(tc_factor_kernels(ctx, false));
             }
             FH_CUDA(ctx, cudaMemcpyAsync(info.data(), ctx->d_info.p, (size_t)ctx->S * sizeof(int),
                                          cudaMemcpyDeviceToHost, ctx->stream));

@@ -86,14 +86,17 @@ struct Subgroups {
 // paths (Af): also the near-diagonal band of the band_count solves in the
 // device list band_list (largest N maxN), a second launch, issued first on
 // band_st (which may be st; the two kernels write disjoint entries, so that on
-// another stream the FP64-bound band overlaps the FP32-bound tiles).
+// another stream the FP64-bound band overlaps the FP32-bound tiles).  A32
+// (mixed paths, may be null): the hi parts of every entry also into the
+// row-major FP32 copy of the tensor-core LU (what launch_convert_rowmajor
+// would make from Af).
 void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_groups,
                             long long tile_base, long long n_tiles, const int *band_list,
                             int band_count, int maxN,
                             const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
-                            double2 *A, float4 *Af, long long out_shift, cudaStream_t st,
+                            double2 *A, float4 *Af, float2 *A32, long long out_shift, cudaStream_t st,
                             cudaStream_t band_st);
 // Solve s uses the incidence direction pdir[prob[s]].
 void launch_rhs(const SolveTables &t, int S, int maxN, const double2 *z, const double2 *dz,

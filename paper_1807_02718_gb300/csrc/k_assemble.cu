@@ -178,11 +178,14 @@ __global__ void __launch_bounds__(256) assemble_group_kernel(
 // are the same for A(i, l) and A(l, i): a CTA takes a tile (tr, tc) of the
 // upper triangle (flat index tc (tc + 1) / 2 + tr within the subgroup) and
 // writes both entries of every node pair (i < l on a diagonal tile), the
-// second one with its own geometry factors (N_li, s_i, s_l swapped).
+// second one with its own geometry factors (N_li, s_i, s_l swapped).  With
+// A32 non-null the hi parts also go to the row-major FP32 copy that the
+// tensor-core LU factors (A32(i, l) at i N + l, the same offsets as A).
 __global__ void __launch_bounds__(256, 3) assemble_group_df_kernel(
     SolveTables t, Subgroups grp, int n_groups, const double2 *__restrict__ dz,
     const float4 *__restrict__ zf, const float4 *__restrict__ dzf, const float2 *__restrict__ sf,
-    const float2 *__restrict__ wpf, float4 *__restrict__ A, long long out_shift, long long tile_base) {
+    const float2 *__restrict__ wpf, float4 *__restrict__ A, float2 *__restrict__ A32, long long out_shift,
+    long long tile_base) {
     const long long b = tile_base + blockIdx.x;
     const int g = find_solve(grp.tile_off, n_groups, b);
     const int2 sgv = grp.sg[g];
@@ -298,11 +301,13 @@ __global__ void __launch_bounds__(256, 3) assemble_group_df_kernel(
                     const dfv ar = df_dot2(sq, df_dot2(A1, J1, df_neg(B1), Y1), eq, df_mul(C1, J0));
                     const dfv ai = df_dot2(sq, df_mul(B1, J1), eq, df_dot2(C1, Y0, df_neg(D1), J0));
                     A[mo + e_il] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+                    if (A32) A32[mo + e_li] = make_float2(ar.hi, ai.hi);
                 }
                 {
                     const dfv br = df_dot2(sq, df_dot2(A2, J1, df_neg(B2), Y1), eq, df_mul(C2, J0));
                     const dfv bi = df_dot2(sq, df_mul(B2, J1), eq, df_dot2(C2, Y0, df_neg(D2), J0));
                     A[mo + e_li] = make_float4(br.hi, br.lo, bi.hi, bi.lo);
+                    if (A32) A32[mo + e_il] = make_float2(br.hi, bi.hi);
                 }
                 const dfv cn = df_dot2(c, sc, df_neg(sv), ss);
                 sv = df_dot2(sv, sc, c, ss);
@@ -317,11 +322,11 @@ __global__ void __launch_bounds__(256, 3) assemble_group_df_kernel(
 // FP64 with the FP64 kernel's formulas: there r is of the order of the node
 // spacing and ln r nearly cancels against the Kress log table.  One thread
 // per entry, so that no warp of assemble_group_df_kernel runs FP64 Bessel
-// series for a few lanes.
+// series for a few lanes.  A32 (may be null): the hi parts, row-major.
 __global__ void __launch_bounds__(256) assemble_band_kernel(
     SolveTables t, const int *__restrict__ list, const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ ddz, const double *__restrict__ kress,
-    const double *__restrict__ logsin, float4 *__restrict__ A, long long out_shift) {
+    const double *__restrict__ logsin, float4 *__restrict__ A, float2 *__restrict__ A32, long long out_shift) {
     constexpr int kW = 2 * kNearBand + 1;
     const int s = list[blockIdx.y];
     const int N = t.N[s];
@@ -367,7 +372,9 @@ __global__ void __launch_bounds__(256) assemble_band_kernel(
         ar = Rw * L1 + pin * (L2r + et * Mi);
         ai = Rw * (-et * M1) + pin * (Li - et * M2r);
     }
-    A[t.mat_off[s] + out_shift + (long long)l * N + i] = df_pack(ar, ai);
+    const float4 v = df_pack(ar, ai);
+    A[t.mat_off[s] + out_shift + (long long)l * N + i] = v;
+    if (A32) A32[t.mat_off[s] + out_shift + (long long)i * N + l] = make_float2(v.x, v.z);
 }
 
 // g_i = dB/dn - i eta B = i (kappa p.nu_i - eta) e^{i kappa p.z_i}
@@ -399,17 +406,17 @@ void launch_assemble_groups(const SolveTables &t, const Subgroups &g, int n_grou
                             const double2 *z, const double2 *dz,
                             const double2 *ddz, const double *kress, const double *logsin,
                             const float4 *zf, const float4 *dzf, const float2 *sf, const float2 *wpf,
-                            double2 *A, float4 *Af, long long out_shift, cudaStream_t st,
+                            double2 *A, float4 *Af, float2 *A32, long long out_shift, cudaStream_t st,
                             cudaStream_t band_st) {
     if (n_tiles <= 0 || n_groups <= 0) return;
     if (Af) {
         if (band_count > 0) {
             const dim3 grid((maxN * (2 * kNearBand + 1) + 255) / 256, band_count);
             assemble_band_kernel<<<grid, 256, 0, band_st>>>(t, band_list, z, dz, ddz, kress, logsin, Af,
-                                                            out_shift);
+                                                            A32, out_shift);
         }
         assemble_group_df_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, dz, zf, dzf, sf,
-                                                                    wpf, Af, out_shift, tile_base);
+                                                                    wpf, Af, A32, out_shift, tile_base);
     } else
         assemble_group_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(t, g, n_groups, z, dz, ddz, kress,
                                                                  logsin, A, out_shift, tile_base);
