@@ -287,8 +287,10 @@ __device__ void lu_solve_shared(const float2 *__restrict__ a, int n, float2 *y) 
 // Inverses of the 32 x 32 diagonal blocks of row-major factors, computed once
 // per factorisation: one CTA (two warps) per block; warp 0 inverts the unit
 // lower triangle, warp 1 the upper one, lane j solving for column j; the
-// inverses are stored row-major, L^{-1} then U^{-1}, 2048 values per block.
-// A partial last block is padded with the identity.
+// inverses are stored L^{-1} then U^{-1}, 2048 values per block, each as 16
+// column pairs x 32 rows of float4 (entry (i, 2h + c) at 64 h + 2 i + c), so
+// that the solve's diagonal warp reads a column pair of all 32 rows with one
+// 512-byte load.  A partial last block is padded with the identity.
 __global__ void __launch_bounds__(64) diag_inverse_kernel(const int2 *__restrict__ blocks,
                                                           const int *__restrict__ Ns,
                                                           const long long *__restrict__ mat_off,
@@ -340,135 +342,126 @@ __global__ void __launch_bounds__(64) diag_inverse_kernel(const int2 *__restrict
     __syncthreads();
     float2 *dst = inv + (long long)(blk_off[s] + b) * 2048;
     for (int e = tid; e < 2048; e += 64) {
-        const int ww = e >> 10, i = (e >> 5) & 31, q = e & 31;
-        dst[e] = T[ww][i][q];
+        const int ww = e >> 10, h = (e >> 6) & 15, i = (e >> 1) & 31, c = e & 1;
+        dst[e] = T[ww][i][2 * h + c];
     }
 }
 
-// Software-pipelined form of lu_solve_rowmajor for n <= blockDim.x - 32:
-// thread t < n keeps row t and the last warp (which owns no row) does the
-// diagonal-block products.  The loads a step needs (the last warp: the next
-// block inverse; a row thread: its row's segment of the next block) are
-// issued as soon as the current step has consumed the register buffer, so
-// that they are in flight across the barriers and the other warps' work
-// rather than on the critical path of each step.  Same arithmetic, in the
-// same order, as the blocked form.
-__device__ void lu_solve_rowmajor_pipe(const float2 *__restrict__ a, int n,
-                                       const float2 *__restrict__ inv, float2 *y) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    const bool dw = tid >= (int)blockDim.x - 32;   // the diagonal warp
+// Row-major factors (tensor-core LU), blockDim = 512: blocked substitution
+// over 32-row blocks, forward (L) then backward (U).  The last warp forms each
+// diagonal block's values as the product with its precomputed inverse (one
+// warp, no dependent chain).  The other 15 warps own the 32-row chunks w, w +
+// 15, ... and update every active row by its 32-column segment of the block:
+// eight lanes per row, lane h holding columns 2h, 2h + 1, 16 + 2h, 17 + 2h
+// (two 16-byte loads, so that one warp load covers four rows in four
+// 128-byte lines), then the eight partial sums of a lane group's eight rows
+// are reduced and scattered by shuffles so that lane h ends with row h's
+// total.  The next block inverse and the segments of a warp's first chunk of
+// the next step are loaded while the current step finishes.  N is even, so
+// that every segment is 16-byte aligned.
+__device__ void lu_solve_rowmajor(const float2 *__restrict__ a, int n, const float2 *__restrict__ inv,
+                                  float2 *y) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (int)(blockDim.x >> 5) - 1;   // row warps
+    const bool dw = warp == nw;                  // the diagonal warp
+    const int gq = lane >> 3, h = lane & 7;
     const int nblk = (n + 31) / 32, steps = 2 * nblk;
-    float4 r[16];   // next block inverse row (diagonal warp) or next row segment
-    // step k: pass 0 (L, forward) over blocks 0 .. nblk-1, then pass 1 (U,
-    // backward) over blocks nblk-1 .. 0; rows updated: below (L) or above (U)
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 r[16];   // next block inverse (diagonal warp) or the first chunk's segments
     auto block_of = [&](int k) { return k < nblk ? k : steps - 1 - k; };
-    auto active = [&](int k) {
-        const int b = block_of(k), jb = 32 * b, je = min(jb + 32, n);
-        return !dw && (k < nblk ? (tid >= je && tid < n) : (tid < jb));
+    // chunks updated at step k: below the block (forward) or above it (backward)
+    auto chunk_lo = [&](int k) { return k < nblk ? k + 1 : 0; };
+    auto chunk_hi = [&](int k) { return k < nblk ? nblk : steps - 1 - k; };
+    auto first_chunk = [&](int k) {   // the smallest c >= chunk_lo(k) with c = warp mod nw
+        const int lo = chunk_lo(k);
+        return lo + ((warp - lo % nw) + nw) % nw;
     };
     auto load_inv = [&](int k) {
-        const int pass = k < nblk ? 0 : 1, b = block_of(k);
-        const float4 *row = reinterpret_cast<const float4 *>(inv + (long long)b * 2048 + pass * 1024 + lane * 32);
+        const float4 *blk = reinterpret_cast<const float4 *>(inv + (long long)block_of(k) * 2048 +
+                                                             (k < nblk ? 0 : 1024));
 #pragma unroll
-        for (int h = 0; h < 16; ++h) r[h] = row[h];
+        for (int q = 0; q < 16; ++q) r[q] = blk[q * 32 + lane];
     };
-    auto load_row = [&](int k) {
+    auto load_chunk = [&](int k, int c) {   // rows 32 c + 4 j + gq, j < 8
         const int jb = 32 * block_of(k), je = min(jb + 32, n);
-        const float4 *src = reinterpret_cast<const float4 *>(a + (long long)tid * n + jb);
+        const bool v0 = jb + 2 * h < je, v1 = jb + 16 + 2 * h < je;   // je - jb is even
 #pragma unroll
-        for (int h = 0; h < 16; ++h)
-            if (jb + 2 * h < je) r[h] = src[h];
+        for (int j = 0; j < 8; ++j) {
+            const int i = 32 * c + 4 * j + gq;
+            const float4 *src = reinterpret_cast<const float4 *>(a + (long long)i * n + jb + 2 * h);
+            r[2 * j] = (i < n && v0) ? src[0] : z4;
+            r[2 * j + 1] = (i < n && v1) ? src[8] : z4;
+        }
+    };
+    auto update_chunk = [&](int k, int c) {   // the chunk's segments in r
+        const int jb = 32 * block_of(k), je = min(jb + 32, n);
+        const bool v0 = jb + 2 * h < je, v1 = jb + 16 + 2 * h < je;
+        const float2 z2 = make_float2(0.f, 0.f);
+        const float2 ya = v0 ? y[jb + 2 * h] : z2, yb = v0 ? y[jb + 2 * h + 1] : z2;
+        const float2 yc = v1 ? y[jb + 16 + 2 * h] : z2, yd = v1 ? y[jb + 17 + 2 * h] : z2;
+        float sx[8], sy[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 l0 = r[2 * j], l1 = r[2 * j + 1];
+            sx[j] = l0.x * ya.x - l0.y * ya.y + l0.z * yb.x - l0.w * yb.y + l1.x * yc.x - l1.y * yc.y +
+                    l1.z * yd.x - l1.w * yd.y;
+            sy[j] = l0.x * ya.y + l0.y * ya.x + l0.z * yb.y + l0.w * yb.x + l1.x * yc.y + l1.y * yc.x +
+                    l1.z * yd.y + l1.w * yd.x;
+        }
+        // reduce over the eight lanes and scatter: lane h keeps row h's sum
+        const bool b2 = (h >> 2) & 1, b1 = (h >> 1) & 1, b0 = h & 1;
+        float ax[4], ay[4], bx[2], by[2];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            ax[t] = (b2 ? sx[t + 4] : sx[t]) + __shfl_xor_sync(0xffffffffu, b2 ? sx[t] : sx[t + 4], 4);
+            ay[t] = (b2 ? sy[t + 4] : sy[t]) + __shfl_xor_sync(0xffffffffu, b2 ? sy[t] : sy[t + 4], 4);
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            bx[t] = (b1 ? ax[t + 2] : ax[t]) + __shfl_xor_sync(0xffffffffu, b1 ? ax[t] : ax[t + 2], 2);
+            by[t] = (b1 ? ay[t + 2] : ay[t]) + __shfl_xor_sync(0xffffffffu, b1 ? ay[t] : ay[t + 2], 2);
+        }
+        const float tx = (b0 ? bx[1] : bx[0]) + __shfl_xor_sync(0xffffffffu, b0 ? bx[0] : bx[1], 1);
+        const float ty = (b0 ? by[1] : by[0]) + __shfl_xor_sync(0xffffffffu, b0 ? by[0] : by[1], 1);
+        const int i = 32 * c + 4 * h + gq;
+        if (i < n) {
+            float2 yi = y[i];
+            yi.x -= tx;
+            yi.y -= ty;
+            y[i] = yi;
+        }
     };
     if (dw) load_inv(0);
-    else if (active(0)) load_row(0);
+    else if (first_chunk(0) < chunk_hi(0)) load_chunk(0, first_chunk(0));
     for (int k = 0; k < steps; ++k) {
         const int jb = 32 * block_of(k), je = min(jb + 32, n);
         if (dw) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int h = 0; h < 16; ++h) {
-                const int q = jb + 2 * h;
-                if (q < je) {
-                    const float2 y0 = y[q], y1 = y[q + 1];
-                    acc.x += r[h].x * y0.x - r[h].y * y0.y + r[h].z * y1.x - r[h].w * y1.y;
-                    acc.y += r[h].x * y0.y + r[h].y * y0.x + r[h].z * y1.y + r[h].w * y1.x;
+            for (int q = 0; q < 16; ++q)
+                if (jb + 2 * q < je) {
+                    const float2 y0 = y[jb + 2 * q], y1 = y[jb + 2 * q + 1];
+                    acc.x += r[q].x * y0.x - r[q].y * y0.y + r[q].z * y1.x - r[q].w * y1.y;
+                    acc.y += r[q].x * y0.y + r[q].y * y0.x + r[q].z * y1.y + r[q].w * y1.x;
                 }
-            }
             if (k + 1 < steps) load_inv(k + 1);
             __syncwarp();
             if (jb + lane < je) y[jb + lane] = acc;
         }
         __syncthreads();
-        if (active(k)) {
-            float2 yi = y[tid];
-#pragma unroll
-            for (int h = 0; h < 16; ++h)
-                if (jb + 2 * h < je) {
-                    const float2 y0 = y[jb + 2 * h], y1 = y[jb + 2 * h + 1];
-                    yi.x -= r[h].x * y0.x - r[h].y * y0.y + r[h].z * y1.x - r[h].w * y1.y;
-                    yi.y -= r[h].x * y0.y + r[h].y * y0.x + r[h].z * y1.y + r[h].w * y1.x;
+        if (!dw) {
+            const int hi = chunk_hi(k);
+            int c = first_chunk(k);
+            if (c < hi) {
+                update_chunk(k, c);
+                for (c += nw; c < hi; c += nw) {
+                    load_chunk(k, c);
+                    update_chunk(k, c);
                 }
-            y[tid] = yi;
+            }
+            if (k + 1 < steps && first_chunk(k + 1) < chunk_hi(k + 1)) load_chunk(k + 1, first_chunk(k + 1));
         }
-        if (k + 1 < steps && active(k + 1)) load_row(k + 1);
         __syncthreads();
-    }
-}
-
-// Row-major factors (tensor-core LU): blocked substitution in which each
-// 32-row diagonal step is a product with the precomputed block inverse (one
-// warp, no dependent chain) and the off-diagonal updates use 16-byte loads
-// of the row segments; written for blockDim = 512.
-__device__ void lu_solve_rowmajor(const float2 *__restrict__ a, int n, const float2 *__restrict__ inv,
-                                  float2 *y) {
-    if (n <= (int)blockDim.x - 32) {
-        lu_solve_rowmajor_pipe(a, n, inv, y);
-        return;
-    }
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int nblk = (n + 31) / 32;
-    for (int pass = 0; pass < 2; ++pass) {           // 0: L (forward), 1: U (backward)
-        for (int bi = 0; bi < nblk; ++bi) {
-            const int b = pass == 0 ? bi : nblk - 1 - bi;
-            const int jb = b * 32, je = min(jb + 32, n);
-            if (tid < 32) {
-                const float4 *row = reinterpret_cast<const float4 *>(inv + (long long)b * 2048 + pass * 1024 + lane * 32);
-                float4 v[16];
-#pragma unroll
-                for (int h = 0; h < 16; ++h) v[h] = row[h];
-                float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int h = 0; h < 16; ++h) {
-                    const int q = jb + 2 * h;
-                    if (q < je) {
-                        const float2 y0 = y[q], y1 = y[q + 1];
-                        acc.x += v[h].x * y0.x - v[h].y * y0.y + v[h].z * y1.x - v[h].w * y1.y;
-                        acc.y += v[h].x * y0.y + v[h].y * y0.x + v[h].z * y1.y + v[h].w * y1.x;
-                    }
-                }
-                __syncwarp();
-                if (jb + lane < je) y[jb + lane] = acc;
-            }
-            __syncthreads();
-            const int r0 = pass == 0 ? je : 0, r1 = pass == 0 ? n : jb;
-            for (int i = r0 + tid; i < r1; i += blockDim.x) {
-                float2 yi = y[i];
-                const float4 *src = reinterpret_cast<const float4 *>(a + (long long)i * n + jb);
-                float4 l[16];
-#pragma unroll
-                for (int h = 0; h < 16; ++h)
-                    if (jb + 2 * h < je) l[h] = src[h];
-#pragma unroll
-                for (int h = 0; h < 16; ++h)
-                    if (jb + 2 * h < je) {
-                        const float2 y0 = y[jb + 2 * h], y1 = y[jb + 2 * h + 1];
-                        yi.x -= l[h].x * y0.x - l[h].y * y0.y + l[h].z * y1.x - l[h].w * y1.y;
-                        yi.y -= l[h].x * y0.y + l[h].y * y0.x + l[h].z * y1.y + l[h].w * y1.x;
-                    }
-                y[i] = yi;
-            }
-            __syncthreads();
-        }
     }
 }
 
