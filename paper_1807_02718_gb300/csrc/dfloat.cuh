@@ -224,12 +224,12 @@ __device__ __forceinline__ void g_stage(GShared &tb) {
 }
 
 // The binary32 part of a remainder polynomial: G - c0 = t (c1 + c2 t + ...
-// + c7 t^6), its eight coefficients (c0 unused) as two 16-byte loads.
+// + c5 t^4), its coefficients (c0 unused) as two 16-byte loads of the eight
+// table entries; c6 and c7 are zero on every interval (gen_bessel_cheb.py
+// checks that at most six terms are needed).
 __device__ __forceinline__ float g_poly(const float *c, float t) {
     const float4 lo = reinterpret_cast<const float4 *>(c)[0], hi = reinterpret_cast<const float4 *>(c)[1];
-    float a = fmaf(hi.w, t, hi.z);
-    a = fmaf(a, t, hi.y);
-    a = fmaf(a, t, hi.x);
+    float a = fmaf(hi.y, t, hi.x);
     a = fmaf(a, t, lo.w);
     a = fmaf(a, t, lo.z);
     a = fmaf(a, t, lo.y);

@@ -141,7 +141,8 @@ def pq_table():
 # rest (|.| <= 1e-6) in binary32, which leaves ~1e-14 absolute error.
 LEAD = [(mp.mpf(1), mp.mpf(-9) / 8192), (mp.mpf(-1) / 64, mp.mpf(75) / 524288),
         (mp.mpf(1), mp.mpf(15) / 8192), (mp.mpf(3) / 64, mp.mpf(-105) / 524288)]
-G_TERMS = 8
+G_TERMS = 8   # table stride (two float4 per polynomial)
+G_EVAL = 6    # nonzero terms the device sums
 
 
 def g_table():
@@ -174,7 +175,7 @@ def g_table():
             c = [v for v in c]
             while len(c) > 1 and abs(c[-1]) < mp.mpf("1e-9") * scale:
                 c.pop()
-            if len(c) > G_TERMS:
+            if len(c) > G_EVAL:   # the device evaluates c0 .. c5 (g_poly in dfloat.cuh)
                 raise SystemExit(f"G{k} on [{x0},{x1}) needs {len(c)} terms")
             c = c + [mp.mpf(0)] * (G_TERMS - len(c))
             rows.append(cheb_to_monomial(c))
