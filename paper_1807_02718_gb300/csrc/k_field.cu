@@ -145,7 +145,7 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool 
 // and 1 / sqrt(kappa_j) on the staged densities, so that the Hankel form
 // returns sqrt(kappa_j) H0 and needs no amplitude product per frequency.
 template <int kG>   // largest subgroup size of the launch (<= kGroup)
-__global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
+__global__ void __launch_bounds__(kTgt, 5) field_partial_df_kernel(
     SolveTables t, Subgroups grp, const int2 *__restrict__ items, int item_begin, int chunk,
     const double2 *__restrict__ z, const double2 *__restrict__ dz,
     const double2 *__restrict__ psi, const double *__restrict__ x, int n_x,
@@ -168,6 +168,9 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
     __shared__ float k3s[3];   // kappa_0 as three binary32 pieces
     __shared__ float4 zs[kChunk];             // node coordinates, double-float
     __shared__ float4 ps[kGroup][kChunk];   // (pi/n)|z'|/4 psi_j / sqrt(kappa_j) as (re hi, re lo, im hi, im lo)
+    // each thread's sums (re hi, re lo, im hi, im lo) per frequency, in its own
+    // column: the frequency loop stays rolled (a small instruction footprint)
+    __shared__ float accs[kG][4][kTgt];
     __shared__ GShared gt;
     g_stage(gt);
     if (threadIdx.x == 0) {
@@ -217,9 +220,10 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
     if (it >= n_x) return;
     const dfv npx = df_neg(df_from(x[2 * it])), npy = df_neg(df_from(x[2 * it + 1]));
     const dfv two_over_pi = df_make(0.6366197466850281f, 2.5682552973194106e-08f);   // 2/pi
-    float ah[kG][2], al[kG][2];
 #pragma unroll
-    for (int j = 0; j < kG; ++j) ah[j][0] = ah[j][1] = al[j][0] = al[j][1] = 0.f;
+    for (int j = 0; j < kG; ++j)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) accs[j][h][threadIdx.x] = 0.f;
     for (int e = 0; e < ne; ++e) {
         const float4 z4 = zs[e];
         const dfv d1 = df_add(df_make(z4.x, z4.y), npx), d2 = df_add(df_make(z4.z, z4.w), npy);
@@ -234,7 +238,8 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
         c = df_mul(c, amp0);
         sv = df_mul(sv, amp0);
         const dfv lnr = kapf[0] * rd.hi < 8.0f ? df_log(rd) : df_make(0.f, 0.f);   // shared by the group
-#pragma unroll
+        const bool renorm = (e & 15) == 15;
+#pragma unroll 1
         for (int j = 0; j < kG; ++j) {
             if (j < cnt) {
                 const float xf = kapf[j] * rd.hi;
@@ -252,30 +257,34 @@ __global__ void __launch_bounds__(kTgt, 3) field_partial_df_kernel(
                 const float4 q4 = ps[j][e];
                 const dfv qr = df_make(q4.x, q4.y), qi = df_make(q4.z, q4.w);
                 // acc += (-Y0 qr - J0 qi) + i (-Y0 qi + J0 qr)
-                df_acc(ah[j][0], al[j][0], Y0, qr, true);
-                df_acc(ah[j][0], al[j][0], J0, qi, true);
-                df_acc(ah[j][1], al[j][1], Y0, qi, true);
-                df_acc(ah[j][1], al[j][1], J0, qr, false);
+                float *ac = &accs[j][0][threadIdx.x];
+                float rh = ac[0], rl = ac[kTgt], ih = ac[2 * kTgt], il = ac[3 * kTgt];
+                df_acc(rh, rl, Y0, qr, true);
+                df_acc(rh, rl, J0, qi, true);
+                df_acc(ih, il, Y0, qi, true);
+                df_acc(ih, il, J0, qr, false);
+                if (renorm) {   // every 16 nodes
+                    const dfv vr = df_quick(rh, rl), vi = df_quick(ih, il);
+                    rh = vr.hi;
+                    rl = vr.lo;
+                    ih = vi.hi;
+                    il = vi.lo;
+                }
+                ac[0] = rh;
+                ac[kTgt] = rl;
+                ac[2 * kTgt] = ih;
+                ac[3 * kTgt] = il;
                 const dfv cn = df_dot2(c, sc, df_neg(sv), ss);
                 sv = df_dot2(sv, sc, c, ss);
                 c = cn;
             }
         }
-        if ((e & 15) == 15)
-#pragma unroll
-            for (int j = 0; j < kG; ++j)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const dfv v = df_quick(ah[j][h], al[j][h]);
-                    ah[j][h] = v.hi;
-                    al[j][h] = v.lo;
-                }
     }
-#pragma unroll
-    for (int j = 0; j < kG; ++j)
-        if (j < cnt)
-            part[((long long)w * kGroup + j) * n_x + it] =
-                make_double2((double)ah[j][0] + (double)al[j][0], (double)ah[j][1] + (double)al[j][1]);
+    for (int j = 0; j < cnt; ++j) {
+        const float *ac = &accs[j][0][threadIdx.x];
+        part[((long long)w * kGroup + j) * n_x + it] =
+            make_double2((double)ac[0] + (double)ac[kTgt], (double)ac[2 * kTgt] + (double)ac[3 * kTgt]);
+    }
 }
 
 // V[solve_j[s0 + j]][x] = sum over the subgroup's items, in item order.
