@@ -102,6 +102,10 @@ struct fh_ctx {
     // stream, forked and joined around each tile launch
     cudaStream_t band = nullptr;
     cudaEvent_t ev_band0 = nullptr, ev_band1 = nullptr;
+    // the tensor-core LU's smaller cluster sizes (lowest priority), beside the
+    // largest systems' launch on the context stream
+    cudaStream_t fill = nullptr;
+    cudaEvent_t ev_fill0 = nullptr, ev_fill1 = nullptr;
     // frequency subgroups (one problem, equal N, at most tune.assemble_group
     // solves for the assembly, tune.field_group for the target fields)
     int n_groups = 0;
@@ -174,6 +178,9 @@ struct fh_ctx {
         if (band) cudaStreamDestroy(band);
         if (ev_band0) cudaEventDestroy(ev_band0);
         if (ev_band1) cudaEventDestroy(ev_band1);
+        if (fill) cudaStreamDestroy(fill);
+        if (ev_fill0) cudaEventDestroy(ev_fill0);
+        if (ev_fill1) cudaEventDestroy(ev_fill1);
         if (own) cudaStreamDestroy(own);
     }
 };
@@ -996,7 +1003,10 @@ fh_status fh_create(fh_ctx **out, int device, int precision) {
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_band0, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_band1, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_band1, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->fill, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fill0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fill1, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return FH_ECUDA;
     }
@@ -1098,27 +1108,50 @@ fh_status ensure_tc_work(fh_ctx *ctx) {
 
 // Tensor-core LU of the solves order[s0 .. s1-1] (d_info and d_tcerr are
 // cleared by the caller), after their row-major FP32 copies when convert
-// (the assembly wrote them otherwise).
-fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1, bool convert) {
+// (the assembly wrote them otherwise).  With fill, the solves of the largest
+// cluster size are factored on the context stream and the rest on the
+// lowest-priority fill stream from the same point, so that the small
+// systems' CTAs take the SMs that the last wave of large systems leaves idle
+// (the systems are independent; both streams join before the refinement).
+fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1, bool convert, bool fill) {
     if (convert)
         fh::launch_convert_rowmajor(ctx->d_order.as<int>() + s0, s1 - s0, ctx->d_N.as<int>(),
                                     ctx->d_mat_off.as<long long>(), ctx->d_A.as<float4>(),
                                     ctx->d_A32.as<float2>(), ctx->stream);
-    const cudaError_t e = fh::launch_lu_factor_tc(
-        ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>() + s0,
-        ctx->order.data() + s0, ctx->solve_N.data(), s1 - s0, ctx->d_N.as<int>(),
-        ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),
-        ctx->d_vec_off.as<int>(), ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(),
-        fh::LuTcWork{ctx->d_lu_maps.p, ctx->d_lu_opnd.as<uint8_t>(), ctx->d_lu_aoff.as<long long>(),
-                     ctx->d_lu_boff.as<long long>()},
-        ctx->stream);
+    int split = s1;
+    if (fill && s1 > s0) {
+        const int rows = ctx->tune.lu_rows_per_cta;
+        const int cs0 = fh::lu_tc_cluster(ctx->solve_N[ctx->order[s0]], rows);
+        split = s0;
+        while (split < s1 && fh::lu_tc_cluster(ctx->solve_N[ctx->order[split]], rows) == cs0) ++split;
+    }
+    if (split < s1) {
+        FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill0, ctx->stream));
+        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->fill, ctx->ev_fill0, 0));
+    }
+    auto launch = [&](int a, int b, cudaStream_t st) {
+        return fh::launch_lu_factor_tc(
+            ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>() + a,
+            ctx->order.data() + a, ctx->solve_N.data(), b - a, ctx->d_N.as<int>(),
+            ctx->d_mat_off.as<long long>(), ctx->d_A32.as<float2>(), ctx->d_piv.as<int>(),
+            ctx->d_vec_off.as<int>(), ctx->d_info.as<int>(), ctx->d_tcerr.as<int>(),
+            fh::LuTcWork{ctx->d_lu_maps.p, ctx->d_lu_opnd.as<uint8_t>(), ctx->d_lu_aoff.as<long long>(),
+                         ctx->d_lu_boff.as<long long>()},
+            st);
+    };
+    cudaError_t e = launch(s0, split, ctx->stream);
+    if (e == cudaSuccess && split < s1) e = launch(split, s1, ctx->fill);
     if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
+    if (split < s1) {
+        FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill1, ctx->fill));
+        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_fill1, 0));
+    }
     return FH_OK;
 }
 
 fh_status tc_factor_kernels(fh_ctx *ctx, bool convert) {
     FH_CUDA(ctx, cudaMemsetAsync(ctx->d_tcerr.p, 0, sizeof(int), ctx->stream));
-    return tc_factor_range(ctx, 0, ctx->S, convert);
+    return tc_factor_range(ctx, 0, ctx->S, convert, true);
 }
 
 int tc_launches(fh_ctx *ctx, int s0, int s1, bool convert) {
@@ -1178,7 +1211,7 @@ fh_status split_front(fh_ctx *ctx, bool refine) {
         OnStream on(ctx, ctx->side);
         {
             PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, 0, SL, false));
-            FH_TRY(tc_factor_range(ctx, 0, SL, false));
+            FH_TRY(tc_factor_range(ctx, 0, SL, false, false));
         }
         if (refine) FH_TRY(refine_range(ctx, true, 0, SL, 0, ctx->n_rchunk_early, 0, ctx->n_dblk_early));
     }
@@ -1189,7 +1222,7 @@ fh_status split_front(fh_ctx *ctx, bool refine) {
     }
     {
         PhaseScope ps(ctx, FH_PH_FACTOR, tc_launches(ctx, SL, S, false));
-        FH_TRY(tc_factor_range(ctx, SL, S, false));
+        FH_TRY(tc_factor_range(ctx, SL, S, false, true));
     }
     if (refine)
         FH_TRY(refine_range(ctx, true, SL, S, ctx->n_rchunk_early, ctx->n_rchunk, ctx->n_dblk_early, ctx->n_dblk));
