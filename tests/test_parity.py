@@ -383,14 +383,19 @@ def test_densities_tensor_core_lu(name, prec):
 
 @pytest.mark.parametrize("prec", list(TC_PRECISIONS))
 def test_large_config_tensor_core_lu(prec):
-    """The benchmark workload (N = 64..480, one CTA per system)."""
+    """The 256-frequency kite (N = 64..480, one CTA per system).  The LU is
+    only a preconditioner, so a wrong entry in the FP32 copy it factors (written
+    by the assembly) would show as extra sweeps rather than wrong densities: the
+    sweep count is pinned at the 3 the split operands need (2^-16 BF16, 2^-21
+    TF32, both contracting the error by more than 1e-4 per sweep)."""
     wl = fi.kite_pulses(n_near=256, n_far=64)
     pr = make(wl, TC_PRECISIONS[prec])
     st = pr.solve()
     psi_o = O.solve_all(wl)
     worst = max(rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) for j in range(1, wl.J))
     assert worst < TOL, worst
-    assert st.refine_iters_max <= 10
+    assert st.refine_iters_max <= 3, st.refine_iters_max
+    assert st.residual_max < 1e-12
 
 
 @pytest.mark.parametrize("prec", list(TC_PRECISIONS))
