@@ -1008,14 +1008,14 @@ cudaError_t launch_group(const int *order, int count, int cs, const int *N, cons
 
 }  // namespace
 
-// Every CTA owns kThreads = 512 panel rows, so at least ceil(n / 512) CTAs;
-// smaller rows_per_cta spreads the trailing updates over more CTAs.
+// Every CTA owns kThreads = 512 panel rows, so at least ceil(n / 512) CTAs,
+// and exactly that many (any cluster size up to 8: rows, items and U12
+// columns are split by rank); smaller rows_per_cta spreads the trailing
+// updates over more CTAs.
 int lu_tc_cluster(int n, int rows_per_cta) {
     const int rows = rows_per_cta >= kThreads ? kThreads : rows_per_cta >= 256 ? 256 : 128;
     const int need = (n + rows - 1) / rows;
-    int cs = 1;
-    while (cs < need && cs < 8) cs *= 2;
-    return cs;
+    return need < 1 ? 1 : need > kMaxCluster ? kMaxCluster : need;
 }
 
 int lu_tc_launches(const int *order_h, const int *N_h, int S, int rows_per_cta) {
