@@ -102,10 +102,11 @@ struct fh_ctx {
     // stream, forked and joined around each tile launch
     cudaStream_t band = nullptr;
     cudaEvent_t ev_band0 = nullptr, ev_band1 = nullptr;
-    // the tensor-core LU's smaller cluster sizes (lowest priority), beside the
-    // largest systems' launch on the context stream
-    cudaStream_t fill = nullptr;
-    cudaEvent_t ev_fill0 = nullptr, ev_fill1 = nullptr;
+    // the tensor-core LU's smaller cluster sizes, one stream each (lowest
+    // priority), beside the largest systems' launch on the context stream
+    static constexpr int kFill = 3;
+    cudaStream_t fill[kFill] = {};
+    cudaEvent_t ev_fill0 = nullptr, ev_fill1[kFill] = {};
     // frequency subgroups (one problem, equal N, at most tune.assemble_group
     // solves for the assembly, tune.field_group for the target fields)
     int n_groups = 0;
@@ -178,9 +179,11 @@ struct fh_ctx {
         if (band) cudaStreamDestroy(band);
         if (ev_band0) cudaEventDestroy(ev_band0);
         if (ev_band1) cudaEventDestroy(ev_band1);
-        if (fill) cudaStreamDestroy(fill);
+        for (int f = 0; f < kFill; ++f) {
+            if (fill[f]) cudaStreamDestroy(fill[f]);
+            if (ev_fill1[f]) cudaEventDestroy(ev_fill1[f]);
+        }
         if (ev_fill0) cudaEventDestroy(ev_fill0);
-        if (ev_fill1) cudaEventDestroy(ev_fill1);
         if (own) cudaStreamDestroy(own);
     }
 };
@@ -1004,12 +1007,16 @@ fh_status fh_create(fh_ctx **out, int device, int precision) {
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_band0, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_band1, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&ctx->fill, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fill0, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fill1, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_fill0, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return FH_ECUDA;
     }
+    for (int f = 0; f < fh_ctx::kFill; ++f)
+        if (cudaStreamCreateWithPriority(&ctx->fill[f], cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_fill1[f], cudaEventDisableTiming) != cudaSuccess) {
+            delete ctx;
+            return FH_ECUDA;
+        }
     ctx->stream = ctx->own;
     *out = ctx;
     return FH_OK;
@@ -1109,26 +1116,30 @@ fh_status ensure_tc_work(fh_ctx *ctx) {
 // Tensor-core LU of the solves order[s0 .. s1-1] (d_info and d_tcerr are
 // cleared by the caller), after their row-major FP32 copies when convert
 // (the assembly wrote them otherwise).  With fill, the solves of the largest
-// cluster size are factored on the context stream and the rest on the
-// lowest-priority fill stream from the same point, so that the small
-// systems' CTAs take the SMs that the last wave of large systems leaves idle
-// (the systems are independent; both streams join before the refinement).
+// cluster size are factored on the context stream and each smaller cluster
+// size on a lowest-priority fill stream of its own (the last one takes the
+// rest), all from the same point, so that the smaller systems' CTAs take the
+// SMs that the tail of each larger size leaves idle (the systems are
+// independent; the streams join before the refinement).
 fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1, bool convert, bool fill) {
     if (convert)
         fh::launch_convert_rowmajor(ctx->d_order.as<int>() + s0, s1 - s0, ctx->d_N.as<int>(),
                                     ctx->d_mat_off.as<long long>(), ctx->d_A.as<float4>(),
                                     ctx->d_A32.as<float2>(), ctx->stream);
-    int split = s1;
-    if (fill && s1 > s0) {
+    // runs of equal cluster size in order (sorted by decreasing N)
+    int cut[fh_ctx::kFill + 2];
+    int nrun = 0;
+    cut[0] = s0;
+    if (fill) {
         const int rows = ctx->tune.lu_rows_per_cta;
-        const int cs0 = fh::lu_tc_cluster(ctx->solve_N[ctx->order[s0]], rows);
-        split = s0;
-        while (split < s1 && fh::lu_tc_cluster(ctx->solve_N[ctx->order[split]], rows) == cs0) ++split;
+        for (int i = s0 + 1; i < s1 && nrun < fh_ctx::kFill; ++i)
+            if (fh::lu_tc_cluster(ctx->solve_N[ctx->order[i]], rows) !=
+                fh::lu_tc_cluster(ctx->solve_N[ctx->order[i - 1]], rows))
+                cut[++nrun] = i;
     }
-    if (split < s1) {
-        FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill0, ctx->stream));
-        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->fill, ctx->ev_fill0, 0));
-    }
+    cut[++nrun] = s1;   // runs [cut[r], cut[r + 1]), r < nrun; run 0 on the context stream
+    if (nrun > 1) FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill0, ctx->stream));
+    for (int r = 1; r < nrun; ++r) FH_CUDA(ctx, cudaStreamWaitEvent(ctx->fill[r - 1], ctx->ev_fill0, 0));
     auto launch = [&](int a, int b, cudaStream_t st) {
         return fh::launch_lu_factor_tc(
             ctx->precision == FH_MIXED_TF32 ? 2 : 1, ctx->tune.lu_rows_per_cta, ctx->d_order.as<int>() + a,
@@ -1139,12 +1150,13 @@ fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1, bool convert, bool fill) 
                          ctx->d_lu_boff.as<long long>()},
             st);
     };
-    cudaError_t e = launch(s0, split, ctx->stream);
-    if (e == cudaSuccess && split < s1) e = launch(split, s1, ctx->fill);
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < nrun && e == cudaSuccess; ++r)
+        e = launch(cut[r], cut[r + 1], r == 0 ? ctx->stream : ctx->fill[r - 1]);
     if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
-    if (split < s1) {
-        FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill1, ctx->fill));
-        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_fill1, 0));
+    for (int r = 1; r < nrun; ++r) {
+        FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill1[r - 1], ctx->fill[r - 1]));
+        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_fill1[r - 1], 0));
     }
     return FH_OK;
 }
