@@ -107,6 +107,8 @@ struct fh_ctx {
     static constexpr int kFill = 3;
     cudaStream_t fill[kFill] = {};
     cudaEvent_t ev_fill0 = nullptr, ev_fill1[kFill] = {};
+    cudaStream_t lu_hi = nullptr;        // the largest cluster size, high priority
+    cudaEvent_t ev_hi = nullptr;
     // frequency subgroups (one problem, equal N, at most tune.assemble_group
     // solves for the assembly, tune.field_group for the target fields)
     int n_groups = 0;
@@ -184,6 +186,8 @@ struct fh_ctx {
             if (ev_fill1[f]) cudaEventDestroy(ev_fill1[f]);
         }
         if (ev_fill0) cudaEventDestroy(ev_fill0);
+        if (lu_hi) cudaStreamDestroy(lu_hi);
+        if (ev_hi) cudaEventDestroy(ev_hi);
         if (own) cudaStreamDestroy(own);
     }
 };
@@ -1007,7 +1011,9 @@ fh_status fh_create(fh_ctx **out, int device, int precision) {
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_band0, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_band1, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fill0, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_fill0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->lu_hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_hi, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return FH_ECUDA;
     }
@@ -1137,8 +1143,13 @@ fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1, bool convert, bool fill) 
                 fh::lu_tc_cluster(ctx->solve_N[ctx->order[i - 1]], rows))
                 cut[++nrun] = i;
     }
-    cut[++nrun] = s1;   // runs [cut[r], cut[r + 1]), r < nrun; run 0 on the context stream
-    if (nrun > 1) FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill0, ctx->stream));
+    cut[++nrun] = s1;   // runs [cut[r], cut[r + 1]), r < nrun
+    // run 0 on the high-priority stream (its clusters are handed out first), the rest on the fill streams
+    cudaStream_t st0 = nrun > 1 ? ctx->lu_hi : ctx->stream;
+    if (nrun > 1) {
+        FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill0, ctx->stream));
+        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->lu_hi, ctx->ev_fill0, 0));
+    }
     for (int r = 1; r < nrun; ++r) FH_CUDA(ctx, cudaStreamWaitEvent(ctx->fill[r - 1], ctx->ev_fill0, 0));
     auto launch = [&](int a, int b, cudaStream_t st) {
         return fh::launch_lu_factor_tc(
@@ -1152,8 +1163,12 @@ fh_status tc_factor_range(fh_ctx *ctx, int s0, int s1, bool convert, bool fill) 
     };
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < nrun && e == cudaSuccess; ++r)
-        e = launch(cut[r], cut[r + 1], r == 0 ? ctx->stream : ctx->fill[r - 1]);
+        e = launch(cut[r], cut[r + 1], r == 0 ? st0 : ctx->fill[r - 1]);
     if (e != cudaSuccess) return fail(ctx, FH_ECUDA, "tensor-core LU launch: %s", cudaGetErrorString(e));
+    if (nrun > 1) {
+        FH_CUDA(ctx, cudaEventRecord(ctx->ev_hi, ctx->lu_hi));
+        FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_hi, 0));
+    }
     for (int r = 1; r < nrun; ++r) {
         FH_CUDA(ctx, cudaEventRecord(ctx->ev_fill1[r - 1], ctx->fill[r - 1]));
         FH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_fill1[r - 1], 0));
