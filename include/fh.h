@@ -88,7 +88,11 @@ typedef struct {
 
 /* Create a context on CUDA device `device` with solve precision `precision`
  * (FH_FP64, FH_MIXED_FP32, FH_MIXED_TF32 or FH_MIXED_BF16).  *out receives the context.  The context owns a
- * non-blocking CUDA stream until fh_set_stream selects another one.
+ * non-blocking CUDA stream until fh_set_stream selects another one.  Inside a
+ * call, independent work may fork onto private helper streams of the context
+ * (the near-diagonal band of the assembly, the largest systems started early,
+ * the tensor-core LU's cluster sizes); every fork is joined back into the
+ * context stream within the same call, so all results are ordered on it.
  * Errors: FH_EINVAL (bad precision / NULL out), FH_ECUDA (no such device). */
 fh_status fh_create(fh_ctx **out, int device, int precision);
 
