@@ -175,6 +175,7 @@ struct PanelShared {
     uint64_t bar[2];
     uint32_t tslot;
     int wait_failed;                            // a completion wait of this CTA gave up
+    int ffail[kMaxCluster];                     // diagonal-pivot fast path: verdict of every CTA
 };
 
 // Arg-max of packed keys over a warp; returns (hi, lo) of the best.
@@ -409,6 +410,141 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         int mypos = myslot;
         bool active = own;
 
+        // 1a. Checked fast path.  Partial pivoting keeps the diagonal row
+        // whenever, at every column, no row below it has a larger key (the
+        // same packed |re| + |im| keys and tie rule as below: the diagonal is
+        // the smallest position, so it wins ties).  For the second-kind CFIE
+        // systems that holds with a wide margin (the largest key below the
+        // diagonal is ~1/4 of it), and then the per-column search and
+        // exchange across the cluster decide nothing.  So: the warp owning
+        // the panel's first rows (CTA 0, threads 0-31) eliminates the 32 x 32
+        // diagonal block, checking the keys among its rows and writing each
+        // pivot row and its reciprocal into u11 (the A staging space, idle
+        // during the panel); u11 goes to every CTA; every other row is
+        // eliminated against u11 with its own key checked; one verdict per
+        // panel.  The arithmetic is that of the search path below.  If any
+        // check fails (or a pivot is zero or not finite) the panel is
+        // reloaded and factored by the search path.
+        bool fast = false;
+        {
+            float2 (*u11)[NB + 2] = reinterpret_cast<float2 (*)[NB + 2]>(sA);   // [c][q]; pinv at [c][NB]
+            uint32_t fail = 0u;
+            const bool dwarp = rank == 0 && warp == 0;     // rows 0-31: the diagonal block
+            const bool lrow = own && myslot >= nb;         // rows eliminated against u11
+            auto diag_step = [&](auto rows_c, const int q0) {
+                constexpr int kRows = decltype(rows_c)::value;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = q0 + i;
+                    if (c < nb) {
+                        if (lane == c) {
+#pragma unroll
+                            for (int e = i; e < kRows; ++e)
+                                if (q0 + e < NB) u11[c][q0 + e] = v[e];
+                        }
+                        __syncwarp();
+                        const float2 pvt = u11[c][c];
+                        const uint32_t kd = __float_as_uint(fabsf(pvt.x) + fabsf(pvt.y));
+                        const bool act = own && lane > c;
+                        const uint32_t kr = act ? __float_as_uint(fabsf(v[i].x) + fabsf(v[i].y)) : 0u;
+                        const uint32_t kmax = __reduce_max_sync(0xffffffffu, kr);
+                        if (kmax > kd || kd == 0u || kd >= 0x7F800000u) fail = 1u;
+                        const float rd = 1.f / (pvt.x * pvt.x + pvt.y * pvt.y);
+                        const float2 pinv = make_float2(pvt.x * rd, -pvt.y * rd);
+                        if (lane == 0) u11[c][NB] = pinv;
+                        if (act) {
+                            const float2 l = cmul(v[i], pinv);
+                            v[i] = l;
+#pragma unroll
+                            for (int e = i + 1; e < kRows; ++e)
+                                if (q0 + e < NB) {
+                                    const float2 u = u11[c][q0 + e];
+                                    v[e].x -= l.x * u.x - l.y * u.y;
+                                    v[e].y -= l.x * u.y + l.y * u.x;
+                                }
+                        }
+                        __syncwarp();
+                    }
+                }
+                float2 t[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) t[e] = v[e];
+#pragma unroll
+                for (int e = 0; e + 4 < NB; ++e) v[e] = v[e + 4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[NB - 4 + e] = t[e];
+            };
+            auto row_step = [&](auto rows_c, const int q0) {
+                constexpr int kRows = decltype(rows_c)::value;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = q0 + i;
+                    if (c < nb && lrow) {
+                        const float2 pvt = u11[c][c], pinv = u11[c][NB];
+                        const uint32_t kd = __float_as_uint(fabsf(pvt.x) + fabsf(pvt.y));
+                        if (__float_as_uint(fabsf(v[i].x) + fabsf(v[i].y)) > kd) fail = 1u;
+                        const float2 l = cmul(v[i], pinv);
+                        v[i] = l;
+#pragma unroll
+                        for (int e = i + 1; e < kRows; ++e)
+                            if (q0 + e < NB) {
+                                const float2 u = u11[c][q0 + e];
+                                v[e].x -= l.x * u.x - l.y * u.y;
+                                v[e].y -= l.x * u.y + l.y * u.x;
+                            }
+                    }
+                }
+                float2 t[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) t[e] = v[e];
+#pragma unroll
+                for (int e = 0; e + 4 < NB; ++e) v[e] = v[e + 4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[NB - 4 + e] = t[e];
+            };
+            if (dwarp) {
+#pragma unroll 1
+                for (int q0 = 0; q0 < NB / 2; q0 += 4) diag_step(std::integral_constant<int, NB>{}, q0);
+#pragma unroll 1
+                for (int q0 = NB / 2; q0 < NB; q0 += 4) diag_step(std::integral_constant<int, NB / 2>{}, q0);
+                if constexpr (kMulti) {   // u11 (pivot rows and reciprocals) to the other CTAs
+                    const float4 *src = reinterpret_cast<const float4 *>(&u11[0][0]);
+                    constexpr int kU4 = NB * (NB + 2) / 2;
+                    for (int r = 1; r < cs; ++r) {
+                        float4 *dst = reinterpret_cast<float4 *>(at_rank(&u11[0][0], cs, r));
+                        for (int e = lane; e < kU4; e += 32) dst[e] = src[e];
+                    }
+                }
+            }
+            sys_sync(cs, false);   // u11 in every CTA
+            if (lrow) {
+#pragma unroll 1
+                for (int q0 = 0; q0 < NB / 2; q0 += 4) row_step(std::integral_constant<int, NB>{}, q0);
+#pragma unroll 1
+                for (int q0 = NB / 2; q0 < NB; q0 += 4) row_step(std::integral_constant<int, NB / 2>{}, q0);
+            }
+            const int any = __syncthreads_or((int)fail);
+            if constexpr (kMulti) {
+                if (tid == 0)
+                    for (int r = 0; r < cs; ++r) *at_rank(&ps.ffail[rank], cs, r) = any;
+                sys_sync(cs, false);
+                int all = 0;
+                for (int r = 0; r < cs; ++r) all |= ps.ffail[r];
+                fast = all == 0;
+            } else {
+                fast = any == 0;
+            }
+            if (!fast) {   // the search path below, from the panel as loaded
+                const float4 *src = reinterpret_cast<const float4 *>(a + (long long)(k0 + (own ? myslot : 0)) * n + k0);
+#pragma unroll
+                for (int h = 0; h < NB / 2; ++h) {
+                    const float4 t = (own && 2 * h < nb) ? __ldcg(src + h) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[2 * h] = make_float2(t.x, t.y);
+                    v[2 * h + 1] = make_float2(t.z, t.w);
+                }
+            }
+        }
+
         // 1. panel factorisation in registers, four columns per step of a
         // short rolled loop: v rotates left by four after each step, so that
         // v[i] is column q0 + i of the step and v[e] column q0 + e (e < 32 - q0;
@@ -416,6 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
         // the eighth step).  Two loop bodies, all 32 entries while q0 < 16 and
         // the first 16 after, keep the code small enough for the instruction
         // cache; the entries past the panel are skipped by predicate.
+        if (!fast) {
         if constexpr (kMulti) {
             auto panel_step = [&](auto rows_c, auto group_c, const int q0) {
                 constexpr int kRows = decltype(rows_c)::value, kGroup = decltype(group_c)::value;
@@ -612,6 +749,7 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
             }
         }
         }
+        }   // !fast
         if (bad) break;
 
         // 2. panel to its final rows (and the L21 rows to the staged A

@@ -412,6 +412,30 @@ def test_tensor_core_lu_clusters(prec):
         assert rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) < TOL
 
 
+@pytest.mark.parametrize("prec", list(TC_PRECISIONS))
+def test_tensor_core_lu_row_exchanges(prec):
+    """The tensor-core LU keeps the diagonal pivots only where partial pivoting
+    would (each panel checked; otherwise the panel is factored again with the
+    per-column search).  With the CFIE coupling eta = omega no row is ever
+    exchanged; with eta = 1000 omega the single layer dominates and the
+    highest frequencies of the small kite (N 66..110) and the 520-point
+    system of the cluster case need exchanges (checked on the oracle's
+    matrices), while the 2600- and 1536-point systems (clusters of 6 and 3
+    CTAs) keep the diagonal: every combination agrees with the oracle.  (The
+    refinement stops on its correction tolerance; with the single layer scaled
+    by 1000 the final relative residual is ~1e-12, so it is bounded at 1e-11.)"""
+    for wl in (fi.small_kite(J=10, W=7.0), fi.small_kite(J=4, W=60.0)):
+        if wl.J == 4:
+            wl.N = np.asarray([0, 2600, 1536, 520], dtype=np.int32)
+        wl.eta = 1e3 * wl.omega
+        pr = make(wl, TC_PRECISIONS[prec])
+        st = pr.solve(wl.eta)
+        assert st.residual_max < 1e-11
+        psi_o = O.solve_all(wl)
+        for j in range(1, wl.J):
+            assert rel(F.fh_get_density(pr.ctx, j, int(wl.N[j])), psi_o[j]) < TOL, (wl.J, j)
+
+
 def test_resample_on_resident_target_fields():
     """fh_resample_p: new times on the target fields left by the last sample
     (no fresh step F5) equal a fresh fh_sample at those times bit for bit, and
