@@ -188,15 +188,15 @@ def window_pairs(wl):
 # their roofline), from ncu captures of one launch of each kernel on the
 # wide-band kite (summaries in profiles/).  Their algorithmic rates are given
 # in the method's own units (matrix entries/s, target-node pairs/s).
-NCU_PIPE = {"lu_factor_tc_kernel": {"tensor_pipe_active_pct": 9.0, "issue_active_pct": 22.5,
-                                    "dram_throughput_pct": 8.2,
+NCU_PIPE = {"lu_factor_tc_kernel": {"tensor_pipe_active_pct": 9.8, "issue_active_pct": 17.9,
+                                    "dram_throughput_pct": 8.9,
                                     "capture": "profiles/lu_factor_tc_kite_wide.md (BF16)"}}
 # DRAM bytes (read + write) of the dominant kernels per step, from the same
 # captures (None where no capture of the current kernel exists): the LU's
 # capture of the clusters of 4 CTAs of the reduced case (13 systems, N
-# 1568..1920: 5.47 GB), scaled to the headline workload's factorisation by
+# 1568..1920: 5.44 GB), scaled to the headline workload's factorisation by
 # sum N^3 (13.3x).
-MEASURED_TRAFFIC = {"lu_factor_tc_kernel": 7.28e10}
+MEASURED_TRAFFIC = {"lu_factor_tc_kernel": 7.24e10}
 
 
 def phase_rooflines(wl, precision, ms, iters, peaks, contract_tc=False):
