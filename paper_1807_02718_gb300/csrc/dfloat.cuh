@@ -106,6 +106,21 @@ __device__ __forceinline__ dfv df_dot2(dfv a, dfv b, dfv c, dfv d) {
     return df_quick(s, ((p - (s - bb)) + (q - bb)) + (e + f));
 }
 
+// acc += a * b (or -= when neg): exact FP32 product hi*hi with its FMA
+// residual and the cross terms; the running sum (sh, sl) is a two-sum pair
+// that the caller renormalises (df_quick) every few terms.
+__device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool neg) {
+    float p = a.hi * b.hi;
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    if (neg) { p = -p; pe = -pe; }
+    const float t = sh + p;
+    const float z = t - sh;
+    sl += ((sh - (t - z)) + (p - z)) + pe;
+    sh = t;
+}
+
 __device__ __forceinline__ dfv df_sqrt(dfv a) {
     const float s = sqrtf(a.hi);
     const float e = (fmaf(-s, s, a.hi) + a.lo) * (0.5f / s);

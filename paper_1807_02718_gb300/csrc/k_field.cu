@@ -121,20 +121,6 @@ __global__ void __launch_bounds__(kTgt) field_partial_kernel(
         if (j < cnt) part[((long long)w * kGroup + j) * n_x + it] = acc[j];
 }
 
-// acc += a * b (or -= when neg): exact FP32 product hi*hi with its FMA
-// residual and the cross terms; the running sum is a two-sum pair that is
-// renormalised by the caller.
-__device__ __forceinline__ void df_acc(float &sh, float &sl, dfv a, dfv b, bool neg) {
-    float p = a.hi * b.hi;
-    float pe = fmaf(a.hi, b.hi, -p);
-    pe = fmaf(a.hi, b.lo, pe);
-    pe = fmaf(a.lo, b.hi, pe);
-    if (neg) { p = -p; pe = -pe; }
-    const float t = sh + p;
-    const float z = t - sh;
-    sl += ((sh - (t - z)) + (p - z)) + pe;
-    sh = t;
-}
 
 // Mixed-precision variant of field_partial_kernel: the same sums with the
 // distances, H0 (Hankel form for kappa r >= 8, the small-argument series with

@@ -37,6 +37,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "fc_gram_table.h"
 #include "fh_internal.h"
 
@@ -51,6 +52,26 @@ constexpr int kGl = 32;
 __constant__ double c_cheb[kSNq][kSNq];   // interpolant coefficients a_n = sum_c c_cheb[n][c] f_c
 __constant__ double c_glx[kGl], c_glw[kGl];
 __constant__ double c_mu[kSM];
+
+// acc += a * b (or -= when neg) with the low part compensated too: the
+// running sum is (sh, sl, sc), the product's FMA residual and cross terms
+// and the exact two-sum error of the high part enter sl by a second two-sum
+// (the smooth weights' sums cancel strongly).
+__device__ __forceinline__ void df_acc_c(float &sh, float &sl, float &sc, dfv a, dfv b, bool neg) {
+    float p = a.hi * b.hi;
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    if (neg) { p = -p; pe = -pe; }
+    const float t = sh + p;
+    const float z = t - sh;
+    const float x = ((sh - (t - z)) + (p - z)) + pe;
+    const float u = sl + x;
+    const float w = u - sl;
+    sc += (sl - (u - w)) + (x - w);
+    sl = u;
+    sh = t;
+}
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -110,7 +131,7 @@ __global__ void fc_rows_kernel(int n, double *__restrict__ Xc) {
 
 // E[mi * n + p] (mi = m + L/2): coefficient c'_m about the interval centre
 // per unit sample p:  (1/L) e^{i pi m (n-1)/L} sum_l e^{-2 pi i m l / L} X[l][p].
-__global__ void fc_dft_kernel(int n, int L, const double *__restrict__ Xc, double2 *__restrict__ E) {
+__global__ void fc_dft_kernel(int n, int L, const double *__restrict__ Xc, float4 *__restrict__ E) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x, mi = blockIdx.y;
     if (p >= n) return;
     const long long m = mi - L / 2;
@@ -123,18 +144,24 @@ __global__ void fc_dft_kernel(int n, int L, const double *__restrict__ Xc, doubl
     }
     const double2 sh = expi_pi_ratio(m * (n - 1), L);
     const double2 r = cmul(acc, sh);
-    E[(long long)mi * n + p] = make_double2(r.x / L, r.y / L);
+    E[(long long)mi * n + p] = df_pack(r.x / L, r.y / L);   // double-float pairs for the weights
 }
 
 // Smooth-piece weights: one CTA per time; for every window the kernel row
 // K_m(t - s_k) goes to shared memory, then each thread forms D_p = sum_m K_m
 // E[m][p] for its samples and accumulates B_k(w_p) D_p.  Rows 0..n-1 of the
-// weight planes: Gr = Re G / pi, Gm = -Im G / pi.
+// weight planes: Gr = Re G / pi, Gm = -Im G / pi.  The kernel row (FP64) and
+// E are held as double-float pairs and the L-term sums D_p run in
+// double-float on the FP32 pipe (exact products, compensated two-sum
+// accumulation); B_k D_p and the sum over windows stay FP64.  The pairs'
+// ~2^-48 rounding, amplified like any input rounding by the FC(Gram)
+// continuation, leaves ~1e-10 of u (measured 8.8e-11 on the small kite
+// against 3.8e-11 with FP64 sums), 50x below the split rule's own error.
 __global__ void __launch_bounds__(256) smooth_weights_kernel(
     int n, int L, double A, double P, double delta, int K, const double *__restrict__ s,
-    const double2 *__restrict__ B, int J, int j_c, const double2 *__restrict__ E,
+    const double2 *__restrict__ B, int J, int j_c, const float4 *__restrict__ E,
     const double *__restrict__ T, int n_T, double *__restrict__ Gr, double *__restrict__ Gm) {
-    extern __shared__ double2 km[];   // L values
+    extern __shared__ float4 km[];   // L values (re hi, re lo, im hi, im lo)
     const int it = blockIdx.x;
     const double t = T[it];
     const double alpha = P / (2.0 * kPi), r = 2.0 * A / P;
@@ -149,19 +176,25 @@ __global__ void __launch_bounds__(256) smooth_weights_kernel(
             for (int mi = threadIdx.x; mi < L; mi += blockDim.x) {
                 const double y = r * (alpha * tp - (double)(mi - L / 2));
                 const double sv = y == 0.0 ? 1.0 : sinpi(y) / (kPi * y);
-                km[mi] = make_double2(2.0 * A * sv * ph.x, 2.0 * A * sv * ph.y);
+                km[mi] = df_pack(2.0 * A * sv * ph.x, 2.0 * A * sv * ph.y);
             }
             __syncthreads();
             for (int q = 0; q < kPer; ++q) {
                 const int p = p0 + q * blockDim.x + threadIdx.x;
                 if (p >= n) continue;
-                double2 d = make_double2(0.0, 0.0);
+                float rh = 0.f, rl = 0.f, rc = 0.f, ih = 0.f, il = 0.f, ic = 0.f;
                 for (int mi = 0; mi < L; ++mi) {
-                    const double2 e = __ldg(&E[(long long)mi * n + p]);
-                    const double2 kk = km[mi];
-                    d.x += kk.x * e.x - kk.y * e.y;
-                    d.y += kk.x * e.y + kk.y * e.x;
+                    const float4 e = __ldg(&E[(long long)mi * n + p]);
+                    const float4 kk = km[mi];
+                    const dfv kr = df_make(kk.x, kk.y), ki = df_make(kk.z, kk.w);
+                    const dfv er = df_make(e.x, e.y), ei = df_make(e.z, e.w);
+                    df_acc_c(rh, rl, rc, kr, er, false);   // Re: kr er - ki ei
+                    df_acc_c(rh, rl, rc, ki, ei, true);
+                    df_acc_c(ih, il, ic, kr, ei, false);   // Im: kr ei + ki er
+                    df_acc_c(ih, il, ic, ki, er, false);
                 }
+                const double2 d = make_double2((double)rh + (double)rl + (double)rc,
+                                               (double)ih + (double)il + (double)ic);
                 acc[q] = cadd(acc[q], cmul(B[(long long)k * J + j_c + p], d));
             }
         }
@@ -450,7 +483,7 @@ extern "C" fh_status fh_synthesize_sing(int J, double W, int j_c, int K, const d
     {
         Scratch sc{{}, st};
         double *Xc = sc.get<double>((size_t)kFcC * n);
-        double2 *E = sc.get<double2>((size_t)L * n);
+        float4 *E = sc.get<float4>((size_t)L * n);   // the FC operator as double-float pairs
         double2 *Vp = sc.get<double2>((size_t)ns * n_x);
         double *Gr = sc.get<double>((size_t)ns * n_T);
         double *Gm = sc.get<double>((size_t)ns * n_T);
@@ -461,7 +494,7 @@ extern "C" fh_status fh_synthesize_sing(int J, double W, int j_c, int K, const d
         fc_rows_kernel<<<dim3(grid_of(n, 128), kFcC), 128, 0, st>>>(n, Xc);
         fc_dft_kernel<<<dim3(grid_of(n, 128), L), 128, 0, st>>>(n, L, Xc, E);
         const double A = 0.5 * (W - wc), P = L * dw, delta = 0.5 * (wc + W);
-        const size_t smem = (size_t)L * sizeof(double2);
+        const size_t smem = (size_t)L * sizeof(float4);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(smooth_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         smooth_weights_kernel<<<n_T, 256, smem, st>>>(n, L, A, P, delta, K, d_s,
