@@ -246,32 +246,40 @@ __device__ void cheb_moments(double kap, double2 (&rho)[kSNq]) {
     }
 }
 
-// Singular-piece weights: one thread per (time, Clenshaw-Curtis point);
-// rows n .. n+23 of the weight planes.
+// Singular-piece weights: one thread per (time, interval of the graded
+// mesh); the interval's eight Clenshaw-Curtis points share its Chebyshev
+// moments and phase, computed once per window.  Rows n .. n+23 of the weight
+// planes (row n + 8 (jv - 1) + c for point c of interval jv).
 __global__ void fcc_weights_kernel(int n, int K, const double *__restrict__ s, const double2 *__restrict__ Bs,
                                    const double *__restrict__ T, int n_T, double *__restrict__ Gr,
                                    double *__restrict__ Gm) {
-    const int it = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    const int it = blockIdx.x * blockDim.x + threadIdx.x, jv = blockIdx.y + 1;
     if (it >= n_T) return;
-    const int jv = i / kSNq + 1, c = i % kSNq;          // interval [mu_{jv-1}, mu_jv] (0-based c_mu)
-    const double a = c_mu[jv - 1], b = c_mu[jv];
+    const double a = c_mu[jv - 1], b = c_mu[jv];        // interval [mu_{jv-1}, mu_jv] (0-based c_mu)
     const double h = 0.5 * (b - a), dl = 0.5 * (a + b);
-    double2 acc = make_double2(0.0, 0.0);
+    const int i0 = (jv - 1) * kSNq;
+    double2 acc[kSNq];
+    for (int c = 0; c < kSNq; ++c) acc[c] = make_double2(0.0, 0.0);
     for (int k = 0; k < K; ++k) {
         const double tp = T[it] - s[k];
         double2 rho[kSNq];
         cheb_moments(h * tp, rho);
-        double2 w = make_double2(0.0, 0.0);
-        for (int q = 0; q < kSNq; ++q) {
-            w.x += c_cheb[q][c] * rho[q].x;
-            w.y += c_cheb[q][c] * rho[q].y;
-        }
         const double2 ph = expi(-dl * tp);
-        w = cmul(w, ph);
-        acc = cadd(acc, cmul(Bs[(long long)k * kNsing + i], make_double2(h * w.x, h * w.y)));
+#pragma unroll
+        for (int c = 0; c < kSNq; ++c) {
+            double2 w = make_double2(0.0, 0.0);
+            for (int q = 0; q < kSNq; ++q) {
+                w.x += c_cheb[q][c] * rho[q].x;
+                w.y += c_cheb[q][c] * rho[q].y;
+            }
+            w = cmul(w, ph);
+            acc[c] = cadd(acc[c], cmul(Bs[(long long)k * kNsing + i0 + c], make_double2(h * w.x, h * w.y)));
+        }
     }
-    Gr[(long long)(n + i) * n_T + it] = acc.x / kPi;
-    Gm[(long long)(n + i) * n_T + it] = -acc.y / kPi;
+    for (int c = 0; c < kSNq; ++c) {
+        Gr[(long long)(n + i0 + c) * n_T + it] = acc[c].x / kPi;
+        Gm[(long long)(n + i0 + c) * n_T + it] = -acc[c].y / kPi;
+    }
 }
 
 // V' = [V rows j_c .. J-1 ; Vs rows 0 .. 23]
@@ -500,7 +508,7 @@ extern "C" fh_status fh_synthesize_sing(int J, double W, int j_c, int K, const d
         smooth_weights_kernel<<<n_T, 256, smem, st>>>(n, L, A, P, delta, K, d_s,
                                                       reinterpret_cast<const double2 *>(d_B), J, j_c, E, d_T, n_T,
                                                       Gr, Gm);
-        fcc_weights_kernel<<<dim3(grid_of(n_T, 128), kNsing), 128, 0, st>>>(
+        fcc_weights_kernel<<<dim3(grid_of(n_T, 64), kSM - 1), 64, 0, st>>>(   // 3 n_T / 64 CTAs
             n, K, d_s, reinterpret_cast<const double2 *>(d_Bs), d_T, n_T, Gr, Gm);
         stack_fields_kernel<<<dim3(grid_of(n_x, 128), ns), 128, 0, st>>>(
             n, n_x, j_c, reinterpret_cast<const double2 *>(d_V), reinterpret_cast<const double2 *>(d_Vs), Vp);
