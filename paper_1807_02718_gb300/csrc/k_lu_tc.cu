@@ -342,6 +342,8 @@ __global__ void __launch_bounds__(kThreads, 1) lu_factor_tc_kernel(
     // second's pivots (32 x 32), kept in the A space between the updates
     float2 (*lpq)[NB + 2] = reinterpret_cast<float2 (*)[NB + 2]>(sA);
     static_assert(NB * (NB + 2) * 8 <= LT::kASpace, "the pair's L block fits the A space");
+    static_assert(NB * (NB + 2) * 8 <= LT::kASpace && (NB * (NB + 2)) % 2 == 0,
+                  "the pivot-row table of the checked-pivot panel fits the A space as whole float4s");
 
     const int cs = kMulti ? cs_arg : 1;
     const int rank = kMulti ? (int)cg::this_cluster().block_rank() : 0;
