@@ -300,7 +300,10 @@ fh_status fh_sing_frequencies(double omega_c, double *out);
  * (eq. approx) of the FC(Gram) Fourier continuation (Remark Fourier-FC; d = 6
  * matching and C = 31 continuation points) of the samples at omega_j, j =
  * j_c .. J-1; the singular piece on (0, w_c] is the Filon-Clenshaw-Curtis rule
- * on the points of fh_sing_frequencies(w_c).
+ * on the points of fh_sing_frequencies(w_c).  The smooth piece's sums over the
+ * continuation run in compensated double-float on the FP32 pipe, everything
+ * else in FP64: u agrees with the FP64 oracle's split synthesis to ~1e-10
+ * relative (measured 8.8e-11 on a small kite, 1.1e-12 on the circle).
  *   J, W       uniform mesh omega_j = j W/(J-1); n = J - j_c >= 12 and n + 31 even
  *   j_c        index of w_c (>= 1)
  *   K, d_s     window centres (device, K doubles)
